@@ -1,0 +1,203 @@
+"""ctypes wrapper of the C oracle (``qaoa_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by ``__graft_entry__.smoke``
+and by the CPU-baseline leg of ``bench.py``.  The CUDA library never imports
+it.  ``build()`` compiles the C file with gcc (OpenMP when available) into
+``oracle/_build/liboracle.so``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qaoa_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+
+MIXER_X = 0
+MIXER_RING = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle; returns the path of the shared library."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    base = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    try:
+        subprocess.run(base[:4] + ["-fopenmp"] + base[4:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "oracle_set_threads": (None, [i32]),
+            "oracle_get_threads": (i32, []),
+            "oracle_dicke_states": (i64, [i32, i32, P]),
+            "oracle_cost_maxcut": (None, [i32, i32, P, P, i64, P, P]),
+            "oracle_cost_sk": (None, [i32, P, i64, P, P]),
+            "oracle_cost_dks": (None, [i32, i32, P, i64, P, P]),
+            "oracle_qaoa_state": (i32, [i32, i32, i64, P, P, i32, P, P, P]),
+            "oracle_qaoa_expectation": (f64, [i32, i32, i64, P, P, i32, P, P]),
+            "oracle_qaoa_gradient": (i32, [i32, i32, i64, P, P, i32, P, P, P, P]),
+            "oracle_mixer_apply": (i32, [i32, i32, i64, P, f64, P]),
+            "oracle_hm_apply": (i32, [i32, i32, i64, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _c128(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def set_threads(t: int) -> None:
+    _load().oracle_set_threads(int(t))
+
+
+def get_threads() -> int:
+    return int(_load().oracle_get_threads())
+
+
+def dicke_states(n: int, k: int) -> np.ndarray:
+    lib = _load()
+    cnt = lib.oracle_dicke_states(n, k, None)
+    out = np.empty(cnt, dtype=np.uint64)
+    lib.oracle_dicke_states(n, k, _ptr(out))
+    return out
+
+
+def _states_dim(n, states):
+    if states is None:
+        return 1 << n, None
+    states = np.ascontiguousarray(states, dtype=np.uint64)
+    return states.shape[0], states
+
+
+def cost_maxcut(n, edges, weights=None, states=None) -> np.ndarray:
+    dim, states = _states_dim(n, states)
+    e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+    w = _f64(weights)
+    out = np.empty(dim, dtype=np.float64)
+    _load().oracle_cost_maxcut(n, e.shape[0], _ptr(e), _ptr(w), dim, _ptr(states), _ptr(out))
+    return out
+
+
+def cost_sk(n, J, states=None) -> np.ndarray:
+    dim, states = _states_dim(n, states)
+    Jd = _f64(np.asarray(J)).reshape(n, n)
+    out = np.empty(dim, dtype=np.float64)
+    _load().oracle_cost_sk(n, _ptr(Jd), dim, _ptr(states), _ptr(out))
+    return out
+
+
+def cost_dks(n, edges, states) -> np.ndarray:
+    dim, states = _states_dim(n, states)
+    e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+    out = np.empty(dim, dtype=np.float64)
+    _load().oracle_cost_dks(n, e.shape[0], _ptr(e), dim, _ptr(states), _ptr(out))
+    return out
+
+
+def _problem(mixer, n, cost, states):
+    kind = {"x": MIXER_X, "ring": MIXER_RING}[mixer]
+    cost = _f64(cost)
+    if kind == MIXER_RING:
+        if states is None:
+            raise ValueError("the ring mixer needs the feasible states")
+        states = np.ascontiguousarray(states, dtype=np.uint64)
+    else:
+        states = None
+    return kind, cost, states, cost.shape[0]
+
+
+def qaoa_state(n, cost, angles, mixer="x", states=None, psi0=None) -> np.ndarray:
+    kind, cost, states, dim = _problem(mixer, n, cost, states)
+    a = _f64(angles)
+    p = a.shape[0] // 2
+    out = np.empty(dim, dtype=np.complex128)
+    r = _load().oracle_qaoa_state(kind, n, dim, _ptr(states), _ptr(cost), p, _ptr(a),
+                                  _ptr(_c128(psi0)), _ptr(out))
+    if r:
+        raise RuntimeError(f"oracle_qaoa_state failed ({r})")
+    return out
+
+
+def qaoa_expectation(n, cost, angles, mixer="x", states=None, psi0=None) -> float:
+    kind, cost, states, dim = _problem(mixer, n, cost, states)
+    a = _f64(angles)
+    p = a.shape[0] // 2
+    e = _load().oracle_qaoa_expectation(kind, n, dim, _ptr(states), _ptr(cost), p, _ptr(a),
+                                        _ptr(_c128(psi0)))
+    if not np.isfinite(e):
+        raise RuntimeError("oracle_qaoa_expectation failed")
+    return float(e)
+
+
+def qaoa_gradient(n, cost, angles, mixer="x", states=None, psi0=None):
+    """Returns (E, grad[2p]) by exact reverse mode in complex128."""
+    kind, cost, states, dim = _problem(mixer, n, cost, states)
+    a = _f64(angles)
+    p = a.shape[0] // 2
+    E = np.zeros(1)
+    g = np.zeros(2 * p)
+    r = _load().oracle_qaoa_gradient(kind, n, dim, _ptr(states), _ptr(cost), p, _ptr(a),
+                                     _ptr(_c128(psi0)), _ptr(E), _ptr(g))
+    if r:
+        raise RuntimeError(f"oracle_qaoa_gradient failed ({r})")
+    return float(E[0]), g
+
+
+def mixer_apply(n, psi, beta, mixer="x", states=None) -> np.ndarray:
+    kind = {"x": MIXER_X, "ring": MIXER_RING}[mixer]
+    v = _c128(psi).copy()
+    st = None if states is None else np.ascontiguousarray(states, dtype=np.uint64)
+    r = _load().oracle_mixer_apply(kind, n, v.shape[0], _ptr(st), float(beta), _ptr(v))
+    if r:
+        raise RuntimeError(f"oracle_mixer_apply failed ({r})")
+    return v
+
+
+def hm_apply(n, psi, mixer="x", states=None) -> np.ndarray:
+    kind = {"x": MIXER_X, "ring": MIXER_RING}[mixer]
+    v = _c128(psi)
+    st = None if states is None else np.ascontiguousarray(states, dtype=np.uint64)
+    out = np.empty_like(v)
+    r = _load().oracle_hm_apply(kind, n, v.shape[0], _ptr(st), _ptr(v), _ptr(out))
+    if r:
+        raise RuntimeError(f"oracle_hm_apply failed ({r})")
+    return out

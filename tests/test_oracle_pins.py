@@ -1,0 +1,416 @@
+"""Pins of the CPU oracle against facts that do not reuse its arithmetic.
+
+Each test names what fixes the expected value: a dense matrix exponential
+built from Pauli matrices, the Hadamard-diagonal identity of Eq. 2, the p=1
+MaxCut closed form, sum rules of the cost functions, symmetries of Eq. 1,
+the free-fermion spectrum of the ring mixer, or finite differences.  The
+paper prints no numerical value for any worked example, so there is no
+printed number to pin against.
+"""
+
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from qaoa_inputs import erdos_renyi, random_regular3, sk_couplings
+
+# ----------------------------------------------------------------- helpers
+
+PX = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+PY = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+P1 = np.eye(2, dtype=np.complex128)
+
+
+def pauli_op(n, ops):
+    """Dense 2^n x 2^n tensor product; ops maps qubit -> 2x2; qubit i is bit i
+    of the basis index (the kron's last factor is qubit 0)."""
+    out = np.array([[1.0 + 0j]])
+    for q in reversed(range(n)):
+        out = np.kron(out, ops.get(q, P1))
+    return out
+
+
+def dense_x_mixer(n):
+    return sum(pauli_op(n, {i: PX}) for i in range(n))
+
+
+def dense_ring_mixer(n):
+    H = 0
+    for i in range(n):
+        j = (i + 1) % n
+        H = H + pauli_op(n, {i: PX, j: PX}) + pauli_op(n, {i: PY, j: PY})
+    return H
+
+
+def bits_matrix(n, xs=None):
+    xs = np.arange(1 << n, dtype=np.int64) if xs is None else np.asarray(xs, dtype=np.int64)
+    return ((xs[:, None] >> np.arange(n)[None, :]) & 1).astype(np.int64)
+
+
+def dense_qaoa_state(H_M, cost, angles, psi0):
+    p = len(angles) // 2
+    v = psi0.astype(np.complex128)
+    for k in range(p):
+        v = np.exp(-1j * angles[p + k] * cost) * v
+        v = sla.expm(-1j * angles[k] * H_M) @ v
+    return v
+
+
+# --------------------------------------------------------- feasible states
+
+@pytest.mark.parametrize("n,k", [(1, 0), (4, 2), (6, 3), (8, 4), (10, 1), (12, 12)])
+def test_dicke_states(oracle_mod, n, k):
+    s = oracle_mod.dicke_states(n, k)
+    assert s.shape[0] == math.comb(n, k)
+    assert np.all(np.diff(s.astype(np.int64)) > 0)
+    assert all(bin(int(x)).count("1") == k for x in s)
+    assert np.all(s < (1 << n))
+
+
+# ------------------------------------------------------------ cost vectors
+
+@pytest.mark.parametrize("n,seed", [(3, 1), (7, 2), (10, 3), (12, 4)])
+def test_maxcut_cost_matrix_form(oracle_mod, n, seed):
+    """Cut size = sum over edges of (1 - z_u z_v)/2 with z = 1 - 2x; checked
+    as a matrix expression and against the sum rule mean = |E|/2."""
+    e = erdos_renyi(n, 0.5, seed)
+    c = oracle_mod.cost_maxcut(n, e)
+    z = 1 - 2 * bits_matrix(n)
+    A = np.zeros((n, n))
+    A[e[:, 0], e[:, 1]] = 1
+    ref = 0.5 * (A.sum() - np.einsum("xi,ij,xj->x", z, A, z))
+    np.testing.assert_array_equal(c, ref)
+    assert c.mean() == pytest.approx(len(e) / 2, abs=1e-12)
+    # complement symmetry: flipping every bit keeps the cut
+    np.testing.assert_array_equal(c, c[::-1])
+
+
+def test_weighted_maxcut(oracle_mod):
+    n = 6
+    e = erdos_renyi(n, 0.6, 9)
+    w = np.linspace(0.5, 2.0, len(e))
+    c = oracle_mod.cost_maxcut(n, e, weights=w)
+    assert c.mean() == pytest.approx(w.sum() / 2, abs=1e-12)
+    assert c.max() <= w.sum() + 1e-12
+
+
+@pytest.mark.parametrize("n,seed", [(2, 5), (6, 6), (11, 7)])
+def test_sk_cost_quadratic_form(oracle_mod, n, seed):
+    """C = z^T J z / 2 for symmetric zero-diagonal J; mean over all x is 0,
+    global spin flip leaves C unchanged."""
+    J = sk_couplings(n, seed).astype(np.float64)
+    c = oracle_mod.cost_sk(n, J)
+    z = (1 - 2 * bits_matrix(n)).astype(np.float64)
+    ref = 0.5 * np.einsum("xi,ij,xj->x", z, J, z)
+    np.testing.assert_allclose(c, ref, rtol=0, atol=1e-12)
+    assert abs(c.mean()) < 1e-12
+    np.testing.assert_allclose(c, c[::-1], atol=1e-12)
+
+
+def test_sk_cost_exact_in_float64(oracle_mod):
+    """Couplings on the 2^-20 grid make every C(x) a multiple of 2^-20, so
+    the float64 sums carry no rounding at all."""
+    n = 14
+    J = sk_couplings(n, 11).astype(np.float64)
+    assert np.all(J * 2**20 == np.rint(J * 2**20))
+    c = oracle_mod.cost_sk(n, J)
+    assert np.all(c * 2**20 == np.rint(c * 2**20))
+
+
+@pytest.mark.parametrize("n,k,seed", [(6, 3, 1), (8, 4, 2), (10, 5, 3)])
+def test_dks_cost(oracle_mod, n, k, seed):
+    """Induced edge count = x^T A x on Dicke states; mean over the weight-k
+    set is |E| k(k-1) / (n(n-1))."""
+    e = erdos_renyi(n, 0.5, seed)
+    s = oracle_mod.dicke_states(n, k)
+    c = oracle_mod.cost_dks(n, e, s)
+    x = bits_matrix(n, s.astype(np.int64))
+    A = np.zeros((n, n))
+    A[e[:, 0], e[:, 1]] = 1
+    np.testing.assert_array_equal(c, np.einsum("xi,ij,xj->x", x, A, x))
+    assert c.mean() == pytest.approx(len(e) * k * (k - 1) / (n * (n - 1)), abs=1e-12)
+
+
+# ------------------------------------------------- mixer operators, Eq. 2
+
+@pytest.mark.parametrize("n", [1, 2, 5, 8])
+def test_x_mixer_hadamard_form(oracle_mod, n):
+    """Eq. 2: e^{-i b sum X_i} = H^n diag(e^{-i b (n - 2|x|)}) H^n."""
+    rng = np.random.default_rng(n)
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    beta = 0.731
+    Hn = sla.hadamard(1 << n) / math.sqrt(1 << n)
+    w = bits_matrix(n).sum(axis=1)
+    ref = Hn @ (np.exp(-1j * beta * (n - 2 * w)) * (Hn @ v))
+    np.testing.assert_allclose(oracle_mod.mixer_apply(n, v, beta), ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 3, 6])
+def test_x_hm_matches_pauli_sum(oracle_mod, n):
+    rng = np.random.default_rng(10 + n)
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    np.testing.assert_allclose(oracle_mod.hm_apply(n, v), dense_x_mixer(n) @ v, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,k", [(3, 1), (4, 2), (6, 3), (7, 2), (8, 4)])
+def test_ring_hm_matches_pauli_sum(oracle_mod, n, k):
+    """Ring H_M built from Pauli X, Y on the full 2^n space, restricted to the
+    weight-k states, equals the oracle's bit-swap form, and the full operator
+    does not leak out of the weight-k subspace."""
+    s = oracle_mod.dicke_states(n, k).astype(np.int64)
+    Hf = dense_ring_mixer(n)
+    mask = np.zeros(1 << n, bool)
+    mask[s] = True
+    assert np.abs(Hf[np.ix_(~mask, mask)]).max() == 0
+    D = len(s)
+    Hs = np.stack([oracle_mod.hm_apply(n, np.eye(D)[i], "ring", s) for i in range(D)], axis=1)
+    np.testing.assert_allclose(Hs, Hf[np.ix_(s, s)], atol=1e-12)
+
+
+def free_fermion_ring_spectrum(n, k):
+    """Jordan-Wigner: the XY ring is free hopping with amplitude 2, single
+    particle energies 4 cos(2 pi (m + s)/n), s = 0 for odd k (periodic),
+    s = 1/2 for even k (antiperiodic); many-body levels sum k distinct modes."""
+    s = 0.0 if k % 2 else 0.5
+    eps = [4 * math.cos(2 * math.pi * (m + s) / n) for m in range(n)]
+    return np.sort([sum(c) for c in itertools.combinations(eps, k)])
+
+
+@pytest.mark.parametrize("n,k", [(4, 2), (5, 2), (6, 3), (7, 3), (8, 4), (9, 4)])
+def test_ring_spectrum_free_fermions(oracle_mod, n, k):
+    s = oracle_mod.dicke_states(n, k)
+    D = len(s)
+    Hs = np.stack([oracle_mod.hm_apply(n, np.eye(D)[i], "ring", s) for i in range(D)], axis=1)
+    np.testing.assert_allclose(Hs, Hs.conj().T, atol=0)
+    ev = np.linalg.eigvalsh(Hs)
+    np.testing.assert_allclose(ev, free_fermion_ring_spectrum(n, k), atol=1e-10)
+    assert np.trace(Hs).real == pytest.approx(0, abs=1e-12)
+    assert np.trace(Hs @ Hs).real == pytest.approx(8 * n * math.comb(n - 2, k - 1), rel=1e-12)
+
+
+@pytest.mark.parametrize("n,k,beta", [(6, 3, 0.4), (8, 4, 2.9), (7, 3, -1.3)])
+def test_ring_mixer_exponential(oracle_mod, n, k, beta):
+    """The oracle's series for e^{-i beta H} equals scipy's expm of the
+    Pauli-built, restricted ring Hamiltonian."""
+    s = oracle_mod.dicke_states(n, k).astype(np.int64)
+    Hs = dense_ring_mixer(n)[np.ix_(s, s)]
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(len(s)) + 1j * rng.standard_normal(len(s))
+    ref = sla.expm(-1j * beta * Hs) @ v
+    got = oracle_mod.mixer_apply(n, v, beta, "ring", s)
+    np.testing.assert_allclose(got, ref, atol=1e-11 * np.abs(v).max())
+
+
+# -------------------------------------------------------- QAOA state, Eq. 1
+
+@pytest.mark.parametrize("n,p,seed", [(1, 1, 1), (3, 2, 2), (5, 3, 3), (8, 2, 4)])
+def test_x_state_vs_dense_expm(oracle_mod, n, p, seed):
+    e = erdos_renyi(n, 0.5, seed) if n > 1 else np.zeros((0, 2), np.int32)
+    cost = oracle_mod.cost_maxcut(n, e)
+    ang = np.random.default_rng(seed).random(2 * p) * np.pi
+    psi0 = np.full(1 << n, 2 ** (-n / 2), dtype=np.complex128)
+    ref = dense_qaoa_state(dense_x_mixer(n), cost, ang, psi0)
+    got = oracle_mod.qaoa_state(n, cost, ang)
+    np.testing.assert_allclose(got, ref, atol=1e-12)
+    E = oracle_mod.qaoa_expectation(n, cost, ang)
+    assert E == pytest.approx(float(np.real(ref.conj() @ (cost * ref))), abs=1e-12)
+
+
+def test_x_state_custom_initial_state(oracle_mod):
+    """Warm start (Sec. 3, initial_state): an arbitrary normalised psi_0."""
+    n, p = 6, 3
+    J = sk_couplings(n, 21).astype(np.float64)
+    cost = oracle_mod.cost_sk(n, J)
+    rng = np.random.default_rng(22)
+    psi0 = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    ang = rng.random(2 * p) * np.pi
+    ref = dense_qaoa_state(dense_x_mixer(n), cost, ang, psi0)
+    np.testing.assert_allclose(oracle_mod.qaoa_state(n, cost, ang, psi0=psi0), ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,k,p", [(6, 3, 3), (8, 4, 2), (7, 2, 2)])
+def test_ring_state_vs_dense_expm(oracle_mod, n, k, p):
+    """Densest k-subgraph with the ring mixer from the uniform Dicke state
+    (Sec. 2.1, Listing 2, default initial state of Sec. 3)."""
+    e = erdos_renyi(n, 0.5, 40 + n)
+    s = oracle_mod.dicke_states(n, k)
+    cost = oracle_mod.cost_dks(n, e, s)
+    Hs = dense_ring_mixer(n)[np.ix_(s.astype(np.int64), s.astype(np.int64))]
+    ang = np.random.default_rng(n + k).random(2 * p) * np.pi
+    psi0 = np.full(len(s), 1 / math.sqrt(len(s)), dtype=np.complex128)
+    ref = dense_qaoa_state(Hs, cost, ang, psi0)
+    got = oracle_mod.qaoa_state(n, cost, ang, "ring", s)
+    np.testing.assert_allclose(got, ref, atol=1e-11)
+
+
+def maxcut_p1_closed_form(n, edges, beta, gamma):
+    """p=1 MaxCut expectation for any graph (Wang, Hadfield, Jiang, Rieffel,
+    PRA 97, 022304 (2018), Theorem 1), phase e^{-i gamma C} then mixer
+    e^{-i beta sum X}: per edge (u,v) with d = deg u - 1, e = deg v - 1 and
+    f triangles through (u,v),
+    <C_uv> = 1/2 + 1/4 sin 4b sin g (cos^d g + cos^e g)
+                 - 1/4 sin^2 2b cos^(d+e-2f) g (1 - cos^f 2g)."""
+    adj = [set() for _ in range(n)]
+    for u, v in edges:
+        adj[u].add(v)
+        adj[v].add(u)
+    tot = 0.0
+    for u, v in edges:
+        d, e = len(adj[u]) - 1, len(adj[v]) - 1
+        f = len(adj[u] & adj[v])
+        cg = math.cos(gamma)
+        tot += (0.5 + 0.25 * math.sin(4 * beta) * math.sin(gamma) * (cg**d + cg**e)
+                - 0.25 * math.sin(2 * beta) ** 2 * cg ** (d + e - 2 * f)
+                * (1 - math.cos(2 * gamma) ** f))
+    return tot
+
+
+@pytest.mark.parametrize("graph", ["er7", "er10", "3reg12", "k5", "er12"])
+def test_p1_maxcut_closed_form(oracle_mod, graph):
+    if graph == "er7":
+        n, e = 7, erdos_renyi(7, 0.5, 1)
+    elif graph == "er10":
+        n, e = 10, erdos_renyi(10, 0.4, 2)
+    elif graph == "er12":
+        n, e = 12, erdos_renyi(12, 0.5, 3)
+    elif graph == "3reg12":
+        n, e = 12, random_regular3(12, 4)
+    else:
+        n = 5
+        e = np.array(list(itertools.combinations(range(5), 2)), dtype=np.int32)
+    cost = oracle_mod.cost_maxcut(n, e)
+    for beta, gamma in [(0.37, 0.81), (1.1, -0.4), (2.5, 2.0), (0.0, 1.3)]:
+        E = oracle_mod.qaoa_expectation(n, cost, [beta, gamma])
+        assert E == pytest.approx(maxcut_p1_closed_form(n, e, beta, gamma), abs=1e-12)
+
+
+# ------------------------------------------------------------- invariants
+
+def test_invariants_x_mixer(oracle_mod):
+    n, p = 9, 4
+    e = erdos_renyi(n, 0.5, 77)
+    cost = oracle_mod.cost_maxcut(n, e)
+    rng = np.random.default_rng(5)
+    ang = rng.random(2 * p) * np.pi
+    psi = oracle_mod.qaoa_state(n, cost, ang)
+    assert np.linalg.norm(psi) == pytest.approx(1, abs=1e-13)
+    E = oracle_mod.qaoa_expectation(n, cost, ang)
+    mean = len(e) / 2
+    assert oracle_mod.qaoa_expectation(n, cost, np.zeros(2 * p)) == pytest.approx(mean, abs=1e-12)
+    # beta = 0: phases alone leave |psi|^2 uniform; gamma = 0: |+> is an X eigenstate
+    a = ang.copy(); a[:p] = 0
+    assert oracle_mod.qaoa_expectation(n, cost, a) == pytest.approx(mean, abs=1e-12)
+    a = ang.copy(); a[p:] = 0
+    assert oracle_mod.qaoa_expectation(n, cost, a) == pytest.approx(mean, abs=1e-12)
+    # real C, real H_M, real psi_0: E(-b,-g) = E(b,g) but E(b,-g) differs
+    assert oracle_mod.qaoa_expectation(n, cost, -ang) == pytest.approx(E, abs=1e-12)
+    a = ang.copy(); a[p:] *= -1
+    assert abs(oracle_mod.qaoa_expectation(n, cost, a) - E) > 1e-3
+    # e^{-i pi X} = -I: beta period pi; integer C: gamma period 2 pi
+    a = ang.copy(); a[1] += np.pi
+    assert oracle_mod.qaoa_expectation(n, cost, a) == pytest.approx(E, abs=1e-12)
+    a = ang.copy(); a[p + 2] += 2 * np.pi
+    assert oracle_mod.qaoa_expectation(n, cost, a) == pytest.approx(E, abs=1e-12)
+    # the round order matters: swapping two rounds changes E
+    a = ang.copy(); a[[0, 1]] = a[[1, 0]]; a[[p, p + 1]] = a[[p + 1, p]]
+    assert abs(oracle_mod.qaoa_expectation(n, cost, a) - E) > 1e-6
+
+
+def test_invariants_ring_mixer(oracle_mod):
+    n, k, p = 8, 4, 3
+    e = erdos_renyi(n, 0.5, 8)
+    s = oracle_mod.dicke_states(n, k)
+    cost = oracle_mod.cost_dks(n, e, s)
+    ang = np.random.default_rng(9).random(2 * p) * np.pi
+    psi = oracle_mod.qaoa_state(n, cost, ang, "ring", s)
+    assert np.linalg.norm(psi) == pytest.approx(1, abs=1e-12)
+    mean = cost.mean()
+    assert oracle_mod.qaoa_expectation(n, cost, np.zeros(2 * p), "ring", s) == pytest.approx(mean, abs=1e-12)
+    E = oracle_mod.qaoa_expectation(n, cost, ang, "ring", s)
+    assert oracle_mod.qaoa_expectation(n, cost, -ang, "ring", s) == pytest.approx(E, abs=1e-11)
+
+
+# --------------------------------------------------------------- gradient
+
+def richardson_fd(f, x, h=1e-3):
+    """Central differences at h and h/2 combined to cancel the h^2 term."""
+    g = np.zeros_like(x)
+    for i in range(len(x)):
+        def d(hh):
+            ep = np.zeros_like(x); ep[i] = hh
+            return (f(x + ep) - f(x - ep)) / (2 * hh)
+        g[i] = (4 * d(h / 2) - d(h)) / 3
+    return g
+
+
+@pytest.mark.parametrize("case", ["maxcut_x", "sk_x", "dks_ring", "warm_x"])
+def test_gradient_vs_finite_differences(oracle_mod, case):
+    rng = np.random.default_rng({"maxcut_x": 1, "sk_x": 2, "dks_ring": 3, "warm_x": 4}[case])
+    psi0 = None
+    if case == "maxcut_x":
+        n, p, mix, st = 7, 3, "x", None
+        cost = oracle_mod.cost_maxcut(n, erdos_renyi(n, 0.5, 3))
+    elif case == "sk_x":
+        n, p, mix, st = 6, 4, "x", None
+        cost = oracle_mod.cost_sk(n, sk_couplings(n, 4).astype(np.float64))
+    elif case == "warm_x":
+        n, p, mix, st = 5, 2, "x", None
+        cost = oracle_mod.cost_maxcut(n, erdos_renyi(n, 0.7, 5))
+        psi0 = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+        psi0 /= np.linalg.norm(psi0)
+    else:
+        n, k, p, mix = 7, 3, 2, "ring"
+        st = oracle_mod.dicke_states(n, k)
+        cost = oracle_mod.cost_dks(n, erdos_renyi(n, 0.5, 6), st)
+    ang = rng.random(2 * p) * np.pi
+    E, g = oracle_mod.qaoa_gradient(n, cost, ang, mix, st, psi0)
+    assert E == pytest.approx(oracle_mod.qaoa_expectation(n, cost, ang, mix, st, psi0), abs=1e-12)
+    fd = richardson_fd(lambda a: oracle_mod.qaoa_expectation(n, cost, a, mix, st, psi0), ang)
+    np.testing.assert_allclose(g, fd, atol=1e-8 * max(1.0, np.abs(g).max()))
+    if psi0 is None:
+        # real C, H_M and psi_0: E is even in the angles, the gradient odd
+        _, gm = oracle_mod.qaoa_gradient(n, cost, -ang, mix, st, psi0)
+        np.testing.assert_allclose(gm, -g, atol=1e-10)
+
+
+def test_gradient_zero_at_zero_angles(oracle_mod):
+    """At zero angles psi_0 = |+>^n is an eigenvector of sum X_i and of no
+    phase, so both partial derivatives vanish."""
+    n, p = 8, 3
+    cost = oracle_mod.cost_sk(n, sk_couplings(n, 31).astype(np.float64))
+    E, g = oracle_mod.qaoa_gradient(n, cost, np.zeros(2 * p))
+    assert E == pytest.approx(cost.mean(), abs=1e-12)
+    np.testing.assert_allclose(g, 0, atol=1e-12)
+
+
+def test_gradient_p1_closed_form(oracle_mod):
+    """d<C>/d(beta, gamma) of the p=1 closed form, by central differences of
+    the closed form itself."""
+    n = 8
+    e = erdos_renyi(n, 0.5, 12)
+    cost = oracle_mod.cost_maxcut(n, e)
+    b, gm = 0.61, 1.27
+    _, g = oracle_mod.qaoa_gradient(n, cost, [b, gm])
+    h = 1e-5
+    db = (maxcut_p1_closed_form(n, e, b + h, gm) - maxcut_p1_closed_form(n, e, b - h, gm)) / (2 * h)
+    dg = (maxcut_p1_closed_form(n, e, b, gm + h) - maxcut_p1_closed_form(n, e, b, gm - h)) / (2 * h)
+    np.testing.assert_allclose(g, [db, dg], atol=1e-8)
+
+
+# ------------------------------------------------------- input generators
+
+def test_generators():
+    e = random_regular3(20, 3)
+    deg = np.bincount(e.ravel(), minlength=20)
+    assert np.all(deg == 3) and len({tuple(r) for r in e}) == 30
+    assert np.all(e[:, 0] < e[:, 1])
+    e2 = erdos_renyi(30, 0.3, 1)
+    assert 0.2 < len(e2) / (30 * 29 / 2) < 0.4
+    np.testing.assert_array_equal(erdos_renyi(12, 0.5, 7), erdos_renyi(12, 0.5, 7))
+    J = sk_couplings(10, 2)
+    assert J.dtype == np.float32 and np.all(J == J.T) and np.all(np.diag(J) == 0)
+    assert np.all(J.astype(np.float64) * 2**20 == np.rint(J.astype(np.float64) * 2**20))
