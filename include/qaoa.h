@@ -1,0 +1,251 @@
+/*
+ * qaoa.h -- C ABI of the GB300 (sm_103a) QAOA statevector library.
+ *
+ * The library evaluates the p-round QAOA expectation of arXiv 2312.06451
+ * (JuliQAOA), Eq. 1,
+ *
+ *     |beta,gamma> = e^{-i b_p H_M} e^{-i g_p H_C} ... e^{-i b_1 H_M} e^{-i g_1 H_C} |psi_0>,
+ *     <C>          = <beta,gamma| C |beta,gamma>                        (Sec. 1)
+ *
+ * over a cost vector C(x) precomputed on the feasible set (Sec. 2.1), with
+ * either the transverse-field mixer H_M = sum_i X_i applied as per-qubit
+ * rotations (Sec. 2.1 Eq. 2, Sec. 2.2) or a constrained mixer applied through
+ * a stored eigendecomposition H_M = V D V^-1 (Sec. 2.1, Sec. 2.2), and the
+ * gradient of <C> with respect to all 2p angles (Sec. 2.3, Sec. 4).
+ *
+ * Conventions shared by every call
+ *   - Qubit i is bit i of the basis-state index x (bit 0 = least significant).
+ *   - A state is an array of complex64 amplitudes stored as interleaved
+ *     float pairs (re, im), one per feasible basis state, in increasing x.
+ *   - Angles are float64 in the order of Listing 1:
+ *     [beta_1, ..., beta_p, gamma_1, ..., gamma_p]; gradients use the same order.
+ *   - Round k applies the phase separator with gamma_k first, then the mixer
+ *     with beta_k (Eq. 1).
+ *   - The default initial state is the uniform superposition over the feasible
+ *     set: 2^{-n/2} on all 2^n states, or 1/sqrt(D) on the D Hamming-weight-k
+ *     states (Sec. 3, default of simulate()).
+ *   - To minimise instead of maximise, negate the cost vector (Sec. 3).
+ *
+ * Memory ownership
+ *   Pointers named d_* are device memory owned by the caller; the library never
+ *   frees or retains them past the call.  Pointers without the prefix are host
+ *   memory.  Scratch (work states, per-round checkpoints, reduction partials,
+ *   launch descriptors) belongs to the context: it is allocated on first need,
+ *   grown when a larger problem arrives, reused across calls (Sec. 2.2: memory
+ *   is pre-allocated and re-used) and freed by qaoa_destroy().
+ *
+ * Errors
+ *   Every call returns a qaoa_status.  Nothing aborts, traps or prints.  On a
+ *   non-OK status, qaoa_last_error() gives a one-line description.  Arguments
+ *   are validated (sizes, dtypes, p >= 1, finite angles, a device-memory
+ *   estimate) before any kernel is launched.  A CUDA error from a launch or a
+ *   copy is reported as QAOA_ERR_CUDA with the CUDA error string.
+ *
+ * Streams
+ *   All work is issued on the stream given to qaoa_create().  Calls that take
+ *   host result pointers synchronise that stream before returning; the batched
+ *   call only enqueues work and writes device results, so it can be captured
+ *   into a CUDA graph by the caller after one warm-up call has sized the
+ *   context's scratch.
+ */
+#ifndef QAOA_GB300_H
+#define QAOA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QAOA_OK = 0,
+    QAOA_ERR_INVALID = 1,     /* bad argument (size, dtype, pointer, angle) */
+    QAOA_ERR_OOM = 2,         /* device memory for the scratch is not available */
+    QAOA_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    QAOA_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    QAOA_ERR_UNSUPPORTED = 5  /* valid request outside what this build implements */
+} qaoa_status;
+
+typedef struct qaoa_ctx qaoa_ctx;
+
+/* Cost-vector element types. */
+enum {
+    QAOA_COST_F32 = 0, /* float32 cost values */
+    QAOA_COST_U8 = 1   /* integer costs 0..255 stored as uint8 */
+};
+
+/* Built-in cost functions (Sec. 2.1 and Sec. 3).
+ *   MAXCUT : C(x) = #{edges (u,v) : x_u != x_v}                    (Listing 1)
+ *   WMAXCUT: C(x) = sum over edges of w_uv [x_u != x_v]
+ *   SK     : C(x) = sum_{i<j} J_ij z_i z_j, z_i = 1 - 2 x_i; an arbitrary user
+ *            cost, which the paper allows for any function of x (Sec. 3).
+ *   DKS    : densest k-subgraph, C(x) = #{edges (u,v) : x_u = x_v = 1} on the
+ *            Hamming-weight-k states (Sec. 2.1, Listing 2). */
+enum {
+    QAOA_PROBLEM_MAXCUT = 0,
+    QAOA_PROBLEM_WMAXCUT = 1,
+    QAOA_PROBLEM_SK = 2,
+    QAOA_PROBLEM_DKS = 3
+};
+
+/* Mixer kinds. */
+enum {
+    QAOA_MIXER_X = 0,    /* H_M = sum_i X_i on all 2^n states (Sec. 2.1, Eq. 2) */
+    QAOA_MIXER_EIGEN = 1 /* H_M = V diag(lambda) V^T on D feasible states (Sec. 2.1) */
+};
+
+/* Precision of the dense eigenbasis products for QAOA_MIXER_EIGEN. */
+enum {
+    QAOA_GEMM_FP32_SIMT = 0, /* complex64 CUDA-core products, fp32 accumulate */
+    QAOA_GEMM_3XTF32 = 1,    /* tensor cores, tf32 hi/lo split, 3 products */
+    QAOA_GEMM_BF16X3 = 2     /* tensor cores, bf16 hi/lo split, 3 products */
+};
+
+/* Problem description for qaoa_cost_precompute (all pointers host memory).
+ *   n      qubits (1..34 unconstrained, 2..40 constrained)
+ *   k      Hamming weight of the feasible states for DKS, else -1
+ *   m      edge count; edges holds 2m vertex indices (u_0, v_0, u_1, ...)
+ *   weights m float32 weights (WMAXCUT only)
+ *   J      n*n float32 row-major couplings (SK only; entries with i < j used) */
+typedef struct {
+    int kind;
+    int n;
+    int k;
+    int m;
+    const int32_t *edges;
+    const float *weights;
+    const float *J;
+} qaoa_problem;
+
+/* Mixer description.
+ *   kind   QAOA_MIXER_X or QAOA_MIXER_EIGEN
+ *   n      qubits
+ *   dim    feasible-set size: 2^n for X, D for EIGEN
+ *   d_V    EIGEN: D x D float32, row-major, real orthogonal eigenvectors as
+ *          columns (H_M V = V diag(lambda))
+ *   d_lambda EIGEN: D float64 eigenvalues
+ *   gemm_precision EIGEN: one of QAOA_GEMM_* */
+typedef struct {
+    int kind;
+    int n;
+    int64_t dim;
+    const float *d_V;
+    const double *d_lambda;
+    int gemm_precision;
+} qaoa_mixer;
+
+/* ------------------------------------------------------------- context */
+
+/* Create a context bound to CUDA device `device` and the stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The context owns all
+ * scratch memory and the error text. */
+qaoa_status qaoa_create(qaoa_ctx **ctx, int device, void *cuda_stream);
+
+/* Free every scratch allocation and the context.  NULL is ignored. */
+void qaoa_destroy(qaoa_ctx *ctx);
+
+/* Text of the last error on this context ("" if none).  Valid until the next
+ * call on the context. */
+const char *qaoa_last_error(const qaoa_ctx *ctx);
+
+/* Bytes of device scratch the context currently holds. */
+int64_t qaoa_scratch_bytes(const qaoa_ctx *ctx);
+
+/* ------------------------------------------------------- pre-computation */
+
+/* Cost vector over the feasible set (Sec. 2.1: C(x) is computed once, stored
+ * for every feasible x and re-used by every evaluation).
+ *   d_cost      device output, dim elements of cost_dtype
+ *   cost_dtype  QAOA_COST_U8 (integer costs; fails with QAOA_ERR_INVALID if a
+ *               value can exceed 255) or QAOA_COST_F32
+ *   dim         2^n for unconstrained problems, binom(n,k) for DKS
+ * SK with couplings on the 2^-20 grid (|J| < 8) is summed exactly in integers
+ * and rounded once to float32; other couplings are summed in float64. */
+qaoa_status qaoa_cost_precompute(qaoa_ctx *ctx, const qaoa_problem *prob, void *d_cost,
+                                 int cost_dtype, int64_t dim);
+
+/* The binom(n,k) Hamming-weight-k basis states in increasing integer order
+ * (Sec. 2.1 feasible subspace; Sec. 2.4 orders them as Gosper's hack does).
+ * d_states: device output, dim uint64 values. */
+qaoa_status qaoa_dicke_states(qaoa_ctx *ctx, int n, int k, uint64_t *d_states, int64_t dim);
+
+/* Dense ring mixer H_M = sum_i (X_i X_{i+1} + Y_i Y_{i+1}), ring read as
+ * periodic, restricted to the Hamming-weight-k states (Sec. 2.1), written
+ * row-major into d_H (dim x dim float64, device).  Its eigendecomposition
+ * gives the d_V / d_lambda of a QAOA_MIXER_EIGEN mixer. */
+qaoa_status qaoa_ring_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, int64_t dim);
+
+/* ----------------------------------------------------------- simulation */
+
+/* <C> of Eq. 1 for one angle set.
+ *   d_cost, cost_dtype  cost vector over the mixer's feasible set
+ *   d_init  device complex64 initial state (mixer->dim amplitudes) or NULL for
+ *           the uniform superposition (Sec. 3, initial_state)
+ *   p       rounds (>= 1); angles: host, 2p float64; E: host output.
+ * Synchronous on the context stream. */
+qaoa_status qaoa_expectation(qaoa_ctx *ctx, const void *d_cost, int cost_dtype,
+                             const qaoa_mixer *mixer, const void *d_init, int p,
+                             const double *angles, double *E);
+
+/* <C> and its 2p partial derivatives by one forward and one adjoint
+ * (reverse) sweep (Sec. 2.3, Sec. 4: the gradient for a constant multiple of
+ * one evaluation).  grad: host output, 2p float64 in the angle order.
+ *   ckpt  1 = keep the state at every round boundary in scratch and reload it
+ *         in the adjoint sweep; 0 = recover earlier states by undoing each
+ *         round (less memory, one more state write per round). */
+qaoa_status qaoa_gradient(qaoa_ctx *ctx, const void *d_cost, int cost_dtype,
+                          const qaoa_mixer *mixer, const void *d_init, int p,
+                          const double *angles, double *E, double *grad, int ckpt);
+
+/* One batched job: n_sets angle sets evaluated on one cost vector and mixer.
+ *   d_angles  device, n_sets x 2p float64 (row = one angle set)
+ *   d_E       device output, n_sets float64
+ *   d_grad    device output, n_sets x 2p float64 (ignored unless want_grad)
+ *   d_init    device initial state shared by all sets, or NULL */
+typedef struct {
+    const void *d_cost;
+    int cost_dtype;
+    const qaoa_mixer *mixer;
+    int p;
+    int n_sets;
+    const double *d_angles;
+    double *d_E;
+    double *d_grad;
+    const void *d_init;
+} qaoa_job;
+
+/* Many angle sets of many problem instances (of uneven size) in one enqueued
+ * sequence of launches, for the angle-finding outer loop (Sec. 2.3) that
+ * calls the simulator many times.  Asynchronous: results land in the jobs'
+ * device buffers when the context stream reaches them.  Scratch is sized by
+ * the first call with a given job list; after that the same call enqueues no
+ * allocation and may be captured in a CUDA graph.  Fails with QAOA_ERR_OOM
+ * before launching anything when the scratch would not fit. */
+qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *jobs,
+                                     int want_grad);
+
+/* ------------------------------------------------------------ measurement */
+
+/* Per-kernel-family launch statistics, collected when profiling is on: each
+ * launch is bracketed by CUDA events on the context stream and its algorithmic
+ * bytes (the bytes the method must move: state reads and writes and cost
+ * reads, no scratch) are added up. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+    double algo_bytes;
+} qaoa_kernel_stat;
+
+qaoa_status qaoa_set_profiling(qaoa_ctx *ctx, int enable);
+/* Fills up to max entries; returns the number of kernel families (or -1). */
+int qaoa_kernel_stats(qaoa_ctx *ctx, qaoa_kernel_stat *out, int max);
+void qaoa_reset_stats(qaoa_ctx *ctx);
+/* Kernel launches issued by this context since creation or the last reset. */
+int64_t qaoa_launch_count(const qaoa_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QAOA_GB300_H */

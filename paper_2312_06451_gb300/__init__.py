@@ -1,0 +1,265 @@
+"""GB300 (sm_103a) QAOA statevector simulation: Python binding of the C ABI.
+
+Every method below marshals arguments into one call of the C library declared
+in ``include/qaoa.h`` (same names without the ``qaoa_`` prefix on the context
+methods); all computation happens in the CUDA kernels.  PyTorch provides device
+memory and streams only.  There is no CPU fallback: without the built library
+or a CUDA device the calls raise.
+
+Conventions (arXiv 2312.06451, Eq. 1 and Listing 1): qubit i is bit i of the
+basis index, angles are ``[beta_1..beta_p, gamma_1..gamma_p]``, round k applies
+``e^{-i gamma_k C}`` then ``e^{-i beta_k H_M}``, the default initial state is the
+uniform superposition over the feasible set.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _binding as B
+from ._binding import QAOAError  # noqa: F401
+
+__all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError",
+           "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched"]
+
+_PROBLEMS = {"maxcut": B.QAOA_PROBLEM_MAXCUT, "wmaxcut": B.QAOA_PROBLEM_WMAXCUT,
+             "sk": B.QAOA_PROBLEM_SK, "dks": B.QAOA_PROBLEM_DKS}
+_GEMM = {"fp32": B.QAOA_GEMM_FP32_SIMT, "3xtf32": B.QAOA_GEMM_3XTF32, "bf16x3": B.QAOA_GEMM_BF16X3}
+
+
+def _cost_dtype(t: torch.Tensor) -> int:
+    if t.dtype == torch.uint8:
+        return B.QAOA_COST_U8
+    if t.dtype == torch.float32:
+        return B.QAOA_COST_F32
+    raise TypeError(f"cost vector must be uint8 or float32, got {t.dtype}")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_tensor(t, name):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    return t
+
+
+class XMixer:
+    """Transverse-field mixer H_M = sum_i X_i on all 2^n states (Eq. 2)."""
+
+    def __init__(self, n: int):
+        self.n = int(n)
+        self.dim = 1 << self.n
+        self.struct = B.QaoaMixer(B.QAOA_MIXER_X, self.n, self.dim, None, None, 0)
+
+
+class EigenMixer:
+    """Constrained mixer through its stored eigendecomposition H_M V = V diag(lam)
+    on the D feasible states (Sec. 2.1); V: D x D float32 CUDA tensor (columns
+    are eigenvectors), lam: D float64 CUDA tensor."""
+
+    def __init__(self, n: int, V: torch.Tensor, lam: torch.Tensor, precision: str = "3xtf32"):
+        V = _dev_tensor(V, "V")
+        lam = _dev_tensor(lam, "lam")
+        if V.dtype != torch.float32 or lam.dtype != torch.float64:
+            raise TypeError("V must be float32 and lam float64")
+        self.n = int(n)
+        self.dim = int(lam.shape[0])
+        self.V, self.lam = V, lam
+        self.struct = B.QaoaMixer(B.QAOA_MIXER_EIGEN, self.n, self.dim, V.data_ptr(), lam.data_ptr(),
+                                  _GEMM[precision])
+
+
+class Context:
+    """A library context bound to one device and one CUDA stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self._lib = B.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.device = int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        st = self._lib.qaoa_create(ctypes.byref(h), self.device, ctypes.c_void_p(self.stream.cuda_stream))
+        if st != B.QAOA_OK:
+            raise QAOAError(st, "qaoa_create failed")
+        self._h = h
+
+    # ------------------------------------------------------------ plumbing
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.qaoa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int):
+        if st != B.QAOA_OK:
+            msg = self._lib.qaoa_last_error(self._h)
+            raise QAOAError(st, msg.decode() if msg else "")
+
+    # ----------------------------------------------------- pre-computation
+    def cost_precompute(self, problem: str, n: int, *, edges=None, weights=None, J=None, k: int = -1,
+                        dtype: torch.dtype = torch.uint8) -> torch.Tensor:
+        """Cost vector over the feasible set as a new CUDA tensor (qaoa_cost_precompute)."""
+        kind = _PROBLEMS[problem]
+        e = None if edges is None else np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+        Jh = None if J is None else np.ascontiguousarray(J, dtype=np.float32).reshape(n, n)
+        m = 0 if e is None else e.shape[0]
+        if kind == B.QAOA_PROBLEM_DKS:
+            dim = int(np.round(np.prod([(n - i) / (i + 1) for i in range(k)]))) if k > 0 else 1
+        else:
+            dim = 1 << n
+        out = torch.empty(dim, dtype=dtype, device=f"cuda:{self.device}")
+        prob = B.QaoaProblem(kind, n, k, m,
+                             None if e is None else e.ctypes.data_as(ctypes.c_void_p),
+                             None if w is None else w.ctypes.data_as(ctypes.c_void_p),
+                             None if Jh is None else Jh.ctypes.data_as(ctypes.c_void_p))
+        self._check(self._lib.qaoa_cost_precompute(self._h, ctypes.byref(prob), _ptr(out),
+                                                   _cost_dtype(out), dim))
+        return out
+
+    def dicke_states(self, n: int, k: int) -> torch.Tensor:
+        """Hamming-weight-k states in increasing order (int64 CUDA tensor)."""
+        dim = int(round(np.prod([(n - i) / (i + 1) for i in range(k)]))) if k > 0 else 1
+        out = torch.empty(dim, dtype=torch.int64, device=f"cuda:{self.device}")
+        self._check(self._lib.qaoa_dicke_states(self._h, n, k, _ptr(out), dim))
+        return out
+
+    def ring_hamiltonian(self, n: int, k: int) -> torch.Tensor:
+        """Dense ring mixer on the weight-k states (float64 CUDA tensor)."""
+        dim = int(round(np.prod([(n - i) / (i + 1) for i in range(k)]))) if k > 0 else 1
+        out = torch.empty((dim, dim), dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(self._lib.qaoa_ring_hamiltonian(self._h, n, k, _ptr(out), dim))
+        return out
+
+    # ---------------------------------------------------------- simulation
+    def expectation(self, cost: torch.Tensor, mixer, angles, init: torch.Tensor | None = None) -> float:
+        """<C> for one angle set (qaoa_expectation); angles: 2p host values."""
+        cost = _dev_tensor(cost, "cost")
+        init = _dev_tensor(init, "init")
+        a = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).ravel())
+        E = ctypes.c_double()
+        self._check(self._lib.qaoa_expectation(self._h, _ptr(cost), _cost_dtype(cost),
+                                               ctypes.byref(mixer.struct), _ptr(init), a.shape[0] // 2,
+                                               a.ctypes.data_as(ctypes.c_void_p), ctypes.byref(E)))
+        return E.value
+
+    def gradient(self, cost: torch.Tensor, mixer, angles, init: torch.Tensor | None = None,
+                 ckpt: bool = True):
+        """(<C>, d<C>/d angles) for one angle set (qaoa_gradient)."""
+        cost = _dev_tensor(cost, "cost")
+        init = _dev_tensor(init, "init")
+        a = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).ravel())
+        E = ctypes.c_double()
+        g = np.zeros(a.shape[0], dtype=np.float64)
+        self._check(self._lib.qaoa_gradient(self._h, _ptr(cost), _cost_dtype(cost), ctypes.byref(mixer.struct),
+                                            _ptr(init), a.shape[0] // 2, a.ctypes.data_as(ctypes.c_void_p),
+                                            ctypes.byref(E), g.ctypes.data_as(ctypes.c_void_p),
+                                            1 if ckpt else 0))
+        return E.value, g
+
+    def expectation_batched(self, jobs, want_grad: bool = False):
+        """Enqueue many angle sets / instances (qaoa_expectation_batched).
+
+        jobs: list of dicts with keys cost, mixer, angles (n_sets x 2p float64
+        CUDA tensor), E (n_sets float64 CUDA tensor), grad (n_sets x 2p, when
+        want_grad) and optionally init.  Asynchronous on the context stream."""
+        arr = (B.QaoaJob * len(jobs))()
+        keep = []
+        for i, j in enumerate(jobs):
+            ang = _dev_tensor(j["angles"], "angles")
+            E = _dev_tensor(j["E"], "E")
+            G = _dev_tensor(j.get("grad"), "grad")
+            cost = _dev_tensor(j["cost"], "cost")
+            init = _dev_tensor(j.get("init"), "init")
+            if ang.dtype != torch.float64 or E.dtype != torch.float64 or (G is not None and G.dtype != torch.float64):
+                raise TypeError("angles, E and grad must be float64")
+            n_sets = ang.shape[0] if ang.dim() == 2 else 1
+            p = ang.shape[-1] // 2
+            mx = j["mixer"]
+            keep.append(mx)
+            arr[i] = B.QaoaJob(cost.data_ptr(), _cost_dtype(cost), ctypes.pointer(mx.struct), p, n_sets,
+                               ang.data_ptr(), E.data_ptr(), None if G is None else G.data_ptr(),
+                               None if init is None else init.data_ptr())
+        self._check(self._lib.qaoa_expectation_batched(self._h, len(jobs), arr, 1 if want_grad else 0))
+
+    # --------------------------------------------------------- measurement
+    def set_profiling(self, on: bool = True):
+        self._check(self._lib.qaoa_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_stats(self):
+        """{family: {launches, total_ms, algo_bytes}} of the profiled launches."""
+        n = self._lib.qaoa_kernel_stats(self._h, None, 0)
+        arr = (B.QaoaKernelStat * max(n, 1))()
+        n = self._lib.qaoa_kernel_stats(self._h, arr, n)
+        return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms,
+                                       "algo_bytes": arr[i].algo_bytes} for i in range(n)}
+
+    def reset_stats(self):
+        self._lib.qaoa_reset_stats(self._h)
+
+    def launch_count(self) -> int:
+        return int(self._lib.qaoa_launch_count(self._h))
+
+    def scratch_bytes(self) -> int:
+        return int(self._lib.qaoa_scratch_bytes(self._h))
+
+
+# Module-level aliases with the C names.
+def qaoa_cost_precompute(ctx: Context, *args, **kw):
+    return ctx.cost_precompute(*args, **kw)
+
+
+def qaoa_expectation(ctx: Context, *args, **kw):
+    return ctx.expectation(*args, **kw)
+
+
+def qaoa_gradient(ctx: Context, *args, **kw):
+    return ctx.gradient(*args, **kw)
+
+
+def qaoa_expectation_batched(ctx: Context, *args, **kw):
+    return ctx.expectation_batched(*args, **kw)
+
+
+class QAOAExpectation(torch.autograd.Function):
+    """E = <C>(angles) with the adjoint gradient (Sec. 2.3).
+
+    Usage: ``E = QAOAExpectation.apply(angles, ctx, cost, mixer)`` with angles a
+    float64 tensor of length 2p.  When angles requires grad, the forward runs
+    qaoa_gradient (one forward and one adjoint sweep) and keeps the gradient;
+    backward returns grad_out * dE/dangles."""
+
+    @staticmethod
+    def forward(fctx, angles, qctx, cost, mixer, init=None, ckpt=True):
+        a = angles.detach().to("cpu", torch.float64).contiguous().numpy()
+        if angles.requires_grad:
+            E, g = qctx.gradient(cost, mixer, a, init, ckpt)
+            fctx.save_for_backward(torch.from_numpy(g).to(angles.device))
+        else:
+            E = qctx.expectation(cost, mixer, a, init)
+            fctx.save_for_backward(torch.zeros_like(angles, dtype=torch.float64))
+        return torch.tensor(E, dtype=torch.float64, device=angles.device)
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        (g,) = fctx.saved_tensors
+        return grad_out * g, None, None, None, None, None

@@ -1,0 +1,1028 @@
+// C ABI of the library (include/qaoa.h): context, scratch arena, argument
+// validation, the pass schedule of the X mixer, launch planning and
+// measurement hooks.  All arithmetic of the method runs in the kernels of
+// kernels_xmix.cu / kernels_cost.cu / kernels_eig.cu; this file only decides
+// what to launch on which buffers.
+#include "../../include/qaoa.h"
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+using namespace qg;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct StatAcc {
+    int64_t launches = 0;
+    double ms = 0.0;
+    double bytes = 0.0;
+};
+
+struct PendingEv {
+    int fam;
+    cudaEvent_t a, b;
+};
+
+// One unit of work: one angle set of one problem instance.
+struct Unit {
+    const void *cost;
+    int cost_dtype;
+    int n;
+    int p;
+    const double *angles;  // device, 2p
+    double *E;             // device
+    double *grad;          // device, 2p (gradient runs)
+    const float2 *init;    // device or nullptr
+    int tsize;             // phase-table entries (uint8 costs)
+};
+
+enum LaunchKind { LK_PREP, LK_SMALL, LK_XPASS, LK_REDUCE };
+
+struct LaunchRec {
+    int kind;
+    int T = 0, bwd = 0, cost_dtype = 0;
+    size_t desc_off = 0, tb_off = 0;
+    int ndesc = 0;
+    uint32_t tiles = 0;
+    int small_maxn = 0, small_grad = 0;
+    int fam = 0;
+    double bytes = 0.0;
+};
+
+struct Plan {
+    uint64_t key = 0;
+    bool valid = false;
+    std::vector<LaunchRec> launches;
+};
+
+// Global-bit layout of one pass: local bits 0..c-1 are global bits 0..c-1,
+// local bits c..T-1 are global bits lo..lo+T-c-1.
+struct Group {
+    int c, lo;
+};
+
+constexpr int kMaxXQubits = 32;   // 32-bit element offsets in the pass kernel
+constexpr int kCminDefault = 4;   // >= 16 contiguous amplitudes = one 128-byte line
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
+
+uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; i++) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// Passes of one mixer round for n qubits and tile bits T: one contiguous pass
+// over qubits 0..T-1, then the remaining n-T qubits in balanced contiguous
+// chunks of at most T-cmin qubits, each gathered with 2^c contiguous
+// amplitudes (c >= cmin).
+std::vector<Group> make_groups(int n, int T, int cmin) {
+    std::vector<Group> g;
+    g.push_back({T, T});
+    const int R = n - T;
+    if (R <= 0) return g;
+    const int hmax = T - cmin;
+    const int P = (R + hmax - 1) / hmax;
+    int lo = T;
+    for (int j = 0; j < P; j++) {
+        const int h = R / P + (j < R % P ? 1 : 0);
+        g.push_back({T - h, lo});
+        lo += h;
+    }
+    return g;
+}
+
+int choose_T(int n) { return n < 13 ? n : 13; }
+
+}  // namespace
+
+struct qaoa_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int *d_err = nullptr;
+    std::map<std::string, Buf> bufs;
+    void *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    double *h_io = nullptr;
+    size_t h_io_count = 0;
+    bool profiling = false;
+    std::vector<std::string> fam_names;
+    std::map<std::string, int> fam_index;
+    std::vector<StatAcc> fam_stats;
+    std::vector<PendingEv> pending;
+    std::vector<cudaEvent_t> ev_pool;
+    int64_t launches = 0;
+    Plan plan;
+};
+
+namespace {
+
+qaoa_status fail(qaoa_ctx *ctx, qaoa_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return st;
+}
+
+qaoa_status cuda_fail(qaoa_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, QAOA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define QG_CUDA(ctx, call, what)                          \
+    do {                                                  \
+        cudaError_t e__ = (call);                         \
+        if (e__ != cudaSuccess) return cuda_fail(ctx, e__, what); \
+    } while (0)
+
+int family(qaoa_ctx *ctx, const std::string &name) {
+    auto it = ctx->fam_index.find(name);
+    if (it != ctx->fam_index.end()) return it->second;
+    const int id = (int)ctx->fam_names.size();
+    ctx->fam_names.push_back(name);
+    ctx->fam_stats.push_back(StatAcc());
+    ctx->fam_index[name] = id;
+    return id;
+}
+
+cudaEvent_t take_event(qaoa_ctx *ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+bool capturing(qaoa_ctx *ctx) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(ctx->stream, &cs);
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Device scratch by name; grows (never shrinks) and invalidates the cached
+// plan when a buffer moves.
+qaoa_status scratch(qaoa_ctx *ctx, const char *name, size_t bytes, void **out) {
+    Buf &b = ctx->bufs[name];
+    if (b.bytes >= bytes && b.p) {
+        *out = b.p;
+        return QAOA_OK;
+    }
+    if (capturing(ctx))
+        return fail(ctx, QAOA_ERR_INVALID,
+                    "scratch '%s' must grow during stream capture; run the call once uncaptured first",
+                    name);
+    if (b.p) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    ctx->plan.valid = false;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, kAlign));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, QAOA_ERR_OOM, "cannot allocate %.3f GiB of scratch for '%s'",
+                    bytes / 1073741824.0, name);
+    }
+    b.p = p;
+    b.bytes = std::max<size_t>(bytes, kAlign);
+    *out = p;
+    return QAOA_OK;
+}
+
+qaoa_status host_stage(qaoa_ctx *ctx, size_t bytes) {
+    if (ctx->h_stage_bytes >= bytes) return QAOA_OK;
+    if (ctx->h_stage) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFreeHost(ctx->h_stage);
+    }
+    ctx->h_stage = nullptr;
+    ctx->h_stage_bytes = 0;
+    QG_CUDA(ctx, cudaMallocHost(&ctx->h_stage, bytes), "cudaMallocHost");
+    ctx->h_stage_bytes = bytes;
+    return QAOA_OK;
+}
+
+// ------------------------------------------------------------- planning
+
+struct UnitLayout {
+    int T_f, T_b;
+    std::vector<Group> gf, gb;
+    uint32_t tiles_f, tiles_b;
+    int64_t stride;  // partial slots per quantity
+    int vecs;        // state vectors held in scratch
+};
+
+UnitLayout layout_for(const Unit &u, bool grad, int ckpt) {
+    UnitLayout L;
+    L.T_f = choose_T(u.n);
+    L.T_b = choose_T(u.n);
+    L.gf = make_groups(u.n, L.T_f, kCminDefault);
+    L.gb = make_groups(u.n, L.T_b, kCminDefault);
+    L.tiles_f = 1u << (u.n - L.T_f);
+    L.tiles_b = 1u << (u.n - L.T_b);
+    L.stride = std::max<int64_t>(L.tiles_f, (int64_t)L.gb.size() * L.tiles_b);
+    L.vecs = grad ? (2 + (ckpt ? u.p - 1 : 0)) : 1;
+    return L;
+}
+
+void fill_geometry(PassDesc &d, int n, int T, const Group &g) {
+    d.n = (uint8_t)n;
+    bool used[64] = {false};
+    for (int j = 0; j < T; j++) {
+        const int gp = j < g.c ? j : g.lo + (j - g.c);
+        d.gpos[j] = (uint8_t)gp;
+        used[gp] = true;
+    }
+    int nf = 0;
+    for (int b = 0; b < n; b++)
+        if (!used[b]) d.fpos[nf++] = (uint8_t)b;
+    d.nfree = (uint8_t)nf;
+    d.ntiles = 1u << nf;
+    d.active = (g.c == T) ? ((1u << T) - 1u) : (((1u << T) - 1u) & ~((1u << g.c) - 1u));
+}
+
+double pass_bytes(const PassDesc &d, int bwd, int cost_bytes) {
+    const double N = std::ldexp(1.0, d.n);
+    double b = 0.0;
+    if (!bwd) {
+        if (!(d.flags & PF_GEN_INIT)) b += 8;
+        if (d.psi_out) b += 8;
+        if (d.flags & PF_PHASE) b += cost_bytes;
+        if (d.flags & PF_E) b += cost_bytes;
+    } else {
+        b += 8;  // psi
+        if (!(d.flags & PF_LAM_FROM_C)) b += 8;
+        else b += cost_bytes;
+        if (d.flags & PF_PHASE) b += cost_bytes;
+        if (d.psi_out) b += 8;
+        if (d.lam_out) b += 8;
+    }
+    return b * N;
+}
+
+// Descriptors of every pass of one unit: forward rounds, then adjoint rounds
+// in reverse.  Buffers: W = running state, L = adjoint state, CK[k] = state
+// after round k (0-based, k < p-1) when checkpointing.
+void unit_passes(const Unit &u, const UnitLayout &L, bool grad, int ckpt, float2 *W, float2 *Lam,
+                 float2 *CK, const RoundCoef *coef, const float2 *table, double *part,
+                 std::vector<PassDesc> &fwd, std::vector<PassDesc> &bwd) {
+    const int p = u.p;
+    const int64_t N = 1ll << u.n;
+    const int Pf = (int)L.gf.size(), Pb = (int)L.gb.size();
+    const float amp0 = (float)(1.0 / std::sqrt(std::ldexp(1.0, u.n)));
+    auto ck = [&](int k) { return CK + (int64_t)k * N; };
+    for (int k = 0; k < p; k++) {
+        for (int g = 0; g < Pf; g++) {
+            PassDesc d;
+            std::memset(&d, 0, sizeof(d));
+            fill_geometry(d, u.n, L.T_f, L.gf[g]);
+            d.cost = u.cost;
+            d.coef = coef + k;
+            d.table = table ? table + (int64_t)k * kPhaseTable : nullptr;
+            d.amp0 = amp0;
+            const bool first = g == 0, last = g == Pf - 1;
+            if (first) {
+                d.flags |= PF_PHASE;
+                if (k == 0) {
+                    if (u.init) d.psi_in = u.init;
+                    else d.flags |= PF_GEN_INIT;
+                } else {
+                    d.psi_in = (grad && ckpt) ? ck(k - 1) : W;
+                }
+            } else {
+                d.psi_in = W;
+            }
+            if (last && k == p - 1) {
+                d.flags |= PF_E;
+                d.part_E = part;
+                d.psi_out = grad ? W : nullptr;
+            } else if (last && grad && ckpt) {
+                d.psi_out = ck(k);
+            } else {
+                d.psi_out = W;
+            }
+            fwd.push_back(d);
+        }
+    }
+    if (!grad) return;
+    for (int k = p - 1; k >= 0; k--) {
+        for (int g = 0; g < Pb; g++) {
+            PassDesc d;
+            std::memset(&d, 0, sizeof(d));
+            fill_geometry(d, u.n, L.T_b, L.gb[g]);
+            d.cost = u.cost;
+            d.coef = coef + k;
+            d.table = table ? table + (int64_t)k * kPhaseTable : nullptr;
+            d.amp0 = amp0;
+            const bool first_round = k == p - 1;
+            const bool last = g == Pb - 1;
+            if (g == 0) {
+                d.psi_in = (first_round || !ckpt) ? W : ck(k);
+                if (first_round) d.flags |= PF_LAM_FROM_C;
+                else d.lam_in = Lam;
+            } else {
+                d.psi_in = W;
+                d.lam_in = Lam;
+            }
+            if (last) {
+                d.flags |= PF_PHASE;
+                d.part_gamma = part + (int64_t)(1 + p + k) * L.stride;
+                if (!ckpt && k > 0) {
+                    d.flags |= PF_UNPHASE_PSI;
+                    d.psi_out = W;
+                }
+                d.lam_out = k > 0 ? Lam : nullptr;
+            } else {
+                d.psi_out = W;
+                d.lam_out = Lam;
+            }
+            d.part_beta = part + (int64_t)(1 + k) * L.stride + (int64_t)g * L.tiles_b;
+            bwd.push_back(d);
+        }
+    }
+}
+
+const char *dtype_name(int dt) { return dt == QAOA_COST_U8 ? "u8" : "f32"; }
+
+// Build (or reuse) the launch plan for a unit list and enqueue it.
+qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, int ckpt) {
+    uint64_t key = fnv1a(units.data(), units.size() * sizeof(Unit));
+    const int flags2[2] = {grad ? 1 : 0, ckpt};
+    key = fnv1a(flags2, sizeof(flags2), key);
+
+    if (!(ctx->plan.valid && ctx->plan.key == key)) {
+        if (capturing(ctx))
+            return fail(ctx, QAOA_ERR_INVALID,
+                        "launch plan not built; run the same call once before stream capture");
+        // ---- per-unit metadata: coefficients, tables, partials
+        const int nu = (int)units.size();
+        const int smax = small_max_n();
+        std::vector<size_t> off_coef(nu), off_tab(nu), off_part(nu);
+        std::vector<UnitLayout> lay(nu);
+        size_t meta = 0;
+        for (int i = 0; i < nu; i++) {
+            const Unit &u = units[i];
+            off_coef[i] = meta;
+            meta = align_up(meta + sizeof(RoundCoef) * u.p);
+            off_tab[i] = meta;
+            if (u.cost_dtype == QAOA_COST_U8) meta = align_up(meta + sizeof(float2) * kPhaseTable * u.p);
+            off_part[i] = meta;
+            if (u.n > smax) {
+                lay[i] = layout_for(u, grad, ckpt);
+                meta = align_up(meta + sizeof(double) * (2 * u.p + 1) * lay[i].stride);
+            }
+        }
+        void *d_meta = nullptr;
+        qaoa_status st = scratch(ctx, "meta", meta, &d_meta);
+        if (st) return st;
+        char *mb = static_cast<char *>(d_meta);
+
+        // ---- state memory: pass units grouped by launch shape, admitted in waves
+        struct GKey {
+            int Tf, Tb, Pf, Pb, p, dt;
+            bool operator<(const GKey &o) const {
+                return std::tie(Tf, Tb, Pf, Pb, p, dt) < std::tie(o.Tf, o.Tb, o.Pf, o.Pb, o.p, o.dt);
+            }
+        };
+        std::map<GKey, std::vector<int>> groups;
+        for (int i = 0; i < nu; i++) {
+            if (units[i].n <= smax) continue;
+            const UnitLayout &L = lay[i];
+            groups[{L.T_f, L.T_b, (int)L.gf.size(), (int)L.gb.size(), units[i].p, units[i].cost_dtype}]
+                .push_back(i);
+        }
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const size_t held = ctx->bufs.count("state") ? ctx->bufs["state"].bytes : 0;
+        const double budget_d = (double)(free_b + held) * 0.92 - 1.0 * (1ull << 30);
+        const size_t budget = budget_d > 0 ? (size_t)budget_d : 0;
+        // waves: consecutive units of a group whose states fit the budget together
+        struct Wave {
+            GKey gk;
+            std::vector<int> us;
+            std::vector<size_t> soff;
+        };
+        std::vector<Wave> waves;
+        size_t state_need = 0;
+        for (auto &kv : groups) {
+            Wave w;
+            w.gk = kv.first;
+            size_t used = 0;
+            for (int i : kv.second) {
+                const size_t need = align_up((size_t)lay[i].vecs * (sizeof(float2) << units[i].n));
+                if (need > budget)
+                    return fail(ctx, QAOA_ERR_OOM,
+                                "one angle set at n=%d needs %.2f GiB of state scratch, %.2f GiB available",
+                                units[i].n, need / 1073741824.0, budget / 1073741824.0);
+                if (used + need > budget && !w.us.empty()) {
+                    waves.push_back(w);
+                    w.us.clear();
+                    w.soff.clear();
+                    used = 0;
+                }
+                w.us.push_back(i);
+                w.soff.push_back(used);
+                used += need;
+                state_need = std::max(state_need, used);
+            }
+            if (!w.us.empty()) waves.push_back(w);
+        }
+        void *d_state = nullptr;
+        if (state_need) {
+            st = scratch(ctx, "state", state_need, &d_state);
+            if (st) return st;
+        }
+
+        // ---- descriptors
+        std::vector<char> host;  // packed descriptor image
+        auto put = [&](const void *src, size_t bytes) {
+            const size_t off = align_up(host.size(), 16);
+            host.resize(off + bytes);
+            std::memcpy(host.data() + off, src, bytes);
+            return off;
+        };
+        std::vector<LaunchRec> L;
+
+        std::vector<PrepDesc> prep(nu);
+        for (int i = 0; i < nu; i++) {
+            const Unit &u = units[i];
+            prep[i].angles = u.angles;
+            prep[i].coef = reinterpret_cast<RoundCoef *>(mb + off_coef[i]);
+            prep[i].table = u.cost_dtype == QAOA_COST_U8 ? reinterpret_cast<float2 *>(mb + off_tab[i]) : nullptr;
+            prep[i].p = u.p;
+            prep[i].tsize = u.tsize;
+        }
+        {
+            LaunchRec r;
+            r.kind = LK_PREP;
+            r.desc_off = put(prep.data(), sizeof(PrepDesc) * nu);
+            r.ndesc = nu;
+            r.fam = family(ctx, "prep_coefficients");
+            L.push_back(r);
+        }
+        for (int dt = 0; dt < 2; dt++) {
+            std::vector<SmallDesc> sd;
+            int maxn = 0;
+            double bytes = 0;
+            for (int i = 0; i < nu; i++) {
+                const Unit &u = units[i];
+                if (u.n > smax || u.cost_dtype != dt) continue;
+                SmallDesc s;
+                std::memset(&s, 0, sizeof(s));
+                s.cost = u.cost;
+                s.init = u.init;
+                s.coef = prep[i].coef;
+                s.table = prep[i].table;
+                s.E_out = u.E;
+                s.grad_out = grad ? u.grad : nullptr;
+                s.n = u.n;
+                s.p = u.p;
+                s.amp0 = 1.0f / std::sqrt((float)(1u << u.n));
+                sd.push_back(s);
+                maxn = std::max(maxn, u.n);
+                bytes += std::ldexp(1.0, u.n) * (dt == QAOA_COST_U8 ? 1 : 4) * (grad ? 3 : 2);
+            }
+            if (sd.empty()) continue;
+            LaunchRec r;
+            r.kind = LK_SMALL;
+            r.cost_dtype = dt;
+            r.desc_off = put(sd.data(), sizeof(SmallDesc) * sd.size());
+            r.ndesc = (int)sd.size();
+            r.small_maxn = maxn;
+            r.small_grad = grad ? 1 : 0;
+            r.bytes = bytes;
+            r.fam = family(ctx, std::string(grad ? "small_grad_" : "small_fwd_") + dtype_name(dt));
+            L.push_back(r);
+        }
+        std::vector<RedDesc> red;
+        for (const Wave &w : waves) {
+            const GKey &gk = w.gk;
+            std::vector<std::vector<PassDesc>> steps;
+            for (size_t wi = 0; wi < w.us.size(); wi++) {
+                const int i = w.us[wi];
+                const Unit &u = units[i];
+                const int64_t N = 1ll << u.n;
+                float2 *base = reinterpret_cast<float2 *>(static_cast<char *>(d_state) + w.soff[wi]);
+                float2 *W = base, *Lam = grad ? base + N : nullptr, *CK = grad ? base + 2 * N : nullptr;
+                std::vector<PassDesc> f, b;
+                unit_passes(u, lay[i], grad, ckpt, W, Lam, CK, prep[i].coef, prep[i].table,
+                            reinterpret_cast<double *>(mb + off_part[i]), f, b);
+                std::vector<PassDesc> all = f;
+                all.insert(all.end(), b.begin(), b.end());
+                if (steps.size() < all.size()) steps.resize(all.size());
+                for (size_t s = 0; s < all.size(); s++) steps[s].push_back(all[s]);
+                RedDesc rd;
+                rd.part = reinterpret_cast<double *>(mb + off_part[i]);
+                rd.stride = lay[i].stride;
+                rd.cntE = (int)lay[i].tiles_f;
+                rd.cntB = (int)(lay[i].gb.size() * lay[i].tiles_b);
+                rd.cntG = (int)lay[i].tiles_b;
+                rd.p = u.p;
+                rd.E_out = u.E;
+                rd.grad_out = grad ? u.grad : nullptr;
+                red.push_back(rd);
+            }
+            const int nfwd = gk.p * gk.Pf;
+            for (size_t s = 0; s < steps.size(); s++) {
+                const bool bwd = (int)s >= nfwd;
+                const int T = bwd ? gk.Tb : gk.Tf;
+                std::vector<uint32_t> tb(steps[s].size() + 1, 0);
+                double bytes = 0;
+                for (size_t j = 0; j < steps[s].size(); j++) {
+                    tb[j + 1] = tb[j] + steps[s][j].ntiles;
+                    bytes += pass_bytes(steps[s][j], bwd, gk.dt == QAOA_COST_U8 ? 1 : 4);
+                }
+                LaunchRec r;
+                r.kind = LK_XPASS;
+                r.T = T;
+                r.bwd = bwd;
+                r.cost_dtype = gk.dt;
+                r.desc_off = put(steps[s].data(), sizeof(PassDesc) * steps[s].size());
+                r.tb_off = put(tb.data(), sizeof(uint32_t) * tb.size());
+                r.ndesc = (int)steps[s].size();
+                r.tiles = tb.back();
+                r.bytes = bytes;
+                char nm[64];
+                snprintf(nm, sizeof(nm), "xpass_%s_T%d_%s", bwd ? "bwd" : "fwd", T, dtype_name(gk.dt));
+                r.fam = family(ctx, nm);
+                L.push_back(r);
+            }
+        }
+        if (!red.empty()) {
+            LaunchRec r;
+            r.kind = LK_REDUCE;
+            r.desc_off = put(red.data(), sizeof(RedDesc) * red.size());
+            r.ndesc = (int)red.size();
+            r.fam = family(ctx, "reduce_partials");
+            L.push_back(r);
+        }
+        // ---- upload
+        void *d_desc = nullptr;
+        st = scratch(ctx, "desc", host.size(), &d_desc);
+        if (st) return st;
+        st = host_stage(ctx, host.size());
+        if (st) return st;
+        std::memcpy(ctx->h_stage, host.data(), host.size());
+        QG_CUDA(ctx, cudaMemcpyAsync(d_desc, ctx->h_stage, host.size(), cudaMemcpyHostToDevice, ctx->stream),
+                "descriptor upload");
+        QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "descriptor upload");
+        ctx->plan.launches = L;
+        ctx->plan.key = key;
+        ctx->plan.valid = true;
+    }
+
+    // ---- enqueue
+    char *db = static_cast<char *>(ctx->bufs["desc"].p);
+    const bool prof = ctx->profiling && !capturing(ctx);
+    for (const LaunchRec &r : ctx->plan.launches) {
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (prof) {
+            ea = take_event(ctx);
+            eb = take_event(ctx);
+            cudaEventRecord(ea, ctx->stream);
+        }
+        cudaError_t e = cudaSuccess;
+        switch (r.kind) {
+        case LK_PREP:
+            e = launch_prep(reinterpret_cast<const PrepDesc *>(db + r.desc_off), r.ndesc, ctx->d_err,
+                            ctx->stream);
+            break;
+        case LK_SMALL:
+            e = launch_small(reinterpret_cast<const SmallDesc *>(db + r.desc_off), r.ndesc, r.cost_dtype,
+                             r.small_grad, r.small_maxn, ctx->d_err, ctx->stream);
+            break;
+        case LK_XPASS:
+            e = launch_xpass(r.T, r.bwd, r.cost_dtype, reinterpret_cast<const PassDesc *>(db + r.desc_off),
+                             reinterpret_cast<const uint32_t *>(db + r.tb_off), r.ndesc, r.tiles,
+                             ctx->d_err, ctx->stream);
+            break;
+        case LK_REDUCE:
+            e = launch_reduce(reinterpret_cast<const RedDesc *>(db + r.desc_off), r.ndesc, ctx->stream);
+            break;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+        ctx->launches++;
+        if (prof) {
+            cudaEventRecord(eb, ctx->stream);
+            ctx->pending.push_back({r.fam, ea, eb});
+            ctx->fam_stats[r.fam].launches++;
+            ctx->fam_stats[r.fam].bytes += r.bytes;
+        }
+    }
+    return QAOA_OK;
+}
+
+qaoa_status check_x_args(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const qaoa_mixer *mx,
+                         const void *d_init, int p) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    if (!mx) return fail(ctx, QAOA_ERR_INVALID, "mixer is NULL");
+    if (mx->kind == QAOA_MIXER_EIGEN)
+        return fail(ctx, QAOA_ERR_UNSUPPORTED, "eigenbasis mixer not available in this build");
+    if (mx->kind != QAOA_MIXER_X) return fail(ctx, QAOA_ERR_INVALID, "unknown mixer kind %d", mx->kind);
+    if (mx->n < 1 || mx->n > kMaxXQubits)
+        return fail(ctx, QAOA_ERR_INVALID, "X mixer needs 1 <= n <= %d (got %d)", kMaxXQubits, mx->n);
+    if (mx->dim != (1ll << mx->n))
+        return fail(ctx, QAOA_ERR_INVALID, "X mixer dim must be 2^n (n=%d, dim=%lld)", mx->n,
+                    (long long)mx->dim);
+    if (p < 1 || p > 4096) return fail(ctx, QAOA_ERR_INVALID, "p must be in [1, 4096] (got %d)", p);
+    if (cost_dtype != QAOA_COST_F32 && cost_dtype != QAOA_COST_U8)
+        return fail(ctx, QAOA_ERR_INVALID, "unknown cost dtype %d", cost_dtype);
+    if (!d_cost || ((uintptr_t)d_cost & 15))
+        return fail(ctx, QAOA_ERR_INVALID, "d_cost must be a 16-byte aligned device pointer");
+    if (d_init && ((uintptr_t)d_init & 15))
+        return fail(ctx, QAOA_ERR_INVALID, "d_init must be 16-byte aligned");
+    return QAOA_OK;
+}
+
+qaoa_status read_dev_err(qaoa_ctx *ctx) {
+    int h = 0;
+    QG_CUDA(ctx, cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+            "error word read");
+    QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    if (h) {
+        cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
+        if (h & DERR_BAD_ANGLE) return fail(ctx, QAOA_ERR_INVALID, "non-finite angle");
+        return fail(ctx, QAOA_ERR_CUDA, "device error word 0x%x", h);
+    }
+    return QAOA_OK;
+}
+
+qaoa_status scalar_run(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const qaoa_mixer *mixer,
+                       const void *d_init, int p, const double *angles, double *E, double *grad,
+                       int ckpt) {
+    qaoa_status st = check_x_args(ctx, d_cost, cost_dtype, mixer, d_init, p);
+    if (st) return st;
+    if (!angles || !E || (grad == nullptr) != (ckpt < 0))
+        return fail(ctx, QAOA_ERR_INVALID, "angles and result pointers must be non-NULL");
+    for (int i = 0; i < 2 * p; i++)
+        if (!std::isfinite(angles[i])) return fail(ctx, QAOA_ERR_INVALID, "angle %d is not finite", i);
+    const size_t cnt = (size_t)4 * p + 1;
+    void *d_io = nullptr;
+    st = scratch(ctx, "io", cnt * sizeof(double), &d_io);
+    if (st) return st;
+    if (ctx->h_io_count < cnt) {
+        if (ctx->h_io) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFreeHost(ctx->h_io);
+        }
+        ctx->h_io = nullptr;
+        ctx->h_io_count = 0;
+        QG_CUDA(ctx, cudaMallocHost(reinterpret_cast<void **>(&ctx->h_io), cnt * sizeof(double)),
+                "cudaMallocHost");
+        ctx->h_io_count = cnt;
+    }
+    std::memcpy(ctx->h_io, angles, sizeof(double) * 2 * p);
+    double *io = static_cast<double *>(d_io);
+    QG_CUDA(ctx, cudaMemcpyAsync(io, ctx->h_io, sizeof(double) * 2 * p, cudaMemcpyHostToDevice, ctx->stream),
+            "angle upload");
+    Unit u;
+    std::memset(&u, 0, sizeof(u));
+    u.cost = d_cost;
+    u.cost_dtype = cost_dtype;
+    u.n = mixer->n;
+    u.p = p;
+    u.angles = io;
+    u.E = io + 2 * p;
+    u.grad = grad ? io + 2 * p + 1 : nullptr;
+    u.init = static_cast<const float2 *>(d_init);
+    u.tsize = kPhaseTable;
+    std::vector<Unit> us(1, u);
+    st = run_units(ctx, us, grad != nullptr, grad ? (ckpt ? 1 : 0) : 0);
+    if (st) return st;
+    const size_t nout = grad ? (size_t)2 * p + 1 : 1;
+    QG_CUDA(ctx, cudaMemcpyAsync(ctx->h_io + 2 * p, io + 2 * p, sizeof(double) * nout, cudaMemcpyDeviceToHost,
+                                 ctx->stream),
+            "result download");
+    st = read_dev_err(ctx);
+    if (st) return st;
+    *E = ctx->h_io[2 * p];
+    if (grad) std::memcpy(grad, ctx->h_io + 2 * p + 1, sizeof(double) * 2 * p);
+    return QAOA_OK;
+}
+
+}  // namespace
+
+// ======================================================================
+extern "C" {
+
+qaoa_status qaoa_create(qaoa_ctx **out, int device, void *cuda_stream) {
+    if (!out) return QAOA_ERR_INVALID;
+    *out = nullptr;
+    qaoa_ctx *ctx = nullptr;
+    try {
+        ctx = new qaoa_ctx();
+    } catch (...) {
+        return QAOA_ERR_OOM;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        delete ctx;
+        return QAOA_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete ctx;
+        return QAOA_ERR_CUDA;
+    }
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess || upload_binom_table() != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->d_err) cudaFree(ctx->d_err);
+        delete ctx;
+        return QAOA_ERR_CUDA;
+    }
+    *out = ctx;
+    return QAOA_OK;
+}
+
+void qaoa_destroy(qaoa_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->bufs)
+        if (kv.second.p) cudaFree(kv.second.p);
+    for (auto &pe : ctx->pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->h_io) cudaFreeHost(ctx->h_io);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+}
+
+const char *qaoa_last_error(const qaoa_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t qaoa_scratch_bytes(const qaoa_ctx *ctx) {
+    if (!ctx) return -1;
+    int64_t t = 0;
+    for (auto &kv : ctx->bufs) t += (int64_t)kv.second.bytes;
+    return t;
+}
+
+qaoa_status qaoa_cost_precompute(qaoa_ctx *ctx, const qaoa_problem *prob, void *d_cost, int cost_dtype,
+                                 int64_t dim) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    try {
+        ctx->err.clear();
+        if (!prob || !d_cost) return fail(ctx, QAOA_ERR_INVALID, "problem and d_cost must be non-NULL");
+        const int n = prob->n;
+        if (cost_dtype != QAOA_COST_F32 && cost_dtype != QAOA_COST_U8)
+            return fail(ctx, QAOA_ERR_INVALID, "unknown cost dtype %d", cost_dtype);
+        const bool dks = prob->kind == QAOA_PROBLEM_DKS;
+        if (n < 1 || n > (dks ? binom_table_max() : 34))
+            return fail(ctx, QAOA_ERR_INVALID, "n=%d out of range", n);
+        int64_t want;
+        if (dks) {
+            if (prob->k < 0 || prob->k > n) return fail(ctx, QAOA_ERR_INVALID, "bad k=%d", prob->k);
+            double b = 1;
+            for (int i = 0; i < prob->k; i++) b = b * (n - i) / (i + 1);
+            want = (int64_t)std::llround(b);
+        } else {
+            want = 1ll << n;
+        }
+        if (dim != want)
+            return fail(ctx, QAOA_ERR_INVALID, "dim=%lld but the feasible set has %lld states",
+                        (long long)dim, (long long)want);
+        cudaSetDevice(ctx->device);
+        if (prob->kind == QAOA_PROBLEM_MAXCUT || prob->kind == QAOA_PROBLEM_WMAXCUT || dks) {
+            if (prob->m < 0 || (prob->m > 0 && !prob->edges))
+                return fail(ctx, QAOA_ERR_INVALID, "edge list missing");
+            uint64_t nbr[64] = {0};
+            for (int e = 0; e < prob->m; e++) {
+                int u = prob->edges[2 * e], v = prob->edges[2 * e + 1];
+                if (u < 0 || v < 0 || u >= n || v >= n || u == v)
+                    return fail(ctx, QAOA_ERR_INVALID, "edge %d = (%d,%d) invalid for n=%d", e, u, v, n);
+                if (u > v) std::swap(u, v);
+                if (nbr[u] & (1ull << v))
+                    return fail(ctx, QAOA_ERR_INVALID, "edge (%d,%d) repeated", u, v);
+                nbr[u] |= 1ull << v;
+            }
+            if (cost_dtype == QAOA_COST_U8 && prob->m > 255 && prob->kind != QAOA_PROBLEM_WMAXCUT)
+                return fail(ctx, QAOA_ERR_INVALID, "%d edges: costs may exceed 255, use float32", prob->m);
+            cudaError_t e;
+            if (prob->kind == QAOA_PROBLEM_WMAXCUT) {
+                if (cost_dtype != QAOA_COST_F32 || !prob->weights)
+                    return fail(ctx, QAOA_ERR_INVALID, "weighted MaxCut needs weights and float32 costs");
+                void *dw = nullptr, *de = nullptr;
+                qaoa_status st = scratch(ctx, "pre_w", sizeof(float) * std::max(1, prob->m), &dw);
+                if (st) return st;
+                st = scratch(ctx, "pre_e", sizeof(int32_t) * 2 * std::max(1, prob->m), &de);
+                if (st) return st;
+                QG_CUDA(ctx, cudaMemcpyAsync(dw, prob->weights, sizeof(float) * prob->m, cudaMemcpyHostToDevice,
+                                             ctx->stream), "weights upload");
+                QG_CUDA(ctx, cudaMemcpyAsync(de, prob->edges, sizeof(int32_t) * 2 * prob->m,
+                                             cudaMemcpyHostToDevice, ctx->stream), "edges upload");
+                e = launch_cost_maxcut(n, nbr, static_cast<float *>(dw), static_cast<int32_t *>(de), prob->m, 1,
+                                       dim, d_cost, cost_dtype, ctx->stream);
+            } else if (dks) {
+                e = launch_cost_dks(n, prob->k, nbr, dim, d_cost, cost_dtype, ctx->stream);
+            } else {
+                e = launch_cost_maxcut(n, nbr, nullptr, nullptr, prob->m, 0, dim, d_cost, cost_dtype,
+                                       ctx->stream);
+            }
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cost kernel launch");
+            ctx->launches++;
+        } else if (prob->kind == QAOA_PROBLEM_SK) {
+            if (!prob->J) return fail(ctx, QAOA_ERR_INVALID, "SK needs J");
+            if (cost_dtype != QAOA_COST_F32) return fail(ctx, QAOA_ERR_INVALID, "SK costs are float32");
+            if (n > 40) return fail(ctx, QAOA_ERR_INVALID, "SK supports n <= 40");
+            bool exact = true;
+            std::vector<int32_t> Jq(n * n, 0);
+            std::vector<double> Jd(n * n, 0.0);
+            for (int i = 0; i < n; i++)
+                for (int j = 0; j < n; j++) {
+                    const double v = (double)prob->J[i * n + j];
+                    if (!std::isfinite(v)) return fail(ctx, QAOA_ERR_INVALID, "J[%d][%d] not finite", i, j);
+                    Jd[i * n + j] = v;
+                    const double q = v * 1048576.0;
+                    if (std::fabs(v) >= 8.0 || q != std::rint(q)) exact = false;
+                    else Jq[i * n + j] = (int32_t)q;
+                }
+            void *dj = nullptr;
+            qaoa_status st = scratch(ctx, "pre_J", sizeof(double) * n * n, &dj);
+            if (st) return st;
+            cudaError_t e;
+            if (exact) {
+                QG_CUDA(ctx, cudaMemcpyAsync(dj, Jq.data(), sizeof(int32_t) * n * n, cudaMemcpyHostToDevice,
+                                             ctx->stream), "J upload");
+                e = launch_cost_sk(n, static_cast<int32_t *>(dj), nullptr, 1, dim, static_cast<float *>(d_cost),
+                                   ctx->stream);
+            } else {
+                QG_CUDA(ctx, cudaMemcpyAsync(dj, Jd.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice,
+                                             ctx->stream), "J upload");
+                e = launch_cost_sk(n, nullptr, static_cast<double *>(dj), 0, dim, static_cast<float *>(d_cost),
+                                   ctx->stream);
+            }
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cost kernel launch");
+            ctx->launches++;
+        } else {
+            return fail(ctx, QAOA_ERR_INVALID, "unknown problem kind %d", prob->kind);
+        }
+        QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "cost precompute");
+        return QAOA_OK;
+    } catch (...) {
+        return fail(ctx, QAOA_ERR_OOM, "host allocation failed");
+    }
+}
+
+qaoa_status qaoa_dicke_states(qaoa_ctx *ctx, int n, int k, uint64_t *d_states, int64_t dim) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    ctx->err.clear();
+    if (n < 1 || n > binom_table_max() || k < 0 || k > n || !d_states)
+        return fail(ctx, QAOA_ERR_INVALID, "bad Dicke arguments n=%d k=%d", n, k);
+    double b = 1;
+    for (int i = 0; i < k; i++) b = b * (n - i) / (i + 1);
+    if (dim != (int64_t)std::llround(b)) return fail(ctx, QAOA_ERR_INVALID, "dim must be binom(n,k)");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = launch_dicke_states(n, k, dim, d_states, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dicke kernel launch");
+    ctx->launches++;
+    QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "dicke states");
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_ring_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, int64_t dim) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    ctx->err.clear();
+    if (n < 3 || n > binom_table_max() || k < 0 || k > n || !d_H)
+        return fail(ctx, QAOA_ERR_INVALID, "ring mixer needs 3 <= n <= %d and 0 <= k <= n",
+                    binom_table_max());
+    double b = 1;
+    for (int i = 0; i < k; i++) b = b * (n - i) / (i + 1);
+    if (dim != (int64_t)std::llround(b)) return fail(ctx, QAOA_ERR_INVALID, "dim must be binom(n,k)");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = launch_ring_hamiltonian(n, k, dim, d_H, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ring kernel launch");
+    ctx->launches++;
+    QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "ring hamiltonian");
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_expectation(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const qaoa_mixer *mixer,
+                             const void *d_init, int p, const double *angles, double *E) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    try {
+        ctx->err.clear();
+        cudaSetDevice(ctx->device);
+        return scalar_run(ctx, d_cost, cost_dtype, mixer, d_init, p, angles, E, nullptr, -1);
+    } catch (...) {
+        return fail(ctx, QAOA_ERR_OOM, "host allocation failed");
+    }
+}
+
+qaoa_status qaoa_gradient(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const qaoa_mixer *mixer,
+                          const void *d_init, int p, const double *angles, double *E, double *grad,
+                          int ckpt) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    try {
+        ctx->err.clear();
+        if (!grad) return fail(ctx, QAOA_ERR_INVALID, "grad must be non-NULL");
+        cudaSetDevice(ctx->device);
+        return scalar_run(ctx, d_cost, cost_dtype, mixer, d_init, p, angles, E, grad, ckpt ? 1 : 0);
+    } catch (...) {
+        return fail(ctx, QAOA_ERR_OOM, "host allocation failed");
+    }
+}
+
+qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *jobs, int want_grad) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    try {
+        ctx->err.clear();
+        if (n_jobs < 1 || !jobs) return fail(ctx, QAOA_ERR_INVALID, "no jobs");
+        cudaSetDevice(ctx->device);
+        std::vector<Unit> units;
+        for (int j = 0; j < n_jobs; j++) {
+            const qaoa_job &jb = jobs[j];
+            qaoa_status st = check_x_args(ctx, jb.d_cost, jb.cost_dtype, jb.mixer, jb.d_init, jb.p);
+            if (st) return st;
+            if (jb.n_sets < 1 || !jb.d_angles || !jb.d_E || (want_grad && !jb.d_grad))
+                return fail(ctx, QAOA_ERR_INVALID, "job %d: bad sets or output pointers", j);
+            for (int s = 0; s < jb.n_sets; s++) {
+                Unit u;
+                std::memset(&u, 0, sizeof(u));
+                u.cost = jb.d_cost;
+                u.cost_dtype = jb.cost_dtype;
+                u.n = jb.mixer->n;
+                u.p = jb.p;
+                u.angles = jb.d_angles + (int64_t)s * 2 * jb.p;
+                u.E = jb.d_E + s;
+                u.grad = want_grad ? jb.d_grad + (int64_t)s * 2 * jb.p : nullptr;
+                u.init = static_cast<const float2 *>(jb.d_init);
+                u.tsize = kPhaseTable;
+                units.push_back(u);
+            }
+        }
+        return run_units(ctx, units, want_grad != 0, 1);
+    } catch (...) {
+        return fail(ctx, QAOA_ERR_OOM, "host allocation failed");
+    }
+}
+
+qaoa_status qaoa_set_profiling(qaoa_ctx *ctx, int enable) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    ctx->profiling = enable != 0;
+    return QAOA_OK;
+}
+
+int qaoa_kernel_stats(qaoa_ctx *ctx, qaoa_kernel_stat *out, int max) {
+    if (!ctx) return -1;
+    cudaSetDevice(ctx->device);
+    if (!ctx->pending.empty()) {
+        cudaStreamSynchronize(ctx->stream);
+        for (auto &pe : ctx->pending) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) ctx->fam_stats[pe.fam].ms += ms;
+            ctx->ev_pool.push_back(pe.a);
+            ctx->ev_pool.push_back(pe.b);
+        }
+        ctx->pending.clear();
+    }
+    const int nf = (int)ctx->fam_names.size();
+    for (int i = 0; i < nf && i < max && out; i++) {
+        std::memset(&out[i], 0, sizeof(out[i]));
+        std::snprintf(out[i].name, sizeof(out[i].name), "%s", ctx->fam_names[i].c_str());
+        out[i].launches = ctx->fam_stats[i].launches;
+        out[i].total_ms = ctx->fam_stats[i].ms;
+        out[i].algo_bytes = ctx->fam_stats[i].bytes;
+    }
+    return nf;
+}
+
+void qaoa_reset_stats(qaoa_ctx *ctx) {
+    if (!ctx) return;
+    qaoa_kernel_stats(ctx, nullptr, 0);
+    for (auto &s : ctx->fam_stats) s = StatAcc();
+    ctx->launches = 0;
+}
+
+int64_t qaoa_launch_count(const qaoa_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+}  // extern "C"
