@@ -14,22 +14,28 @@ enum DevErr : int {
     DERR_BAD_DESC = 1,   // a block found no launch descriptor for its index
     DERR_BAD_ANGLE = 2,  // a non-finite angle reached the coefficient kernel
     DERR_BAD_COST = 4,   // a u8 cost above the phase-table size
+    DERR_TIMEOUT = 8,    // a bounded mbarrier wait gave up
 };
 
 // ------------------------------------------------- per-round coefficients
 // Produced on the device from the float64 angles (prep kernel), consumed by
-// every mixer/phase kernel.  The X rotation e^{-i b X} = cos b - i sin b X is
-// applied in factored form: with |tan b| <= 1 it is cos b * (1 - i tan b X)
-// (bmode 0, bt = tan b, bs = cos b); otherwise sin b * (cot b - i X) (bmode 1,
-// bt = cot b, bs = sin b).  The scalar factor is applied once per pass.
+// every mixer/phase kernel.
+//
+// The pass kernels keep states in the twisted basis s_x = (-i)^{|x|} psi_x
+// (a diagonal unitary: it commutes with the phase separator and leaves |psi|^2
+// unchanged).  There e^{-i b X} becomes the real rotation
+// [[cos b, sin b], [-sin b, cos b]] acting alike on real and imaginary parts.
+// bmode 0 applies it as cos b * [[1, t], [-t, 1]], t = tan b, with the cos b
+// factors applied once per stage or per pass; bmode 2 (|cos b| tiny) applies
+// the rotation directly.
 struct RoundCoef {
-    float bt;
-    float bs;
-    int bmode;
-    float g_hi;  // gamma / (2 pi), float32 head
-    float g_lo;  // gamma / (2 pi) - g_hi, float32 tail
-    float cb;    // cos b
-    float sb;    // sin b
+    float bt;      // tan b
+    float cb;      // cos b
+    float sb;      // sin b
+    int bmode;     // 0: tan form, 2: direct form
+    float g_hi;    // gamma / (2 pi), float32 head
+    float g_lo;    // gamma / (2 pi) - g_hi, float32 tail
+    int rescale;   // 1: apply the cos factors after every stage (|cos b| < 1/4)
     float pad;
 };
 
@@ -43,8 +49,12 @@ enum PassFlags : uint32_t {
     PF_E = 2u,           // fwd: expectation partial after the rotations
     PF_LAM_FROM_C = 4u,  // bwd: lambda = C psi (first adjoint pass)
     PF_GEN_INIT = 8u,    // fwd: psi = amp0 everywhere instead of a load
-    PF_UNPHASE_PSI = 16u // bwd: also undo the phase on psi (psi_out written)
+    PF_UNPHASE_PSI = 16u, // bwd: also undo the phase on psi (psi_out written)
+    PF_TWIST_IN = 32u    // fwd: psi_in is a user state in the plain basis
 };
+
+// Per-warp partial sums per tile of the pass kernel.
+constexpr int kPassWarps = 8;
 
 // One pass of one unit (= one angle set of one problem).  A tile is 2^T
 // amplitudes: local bit j of the tile index maps to global bit gpos[j]; the
@@ -60,16 +70,26 @@ struct PassDesc {
     double *part_beta;    // [tile] partial sums, this pass
     double *part_gamma;   // [tile]
     double *part_E;       // [tile]
+    // TMA tensor maps (CUtensorMap, 64-byte aligned, device memory) of the
+    // gathered tile of psi_in / lam_in / cost, or nullptr: then the tile is
+    // fetched as 2^(T-c) one-dimensional bulk copies of 2^c elements.
+    const void *tm_psi;
+    const void *tm_lam;
+    const void *tm_cost;
     float amp0;
     uint32_t active;      // local bits rotated in this pass
     uint32_t flags;
     uint32_t ntiles;
     uint8_t n;
     uint8_t nfree;
-    uint8_t pad[2];
+    uint8_t c;            // local bits 0..c-1 are global bits 0..c-1 (one contiguous run)
+    uint8_t pad;
     uint8_t gpos[16];
     uint8_t fpos[36];
 };
+
+// Tile of the pass kernel: 2^12 amplitudes, 256 threads x 16 amplitudes.
+constexpr int kPassTileBits = 12;
 
 // Whole-state-on-chip kernel for small n (all rounds in one block).
 struct SmallDesc {
@@ -93,26 +113,33 @@ struct PrepDesc {
     int tsize;             // table entries used (<= kPhaseTable)
 };
 
-struct RedDesc {
-    const double *part;  // [(2p+1)][stride]
-    int64_t stride;
-    int cntE, cntB, cntG;
-    int p;
-    double *E_out;
-    double *grad_out;    // nullptr: expectation only
+// Two-level deterministic reduction of the per-(tile, warp) partial sums.
+// Level 1: one block per chunk of at most kRedChunk partials -> level2[i].
+// Level 2: one warp per output sums its chunks in order, times scale.
+constexpr int kRedChunk = 8192;
+struct RedChunk {
+    const double *src;
+    int cnt;
+    int pad;
+};
+struct RedOut {
+    int first;      // first chunk
+    int n;          // chunks
+    double *out;    // device result
+    double scale;   // 1 for <C>, 2 for the derivatives (2 Im <...>)
 };
 
 // ------------------------------------------------------- launch wrappers
 // Each returns the cudaError_t of the launch.
 cudaError_t launch_prep(const PrepDesc *d_descs, int ndesc, int *d_err, cudaStream_t s);
-cudaError_t launch_reduce(const RedDesc *d_descs, int ndesc, cudaStream_t s);
+cudaError_t launch_reduce(const RedChunk *d_chunks, int nchunks, double *d_level2, const RedOut *d_outs,
+                          int nouts, cudaStream_t s);
 cudaError_t launch_small(const SmallDesc *d_descs, int ndesc, int cost_dtype, int want_grad,
                          int max_n, int *d_err, cudaStream_t s);
-// T: tile bits (12, 13, 14); bwd: 0 forward, 1 adjoint.
-cudaError_t launch_xpass(int T, int bwd, int cost_dtype, const PassDesc *d_descs,
+// bwd: 0 forward, 1 adjoint.  Persistent launch over total_tiles tiles.
+cudaError_t launch_xpass(int bwd, int cost_dtype, const PassDesc *d_descs,
                          const uint32_t *d_tile_begin, int ndesc, uint32_t total_tiles,
                          int *d_err, cudaStream_t s);
-bool xpass_supported(int T, int bwd);
 int small_max_n();
 
 // Cost precompute (kernels_cost.cu).

@@ -33,6 +33,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace qg {
 namespace {
 
@@ -72,68 +74,109 @@ __device__ __forceinline__ float2 phase_f32(float C, float ghi, float glo) {
     return make_float2(c, -s);
 }
 
-// Rotation e^{-i b X} on register pairs (i, i | 1<<RB), without its scalar
-// factor (see RoundCoef).
+// ----------------------------------------------------------------------------
+// Packed (f32x2) rotations in the twisted basis s_x = (-i)^{|x|} psi_x, where
+// e^{-i b X} on a qubit is the real matrix [[c, s], [-s, c]] applied to the
+// (re, im) pair of both amplitudes alike.  Register pairs (i, i | 1<<RB).
+struct Rot {
+    float2 tt, ntt;  // (t, t), (-t, -t), t = tan b   (bmode 0)
+    float c, s;      // cos b, sin b                  (bmode 2)
+    float psc;       // pair-term scale per rotation: c^2 (bmode 0) or 1
+    int mode;
+};
+
 template <int RB>
-__device__ __forceinline__ void rot_pairs(float2 (&a)[32], float t, int mode) {
-    if (mode == 0) {
+__device__ __forceinline__ void rot_pairs(float2 (&a)[16], const Rot &R) {
+    if (R.mode == 0) {
 #pragma unroll
-        for (int i = 0; i < 32; i++) {
+        for (int i = 0; i < 16; i++) {
             if (i & (1 << RB)) continue;
             const int j = i | (1 << RB);
             const float2 x = a[i], y = a[j];
-            a[i] = make_float2(fmaf(t, y.y, x.x), fmaf(-t, y.x, x.y));
-            a[j] = make_float2(fmaf(t, x.y, y.x), fmaf(-t, x.x, y.y));
+            a[i] = __ffma2_rn(R.tt, y, x);   // s0 + t s1
+            a[j] = __ffma2_rn(R.ntt, x, y);  // s1 - t s0
         }
     } else {
+        const float2 cc = make_float2(R.c, R.c), ss = make_float2(R.s, R.s), nss = make_float2(-R.s, -R.s);
 #pragma unroll
-        for (int i = 0; i < 32; i++) {
+        for (int i = 0; i < 16; i++) {
             if (i & (1 << RB)) continue;
             const int j = i | (1 << RB);
             const float2 x = a[i], y = a[j];
-            a[i] = make_float2(fmaf(t, x.x, y.y), fmaf(t, x.y, -y.x));
-            a[j] = make_float2(fmaf(t, y.x, x.y), fmaf(t, y.y, -x.x));
+            a[i] = __ffma2_rn(ss, y, __fmul2_rn(cc, x));   // c s0 + s s1
+            a[j] = __ffma2_rn(nss, x, __fmul2_rn(cc, y));  // c s1 - s s0
         }
     }
 }
 
-// sum over register pairs of Im( conj(l_a) p_b + conj(l_b) p_a ), i.e. this
-// thread's share of Im <l| X_q |p> for the qubit on register bit RB.
+// This thread's share of Im <lambda| X_q |psi> in the twisted basis, where
+// X_q becomes [[0, i], [-i, 0]]: sum over pairs of l0.p1 - l1.p0 (real dot
+// products of (re, im) pairs), with four independent packed accumulators.
 template <int RB>
-__device__ __forceinline__ float pair_im(const float2 (&l)[32], const float2 (&p)[32]) {
-    float s = 0.f;
+__device__ __forceinline__ float pair_dot(const float2 (&l)[16], const float2 (&p)[16]) {
+    float2 ap[4], am[4];
 #pragma unroll
-    for (int i = 0; i < 32; i++) {
+    for (int k = 0; k < 4; k++) ap[k] = am[k] = make_float2(0.f, 0.f);
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
         if (i & (1 << RB)) continue;
         const int j = i | (1 << RB);
-        s = fmaf(l[i].x, p[j].y, s);
-        s = fmaf(-l[i].y, p[j].x, s);
-        s = fmaf(l[j].x, p[i].y, s);
-        s = fmaf(-l[j].y, p[i].x, s);
+        ap[k & 3] = __ffma2_rn(l[i], p[j], ap[k & 3]);
+        am[k & 3] = __ffma2_rn(l[j], p[i], am[k & 3]);
+        k++;
     }
-    return s;
+    const float2 sp = __fadd2_rn(__fadd2_rn(ap[0], ap[1]), __fadd2_rn(ap[2], ap[3]));
+    const float2 sm = __fadd2_rn(__fadd2_rn(am[0], am[1]), __fadd2_rn(am[2], am[3]));
+    return (sp.x + sp.y) - (sm.x + sm.y);
 }
 
-// One rotation step on register bit RB if its local qubit is active.
+// One rotation step on register bit RB if its qubit is active.
 template <int RB, int BWD>
-__device__ __forceinline__ void rot_step(float2 (&a)[32], float2 (&b)[32], uint32_t active, int lb,
-                                         float t, int mode, float sc2, float &pscale, float &bacc) {
-    if (!((active >> lb) & 1u)) return;
+__device__ __forceinline__ void rot_step(float2 (&a)[16], float2 (&l)[16], bool on, const Rot &R,
+                                         float &pscale, float &bacc) {
+    if (!on) return;
     if (BWD) {
-        bacc = fmaf(pair_im<RB>(b, a), pscale, bacc);
-        pscale *= sc2;
-        rot_pairs<RB>(b, t, mode);
+        bacc = fmaf(pair_dot<RB>(l, a), pscale, bacc);
+        pscale *= R.psc;
+        rot_pairs<RB>(l, R);
     }
-    rot_pairs<RB>(a, t, mode);
+    rot_pairs<RB>(a, R);
+}
+
+template <int BWD>
+__device__ __forceinline__ void scale_all(float2 (&a)[16], float2 (&l)[16], float f) {
+    const float2 ff = make_float2(f, f);
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        a[i] = __fmul2_rn(ff, a[i]);
+        if (BWD) l[i] = __fmul2_rn(ff, l[i]);
+    }
+}
+
+// (-i)^k * v
+__device__ __forceinline__ float2 twist(float2 v, int k) {
+    switch (k & 3) {
+    case 0: return v;
+    case 1: return make_float2(v.y, -v.x);
+    case 2: return make_float2(-v.x, -v.y);
+    default: return make_float2(-v.y, v.x);
+    }
+}
+
+// Warp sum of one float per lane in float64 (fixed order); valid in lane 0.
+__device__ __forceinline__ double warp_sum(float v) {
+    double d = (double)v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    return d;
 }
 
 // Deterministic block sum of one float per thread, accumulated in float64;
 // the result is valid in thread 0.
 template <int NW>
 __device__ __forceinline__ double block_sum(float v, double *red) {
-    double d = (double)v;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    double d = warp_sum(v);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = d;
     __syncthreads();
@@ -162,242 +205,434 @@ __device__ __forceinline__ int find_desc(const uint32_t *__restrict__ tile_begin
     return found;
 }
 
+// ----------------------------------------------------------- TMA / mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after kSpinLimit polls (seconds), never hangs.
+constexpr uint32_t kSpinLimit = 1u << 22;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+// One bulk (TMA) copy global -> shared, completing on mbarrier `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+// One TMA tensor copy of a 4-d box (coordinates c0..c3) global -> shared.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
 // --------------------------------------------------------------------------
-// The pass kernel.  T: tile bits; BWD: 0 forward, 1 adjoint; COST: 0 float32,
-// 1 uint8 cost.  Register layouts of a tile (local bit numbers), W = T - 10:
-//   stage 1: amp bit 0 -> local 0 (inside a 16-byte vector), lanes -> 1..5,
-//            warps -> 6..5+W, amp bits 1..4 -> 6+W..T-1
-//   stage 2: amp bits 0..4 -> 1..5, lanes -> {0,6,7,8,9}, warps -> 10..T-1
-//   stage 3: amp bits 0..4 -> 6..10, lanes -> 0..4, warps -> {5, 11..T-1}
-// Rotated on stage 1: local 0 and 6+W..T-1; stage 2: 1..5; stage 3: 6..5+W.
-template <int T, int BWD, int COST>
-__global__ void __launch_bounds__(1 << (T - 5), (BWD || T >= 14) ? 1 : 2)
-xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ tile_begin,
-             int ndesc, int *err) {
-    constexpr int NT = 1 << (T - 5);
-    constexpr int NW = NT / 32;
-    constexpr int W = T - 10;
-    constexpr int S1R0 = 6 + W;
-    constexpr int TILE = 1 << T;
+// The pass kernel (persistent).  A tile is 2^12 amplitudes; 256 threads hold
+// 16 amplitudes each (per vector).  Tile-local bit j is global bit gpos[j]
+// (bits 0..c-1 are the contiguous run).  Register layouts (local bits):
+//   stage 1: amp bit 0 -> 0 (16-byte pair), lanes -> 1..5, warps -> 6..8,
+//            amp bits 1..3 -> 9..11                (read from the TMA buffer)
+//   stage 2: amp bits 0..3 -> 1..4, lanes -> {0,6,7,8,5}, warps -> 9..11
+//   stage 3: amp bits 0..3 -> 5..8, lanes -> 0..4, warps -> 9..11  (stores)
+// Rotated on stage 1: local 0, 9, 10, 11; stage 2: 1..4; stage 3: 5..8.
+//
+// Pipeline: warp 0 loads the tiles of this CTA with TMA copies into NBUF
+// shared-memory buffers (completion on one mbarrier per buffer; the tile's
+// descriptor index and base offset travel with it through the barrier); a
+// tile is transposed in place in its buffer, which goes back to the loader as
+// soon as its last stage has been read.
+constexpr int kT = kPassTileBits;
+constexpr int kTile = 1 << kT;
+constexpr int kNT = 256;
+constexpr int kNW = kNT / 32;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *sm_a = reinterpret_cast<float2 *>(smem_raw);
-    float2 *sm_b = sm_a + TILE;                         // adjoint only
-    float2 *stab = sm_a + (BWD ? 2 : 1) * TILE;          // phase table
-    __shared__ PassDesc D;
-    __shared__ int s_di;
-    __shared__ double s_red[NW];
+__device__ __forceinline__ uint32_t deposit(uint32_t v, const uint8_t *pos, int nbits) {
+    uint32_t o = 0;
+    for (int k = 0; k < nbits; k++) o |= ((v >> k) & 1u) << pos[k];
+    return o;
+}
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_di = find_desc(tile_begin, ndesc, blockIdx.x);
-    __syncthreads();
-    const int di = s_di;
+template <int BWD, int COST>
+struct PassGeom {
+    static constexpr uint32_t kPsiB = kTile * 8;
+    static constexpr uint32_t kCostB = kTile * (COST == 0 ? 4 : 1);
+    static constexpr uint32_t kBufB = kPsiB * (BWD ? 2 : 1) + kCostB;
+    static constexpr uint32_t kHead = 256 + kPhaseTable * 8;  // barriers, tile info, phase table
+};
+
+struct TileInfo {
+    int di;
+    uint32_t tl;    // tile index within the descriptor
+    uint32_t base;  // global element offset of local index 0
+    uint32_t pad;
+};
+
+template <int BWD>
+__device__ __forceinline__ bool needs_cost(uint32_t flags) {
+    return BWD ? (flags & (PF_LAM_FROM_C | PF_PHASE)) != 0 : (flags & (PF_PHASE | PF_E)) != 0;
+}
+
+// Warp 0: start the loads of tile t into buffer buf (all 32 lanes call).
+template <int BWD, int COST>
+__device__ __forceinline__ void issue_tile(uint32_t t, unsigned char *buf, uint32_t bar, TileInfo *info,
+                                           const PassDesc *__restrict__ descs,
+                                           const uint32_t *__restrict__ tile_begin, int ndesc) {
+    using G = PassGeom<BWD, COST>;
+    const int lane = threadIdx.x & 31;
+    const int di = find_desc(tile_begin, ndesc, t);
+    fence_proxy_async();
     if (di < 0) {
-        if (tid == 0) atomicOr(err, DERR_BAD_DESC);
+        if (lane == 0) {
+            info->di = -1;
+            mbar_arrive_tx(bar, 0);
+        }
         return;
     }
-    {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(descs + di);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(&D);
-        for (int i = tid; i < (int)(sizeof(PassDesc) / 4); i += NT) dst[i] = src[i];
+    const PassDesc *Dg = descs + di;
+    const uint32_t flags = Dg->flags;
+    const int c = Dg->c;
+    const uint32_t tl = t - tile_begin[di];
+    const uint32_t base = deposit(tl, Dg->fpos, Dg->nfree);
+    const bool ld_psi = BWD || !(flags & PF_GEN_INIT);
+    const bool ld_lam = BWD && !(flags & PF_LAM_FROM_C);
+    const bool ld_cost = needs_cost<BWD>(flags);
+    const uint32_t bytes = (ld_psi ? G::kPsiB : 0) + (ld_lam ? G::kPsiB : 0) + (ld_cost ? G::kCostB : 0);
+    if (lane == 0) {
+        info->di = di;
+        info->tl = tl;
+        info->base = base;
+        mbar_arrive_tx(bar, bytes);
+    }
+    __syncwarp();
+    const uint32_t sb = smem_u32(buf);
+    const float2 *psi = Dg->psi_in;
+    const float2 *lam = Dg->lam_in;
+    const unsigned char *cost = static_cast<const unsigned char *>(Dg->cost);
+    constexpr uint32_t cb = COST == 0 ? 4 : 1;
+    // Gathered tile with a tensor map: one TMA op per operand.  Box = 2^c
+    // contiguous elements x 2^(T-c) rows at stride 2^lo; tile coordinates
+    // are the free bits below lo (dim 1) and above lo + T - c (dim 3).
+    const void *tm_psi = Dg->tm_psi, *tm_lam = Dg->tm_lam, *tm_cost = Dg->tm_cost;
+    bool seg_psi = ld_psi, seg_lam = ld_lam, seg_cost = ld_cost;
+    if (lane == 0 && (tm_psi || tm_lam || tm_cost)) {
+        const int lo = Dg->gpos[c];  // gathered pass: lo > c
+        const int c1 = (int)(tl & ((1u << (lo - c)) - 1u)), c3 = (int)(tl >> (lo - c));
+        if (ld_psi && tm_psi) tma_load_4d(sb, tm_psi, 0, c1, 0, c3, bar);
+        if (ld_lam && tm_lam) tma_load_4d(sb + G::kPsiB, tm_lam, 0, c1, 0, c3, bar);
+        if (ld_cost && tm_cost) tma_load_4d(sb + G::kPsiB * (BWD ? 2 : 1), tm_cost, 0, c1, 0, c3, bar);
+    }
+    seg_psi = seg_psi && !tm_psi;
+    seg_lam = seg_lam && !tm_lam;
+    seg_cost = seg_cost && !tm_cost;
+    if (!(seg_psi || seg_lam || seg_cost)) return;
+    const int nseg = 1 << (kT - c);
+    const uint32_t segn = 1u << c;
+    for (int s = lane; s < nseg; s += 32) {
+        const uint32_t off = base + deposit((uint32_t)s, Dg->gpos + c, kT - c);
+        const uint32_t ls = (uint32_t)s << c;
+        if (seg_psi) bulk_g2s(sb + ls * 8, psi + off, segn * 8, bar);
+        if (seg_lam) bulk_g2s(sb + G::kPsiB + ls * 8, lam + off, segn * 8, bar);
+        if (seg_cost)
+            bulk_g2s(sb + G::kPsiB * (BWD ? 2 : 1) + ls * cb, cost + (size_t)off * cb, segn * cb, bar);
+    }
+}
+
+template <int BWD, int COST, int NBUF>
+__global__ void __launch_bounds__(kNT, (BWD && NBUF > 1) ? 1 : 2)
+xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ tile_begin, int ndesc,
+             uint32_t total, int *err) {
+    using G = PassGeom<BWD, COST>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+    TileInfo *tinfo = reinterpret_cast<TileInfo *>(smem_raw + 64);
+    float2 *stab = reinterpret_cast<float2 *>(smem_raw + 256);
+    unsigned char *bufs = smem_raw + G::kHead;
+    __shared__ PassDesc D;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int b = 0; b < NBUF; b++) mbar_init(smem_u32(&bars[b]), 1);
+        fence_mbar_init();
     }
     __syncthreads();
-    const uint32_t tile = blockIdx.x - tile_begin[di];
-    const uint32_t flags = D.flags;
-    const uint32_t active = D.active;
-
-    if (COST == 1 && (flags & PF_PHASE)) {
-        for (int i = tid; i < kPhaseTable; i += NT) stab[i] = D.table[i];
-        __syncthreads();
+    const uint32_t stride = gridDim.x;
+    if (warp == 0) {
+        for (int k = 0; k < NBUF; k++) {
+            const uint32_t t = blockIdx.x + (uint32_t)k * stride;
+            if (t < total)
+                issue_tile<BWD, COST>(t, bufs + k * G::kBufB, smem_u32(&bars[k]), &tinfo[k], descs, tile_begin,
+                                      ndesc);
+        }
     }
 
-    const RoundCoef cf = *D.coef;
-    float t = cf.bt, sc = cf.bs;
-    const int mode = cf.bmode;
-    if (BWD) {  // undo: e^{+i b X}, i.e. the coefficients of -b
-        t = -t;
-        if (mode) sc = -sc;
-    }
-    const float sc2 = sc * sc;
-    const float ghi = cf.g_hi, glo = cf.g_lo;
+    // per-descriptor constants
+    int cur = -1;
+    Rot R;
+    float ghi = 0.f, glo = 0.f, amp0 = 0.f;
+    float fs1 = 1.f, fs2 = 1.f, fs3 = 1.f, fse = 1.f;
+    uint32_t flags = 0, active = 0, g3 = 0;
+    uint32_t rs3[4] = {0, 0, 0, 0};
+    bool rescale = false;
 
-    // Element offsets fit 32 bits: the X path is limited to n <= 32.
-    uint32_t base = 0;
-    for (int bb = 0; bb < D.nfree; bb++) base |= ((tile >> bb) & 1u) << D.fpos[bb];
-    auto gofs = [&](uint32_t l) {
-        uint32_t o = 0;
-#pragma unroll
-        for (int j = 0; j < T; j++)
-            if ((l >> j) & 1u) o += 1u << D.gpos[j];
-        return o;
-    };
-
-    float2 a[32];  // psi
-    float2 b[32];  // lambda (adjoint)
-    float pscale = 1.f, bacc = 0.f;
-
-    // ---------------- stage 1: coalesced load, phase / lambda = C psi
     const uint32_t l1 = ((uint32_t)lane << 1) | ((uint32_t)warp << 6);
-    {
-        const uint32_t g1 = base + gofs(l1);
-        uint32_t rs[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) rs[k] = 1u << D.gpos[S1R0 + k];
-        const bool gen = !BWD && (flags & PF_GEN_INIT);
-        const bool need_c = BWD ? (flags & PF_LAM_FROM_C) : (flags & PF_PHASE);
-#pragma unroll
-        for (int r = 0; r < 16; r++) {
-            const uint32_t off = g1 + ((r & 1) ? rs[0] : 0) + ((r & 2) ? rs[1] : 0) +
-                                 ((r & 4) ? rs[2] : 0) + ((r & 8) ? rs[3] : 0);
-            if (gen) {
-                a[2 * r] = make_float2(D.amp0, 0.f);
-                a[2 * r + 1] = make_float2(D.amp0, 0.f);
-            } else {
-                const float4 v = __ldcs(reinterpret_cast<const float4 *>(D.psi_in + off));
-                a[2 * r] = make_float2(v.x, v.y);
-                a[2 * r + 1] = make_float2(v.z, v.w);
+    const uint32_t l2 = ((uint32_t)lane & 1u) | ((((uint32_t)lane >> 1) & 7u) << 6) |
+                        ((((uint32_t)lane >> 4) & 1u) << 5) | ((uint32_t)warp << 9);
+    const uint32_t l3 = (uint32_t)lane | ((uint32_t)warp << 9);
+    const uint32_t p1 = swz(l1), p2 = swz(l2), p3 = swz(l3);
+
+    for (uint32_t it = 0;; it++) {
+        const uint32_t t = blockIdx.x + it * stride;
+        if (t >= total) break;
+        const int b = (int)(it % NBUF);
+        const uint32_t bar = smem_u32(&bars[b]);
+        const bool ok = mbar_wait(bar, (it / NBUF) & 1u);
+        const TileInfo ti = tinfo[b];
+        const int di = ok ? ti.di : -1;
+        if (di != cur) {  // uniform: every thread read the same tile info
+            __syncthreads();  // the previous tile's epilogue is done with D / stab
+            if (di < 0) {
+                if (tid == 0) atomicOr(err, ok ? DERR_BAD_DESC : DERR_TIMEOUT);
+                // let every load this CTA started land before the block exits
+                for (int k = 1; k < NBUF; k++) {
+                    const uint32_t tk = t + (uint32_t)k * stride;
+                    if (tk < total) mbar_wait(smem_u32(&bars[(it + k) % NBUF]), ((it + k) / NBUF) & 1u);
+                }
+                if (!ok) mbar_wait(bar, (it / NBUF) & 1u);
+                return;
             }
-            if (BWD && !(flags & PF_LAM_FROM_C)) {
-                const float4 v = __ldcs(reinterpret_cast<const float4 *>(D.lam_in + off));
-                b[2 * r] = make_float2(v.x, v.y);
-                b[2 * r + 1] = make_float2(v.z, v.w);
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(descs + di);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&D);
+            for (int i = tid; i < (int)(sizeof(PassDesc) / 4); i += kNT) dst[i] = src[i];
+            __syncthreads();
+            const RoundCoef cf = *D.coef;
+            flags = D.flags;
+            active = D.active;
+            amp0 = D.amp0;
+            // undoing a round (adjoint) uses the coefficients of -b
+            const float sgn = BWD ? -1.f : 1.f;
+            R.mode = cf.bmode;
+            R.tt = make_float2(sgn * cf.bt, sgn * cf.bt);
+            R.ntt = make_float2(-sgn * cf.bt, -sgn * cf.bt);
+            R.c = cf.cb;
+            R.s = sgn * cf.sb;
+            R.psc = cf.bmode == 0 ? cf.cb * cf.cb : 1.f;
+            rescale = cf.bmode == 0 && cf.rescale;
+            {
+                const float c = cf.bmode == 0 ? cf.cb : 1.f;
+                const int k1 = __popc(active & 0xE01u), k2 = __popc(active & 0x1Eu), k3 = __popc(active & 0x1E0u);
+                float p = 1.f;
+                fs1 = fs2 = fs3 = 1.f;
+                for (int k = 0; k < k1; k++) fs1 *= c;
+                for (int k = 0; k < k2; k++) fs2 *= c;
+                for (int k = 0; k < k3; k++) fs3 *= c;
+                p = fs1 * fs2 * fs3;
+                fse = rescale ? 1.f : p;
             }
-            if (need_c) {
-                float c0, c1;
-                if (COST == 0) {
-                    const float2 cc = __ldg(reinterpret_cast<const float2 *>(D.cost) + (off >> 1));
-                    c0 = cc.x;
-                    c1 = cc.y;
+            ghi = cf.g_hi;
+            glo = cf.g_lo;
+            g3 = 0;
+            for (int j = 0; j < kT; j++)
+                if ((l3 >> j) & 1u) g3 += 1u << D.gpos[j];
+#pragma unroll
+            for (int k = 0; k < 4; k++) rs3[k] = 1u << D.gpos[5 + k];
+            if (COST == 1 && (flags & PF_PHASE))
+                for (int i = tid; i < kPhaseTable; i += kNT) stab[i] = D.table[i];
+            __syncthreads();
+            cur = di;
+        }
+        const uint32_t base = ti.base, tl = ti.tl;
+
+        float2 *sp = reinterpret_cast<float2 *>(bufs + b * G::kBufB);
+        float2 *sl = sp + kTile;
+        const unsigned char *scost = bufs + b * G::kBufB + G::kPsiB * (BWD ? 2 : 1);
+        float2 a[16];
+        float2 l[16];
+        float pscale = 1.f, bacc = 0.f;
+
+        // ---------------- stage 1: read the landed tile, phase / lambda = C psi
+        {
+            const bool gen = !BWD && (flags & PF_GEN_INIT);
+            const bool twist_in = !BWD && (flags & PF_TWIST_IN);
+            const bool need_c = BWD ? (flags & PF_LAM_FROM_C) : (flags & PF_PHASE);
+            const int k0 = __popc(base) + __popc(l1);
+#pragma unroll
+            for (int r = 0; r < 8; r++) {
+                const uint32_t idx = l1 | ((uint32_t)r << 9);
+                if (gen) {
+                    a[2 * r] = twist(make_float2(amp0, 0.f), k0 + __popc(r));
+                    a[2 * r + 1] = twist(make_float2(amp0, 0.f), k0 + __popc(r) + 1);
                 } else {
-                    const uchar2 cc = __ldg(reinterpret_cast<const uchar2 *>(D.cost) + (off >> 1));
-                    c0 = (float)cc.x;
-                    c1 = (float)cc.y;
-                    if (!BWD) {
-                        a[2 * r] = cmul(a[2 * r], stab[cc.x]);
-                        a[2 * r + 1] = cmul(a[2 * r + 1], stab[cc.y]);
+                    const float4 v = *reinterpret_cast<const float4 *>(sp + idx);
+                    a[2 * r] = make_float2(v.x, v.y);
+                    a[2 * r + 1] = make_float2(v.z, v.w);
+                    if (twist_in) {
+                        a[2 * r] = twist(a[2 * r], k0 + __popc(r));
+                        a[2 * r + 1] = twist(a[2 * r + 1], k0 + __popc(r) + 1);
                     }
                 }
-                if (BWD) {
-                    b[2 * r] = make_float2(c0 * a[2 * r].x, c0 * a[2 * r].y);
-                    b[2 * r + 1] = make_float2(c1 * a[2 * r + 1].x, c1 * a[2 * r + 1].y);
-                } else if (COST == 0) {
-                    a[2 * r] = cmul(a[2 * r], phase_f32(c0, ghi, glo));
-                    a[2 * r + 1] = cmul(a[2 * r + 1], phase_f32(c1, ghi, glo));
+                if (BWD && !(flags & PF_LAM_FROM_C)) {
+                    const float4 v = *reinterpret_cast<const float4 *>(sl + idx);
+                    l[2 * r] = make_float2(v.x, v.y);
+                    l[2 * r + 1] = make_float2(v.z, v.w);
+                }
+                if (need_c) {
+                    float c0, c1;
+                    if (COST == 0) {
+                        const float2 cc = *reinterpret_cast<const float2 *>(
+                            reinterpret_cast<const float *>(scost) + idx);
+                        c0 = cc.x;
+                        c1 = cc.y;
+                    } else {
+                        const uchar2 cc = *reinterpret_cast<const uchar2 *>(scost + idx);
+                        c0 = (float)cc.x;
+                        c1 = (float)cc.y;
+                        if (!BWD) {
+                            a[2 * r] = cmul(a[2 * r], stab[cc.x]);
+                            a[2 * r + 1] = cmul(a[2 * r + 1], stab[cc.y]);
+                        }
+                    }
+                    if (BWD) {
+                        l[2 * r] = __fmul2_rn(make_float2(c0, c0), a[2 * r]);
+                        l[2 * r + 1] = __fmul2_rn(make_float2(c1, c1), a[2 * r + 1]);
+                    } else if (COST == 0) {
+                        a[2 * r] = cmul(a[2 * r], phase_f32(c0, ghi, glo));
+                        a[2 * r + 1] = cmul(a[2 * r + 1], phase_f32(c1, ghi, glo));
+                    }
                 }
             }
         }
-    }
-    rot_step<0, BWD>(a, b, active, 0, t, mode, sc2, pscale, bacc);
-    rot_step<1, BWD>(a, b, active, S1R0 + 0, t, mode, sc2, pscale, bacc);
-    rot_step<2, BWD>(a, b, active, S1R0 + 1, t, mode, sc2, pscale, bacc);
-    rot_step<3, BWD>(a, b, active, S1R0 + 2, t, mode, sc2, pscale, bacc);
-    rot_step<4, BWD>(a, b, active, S1R0 + 3, t, mode, sc2, pscale, bacc);
+        rot_step<0, BWD>(a, l, active & (1u << 0), R, pscale, bacc);
+        rot_step<1, BWD>(a, l, active & (1u << 9), R, pscale, bacc);
+        rot_step<2, BWD>(a, l, active & (1u << 10), R, pscale, bacc);
+        rot_step<3, BWD>(a, l, active & (1u << 11), R, pscale, bacc);
+        if (rescale) {
+            scale_all<BWD>(a, l, fs1);
+            pscale = 1.f;
+        }
 
-    // ---------------- stage 1 -> stage 2 transpose
-    const uint32_t p1 = swz(l1);
+        // ---------------- stage 1 -> 2, in place (swizzled)
+        __syncthreads();
 #pragma unroll
-    for (int r = 0; r < 16; r++) {
-        const uint32_t idx = p1 ^ swz((uint32_t)r << S1R0);
-        *reinterpret_cast<float4 *>(sm_a + idx) =
-            make_float4(a[2 * r].x, a[2 * r].y, a[2 * r + 1].x, a[2 * r + 1].y);
-        if (BWD)
-            *reinterpret_cast<float4 *>(sm_b + idx) =
-                make_float4(b[2 * r].x, b[2 * r].y, b[2 * r + 1].x, b[2 * r + 1].y);
-    }
-    __syncthreads();
-    const uint32_t l2 = ((uint32_t)lane & 1u) | ((((uint32_t)lane >> 1) & 15u) << 6) |
-                        ((uint32_t)warp << 10);
-    const uint32_t p2 = swz(l2);
+        for (int r = 0; r < 8; r++) {
+            const uint32_t idx = p1 ^ swz((uint32_t)r << 9);
+            *reinterpret_cast<float4 *>(sp + idx) = make_float4(a[2 * r].x, a[2 * r].y, a[2 * r + 1].x, a[2 * r + 1].y);
+            if (BWD)
+                *reinterpret_cast<float4 *>(sl + idx) =
+                    make_float4(l[2 * r].x, l[2 * r].y, l[2 * r + 1].x, l[2 * r + 1].y);
+        }
+        __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 32; i++) {
-        a[i] = sm_a[p2 ^ swz((uint32_t)i << 1)];
-        if (BWD) b[i] = sm_b[p2 ^ swz((uint32_t)i << 1)];
-    }
-    rot_step<0, BWD>(a, b, active, 1, t, mode, sc2, pscale, bacc);
-    rot_step<1, BWD>(a, b, active, 2, t, mode, sc2, pscale, bacc);
-    rot_step<2, BWD>(a, b, active, 3, t, mode, sc2, pscale, bacc);
-    rot_step<3, BWD>(a, b, active, 4, t, mode, sc2, pscale, bacc);
-    rot_step<4, BWD>(a, b, active, 5, t, mode, sc2, pscale, bacc);
+        for (int i = 0; i < 16; i++) {
+            a[i] = sp[p2 ^ ((uint32_t)i << 1)];
+            if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
+        }
+        rot_step<0, BWD>(a, l, active & (1u << 1), R, pscale, bacc);
+        rot_step<1, BWD>(a, l, active & (1u << 2), R, pscale, bacc);
+        rot_step<2, BWD>(a, l, active & (1u << 3), R, pscale, bacc);
+        rot_step<3, BWD>(a, l, active & (1u << 4), R, pscale, bacc);
+        if (rescale) {
+            scale_all<BWD>(a, l, fs2);
+            pscale = 1.f;
+        }
 
-    // ---------------- stage 2 -> stage 3 transpose
-    __syncthreads();
+        // ---------------- stage 2 -> 3
+        __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 32; i++) {
-        sm_a[p2 ^ swz((uint32_t)i << 1)] = a[i];
-        if (BWD) sm_b[p2 ^ swz((uint32_t)i << 1)] = b[i];
-    }
-    __syncthreads();
-    const uint32_t l3 = (uint32_t)lane | (((uint32_t)warp & 1u) << 5) | (((uint32_t)warp >> 1) << 11);
-    const uint32_t p3 = swz(l3);
+        for (int i = 0; i < 16; i++) {
+            sp[p2 ^ ((uint32_t)i << 1)] = a[i];
+            if (BWD) sl[p2 ^ ((uint32_t)i << 1)] = l[i];
+        }
+        __syncthreads();
+        const bool epi_c = BWD ? (flags & PF_PHASE) : (flags & PF_E);
+        float cst[16];
 #pragma unroll
-    for (int i = 0; i < 32; i++) {
-        a[i] = sm_a[p3 ^ swz((uint32_t)i << 6)];
-        if (BWD) b[i] = sm_b[p3 ^ swz((uint32_t)i << 6)];
-    }
-    rot_step<0, BWD>(a, b, active, 6, t, mode, sc2, pscale, bacc);
-    if (W > 1) rot_step<1, BWD>(a, b, active, 7, t, mode, sc2, pscale, bacc);
-    if (W > 2) rot_step<2, BWD>(a, b, active, 8, t, mode, sc2, pscale, bacc);
-    if (W > 3) rot_step<3, BWD>(a, b, active, 9, t, mode, sc2, pscale, bacc);
-
-    // ---------------- stage 3: scalar factor, fused epilogue, coalesced store
-    {
-        float fs = 1.f;
-        const int nrot = __popc(active);
-        for (int k = 0; k < nrot; k++) fs *= sc;
-#pragma unroll
-        for (int i = 0; i < 32; i++) {
-            a[i].x *= fs;
-            a[i].y *= fs;
-            if (BWD) {
-                b[i].x *= fs;
-                b[i].y *= fs;
+        for (int i = 0; i < 16; i++) {
+            const uint32_t idx = p3 ^ swz((uint32_t)i << 5);
+            a[i] = sp[idx];
+            if (BWD) l[i] = sl[idx];
+            if (epi_c) {
+                const uint32_t ci = l3 | ((uint32_t)i << 5);
+                cst[i] = COST == 0 ? reinterpret_cast<const float *>(scost)[ci] : (float)scost[ci];
             }
         }
-    }
-    const uint32_t g3 = base + gofs(l3);
-    uint32_t rs3[5];
-#pragma unroll
-    for (int k = 0; k < 5; k++) rs3[k] = 1u << D.gpos[6 + k];
-    const bool epi_c = BWD ? (flags & PF_PHASE) : (flags & PF_E);
-    float eacc = 0.f;
-#pragma unroll
-    for (int i = 0; i < 32; i++) {
-        const uint32_t off = g3 + ((i & 1) ? rs3[0] : 0) + ((i & 2) ? rs3[1] : 0) +
-                             ((i & 4) ? rs3[2] : 0) + ((i & 8) ? rs3[3] : 0) +
-                             ((i & 16) ? rs3[4] : 0);
-        if (epi_c) {
-            float C;
-            float2 ph;
-            if (COST == 0) {
-                C = __ldg(reinterpret_cast<const float *>(D.cost) + off);
-                if (BWD) ph = phase_f32(C, ghi, glo);
-            } else {
-                const unsigned char cc = __ldg(reinterpret_cast<const unsigned char *>(D.cost) + off);
-                C = (float)cc;
-                if (BWD) ph = stab[cc];
-            }
-            if (!BWD) {
-                eacc = fmaf(C, fmaf(a[i].x, a[i].x, a[i].y * a[i].y), eacc);
-            } else {
-                // gamma partial: C Im(conj(mu) phi), then undo the phase
-                eacc = fmaf(C, fmaf(b[i].x, a[i].y, -b[i].y * a[i].x), eacc);
-                b[i] = cmul_conj(b[i], ph);
-                if (flags & PF_UNPHASE_PSI) a[i] = cmul_conj(a[i], ph);
-            }
+        // the buffer is consumed: start the tile NBUF ahead
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t tn = t + (uint32_t)NBUF * stride;
+            if (tn < total)
+                issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc);
         }
-        if (D.psi_out) __stcs(D.psi_out + off, a[i]);
-        if (BWD && D.lam_out) __stcs(D.lam_out + off, b[i]);
-    }
-    if (BWD) {
-        const double tb = block_sum<NW>(bacc, s_red);
-        if (tid == 0 && D.part_beta) D.part_beta[tile] = tb;
-        if (flags & PF_PHASE) {
-            const double tg = block_sum<NW>(eacc, s_red);
-            if (tid == 0 && D.part_gamma) D.part_gamma[tile] = tg;
+        rot_step<0, BWD>(a, l, active & (1u << 5), R, pscale, bacc);
+        rot_step<1, BWD>(a, l, active & (1u << 6), R, pscale, bacc);
+        rot_step<2, BWD>(a, l, active & (1u << 7), R, pscale, bacc);
+        rot_step<3, BWD>(a, l, active & (1u << 8), R, pscale, bacc);
+        scale_all<BWD>(a, l, rescale ? fs3 : fse);
+
+        // ---------------- stage 3: fused epilogue, coalesced store
+        const uint32_t g = base + g3;
+        float eacc = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const uint32_t off = g + ((i & 1) ? rs3[0] : 0) + ((i & 2) ? rs3[1] : 0) +
+                                 ((i & 4) ? rs3[2] : 0) + ((i & 8) ? rs3[3] : 0);
+            if (epi_c) {
+                const float C = cst[i];
+                if (!BWD) {
+                    eacc = fmaf(C, fmaf(a[i].x, a[i].x, a[i].y * a[i].y), eacc);
+                } else {
+                    const float2 ph = COST == 0 ? phase_f32(C, ghi, glo) : stab[(int)C];
+                    eacc = fmaf(C, fmaf(l[i].x, a[i].y, -l[i].y * a[i].x), eacc);
+                    l[i] = cmul_conj(l[i], ph);
+                    if (flags & PF_UNPHASE_PSI) a[i] = cmul_conj(a[i], ph);
+                }
+            }
+            if (D.psi_out) __stcs(D.psi_out + off, a[i]);
+            if (BWD && D.lam_out) __stcs(D.lam_out + off, l[i]);
         }
-    } else if (flags & PF_E) {
-        const double te = block_sum<NW>(eacc, s_red);
-        if (tid == 0 && D.part_E) D.part_E[tile] = te;
+        // per-warp partial sums: slot tile * 8 + warp (no block barrier)
+        if (BWD) {
+            const double tb = warp_sum(bacc);
+            if (lane == 0 && D.part_beta) D.part_beta[tl * kNW + warp] = tb;
+            if (flags & PF_PHASE) {
+                const double tg = warp_sum(eacc);
+                if (lane == 0 && D.part_gamma) D.part_gamma[tl * kNW + warp] = tg;
+            }
+        } else if (flags & PF_E) {
+            const double te = warp_sum(eacc);
+            if (lane == 0 && D.part_E) D.part_E[tl * kNW + warp] = te;
+        }
     }
 }
 
@@ -411,7 +646,7 @@ constexpr int kSmallThreads = 256;
 template <int COST, int GRAD>
 __global__ void __launch_bounds__(kSmallThreads)
 small_kernel(const SmallDesc *__restrict__ descs, int *err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double s_red[kSmallThreads / 32];
     const SmallDesc D = descs[blockIdx.x];
     const int N = 1 << D.n, H = N >> 1, n = D.n, p = D.p;
@@ -517,20 +752,21 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ 
         if (!isfinite(be) || !isfinite(ga)) atomicOr(err, DERR_BAD_ANGLE);
         const double cb = cos(be), sb = sin(be);
         RoundCoef c;
-        if (fabs(cb) >= fabs(sb)) {
+        c.cb = (float)cb;
+        c.sb = (float)sb;
+        // tan form unless cos b is so small that the running 1/cos factors or
+        // the pair-term scale would leave float32 range (then: direct form)
+        if (fabs(cb) >= 2.44140625e-4) {
             c.bmode = 0;
             c.bt = (float)(sb / cb);
-            c.bs = (float)cb;
         } else {
-            c.bmode = 1;
-            c.bt = (float)(cb / sb);
-            c.bs = (float)sb;
+            c.bmode = 2;
+            c.bt = 0.f;
         }
+        c.rescale = fabs(cb) < 0.25 ? 1 : 0;
         const double g = ga / kTwoPi;
         c.g_hi = (float)g;
         c.g_lo = (float)(g - (double)c.g_hi);
-        c.cb = (float)cb;
-        c.sb = (float)sb;
         c.pad = 0.f;
         D.coef[k] = c;
     }
@@ -545,63 +781,65 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ 
     }
 }
 
-// Fixed-order reduction of the per-tile partials of every unit.
-__global__ void __launch_bounds__(256) reduce_kernel(const RedDesc *__restrict__ descs) {
-    const RedDesc D = descs[blockIdx.x];
+// Fixed-order two-level reduction of the per-(tile, warp) partial sums.
+__global__ void __launch_bounds__(256) reduce1_kernel(const RedChunk *__restrict__ chunks, double *level2) {
     __shared__ double red[8];
-    const int nq = D.grad_out ? 2 * D.p + 1 : 1;
-    for (int q = 0; q < nq; q++) {
-        const int cnt = q == 0 ? D.cntE : (q <= D.p ? D.cntB : D.cntG);
-        const double *src = D.part + (int64_t)q * D.stride;
-        double acc = 0.0;
-        for (int i = threadIdx.x; i < cnt; i += 256) acc += src[i];
+    const RedChunk C = chunks[blockIdx.x];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < C.cnt; i += 256) acc += C.src[i];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tot = 0.0;
-            for (int w = 0; w < 8; w++) tot += red[w];
-            if (q == 0)
-                *D.E_out = tot;
-            else
-                D.grad_out[q - 1] = 2.0 * tot;
-        }
-        __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; w++) tot += red[w];
+        level2[blockIdx.x] = tot;
     }
 }
 
-template <int T, int BWD, int COST>
+__global__ void __launch_bounds__(32) reduce2_kernel(const RedOut *__restrict__ outs, const double *level2) {
+    const RedOut O = outs[blockIdx.x];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < O.n; i += 32) acc += level2[O.first + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) *O.out = O.scale * acc;
+}
+
+template <int BWD, int COST, int NBUF>
 cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t tiles, int *err,
                        cudaStream_t s) {
-    constexpr int TILE = 1 << T;
-    const size_t smem = (size_t)(BWD ? 2 : 1) * TILE * sizeof(float2) + kPhaseTable * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(xpass_kernel<T, BWD, COST>,
+    using G = PassGeom<BWD, COST>;
+    const size_t smem = G::kHead + (size_t)NBUF * G::kBufB;
+    static int grid_cap = 0;
+    if (!grid_cap) {
+        cudaError_t e = cudaFuncSetAttribute(xpass_kernel<BWD, COST, NBUF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        int dev = 0, nsm = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xpass_kernel<BWD, COST, NBUF>, kNT, smem);
+        if (e != cudaSuccess) return e;
+        grid_cap = std::max(1, nsm * std::max(1, per_sm));
     }
-    xpass_kernel<T, BWD, COST><<<tiles, 1 << (T - 5), smem, s>>>(d, tb, nd, err);
+    const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)grid_cap);
+    xpass_kernel<BWD, COST, NBUF><<<grid, kNT, smem, s>>>(d, tb, nd, tiles, err);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool xpass_supported(int T, int bwd) { return (T == 12 || T == 13) || (T == 14 && !bwd); }
 int small_max_n() { return kSmallMaxN; }
 
-cudaError_t launch_xpass(int T, int bwd, int cost_dtype, const PassDesc *d, const uint32_t *tb,
-                         int nd, uint32_t tiles, int *err, cudaStream_t s) {
-    const int c = cost_dtype;
-#define QG_X(TT, BB, CC)                                                          \
-    if (T == TT && bwd == BB && c == CC) return launch_one<TT, BB, CC>(d, tb, nd, tiles, err, s);
-    QG_X(12, 0, 0) QG_X(12, 0, 1) QG_X(12, 1, 0) QG_X(12, 1, 1)
-    QG_X(13, 0, 0) QG_X(13, 0, 1) QG_X(13, 1, 0) QG_X(13, 1, 1)
-    QG_X(14, 0, 0) QG_X(14, 0, 1)
-#undef QG_X
-    return cudaErrorInvalidValue;
+cudaError_t launch_xpass(int bwd, int cost_dtype, const PassDesc *d, const uint32_t *tb, int nd,
+                         uint32_t tiles, int *err, cudaStream_t s) {
+    if (tiles == 0) return cudaSuccess;
+    if (!bwd) return cost_dtype == 0 ? launch_one<0, 0, 2>(d, tb, nd, tiles, err, s)
+                                     : launch_one<0, 1, 2>(d, tb, nd, tiles, err, s);
+    return cost_dtype == 0 ? launch_one<1, 0, 1>(d, tb, nd, tiles, err, s)
+                           : launch_one<1, 1, 1>(d, tb, nd, tiles, err, s);
 }
 
 cudaError_t launch_small(const SmallDesc *d, int nd, int cost_dtype, int want_grad, int max_n,
@@ -623,8 +861,12 @@ cudaError_t launch_prep(const PrepDesc *d, int nd, int *err, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const RedDesc *d, int nd, cudaStream_t s) {
-    reduce_kernel<<<nd, 256, 0, s>>>(d);
+cudaError_t launch_reduce(const RedChunk *chunks, int nchunks, double *level2, const RedOut *outs, int nouts,
+                          cudaStream_t s) {
+    reduce1_kernel<<<nchunks, 256, 0, s>>>(chunks, level2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce2_kernel<<<nouts, 32, 0, s>>>(outs, level2);
     return cudaGetLastError();
 }
 

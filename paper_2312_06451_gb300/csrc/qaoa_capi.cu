@@ -3,16 +3,21 @@
 // measurement hooks.  All arithmetic of the method runs in the kernels of
 // kernels_xmix.cu / kernels_cost.cu / kernels_eig.cu; this file only decides
 // what to launch on which buffers.
-#include "../../include/qaoa.h"
+#include "qaoa.h"
 #include "common.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 using namespace qg;
@@ -75,6 +80,7 @@ struct Group {
 
 constexpr int kMaxXQubits = 32;   // 32-bit element offsets in the pass kernel
 constexpr int kCminDefault = 4;   // >= 16 contiguous amplitudes = one 128-byte line
+constexpr int kTmaSegBits = 8;    // shorter runs are fetched through a TMA tensor map
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
@@ -108,7 +114,19 @@ std::vector<Group> make_groups(int n, int T, int cmin) {
     return g;
 }
 
-int choose_T(int n) { return n < 13 ? n : 13; }
+// Minimum contiguous run (log2 amplitudes) of a gathered pass: 2^4 complex64
+// amplitudes = one 128-byte line (and 16 bytes of uint8 cost, the bulk-copy
+// granule).  QAOA_MIN_CONTIG overrides it for tuning sweeps (4..8).
+int env_int(const char *name, int dflt, int lo, int hi) {
+    const char *v = std::getenv(name);
+    if (!v || !*v) return dflt;
+    const int x = std::atoi(v);
+    return (x < lo || x > hi) ? dflt : x;
+}
+int min_contig() {
+    static const int c = env_int("QAOA_MIN_CONTIG", kCminDefault, 4, 8);
+    return c;
+}
 
 }  // namespace
 
@@ -226,6 +244,44 @@ qaoa_status host_stage(qaoa_ctx *ctx, size_t bytes) {
     return QAOA_OK;
 }
 
+// --------------------------------------------------------- tensor maps
+// cuTensorMapEncodeTiled from the driver through the runtime (no libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Gathered tile of a 2^n-element vector: 2^c contiguous elements (dim 0),
+// the free bits c..lo-1 (dim 1), the 2^(T-c) rows of the gathered qubits
+// lo..lo+T-c-1 (dim 2), the free bits above them (dim 3).
+bool encode_gather_map(CUtensorMap *m, const void *base, int n, int c, int lo, int elsz) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const int h = kPassTileBits - c;
+    const cuuint64_t dims[4] = {1ull << c, 1ull << (lo - c), 1ull << h, 1ull << (n - lo - h)};
+    const cuuint64_t strides[3] = {(1ull << c) * elsz, (1ull << lo) * elsz, (1ull << (lo + h)) * elsz};
+    const cuuint32_t box[4] = {1u << c, 1u, 1u << h, 1u};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt = elsz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : elsz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                               : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    return enc(m, dt, 4, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // ------------------------------------------------------------- planning
 
 struct UnitLayout {
@@ -238,13 +294,13 @@ struct UnitLayout {
 
 UnitLayout layout_for(const Unit &u, bool grad, int ckpt) {
     UnitLayout L;
-    L.T_f = choose_T(u.n);
-    L.T_b = choose_T(u.n);
-    L.gf = make_groups(u.n, L.T_f, kCminDefault);
-    L.gb = make_groups(u.n, L.T_b, kCminDefault);
+    L.T_f = kPassTileBits;
+    L.T_b = kPassTileBits;
+    L.gf = make_groups(u.n, L.T_f, min_contig());
+    L.gb = make_groups(u.n, L.T_b, min_contig());
     L.tiles_f = 1u << (u.n - L.T_f);
     L.tiles_b = 1u << (u.n - L.T_b);
-    L.stride = std::max<int64_t>(L.tiles_f, (int64_t)L.gb.size() * L.tiles_b);
+    L.stride = std::max<int64_t>(L.tiles_f, (int64_t)L.gb.size() * L.tiles_b) * kPassWarps;
     L.vecs = grad ? (2 + (ckpt ? u.p - 1 : 0)) : 1;
     return L;
 }
@@ -261,6 +317,7 @@ void fill_geometry(PassDesc &d, int n, int T, const Group &g) {
     for (int b = 0; b < n; b++)
         if (!used[b]) d.fpos[nf++] = (uint8_t)b;
     d.nfree = (uint8_t)nf;
+    d.c = (uint8_t)g.c;
     d.ntiles = 1u << nf;
     d.active = (g.c == T) ? ((1u << T) - 1u) : (((1u << T) - 1u) & ~((1u << g.c) - 1u));
 }
@@ -308,8 +365,12 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, int ckpt, float2
             if (first) {
                 d.flags |= PF_PHASE;
                 if (k == 0) {
-                    if (u.init) d.psi_in = u.init;
-                    else d.flags |= PF_GEN_INIT;
+                    if (u.init) {
+                        d.psi_in = u.init;
+                        d.flags |= PF_TWIST_IN;
+                    } else {
+                        d.flags |= PF_GEN_INIT;
+                    }
                 } else {
                     d.psi_in = (grad && ckpt) ? ck(k - 1) : W;
                 }
@@ -329,8 +390,12 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, int ckpt, float2
         }
     }
     if (!grad) return;
+    // Adjoint rounds in reverse.  Within a round the groups run in reverse
+    // order, so the phase (gamma partial, undone phase) rides on the
+    // contiguous group 0, the last pass of the round.
     for (int k = p - 1; k >= 0; k--) {
-        for (int g = 0; g < Pb; g++) {
+        for (int q = 0; q < Pb; q++) {
+            const int g = Pb - 1 - q;
             PassDesc d;
             std::memset(&d, 0, sizeof(d));
             fill_geometry(d, u.n, L.T_b, L.gb[g]);
@@ -339,8 +404,8 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, int ckpt, float2
             d.table = table ? table + (int64_t)k * kPhaseTable : nullptr;
             d.amp0 = amp0;
             const bool first_round = k == p - 1;
-            const bool last = g == Pb - 1;
-            if (g == 0) {
+            const bool last = q == Pb - 1;
+            if (q == 0) {
                 d.psi_in = (first_round || !ckpt) ? W : ck(k);
                 if (first_round) d.flags |= PF_LAM_FROM_C;
                 else d.lam_in = Lam;
@@ -360,7 +425,7 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, int ckpt, float2
                 d.psi_out = W;
                 d.lam_out = Lam;
             }
-            d.part_beta = part + (int64_t)(1 + k) * L.stride + (int64_t)g * L.tiles_b;
+            d.part_beta = part + (int64_t)(1 + k) * L.stride + (int64_t)q * L.tiles_b * kPassWarps;
             bwd.push_back(d);
         }
     }
@@ -518,7 +583,55 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             r.fam = family(ctx, std::string(grad ? "small_grad_" : "small_fwd_") + dtype_name(dt));
             L.push_back(r);
         }
-        std::vector<RedDesc> red;
+        std::vector<RedChunk> rchunks;
+        std::vector<RedOut> routs;
+        // partials of unit quantity q: cnt values at src -> chunks + one output
+        auto add_reduction = [&](const double *src, int64_t cnt, double *out, double scale) {
+            RedOut o;
+            o.first = (int)rchunks.size();
+            for (int64_t j = 0; j < cnt; j += kRedChunk) {
+                RedChunk ch;
+                ch.src = src + j;
+                ch.cnt = (int)std::min<int64_t>(kRedChunk, cnt - j);
+                ch.pad = 0;
+                rchunks.push_back(ch);
+            }
+            o.n = (int)rchunks.size() - o.first;
+            o.out = out;
+            o.scale = scale;
+            routs.push_back(o);
+        };
+        // tensor maps of gathered tiles with short runs (< 2^kTmaSegBits elements),
+        // deduplicated; PassDesc.tm_* temporarily hold (index + 1)
+        std::vector<CUtensorMap> maps;
+        std::map<std::tuple<const void *, int, int, int, int>, size_t> map_index;
+        std::vector<std::pair<size_t, int>> xpass_descs;  // (image offset, count)
+        auto map_for = [&](const void *basep, int n, int c, int lo, int elsz) -> const void * {
+            const auto key = std::make_tuple(basep, n, c, lo, elsz);
+            auto it = map_index.find(key);
+            size_t idx;
+            if (it != map_index.end()) {
+                idx = it->second;
+            } else {
+                CUtensorMap m;
+                if (!encode_gather_map(&m, basep, n, c, lo, elsz)) return nullptr;
+                idx = maps.size();
+                maps.push_back(m);
+                map_index[key] = idx;
+            }
+            return reinterpret_cast<const void *>((uintptr_t)(idx + 1));
+        };
+        auto attach_maps = [&](PassDesc &d, bool bwd, int dt) {
+            if (d.c >= kTmaSegBits) return;
+            const int lo = d.gpos[d.c];
+            const int cb = dt == QAOA_COST_U8 ? 1 : 4;
+            const bool ld_psi = bwd || !(d.flags & PF_GEN_INIT);
+            const bool ld_lam = bwd && !(d.flags & PF_LAM_FROM_C);
+            const bool ld_cost = bwd ? (d.flags & (PF_LAM_FROM_C | PF_PHASE)) : (d.flags & (PF_PHASE | PF_E));
+            if (ld_psi) d.tm_psi = map_for(d.psi_in, d.n, d.c, lo, 8);
+            if (ld_lam) d.tm_lam = map_for(d.lam_in, d.n, d.c, lo, 8);
+            if (ld_cost) d.tm_cost = map_for(d.cost, d.n, d.c, lo, cb);
+        };
         for (const Wave &w : waves) {
             const GKey &gk = w.gk;
             std::vector<std::vector<PassDesc>> steps;
@@ -535,16 +648,20 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 all.insert(all.end(), b.begin(), b.end());
                 if (steps.size() < all.size()) steps.resize(all.size());
                 for (size_t s = 0; s < all.size(); s++) steps[s].push_back(all[s]);
-                RedDesc rd;
-                rd.part = reinterpret_cast<double *>(mb + off_part[i]);
-                rd.stride = lay[i].stride;
-                rd.cntE = (int)lay[i].tiles_f;
-                rd.cntB = (int)(lay[i].gb.size() * lay[i].tiles_b);
-                rd.cntG = (int)lay[i].tiles_b;
-                rd.p = u.p;
-                rd.E_out = u.E;
-                rd.grad_out = grad ? u.grad : nullptr;
-                red.push_back(rd);
+                {
+                    const double *part = reinterpret_cast<const double *>(mb + off_part[i]);
+                    const int64_t S = lay[i].stride;
+                    add_reduction(part, (int64_t)lay[i].tiles_f * kPassWarps, u.E, 1.0);
+                    if (grad) {
+                        for (int k = 0; k < u.p; k++) {
+                            add_reduction(part + (1 + k) * S,
+                                          (int64_t)lay[i].gb.size() * lay[i].tiles_b * kPassWarps, u.grad + k,
+                                          2.0);
+                            add_reduction(part + (1 + u.p + k) * S, (int64_t)lay[i].tiles_b * kPassWarps,
+                                          u.grad + u.p + k, 2.0);
+                        }
+                    }
+                }
             }
             const int nfwd = gk.p * gk.Pf;
             for (size_t s = 0; s < steps.size(); s++) {
@@ -555,6 +672,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 for (size_t j = 0; j < steps[s].size(); j++) {
                     tb[j + 1] = tb[j] + steps[s][j].ntiles;
                     bytes += pass_bytes(steps[s][j], bwd, gk.dt == QAOA_COST_U8 ? 1 : 4);
+                    attach_maps(steps[s][j], bwd, gk.dt);
                 }
                 LaunchRec r;
                 r.kind = LK_XPASS;
@@ -562,28 +680,57 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 r.bwd = bwd;
                 r.cost_dtype = gk.dt;
                 r.desc_off = put(steps[s].data(), sizeof(PassDesc) * steps[s].size());
+                xpass_descs.push_back({r.desc_off, (int)steps[s].size()});
                 r.tb_off = put(tb.data(), sizeof(uint32_t) * tb.size());
                 r.ndesc = (int)steps[s].size();
                 r.tiles = tb.back();
                 r.bytes = bytes;
                 char nm[64];
-                snprintf(nm, sizeof(nm), "xpass_%s_T%d_%s", bwd ? "bwd" : "fwd", T, dtype_name(gk.dt));
+                const int c0 = steps[s][0].c;
+                snprintf(nm, sizeof(nm), "xpass_%s_%s_%s", bwd ? "bwd" : "fwd",
+                         c0 >= kPassTileBits ? "contig" : (c0 >= 6 ? "gather_wide" : "gather"),
+                         dtype_name(gk.dt));
                 r.fam = family(ctx, nm);
                 L.push_back(r);
             }
         }
-        if (!red.empty()) {
+        if (!routs.empty()) {
             LaunchRec r;
             r.kind = LK_REDUCE;
-            r.desc_off = put(red.data(), sizeof(RedDesc) * red.size());
-            r.ndesc = (int)red.size();
+            r.desc_off = put(rchunks.data(), sizeof(RedChunk) * rchunks.size());
+            r.tb_off = put(routs.data(), sizeof(RedOut) * routs.size());
+            r.ndesc = (int)rchunks.size();
+            r.tiles = (uint32_t)routs.size();
             r.fam = family(ctx, "reduce_partials");
             L.push_back(r);
+        }
+        if (!rchunks.empty()) {
+            void *d_l2 = nullptr;
+            st = scratch(ctx, "level2", sizeof(double) * rchunks.size(), &d_l2);
+            if (st) return st;
+        }
+        // ---- tensor maps at the end of the image (128-byte aligned), then
+        // the device addresses patched into the descriptors
+        size_t maps_off = 0;
+        if (!maps.empty()) {
+            maps_off = align_up(host.size(), 128);
+            host.resize(maps_off + maps.size() * sizeof(CUtensorMap));
+            std::memcpy(host.data() + maps_off, maps.data(), maps.size() * sizeof(CUtensorMap));
         }
         // ---- upload
         void *d_desc = nullptr;
         st = scratch(ctx, "desc", host.size(), &d_desc);
         if (st) return st;
+        for (const auto &xd : xpass_descs) {
+            PassDesc *pd = reinterpret_cast<PassDesc *>(host.data() + xd.first);
+            for (int j = 0; j < xd.second; j++) {
+                const void **fields[3] = {&pd[j].tm_psi, &pd[j].tm_lam, &pd[j].tm_cost};
+                for (const void **f : fields)
+                    if (*f)
+                        *f = static_cast<char *>(d_desc) + maps_off +
+                             ((uintptr_t)*f - 1) * sizeof(CUtensorMap);
+            }
+        }
         st = host_stage(ctx, host.size());
         if (st) return st;
         std::memcpy(ctx->h_stage, host.data(), host.size());
@@ -616,12 +763,14 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                              r.small_grad, r.small_maxn, ctx->d_err, ctx->stream);
             break;
         case LK_XPASS:
-            e = launch_xpass(r.T, r.bwd, r.cost_dtype, reinterpret_cast<const PassDesc *>(db + r.desc_off),
+            e = launch_xpass(r.bwd, r.cost_dtype, reinterpret_cast<const PassDesc *>(db + r.desc_off),
                              reinterpret_cast<const uint32_t *>(db + r.tb_off), r.ndesc, r.tiles,
                              ctx->d_err, ctx->stream);
             break;
         case LK_REDUCE:
-            e = launch_reduce(reinterpret_cast<const RedDesc *>(db + r.desc_off), r.ndesc, ctx->stream);
+            e = launch_reduce(reinterpret_cast<const RedChunk *>(db + r.desc_off), r.ndesc,
+                              static_cast<double *>(ctx->bufs["level2"].p),
+                              reinterpret_cast<const RedOut *>(db + r.tb_off), (int)r.tiles, ctx->stream);
             break;
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
