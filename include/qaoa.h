@@ -224,6 +224,34 @@ typedef struct {
 qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *jobs,
                                      int want_grad);
 
+/* ------------------------------------------------ allocation-free variant */
+
+/* <C> (and, when d_grad != NULL, its 2p derivatives) for one angle set of a
+ * small problem, n <= 12 qubits and p <= 96 rounds, with the transverse-field
+ * mixer and the uniform initial state -- without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (a host that owns and pre-partitions all device
+ * memory, code running where allocation after start-up is forbidden).
+ *
+ *   d_cost      device cost vector, 2^n elements of cost_dtype (16-byte aligned)
+ *   d_angles    device, 2p float64 in the usual order
+ *   d_E         device output, 1 float64
+ *   d_grad      device output, 2p float64, or NULL for the expectation only
+ *   cuda_stream the stream to run on (NULL = legacy default stream)
+ *
+ * Scratch (coefficients, phase tables, launch descriptors, an error word) is a
+ * fixed 256 KiB file-scope device array that every device loading the library
+ * keeps until exit; sizes beyond n = 12 or p = 96 are rejected with
+ * QAOA_ERR_INVALID.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) once; make that first call before any stream
+ * capture.  The call is synchronous on cuda_stream.  All calls share the one
+ * array: calls that overlap on the GPU (other threads or streams) race, so
+ * serialise them.  No other context or state is needed.  A non-finite angle
+ * returns QAOA_ERR_INVALID; a CUDA failure QAOA_ERR_CUDA. */
+qaoa_status qaoa_gradient_small_noalloc(const void *d_cost, int cost_dtype, int n, int p,
+                                        const double *d_angles, double *d_E, double *d_grad,
+                                        void *cuda_stream);
+
 /* ------------------------------------------------------------ measurement */
 
 /* Per-kernel-family launch statistics, collected when profiling is on: each

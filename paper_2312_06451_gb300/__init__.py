@@ -23,7 +23,8 @@ from . import _binding as B
 from ._binding import QAOAError  # noqa: F401
 
 __all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError",
-           "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched"]
+           "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched",
+           "qaoa_gradient_small_noalloc"]
 
 _PROBLEMS = {"maxcut": B.QAOA_PROBLEM_MAXCUT, "wmaxcut": B.QAOA_PROBLEM_WMAXCUT,
              "sk": B.QAOA_PROBLEM_SK, "dks": B.QAOA_PROBLEM_DKS}
@@ -238,6 +239,24 @@ def qaoa_gradient(ctx: Context, *args, **kw):
 
 def qaoa_expectation_batched(ctx: Context, *args, **kw):
     return ctx.expectation_batched(*args, **kw)
+
+
+def qaoa_gradient_small_noalloc(cost: torch.Tensor, n: int, angles: torch.Tensor, E: torch.Tensor,
+                                grad: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None):
+    """<C> (and the gradient) for n <= 12, p <= 96 through the C entry point
+    that allocates no device memory (for callers that cannot allocate: the
+    library keeps a fixed device array instead).  angles, E, grad: float64 CUDA
+    tensors (2p, 1, 2p); results land in E and grad.  Synchronous."""
+    lib = B.load()
+    cost = _dev_tensor(cost, "cost")
+    angles = _dev_tensor(angles, "angles")
+    E = _dev_tensor(E, "E")
+    grad = _dev_tensor(grad, "grad")
+    s = stream if stream is not None else torch.cuda.current_stream(cost.device)
+    st = lib.qaoa_gradient_small_noalloc(_ptr(cost), _cost_dtype(cost), int(n), angles.numel() // 2,
+                                         _ptr(angles), _ptr(E), _ptr(grad), ctypes.c_void_p(s.cuda_stream))
+    if st != B.QAOA_OK:
+        raise QAOAError(st, "qaoa_gradient_small_noalloc failed")
 
 
 class QAOAExpectation(torch.autograd.Function):

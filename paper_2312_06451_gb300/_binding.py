@@ -64,6 +64,8 @@ SIGNATURES = {
     "qaoa_kernel_stats": (c_int, [c_void_p, ctypes.POINTER(QaoaKernelStat), c_int]),
     "qaoa_reset_stats": (None, [c_void_p]),
     "qaoa_launch_count": (c_int64, [c_void_p]),
+    "qaoa_gradient_small_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                            c_void_p]),
 }
 
 _lock = threading.Lock()
