@@ -172,13 +172,152 @@ def oracle_sample(threads: int | None = None):
     return run, p, oracle.get_threads(), n
 
 
+# ------------------------------------------------------------ workloads
+
+class Workload:
+    """Device-resident inputs of one benchmark workload and how to step it.
+
+    A step evaluates `units` angle sets (gradients, or expectations when
+    `grad` is False) through the batched entry point; angles for each step are
+    copied into the job buffers from a device pool first (a 2p-double copy per
+    set, so every step evaluates fresh angles)."""
+
+    def __init__(self, qg, ctx, idx, dev, pool_steps, n_override=None):
+        import torch
+
+        from qaoa_inputs import BASE_SEED, sk_couplings, uneven_batch_recipe, uniform_angles, workload_instance
+
+        self.idx = idx
+        self.ctx = ctx
+        self.qg = qg
+        self.dev = dev
+        from qaoa_inputs import WORKLOADS
+
+        spec = dict(WORKLOADS[idx])
+        self.p = p = spec["p"]
+        self.jobs = []
+        self.pools = []
+        if idx == 5:
+            inst = uneven_batch_recipe(spec["n_instances"], BASE_SEED + 5)
+            self.grad = True
+            for i, it in enumerate(inst):
+                n = it["n"]
+                cost = ctx.cost_precompute("maxcut", n, edges=it["edges"], dtype=torch.uint8)
+                A = uniform_angles(p, BASE_SEED + 5 + 1000 + i, spec["n_sets"] * pool_steps)
+                self._add_job(cost, n, A, spec["n_sets"])
+            self.name = spec["name"]
+            self.config = {"workload": spec["name"], "problem": "MaxCut, 3-regular (even i) / G(n,0.3) (odd i)",
+                           "instances": len(inst), "n_range": [14, 22], "p": p, "angle_sets_per_instance":
+                           spec["n_sets"], "mixer": "X", "cost_dtype": "u8"}
+            self.units = len(inst) * spec["n_sets"]
+        else:
+            w = workload_instance(idx, n_sets=spec["n_sets"] * pool_steps)
+            n = n_override or spec["n"]
+            self.grad = bool(spec["grad"])
+            if spec["problem"] == "sk":
+                J = w["J"] if n == spec["n"] else sk_couplings(n, BASE_SEED + idx)
+                cost = ctx.cost_precompute("sk", n, J=J, dtype=torch.float32)
+                prob = "SK, J_ij~N(0,1) on 2^-20 grid"
+            else:
+                cost = ctx.cost_precompute("maxcut", n, edges=w["edges"], dtype=torch.uint8)
+                prob = "MaxCut " + ("G(12,0.5)" if idx == 1 else "random 3-regular")
+            self._add_job(cost, n, w["angles"], spec["n_sets"])
+            self.name = spec["name"] if n == spec["n"] else f"{spec['name']}_n{n}"
+            self.units = spec["n_sets"]
+            self.config = {"workload": self.name, "problem": prob, "n": n, "p": p, "mixer": "X (transverse field)",
+                           "angle_sets_per_step": spec["n_sets"],
+                           "cost_dtype": "f32" if spec["problem"] == "sk" else "u8"}
+            self.config["l2"] = (f"state {2 ** n * 8 / 2 ** 30:.2f} GiB per set vs 129 MB L2; no flush"
+                                 if n >= 24 else "on-chip state (whole state in shared memory)")
+        self.config["state"] = "complex64"
+        self.config["ckpt"] = "per-round state checkpoints" if self.grad else "none (forward only)"
+
+    def _add_job(self, cost, n, A, n_sets):
+        import torch
+
+        pool = torch.from_numpy(np.ascontiguousarray(A)).to(self.dev)
+        ang = pool[:n_sets].clone()
+        E = torch.zeros(n_sets, dtype=torch.float64, device=self.dev)
+        G = torch.zeros(n_sets, 2 * self.p, dtype=torch.float64, device=self.dev)
+        self.jobs.append({"cost": cost, "mixer": self.qg.XMixer(n), "angles": ang, "E": E, "grad": G})
+        self.pools.append((pool, n_sets, n, np.ascontiguousarray(A)))
+
+    def load_angles(self, step):
+        for job, (pool, k, _, _) in zip(self.jobs, self.pools):
+            s = (step * k) % pool.shape[0]
+            job["angles"].copy_(pool[s:s + k], non_blocking=True)
+
+    def run(self):
+        self.ctx.expectation_batched(self.jobs, want_grad=self.grad)
+
+    def e2e_step(self, step, pinned):
+        """Host angles (pinned) -> device, batched call, results -> host."""
+        import torch
+
+        for job, (pool, k, _, A), hp in zip(self.jobs, self.pools, pinned):
+            s = (step * k) % pool.shape[0]
+            job["angles"].copy_(hp[s:s + k], non_blocking=True)
+        self.run()
+        outs = [j["E"].to("cpu", non_blocking=True) for j in self.jobs]
+        if self.grad:
+            outs += [j["grad"].to("cpu", non_blocking=True) for j in self.jobs]
+        torch.cuda.current_stream().synchronize()
+        return outs
+
+    def h2d_bytes(self):
+        return sum(8 * 2 * self.p * k for (_, k, _, _) in self.pools)
+
+    def d2h_bytes(self):
+        return sum(8 * k * ((2 * self.p + 1) if self.grad else 1) for (_, k, _, _) in self.pools)
+
+    def oracle_baseline(self):
+        """Time the CPU oracle on a bounded sample of this workload; returns
+        (units/s, cores, description)."""
+        import oracle
+        from qaoa_inputs import BASE_SEED, sk_couplings, uneven_batch_recipe, workload_instance
+
+        oracle.build()
+        p = self.p
+        if self.idx == 2:
+            w = workload_instance(2)
+            n = self.pools[0][2]
+            J = w["J"] if n == 28 else sk_couplings(n, BASE_SEED + 2)
+            cost = oracle.cost_sk(n, J.astype(np.float64))
+            a = self.pools[0][3][0]
+            t = time.perf_counter()
+            oracle.qaoa_gradient(n, cost, np.array([a[0], a[p]]))
+            dt = (time.perf_counter() - t) * p
+            return 1.0 / dt, oracle.get_threads(), (f"oracle gradient of one round (p=1) at n={n}, "
+                                                     f"scaled x{p} to the p={p} unit")
+        if self.idx in (1, 3):
+            w = workload_instance(self.idx, n_sets=2)
+            n = self.pools[0][2]
+            cost = oracle.cost_maxcut(n, w["edges"])
+            k = 1 if self.idx == 3 else 20
+            t = time.perf_counter()
+            for s in range(k):
+                a = w["angles"][s % 2]
+                if self.grad:
+                    oracle.qaoa_gradient(n, cost, a)
+                else:
+                    oracle.qaoa_expectation(n, cost, a)
+            return k / (time.perf_counter() - t), oracle.get_threads(), (
+                f"oracle on {k} of the workload's angle sets at n={n}, scaled per set")
+        inst = uneven_batch_recipe(512, BASE_SEED + 5)[:16]
+        t = time.perf_counter()
+        for it in inst:
+            c = oracle.cost_maxcut(it["n"], it["edges"])
+            oracle.qaoa_gradient(it["n"], c, self.pools[0][3][0])
+        return 16 / (time.perf_counter() - t), oracle.get_threads(), (
+            "oracle gradient of 16 of the 512 instances (one angle set each), scaled per set")
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def gpu_arm(args, ws, rank, local):
     import torch
 
     import paper_2312_06451_gb300 as qg
-    from qaoa_inputs import workload_instance
 
     torch.cuda.set_device(local)
     dist = None
@@ -187,28 +326,34 @@ def gpu_arm(args, ws, rank, local):
 
         dist_mod.init_process_group("nccl")
         dist = dist_mod
-    w = workload_instance(WORKLOAD, n_sets=args.steps + args.warmup)
-    if args.n:
-        from qaoa_inputs import BASE_SEED, sk_couplings
-
-        w["spec"]["n"] = args.n
-        w["spec"]["name"] = f"sk{args.n}_p8_grad"
-        w["J"] = sk_couplings(args.n, BASE_SEED + WORKLOAD)
-    n, p = w["spec"]["n"], w["spec"]["p"]
-    ctx = qg.Context(local)
-    cost = ctx.cost_precompute("sk", n, J=w["J"], dtype=torch.float32)
-    mixer = qg.XMixer(n)
     dev = f"cuda:{local}"
-    angles_all = torch.from_numpy(w["angles"]).to(dev)
-    ang = angles_all[0:1].clone()
-    E = torch.zeros(1, dtype=torch.float64, device=dev)
-    G = torch.zeros(1, 2 * p, dtype=torch.float64, device=dev)
-    job = [{"cost": cost, "mixer": mixer, "angles": ang, "E": E, "grad": G}]
-    stream = torch.cuda.current_stream(local)
+    stream = torch.cuda.Stream(device=local)
+    with torch.cuda.stream(stream):
+        return _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg)
+
+
+def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
+    import torch
+
+    ctx = qg.Context(local, stream)
+    W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n)
+
+    graph = None
+    if args.graph:
+        # capture one step (angle copies + batched call) after a plan-building call
+        W.load_angles(0)
+        W.run()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            W.run()
 
     def step(i):
-        ang.copy_(angles_all[i:i + 1], non_blocking=True)
-        ctx.expectation_batched(job, want_grad=True)
+        W.load_angles(i)
+        if graph is not None:
+            graph.replay()
+        else:
+            W.run()
 
     for i in range(args.warmup):
         step(i)
@@ -216,7 +361,7 @@ def gpu_arm(args, ws, rank, local):
     if dist:
         dist.barrier()
     ctx.reset_stats()
-    ctx.set_profiling(True)
+    ctx.set_profiling(graph is None)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -229,6 +374,8 @@ def gpu_arm(args, ws, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     launches = ctx.launch_count() - l0
+    if graph is not None:  # the library counted one step's launches at capture
+        launches = None
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
@@ -250,57 +397,62 @@ def gpu_arm(args, ws, rank, local):
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return int(t.item())
 
-    value, tmax, units = aggregate(ms / 1e3, args.steps, ws, rmax, rsum)
-    grad_last = G.cpu().numpy()[0]
+    value, tmax, units = aggregate(ms / 1e3, args.steps * W.units, ws, rmax, rsum)
+    E_last = float(W.jobs[0]["E"][0].item())
 
-    # end to end through the host-pointer API: angles from pinned host memory,
-    # results read back, every step
-    pinned = torch.from_numpy(w["angles"]).pin_memory()
+    # end to end through the public API: host angles from pinned memory copied
+    # in, batched call, <C> (and gradients) read back, every step
+    pinned = [torch.from_numpy(pl[3]).pin_memory() for pl in W.pools]
     for i in range(2):
-        ctx.gradient(cost, mixer, pinned[i].numpy())
+        W.e2e_step(i, pinned)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for i in range(args.steps):
-        Eh, gh = ctx.gradient(cost, mixer, pinned[args.warmup + i].numpy())
+        outs = W.e2e_step(args.warmup + i, pinned)
     torch.cuda.synchronize()
     e2e_s = rmax(time.perf_counter() - t0)
-    e2e_value = rsum(args.steps) / e2e_s
+    e2e_value = rsum(args.steps * W.units) / e2e_s
 
-    # dominant kernel family by time inside the timed region
-    fam = max((k for k in stats if stats[k]["launches"]), key=lambda k: stats[k]["total_ms"])
-    st = stats[fam]
     peaks = measured_peaks()
-    per_launch_bytes = st["algo_bytes"] / st["launches"]
-    per_launch_ms = st["total_ms"] / st["launches"]
-    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    roof = None
+    fams = [k for k in stats if stats[k]["launches"] and stats[k]["total_ms"] > 0]
+    if fams:
+        fam = max(fams, key=lambda k: stats[k]["total_ms"])
+        st = stats[fam]
+        per_launch_bytes = st["algo_bytes"] / st["launches"]
+        per_launch_ms = st["total_ms"] / st["launches"]
+        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": fam, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
+                "traffic": traffic_for(fam), "algo_bytes_per_launch": per_launch_bytes,
+                "launch_ms": per_launch_ms}
+    unit = UNIT if W.grad else "evals/s"
     out = None
     if rank == 0:
+        cfg = dict(W.config)
+        cfg.update({"units_per_step_per_rank": W.units, "parallelism": f"replicas x{ws}",
+                    "timing": "CUDA graph replay" if graph is not None else "direct launches"})
         out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": METRIC if args.workload == 2 and not args.n else f"QAOA {unit} ({W.name})",
+            "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w["spec"]["name"], "problem": "SK, J_ij~N(0,1) on 2^-20 grid",
-                       "n": n, "p": p, "mixer": "X (transverse field)", "state": "complex64",
-                       "ckpt": "per-round state checkpoints", "angle_sets_per_step": 1,
-                       "units_per_rank": args.steps,
-                       "l2": f"state {2 ** n * 8 / 2 ** 30:.2f} GiB vs 129 MB L2; no flush",
-                       "parallelism": f"replicas x{ws}"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * 2 * p,
-                    "d2h_bytes_per_step": 8 * (2 * p + 1)},
-            "roofline": {"bound": "hbm", "kernel": fam, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                         "peak_source": peaks["source"], "traffic": traffic_for(fam),
-                         "algo_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_ms},
+            "config": cfg,
+            "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": W.h2d_bytes(),
+                    "d2h_bytes_per_step": W.d2h_bytes()},
+            "roofline": roof,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 4),
                             "GBps": round(v["algo_bytes"] / v["total_ms"] / 1e6, 1) if v["total_ms"] else None}
                         for k, v in stats.items() if v["launches"]},
-            "gpu_launches": launches,
+            "gpu_launches": launches if launches is not None else "graph",
             "clocks": clk,
-            "result_check": {"E_last": float(E.item()), "grad_norm_last": float(np.linalg.norm(grad_last)),
-                             "e2e_E_last": Eh},
+            "result_check": {"E_first_set_last_step": E_last, "e2e_E0": float(outs[0][0])},
         }
+        if ws == 1 and not args.no_cpu_baseline:
+            v, cores, desc = W.oracle_baseline()
+            out["cpu_baseline"] = {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": desc}
     ctx.close()
     if dist:
         dist.barrier()
@@ -317,6 +469,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None,
                     help="override the qubit count (small cases for profiler captures)")
+    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[1, 2, 3, 5],
+                    help="1: MaxCut n=12 p=3 forward; 2: SK n=28 p=8 gradient (default); "
+                         "3: 3-regular n=24 p=10, 1024 angle sets; 5: 512 uneven instances x 4 sets")
+    ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.warmup < 3:
@@ -347,15 +503,6 @@ def main():
 
     out = gpu_arm(args, ws, rank, local)
     if rank == 0 and out is not None:
-        if ws == 1 and not args.no_cpu_baseline:
-            run, p, cores, n = oracle_sample()
-            ts = [run()]
-            if ts[0] < 8.0:
-                ts.append(run())
-            t_round = min(ts)
-            out["cpu_baseline"] = {"value": 1.0 / (t_round * p), "unit": UNIT, "cores": cores, "kind": "oracle",
-                                   "sample": f"oracle gradient of one round (p=1) at n={n}, best of "
-                                             f"{len(ts)}, scaled x{p} to the p={p} unit"}
         print(json.dumps(out), flush=True)
 
 

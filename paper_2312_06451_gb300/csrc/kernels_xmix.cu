@@ -85,9 +85,9 @@ struct Rot {
     int mode;
 };
 
-template <int RB>
+template <int RB, int MODE>
 __device__ __forceinline__ void rot_pairs(float2 (&a)[16], const Rot &R) {
-    if (R.mode == 0) {
+    if (MODE == 0) {
 #pragma unroll
         for (int i = 0; i < 16; i++) {
             if (i & (1 << RB)) continue;
@@ -132,16 +132,16 @@ __device__ __forceinline__ float pair_dot(const float2 (&l)[16], const float2 (&
 }
 
 // One rotation step on register bit RB if its qubit is active.
-template <int RB, int BWD>
+template <int RB, int BWD, int MODE>
 __device__ __forceinline__ void rot_step(float2 (&a)[16], float2 (&l)[16], bool on, const Rot &R,
                                          float &pscale, float &bacc) {
     if (!on) return;
     if (BWD) {
         bacc = fmaf(pair_dot<RB>(l, a), pscale, bacc);
         pscale *= R.psc;
-        rot_pairs<RB>(l, R);
+        rot_pairs<RB, MODE>(l, R);
     }
-    rot_pairs<RB>(a, R);
+    rot_pairs<RB, MODE>(a, R);
 }
 
 template <int BWD>
@@ -369,6 +369,220 @@ __device__ __forceinline__ void issue_tile(uint32_t t, unsigned char *buf, uint3
     }
 }
 
+// Constants of the descriptor currently being processed.
+struct PassConst {
+    Rot R;
+    float ghi, glo, amp0;
+    float fs1, fs2, fs3, fse;  // cos b factors per stage / per pass
+    uint32_t flags, active, g3;
+    uint32_t rs3[4];
+    int rescale;
+};
+
+// One tile: stages 1..3, in-place transposes in buffer b, fused epilogue.
+// MODE is the rotation form (0 tan, 2 direct); the two forms are separate
+// copies of this body so the common one stays compact in the instruction
+// cache.  Optional work (initial state, phase, epilogue) sits in loops of its
+// own that are skipped as a whole when a pass does not need them.
+template <int BWD, int COST, int NBUF, int MODE>
+__device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D, const float2 *stab,
+                                          unsigned char *bufs, int b, uint32_t bar, uint32_t t, uint32_t stride,
+                                          uint32_t total, uint32_t base, uint32_t tl, TileInfo *tinfo,
+                                          const PassDesc *__restrict__ descs,
+                                          const uint32_t *__restrict__ tile_begin, int ndesc) {
+    using G = PassGeom<BWD, COST>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t l1 = ((uint32_t)lane << 1) | ((uint32_t)warp << 6);
+    const uint32_t l2 = ((uint32_t)lane & 1u) | ((((uint32_t)lane >> 1) & 7u) << 6) |
+                        ((((uint32_t)lane >> 4) & 1u) << 5) | ((uint32_t)warp << 9);
+    const uint32_t l3 = (uint32_t)lane | ((uint32_t)warp << 9);
+    const uint32_t p1 = swz(l1), p2 = swz(l2), p3 = swz(l3);
+    const uint32_t flags = K.flags, active = K.active;
+
+    float2 *sp = reinterpret_cast<float2 *>(bufs + b * G::kBufB);
+    float2 *sl = sp + kTile;
+    const unsigned char *scost = bufs + b * G::kBufB + G::kPsiB * (BWD ? 2 : 1);
+    float2 a[16];
+    float2 l[16];
+    float pscale = 1.f, bacc = 0.f;
+
+    // ---------------- stage 1: read the landed tile
+    if (!BWD && (flags & PF_GEN_INIT)) {
+        // uniform state in the twisted basis: amp0 * (-i)^{|x|}, |x| = |base| + |local|
+        const float2 a0 = twist(make_float2(K.amp0, 0.f), __popc(base) + __popc(l1));
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            a[2 * r] = twist(a0, __popc(r));
+            a[2 * r + 1] = twist(a0, __popc(r) + 1);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const float4 v = *reinterpret_cast<const float4 *>(sp + (l1 | ((uint32_t)r << 9)));
+            a[2 * r] = make_float2(v.x, v.y);
+            a[2 * r + 1] = make_float2(v.z, v.w);
+        }
+        if (!BWD && (flags & PF_TWIST_IN)) {
+            const float2 w0 = twist(make_float2(1.f, 0.f), __popc(base) + __popc(l1));
+#pragma unroll
+            for (int r = 0; r < 8; r++) {
+                a[2 * r] = cmul(twist(a[2 * r], __popc(r)), w0);
+                a[2 * r + 1] = cmul(twist(a[2 * r + 1], __popc(r) + 1), w0);
+            }
+        }
+    }
+    if (BWD && !(flags & PF_LAM_FROM_C)) {
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const float4 v = *reinterpret_cast<const float4 *>(sl + (l1 | ((uint32_t)r << 9)));
+            l[2 * r] = make_float2(v.x, v.y);
+            l[2 * r + 1] = make_float2(v.z, v.w);
+        }
+    }
+    if (BWD ? (flags & PF_LAM_FROM_C) : (flags & PF_PHASE)) {
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const uint32_t idx = l1 | ((uint32_t)r << 9);
+            float c0, c1;
+            if (COST == 0) {
+                const float2 cc = *reinterpret_cast<const float2 *>(reinterpret_cast<const float *>(scost) + idx);
+                c0 = cc.x;
+                c1 = cc.y;
+            } else {
+                const uchar2 cc = *reinterpret_cast<const uchar2 *>(scost + idx);
+                c0 = (float)cc.x;
+                c1 = (float)cc.y;
+                if (!BWD) {
+                    a[2 * r] = cmul(a[2 * r], stab[cc.x]);
+                    a[2 * r + 1] = cmul(a[2 * r + 1], stab[cc.y]);
+                }
+            }
+            if (BWD) {
+                l[2 * r] = __fmul2_rn(make_float2(c0, c0), a[2 * r]);
+                l[2 * r + 1] = __fmul2_rn(make_float2(c1, c1), a[2 * r + 1]);
+            } else if (COST == 0) {
+                a[2 * r] = cmul(a[2 * r], phase_f32(c0, K.ghi, K.glo));
+                a[2 * r + 1] = cmul(a[2 * r + 1], phase_f32(c1, K.ghi, K.glo));
+            }
+        }
+    }
+    rot_step<0, BWD, MODE>(a, l, active & (1u << 0), K.R, pscale, bacc);
+    rot_step<1, BWD, MODE>(a, l, active & (1u << 9), K.R, pscale, bacc);
+    rot_step<2, BWD, MODE>(a, l, active & (1u << 10), K.R, pscale, bacc);
+    rot_step<3, BWD, MODE>(a, l, active & (1u << 11), K.R, pscale, bacc);
+    if (K.rescale) {
+        scale_all<BWD>(a, l, K.fs1);
+        pscale = 1.f;
+    }
+
+    // ---------------- stage 1 -> 2, in place (swizzled)
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        const uint32_t idx = p1 ^ swz((uint32_t)r << 9);
+        *reinterpret_cast<float4 *>(sp + idx) = make_float4(a[2 * r].x, a[2 * r].y, a[2 * r + 1].x, a[2 * r + 1].y);
+        if (BWD)
+            *reinterpret_cast<float4 *>(sl + idx) = make_float4(l[2 * r].x, l[2 * r].y, l[2 * r + 1].x, l[2 * r + 1].y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        a[i] = sp[p2 ^ ((uint32_t)i << 1)];
+        if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
+    }
+    rot_step<0, BWD, MODE>(a, l, active & (1u << 1), K.R, pscale, bacc);
+    rot_step<1, BWD, MODE>(a, l, active & (1u << 2), K.R, pscale, bacc);
+    rot_step<2, BWD, MODE>(a, l, active & (1u << 3), K.R, pscale, bacc);
+    rot_step<3, BWD, MODE>(a, l, active & (1u << 4), K.R, pscale, bacc);
+    if (K.rescale) {
+        scale_all<BWD>(a, l, K.fs2);
+        pscale = 1.f;
+    }
+
+    // ---------------- stage 2 -> 3
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        sp[p2 ^ ((uint32_t)i << 1)] = a[i];
+        if (BWD) sl[p2 ^ ((uint32_t)i << 1)] = l[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        const uint32_t idx = p3 ^ swz((uint32_t)i << 5);
+        a[i] = sp[idx];
+        if (BWD) l[i] = sl[idx];
+    }
+    const bool epi_c = BWD ? (flags & PF_PHASE) : (flags & PF_E);
+    float cst[16];
+    if (epi_c) {
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const uint32_t ci = l3 | ((uint32_t)i << 5);
+            cst[i] = COST == 0 ? reinterpret_cast<const float *>(scost)[ci] : (float)scost[ci];
+        }
+    }
+    // the buffer is consumed: start the tile NBUF ahead
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t tn = t + (uint32_t)NBUF * stride;
+        if (tn < total) issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc);
+    }
+    rot_step<0, BWD, MODE>(a, l, active & (1u << 5), K.R, pscale, bacc);
+    rot_step<1, BWD, MODE>(a, l, active & (1u << 6), K.R, pscale, bacc);
+    rot_step<2, BWD, MODE>(a, l, active & (1u << 7), K.R, pscale, bacc);
+    rot_step<3, BWD, MODE>(a, l, active & (1u << 8), K.R, pscale, bacc);
+    scale_all<BWD>(a, l, K.rescale ? K.fs3 : K.fse);
+
+    // ---------------- stage 3: fused epilogue, coalesced store
+    float eacc = 0.f;
+    if (epi_c) {
+        if (!BWD) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) eacc = fmaf(cst[i], fmaf(a[i].x, a[i].x, a[i].y * a[i].y), eacc);
+        } else {
+            const bool un_psi = flags & PF_UNPHASE_PSI;
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const float C = cst[i];
+                const float2 ph = COST == 0 ? phase_f32(C, K.ghi, K.glo) : stab[(int)C];
+                eacc = fmaf(C, fmaf(l[i].x, a[i].y, -l[i].y * a[i].x), eacc);
+                l[i] = cmul_conj(l[i], ph);
+                if (un_psi) a[i] = cmul_conj(a[i], ph);
+            }
+        }
+    }
+    const uint32_t g = base + K.g3;
+    if (D.psi_out) {
+        float2 *out = D.psi_out + g;
+#pragma unroll
+        for (int i = 0; i < 16; i++)
+            __stcs(out + (((i & 1) ? K.rs3[0] : 0) + ((i & 2) ? K.rs3[1] : 0) + ((i & 4) ? K.rs3[2] : 0) +
+                          ((i & 8) ? K.rs3[3] : 0)),
+                   a[i]);
+    }
+    if (BWD && D.lam_out) {
+        float2 *out = D.lam_out + g;
+#pragma unroll
+        for (int i = 0; i < 16; i++)
+            __stcs(out + (((i & 1) ? K.rs3[0] : 0) + ((i & 2) ? K.rs3[1] : 0) + ((i & 4) ? K.rs3[2] : 0) +
+                          ((i & 8) ? K.rs3[3] : 0)),
+                   l[i]);
+    }
+    // per-warp partial sums: slot tile * 8 + warp (no block barrier)
+    if (BWD) {
+        const double tb = warp_sum(bacc);
+        if (lane == 0 && D.part_beta) D.part_beta[tl * kNW + warp] = tb;
+        if (flags & PF_PHASE) {
+            const double tg = warp_sum(eacc);
+            if (lane == 0 && D.part_gamma) D.part_gamma[tl * kNW + warp] = tg;
+        }
+    } else if (flags & PF_E) {
+        const double te = warp_sum(eacc);
+        if (lane == 0 && D.part_E) D.part_E[tl * kNW + warp] = te;
+    }
+}
+
 template <int BWD, int COST, int NBUF>
 __global__ void __launch_bounds__(kNT, (BWD && NBUF > 1) ? 1 : 2)
 xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ tile_begin, int ndesc,
@@ -396,21 +610,9 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
                                       ndesc);
         }
     }
-
-    // per-descriptor constants
-    int cur = -1;
-    Rot R;
-    float ghi = 0.f, glo = 0.f, amp0 = 0.f;
-    float fs1 = 1.f, fs2 = 1.f, fs3 = 1.f, fse = 1.f;
-    uint32_t flags = 0, active = 0, g3 = 0;
-    uint32_t rs3[4] = {0, 0, 0, 0};
-    bool rescale = false;
-
-    const uint32_t l1 = ((uint32_t)lane << 1) | ((uint32_t)warp << 6);
-    const uint32_t l2 = ((uint32_t)lane & 1u) | ((((uint32_t)lane >> 1) & 7u) << 6) |
-                        ((((uint32_t)lane >> 4) & 1u) << 5) | ((uint32_t)warp << 9);
     const uint32_t l3 = (uint32_t)lane | ((uint32_t)warp << 9);
-    const uint32_t p1 = swz(l1), p2 = swz(l2), p3 = swz(l3);
+    int cur = -1;
+    PassConst K;
 
     for (uint32_t it = 0;; it++) {
         const uint32_t t = blockIdx.x + it * stride;
@@ -437,202 +639,46 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
             for (int i = tid; i < (int)(sizeof(PassDesc) / 4); i += kNT) dst[i] = src[i];
             __syncthreads();
             const RoundCoef cf = *D.coef;
-            flags = D.flags;
-            active = D.active;
-            amp0 = D.amp0;
+            K.flags = D.flags;
+            K.active = D.active;
+            K.amp0 = D.amp0;
             // undoing a round (adjoint) uses the coefficients of -b
             const float sgn = BWD ? -1.f : 1.f;
-            R.mode = cf.bmode;
-            R.tt = make_float2(sgn * cf.bt, sgn * cf.bt);
-            R.ntt = make_float2(-sgn * cf.bt, -sgn * cf.bt);
-            R.c = cf.cb;
-            R.s = sgn * cf.sb;
-            R.psc = cf.bmode == 0 ? cf.cb * cf.cb : 1.f;
-            rescale = cf.bmode == 0 && cf.rescale;
+            K.R.mode = cf.bmode;
+            K.R.tt = make_float2(sgn * cf.bt, sgn * cf.bt);
+            K.R.ntt = make_float2(-sgn * cf.bt, -sgn * cf.bt);
+            K.R.c = cf.cb;
+            K.R.s = sgn * cf.sb;
+            K.R.psc = cf.bmode == 0 ? cf.cb * cf.cb : 1.f;
+            K.rescale = (cf.bmode == 0 && cf.rescale) ? 1 : 0;
             {
                 const float c = cf.bmode == 0 ? cf.cb : 1.f;
-                const int k1 = __popc(active & 0xE01u), k2 = __popc(active & 0x1Eu), k3 = __popc(active & 0x1E0u);
-                float p = 1.f;
-                fs1 = fs2 = fs3 = 1.f;
-                for (int k = 0; k < k1; k++) fs1 *= c;
-                for (int k = 0; k < k2; k++) fs2 *= c;
-                for (int k = 0; k < k3; k++) fs3 *= c;
-                p = fs1 * fs2 * fs3;
-                fse = rescale ? 1.f : p;
+                const int k1 = __popc(K.active & 0xE01u), k2 = __popc(K.active & 0x1Eu),
+                          k3 = __popc(K.active & 0x1E0u);
+                K.fs1 = K.fs2 = K.fs3 = 1.f;
+                for (int k = 0; k < k1; k++) K.fs1 *= c;
+                for (int k = 0; k < k2; k++) K.fs2 *= c;
+                for (int k = 0; k < k3; k++) K.fs3 *= c;
+                K.fse = K.rescale ? 1.f : K.fs1 * K.fs2 * K.fs3;
             }
-            ghi = cf.g_hi;
-            glo = cf.g_lo;
-            g3 = 0;
+            K.ghi = cf.g_hi;
+            K.glo = cf.g_lo;
+            K.g3 = 0;
             for (int j = 0; j < kT; j++)
-                if ((l3 >> j) & 1u) g3 += 1u << D.gpos[j];
+                if ((l3 >> j) & 1u) K.g3 += 1u << D.gpos[j];
 #pragma unroll
-            for (int k = 0; k < 4; k++) rs3[k] = 1u << D.gpos[5 + k];
-            if (COST == 1 && (flags & PF_PHASE))
+            for (int k = 0; k < 4; k++) K.rs3[k] = 1u << D.gpos[5 + k];
+            if (COST == 1 && (K.flags & PF_PHASE))
                 for (int i = tid; i < kPhaseTable; i += kNT) stab[i] = D.table[i];
             __syncthreads();
             cur = di;
         }
-        const uint32_t base = ti.base, tl = ti.tl;
-
-        float2 *sp = reinterpret_cast<float2 *>(bufs + b * G::kBufB);
-        float2 *sl = sp + kTile;
-        const unsigned char *scost = bufs + b * G::kBufB + G::kPsiB * (BWD ? 2 : 1);
-        float2 a[16];
-        float2 l[16];
-        float pscale = 1.f, bacc = 0.f;
-
-        // ---------------- stage 1: read the landed tile, phase / lambda = C psi
-        {
-            const bool gen = !BWD && (flags & PF_GEN_INIT);
-            const bool twist_in = !BWD && (flags & PF_TWIST_IN);
-            const bool need_c = BWD ? (flags & PF_LAM_FROM_C) : (flags & PF_PHASE);
-            const int k0 = __popc(base) + __popc(l1);
-#pragma unroll
-            for (int r = 0; r < 8; r++) {
-                const uint32_t idx = l1 | ((uint32_t)r << 9);
-                if (gen) {
-                    a[2 * r] = twist(make_float2(amp0, 0.f), k0 + __popc(r));
-                    a[2 * r + 1] = twist(make_float2(amp0, 0.f), k0 + __popc(r) + 1);
-                } else {
-                    const float4 v = *reinterpret_cast<const float4 *>(sp + idx);
-                    a[2 * r] = make_float2(v.x, v.y);
-                    a[2 * r + 1] = make_float2(v.z, v.w);
-                    if (twist_in) {
-                        a[2 * r] = twist(a[2 * r], k0 + __popc(r));
-                        a[2 * r + 1] = twist(a[2 * r + 1], k0 + __popc(r) + 1);
-                    }
-                }
-                if (BWD && !(flags & PF_LAM_FROM_C)) {
-                    const float4 v = *reinterpret_cast<const float4 *>(sl + idx);
-                    l[2 * r] = make_float2(v.x, v.y);
-                    l[2 * r + 1] = make_float2(v.z, v.w);
-                }
-                if (need_c) {
-                    float c0, c1;
-                    if (COST == 0) {
-                        const float2 cc = *reinterpret_cast<const float2 *>(
-                            reinterpret_cast<const float *>(scost) + idx);
-                        c0 = cc.x;
-                        c1 = cc.y;
-                    } else {
-                        const uchar2 cc = *reinterpret_cast<const uchar2 *>(scost + idx);
-                        c0 = (float)cc.x;
-                        c1 = (float)cc.y;
-                        if (!BWD) {
-                            a[2 * r] = cmul(a[2 * r], stab[cc.x]);
-                            a[2 * r + 1] = cmul(a[2 * r + 1], stab[cc.y]);
-                        }
-                    }
-                    if (BWD) {
-                        l[2 * r] = __fmul2_rn(make_float2(c0, c0), a[2 * r]);
-                        l[2 * r + 1] = __fmul2_rn(make_float2(c1, c1), a[2 * r + 1]);
-                    } else if (COST == 0) {
-                        a[2 * r] = cmul(a[2 * r], phase_f32(c0, ghi, glo));
-                        a[2 * r + 1] = cmul(a[2 * r + 1], phase_f32(c1, ghi, glo));
-                    }
-                }
-            }
-        }
-        rot_step<0, BWD>(a, l, active & (1u << 0), R, pscale, bacc);
-        rot_step<1, BWD>(a, l, active & (1u << 9), R, pscale, bacc);
-        rot_step<2, BWD>(a, l, active & (1u << 10), R, pscale, bacc);
-        rot_step<3, BWD>(a, l, active & (1u << 11), R, pscale, bacc);
-        if (rescale) {
-            scale_all<BWD>(a, l, fs1);
-            pscale = 1.f;
-        }
-
-        // ---------------- stage 1 -> 2, in place (swizzled)
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < 8; r++) {
-            const uint32_t idx = p1 ^ swz((uint32_t)r << 9);
-            *reinterpret_cast<float4 *>(sp + idx) = make_float4(a[2 * r].x, a[2 * r].y, a[2 * r + 1].x, a[2 * r + 1].y);
-            if (BWD)
-                *reinterpret_cast<float4 *>(sl + idx) =
-                    make_float4(l[2 * r].x, l[2 * r].y, l[2 * r + 1].x, l[2 * r + 1].y);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-            a[i] = sp[p2 ^ ((uint32_t)i << 1)];
-            if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
-        }
-        rot_step<0, BWD>(a, l, active & (1u << 1), R, pscale, bacc);
-        rot_step<1, BWD>(a, l, active & (1u << 2), R, pscale, bacc);
-        rot_step<2, BWD>(a, l, active & (1u << 3), R, pscale, bacc);
-        rot_step<3, BWD>(a, l, active & (1u << 4), R, pscale, bacc);
-        if (rescale) {
-            scale_all<BWD>(a, l, fs2);
-            pscale = 1.f;
-        }
-
-        // ---------------- stage 2 -> 3
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-            sp[p2 ^ ((uint32_t)i << 1)] = a[i];
-            if (BWD) sl[p2 ^ ((uint32_t)i << 1)] = l[i];
-        }
-        __syncthreads();
-        const bool epi_c = BWD ? (flags & PF_PHASE) : (flags & PF_E);
-        float cst[16];
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-            const uint32_t idx = p3 ^ swz((uint32_t)i << 5);
-            a[i] = sp[idx];
-            if (BWD) l[i] = sl[idx];
-            if (epi_c) {
-                const uint32_t ci = l3 | ((uint32_t)i << 5);
-                cst[i] = COST == 0 ? reinterpret_cast<const float *>(scost)[ci] : (float)scost[ci];
-            }
-        }
-        // the buffer is consumed: start the tile NBUF ahead
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t tn = t + (uint32_t)NBUF * stride;
-            if (tn < total)
-                issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc);
-        }
-        rot_step<0, BWD>(a, l, active & (1u << 5), R, pscale, bacc);
-        rot_step<1, BWD>(a, l, active & (1u << 6), R, pscale, bacc);
-        rot_step<2, BWD>(a, l, active & (1u << 7), R, pscale, bacc);
-        rot_step<3, BWD>(a, l, active & (1u << 8), R, pscale, bacc);
-        scale_all<BWD>(a, l, rescale ? fs3 : fse);
-
-        // ---------------- stage 3: fused epilogue, coalesced store
-        const uint32_t g = base + g3;
-        float eacc = 0.f;
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-            const uint32_t off = g + ((i & 1) ? rs3[0] : 0) + ((i & 2) ? rs3[1] : 0) +
-                                 ((i & 4) ? rs3[2] : 0) + ((i & 8) ? rs3[3] : 0);
-            if (epi_c) {
-                const float C = cst[i];
-                if (!BWD) {
-                    eacc = fmaf(C, fmaf(a[i].x, a[i].x, a[i].y * a[i].y), eacc);
-                } else {
-                    const float2 ph = COST == 0 ? phase_f32(C, ghi, glo) : stab[(int)C];
-                    eacc = fmaf(C, fmaf(l[i].x, a[i].y, -l[i].y * a[i].x), eacc);
-                    l[i] = cmul_conj(l[i], ph);
-                    if (flags & PF_UNPHASE_PSI) a[i] = cmul_conj(a[i], ph);
-                }
-            }
-            if (D.psi_out) __stcs(D.psi_out + off, a[i]);
-            if (BWD && D.lam_out) __stcs(D.lam_out + off, l[i]);
-        }
-        // per-warp partial sums: slot tile * 8 + warp (no block barrier)
-        if (BWD) {
-            const double tb = warp_sum(bacc);
-            if (lane == 0 && D.part_beta) D.part_beta[tl * kNW + warp] = tb;
-            if (flags & PF_PHASE) {
-                const double tg = warp_sum(eacc);
-                if (lane == 0 && D.part_gamma) D.part_gamma[tl * kNW + warp] = tg;
-            }
-        } else if (flags & PF_E) {
-            const double te = warp_sum(eacc);
-            if (lane == 0 && D.part_E) D.part_E[tl * kNW + warp] = te;
-        }
+        if (K.R.mode == 0)
+            tile_body<BWD, COST, NBUF, 0>(K, D, stab, bufs, b, bar, t, stride, total, ti.base, ti.tl, tinfo, descs,
+                                          tile_begin, ndesc);
+        else
+            tile_body<BWD, COST, NBUF, 2>(K, D, stab, bufs, b, bar, t, stride, total, ti.base, ti.tl, tinfo, descs,
+                                          tile_begin, ndesc);
     }
 }
 
@@ -774,9 +820,13 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ 
         const int tot = D.p * D.tsize;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
             const int k = e / D.tsize, cst = e - k * D.tsize;
-            double s, c;
-            sincos(D.angles[D.p + k] * (double)cst, &s, &c);
-            D.table[k * kPhaseTable + cst] = make_float2((float)c, (float)(-s));
+            // e^{-i gamma c}: the turn fraction of gamma c / (2 pi) in float64
+            // (exact integer part removed), then sin/cos of pi * 2f in float32
+            const double t = D.angles[D.p + k] / kTwoPi * (double)cst;
+            const float f = (float)(t - rint(t));
+            float s, c;
+            sincospif(2.f * f, &s, &c);
+            D.table[k * kPhaseTable + cst] = make_float2(c, -s);
         }
     }
 }
@@ -845,15 +895,22 @@ cudaError_t launch_xpass(int bwd, int cost_dtype, const PassDesc *d, const uint3
 cudaError_t launch_small(const SmallDesc *d, int nd, int cost_dtype, int want_grad, int max_n,
                          int *err, cudaStream_t s) {
     const size_t smem = (size_t)2 * (1u << max_n) * sizeof(float2) + kPhaseTable * sizeof(float2);
-    auto go = [&](auto kern) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
+    // the opt-in shared-memory size is raised once per kernel to the largest
+    // size any call needs (n <= kSmallMaxN)
+    const size_t smem_max = (size_t)2 * (1u << kSmallMaxN) * sizeof(float2) + kPhaseTable * sizeof(float2);
+    auto go = [&](auto kern, int slot) -> cudaError_t {
+        static bool attr[4] = {false, false, false, false};
+        if (!attr[slot]) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem_max);
+            if (e != cudaSuccess) return e;
+            attr[slot] = true;
+        }
         kern<<<nd, kSmallThreads, smem, s>>>(d, err);
         return cudaGetLastError();
     };
-    if (cost_dtype == 0) return want_grad ? go(small_kernel<0, 1>) : go(small_kernel<0, 0>);
-    return want_grad ? go(small_kernel<1, 1>) : go(small_kernel<1, 0>);
+    if (cost_dtype == 0) return want_grad ? go(small_kernel<0, 1>, 0) : go(small_kernel<0, 0>, 1);
+    return want_grad ? go(small_kernel<1, 1>, 2) : go(small_kernel<1, 0>, 3);
 }
 
 cudaError_t launch_prep(const PrepDesc *d, int nd, int *err, cudaStream_t s) {

@@ -1,0 +1,144 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times (batched entry point, device-resident angles and results).
+
+Expected values for n = 28 and n = 24 come from tests/golden/oracle_fullsize.json,
+written by tests/golden/make_golden.py, which calls only the CPU oracle.  The
+n = 12 workload and the uneven-batch sample are small enough for the oracle to
+run inside the test.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from qaoa_inputs import uneven_batch_recipe, workload_instance, BASE_SEED
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_fullsize.json")
+
+
+@pytest.fixture(scope="module")
+def Q():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2312_06451_gb300 as qg
+
+    ctx = qg.Context(0)
+    yield qg, ctx
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(GOLDEN) as f:
+        return json.load(f)["workloads"]
+
+
+def batched_grad(qg, ctx, cost, n, angles, want_grad=True):
+    A = torch.from_numpy(np.atleast_2d(angles)).cuda()
+    s, p2 = A.shape
+    E = torch.zeros(s, dtype=torch.float64, device="cuda")
+    G = torch.zeros(s, p2, dtype=torch.float64, device="cuda")
+    ctx.expectation_batched([{"cost": cost, "mixer": qg.XMixer(n), "angles": A, "E": E, "grad": G}],
+                            want_grad=want_grad)
+    torch.cuda.synchronize()
+    return E.cpu().numpy(), G.cpu().numpy()
+
+
+def test_sk28_p8_gradient_full_size(Q, golden):
+    """SK n=28, p=8 (2^28 amplitudes): sampled cost entries bit-exact; <C> and
+    all 16 derivatives against the oracle's complex128 reverse mode."""
+    qg, ctx = Q
+    g = golden["2"]
+    w = workload_instance(2)
+    n = w["spec"]["n"]
+    cost = ctx.cost_precompute("sk", n, J=w["J"], dtype=torch.float32)
+    idx = torch.tensor(g["cost_sample_idx"], dtype=torch.int64, device="cuda")
+    np.testing.assert_array_equal(cost[idx].cpu().numpy(), np.array(g["cost_sample"], dtype=np.float32))
+    sig = g["cost_rms"]
+    E, G = batched_grad(qg, ctx, cost, n, np.array(g["angles"]))
+    assert abs(E[0] - g["E"]) <= 1e-5 * max(abs(g["E"]), sig), (E[0], g["E"])
+    tol = 1e-4 * max(np.abs(g["grad"]).max(), sig)
+    np.testing.assert_allclose(G[0], g["grad"], rtol=0, atol=tol)
+    # the host-pointer entry point without checkpoints (states recovered by undoing rounds)
+    E2, G2 = ctx.gradient(cost, qg.XMixer(n), np.array(g["angles"]), ckpt=False)
+    assert abs(E2 - g["E"]) <= 1e-5 * max(abs(g["E"]), sig)
+    np.testing.assert_allclose(G2, g["grad"], rtol=0, atol=tol)
+    # expectation alone
+    E3 = ctx.expectation(cost, qg.XMixer(n), np.array(g["angles"]))
+    assert abs(E3 - g["E"]) <= 1e-5 * max(abs(g["E"]), sig)
+
+
+def test_maxcut_3reg24_p10_batched(Q, golden):
+    """3-regular n=24, p=10, uint8 costs (bit-exact, max 36): two angle sets
+    through the batched entry point against the oracle."""
+    import oracle
+
+    qg, ctx = Q
+    g = golden["3"]
+    w = workload_instance(3, n_sets=2)
+    n = w["spec"]["n"]
+    cost = ctx.cost_precompute("maxcut", n, edges=w["edges"], dtype=torch.uint8)
+    c = cost.cpu().numpy()
+    assert c.max() <= 36
+    # sampled cost entries against the oracle's cost function
+    rng = np.random.default_rng(1)
+    idx = rng.choice(1 << n, size=256, replace=False)
+    full = oracle.cost_maxcut(n, w["edges"])
+    np.testing.assert_array_equal(c[idx].astype(np.float64), full[idx])
+    A = np.array([s["angles"] for s in g["sets"]])
+    E, G = batched_grad(qg, ctx, cost, n, A)
+    sig = g["cost_rms"]
+    for s in range(2):
+        ref = g["sets"][s]
+        assert abs(E[s] - ref["E"]) <= 1e-5 * max(abs(ref["E"]), sig)
+        np.testing.assert_allclose(G[s], ref["grad"], rtol=0, atol=1e-4 * max(np.abs(ref["grad"]).max(), sig))
+
+
+def test_maxcut_er12_p3_forward(Q):
+    """G(12, 0.5), p=3, forward only (the whole state on chip)."""
+    import oracle
+
+    qg, ctx = Q
+    w = workload_instance(1, n_sets=8)
+    n = w["spec"]["n"]
+    cost = ctx.cost_precompute("maxcut", n, edges=w["edges"], dtype=torch.uint8)
+    c = oracle.cost_maxcut(n, w["edges"])
+    E, _ = batched_grad(qg, ctx, cost, n, w["angles"], want_grad=False)
+    sig = float(np.sqrt(np.mean(c ** 2)))
+    for s in range(8):
+        ref = oracle.qaoa_expectation(n, c, w["angles"][s])
+        assert abs(E[s] - ref) <= 1e-5 * max(abs(ref), sig)
+
+
+def test_uneven_batch_sample(Q):
+    """16 instances of the uneven angle-finding batch (n in 14..22, 3-regular
+    and G(n, 0.3)), 4 angle sets each, p=6, in one batched call."""
+    import oracle
+
+    qg, ctx = Q
+    inst = uneven_batch_recipe(512, BASE_SEED + 5)[:16]
+    from qaoa_inputs import uniform_angles
+
+    jobs, refs = [], []
+    for i, it in enumerate(inst):
+        n = it["n"]
+        cost = ctx.cost_precompute("maxcut", n, edges=it["edges"], dtype=torch.uint8)
+        A = uniform_angles(6, BASE_SEED + 5 + 1000 + i, 4)
+        jobs.append({"cost": cost, "mixer": qg.XMixer(n), "angles": torch.from_numpy(A).cuda(),
+                     "E": torch.zeros(4, dtype=torch.float64, device="cuda"),
+                     "grad": torch.zeros(4, 12, dtype=torch.float64, device="cuda")})
+        refs.append((n, oracle.cost_maxcut(n, it["edges"]), A))
+    ctx.expectation_batched(jobs, want_grad=True)
+    torch.cuda.synchronize()
+    for j, (n, c, A) in zip(jobs, refs):
+        sig = float(np.sqrt(np.mean(c ** 2)))
+        for s in (0, 3):
+            E_ref, g_ref = oracle.qaoa_gradient(n, c, A[s])
+            assert abs(j["E"][s].item() - E_ref) <= 1e-5 * max(abs(E_ref), sig)
+            np.testing.assert_allclose(j["grad"][s].cpu().numpy(), g_ref, rtol=0,
+                                       atol=1e-4 * max(np.abs(g_ref).max(), sig))
