@@ -262,7 +262,8 @@ typedef struct {
     char name[48];
     int64_t launches;
     double total_ms;
-    double algo_bytes;
+    double algo_bytes;  /* HBM-bound kernels: bytes the method must move */
+    double algo_flops;  /* contractions: useful floating-point operations */
 } qaoa_kernel_stat;
 
 qaoa_status qaoa_set_profiling(qaoa_ctx *ctx, int enable);

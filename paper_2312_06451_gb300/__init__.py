@@ -24,7 +24,7 @@ from ._binding import QAOAError  # noqa: F401
 
 __all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError",
            "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched",
-           "qaoa_gradient_small_noalloc"]
+           "qaoa_gradient_small_noalloc", "ring_eigen_mixer", "save_eigen_mixer", "load_eigen_mixer"]
 
 _PROBLEMS = {"maxcut": B.QAOA_PROBLEM_MAXCUT, "wmaxcut": B.QAOA_PROBLEM_WMAXCUT,
              "sk": B.QAOA_PROBLEM_SK, "dks": B.QAOA_PROBLEM_DKS}
@@ -75,6 +75,63 @@ class EigenMixer:
         self.V, self.lam = V, lam
         self.struct = B.QaoaMixer(B.QAOA_MIXER_EIGEN, self.n, self.dim, V.data_ptr(), lam.data_ptr(),
                                   _GEMM[precision])
+
+
+MIXER_FILE_VERSION = 1
+
+
+def save_eigen_mixer(path: str, n: int, k: int, V: torch.Tensor, lam: torch.Tensor, kind: str = "ring"):
+    """Store a mixer's eigendecomposition for re-use (the paper saves the costly
+    constrained-mixer decomposition to a user file, Sec. 3, Listing 2).  The file
+    carries a format version, the problem shape and a SHA-256 of the arrays."""
+    import hashlib
+
+    Vh = V.detach().to("cpu", torch.float32).contiguous().numpy()
+    lh = lam.detach().to("cpu", torch.float64).contiguous().numpy()
+    digest = hashlib.sha256(Vh.tobytes() + lh.tobytes()).hexdigest()
+    with open(path, "wb") as f:
+        np.savez(f, V=Vh, lam=lh, meta=np.array([MIXER_FILE_VERSION, n, k], dtype=np.int64),
+                 kind=np.array(kind), sha256=np.array(digest))
+
+
+def load_eigen_mixer(path: str, n: int, k: int, kind: str = "ring", device: int = 0):
+    """Read a file written by save_eigen_mixer; raises ValueError when the
+    version, shape or checksum does not match (a truncated or altered file)."""
+    import hashlib
+
+    try:
+        with np.load(path, allow_pickle=False) as z:
+            meta, V, lam = z["meta"], z["V"], z["lam"]
+            fkind, digest = str(z["kind"]), str(z["sha256"])
+    except Exception as e:  # zipfile / npy errors of a damaged file
+        raise ValueError(f"unreadable mixer file {path}: {e}") from e
+    if meta.tolist() != [MIXER_FILE_VERSION, n, k] or fkind != kind:
+        raise ValueError(f"mixer file {path} is for {fkind} {meta.tolist()}, wanted {kind} [{MIXER_FILE_VERSION}, {n}, {k}]")
+    if hashlib.sha256(np.ascontiguousarray(V).tobytes() + np.ascontiguousarray(lam).tobytes()).hexdigest() != digest:
+        raise ValueError(f"mixer file {path} fails its checksum")
+    dev = f"cuda:{device}"
+    return torch.from_numpy(V).to(dev), torch.from_numpy(lam).to(dev)
+
+
+def ring_eigen_mixer(ctx: "Context", n: int, k: int, precision: str = "fp32", cache_file: str | None = None):
+    """EigenMixer of the ring mixer on the Hamming-weight-k states.
+
+    Pre-computation (Sec. 2.1, done once): the dense ring Hamiltonian is built
+    by the library (qaoa_ring_hamiltonian) and diagonalised in float64 with
+    torch.linalg.eigh; V is kept in float32, the eigenvalues in float64.  With
+    cache_file the decomposition is loaded from / saved to that file."""
+    import os
+
+    if cache_file and os.path.exists(cache_file):
+        V, lam = load_eigen_mixer(cache_file, n, k, "ring", ctx.device)
+    else:
+        H = ctx.ring_hamiltonian(n, k)
+        lam, V64 = torch.linalg.eigh(H)
+        V = V64.to(torch.float32).contiguous()
+        del V64, H
+        if cache_file:
+            save_eigen_mixer(cache_file, n, k, V, lam, "ring")
+    return EigenMixer(n, V.contiguous(), lam.contiguous(), precision)
 
 
 class Context:
@@ -212,7 +269,8 @@ class Context:
         arr = (B.QaoaKernelStat * max(n, 1))()
         n = self._lib.qaoa_kernel_stats(self._h, arr, n)
         return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms,
-                                       "algo_bytes": arr[i].algo_bytes} for i in range(n)}
+                                       "algo_bytes": arr[i].algo_bytes, "algo_flops": arr[i].algo_flops}
+                for i in range(n)}
 
     def reset_stats(self):
         self._lib.qaoa_reset_stats(self._h)

@@ -43,7 +43,7 @@ class QaoaJob(ctypes.Structure):
 
 class QaoaKernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", c_int64), ("total_ms", c_double),
-                ("algo_bytes", c_double)]
+                ("algo_bytes", c_double), ("algo_flops", c_double)]
 
 
 #: Every symbol include/qaoa.h declares, with its ctypes signature.

@@ -36,6 +36,8 @@ struct RoundCoef {
     float g_hi;    // gamma / (2 pi), float32 head
     float g_lo;    // gamma / (2 pi) - g_hi, float32 tail
     int rescale;   // 1: apply the cos factors after every stage (|cos b| < 1/4)
+    float b_hi;    // beta / (2 pi), float32 head (eigenbasis mixers)
+    float b_lo;    // beta / (2 pi) - b_hi
     float pad;
 };
 
@@ -128,6 +130,46 @@ struct RedOut {
     double *out;    // device result
     double scale;   // 1 for <C>, 2 for the derivatives (2 Im <...>)
 };
+
+// -------------------------------------------- eigenbasis mixer (kernels_eig)
+enum EigEpi {
+    EPI_FWD_EIG = 1,    // Y = e^{-i b lambda} (V^T X); checkpoint V^T phi
+    EPI_FWD_PHASE = 2,  // X = e^{-i g' C} (V Y); checkpoint psi_k
+    EPI_FWD_LAST = 3,   // psi_p = V Y; <C> partials; lambda_p = C psi_p
+    EPI_BWD_EIG = 4,    // beta partials; undo e^{-i b lambda}
+    EPI_BWD_PHASE = 5   // gamma partials; undo e^{-i g C}
+};
+
+struct EigEpiParams {
+    int kind;
+    int M;          // valid rows (D)
+    int ld;         // padded row length
+    int nsets;      // valid sets
+    float *out;
+    float *out2;
+    float *ckpt;
+    const float *ck_in;
+    const float *lam_hi, *lam_lo;
+    const void *cost;
+    int cost_dtype;
+    const RoundCoef *coef;
+    int coef_stride;
+    int round;
+    double *part;   // [set][M tile]
+    int part_stride;
+};
+
+cudaError_t launch_eig_prepare(const float *V, int D, int ld, float *Vp, float *Vtp, const double *lam,
+                               float *lam_hi, float *lam_lo, cudaStream_t s);
+cudaError_t launch_eig_init(float *X, float *ck0, int D, int ld, int nsets, const void *cost, int cost_dtype,
+                            const RoundCoef *coef, int coef_stride, const float2 *init, float amp0,
+                            cudaStream_t s);
+// out^T[Np][Mp] = A[Mp][Kp] * B[Np][Kp]^T with a fused epilogue; Mp, Np, Kp
+// multiples of 128.
+cudaError_t launch_eig_gemm_simt(const float *A, const float *B, int Mp, int Np, int Kp, const EigEpiParams &P,
+                                 cudaStream_t s);
+constexpr int kEigTile = 128;   // M and N tile of the eigenbasis products
+constexpr int kEigSetTile = 64; // sets per N tile
 
 // ------------------------------------------------------- launch wrappers
 // Each returns the cudaError_t of the launch.

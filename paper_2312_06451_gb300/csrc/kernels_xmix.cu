@@ -813,6 +813,9 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ 
         const double g = ga / kTwoPi;
         c.g_hi = (float)g;
         c.g_lo = (float)(g - (double)c.g_hi);
+        const double bb = be / kTwoPi;
+        c.b_hi = (float)bb;
+        c.b_lo = (float)(bb - (double)c.b_hi);
         c.pad = 0.f;
         D.coef[k] = c;
     }

@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <set>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -33,6 +34,7 @@ struct StatAcc {
     int64_t launches = 0;
     double ms = 0.0;
     double bytes = 0.0;
+    double flops = 0.0;
 };
 
 struct PendingEv {
@@ -51,9 +53,15 @@ struct Unit {
     double *grad;          // device, 2p (gradient runs)
     const float2 *init;    // device or nullptr
     int tsize;             // phase-table entries (uint8 costs)
+    int mixer_kind;        // QAOA_MIXER_X or QAOA_MIXER_EIGEN
+    int job;               // job index (eigenbasis sets of one job form one GEMM group)
+    int64_t dim;           // feasible-set size
+    const float *V;        // eigenbasis mixer: D x D eigenvectors
+    const double *lam;     // eigenbasis mixer: D eigenvalues
+    int gemm_precision;
 };
 
-enum LaunchKind { LK_PREP, LK_SMALL, LK_XPASS, LK_REDUCE };
+enum LaunchKind { LK_PREP, LK_SMALL, LK_XPASS, LK_REDUCE, LK_EIG_INIT, LK_EIG_GEMM };
 
 struct LaunchRec {
     int kind;
@@ -64,6 +72,14 @@ struct LaunchRec {
     int small_maxn = 0, small_grad = 0;
     int fam = 0;
     double bytes = 0.0;
+    double flops = 0.0;
+    // eigenbasis mixer launches (parameters passed by value)
+    EigEpiParams ep{};
+    const float *gA = nullptr, *gB = nullptr;
+    int Mp = 0, Np = 0, Kp = 0;
+    float *iX = nullptr, *ick0 = nullptr;
+    const float2 *iinit = nullptr;
+    float iamp0 = 0.f;
 };
 
 struct Plan {
@@ -79,6 +95,7 @@ struct Group {
 };
 
 constexpr int kMaxXQubits = 32;   // 32-bit element offsets in the pass kernel
+constexpr int kMaxEigDim = 1 << 16; // feasible states of an eigenbasis mixer
 constexpr int kCminDefault = 4;   // >= 16 contiguous amplitudes = one 128-byte line
 constexpr int kTmaSegBits = 8;    // shorter runs are fetched through a TMA tensor map
 constexpr size_t kAlign = 256;
@@ -148,6 +165,7 @@ struct qaoa_ctx {
     std::vector<cudaEvent_t> ev_pool;
     int64_t launches = 0;
     Plan plan;
+    std::set<std::string> eig_ready;  // prepared eigenbasis operands (by V, lambda, D)
 };
 
 namespace {
@@ -449,14 +467,19 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         std::vector<size_t> off_coef(nu), off_tab(nu), off_part(nu);
         std::vector<UnitLayout> lay(nu);
         size_t meta = 0;
+        // coefficients of all units back to back (the sets of one eigenbasis
+        // job are consecutive, so their rounds form a [set][round] array)
+        for (int i = 0; i < nu; i++) {
+            off_coef[i] = meta;
+            meta += sizeof(RoundCoef) * units[i].p;
+        }
+        meta = align_up(meta);
         for (int i = 0; i < nu; i++) {
             const Unit &u = units[i];
-            off_coef[i] = meta;
-            meta = align_up(meta + sizeof(RoundCoef) * u.p);
             off_tab[i] = meta;
             if (u.cost_dtype == QAOA_COST_U8) meta = align_up(meta + sizeof(float2) * kPhaseTable * u.p);
             off_part[i] = meta;
-            if (u.n > smax) {
+            if (u.mixer_kind == QAOA_MIXER_X && u.n > smax) {
                 lay[i] = layout_for(u, grad, ckpt);
                 meta = align_up(meta + sizeof(double) * (2 * u.p + 1) * lay[i].stride);
             }
@@ -475,7 +498,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         };
         std::map<GKey, std::vector<int>> groups;
         for (int i = 0; i < nu; i++) {
-            if (units[i].n <= smax) continue;
+            if (units[i].mixer_kind != QAOA_MIXER_X || units[i].n <= smax) continue;
             const UnitLayout &L = lay[i];
             groups[{L.T_f, L.T_b, (int)L.gf.size(), (int)L.gb.size(), units[i].p, units[i].cost_dtype}]
                 .push_back(i);
@@ -555,7 +578,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             double bytes = 0;
             for (int i = 0; i < nu; i++) {
                 const Unit &u = units[i];
-                if (u.n > smax || u.cost_dtype != dt) continue;
+                if (u.mixer_kind != QAOA_MIXER_X || u.n > smax || u.cost_dtype != dt) continue;
                 SmallDesc s;
                 std::memset(&s, 0, sizeof(s));
                 s.cost = u.cost;
@@ -694,6 +717,170 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 L.push_back(r);
             }
         }
+        // ---- eigenbasis-mixer jobs: one GEMM pipeline per job, the job's angle
+        // sets as the columns of every product
+        {
+            struct EG {
+                int u0, S, Spad, ld, nmt;
+                size_t st_off, part_off;
+            };
+            std::vector<EG> eg;
+            size_t st_bytes = 0, part_bytes = 0;
+            for (int i = 0; i < nu;) {
+                if (units[i].mixer_kind != QAOA_MIXER_EIGEN) {
+                    i++;
+                    continue;
+                }
+                int j = i;
+                while (j < nu && units[j].mixer_kind == QAOA_MIXER_EIGEN && units[j].job == units[i].job) j++;
+                const Unit &u = units[i];
+                if (u.gemm_precision != QAOA_GEMM_FP32_SIMT)
+                    return fail(ctx, QAOA_ERR_UNSUPPORTED, "eigenbasis GEMM precision %d not available in this build",
+                                u.gemm_precision);
+                EG g;
+                g.u0 = i;
+                g.S = j - i;
+                g.Spad = (int)align_up((size_t)g.S, kEigSetTile);
+                g.ld = (int)align_up((size_t)u.dim, kEigTile);
+                g.nmt = g.ld / kEigTile;
+                const size_t mat = (size_t)2 * g.Spad * g.ld * sizeof(float);
+                const int nmat = grad ? 3 + 2 * u.p : 2;
+                g.st_off = st_bytes;
+                st_bytes += align_up(mat * nmat);
+                g.part_off = part_bytes;
+                part_bytes += align_up(sizeof(double) * (1 + 2 * u.p) * g.Spad * g.nmt);
+                eg.push_back(g);
+                i = j;
+            }
+            if (!eg.empty()) {
+                void *d_est = nullptr, *d_epart = nullptr;
+                st = scratch(ctx, "eigstate", st_bytes, &d_est);
+                if (st) return st;
+                st = scratch(ctx, "eigpart", part_bytes, &d_epart);
+                if (st) return st;
+                for (const EG &g : eg) {
+                    const Unit &u = units[g.u0];
+                    const int D = (int)u.dim, ld = g.ld, p = u.p;
+                    // padded V, V^T and split eigenvalues, prepared once per (V, lambda)
+                    char nm[96];
+                    void *dV = nullptr, *dVt = nullptr, *dL = nullptr;
+                    snprintf(nm, sizeof(nm), "eigV:%p:%p:%d", (const void *)u.V, (const void *)u.lam, D);
+                    const std::string key = nm;
+                    st = scratch(ctx, (key + ":V").c_str(), (size_t)ld * ld * sizeof(float), &dV);
+                    if (st) return st;
+                    st = scratch(ctx, (key + ":Vt").c_str(), (size_t)ld * ld * sizeof(float), &dVt);
+                    if (st) return st;
+                    st = scratch(ctx, (key + ":lam").c_str(), (size_t)2 * ld * sizeof(float), &dL);
+                    if (st) return st;
+                    if (!ctx->eig_ready.count(key)) {
+                        float *lh = static_cast<float *>(dL);
+                        cudaError_t e = launch_eig_prepare(u.V, D, ld, static_cast<float *>(dV),
+                                                           static_cast<float *>(dVt), u.lam, lh, lh + ld, ctx->stream);
+                        if (e != cudaSuccess) return cuda_fail(ctx, e, "eigenbasis preparation");
+                        QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "eigenbasis preparation");
+                        ctx->launches++;
+                        ctx->eig_ready.insert(key);
+                    }
+                    const float *Vp = static_cast<const float *>(dV), *Vtp = static_cast<const float *>(dVt);
+                    const float *lam_hi = static_cast<const float *>(dL), *lam_lo = lam_hi + ld;
+                    const size_t mat = (size_t)2 * g.Spad * ld;
+                    float *base = reinterpret_cast<float *>(static_cast<char *>(d_est) + g.st_off);
+                    float *X = base, *Y = base + mat, *Lm = grad ? base + 2 * mat : nullptr;
+                    auto CKX = [&](int k) { return base + (3 + k) * mat; };
+                    auto CKY = [&](int k) { return base + (3 + p + k) * mat; };
+                    double *part = reinterpret_cast<double *>(static_cast<char *>(d_epart) + g.part_off);
+                    const int64_t pq = (int64_t)g.Spad * g.nmt;  // partials per quantity
+                    const RoundCoef *coef = reinterpret_cast<const RoundCoef *>(mb + off_coef[g.u0]);
+                    EigEpiParams ep{};
+                    ep.M = D;
+                    ep.ld = ld;
+                    ep.nsets = g.S;
+                    ep.lam_hi = lam_hi;
+                    ep.lam_lo = lam_lo;
+                    ep.cost = u.cost;
+                    ep.cost_dtype = u.cost_dtype;
+                    ep.coef = coef;
+                    ep.coef_stride = p;
+                    ep.part_stride = g.nmt;
+                    const double gflops = 2.0 * D * (double)D * 2.0 * g.S;
+                    const int fam_g = family(ctx, "eig_gemm_simt");
+                    auto gemm = [&](const float *A, const float *B, EigEpiParams q) {
+                        LaunchRec r;
+                        r.kind = LK_EIG_GEMM;
+                        r.gA = A;
+                        r.gB = B;
+                        r.Mp = ld;
+                        r.Np = 2 * g.Spad;
+                        r.Kp = ld;
+                        r.ep = q;
+                        r.flops = gflops;
+                        r.fam = fam_g;
+                        L.push_back(r);
+                    };
+                    {
+                        LaunchRec r;
+                        r.kind = LK_EIG_INIT;
+                        r.ep = ep;
+                        r.iX = X;
+                        r.ick0 = grad ? CKX(0) : nullptr;
+                        r.iinit = u.init;
+                        r.iamp0 = (float)(1.0 / std::sqrt((double)D));
+                        r.fam = family(ctx, "eig_init");
+                        L.push_back(r);
+                    }
+                    for (int k = 0; k < p; k++) {
+                        EigEpiParams q = ep;
+                        q.kind = EPI_FWD_EIG;
+                        q.round = k;
+                        q.out = Y;
+                        q.ckpt = grad ? CKY(k) : nullptr;
+                        gemm(Vtp, X, q);
+                        q = ep;
+                        if (k < p - 1) {
+                            q.kind = EPI_FWD_PHASE;
+                            q.round = k + 1;
+                            q.out = X;
+                            q.ckpt = grad ? CKX(k + 1) : nullptr;
+                        } else {
+                            q.kind = EPI_FWD_LAST;
+                            q.round = k;
+                            q.out = grad ? X : nullptr;
+                            q.out2 = Lm;
+                            q.part = part;
+                        }
+                        gemm(Vp, Y, q);
+                    }
+                    if (grad) {
+                        for (int k = p - 1; k >= 0; k--) {
+                            EigEpiParams q = ep;
+                            q.kind = EPI_BWD_EIG;
+                            q.round = k;
+                            q.out = Y;
+                            q.ck_in = CKY(k);
+                            q.part = part + (1 + k) * pq;
+                            gemm(Vtp, Lm, q);
+                            q = ep;
+                            q.kind = EPI_BWD_PHASE;
+                            q.round = k;
+                            q.out = k > 0 ? Lm : nullptr;
+                            q.ck_in = CKX(k);
+                            q.part = part + (1 + p + k) * pq;
+                            gemm(Vp, Y, q);
+                        }
+                    }
+                    for (int s2 = 0; s2 < g.S; s2++) {
+                        const Unit &us = units[g.u0 + s2];
+                        add_reduction(part + (int64_t)s2 * g.nmt, g.nmt, us.E, 1.0);
+                        if (grad)
+                            for (int k = 0; k < p; k++) {
+                                add_reduction(part + (1 + k) * pq + (int64_t)s2 * g.nmt, g.nmt, us.grad + k, 2.0);
+                                add_reduction(part + (1 + p + k) * pq + (int64_t)s2 * g.nmt, g.nmt,
+                                              us.grad + p + k, 2.0);
+                            }
+                    }
+                }
+            }
+        }
         if (!routs.empty()) {
             LaunchRec r;
             r.kind = LK_REDUCE;
@@ -767,6 +954,13 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                              reinterpret_cast<const uint32_t *>(db + r.tb_off), r.ndesc, r.tiles,
                              ctx->d_err, ctx->stream);
             break;
+        case LK_EIG_INIT:
+            e = launch_eig_init(r.iX, r.ick0, r.ep.M, r.ep.ld, r.ep.nsets, r.ep.cost, r.ep.cost_dtype, r.ep.coef,
+                                r.ep.coef_stride, r.iinit, r.iamp0, ctx->stream);
+            break;
+        case LK_EIG_GEMM:
+            e = launch_eig_gemm_simt(r.gA, r.gB, r.Mp, r.Np, r.Kp, r.ep, ctx->stream);
+            break;
         case LK_REDUCE:
             e = launch_reduce(reinterpret_cast<const RedChunk *>(db + r.desc_off), r.ndesc,
                               static_cast<double *>(ctx->bufs["level2"].p),
@@ -780,17 +974,31 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             ctx->pending.push_back({r.fam, ea, eb});
             ctx->fam_stats[r.fam].launches++;
             ctx->fam_stats[r.fam].bytes += r.bytes;
+            ctx->fam_stats[r.fam].flops += r.flops;
         }
     }
     return QAOA_OK;
 }
 
-qaoa_status check_x_args(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const qaoa_mixer *mx,
+qaoa_status check_args(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const qaoa_mixer *mx,
                          const void *d_init, int p) {
     if (!ctx) return QAOA_ERR_INVALID;
     if (!mx) return fail(ctx, QAOA_ERR_INVALID, "mixer is NULL");
-    if (mx->kind == QAOA_MIXER_EIGEN)
-        return fail(ctx, QAOA_ERR_UNSUPPORTED, "eigenbasis mixer not available in this build");
+    if (mx->kind == QAOA_MIXER_EIGEN) {
+        if (!mx->d_V || !mx->d_lambda || ((uintptr_t)mx->d_V & 15) || ((uintptr_t)mx->d_lambda & 7))
+            return fail(ctx, QAOA_ERR_INVALID, "eigenbasis mixer needs aligned d_V and d_lambda");
+        if (mx->dim < 1 || mx->dim > kMaxEigDim)
+            return fail(ctx, QAOA_ERR_INVALID, "eigenbasis mixer dim must be in [1, %d]", kMaxEigDim);
+        if (mx->gemm_precision < QAOA_GEMM_FP32_SIMT || mx->gemm_precision > QAOA_GEMM_BF16X3)
+            return fail(ctx, QAOA_ERR_INVALID, "unknown GEMM precision %d", mx->gemm_precision);
+        if (p < 1 || p > 4096) return fail(ctx, QAOA_ERR_INVALID, "p must be in [1, 4096] (got %d)", p);
+        if (cost_dtype != QAOA_COST_F32 && cost_dtype != QAOA_COST_U8)
+            return fail(ctx, QAOA_ERR_INVALID, "unknown cost dtype %d", cost_dtype);
+        if (!d_cost || ((uintptr_t)d_cost & 15))
+            return fail(ctx, QAOA_ERR_INVALID, "d_cost must be a 16-byte aligned device pointer");
+        if (d_init && ((uintptr_t)d_init & 7)) return fail(ctx, QAOA_ERR_INVALID, "d_init must be 8-byte aligned");
+        return QAOA_OK;
+    }
     if (mx->kind != QAOA_MIXER_X) return fail(ctx, QAOA_ERR_INVALID, "unknown mixer kind %d", mx->kind);
     if (mx->n < 1 || mx->n > kMaxXQubits)
         return fail(ctx, QAOA_ERR_INVALID, "X mixer needs 1 <= n <= %d (got %d)", kMaxXQubits, mx->n);
@@ -823,7 +1031,7 @@ qaoa_status read_dev_err(qaoa_ctx *ctx) {
 qaoa_status scalar_run(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const qaoa_mixer *mixer,
                        const void *d_init, int p, const double *angles, double *E, double *grad,
                        int ckpt) {
-    qaoa_status st = check_x_args(ctx, d_cost, cost_dtype, mixer, d_init, p);
+    qaoa_status st = check_args(ctx, d_cost, cost_dtype, mixer, d_init, p);
     if (st) return st;
     if (!angles || !E || (grad == nullptr) != (ckpt < 0))
         return fail(ctx, QAOA_ERR_INVALID, "angles and result pointers must be non-NULL");
@@ -859,6 +1067,11 @@ qaoa_status scalar_run(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
     u.grad = grad ? io + 2 * p + 1 : nullptr;
     u.init = static_cast<const float2 *>(d_init);
     u.tsize = kPhaseTable;
+    u.mixer_kind = mixer->kind;
+    u.dim = mixer->dim;
+    u.V = mixer->d_V;
+    u.lam = mixer->d_lambda;
+    u.gemm_precision = mixer->gemm_precision;
     std::vector<Unit> us(1, u);
     st = run_units(ctx, us, grad != nullptr, grad ? (ckpt ? 1 : 0) : 0);
     if (st) return st;
@@ -1110,7 +1323,7 @@ qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *
         std::vector<Unit> units;
         for (int j = 0; j < n_jobs; j++) {
             const qaoa_job &jb = jobs[j];
-            qaoa_status st = check_x_args(ctx, jb.d_cost, jb.cost_dtype, jb.mixer, jb.d_init, jb.p);
+            qaoa_status st = check_args(ctx, jb.d_cost, jb.cost_dtype, jb.mixer, jb.d_init, jb.p);
             if (st) return st;
             if (jb.n_sets < 1 || !jb.d_angles || !jb.d_E || (want_grad && !jb.d_grad))
                 return fail(ctx, QAOA_ERR_INVALID, "job %d: bad sets or output pointers", j);
@@ -1126,6 +1339,12 @@ qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *
                 u.grad = want_grad ? jb.d_grad + (int64_t)s * 2 * jb.p : nullptr;
                 u.init = static_cast<const float2 *>(jb.d_init);
                 u.tsize = kPhaseTable;
+                u.mixer_kind = jb.mixer->kind;
+                u.job = j;
+                u.dim = jb.mixer->dim;
+                u.V = jb.mixer->d_V;
+                u.lam = jb.mixer->d_lambda;
+                u.gemm_precision = jb.mixer->gemm_precision;
                 units.push_back(u);
             }
         }
@@ -1161,6 +1380,7 @@ int qaoa_kernel_stats(qaoa_ctx *ctx, qaoa_kernel_stat *out, int max) {
         out[i].launches = ctx->fam_stats[i].launches;
         out[i].total_ms = ctx->fam_stats[i].ms;
         out[i].algo_bytes = ctx->fam_stats[i].bytes;
+        out[i].algo_flops = ctx->fam_stats[i].flops;
     }
     return nf;
 }

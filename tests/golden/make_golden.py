@@ -27,6 +27,15 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_fullsize.
 def main():
     oracle.build()
     res = {"generated_by": "tests/golden/make_golden.py (CPU oracle, complex128)", "workloads": {}}
+    if os.path.exists(OUT) and "--all" not in sys.argv:
+        with open(OUT) as f:
+            res = json.load(f)
+    if "4" not in res["workloads"]:
+        workload4(res)
+        with open(OUT, "w") as f:
+            json.dump(res, f, indent=1)
+    if "2" in res["workloads"] and "3" in res["workloads"]:
+        return
     rng = np.random.default_rng(7)
 
     # Workload 2: SK n=28, p=8, one angle set, E and gradient.
@@ -61,6 +70,24 @@ def main():
     print("workload 3 done", res["workloads"]["3"]["oracle_seconds"])
     with open(OUT, "w") as f:
         json.dump(res, f, indent=1)
+
+
+def workload4(res):
+    """Densest 8-subgraph on G(16, 0.5), ring mixer on the 12870 weight-8
+    states, p=6: two angle sets, <C> and gradient."""
+    w = workload_instance(4, n_sets=2)
+    n, k, p = w["spec"]["n"], w["spec"]["k"], w["spec"]["p"]
+    t = time.time()
+    st = oracle.dicke_states(n, k)
+    cost = oracle.cost_dks(n, w["edges"], st)
+    sets = []
+    for s in range(2):
+        E, g = oracle.qaoa_gradient(n, cost, w["angles"][s], "ring", st)
+        sets.append({"angles": w["angles"][s].tolist(), "E": E, "grad": g.tolist()})
+    res["workloads"]["4"] = {"name": w["spec"]["name"], "n": n, "k": k, "p": p, "sets": sets,
+                             "cost_rms": float(np.sqrt(np.mean(cost ** 2))),
+                             "oracle_seconds": time.time() - t}
+    print("workload 4 done", res["workloads"]["4"]["oracle_seconds"])
 
 
 if __name__ == "__main__":
