@@ -64,6 +64,25 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def gemm_peak(gemm: str):
+    """Denominator of a contraction's roofline.  CUDA-core fp32: 152 SMs x 128
+    FP32 lanes x 2 flop x 2070 MHz (unit counts and maximum clock).  TF32 /
+    split-precision tensor paths: the measured bf16 dense peak x the nominal
+    tf32 / bf16 ratio (1.1 / 2.25); BF16x3 uses the bf16 peak itself."""
+    if gemm == "fp32":
+        return {"bound": "alu", "peak": 152 * 128 * 2 * 2.070e9 / 1e12, "source": "derived: 152 SM x 128 lanes x 2 x 2.07 GHz"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16 = 1901.6
+    src = "fallback"
+    if os.path.exists(path):
+        with open(path) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        src = "measured"
+    if gemm == "bf16x3":
+        return {"bound": "tensor", "peak": bf16, "source": f"{src} bf16 burst"}
+    return {"bound": "tensor", "peak": bf16 * 1.1 / 2.25, "source": f"{src} bf16 burst x 1.1/2.25 (tf32)"}
+
+
 def aggregate(local_seconds: float, local_units: int, world: int, reduce_max=None, reduce_sum=None):
     """Whole-job throughput: units of all ranks over the slowest rank's time."""
     t = reduce_max(local_seconds) if reduce_max else local_seconds
@@ -182,7 +201,7 @@ class Workload:
     copied into the job buffers from a device pool first (a 2p-double copy per
     set, so every step evaluates fresh angles)."""
 
-    def __init__(self, qg, ctx, idx, dev, pool_steps, n_override=None):
+    def __init__(self, qg, ctx, idx, dev, pool_steps, n_override=None, gemm="fp32"):
         import torch
 
         from qaoa_inputs import BASE_SEED, sk_couplings, uneven_batch_recipe, uniform_angles, workload_instance
@@ -197,7 +216,24 @@ class Workload:
         self.p = p = spec["p"]
         self.jobs = []
         self.pools = []
-        if idx == 5:
+        if idx == 4:
+            w = workload_instance(4, n_sets=spec["n_sets"] * pool_steps)
+            n, k = spec["n"], spec["k"]
+            self.grad = True
+            cost = ctx.cost_precompute("dks", n, edges=w["edges"], k=k, dtype=torch.uint8)
+            t0 = time.perf_counter()
+            mixer = qg.ring_eigen_mixer(ctx, n, k, precision=gemm)
+            torch.cuda.synchronize()
+            self.precompute_s = time.perf_counter() - t0
+            self.eig_mixer = mixer
+            self._add_job(cost, n, w["angles"], spec["n_sets"])
+            self.name = spec["name"]
+            self.units = spec["n_sets"]
+            self.config = {"workload": spec["name"], "problem": "densest k-subgraph, G(16,0.5)", "n": n, "k": k,
+                           "feasible_states": int(mixer.dim), "p": p, "mixer": f"ring XY via V diag(e^-ib lambda) V^T",
+                           "gemm": gemm, "angle_sets_per_step": spec["n_sets"], "cost_dtype": "u8",
+                           "eig_precompute_s": round(self.precompute_s, 2)}
+        elif idx == 5:
             inst = uneven_batch_recipe(spec["n_instances"], BASE_SEED + 5)
             self.grad = True
             for i, it in enumerate(inst):
@@ -239,7 +275,8 @@ class Workload:
         ang = pool[:n_sets].clone()
         E = torch.zeros(n_sets, dtype=torch.float64, device=self.dev)
         G = torch.zeros(n_sets, 2 * self.p, dtype=torch.float64, device=self.dev)
-        self.jobs.append({"cost": cost, "mixer": self.qg.XMixer(n), "angles": ang, "E": E, "grad": G})
+        mixer = getattr(self, "eig_mixer", None) or self.qg.XMixer(n)
+        self.jobs.append({"cost": cost, "mixer": mixer, "angles": ang, "E": E, "grad": G})
         self.pools.append((pool, n_sets, n, np.ascontiguousarray(A)))
 
     def load_angles(self, step):
@@ -289,6 +326,17 @@ class Workload:
             dt = (time.perf_counter() - t) * p
             return 1.0 / dt, oracle.get_threads(), (f"oracle gradient of one round (p=1) at n={n}, "
                                                      f"scaled x{p} to the p={p} unit")
+        if self.idx == 4:
+            w = workload_instance(4, n_sets=1)
+            n, k = 16, 8
+            st = oracle.dicke_states(n, k)
+            cost = oracle.cost_dks(n, w["edges"], st)
+            a = w["angles"][0]
+            t = time.perf_counter()
+            oracle.qaoa_gradient(n, cost, np.array([a[0], a[p]]), "ring", st)
+            dt = (time.perf_counter() - t) * p
+            return 1.0 / dt, oracle.get_threads(), (f"oracle gradient of one round (p=1) of one angle set, "
+                                                     f"power-series ring mixer on D={len(st)}, scaled x{p}")
         if self.idx in (1, 3):
             w = workload_instance(self.idx, n_sets=2)
             n = self.pools[0][2]
@@ -336,7 +384,7 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     import torch
 
     ctx = qg.Context(local, stream)
-    W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n)
+    W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n, args.gemm)
 
     graph = None
     if args.graph:
@@ -418,7 +466,16 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     peaks = measured_peaks()
     roof = None
     fams = [k for k in stats if stats[k]["launches"] and stats[k]["total_ms"] > 0]
-    if fams:
+    if fams and stats[max(fams, key=lambda k: stats[k]["total_ms"])]["algo_flops"] > 0:
+        fam = max(fams, key=lambda k: stats[k]["total_ms"])
+        st = stats[fam]
+        achieved = st["algo_flops"] / (st["total_ms"] * 1e-3) / 1e12
+        pk = gemm_peak(args.gemm)
+        roof = {"bound": pk["bound"], "kernel": fam, "achieved": achieved, "peak": pk["peak"], "unit": "TFLOP/s",
+                "frac": achieved / pk["peak"], "peak_source": pk["source"], "traffic": traffic_for(fam),
+                "algo_flops_per_launch": st["algo_flops"] / st["launches"],
+                "launch_ms": st["total_ms"] / st["launches"]}
+    elif fams:
         fam = max(fams, key=lambda k: stats[k]["total_ms"])
         st = stats[fam]
         per_launch_bytes = st["algo_bytes"] / st["launches"]
@@ -469,9 +526,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None,
                     help="override the qubit count (small cases for profiler captures)")
-    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[1, 2, 3, 5],
+    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[1, 2, 3, 4, 5],
                     help="1: MaxCut n=12 p=3 forward; 2: SK n=28 p=8 gradient (default); "
-                         "3: 3-regular n=24 p=10, 1024 angle sets; 5: 512 uneven instances x 4 sets")
+                         "3: 3-regular n=24 p=10, 1024 angle sets; 4: densest 8-subgraph n=16 ring mixer "
+                         "(D=12870), 256 angle sets; 5: 512 uneven instances x 4 sets")
+    ap.add_argument("--gemm", default="fp32", choices=["fp32", "3xtf32", "bf16x3"],
+                    help="eigenbasis product precision (workload 4)")
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
     args = ap.parse_args()
     ws, rank, local = dist_env()

@@ -142,3 +142,31 @@ def test_uneven_batch_sample(Q):
             assert abs(j["E"][s].item() - E_ref) <= 1e-5 * max(abs(E_ref), sig)
             np.testing.assert_allclose(j["grad"][s].cpu().numpy(), g_ref, rtol=0,
                                        atol=1e-4 * max(np.abs(g_ref).max(), sig))
+
+
+def test_dks16_k8_ring_p6_full_size(Q, golden):
+    """Densest 8-subgraph on G(16, 0.5), ring mixer on all 12870 weight-8
+    states through its eigendecomposition, p=6, 256 angle sets in one batched
+    gradient call; sets 0 and 1 against the oracle's power-series mixer."""
+    qg, ctx = Q
+    g = golden["4"]
+    w = workload_instance(4)
+    n, k, p = w["spec"]["n"], w["spec"]["k"], w["spec"]["p"]
+    cost = ctx.cost_precompute("dks", n, edges=w["edges"], k=k, dtype=torch.uint8)
+    mixer = qg.ring_eigen_mixer(ctx, n, k)
+    A = w["angles"]
+    assert np.allclose(A[:2], [s["angles"] for s in g["sets"]])
+    E = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+    G = torch.zeros(A.shape[0], 2 * p, dtype=torch.float64, device="cuda")
+    ctx.expectation_batched([{"cost": cost, "mixer": mixer, "angles": torch.from_numpy(A).cuda(), "E": E,
+                              "grad": G}], want_grad=True)
+    torch.cuda.synchronize()
+    sig = g["cost_rms"]
+    for s in range(2):
+        ref = g["sets"][s]
+        assert abs(E[s].item() - ref["E"]) <= 1e-5 * max(abs(ref["E"]), sig), (E[s].item(), ref["E"])
+        np.testing.assert_allclose(G[s].cpu().numpy(), ref["grad"], rtol=0,
+                                   atol=1e-4 * max(np.abs(ref["grad"]).max(), sig))
+    # every set: <C> within the cost range
+    Eh = E.cpu().numpy()
+    assert np.all(np.isfinite(Eh)) and Eh.min() >= 0 and Eh.max() <= len(w["edges"])
