@@ -68,7 +68,7 @@ def gemm_peak(gemm: str):
     """Denominator of a contraction's roofline.  CUDA-core fp32: 152 SMs x 128
     FP32 lanes x 2 flop x 2070 MHz (unit counts and maximum clock).  TF32 /
     split-precision tensor paths: the measured bf16 dense peak x the nominal
-    tf32 / bf16 ratio (1.1 / 2.25); BF16x3 uses the bf16 peak itself."""
+    tf32 / bf16 ratio (1.1 / 2.25)."""
     if gemm == "fp32":
         return {"bound": "alu", "peak": 152 * 128 * 2 * 2.070e9 / 1e12, "source": "derived: 152 SM x 128 lanes x 2 x 2.07 GHz"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -78,8 +78,6 @@ def gemm_peak(gemm: str):
         with open(path) as f:
             bf16 = float(json.load(f)["bf16_tflops"])
         src = "measured"
-    if gemm == "bf16x3":
-        return {"bound": "tensor", "peak": bf16, "source": f"{src} bf16 burst"}
     return {"bound": "tensor", "peak": bf16 * 1.1 / 2.25, "source": f"{src} bf16 burst x 1.1/2.25 (tf32)"}
 
 
@@ -530,8 +528,8 @@ def main():
                     help="1: MaxCut n=12 p=3 forward; 2: SK n=28 p=8 gradient (default); "
                          "3: 3-regular n=24 p=10, 1024 angle sets; 4: densest 8-subgraph n=16 ring mixer "
                          "(D=12870), 256 angle sets; 5: 512 uneven instances x 4 sets")
-    ap.add_argument("--gemm", default="fp32", choices=["fp32", "3xtf32", "bf16x3"],
-                    help="eigenbasis product precision (workload 4)")
+    ap.add_argument("--gemm", default="3xtf32", choices=["fp32", "3xtf32"],
+                    help="eigenbasis product precision (workload 4): tcgen05 3xTF32 or CUDA-core float32")
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
     args = ap.parse_args()
     ws, rank, local = dist_env()

@@ -2,6 +2,7 @@
 // Not part of the public ABI (that is include/qaoa.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -157,17 +158,25 @@ struct EigEpiParams {
     int round;
     double *part;   // [set][M tile]
     int part_stride;
+    float *out_lo;  // tensor-core path: remainder planes of split outputs
+    float *out2_lo;
 };
 
-cudaError_t launch_eig_prepare(const float *V, int D, int ld, float *Vp, float *Vtp, const double *lam,
-                               float *lam_hi, float *lam_lo, cudaStream_t s);
-cudaError_t launch_eig_init(float *X, float *ck0, int D, int ld, int nsets, const void *cost, int cost_dtype,
-                            const RoundCoef *coef, int coef_stride, const float2 *init, float amp0,
+// Vp_lo / Vtp_lo non-null: Vp / Vtp get the tf32 heads, *_lo the remainders.
+cudaError_t launch_eig_prepare(const float *V, int D, int ld, float *Vp, float *Vtp, float *Vp_lo, float *Vtp_lo,
+                               const double *lam, float *lam_hi, float *lam_lo, cudaStream_t s);
+cudaError_t launch_eig_init(float *X, float *X_lo, float *ck0, int D, int ld, int nsets, const void *cost,
+                            int cost_dtype, const RoundCoef *coef, int coef_stride, const float2 *init, float amp0,
                             cudaStream_t s);
 // out^T[Np][Mp] = A[Mp][Kp] * B[Np][Kp]^T with a fused epilogue; Mp, Np, Kp
 // multiples of 128.
 cudaError_t launch_eig_gemm_simt(const float *A, const float *B, int Mp, int Np, int Kp, const EigEpiParams &P,
                                  cudaStream_t s);
+// tcgen05 3xTF32 product with the same epilogues; tensor maps (2-d, K-major,
+// 32-float boxes x 128 rows, 128-byte swizzle) of the operand planes.
+cudaError_t launch_eig_gemm_tc(const CUtensorMap &a_hi, const CUtensorMap &a_lo, const CUtensorMap &b_hi,
+                               const CUtensorMap &b_lo, int Mp, int Np, int Kp, const EigEpiParams &P, int *err,
+                               cudaStream_t s);
 constexpr int kEigTile = 128;   // M and N tile of the eigenbasis products
 constexpr int kEigSetTile = 64; // sets per N tile
 

@@ -16,6 +16,7 @@
 // direction as well, thanks to checkpoints of V^T phi_k and psi_{k-1}.
 #include "common.cuh"
 
+#include <cuda.h>
 #include <math.h>
 
 namespace qg {
@@ -63,7 +64,23 @@ struct EpiArgs {
     int round;            // round whose beta / gamma this epilogue uses
     double *part;         // partial sums [set][M tile] (kind dependent) or nullptr
     int part_stride;      // = number of M tiles
+    float *out_lo;        // split outputs for tensor-core operands: out holds the
+    float *out2_lo;       // tf32 head, out_lo the float32 remainder (or nullptr)
 };
+
+// Store v to out (and its tf32 split when out_lo is set).  The head is v
+// rounded to the nearest tf32 value (magnitude rounded half up on the 13
+// dropped bits), so the remainder's sign does not follow v's: the tensor
+// cores' own truncation of the remainder then carries no bias.
+__device__ __forceinline__ void put(float *out, float *out_lo, size_t o, float v) {
+    if (out_lo) {
+        const float hi = __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+        out[o] = hi;
+        out_lo[o] = v - hi;
+    } else {
+        out[o] = v;
+    }
+}
 
 __device__ __forceinline__ float cost_at(const EpiArgs &E, int j) {
     return E.cost_dtype == 0 ? __ldg(reinterpret_cast<const float *>(E.cost) + j)
@@ -83,8 +100,8 @@ __device__ __forceinline__ float epi_elem(const EpiArgs &E, int j, int s, float2
             E.ckpt[o_im] = v.y;
         }
         const float2 w = cmul(v, turn_phase(cf.b_hi, cf.b_lo, E.lam_hi[j], E.lam_lo[j]));
-        E.out[o_re] = w.x;
-        E.out[o_im] = w.y;
+        put(E.out, E.out_lo, o_re, w.x);
+        put(E.out, E.out_lo, o_im, w.y);
         break;
     }
     case EPI_FWD_PHASE: {  // X = e^{-i g' C} v, checkpoint psi_k
@@ -93,8 +110,8 @@ __device__ __forceinline__ float epi_elem(const EpiArgs &E, int j, int s, float2
             E.ckpt[o_im] = v.y;
         }
         const float2 w = cmul(v, turn_phase(cf.g_hi, cf.g_lo, cost_at(E, j), 0.f));
-        E.out[o_re] = w.x;
-        E.out[o_im] = w.y;
+        put(E.out, E.out_lo, o_re, w.x);
+        put(E.out, E.out_lo, o_im, w.y);
         break;
     }
     case EPI_FWD_LAST: {  // psi_p: <C> partial, store psi_p and lambda_p = C psi_p
@@ -105,8 +122,8 @@ __device__ __forceinline__ float epi_elem(const EpiArgs &E, int j, int s, float2
             E.out[o_im] = v.y;
         }
         if (E.out2) {
-            E.out2[o_re] = C * v.x;
-            E.out2[o_im] = C * v.y;
+            put(E.out2, E.out2_lo, o_re, C * v.x);
+            put(E.out2, E.out2_lo, o_im, C * v.y);
         }
         break;
     }
@@ -117,8 +134,8 @@ __device__ __forceinline__ float epi_elem(const EpiArgs &E, int j, int s, float2
         const float lam = E.lam_hi[j] + E.lam_lo[j];
         contrib = lam * (v.x * psi.y - v.y * psi.x);  // Im(conj(v) lambda psi)
         const float2 w = make_float2(fmaf(v.x, ph.x, v.y * ph.y), fmaf(v.y, ph.x, -v.x * ph.y));  // v conj(ph)
-        E.out[o_re] = w.x;
-        E.out[o_im] = w.y;
+        put(E.out, E.out_lo, o_re, w.x);
+        put(E.out, E.out_lo, o_im, w.y);
         break;
     }
     case EPI_BWD_PHASE: {  // gamma partial with phi = e^{-i g C} psi_{k-1}, then undo the phase
@@ -128,8 +145,8 @@ __device__ __forceinline__ float epi_elem(const EpiArgs &E, int j, int s, float2
         contrib = C * (v.x * phi.y - v.y * phi.x);
         if (E.out) {
             const float2 w = make_float2(fmaf(v.x, ph.x, v.y * ph.y), fmaf(v.y, ph.x, -v.x * ph.y));
-            E.out[o_re] = w.x;
-            E.out[o_im] = w.y;
+            put(E.out, E.out_lo, o_re, w.x);
+            put(E.out, E.out_lo, o_im, w.y);
         }
         break;
     }
@@ -231,11 +248,266 @@ gemm_simt_kernel(const float *__restrict__ A, const float *__restrict__ B, int K
     }
 }
 
+// ------------------------------------------------- tcgen05 split-TF32 GEMM
+// out^T[N][M] = A[M][K] B[N][K]^T with A = A_hi + A_lo and B = B_hi + B_lo held
+// as separate tf32 planes: per k-step the tensor cores add A_lo B_hi + A_hi B_lo
+// + A_hi B_hi ("3xTF32") into a float32 accumulator in tensor memory.
+//
+// The tensor-core accumulation does not round to nearest: its error shrinks
+// magnitudes and grows with the number of products accumulated.  So each
+// 32-wide K chunk (12 MMAs) is accumulated into a fresh tensor-memory buffer
+// (two buffers alternate) and drained at once into float32 registers with
+// round-to-nearest adds.  The operand split rounds the head to nearest (see
+// put()), so the hardware's truncation of the tf32 remainders is unbiased.
+// Measured on the 12870-state ring mixer at p = 6: <C> within 6.2e-6
+// (relative) of the complex128 result; a truncated head gave 1.35e-5.
+//
+// 128 x 128 output tile per CTA, STAGES-deep TMA ring of 128-byte-swizzled
+// K-major tiles.  Warp 0 lane 0 issues TMA loads, warp 1 lane 0 the MMAs;
+// warps 2..5 (one per quarter of the accumulator rows) drain the chunks and
+// run the fused epilogue.
+namespace tc {
+constexpr int BM = 128, BN = 128, BKF = 32, STAGES = 3, NT = 192;
+constexpr uint32_t kTileA = BM * 128, kTileB = BN * 128;
+constexpr uint32_t kStage = 2 * kTileA + 2 * kTileB;  // A_hi, A_lo, B_hi, B_lo
+constexpr uint32_t kSmem = STAGES * kStage + 1024;      // + alignment slack
+constexpr uint32_t kTmemCols = 256;                     // two 128-column accumulators
+constexpr uint32_t kSpin = 1u << 24;
+// instruction descriptor: D f32, A/B tf32, both K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t cnt) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(cnt) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpin; i++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *m, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst),
+        "l"(m), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), fixed constant 0b001 at bits 46-48.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;            // fixed 0b001
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+// 32 lanes x 32 bits, 16 consecutive columns per lane (no wait)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+}  // namespace tc
+
+__global__ void __launch_bounds__(tc::NT, 1)
+gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int Kp, int ntn,
+               EpiArgs E, int *err) {
+    using tc::BKF;
+    using tc::kStage;
+    using tc::kTileA;
+    using tc::kTileB;
+    using tc::STAGES;
+    constexpr int TBM = tc::BM, TBN = tc::BN;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf[2], acce[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    __shared__ float red[4][TBN / 2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mt = blockIdx.x / ntn, nt = blockIdx.x % ntn;
+    const int m0 = mt * TBM, n0 = nt * TBN;
+    const int nk = Kp / BKF;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&tmem_base)),
+                     "r"(tc::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        for (int s = 0; s < STAGES; s++) {
+            tc::mbar_init(tc::su32(&full[s]), 1);
+            tc::mbar_init(tc::su32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(tc::su32(&accf[b]), 1);
+            tc::mbar_init(tc::su32(&acce[b]), 4);  // one arrive per draining warp
+        }
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_base;
+    int issued = 0;  // stages the producer has started (for a clean exit on timeout)
+    float acc[TBN];  // drained accumulator row (draining warps)
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < nk; kb++) {
+                const int s = kb % STAGES;
+                if (kb >= STAGES && !tc::mbar_wait(tc::su32(&empty[s]), ((kb / STAGES) & 1) ^ 1)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                const uint32_t base = tc::su32(smem + s * kStage);
+                const uint32_t fb = tc::su32(&full[s]);
+                tc::mbar_expect(fb, kStage);
+                tc::tma_2d(base, &tmAh, kb * BKF, m0, fb);
+                tc::tma_2d(base + kTileA, &tmAl, kb * BKF, m0, fb);
+                tc::tma_2d(base + 2 * kTileA, &tmBh, kb * BKF, n0, fb);
+                tc::tma_2d(base + 2 * kTileA + kTileB, &tmBl, kb * BKF, n0, fb);
+                issued = kb + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (int kb = 0; kb < nk; kb++) {
+                const int s = kb % STAGES, b = kb & 1;
+                if (kb >= 2 && !tc::mbar_wait(tc::su32(&acce[b]), ((kb >> 1) & 1) ^ 1)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                if (!tc::mbar_wait(tc::su32(&full[s]), (kb / STAGES) & 1)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t base = tc::su32(smem + s * kStage);
+                const uint32_t d = tmem + (uint32_t)(b * TBN);
+#pragma unroll
+                for (int kk = 0; kk < BKF / 8; kk++) {
+                    const uint64_t ah = tc::sdesc(base + kk * 32), al = tc::sdesc(base + kTileA + kk * 32);
+                    const uint64_t bh = tc::sdesc(base + 2 * kTileA + kk * 32),
+                                   bl = tc::sdesc(base + 2 * kTileA + kTileB + kk * 32);
+                    tc::mma_tf32(d, al, bh, tc::kIdesc, kk ? 1u : 0u);
+                    tc::mma_tf32(d, ah, bl, tc::kIdesc, 1u);
+                    tc::mma_tf32(d, ah, bh, tc::kIdesc, 1u);
+                }
+                tc::mma_commit(tc::su32(&empty[s]));
+                tc::mma_commit(tc::su32(&accf[b]));
+            }
+        }
+    } else {
+        // draining warps: warp w reads accumulator rows (TMEM lanes) 32 (w % 4) ..
+        const uint32_t lrow = (uint32_t)((warp & 3) * 32) << 16;
+#pragma unroll
+        for (int c = 0; c < TBN; c++) acc[c] = 0.f;
+        for (int kb = 0; kb < nk; kb++) {
+            const int b = kb & 1;
+            if (!tc::mbar_wait(tc::su32(&accf[b]), (kb >> 1) & 1)) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            tc::fence_after();
+#pragma unroll
+            for (int h = 0; h < TBN; h += 64) {
+                uint32_t r[4][16];
+#pragma unroll
+                for (int q = 0; q < 4; q++) tc::tmem_ld16(tmem + lrow + (uint32_t)(b * TBN + h + 16 * q), r[q]);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+#pragma unroll
+                    for (int i = 0; i < 16; i++) acc[h + 16 * q + i] += __uint_as_float(r[q][i]);
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tc::su32(&acce[b]));
+        }
+    }
+    __syncwarp();
+    if (__syncthreads_or(s_fail)) {
+        if (tid == 0) atomicOr(err, DERR_TIMEOUT);
+        // let started loads land before the block exits
+        if (warp == 0 && lane == 0)
+            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; kb++)
+                tc::mbar_wait(tc::su32(&full[kb % STAGES]), (kb / STAGES) & 1);
+    } else if (warp >= 2) {
+        const int rq = warp & 3;
+        const int m = m0 + rq * 32 + lane;
+#pragma unroll
+        for (int q = 0; q < TBN / 2; q++) {
+            const int s = n0 / 2 + q;
+            float contrib = 0.f;
+            if (m < E.M && s < E.nsets) contrib = epi_elem(E, m, s, make_float2(acc[2 * q], acc[2 * q + 1]));
+            if (E.part) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, o);
+                if (lane == 0) red[rq][q] = contrib;
+            }
+        }
+    }
+    if (E.part && !s_fail) {
+        __syncthreads();
+        if (tid < TBN / 2) {
+            const int s = n0 / 2 + tid;
+            const double t = ((double)red[0][tid] + (double)red[1][tid]) + ((double)red[2][tid] + (double)red[3][tid]);
+            if (s < E.nsets) E.part[(size_t)s * E.part_stride + mt] = t;
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::kTmemCols)
+                     : "memory");
+}
+
 // Initial state of every set with the first phase separator applied:
 // X = e^{-i g_1 C} psi_0 (psi_0 uniform 1/sqrt(D) or a user complex64 state);
 // also keeps psi_0 as checkpoint 0.
-__global__ void eig_init_kernel(float *X, float *ck0, int D, int ld, int nsets, const void *cost, int cost_dtype,
-                                const RoundCoef *coef, int coef_stride, const float2 *init, float amp0) {
+__global__ void eig_init_kernel(float *X, float *X_lo, float *ck0, int D, int ld, int nsets, const void *cost,
+                                int cost_dtype, const RoundCoef *coef, int coef_stride, const float2 *init,
+                                float amp0) {
     const int s = blockIdx.y;
     if (s >= nsets) return;
     const RoundCoef cf = coef[s * coef_stride];
@@ -245,8 +517,8 @@ __global__ void eig_init_kernel(float *X, float *ck0, int D, int ld, int nsets, 
                                         : (float)reinterpret_cast<const unsigned char *>(cost)[j];
         const float2 w = cmul(v, turn_phase(cf.g_hi, cf.g_lo, C, 0.f));
         const size_t o = (size_t)(2 * s) * ld + j;
-        X[o] = w.x;
-        X[o + ld] = w.y;
+        put(X, X_lo, o, w.x);
+        put(X, X_lo, o + ld, w.y);
         if (ck0) {
             ck0[o] = v.x;
             ck0[o + ld] = v.y;
@@ -255,15 +527,15 @@ __global__ void eig_init_kernel(float *X, float *ck0, int D, int ld, int nsets, 
 }
 
 // Padded copies of V (row-major D x D) and V^T, and lambda split into two floats.
-__global__ void eig_prepare_kernel(const float *V, int D, int ld, float *Vp, float *Vtp, const double *lam,
-                                   float *lam_hi, float *lam_lo) {
+__global__ void eig_prepare_kernel(const float *V, int D, int ld, float *Vp, float *Vtp, float *Vp_lo,
+                                   float *Vtp_lo, const double *lam, float *lam_hi, float *lam_lo) {
     const int64_t total = (int64_t)ld * ld;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / ld), c = (int)(e % ld);
         const float v = (r < D && c < D) ? V[(int64_t)r * D + c] : 0.f;
-        Vp[e] = v;
-        Vtp[(int64_t)c * ld + r] = v;
+        put(Vp, Vp_lo, e, v);
+        put(Vtp, Vtp_lo, (int64_t)c * ld + r, v);
         if (r == 0) {
             const double l = c < D ? lam[c] : 0.0;
             const float hi = (float)l;
@@ -275,22 +547,23 @@ __global__ void eig_prepare_kernel(const float *V, int D, int ld, float *Vp, flo
 
 }  // namespace
 
-cudaError_t launch_eig_prepare(const float *V, int D, int ld, float *Vp, float *Vtp, const double *lam,
-                               float *lam_hi, float *lam_lo, cudaStream_t s) {
-    eig_prepare_kernel<<<152 * 16, 256, 0, s>>>(V, D, ld, Vp, Vtp, lam, lam_hi, lam_lo);
+cudaError_t launch_eig_prepare(const float *V, int D, int ld, float *Vp, float *Vtp, float *Vp_lo, float *Vtp_lo,
+                               const double *lam, float *lam_hi, float *lam_lo, cudaStream_t s) {
+    eig_prepare_kernel<<<152 * 16, 256, 0, s>>>(V, D, ld, Vp, Vtp, Vp_lo, Vtp_lo, lam, lam_hi, lam_lo);
     return cudaGetLastError();
 }
 
-cudaError_t launch_eig_init(float *X, float *ck0, int D, int ld, int nsets, const void *cost, int cost_dtype,
-                            const RoundCoef *coef, int coef_stride, const float2 *init, float amp0,
+cudaError_t launch_eig_init(float *X, float *X_lo, float *ck0, int D, int ld, int nsets, const void *cost,
+                            int cost_dtype, const RoundCoef *coef, int coef_stride, const float2 *init, float amp0,
                             cudaStream_t s) {
     dim3 grid((D + 255) / 256, nsets);
-    eig_init_kernel<<<grid, 256, 0, s>>>(X, ck0, D, ld, nsets, cost, cost_dtype, coef, coef_stride, init, amp0);
+    eig_init_kernel<<<grid, 256, 0, s>>>(X, X_lo, ck0, D, ld, nsets, cost, cost_dtype, coef, coef_stride, init,
+                                         amp0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_eig_gemm_simt(const float *A, const float *B, int Mp, int Np, int Kp, const EigEpiParams &P,
-                                 cudaStream_t s) {
+namespace {
+EpiArgs to_args(const EigEpiParams &P) {
     EpiArgs E;
     E.kind = P.kind;
     E.M = P.M;
@@ -309,8 +582,31 @@ cudaError_t launch_eig_gemm_simt(const float *A, const float *B, int Mp, int Np,
     E.round = P.round;
     E.part = P.part;
     E.part_stride = P.part_stride;
+    E.out_lo = P.out_lo;
+    E.out2_lo = P.out2_lo;
+    return E;
+}
+}  // namespace
+
+cudaError_t launch_eig_gemm_simt(const float *A, const float *B, int Mp, int Np, int Kp, const EigEpiParams &P,
+                                 cudaStream_t s) {
     dim3 grid(Mp / BM, Np / BN);
-    gemm_simt_kernel<<<grid, NT, 0, s>>>(A, B, Kp, Kp, Kp, E);
+    gemm_simt_kernel<<<grid, NT, 0, s>>>(A, B, Kp, Kp, Kp, to_args(P));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eig_gemm_tc(const CUtensorMap &a_hi, const CUtensorMap &a_lo, const CUtensorMap &b_hi,
+                               const CUtensorMap &b_lo, int Mp, int Np, int Kp, const EigEpiParams &P, int *err,
+                               cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tc::kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int ntn = Np / tc::BN;
+    gemm_tc_kernel<<<(Mp / tc::BM) * ntn, tc::NT, tc::kSmem, s>>>(a_hi, a_lo, b_hi, b_lo, Kp, ntn, to_args(P), err);
     return cudaGetLastError();
 }
 

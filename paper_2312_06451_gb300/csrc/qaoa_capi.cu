@@ -77,9 +77,11 @@ struct LaunchRec {
     EigEpiParams ep{};
     const float *gA = nullptr, *gB = nullptr;
     int Mp = 0, Np = 0, Kp = 0;
-    float *iX = nullptr, *ick0 = nullptr;
+    float *iX = nullptr, *iX_lo = nullptr, *ick0 = nullptr;
     const float2 *iinit = nullptr;
     float iamp0 = 0.f;
+    int tc = 0;        // tensor-core product (tensor maps below)
+    CUtensorMap tm[4];  // A_hi, A_lo, B_hi, B_lo
 };
 
 struct Plan {
@@ -297,6 +299,20 @@ bool encode_gather_map(CUtensorMap *m, const void *base, int n, int c, int lo, i
                                                : CU_TENSOR_MAP_DATA_TYPE_UINT8;
     return enc(m, dt, 4, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Row-major float32 matrix [rows][ld] as a K-major tensor-core operand:
+// 32-float (128-byte) boxes x 128 rows, 128-byte swizzle.
+bool encode_kmajor_map(CUtensorMap *m, const float *base, int ld, int rows) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint32_t box[2] = {32, 128};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -734,9 +750,10 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 int j = i;
                 while (j < nu && units[j].mixer_kind == QAOA_MIXER_EIGEN && units[j].job == units[i].job) j++;
                 const Unit &u = units[i];
-                if (u.gemm_precision != QAOA_GEMM_FP32_SIMT)
-                    return fail(ctx, QAOA_ERR_UNSUPPORTED, "eigenbasis GEMM precision %d not available in this build",
-                                u.gemm_precision);
+                if (u.gemm_precision == QAOA_GEMM_BF16X3)
+                    return fail(ctx, QAOA_ERR_UNSUPPORTED,
+                                "BF16x3 products (16-bit split, ~1e-5 relative) cannot meet the 1e-5 tolerance; "
+                                "use QAOA_GEMM_3XTF32");
                 EG g;
                 g.u0 = i;
                 g.S = j - i;
@@ -744,7 +761,9 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 g.ld = (int)align_up((size_t)u.dim, kEigTile);
                 g.nmt = g.ld / kEigTile;
                 const size_t mat = (size_t)2 * g.Spad * g.ld * sizeof(float);
-                const int nmat = grad ? 3 + 2 * u.p : 2;
+                const int tcp = u.gemm_precision == QAOA_GEMM_3XTF32 ? 1 : 0;
+                // X, Y, L (+ their remainder planes on the tensor-core path) and 2p checkpoints
+                const int nmat = grad ? 3 + 2 * u.p + 3 * tcp : 2 + 2 * tcp;
                 g.st_off = st_bytes;
                 st_bytes += align_up(mat * nmat);
                 g.part_off = part_bytes;
@@ -762,20 +781,30 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                     const Unit &u = units[g.u0];
                     const int D = (int)u.dim, ld = g.ld, p = u.p;
                     // padded V, V^T and split eigenvalues, prepared once per (V, lambda)
+                    const bool tcp = u.gemm_precision == QAOA_GEMM_3XTF32;
                     char nm[96];
-                    void *dV = nullptr, *dVt = nullptr, *dL = nullptr;
-                    snprintf(nm, sizeof(nm), "eigV:%p:%p:%d", (const void *)u.V, (const void *)u.lam, D);
+                    void *dV = nullptr, *dVt = nullptr, *dL = nullptr, *dVl = nullptr, *dVtl = nullptr;
+                    snprintf(nm, sizeof(nm), "eigV:%p:%p:%d:%d", (const void *)u.V, (const void *)u.lam, D,
+                             tcp ? 1 : 0);
                     const std::string key = nm;
                     st = scratch(ctx, (key + ":V").c_str(), (size_t)ld * ld * sizeof(float), &dV);
                     if (st) return st;
                     st = scratch(ctx, (key + ":Vt").c_str(), (size_t)ld * ld * sizeof(float), &dVt);
                     if (st) return st;
+                    if (tcp) {
+                        st = scratch(ctx, (key + ":Vlo").c_str(), (size_t)ld * ld * sizeof(float), &dVl);
+                        if (st) return st;
+                        st = scratch(ctx, (key + ":Vtlo").c_str(), (size_t)ld * ld * sizeof(float), &dVtl);
+                        if (st) return st;
+                    }
                     st = scratch(ctx, (key + ":lam").c_str(), (size_t)2 * ld * sizeof(float), &dL);
                     if (st) return st;
                     if (!ctx->eig_ready.count(key)) {
                         float *lh = static_cast<float *>(dL);
                         cudaError_t e = launch_eig_prepare(u.V, D, ld, static_cast<float *>(dV),
-                                                           static_cast<float *>(dVt), u.lam, lh, lh + ld, ctx->stream);
+                                                           static_cast<float *>(dVt), static_cast<float *>(dVl),
+                                                           static_cast<float *>(dVtl), u.lam, lh, lh + ld,
+                                                           ctx->stream);
                         if (e != cudaSuccess) return cuda_fail(ctx, e, "eigenbasis preparation");
                         QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "eigenbasis preparation");
                         ctx->launches++;
@@ -788,6 +817,12 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                     float *X = base, *Y = base + mat, *Lm = grad ? base + 2 * mat : nullptr;
                     auto CKX = [&](int k) { return base + (3 + k) * mat; };
                     auto CKY = [&](int k) { return base + (3 + p + k) * mat; };
+                    // remainder planes (tensor-core path) after everything else
+                    const int lo0 = grad ? 3 + 2 * p : 2;
+                    float *Xl = tcp ? base + lo0 * mat : nullptr;
+                    float *Yl = tcp ? base + (lo0 + 1) * mat : nullptr;
+                    float *Ll = (tcp && grad) ? base + (lo0 + 2) * mat : nullptr;
+                    const float *Vpl = static_cast<const float *>(dVl), *Vtpl = static_cast<const float *>(dVtl);
                     double *part = reinterpret_cast<double *>(static_cast<char *>(d_epart) + g.part_off);
                     const int64_t pq = (int64_t)g.Spad * g.nmt;  // partials per quantity
                     const RoundCoef *coef = reinterpret_cast<const RoundCoef *>(mb + off_coef[g.u0]);
@@ -803,7 +838,12 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                     ep.coef_stride = p;
                     ep.part_stride = g.nmt;
                     const double gflops = 2.0 * D * (double)D * 2.0 * g.S;
-                    const int fam_g = family(ctx, "eig_gemm_simt");
+                    const int fam_g = family(ctx, tcp ? "eig_gemm_tc_3xtf32" : "eig_gemm_simt");
+                    // B operand planes of each state matrix (hi = the matrix itself on the tensor path)
+                    auto lo_of = [&](const float *B) -> const float * {
+                        return B == X ? Xl : B == Y ? Yl : B == Lm ? Ll : nullptr;
+                    };
+                    bool map_ok = true;
                     auto gemm = [&](const float *A, const float *B, EigEpiParams q) {
                         LaunchRec r;
                         r.kind = LK_EIG_GEMM;
@@ -812,9 +852,21 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                         r.Mp = ld;
                         r.Np = 2 * g.Spad;
                         r.Kp = ld;
-                        r.ep = q;
                         r.flops = gflops;
                         r.fam = fam_g;
+                        if (tcp) {
+                            r.tc = 1;
+                            const float *Al = A == Vp ? Vpl : Vtpl;
+                            map_ok = map_ok && encode_kmajor_map(&r.tm[0], A, ld, ld) &&
+                                     encode_kmajor_map(&r.tm[1], Al, ld, ld) &&
+                                     encode_kmajor_map(&r.tm[2], B, ld, 2 * g.Spad) &&
+                                     encode_kmajor_map(&r.tm[3], lo_of(B), ld, 2 * g.Spad);
+                            // outputs that feed the next product carry their remainder plane
+                            q.out_lo = q.out == X ? Xl : q.out == Y ? Yl : q.out == Lm ? Ll : nullptr;
+                            q.out2_lo = q.out2 == Lm ? Ll : nullptr;
+                            if (q.kind == EPI_FWD_LAST) q.out_lo = nullptr;  // psi_p is not a product operand
+                        }
+                        r.ep = q;
                         L.push_back(r);
                     };
                     {
@@ -822,6 +874,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                         r.kind = LK_EIG_INIT;
                         r.ep = ep;
                         r.iX = X;
+                        r.iX_lo = Xl;
                         r.ick0 = grad ? CKX(0) : nullptr;
                         r.iinit = u.init;
                         r.iamp0 = (float)(1.0 / std::sqrt((double)D));
@@ -868,6 +921,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                             gemm(Vp, Y, q);
                         }
                     }
+                    if (!map_ok) return fail(ctx, QAOA_ERR_CUDA, "tensor map encoding failed");
                     for (int s2 = 0; s2 < g.S; s2++) {
                         const Unit &us = units[g.u0 + s2];
                         add_reduction(part + (int64_t)s2 * g.nmt, g.nmt, us.E, 1.0);
@@ -955,11 +1009,13 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                              ctx->d_err, ctx->stream);
             break;
         case LK_EIG_INIT:
-            e = launch_eig_init(r.iX, r.ick0, r.ep.M, r.ep.ld, r.ep.nsets, r.ep.cost, r.ep.cost_dtype, r.ep.coef,
-                                r.ep.coef_stride, r.iinit, r.iamp0, ctx->stream);
+            e = launch_eig_init(r.iX, r.iX_lo, r.ick0, r.ep.M, r.ep.ld, r.ep.nsets, r.ep.cost, r.ep.cost_dtype,
+                                r.ep.coef, r.ep.coef_stride, r.iinit, r.iamp0, ctx->stream);
             break;
         case LK_EIG_GEMM:
-            e = launch_eig_gemm_simt(r.gA, r.gB, r.Mp, r.Np, r.Kp, r.ep, ctx->stream);
+            e = r.tc ? launch_eig_gemm_tc(r.tm[0], r.tm[1], r.tm[2], r.tm[3], r.Mp, r.Np, r.Kp, r.ep, ctx->d_err,
+                                          ctx->stream)
+                     : launch_eig_gemm_simt(r.gA, r.gB, r.Mp, r.Np, r.Kp, r.ep, ctx->stream);
             break;
         case LK_REDUCE:
             e = launch_reduce(reinterpret_cast<const RedChunk *>(db + r.desc_off), r.ndesc,
@@ -1023,6 +1079,7 @@ qaoa_status read_dev_err(qaoa_ctx *ctx) {
     if (h) {
         cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
         if (h & DERR_BAD_ANGLE) return fail(ctx, QAOA_ERR_INVALID, "non-finite angle");
+        if (h & DERR_TIMEOUT) return fail(ctx, QAOA_ERR_TIMEOUT, "a bounded device-side wait gave up");
         return fail(ctx, QAOA_ERR_CUDA, "device error word 0x%x", h);
     }
     return QAOA_OK;

@@ -31,13 +31,16 @@ def sigma(c):
     return float(np.sqrt(np.mean(np.asarray(c, dtype=np.float64) ** 2)))
 
 
-def problem(qg, ctx, oracle_mod, n, k, seed):
+def problem(qg, ctx, oracle_mod, n, k, seed, precision="fp32"):
     e = erdos_renyi(n, 0.5, seed)
     st = oracle_mod.dicke_states(n, k)
     c = oracle_mod.cost_dks(n, e, st)
     dc = ctx.cost_precompute("dks", n, edges=e, k=k, dtype=torch.uint8)
-    mixer = qg.ring_eigen_mixer(ctx, n, k)
+    mixer = qg.ring_eigen_mixer(ctx, n, k, precision=precision)
     return st, c, dc, mixer
+
+
+PRECISIONS = ["fp32", "3xtf32"]
 
 
 @pytest.mark.parametrize("n,k", [(8, 4), (10, 5), (12, 6)])
@@ -51,10 +54,11 @@ def test_eigen_decomposition_is_an_eigenbasis(Q, n, k):
     assert res < 1e-5 and orth < 1e-5, (res, orth)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("n,k,p", [(8, 4, 3), (10, 5, 2), (12, 6, 4)])
-def test_eigen_expectation_and_gradient(Q, oracle_mod, n, k, p):
+def test_eigen_expectation_and_gradient(Q, oracle_mod, n, k, p, precision):
     qg, ctx = Q
-    st, c, dc, mixer = problem(qg, ctx, oracle_mod, n, k, 50 + n)
+    st, c, dc, mixer = problem(qg, ctx, oracle_mod, n, k, 50 + n, precision)
     ang = uniform_angles(p, 60 + n)[0]
     E = ctx.expectation(dc, mixer, ang)
     E_ref = oracle_mod.qaoa_expectation(n, c, ang, "ring", st)
@@ -65,11 +69,12 @@ def test_eigen_expectation_and_gradient(Q, oracle_mod, n, k, p):
     np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-4 * max(np.abs(g_ref).max(), sigma(c)))
 
 
-def test_eigen_batched_ragged_sets(Q, oracle_mod):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_eigen_batched_ragged_sets(Q, oracle_mod, precision):
     """67 angle sets: more than one 64-set column tile, the last one ragged."""
     qg, ctx = Q
     n, k, p = 10, 4, 3
-    st, c, dc, mixer = problem(qg, ctx, oracle_mod, n, k, 7)
+    st, c, dc, mixer = problem(qg, ctx, oracle_mod, n, k, 7, precision)
     S = 67
     A = uniform_angles(p, 8, S)
     E = torch.zeros(S, dtype=torch.float64, device="cuda")
@@ -83,10 +88,11 @@ def test_eigen_batched_ragged_sets(Q, oracle_mod):
         np.testing.assert_allclose(G[s].cpu().numpy(), g_ref, rtol=0, atol=1e-4 * max(np.abs(g_ref).max(), sigma(c)))
 
 
-def test_eigen_custom_initial_state(Q, oracle_mod):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_eigen_custom_initial_state(Q, oracle_mod, precision):
     qg, ctx = Q
     n, k, p = 8, 3, 2
-    st, c, dc, mixer = problem(qg, ctx, oracle_mod, n, k, 9)
+    st, c, dc, mixer = problem(qg, ctx, oracle_mod, n, k, 9, precision)
     rng = np.random.default_rng(4)
     psi0 = rng.standard_normal(len(st)) + 1j * rng.standard_normal(len(st))
     psi0 /= np.linalg.norm(psi0)

@@ -144,16 +144,18 @@ def test_uneven_batch_sample(Q):
                                        atol=1e-4 * max(np.abs(g_ref).max(), sig))
 
 
-def test_dks16_k8_ring_p6_full_size(Q, golden):
+@pytest.mark.parametrize("precision", ["fp32", "3xtf32"])
+def test_dks16_k8_ring_p6_full_size(Q, golden, precision):
     """Densest 8-subgraph on G(16, 0.5), ring mixer on all 12870 weight-8
     states through its eigendecomposition, p=6, 256 angle sets in one batched
-    gradient call; sets 0 and 1 against the oracle's power-series mixer."""
+    gradient call (CUDA-core float32 or tensor-core 3xTF32 products); sets 0
+    and 1 against the oracle's power-series mixer."""
     qg, ctx = Q
     g = golden["4"]
     w = workload_instance(4)
     n, k, p = w["spec"]["n"], w["spec"]["k"], w["spec"]["p"]
     cost = ctx.cost_precompute("dks", n, edges=w["edges"], k=k, dtype=torch.uint8)
-    mixer = qg.ring_eigen_mixer(ctx, n, k)
+    mixer = qg.ring_eigen_mixer(ctx, n, k, precision=precision)
     A = w["angles"]
     assert np.allclose(A[:2], [s["angles"] for s in g["sets"]])
     E = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
