@@ -142,16 +142,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(family: str):
-    """ncu DRAM bytes per launch of a kernel family, if the committed capture
-    was taken on the current kernel source (else None)."""
+def traffic_for(family: str, workload: str):
+    """ncu DRAM bytes per launch of a kernel family on this workload, if the
+    committed capture was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
     ent = d.get(family)
-    if not ent:
+    if not isinstance(ent, dict) or ent.get("workload") != workload:
         return None
     import hashlib
 
@@ -470,7 +470,7 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
         achieved = st["algo_flops"] / (st["total_ms"] * 1e-3) / 1e12
         pk = gemm_peak(args.gemm)
         roof = {"bound": pk["bound"], "kernel": fam, "achieved": achieved, "peak": pk["peak"], "unit": "TFLOP/s",
-                "frac": achieved / pk["peak"], "peak_source": pk["source"], "traffic": traffic_for(fam),
+                "frac": achieved / pk["peak"], "peak_source": pk["source"], "traffic": traffic_for(fam, W.name),
                 "algo_flops_per_launch": st["algo_flops"] / st["launches"],
                 "launch_ms": st["total_ms"] / st["launches"]}
     elif fams:
@@ -481,7 +481,7 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
         achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": fam, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
-                "traffic": traffic_for(fam), "algo_bytes_per_launch": per_launch_bytes,
+                "traffic": traffic_for(fam, W.name), "algo_bytes_per_launch": per_launch_bytes,
                 "launch_ms": per_launch_ms}
     unit = UNIT if W.grad else "evals/s"
     out = None

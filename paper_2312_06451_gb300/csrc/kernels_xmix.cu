@@ -14,7 +14,8 @@
 //     of a tile set covers qubits 0..T-1 with fully contiguous tiles; later
 //     passes gather 2^c contiguous amplitudes (c >= 4: whole 128-byte lines)
 //     times 2^(T-c) strided ones to reach the high qubits.
-//   * Each thread holds 32 amplitudes in registers.  A tile goes through three
+//   * Each thread holds 16 amplitudes of each vector in registers (a tile of
+//     2^12 amplitudes, 256 threads).  A tile goes through three
 //     register layouts ("stages"): the first is the coalesced 16-byte load
 //     layout, the third the coalesced store layout; two shared-memory
 //     transposes (XOR-swizzled, bank-conflict free) move between them.  Every
