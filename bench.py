@@ -11,8 +11,8 @@ between steps.
 
 Prints one JSON line (rank 0).  `value` is measured on the device with CUDA
 events around K steps of the batched entry point (device-resident angles and
-results).  `e2e` times the host-pointer entry point qaoa_gradient (angles
-uploaded from pinned host memory, <C> and the gradient read back every step).
+results).  `e2e` times the same batched call end to end: angles copied in from pinned
+host memory and <C> and the gradients read back to the host, every step.
 `roofline` divides the dominant kernel's algorithmic bytes by its CUDA-event
 time inside the timed region.  `cpu_baseline` times the CPU oracle on the host
 cores on one round of the same workload (scaled to the p-round unit).
@@ -79,6 +79,29 @@ def gemm_peak(gemm: str):
             bf16 = float(json.load(f)["bf16_tflops"])
         src = "measured"
     return {"bound": "tensor", "peak": bf16 * 1.1 / 2.25, "source": f"{src} bf16 burst x 1.1/2.25 (tf32)"}
+
+
+def reducers(dist, device):
+    """Max and sum over ranks of a host scalar (identity without a process
+    group).  `device` is where the one-element tensor lives: the rank's GPU
+    under NCCL, "cpu" under gloo."""
+    import torch
+
+    def rmax(v):
+        if not dist:
+            return v
+        t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    def rsum(v):
+        if not dist:
+            return v
+        t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return int(round(t.item()))
+
+    return rmax, rsum
 
 
 def aggregate(local_seconds: float, local_units: int, world: int, reduce_max=None, reduce_sum=None):
@@ -429,20 +452,7 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     stats = ctx.kernel_stats()
     clk = clocks.stop()
 
-    def rmax(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
-
-    def rsum(v):
-        if not dist:
-            return v
-        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return int(t.item())
-
+    rmax, rsum = reducers(dist, dev)
     value, tmax, units = aggregate(ms / 1e3, args.steps * W.units, ws, rmax, rsum)
     E_last = float(W.jobs[0]["E"][0].item())
 
@@ -460,6 +470,10 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     torch.cuda.synchronize()
     e2e_s = rmax(time.perf_counter() - t0)
     e2e_value = rsum(args.steps * W.units) / e2e_s
+
+    fd = None
+    if W.grad and ws == 1 and not args.no_fd:
+        fd = fd_compare(W, stream, value)
 
     peaks = measured_peaks()
     roof = None
@@ -505,6 +519,8 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
             "clocks": clk,
             "result_check": {"E_first_set_last_step": E_last, "e2e_E0": float(outs[0][0])},
         }
+        if fd is not None:
+            out["fd_baseline"] = fd
         if ws == 1 and not args.no_cpu_baseline:
             v, cores, desc = W.oracle_baseline()
             out["cpu_baseline"] = {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": desc}
@@ -513,6 +529,48 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def fd_compare(W, stream, adjoint_value, h=1e-3, reps=3, max_jobs=8):
+    """The plain finite-difference gradient on the same GPU, for comparison
+    with the adjoint: per angle set, 4p forward <C> evaluations at
+    theta +- h e_j (central differences), issued as one batched forward call
+    per sampled set (the fastest way to run them).  Returns its throughput,
+    the adjoint/FD ratio and the largest difference from the adjoint gradient
+    of the same angles (relative to the gradient's largest component)."""
+    import torch
+
+    jobs, ref = [], []
+    for job in W.jobs[:max_jobs]:
+        a = job["angles"][0].detach().cpu().numpy().astype(np.float64)
+        g = job["grad"][0].detach().cpu().numpy().astype(np.float64)
+        m = a.shape[0]
+        A = np.repeat(a[None, :], 2 * m, axis=0)
+        for j in range(m):
+            A[2 * j, j] += h
+            A[2 * j + 1, j] -= h
+        jobs.append({"cost": job["cost"], "mixer": job["mixer"], "angles": torch.from_numpy(A).to(W.dev),
+                     "E": torch.zeros(2 * m, dtype=torch.float64, device=W.dev)})
+        ref.append(g)
+    W.ctx.expectation_batched(jobs, want_grad=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        W.ctx.expectation_batched(jobs, want_grad=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    rate = len(jobs) / t
+    err = 0.0
+    for jb, g in zip(jobs, ref):
+        E = jb["E"].cpu().numpy()
+        gfd = (E[0::2] - E[1::2]) / (2 * h)
+        err = max(err, float(np.max(np.abs(gfd - g)) / max(np.max(np.abs(g)), 1e-300)))
+    return {"value": rate, "unit": "grad/s", "adjoint_over_fd": adjoint_value / rate,
+            "method": f"central differences h={h}: 4p forward <C> per gradient, complex64 state",
+            "sample": f"{len(jobs)} angle set(s) (first set of the first {len(jobs)} job(s)), {reps} timed calls",
+            "max_abs_diff_vs_adjoint_rel": err}
 
 
 def main():
@@ -531,6 +589,8 @@ def main():
     ap.add_argument("--gemm", default="3xtf32", choices=["fp32", "3xtf32"],
                     help="eigenbasis product precision (workload 4): tcgen05 3xTF32 or CUDA-core float32")
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
+    ap.add_argument("--no-fd", action="store_true",
+                    help="skip the central finite-difference comparison on the same GPU")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.warmup < 3:

@@ -71,6 +71,18 @@ def test_sk28_p8_gradient_full_size(Q, golden):
     # expectation alone
     E3 = ctx.expectation(cost, qg.XMixer(n), np.array(g["angles"]))
     assert abs(E3 - g["E"]) <= 1e-5 * max(abs(g["E"]), sig)
+    # central finite differences (h = 1e-3) of the GPU's own forward <C> for
+    # beta_1 and gamma_p: the O(h^2) truncation (about h^2 sigma_C^2 / 6 for a
+    # gamma) and the complex64 rounding of <C> divided by 2h bound the gap
+    h = 1e-3
+    a = np.array(g["angles"])
+    for j in (0, len(a) - 1):
+        A = np.repeat(a[None, :], 2, axis=0)
+        A[0, j] += h
+        A[1, j] -= h
+        Ef, _ = batched_grad(qg, ctx, cost, n, A, want_grad=False)
+        fd = (Ef[0] - Ef[1]) / (2 * h)
+        assert abs(fd - G[0][j]) <= 2e-3 * max(np.abs(g["grad"]).max(), sig), (j, fd, G[0][j], g["grad"][j])
 
 
 def test_maxcut_3reg24_p10_batched(Q, golden):
