@@ -287,7 +287,24 @@ class Workload:
             self.config["l2"] = (f"state {2 ** n * 8 / 2 ** 30:.2f} GiB per set vs 129 MB L2; no flush"
                                  if n >= 24 else "on-chip state (whole state in shared memory)")
         self.config["state"] = "complex64"
-        self.config["ckpt"] = "per-round state checkpoints" if self.grad else "none (forward only)"
+        if not self.grad:
+            self.config["ckpt"] = "none (forward only)"
+        elif idx == 4:
+            self.config["ckpt"] = "per-round state checkpoints"
+        else:
+            self.config["ckpt"] = "per-pass state checkpoints (the adjoint writes lambda only)"
+
+    def autotune(self):
+        """Pick the pass schedule of every X-mixer problem size in the workload
+        (untimed, before the warm-up); returns {n: schedule}."""
+        out = {}
+        for job in self.jobs:
+            n = job["mixer"].n
+            if not isinstance(job["mixer"], self.qg.XMixer) or n <= 12 or n in out:
+                continue
+            t = self.ctx.autotune(job["cost"], n, p=2, want_grad=self.grad)
+            out[n] = {k: t[k] for k in ("cmin", "split", "nbuf_bwd_contig", "nbuf_bwd_gather")}
+        return out
 
     def _add_job(self, cost, n, A, n_sets):
         import torch
@@ -406,6 +423,10 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
 
     ctx = qg.Context(local, stream)
     W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n, args.gemm)
+    if not args.no_autotune:
+        sched = W.autotune()
+        if sched:
+            W.config["schedule"] = sched if len(sched) > 1 else next(iter(sched.values()))
 
     graph = None
     if args.graph:
@@ -589,6 +610,8 @@ def main():
     ap.add_argument("--gemm", default="3xtf32", choices=["fp32", "3xtf32"],
                     help="eigenbasis product precision (workload 4): tcgen05 3xTF32 or CUDA-core float32")
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default X-mixer pass schedule instead of tuning it before the warm-up")
     ap.add_argument("--no-fd", action="store_true",
                     help="skip the central finite-difference comparison on the same GPU")
     args = ap.parse_args()

@@ -187,12 +187,19 @@ qaoa_status qaoa_expectation(qaoa_ctx *ctx, const void *d_cost, int cost_dtype,
                              const qaoa_mixer *mixer, const void *d_init, int p,
                              const double *angles, double *E);
 
+/* How the adjoint sweep gets back the forward states it needs. */
+enum {
+    QAOA_CKPT_NONE = 0,  /* undo each round on psi as well (2 state vectors) */
+    QAOA_CKPT_ROUND = 1, /* keep the state at every round boundary (p + 1 vectors) */
+    QAOA_CKPT_PASS = 2   /* keep the output of every forward pass (X mixer: about
+                            p * ceil(n / 12) + 1 vectors); the adjoint then writes
+                            only lambda.  Eigenbasis mixers treat it as ROUND. */
+};
+
 /* <C> and its 2p partial derivatives by one forward and one adjoint
  * (reverse) sweep (Sec. 2.3, Sec. 4: the gradient for a constant multiple of
  * one evaluation).  grad: host output, 2p float64 in the angle order.
- *   ckpt  1 = keep the state at every round boundary in scratch and reload it
- *         in the adjoint sweep; 0 = recover earlier states by undoing each
- *         round (less memory, one more state write per round). */
+ *   ckpt  one of QAOA_CKPT_* (any other value is QAOA_ERR_INVALID). */
 qaoa_status qaoa_gradient(qaoa_ctx *ctx, const void *d_cost, int cost_dtype,
                           const qaoa_mixer *mixer, const void *d_init, int p,
                           const double *angles, double *E, double *grad, int ckpt);
@@ -223,6 +230,54 @@ typedef struct {
  * before launching anything when the scratch would not fit. */
 qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *jobs,
                                      int want_grad);
+
+/* Checkpointing used by qaoa_expectation_batched gradients (default
+ * QAOA_CKPT_PASS).  Per unit the planner steps down PASS -> ROUND -> NONE
+ * when one angle set's scratch would not fit in free device memory. */
+qaoa_status qaoa_set_checkpointing(qaoa_ctx *ctx, int mode);
+
+/* ------------------------------------------ X-mixer pass schedule tuning */
+
+/* Schedule of the transverse-field mixer passes for one qubit count and cost
+ * dtype.  Every pass applies the rotations of 12 qubits (Sec. 2.2: the mixer
+ * is a sequence of single-qubit operations, so any grouping gives the same
+ * state): qubits 0..11 in contiguous tiles, then the higher qubits in chunks,
+ * each gathered from runs of 2^c contiguous amplitudes, c = 12 - chunk >= cmin.
+ *   cmin    4..8 (shortest run 2^cmin amplitudes; 4 = one 128-byte line)
+ *   split   0 equal chunks, 1 full chunks first, 2 remainder first
+ *   nbuf_bwd_contig / nbuf_bwd_gather  1 or 2 tile buffers per CTA in the
+ *           adjoint passes (1: two CTAs per SM; 2: one CTA per SM)
+ *   ms      time of the tuning run that chose it (output only)
+ * The schedule changes the rounding order only. */
+typedef struct {
+    int n;
+    int cost_dtype;
+    int cmin;
+    int split;
+    int nbuf_bwd_contig;
+    int nbuf_bwd_gather;
+    double ms;
+} qaoa_xtune;
+
+/* The pass groups a schedule gives (host-only; touches no device).  Writes up
+ * to max (c, lo) pairs: pass j keeps qubits 0..c_j-1 contiguous and gathers
+ * qubits lo_j..lo_j+11-c_j.  Returns the pass count, or -1 for n outside
+ * 13..32, cmin outside 4..8 or split outside 0..2. */
+int qaoa_pass_schedule(int n, int cmin, int split, int *c, int *lo, int max);
+
+/* Autotuner: times forward (+ adjoint when want_grad) sweeps of p rounds
+ * (1..8) on the caller's cost vector for every schedule with the fewest
+ * passes, then the adjoint buffer choices, on the context stream, and keeps
+ * the fastest for (n, cost_dtype) in the context; out (may be NULL) receives
+ * it.  Angles are fixed internal values; results of the runs are discarded.
+ * Synchronous.  Uses the context's scratch like a gradient call of p rounds. */
+qaoa_status qaoa_autotune_x(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, int n, int p,
+                            int want_grad, qaoa_xtune *out);
+/* Set (e.g. restore a saved tuning) or read the schedule used for
+ * (t->n, t->cost_dtype).  Without a stored entry the default is cmin 4,
+ * split 0, one adjoint buffer. */
+qaoa_status qaoa_set_xtune(qaoa_ctx *ctx, const qaoa_xtune *t);
+qaoa_status qaoa_get_xtune(qaoa_ctx *ctx, int n, int cost_dtype, qaoa_xtune *out);
 
 /* ------------------------------------------------ allocation-free variant */
 

@@ -22,7 +22,7 @@ import torch
 from . import _binding as B
 from ._binding import QAOAError  # noqa: F401
 
-__all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError",
+__all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError", "pass_schedule",
            "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched",
            "qaoa_gradient_small_noalloc", "ring_eigen_mixer", "save_eigen_mixer", "load_eigen_mixer"]
 
@@ -221,8 +221,9 @@ class Context:
         return E.value
 
     def gradient(self, cost: torch.Tensor, mixer, angles, init: torch.Tensor | None = None,
-                 ckpt: bool = True):
-        """(<C>, d<C>/d angles) for one angle set (qaoa_gradient)."""
+                 ckpt=True):
+        """(<C>, d<C>/d angles) for one angle set (qaoa_gradient).  ckpt:
+        False / "none", True / "round" or "pass" (QAOA_CKPT_*)."""
         cost = _dev_tensor(cost, "cost")
         init = _dev_tensor(init, "init")
         a = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).ravel())
@@ -231,8 +232,33 @@ class Context:
         self._check(self._lib.qaoa_gradient(self._h, _ptr(cost), _cost_dtype(cost), ctypes.byref(mixer.struct),
                                             _ptr(init), a.shape[0] // 2, a.ctypes.data_as(ctypes.c_void_p),
                                             ctypes.byref(E), g.ctypes.data_as(ctypes.c_void_p),
-                                            1 if ckpt else 0))
+                                            _ckpt_mode(ckpt)))
         return E.value, g
+
+    def set_checkpointing(self, mode):
+        """Checkpointing of batched gradients: "none", "round" or "pass" (default)."""
+        self._check(self._lib.qaoa_set_checkpointing(self._h, _ckpt_mode(mode)))
+
+    # ------------------------------------------------ pass-schedule tuning
+    def autotune(self, cost: torch.Tensor, n: int, p: int = 2, want_grad: bool = True) -> dict:
+        """Time every X-mixer pass schedule for (n, cost dtype) on this cost
+        vector and keep the fastest in the context (qaoa_autotune_x)."""
+        cost = _dev_tensor(cost, "cost")
+        t = B.QaoaXTune()
+        self._check(self._lib.qaoa_autotune_x(self._h, _ptr(cost), _cost_dtype(cost), n, p, 1 if want_grad else 0,
+                                              ctypes.byref(t)))
+        return _xtune_dict(t)
+
+    def set_tuning(self, t: dict):
+        """Install a schedule (e.g. one saved from autotune())."""
+        st = B.QaoaXTune(*(int(t[k]) for k in ("n", "cost_dtype", "cmin", "split", "nbuf_bwd_contig",
+                                               "nbuf_bwd_gather")), float(t.get("ms", 0.0)))
+        self._check(self._lib.qaoa_set_xtune(self._h, ctypes.byref(st)))
+
+    def get_tuning(self, n: int, cost_dtype: int) -> dict:
+        t = B.QaoaXTune()
+        self._check(self._lib.qaoa_get_xtune(self._h, n, cost_dtype, ctypes.byref(t)))
+        return _xtune_dict(t)
 
     def expectation_batched(self, jobs, want_grad: bool = False):
         """Enqueue many angle sets / instances (qaoa_expectation_batched).
@@ -280,6 +306,32 @@ class Context:
 
     def scratch_bytes(self) -> int:
         return int(self._lib.qaoa_scratch_bytes(self._h))
+
+
+def _ckpt_mode(m) -> int:
+    names = {"none": B.QAOA_CKPT_NONE, "round": B.QAOA_CKPT_ROUND, "pass": B.QAOA_CKPT_PASS}
+    if isinstance(m, str):
+        return names[m]
+    if isinstance(m, bool):
+        return B.QAOA_CKPT_ROUND if m else B.QAOA_CKPT_NONE
+    return int(m)
+
+
+def _xtune_dict(t) -> dict:
+    return {k: getattr(t, k) for k in ("n", "cost_dtype", "cmin", "split", "nbuf_bwd_contig", "nbuf_bwd_gather",
+                                       "ms")}
+
+
+def pass_schedule(n: int, cmin: int = 4, split: int = 0):
+    """[(c, lo), ...]: the X-mixer passes of one round (qaoa_pass_schedule;
+    host only, needs no GPU)."""
+    lib = B.load()
+    c = (ctypes.c_int * 16)()
+    lo = (ctypes.c_int * 16)()
+    k = lib.qaoa_pass_schedule(n, cmin, split, c, lo, 16)
+    if k < 0:
+        raise ValueError(f"no schedule for n={n}, cmin={cmin}, split={split}")
+    return [(c[j], lo[j]) for j in range(k)]
 
 
 # Module-level aliases with the C names.

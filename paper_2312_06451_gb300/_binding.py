@@ -23,6 +23,7 @@ QAOA_COST_F32, QAOA_COST_U8 = 0, 1
 QAOA_PROBLEM_MAXCUT, QAOA_PROBLEM_WMAXCUT, QAOA_PROBLEM_SK, QAOA_PROBLEM_DKS = 0, 1, 2, 3
 QAOA_MIXER_X, QAOA_MIXER_EIGEN = 0, 1
 QAOA_GEMM_FP32_SIMT, QAOA_GEMM_3XTF32, QAOA_GEMM_BF16X3 = 0, 1, 2
+QAOA_CKPT_NONE, QAOA_CKPT_ROUND, QAOA_CKPT_PASS = 0, 1, 2
 
 
 class QaoaProblem(ctypes.Structure):
@@ -39,6 +40,11 @@ class QaoaJob(ctypes.Structure):
     _fields_ = [("d_cost", c_void_p), ("cost_dtype", c_int), ("mixer", ctypes.POINTER(QaoaMixer)),
                 ("p", c_int), ("n_sets", c_int), ("d_angles", c_void_p), ("d_E", c_void_p),
                 ("d_grad", c_void_p), ("d_init", c_void_p)]
+
+
+class QaoaXTune(ctypes.Structure):
+    _fields_ = [("n", c_int), ("cost_dtype", c_int), ("cmin", c_int), ("split", c_int),
+                ("nbuf_bwd_contig", c_int), ("nbuf_bwd_gather", c_int), ("ms", c_double)]
 
 
 class QaoaKernelStat(ctypes.Structure):
@@ -66,6 +72,11 @@ SIGNATURES = {
     "qaoa_launch_count": (c_int64, [c_void_p]),
     "qaoa_gradient_small_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                             c_void_p]),
+    "qaoa_set_checkpointing": (c_int, [c_void_p, c_int]),
+    "qaoa_pass_schedule": (c_int, [c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int]),
+    "qaoa_autotune_x": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, ctypes.POINTER(QaoaXTune)]),
+    "qaoa_set_xtune": (c_int, [c_void_p, ctypes.POINTER(QaoaXTune)]),
+    "qaoa_get_xtune": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(QaoaXTune)]),
 }
 
 _lock = threading.Lock()

@@ -188,7 +188,7 @@ cudaError_t launch_reduce(const RedChunk *d_chunks, int nchunks, double *d_level
 cudaError_t launch_small(const SmallDesc *d_descs, int ndesc, int cost_dtype, int want_grad,
                          int max_n, int *d_err, cudaStream_t s);
 // bwd: 0 forward, 1 adjoint.  Persistent launch over total_tiles tiles.
-cudaError_t launch_xpass(int bwd, int cost_dtype, const PassDesc *d_descs,
+cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, const PassDesc *d_descs,
                          const uint32_t *d_tile_begin, int ndesc, uint32_t total_tiles,
                          int *d_err, cudaStream_t s);
 int small_max_n();

@@ -132,17 +132,41 @@ __device__ __forceinline__ float pair_dot(const float2 (&l)[16], const float2 (&
     return (sp.x + sp.y) - (sm.x + sm.y);
 }
 
-// One rotation step on register bit RB if its qubit is active.
-template <int RB, int BWD, int MODE>
-__device__ __forceinline__ void rot_step(float2 (&a)[16], float2 (&l)[16], bool on, const Rot &R,
-                                         float &pscale, float &bacc) {
-    if (!on) return;
+// The rotations of one register layout ("stage"): on bit k = register bit k
+// carries an active qubit.  The adjoint first takes the pair terms
+// <lambda|X_q|psi> of all the stage's qubits at the stage's starting point --
+// any point of the round where both vectors have had the same rotations
+// gives the same value, because all X_q commute -- and then rotates lambda,
+// and psi only when rot_psi is set (its later values are not always needed).
+template <int BWD, int MODE>
+__device__ __forceinline__ void stage_rot(float2 (&a)[16], float2 (&l)[16], uint32_t on, const Rot &R,
+                                          float &pscale, float &bacc, bool rot_psi) {
     if (BWD) {
-        bacc = fmaf(pair_dot<RB>(l, a), pscale, bacc);
-        pscale *= R.psc;
-        rot_pairs<RB, MODE>(l, R);
+        float s = 0.f;
+        if (on & 1u) s += pair_dot<0>(l, a);
+        if (on & 2u) s += pair_dot<1>(l, a);
+        if (on & 4u) s += pair_dot<2>(l, a);
+        if (on & 8u) s += pair_dot<3>(l, a);
+        bacc = fmaf(s, pscale, bacc);
+        for (uint32_t m = on; m; m &= m - 1u) pscale *= R.psc;
+        if (on & 1u) rot_pairs<0, MODE>(l, R);
+        if (on & 2u) rot_pairs<1, MODE>(l, R);
+        if (on & 4u) rot_pairs<2, MODE>(l, R);
+        if (on & 8u) rot_pairs<3, MODE>(l, R);
     }
-    rot_pairs<RB, MODE>(a, R);
+    if (!BWD || rot_psi) {
+        if (on & 1u) rot_pairs<0, MODE>(a, R);
+        if (on & 2u) rot_pairs<1, MODE>(a, R);
+        if (on & 4u) rot_pairs<2, MODE>(a, R);
+        if (on & 8u) rot_pairs<3, MODE>(a, R);
+    }
+}
+
+// Register bits of the stage whose local bits are b0..b3, from the pass's
+// active-qubit mask.
+__device__ __forceinline__ uint32_t stage_mask(uint32_t active, int b0, int b1, int b2, int b3) {
+    return ((active >> b0) & 1u) | (((active >> b1) & 1u) << 1) | (((active >> b2) & 1u) << 2) |
+           (((active >> b3) & 1u) << 3);
 }
 
 template <int BWD>
@@ -290,6 +314,7 @@ struct PassGeom {
     static constexpr uint32_t kPsiB = kTile * 8;
     static constexpr uint32_t kCostB = kTile * (COST == 0 ? 4 : 1);
     static constexpr uint32_t kBufB = kPsiB * (BWD ? 2 : 1) + kCostB;
+    static constexpr uint32_t kStashB = (BWD && COST == 0) ? kTile * 4 : 0;  // after the buffers
     static constexpr uint32_t kHead = 256 + kPhaseTable * 8;  // barriers, tile info, phase table
 };
 
@@ -467,10 +492,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
             }
         }
     }
-    rot_step<0, BWD, MODE>(a, l, active & (1u << 0), K.R, pscale, bacc);
-    rot_step<1, BWD, MODE>(a, l, active & (1u << 9), K.R, pscale, bacc);
-    rot_step<2, BWD, MODE>(a, l, active & (1u << 10), K.R, pscale, bacc);
-    rot_step<3, BWD, MODE>(a, l, active & (1u << 11), K.R, pscale, bacc);
+    stage_rot<BWD, MODE>(a, l, stage_mask(active, 0, 9, 10, 11), K.R, pscale, bacc, true);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs1);
         pscale = 1.f;
@@ -491,10 +513,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
         a[i] = sp[p2 ^ ((uint32_t)i << 1)];
         if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
     }
-    rot_step<0, BWD, MODE>(a, l, active & (1u << 1), K.R, pscale, bacc);
-    rot_step<1, BWD, MODE>(a, l, active & (1u << 2), K.R, pscale, bacc);
-    rot_step<2, BWD, MODE>(a, l, active & (1u << 3), K.R, pscale, bacc);
-    rot_step<3, BWD, MODE>(a, l, active & (1u << 4), K.R, pscale, bacc);
+    stage_rot<BWD, MODE>(a, l, stage_mask(active, 1, 2, 3, 4), K.R, pscale, bacc, true);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs2);
         pscale = 1.f;
@@ -514,25 +533,48 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
         a[i] = sp[idx];
         if (BWD) l[i] = sl[idx];
     }
+    // Cost values of this thread's stage-3 amplitudes, read before the buffer
+    // goes back to the loader: uint8 costs packed four to a register; float
+    // costs of the adjoint copied to this thread's own slots of a stash that
+    // the loader never writes (16 live registers there cause spills).
     const bool epi_c = BWD ? (flags & PF_PHASE) : (flags & PF_E);
     float cst[16];
+    uint32_t cpk[4];
+    float *stash = reinterpret_cast<float *>(bufs + NBUF * G::kBufB);
     if (epi_c) {
+        if (COST == 1) {
 #pragma unroll
-        for (int i = 0; i < 16; i++) {
-            const uint32_t ci = l3 | ((uint32_t)i << 5);
-            cst[i] = COST == 0 ? reinterpret_cast<const float *>(scost)[ci] : (float)scost[ci];
+            for (int q = 0; q < 4; q++) cpk[q] = 0u;
+#pragma unroll
+            for (int i = 0; i < 16; i++)
+                cpk[i >> 2] |= (uint32_t)scost[l3 | ((uint32_t)i << 5)] << (8 * (i & 3));
+        } else if (BWD) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const uint32_t ci = l3 | ((uint32_t)i << 5);
+                stash[ci] = reinterpret_cast<const float *>(scost)[ci];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; i++)
+                cst[i] = reinterpret_cast<const float *>(scost)[l3 | ((uint32_t)i << 5)];
         }
     }
+    auto cost_at = [&](int i) -> float {
+        if (COST == 1) return (float)((cpk[i >> 2] >> (8 * (i & 3))) & 255u);
+        if (BWD) return stash[l3 | ((uint32_t)i << 5)];
+        return cst[i];
+    };
     // the buffer is consumed: start the tile NBUF ahead
     __syncthreads();
     if (warp == 0) {
         const uint32_t tn = t + (uint32_t)NBUF * stride;
         if (tn < total) issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc);
     }
-    rot_step<0, BWD, MODE>(a, l, active & (1u << 5), K.R, pscale, bacc);
-    rot_step<1, BWD, MODE>(a, l, active & (1u << 6), K.R, pscale, bacc);
-    rot_step<2, BWD, MODE>(a, l, active & (1u << 7), K.R, pscale, bacc);
-    rot_step<3, BWD, MODE>(a, l, active & (1u << 8), K.R, pscale, bacc);
+    // psi after the last stage is needed only when it is stored or meets the
+    // phase epilogue (the adjoint with per-pass checkpoints stores lambda only)
+    const bool psi_live = !BWD || D.psi_out != nullptr || (flags & PF_PHASE);
+    stage_rot<BWD, MODE>(a, l, stage_mask(active, 5, 6, 7, 8), K.R, pscale, bacc, psi_live);
     scale_all<BWD>(a, l, K.rescale ? K.fs3 : K.fse);
 
     // ---------------- stage 3: fused epilogue, coalesced store
@@ -540,12 +582,12 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     if (epi_c) {
         if (!BWD) {
 #pragma unroll
-            for (int i = 0; i < 16; i++) eacc = fmaf(cst[i], fmaf(a[i].x, a[i].x, a[i].y * a[i].y), eacc);
+            for (int i = 0; i < 16; i++) eacc = fmaf(cost_at(i), fmaf(a[i].x, a[i].x, a[i].y * a[i].y), eacc);
         } else {
             const bool un_psi = flags & PF_UNPHASE_PSI;
 #pragma unroll
             for (int i = 0; i < 16; i++) {
-                const float C = cst[i];
+                const float C = cost_at(i);
                 const float2 ph = COST == 0 ? phase_f32(C, K.ghi, K.glo) : stab[(int)C];
                 eacc = fmaf(C, fmaf(l[i].x, a[i].y, -l[i].y * a[i].x), eacc);
                 l[i] = cmul_conj(l[i], ph);
@@ -865,7 +907,7 @@ template <int BWD, int COST, int NBUF>
 cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t tiles, int *err,
                        cudaStream_t s) {
     using G = PassGeom<BWD, COST>;
-    const size_t smem = G::kHead + (size_t)NBUF * G::kBufB;
+    const size_t smem = G::kHead + (size_t)NBUF * G::kBufB + G::kStashB;
     static int grid_cap = 0;
     if (!grid_cap) {
         cudaError_t e = cudaFuncSetAttribute(xpass_kernel<BWD, COST, NBUF>,
@@ -887,11 +929,16 @@ cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t t
 
 int small_max_n() { return kSmallMaxN; }
 
-cudaError_t launch_xpass(int bwd, int cost_dtype, const PassDesc *d, const uint32_t *tb, int nd,
+cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, const PassDesc *d, const uint32_t *tb, int nd,
                          uint32_t tiles, int *err, cudaStream_t s) {
     if (tiles == 0) return cudaSuccess;
     if (!bwd) return cost_dtype == 0 ? launch_one<0, 0, 2>(d, tb, nd, tiles, err, s)
                                      : launch_one<0, 1, 2>(d, tb, nd, tiles, err, s);
+    // adjoint: one tile buffer and two CTAs per SM (128 registers a thread),
+    // or two buffers and one CTA per SM (no register cap below 255)
+    if (nbuf == 2)
+        return cost_dtype == 0 ? launch_one<1, 0, 2>(d, tb, nd, tiles, err, s)
+                               : launch_one<1, 1, 2>(d, tb, nd, tiles, err, s);
     return cost_dtype == 0 ? launch_one<1, 0, 1>(d, tb, nd, tiles, err, s)
                            : launch_one<1, 1, 1>(d, tb, nd, tiles, err, s);
 }

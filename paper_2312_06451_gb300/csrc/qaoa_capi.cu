@@ -65,7 +65,7 @@ enum LaunchKind { LK_PREP, LK_SMALL, LK_XPASS, LK_REDUCE, LK_EIG_INIT, LK_EIG_GE
 
 struct LaunchRec {
     int kind;
-    int T = 0, bwd = 0, cost_dtype = 0;
+    int T = 0, bwd = 0, cost_dtype = 0, nbuf = 1;
     size_t desc_off = 0, tb_off = 0;
     int ndesc = 0;
     uint32_t tiles = 0;
@@ -114,19 +114,25 @@ uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull) 
 }
 
 // Passes of one mixer round for n qubits and tile bits T: one contiguous pass
-// over qubits 0..T-1, then the remaining n-T qubits in balanced contiguous
+// over qubits 0..T-1, then the remaining n-T qubits in the fewest contiguous
 // chunks of at most T-cmin qubits, each gathered with 2^c contiguous
-// amplitudes (c >= cmin).
-std::vector<Group> make_groups(int n, int T, int cmin) {
+// amplitudes (c = T - chunk >= cmin).  split: 0 = chunks as equal as
+// possible, 1 = full chunks first and the remainder last, 2 = the remainder
+// first.
+std::vector<Group> make_groups(int n, int T, int cmin, int split) {
     std::vector<Group> g;
     g.push_back({T, T});
     const int R = n - T;
     if (R <= 0) return g;
     const int hmax = T - cmin;
     const int P = (R + hmax - 1) / hmax;
+    const int rem = R - hmax * (P - 1);
     int lo = T;
     for (int j = 0; j < P; j++) {
-        const int h = R / P + (j < R % P ? 1 : 0);
+        int h;
+        if (split == 1) h = j < P - 1 ? hmax : rem;
+        else if (split == 2) h = j == 0 ? rem : hmax;
+        else h = R / P + (j < R % P ? 1 : 0);
         g.push_back({T - h, lo});
         lo += h;
     }
@@ -168,9 +174,18 @@ struct qaoa_ctx {
     int64_t launches = 0;
     Plan plan;
     std::set<std::string> eig_ready;  // prepared eigenbasis operands (by V, lambda, D)
+    std::map<std::pair<int, int>, qaoa_xtune> xtune;  // X-mixer schedules by (n, cost dtype)
+    uint64_t tune_epoch = 0;                          // bumped on every schedule change
+    int ckpt_mode = QAOA_CKPT_PASS;                   // checkpointing of batched gradients
 };
 
 namespace {
+
+bool valid_xtune(const qaoa_xtune &t) {
+    return t.n > small_max_n() && t.n <= kMaxXQubits && (t.cost_dtype == QAOA_COST_F32 || t.cost_dtype == QAOA_COST_U8) &&
+           t.cmin >= 4 && t.cmin <= 8 && t.split >= 0 && t.split <= 2 && (t.nbuf_bwd_contig == 1 || t.nbuf_bwd_contig == 2) &&
+           (t.nbuf_bwd_gather == 1 || t.nbuf_bwd_gather == 2);
+}
 
 qaoa_status fail(qaoa_ctx *ctx, qaoa_status st, const char *fmt, ...) {
     char buf[512];
@@ -323,19 +338,49 @@ struct UnitLayout {
     std::vector<Group> gf, gb;
     uint32_t tiles_f, tiles_b;
     int64_t stride;  // partial slots per quantity
+    int ckpt;        // QAOA_CKPT_* actually used
     int vecs;        // state vectors held in scratch
+    int nb_bc, nb_bg;  // adjoint tile buffers (contiguous / gathered passes)
 };
 
-UnitLayout layout_for(const Unit &u, bool grad, int ckpt) {
+qaoa_xtune default_xtune(int n, int dt) {
+    qaoa_xtune t;
+    std::memset(&t, 0, sizeof(t));
+    t.n = n;
+    t.cost_dtype = dt;
+    t.cmin = min_contig();
+    t.split = 0;
+    t.nbuf_bwd_contig = 1;
+    t.nbuf_bwd_gather = 1;
+    return t;
+}
+
+qaoa_xtune tune_for(const qaoa_ctx *ctx, int n, int dt) {
+    auto it = ctx->xtune.find({n, dt});
+    return it != ctx->xtune.end() ? it->second : default_xtune(n, dt);
+}
+
+int layout_vecs(const UnitLayout &L, int p, bool grad) {
+    if (!grad) return 1;
+    if (L.ckpt == QAOA_CKPT_PASS) return 1 + p * (int)L.gf.size();
+    if (L.ckpt == QAOA_CKPT_ROUND) return 2 + (p - 1);
+    return 2;
+}
+
+UnitLayout layout_for(const qaoa_ctx *ctx, const Unit &u, bool grad, int ckpt) {
+    const qaoa_xtune t = tune_for(ctx, u.n, u.cost_dtype);
     UnitLayout L;
     L.T_f = kPassTileBits;
     L.T_b = kPassTileBits;
-    L.gf = make_groups(u.n, L.T_f, min_contig());
-    L.gb = make_groups(u.n, L.T_b, min_contig());
+    L.gf = make_groups(u.n, L.T_f, t.cmin, t.split);
+    L.gb = L.gf;  // per-pass checkpoints pair forward and adjoint passes one to one
     L.tiles_f = 1u << (u.n - L.T_f);
     L.tiles_b = 1u << (u.n - L.T_b);
     L.stride = std::max<int64_t>(L.tiles_f, (int64_t)L.gb.size() * L.tiles_b) * kPassWarps;
-    L.vecs = grad ? (2 + (ckpt ? u.p - 1 : 0)) : 1;
+    L.ckpt = grad ? ckpt : QAOA_CKPT_NONE;
+    L.vecs = layout_vecs(L, u.p, grad);
+    L.nb_bc = t.nbuf_bwd_contig;
+    L.nb_bg = t.nbuf_bwd_gather;
     return L;
 }
 
@@ -377,15 +422,79 @@ double pass_bytes(const PassDesc &d, int bwd, int cost_bytes) {
 
 // Descriptors of every pass of one unit: forward rounds, then adjoint rounds
 // in reverse.  Buffers: W = running state, L = adjoint state, CK[k] = state
-// after round k (0-based, k < p-1) when checkpointing.
-void unit_passes(const Unit &u, const UnitLayout &L, bool grad, int ckpt, float2 *W, float2 *Lam,
-                 float2 *CK, const RoundCoef *coef, const float2 *table, double *part,
-                 std::vector<PassDesc> &fwd, std::vector<PassDesc> &bwd) {
+// after round k (0-based, k < p-1) with per-round checkpoints; with per-pass
+// checkpoints CK[k Pf + g] = output of forward pass g of round k (W unused).
+void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float2 *Lam, float2 *CK,
+                 const RoundCoef *coef, const float2 *table, double *part, std::vector<PassDesc> &fwd,
+                 std::vector<PassDesc> &bwd) {
     const int p = u.p;
     const int64_t N = 1ll << u.n;
     const int Pf = (int)L.gf.size(), Pb = (int)L.gb.size();
     const float amp0 = (float)(1.0 / std::sqrt(std::ldexp(1.0, u.n)));
+    const int ckpt = L.ckpt;
     auto ck = [&](int k) { return CK + (int64_t)k * N; };
+    auto pk = [&](int k, int g) { return CK + ((int64_t)k * Pf + g) * N; };
+    if (grad && ckpt == QAOA_CKPT_PASS) {
+        for (int k = 0; k < p; k++) {
+            for (int g = 0; g < Pf; g++) {
+                PassDesc d;
+                std::memset(&d, 0, sizeof(d));
+                fill_geometry(d, u.n, L.T_f, L.gf[g]);
+                d.cost = u.cost;
+                d.coef = coef + k;
+                d.table = table ? table + (int64_t)k * kPhaseTable : nullptr;
+                d.amp0 = amp0;
+                if (g == 0) {
+                    d.flags |= PF_PHASE;
+                    if (k == 0) {
+                        if (u.init) {
+                            d.psi_in = u.init;
+                            d.flags |= PF_TWIST_IN;
+                        } else {
+                            d.flags |= PF_GEN_INIT;
+                        }
+                    } else {
+                        d.psi_in = pk(k - 1, Pf - 1);
+                    }
+                } else {
+                    d.psi_in = pk(k, g - 1);
+                }
+                if (g == Pf - 1 && k == p - 1) {
+                    d.flags |= PF_E;
+                    d.part_E = part;
+                }
+                d.psi_out = pk(k, g);
+                fwd.push_back(d);
+            }
+        }
+        // adjoint: pass (k, g) reads the forward output of pass (k, g) and
+        // writes lambda only; the next one reads the forward output before it
+        for (int k = p - 1; k >= 0; k--) {
+            for (int q = 0; q < Pb; q++) {
+                const int g = Pb - 1 - q;
+                PassDesc d;
+                std::memset(&d, 0, sizeof(d));
+                fill_geometry(d, u.n, L.T_b, L.gb[g]);
+                d.cost = u.cost;
+                d.coef = coef + k;
+                d.table = table ? table + (int64_t)k * kPhaseTable : nullptr;
+                d.amp0 = amp0;
+                d.psi_in = pk(k, g);
+                if (k == p - 1 && q == 0) d.flags |= PF_LAM_FROM_C;
+                else d.lam_in = Lam;
+                if (g == 0) {
+                    d.flags |= PF_PHASE;
+                    d.part_gamma = part + (int64_t)(1 + p + k) * L.stride;
+                    d.lam_out = k > 0 ? Lam : nullptr;
+                } else {
+                    d.lam_out = Lam;
+                }
+                d.part_beta = part + (int64_t)(1 + k) * L.stride + (int64_t)q * L.tiles_b * kPassWarps;
+                bwd.push_back(d);
+            }
+        }
+        return;
+    }
     for (int k = 0; k < p; k++) {
         for (int g = 0; g < Pf; g++) {
             PassDesc d;
@@ -472,6 +581,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
     uint64_t key = fnv1a(units.data(), units.size() * sizeof(Unit));
     const int flags2[2] = {grad ? 1 : 0, ckpt};
     key = fnv1a(flags2, sizeof(flags2), key);
+    key = fnv1a(&ctx->tune_epoch, sizeof(ctx->tune_epoch), key);
 
     if (!(ctx->plan.valid && ctx->plan.key == key)) {
         if (capturing(ctx))
@@ -496,7 +606,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             if (u.cost_dtype == QAOA_COST_U8) meta = align_up(meta + sizeof(float2) * kPhaseTable * u.p);
             off_part[i] = meta;
             if (u.mixer_kind == QAOA_MIXER_X && u.n > smax) {
-                lay[i] = layout_for(u, grad, ckpt);
+                lay[i] = layout_for(ctx, u, grad, ckpt);
                 meta = align_up(meta + sizeof(double) * (2 * u.p + 1) * lay[i].stride);
             }
         }
@@ -507,16 +617,18 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
 
         // ---- state memory: pass units grouped by launch shape, admitted in waves
         struct GKey {
-            int Tf, Tb, Pf, Pb, p, dt;
+            int Tf, Tb, Pf, Pb, p, dt, nbc, nbg;
             bool operator<(const GKey &o) const {
-                return std::tie(Tf, Tb, Pf, Pb, p, dt) < std::tie(o.Tf, o.Tb, o.Pf, o.Pb, o.p, o.dt);
+                return std::tie(Tf, Tb, Pf, Pb, p, dt, nbc, nbg) <
+                       std::tie(o.Tf, o.Tb, o.Pf, o.Pb, o.p, o.dt, o.nbc, o.nbg);
             }
         };
         std::map<GKey, std::vector<int>> groups;
         for (int i = 0; i < nu; i++) {
             if (units[i].mixer_kind != QAOA_MIXER_X || units[i].n <= smax) continue;
             const UnitLayout &L = lay[i];
-            groups[{L.T_f, L.T_b, (int)L.gf.size(), (int)L.gb.size(), units[i].p, units[i].cost_dtype}]
+            groups[{L.T_f, L.T_b, (int)L.gf.size(), (int)L.gb.size(), units[i].p, units[i].cost_dtype, L.nb_bc,
+                    L.nb_bg}]
                 .push_back(i);
         }
         size_t free_b = 0, total_b = 0;
@@ -537,7 +649,13 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             w.gk = kv.first;
             size_t used = 0;
             for (int i : kv.second) {
-                const size_t need = align_up((size_t)lay[i].vecs * (sizeof(float2) << units[i].n));
+                size_t need = align_up((size_t)lay[i].vecs * (sizeof(float2) << units[i].n));
+                // fewer checkpoints when one angle set's scratch does not fit
+                while (need > budget && lay[i].ckpt > QAOA_CKPT_NONE) {
+                    lay[i].ckpt--;
+                    lay[i].vecs = layout_vecs(lay[i], units[i].p, grad);
+                    need = align_up((size_t)lay[i].vecs * (sizeof(float2) << units[i].n));
+                }
                 if (need > budget)
                     return fail(ctx, QAOA_ERR_OOM,
                                 "one angle set at n=%d needs %.2f GiB of state scratch, %.2f GiB available",
@@ -680,8 +798,13 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 const int64_t N = 1ll << u.n;
                 float2 *base = reinterpret_cast<float2 *>(static_cast<char *>(d_state) + w.soff[wi]);
                 float2 *W = base, *Lam = grad ? base + N : nullptr, *CK = grad ? base + 2 * N : nullptr;
+                if (grad && lay[i].ckpt == QAOA_CKPT_PASS) {
+                    Lam = base;
+                    CK = base + N;
+                    W = nullptr;
+                }
                 std::vector<PassDesc> f, b;
-                unit_passes(u, lay[i], grad, ckpt, W, Lam, CK, prep[i].coef, prep[i].table,
+                unit_passes(u, lay[i], grad, W, Lam, CK, prep[i].coef, prep[i].table,
                             reinterpret_cast<double *>(mb + off_part[i]), f, b);
                 std::vector<PassDesc> all = f;
                 all.insert(all.end(), b.begin(), b.end());
@@ -718,6 +841,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 r.T = T;
                 r.bwd = bwd;
                 r.cost_dtype = gk.dt;
+                r.nbuf = bwd ? (steps[s][0].c >= kPassTileBits ? gk.nbc : gk.nbg) : 2;
                 r.desc_off = put(steps[s].data(), sizeof(PassDesc) * steps[s].size());
                 xpass_descs.push_back({r.desc_off, (int)steps[s].size()});
                 r.tb_off = put(tb.data(), sizeof(uint32_t) * tb.size());
@@ -1004,7 +1128,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                              r.small_grad, r.small_maxn, ctx->d_err, ctx->stream);
             break;
         case LK_XPASS:
-            e = launch_xpass(r.bwd, r.cost_dtype, reinterpret_cast<const PassDesc *>(db + r.desc_off),
+            e = launch_xpass(r.bwd, r.cost_dtype, r.nbuf, reinterpret_cast<const PassDesc *>(db + r.desc_off),
                              reinterpret_cast<const uint32_t *>(db + r.tb_off), r.ndesc, r.tiles,
                              ctx->d_err, ctx->stream);
             break;
@@ -1130,7 +1254,7 @@ qaoa_status scalar_run(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
     u.lam = mixer->d_lambda;
     u.gemm_precision = mixer->gemm_precision;
     std::vector<Unit> us(1, u);
-    st = run_units(ctx, us, grad != nullptr, grad ? (ckpt ? 1 : 0) : 0);
+    st = run_units(ctx, us, grad != nullptr, grad ? ckpt : 0);
     if (st) return st;
     const size_t nout = grad ? (size_t)2 * p + 1 : 1;
     QG_CUDA(ctx, cudaMemcpyAsync(ctx->h_io + 2 * p, io + 2 * p, sizeof(double) * nout, cudaMemcpyDeviceToHost,
@@ -1364,8 +1488,10 @@ qaoa_status qaoa_gradient(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, con
     try {
         ctx->err.clear();
         if (!grad) return fail(ctx, QAOA_ERR_INVALID, "grad must be non-NULL");
+        if (ckpt < QAOA_CKPT_NONE || ckpt > QAOA_CKPT_PASS)
+            return fail(ctx, QAOA_ERR_INVALID, "ckpt must be one of QAOA_CKPT_NONE/ROUND/PASS (got %d)", ckpt);
         cudaSetDevice(ctx->device);
-        return scalar_run(ctx, d_cost, cost_dtype, mixer, d_init, p, angles, E, grad, ckpt ? 1 : 0);
+        return scalar_run(ctx, d_cost, cost_dtype, mixer, d_init, p, angles, E, grad, ckpt);
     } catch (...) {
         return fail(ctx, QAOA_ERR_OOM, "host allocation failed");
     }
@@ -1405,7 +1531,178 @@ qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *
                 units.push_back(u);
             }
         }
-        return run_units(ctx, units, want_grad != 0, 1);
+        return run_units(ctx, units, want_grad != 0, want_grad ? ctx->ckpt_mode : 0);
+    } catch (...) {
+        return fail(ctx, QAOA_ERR_OOM, "host allocation failed");
+    }
+}
+
+qaoa_status qaoa_set_checkpointing(qaoa_ctx *ctx, int mode) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    if (mode < QAOA_CKPT_NONE || mode > QAOA_CKPT_PASS)
+        return fail(ctx, QAOA_ERR_INVALID, "checkpoint mode must be 0, 1 or 2 (got %d)", mode);
+    ctx->ckpt_mode = mode;
+    return QAOA_OK;
+}
+
+int qaoa_pass_schedule(int n, int cmin, int split, int *c, int *lo, int max) {
+    if (n <= kPassTileBits || n > kMaxXQubits || cmin < 4 || cmin > 8 || split < 0 || split > 2) return -1;
+    const std::vector<Group> g = make_groups(n, kPassTileBits, cmin, split);
+    for (int j = 0; j < (int)g.size() && j < max; j++) {
+        if (c) c[j] = g[j].c;
+        if (lo) lo[j] = g[j].lo;
+    }
+    return (int)g.size();
+}
+
+qaoa_status qaoa_set_xtune(qaoa_ctx *ctx, const qaoa_xtune *t) {
+    if (!ctx || !t) return QAOA_ERR_INVALID;
+    if (!valid_xtune(*t))
+        return fail(ctx, QAOA_ERR_INVALID,
+                    "schedule needs %d < n <= %d, cost dtype 0/1, cmin 4..8, split 0..2, buffers 1 or 2",
+                    small_max_n(), kMaxXQubits);
+    ctx->xtune[{t->n, t->cost_dtype}] = *t;
+    ctx->tune_epoch++;
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_get_xtune(qaoa_ctx *ctx, int n, int cost_dtype, qaoa_xtune *out) {
+    if (!ctx || !out) return QAOA_ERR_INVALID;
+    *out = tune_for(ctx, n, cost_dtype);
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_autotune_x(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, int n, int p, int want_grad,
+                            qaoa_xtune *out) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    try {
+        ctx->err.clear();
+        if (!d_cost || (cost_dtype != QAOA_COST_F32 && cost_dtype != QAOA_COST_U8))
+            return fail(ctx, QAOA_ERR_INVALID, "bad cost vector or dtype");
+        if (n <= small_max_n() || n > kMaxXQubits)
+            return fail(ctx, QAOA_ERR_INVALID, "tuning applies to %d < n <= %d (got %d)", small_max_n(),
+                        kMaxXQubits, n);
+        if (p < 1 || p > 8) return fail(ctx, QAOA_ERR_INVALID, "tuning rounds p must be 1..8 (got %d)", p);
+        if (capturing(ctx)) return fail(ctx, QAOA_ERR_INVALID, "cannot tune during stream capture");
+        cudaSetDevice(ctx->device);
+        // fixed angles (beta away from pi/2, so the rotations take their usual form)
+        std::vector<double> h(4 * p + 1, 0.0);
+        for (int k = 0; k < p; k++) {
+            h[k] = 0.35 + 0.05 * k;
+            h[p + k] = 0.25 + 0.03 * k;
+        }
+        void *d_io = nullptr;
+        qaoa_status st = scratch(ctx, "tune_io", h.size() * sizeof(double), &d_io);
+        if (st) return st;
+        double *io = static_cast<double *>(d_io);
+        QG_CUDA(ctx, cudaMemcpyAsync(io, h.data(), sizeof(double) * 2 * p, cudaMemcpyHostToDevice, ctx->stream),
+                "tuning angles");
+        Unit u;
+        std::memset(&u, 0, sizeof(u));
+        u.cost = d_cost;
+        u.cost_dtype = cost_dtype;
+        u.n = n;
+        u.p = p;
+        u.angles = io;
+        u.E = io + 2 * p;
+        u.grad = want_grad ? io + 2 * p + 1 : nullptr;
+        u.tsize = kPhaseTable;
+        u.mixer_kind = QAOA_MIXER_X;
+        u.dim = 1ll << n;
+        const std::vector<Unit> us(1, u);
+        const int ck = want_grad ? ctx->ckpt_mode : 0;
+        const bool had = ctx->xtune.count({n, cost_dtype}) != 0;
+        const qaoa_xtune saved = tune_for(ctx, n, cost_dtype);
+        cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+        auto restore = [&]() {
+            if (had) ctx->xtune[{n, cost_dtype}] = saved;
+            else ctx->xtune.erase({n, cost_dtype});
+            ctx->tune_epoch++;
+        };
+        // best of three timed sweeps after one untimed sweep that builds the plan
+        auto time_it = [&](const qaoa_xtune &t, double *ms) -> qaoa_status {
+            ctx->xtune[{n, cost_dtype}] = t;
+            ctx->tune_epoch++;
+            qaoa_status s2 = run_units(ctx, us, want_grad != 0, ck);
+            if (s2) return s2;
+            double best = 1e30;
+            for (int r = 0; r < 3; r++) {
+                cudaEventRecord(e0, ctx->stream);
+                s2 = run_units(ctx, us, want_grad != 0, ck);
+                if (s2) return s2;
+                cudaEventRecord(e1, ctx->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) return read_dev_err(ctx);
+                float f = 0.f;
+                cudaEventElapsedTime(&f, e0, e1);
+                best = std::min(best, (double)f);
+            }
+            *ms = best;
+            return read_dev_err(ctx);
+        };
+        // 1. pass groups: every (cmin, split) with the fewest passes, distinct
+        std::vector<qaoa_xtune> cands;
+        std::set<std::vector<int>> seen;
+        size_t fewest = 1000;
+        for (int cm = 4; cm <= 8; cm++)
+            fewest = std::min(fewest, make_groups(n, kPassTileBits, cm, 0).size());
+        for (int cm = 4; cm <= 8; cm++) {
+            for (int sp = 0; sp <= 2; sp++) {
+                const std::vector<Group> g = make_groups(n, kPassTileBits, cm, sp);
+                if (g.size() != fewest) continue;
+                std::vector<int> sig;
+                for (const Group &x : g) {
+                    sig.push_back(x.c);
+                    sig.push_back(x.lo);
+                }
+                if (!seen.insert(sig).second) continue;
+                qaoa_xtune t = default_xtune(n, cost_dtype);
+                t.cmin = cm;
+                t.split = sp;
+                cands.push_back(t);
+            }
+        }
+        qaoa_xtune best = cands.front();
+        best.ms = 1e30;
+        for (qaoa_xtune t : cands) {
+            double ms = 0.0;
+            st = time_it(t, &ms);
+            if (st) {
+                restore();
+                return st;
+            }
+            if (ms < best.ms) {
+                best = t;
+                best.ms = ms;
+            }
+        }
+        // 2. adjoint tile buffers, contiguous and gathered passes
+        if (want_grad) {
+            const qaoa_xtune base = best;
+            for (int bc = 1; bc <= 2; bc++) {
+                for (int bg = 1; bg <= 2; bg++) {
+                    if (bc == base.nbuf_bwd_contig && bg == base.nbuf_bwd_gather) continue;
+                    qaoa_xtune t = base;
+                    t.nbuf_bwd_contig = bc;
+                    t.nbuf_bwd_gather = bg;
+                    double ms = 0.0;
+                    st = time_it(t, &ms);
+                    if (st) {
+                        restore();
+                        return st;
+                    }
+                    if (ms < best.ms) {
+                        best = t;
+                        best.ms = ms;
+                    }
+                }
+            }
+        }
+        ctx->ev_pool.push_back(e0);
+        ctx->ev_pool.push_back(e1);
+        ctx->xtune[{n, cost_dtype}] = best;
+        ctx->tune_epoch++;
+        if (out) *out = best;
+        return QAOA_OK;
     } catch (...) {
         return fail(ctx, QAOA_ERR_OOM, "host allocation failed");
     }
