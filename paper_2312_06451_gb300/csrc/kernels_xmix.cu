@@ -303,12 +303,6 @@ constexpr int kTile = 1 << kT;
 constexpr int kNT = 256;
 constexpr int kNW = kNT / 32;
 
-__device__ __forceinline__ uint32_t deposit(uint32_t v, const uint8_t *pos, int nbits) {
-    uint32_t o = 0;
-    for (int k = 0; k < nbits; k++) o |= ((v >> k) & 1u) << pos[k];
-    return o;
-}
-
 template <int BWD, int COST>
 struct PassGeom {
     static constexpr uint32_t kPsiB = kTile * 8;
@@ -330,14 +324,38 @@ __device__ __forceinline__ bool needs_cost(uint32_t flags) {
     return BWD ? (flags & (PF_LAM_FROM_C | PF_PHASE)) != 0 : (flags & (PF_PHASE | PF_E)) != 0;
 }
 
+// Descriptor of tile t for the loader.  A CTA issues its tiles in
+// increasing order, so the search walks forward from the previous answer
+// (`cursor`, warp 0's own) instead of bisecting tile_begin every time.
+__device__ __forceinline__ int next_desc(const uint32_t *__restrict__ tile_begin, int ndesc, uint32_t t,
+                                         int &cursor) {
+    int di = cursor;
+    if (di < 0 || di >= ndesc || t < tile_begin[di]) di = find_desc(tile_begin, ndesc, t);
+    else
+        while (di < ndesc && t >= tile_begin[di + 1]) di++;
+    if (di >= ndesc) di = -1;
+    if (di >= 0) cursor = di;
+    return di;
+}
+
+// Global offset of local index 0 of tile tl: the tile index's bits fill the
+// free qubits in increasing order, which are c..lo-1 and lo+h..n-1 for a pass
+// keeping qubits 0..c-1 contiguous and gathering lo..lo+h-1 (h = T - c).
+__device__ __forceinline__ uint32_t tile_base(uint32_t tl, int c, int lo) {
+    if (c >= kT) return tl << kT;
+    const int h = kT - c, nb = lo - c;
+    const uint32_t hi = lo + h < 32 ? (tl >> nb) << (lo + h) : 0u;  // nothing above a top block
+    return ((tl & ((1u << nb) - 1u)) << c) | hi;
+}
+
 // Warp 0: start the loads of tile t into buffer buf (all 32 lanes call).
 template <int BWD, int COST>
 __device__ __forceinline__ void issue_tile(uint32_t t, unsigned char *buf, uint32_t bar, TileInfo *info,
                                            const PassDesc *__restrict__ descs,
-                                           const uint32_t *__restrict__ tile_begin, int ndesc) {
+                                           const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor) {
     using G = PassGeom<BWD, COST>;
     const int lane = threadIdx.x & 31;
-    const int di = find_desc(tile_begin, ndesc, t);
+    const int di = next_desc(tile_begin, ndesc, t, cursor);
     fence_proxy_async();
     if (di < 0) {
         if (lane == 0) {
@@ -350,7 +368,7 @@ __device__ __forceinline__ void issue_tile(uint32_t t, unsigned char *buf, uint3
     const uint32_t flags = Dg->flags;
     const int c = Dg->c;
     const uint32_t tl = t - tile_begin[di];
-    const uint32_t base = deposit(tl, Dg->fpos, Dg->nfree);
+    const uint32_t base = tile_base(tl, c, Dg->gpos[c < kT ? c : 0]);
     const bool ld_psi = BWD || !(flags & PF_GEN_INIT);
     const bool ld_lam = BWD && !(flags & PF_LAM_FROM_C);
     const bool ld_cost = needs_cost<BWD>(flags);
@@ -385,8 +403,9 @@ __device__ __forceinline__ void issue_tile(uint32_t t, unsigned char *buf, uint3
     if (!(seg_psi || seg_lam || seg_cost)) return;
     const int nseg = 1 << (kT - c);
     const uint32_t segn = 1u << c;
+    const int glo = c < kT ? Dg->gpos[c] : 0;  // segment s starts at base + s 2^lo
     for (int s = lane; s < nseg; s += 32) {
-        const uint32_t off = base + deposit((uint32_t)s, Dg->gpos + c, kT - c);
+        const uint32_t off = base + ((uint32_t)s << glo);
         const uint32_t ls = (uint32_t)s << c;
         if (seg_psi) bulk_g2s(sb + ls * 8, psi + off, segn * 8, bar);
         if (seg_lam) bulk_g2s(sb + G::kPsiB + ls * 8, lam + off, segn * 8, bar);
@@ -415,7 +434,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
                                           unsigned char *bufs, int b, uint32_t bar, uint32_t t, uint32_t stride,
                                           uint32_t total, uint32_t base, uint32_t tl, TileInfo *tinfo,
                                           const PassDesc *__restrict__ descs,
-                                          const uint32_t *__restrict__ tile_begin, int ndesc) {
+                                          const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor) {
     using G = PassGeom<BWD, COST>;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t l1 = ((uint32_t)lane << 1) | ((uint32_t)warp << 6);
@@ -519,14 +538,16 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
         pscale = 1.f;
     }
 
-    // ---------------- stage 2 -> 3
-    __syncthreads();
+    // ---------------- stage 2 -> 3: local bits 9..11 are the warp index in
+    // both layouts and the swizzle moves bits 1..3 only, so each warp reads
+    // back just what it wrote: a warp barrier is enough
+    __syncwarp();
 #pragma unroll
     for (int i = 0; i < 16; i++) {
         sp[p2 ^ ((uint32_t)i << 1)] = a[i];
         if (BWD) sl[p2 ^ ((uint32_t)i << 1)] = l[i];
     }
-    __syncthreads();
+    __syncwarp();
 #pragma unroll
     for (int i = 0; i < 16; i++) {
         const uint32_t idx = p3 ^ swz((uint32_t)i << 5);
@@ -569,7 +590,8 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     __syncthreads();
     if (warp == 0) {
         const uint32_t tn = t + (uint32_t)NBUF * stride;
-        if (tn < total) issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc);
+        if (tn < total)
+            issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc, cursor);
     }
     // psi after the last stage is needed only when it is stored or meets the
     // phase epilogue (the adjoint with per-pass checkpoints stores lambda only)
@@ -645,12 +667,13 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
     }
     __syncthreads();
     const uint32_t stride = gridDim.x;
+    int cursor = 0;  // loader's descriptor search position (warp 0)
     if (warp == 0) {
         for (int k = 0; k < NBUF; k++) {
             const uint32_t t = blockIdx.x + (uint32_t)k * stride;
             if (t < total)
                 issue_tile<BWD, COST>(t, bufs + k * G::kBufB, smem_u32(&bars[k]), &tinfo[k], descs, tile_begin,
-                                      ndesc);
+                                      ndesc, cursor);
         }
     }
     const uint32_t l3 = (uint32_t)lane | ((uint32_t)warp << 9);
@@ -718,10 +741,10 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
         }
         if (K.R.mode == 0)
             tile_body<BWD, COST, NBUF, 0>(K, D, stab, bufs, b, bar, t, stride, total, ti.base, ti.tl, tinfo, descs,
-                                          tile_begin, ndesc);
+                                          tile_begin, ndesc, cursor);
         else
             tile_body<BWD, COST, NBUF, 2>(K, D, stab, bufs, b, bar, t, stride, total, ti.base, ti.tl, tinfo, descs,
-                                          tile_begin, ndesc);
+                                          tile_begin, ndesc, cursor);
     }
 }
 
