@@ -22,6 +22,8 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
 MIXER_X = 0
 MIXER_RING = 1
+MIXER_CLIQUE = 2
+_MIXERS = {"x": MIXER_X, "ring": MIXER_RING, "clique": MIXER_CLIQUE}
 
 _lock = threading.Lock()
 _lib = None
@@ -134,11 +136,11 @@ def cost_dks(n, edges, states) -> np.ndarray:
 
 
 def _problem(mixer, n, cost, states):
-    kind = {"x": MIXER_X, "ring": MIXER_RING}[mixer]
+    kind = _MIXERS[mixer]
     cost = _f64(cost)
-    if kind == MIXER_RING:
+    if kind != MIXER_X:
         if states is None:
-            raise ValueError("the ring mixer needs the feasible states")
+            raise ValueError(f"the {mixer} mixer needs the feasible states")
         states = np.ascontiguousarray(states, dtype=np.uint64)
     else:
         states = None
@@ -183,7 +185,7 @@ def qaoa_gradient(n, cost, angles, mixer="x", states=None, psi0=None):
 
 
 def mixer_apply(n, psi, beta, mixer="x", states=None) -> np.ndarray:
-    kind = {"x": MIXER_X, "ring": MIXER_RING}[mixer]
+    kind = _MIXERS[mixer]
     v = _c128(psi).copy()
     st = None if states is None else np.ascontiguousarray(states, dtype=np.uint64)
     r = _load().oracle_mixer_apply(kind, n, v.shape[0], _ptr(st), float(beta), _ptr(v))
@@ -193,7 +195,7 @@ def mixer_apply(n, psi, beta, mixer="x", states=None) -> np.ndarray:
 
 
 def hm_apply(n, psi, mixer="x", states=None) -> np.ndarray:
-    kind = {"x": MIXER_X, "ring": MIXER_RING}[mixer]
+    kind = _MIXERS[mixer]
     v = _c128(psi)
     st = None if states is None else np.ascontiguousarray(states, dtype=np.uint64)
     out = np.empty_like(v)

@@ -46,7 +46,7 @@
 
 typedef double complex cplx;
 
-enum { ORACLE_MIXER_X = 0, ORACLE_MIXER_RING = 1 };
+enum { ORACLE_MIXER_X = 0, ORACLE_MIXER_RING = 1, ORACLE_MIXER_CLIQUE = 2 };
 
 /* ------------------------------------------------------------------ threads */
 
@@ -148,10 +148,10 @@ void oracle_cost_dks(int n, int m, const int32_t *edges, int64_t dim,
 /* ---------------------------------------------------------------- mixers */
 
 typedef struct {
-    int kind;               /* ORACLE_MIXER_X or ORACLE_MIXER_RING */
+    int kind;               /* ORACLE_MIXER_X, _RING or _CLIQUE */
     int n;
     int64_t dim;
-    const uint64_t *states; /* ring: the sorted Hamming-weight-k states */
+    const uint64_t *states; /* ring, clique: the sorted Hamming-weight-k states */
 } mixer_t;
 
 /* Position of state s in the sorted feasible list (binary search). */
@@ -172,7 +172,8 @@ static int64_t find_state(const mixer_t *mx, uint64_t s) {
  * X_i X_j + Y_i Y_j.  On two qubits this operator maps |01> <-> |10> with
  * matrix element 2 and annihilates |00>, |11>; so on a basis state it swaps
  * bits i and j with weight 2 when they differ.  The ring is read as periodic
- * (edge n-1 -- 0 included), coefficient 1 per edge. */
+ * (edge n-1 -- 0 included), coefficient 1 per edge.
+ * Clique mixer (Sec. 2.1): the same two-qubit term on every pair i < j. */
 static void hm_apply(const mixer_t *mx, const cplx *v, cplx *out) {
     const int n = mx->n;
     if (mx->kind == ORACLE_MIXER_X) {
@@ -181,6 +182,19 @@ static void hm_apply(const mixer_t *mx, const cplx *v, cplx *out) {
             cplx s = 0.0;
             for (int i = 0; i < n; i++) s += v[x ^ ((int64_t)1 << i)];
             out[x] = s;
+        }
+    } else if (mx->kind == ORACLE_MIXER_CLIQUE) {
+#pragma omp parallel for schedule(static)
+        for (int64_t a = 0; a < mx->dim; a++) {
+            uint64_t x = mx->states[a];
+            cplx s = 0.0;
+            for (int i = 0; i < n; i++)
+                for (int j = i + 1; j < n; j++)
+                    if (bit(x, i) != bit(x, j)) {
+                        uint64_t y = x ^ ((uint64_t)1 << i) ^ ((uint64_t)1 << j);
+                        s += 2.0 * v[find_state(mx, y)];
+                    }
+            out[a] = s;
         }
     } else {
 #pragma omp parallel for schedule(static)
@@ -203,10 +217,11 @@ static void hm_apply(const mixer_t *mx, const cplx *v, cplx *out) {
  * X mixer: the X_i commute, so e^{-i beta sum X_i} = prod_i e^{-i beta X_i};
  * e^{-i beta X} = cos(beta) I - i sin(beta) X acts on each amplitude pair
  * (x, x xor 2^i) (Sec. 2.2: a sequence of single-qubit operations).
- * Ring mixer: the exponential series sum_j (-i tau H)^j / j! applied to v,
- * with beta split into s equal steps tau so that |tau| * ||H|| <= 1/2; the
- * series is summed until its terms fall below 1e-18 of the running sum.
- * ||H|| <= max row sum <= 2n. */
+ * Ring and clique mixers: the exponential series sum_j (-i tau H)^j / j!
+ * applied to v, with beta split into s equal steps tau so that
+ * |tau| * ||H|| <= 1/2; the series is summed until its terms fall below 1e-18
+ * of the running sum.  ||H|| <= max row sum: 2n for the ring, 2 k (n - k)
+ * for the clique (a weight-k state has k (n - k) pairs of differing bits). */
 static void mixer_apply(const mixer_t *mx, double beta, cplx *v, cplx *tmp1, cplx *tmp2) {
     const int64_t dim = mx->dim;
     if (mx->kind == ORACLE_MIXER_X) {
@@ -225,7 +240,12 @@ static void mixer_apply(const mixer_t *mx, double beta, cplx *v, cplx *tmp1, cpl
         }
         return;
     }
-    const double hnorm = 2.0 * mx->n;
+    double hnorm = 2.0 * mx->n;
+    if (mx->kind == ORACLE_MIXER_CLIQUE) {
+        const int k = __builtin_popcountll(mx->states[0]);
+        hnorm = 2.0 * k * (mx->n - k);
+        if (hnorm < 1.0) hnorm = 1.0;
+    }
     int steps = (int)ceil(fabs(beta) * hnorm / 0.5);
     if (steps < 1) steps = 1;
     const double tau = beta / steps;
@@ -265,6 +285,7 @@ static int make_mixer(mixer_t *mx, int kind, int n, int64_t dim, const uint64_t 
     mx->kind = kind; mx->n = n; mx->dim = dim; mx->states = states;
     if (kind == ORACLE_MIXER_X) return dim == ((int64_t)1 << n) ? 0 : -1;
     if (kind == ORACLE_MIXER_RING) return (states && n >= 3) ? 0 : -1;
+    if (kind == ORACLE_MIXER_CLIQUE) return (states && n >= 2 && dim >= 1) ? 0 : -1;
     return -1;
 }
 
@@ -280,7 +301,7 @@ int oracle_qaoa_state(int kind, int n, int64_t dim, const uint64_t *states,
     if (make_mixer(&mx, kind, n, dim, states) || p < 0) return -1;
     cplx *v = (cplx *)psi_out;
     cplx *t1 = NULL, *t2 = NULL;
-    if (kind == ORACLE_MIXER_RING) {
+    if (kind != ORACLE_MIXER_X) {
         t1 = malloc(sizeof(cplx) * dim); t2 = malloc(sizeof(cplx) * dim);
         if (!t1 || !t2) { free(t1); free(t2); return -2; }
     }
@@ -338,8 +359,8 @@ int oracle_qaoa_gradient(int kind, int n, int64_t dim, const uint64_t *states,
     cplx *psi = malloc(sizeof(cplx) * dim);
     cplx *lam = malloc(sizeof(cplx) * dim);
     cplx *hv = malloc(sizeof(cplx) * dim);
-    cplx *t2 = kind == ORACLE_MIXER_RING ? malloc(sizeof(cplx) * dim) : NULL;
-    if (!psi || !lam || !hv || (kind == ORACLE_MIXER_RING && !t2)) {
+    cplx *t2 = kind != ORACLE_MIXER_X ? malloc(sizeof(cplx) * dim) : NULL;
+    if (!psi || !lam || !hv || (kind != ORACLE_MIXER_X && !t2)) {
         free(psi); free(lam); free(hv); free(t2);
         return -2;
     }
@@ -380,7 +401,7 @@ int oracle_mixer_apply(int kind, int n, int64_t dim, const uint64_t *states,
     mixer_t mx;
     if (make_mixer(&mx, kind, n, dim, states)) return -1;
     cplx *t1 = NULL, *t2 = NULL;
-    if (kind == ORACLE_MIXER_RING) {
+    if (kind != ORACLE_MIXER_X) {
         t1 = malloc(sizeof(cplx) * dim); t2 = malloc(sizeof(cplx) * dim);
         if (!t1 || !t2) { free(t1); free(t2); return -2; }
     }

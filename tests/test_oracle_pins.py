@@ -45,6 +45,14 @@ def dense_ring_mixer(n):
     return H
 
 
+def dense_clique_mixer(n):
+    H = 0
+    for i in range(n):
+        for j in range(i + 1, n):
+            H = H + pauli_op(n, {i: PX, j: PX}) + pauli_op(n, {i: PY, j: PY})
+    return H
+
+
 def bits_matrix(n, xs=None):
     xs = np.arange(1 << n, dtype=np.int64) if xs is None else np.asarray(xs, dtype=np.int64)
     return ((xs[:, None] >> np.arange(n)[None, :]) & 1).astype(np.int64)
@@ -204,6 +212,57 @@ def test_ring_mixer_exponential(oracle_mod, n, k, beta):
     np.testing.assert_allclose(got, ref, atol=1e-11 * np.abs(v).max())
 
 
+def total_spin_clique_spectrum(n, k):
+    """sum_{i<j} (X_i X_j + Y_i Y_j) = 2 (S_x^2 + S_y^2) - n = 2 (S^2 - S_z^2) - n
+    with S = (1/2) sum of the Pauli vectors.  On weight k, S_z = m = n/2 - k;
+    spin s (|m| <= s <= n/2) occurs C(n, n/2 - s) - C(n, n/2 - s - 1) times
+    among n spins 1/2, each contributing one state with S_z = m."""
+    m = n / 2 - k
+    levels = []
+    s = abs(m)
+    while s <= n / 2 + 1e-9:
+        j = round(n / 2 - s)
+        mult = math.comb(n, j) - (math.comb(n, j - 1) if j >= 1 else 0)
+        levels += [2 * (s * (s + 1) - m * m) - n] * mult
+        s += 1
+    return np.sort(levels)
+
+
+@pytest.mark.parametrize("n,k", [(2, 1), (4, 2), (5, 2), (6, 3), (7, 1)])
+def test_clique_hm_matches_pauli_sum(oracle_mod, n, k):
+    s = oracle_mod.dicke_states(n, k).astype(np.int64)
+    Hf = dense_clique_mixer(n)
+    mask = np.zeros(1 << n, bool)
+    mask[s] = True
+    assert np.abs(Hf[np.ix_(~mask, mask)]).max() == 0
+    D = len(s)
+    Hs = np.stack([oracle_mod.hm_apply(n, np.eye(D)[i], "clique", s) for i in range(D)], axis=1)
+    np.testing.assert_allclose(Hs, Hf[np.ix_(s, s)], atol=1e-12)
+
+
+@pytest.mark.parametrize("n,k", [(4, 2), (6, 2), (7, 3), (8, 4), (9, 4), (10, 3)])
+def test_clique_spectrum_total_spin(oracle_mod, n, k):
+    s = oracle_mod.dicke_states(n, k)
+    D = len(s)
+    Hs = np.stack([oracle_mod.hm_apply(n, np.eye(D)[i], "clique", s) for i in range(D)], axis=1)
+    np.testing.assert_allclose(Hs, Hs.conj().T, atol=0)
+    np.testing.assert_allclose(np.linalg.eigvalsh(Hs), total_spin_clique_spectrum(n, k), atol=1e-9)
+    assert np.trace(Hs).real == pytest.approx(0, abs=1e-12)
+    # every weight-k state has k (n - k) swap partners, each with element 2
+    assert np.trace(Hs @ Hs).real == pytest.approx(4 * k * (n - k) * D, rel=1e-12)
+
+
+@pytest.mark.parametrize("n,k,beta", [(6, 3, 0.4), (7, 2, -1.1), (8, 4, 2.2)])
+def test_clique_mixer_exponential(oracle_mod, n, k, beta):
+    s = oracle_mod.dicke_states(n, k).astype(np.int64)
+    Hs = dense_clique_mixer(n)[np.ix_(s, s)]
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal(len(s)) + 1j * rng.standard_normal(len(s))
+    ref = sla.expm(-1j * beta * Hs) @ v
+    got = oracle_mod.mixer_apply(n, v, beta, "clique", s)
+    np.testing.assert_allclose(got, ref, atol=1e-11 * np.abs(v).max())
+
+
 # -------------------------------------------------------- QAOA state, Eq. 1
 
 @pytest.mark.parametrize("n,p,seed", [(1, 1, 1), (3, 2, 2), (5, 3, 3), (8, 2, 4)])
@@ -347,9 +406,9 @@ def richardson_fd(f, x, h=1e-3):
     return g
 
 
-@pytest.mark.parametrize("case", ["maxcut_x", "sk_x", "dks_ring", "warm_x"])
+@pytest.mark.parametrize("case", ["maxcut_x", "sk_x", "dks_ring", "warm_x", "dks_clique"])
 def test_gradient_vs_finite_differences(oracle_mod, case):
-    rng = np.random.default_rng({"maxcut_x": 1, "sk_x": 2, "dks_ring": 3, "warm_x": 4}[case])
+    rng = np.random.default_rng({"maxcut_x": 1, "sk_x": 2, "dks_ring": 3, "warm_x": 4, "dks_clique": 5}[case])
     psi0 = None
     if case == "maxcut_x":
         n, p, mix, st = 7, 3, "x", None
@@ -362,6 +421,10 @@ def test_gradient_vs_finite_differences(oracle_mod, case):
         cost = oracle_mod.cost_maxcut(n, erdos_renyi(n, 0.7, 5))
         psi0 = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
         psi0 /= np.linalg.norm(psi0)
+    elif case == "dks_clique":
+        n, k, p, mix = 7, 3, 2, "clique"
+        st = oracle_mod.dicke_states(n, k)
+        cost = oracle_mod.cost_dks(n, erdos_renyi(n, 0.5, 8), st)
     else:
         n, k, p, mix = 7, 3, 2, "ring"
         st = oracle_mod.dicke_states(n, k)
