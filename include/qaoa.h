@@ -175,6 +175,13 @@ qaoa_status qaoa_dicke_states(qaoa_ctx *ctx, int n, int k, uint64_t *d_states, i
  * gives the d_V / d_lambda of a QAOA_MIXER_EIGEN mixer. */
 qaoa_status qaoa_ring_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, int64_t dim);
 
+/* Dense clique XY mixer sum_{i<j} (X_i X_j + Y_i Y_j) on the Hamming-weight-k
+ * states (Sec. 2.1), the matrix whose eigendecomposition a QAOA_MIXER_EIGEN
+ * mixer stores.  Element (a, b) = 2 when states a and b differ by exchanging
+ * one set and one clear bit, else 0.  d_H: device, dim x dim float64,
+ * row-major, dim = C(n, k), 2 <= n <= 40.  Synchronous. */
+qaoa_status qaoa_clique_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, int64_t dim);
+
 /* ----------------------------------------------------------- simulation */
 
 /* <C> of Eq. 1 for one angle set.

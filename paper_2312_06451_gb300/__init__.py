@@ -24,7 +24,8 @@ from ._binding import QAOAError  # noqa: F401
 
 __all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError", "pass_schedule",
            "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched",
-           "qaoa_gradient_small_noalloc", "ring_eigen_mixer", "save_eigen_mixer", "load_eigen_mixer"]
+           "qaoa_gradient_small_noalloc", "ring_eigen_mixer", "clique_eigen_mixer", "xy_eigen_mixer",
+           "save_eigen_mixer", "load_eigen_mixer"]
 
 _PROBLEMS = {"maxcut": B.QAOA_PROBLEM_MAXCUT, "wmaxcut": B.QAOA_PROBLEM_WMAXCUT,
              "sk": B.QAOA_PROBLEM_SK, "dks": B.QAOA_PROBLEM_DKS}
@@ -113,25 +114,39 @@ def load_eigen_mixer(path: str, n: int, k: int, kind: str = "ring", device: int 
     return torch.from_numpy(V).to(dev), torch.from_numpy(lam).to(dev)
 
 
-def ring_eigen_mixer(ctx: "Context", n: int, k: int, precision: str = "fp32", cache_file: str | None = None):
-    """EigenMixer of the ring mixer on the Hamming-weight-k states.
+def xy_eigen_mixer(ctx: "Context", kind: str, n: int, k: int, precision: str = "fp32",
+                   cache_file: str | None = None):
+    """EigenMixer of the ring or clique XY mixer on the Hamming-weight-k states.
 
-    Pre-computation (Sec. 2.1, done once): the dense ring Hamiltonian is built
-    by the library (qaoa_ring_hamiltonian) and diagonalised in float64 with
-    torch.linalg.eigh; V is kept in float32, the eigenvalues in float64.  With
-    cache_file the decomposition is loaded from / saved to that file."""
+    Pre-computation (Sec. 2.1, done once): the dense Hamiltonian is built by
+    the library (qaoa_ring_hamiltonian / qaoa_clique_hamiltonian) and
+    diagonalised in float64 with torch.linalg.eigh; V is kept in float32, the
+    eigenvalues in float64.  With cache_file the decomposition is loaded from /
+    saved to that file (Sec. 3: mixer_clique(...; file))."""
     import os
 
+    if kind not in ("ring", "clique"):
+        raise ValueError(f"unknown XY mixer {kind!r}")
     if cache_file and os.path.exists(cache_file):
-        V, lam = load_eigen_mixer(cache_file, n, k, "ring", ctx.device)
+        V, lam = load_eigen_mixer(cache_file, n, k, kind, ctx.device)
     else:
-        H = ctx.ring_hamiltonian(n, k)
+        H = ctx.ring_hamiltonian(n, k) if kind == "ring" else ctx.clique_hamiltonian(n, k)
         lam, V64 = torch.linalg.eigh(H)
         V = V64.to(torch.float32).contiguous()
         del V64, H
         if cache_file:
-            save_eigen_mixer(cache_file, n, k, V, lam, "ring")
+            save_eigen_mixer(cache_file, n, k, V, lam, kind)
     return EigenMixer(n, V.contiguous(), lam.contiguous(), precision)
+
+
+def ring_eigen_mixer(ctx: "Context", n: int, k: int, precision: str = "fp32", cache_file: str | None = None):
+    """EigenMixer of the ring mixer (see xy_eigen_mixer)."""
+    return xy_eigen_mixer(ctx, "ring", n, k, precision, cache_file)
+
+
+def clique_eigen_mixer(ctx: "Context", n: int, k: int, precision: str = "fp32", cache_file: str | None = None):
+    """EigenMixer of the clique mixer (see xy_eigen_mixer)."""
+    return xy_eigen_mixer(ctx, "clique", n, k, precision, cache_file)
 
 
 class Context:
@@ -206,6 +221,13 @@ class Context:
         dim = int(round(np.prod([(n - i) / (i + 1) for i in range(k)]))) if k > 0 else 1
         out = torch.empty((dim, dim), dtype=torch.float64, device=f"cuda:{self.device}")
         self._check(self._lib.qaoa_ring_hamiltonian(self._h, n, k, _ptr(out), dim))
+        return out
+
+    def clique_hamiltonian(self, n: int, k: int) -> torch.Tensor:
+        """Dense clique mixer on the weight-k states (float64 CUDA tensor)."""
+        dim = int(round(np.prod([(n - i) / (i + 1) for i in range(k)]))) if k > 0 else 1
+        out = torch.empty((dim, dim), dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(self._lib.qaoa_clique_hamiltonian(self._h, n, k, _ptr(out), dim))
         return out
 
     # ---------------------------------------------------------- simulation

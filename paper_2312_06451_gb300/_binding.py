@@ -61,6 +61,7 @@ SIGNATURES = {
     "qaoa_cost_precompute": (c_int, [c_void_p, ctypes.POINTER(QaoaProblem), c_void_p, c_int, c_int64]),
     "qaoa_dicke_states": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int64]),
     "qaoa_ring_hamiltonian": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int64]),
+    "qaoa_clique_hamiltonian": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int64]),
     "qaoa_expectation": (c_int, [c_void_p, c_void_p, c_int, ctypes.POINTER(QaoaMixer), c_void_p, c_int,
                                  c_void_p, c_void_p]),
     "qaoa_gradient": (c_int, [c_void_p, c_void_p, c_int, ctypes.POINTER(QaoaMixer), c_void_p, c_int,

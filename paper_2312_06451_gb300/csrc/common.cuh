@@ -203,6 +203,7 @@ cudaError_t launch_cost_dks(int n, int k, const uint64_t *nbr_hi_host, int64_t d
                             int dtype, cudaStream_t s);
 cudaError_t launch_dicke_states(int n, int k, int64_t dim, uint64_t *d_out, cudaStream_t s);
 cudaError_t launch_ring_hamiltonian(int n, int k, int64_t dim, double *d_H, cudaStream_t s);
+cudaError_t launch_clique_hamiltonian(int n, int k, int64_t dim, double *d_H, cudaStream_t s);
 int binom_table_max();
 cudaError_t upload_binom_table();
 

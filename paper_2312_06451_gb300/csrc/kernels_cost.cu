@@ -167,6 +167,23 @@ __global__ void ring_h_kernel(int n, int k, int64_t dim, double *H) {
     }
 }
 
+// Row a of the clique mixer restricted to weight-k states: the same swap
+// term on every pair i < j whose bits differ.
+__global__ void clique_h_kernel(int n, int k, int64_t dim, double *H) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < dim;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = unrank_colex(a, n, k);
+        for (int i = 0; i < n; i++) {
+            if (!((x >> i) & 1)) continue;  // i: a set bit, j: a clear bit
+            for (int j = 0; j < n; j++) {
+                if ((x >> j) & 1) continue;
+                const uint64_t y = x ^ (1ull << i) ^ (1ull << j);
+                H[a * dim + rank_colex(y)] += 2.0;
+            }
+        }
+    }
+}
+
 unsigned grid_for(int64_t dim, int threads) {
     int64_t b = (dim + threads - 1) / threads;
     if (b > 152 * 64) b = 152 * 64;
@@ -220,6 +237,13 @@ cudaError_t launch_ring_hamiltonian(int n, int k, int64_t dim, double *d_H, cuda
     cudaError_t e = cudaMemsetAsync(d_H, 0, (size_t)dim * (size_t)dim * sizeof(double), s);
     if (e != cudaSuccess) return e;
     ring_h_kernel<<<grid_for(dim, 128), 128, 0, s>>>(n, k, dim, d_H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clique_hamiltonian(int n, int k, int64_t dim, double *d_H, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_H, 0, (size_t)dim * (size_t)dim * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    clique_h_kernel<<<grid_for(dim, 128), 128, 0, s>>>(n, k, dim, d_H);
     return cudaGetLastError();
 }
 

@@ -1469,6 +1469,23 @@ qaoa_status qaoa_ring_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, int6
     return QAOA_OK;
 }
 
+qaoa_status qaoa_clique_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, int64_t dim) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    ctx->err.clear();
+    if (n < 2 || n > binom_table_max() || k < 0 || k > n || !d_H)
+        return fail(ctx, QAOA_ERR_INVALID, "clique mixer needs 2 <= n <= %d and 0 <= k <= n",
+                    binom_table_max());
+    double b = 1;
+    for (int i = 0; i < k; i++) b = b * (n - i) / (i + 1);
+    if (dim != (int64_t)std::llround(b)) return fail(ctx, QAOA_ERR_INVALID, "dim must be binom(n,k)");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = launch_clique_hamiltonian(n, k, dim, d_H, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "clique kernel launch");
+    ctx->launches++;
+    QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "clique hamiltonian");
+    return QAOA_OK;
+}
+
 qaoa_status qaoa_expectation(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const qaoa_mixer *mixer,
                              const void *d_init, int p, const double *angles, double *E) {
     if (!ctx) return QAOA_ERR_INVALID;

@@ -1,7 +1,7 @@
 """Parity of the eigenbasis (constrained) mixer path with the CPU oracle.
 
 The GPU path applies e^{-i b H_M} as V e^{-i b lambda} V^T with V from a
-float64 eigendecomposition of the ring Hamiltonian (Sec. 2.1, 2.2); the oracle
+float64 eigendecomposition of the ring or clique Hamiltonian (Sec. 2.1, 2.2); the oracle
 applies the same exponential by its power series, never forming V.  Densest
 k-subgraph costs on the Dicke subspace, uniform Dicke initial state.
 Tolerances as everywhere: |dE| <= 1e-5 max(|E|, sigma_C), |dg| <= 1e-4 max(|g|, sigma_C).
@@ -31,13 +31,37 @@ def sigma(c):
     return float(np.sqrt(np.mean(np.asarray(c, dtype=np.float64) ** 2)))
 
 
-def problem(qg, ctx, oracle_mod, n, k, seed, precision="fp32"):
+def problem(qg, ctx, oracle_mod, n, k, seed, precision="fp32", kind="ring"):
     e = erdos_renyi(n, 0.5, seed)
     st = oracle_mod.dicke_states(n, k)
     c = oracle_mod.cost_dks(n, e, st)
     dc = ctx.cost_precompute("dks", n, edges=e, k=k, dtype=torch.uint8)
-    mixer = qg.ring_eigen_mixer(ctx, n, k, precision=precision)
+    mixer = qg.xy_eigen_mixer(ctx, kind, n, k, precision=precision)
     return st, c, dc, mixer
+
+
+@pytest.mark.parametrize("kind", ["ring", "clique"])
+@pytest.mark.parametrize("n,k", [(5, 2), (8, 4), (9, 3)])
+def test_xy_hamiltonian_matches_oracle(Q, oracle_mod, kind, n, k):
+    """The library's dense mixer equals the oracle's H_M applied to basis vectors."""
+    qg, ctx = Q
+    H = (ctx.ring_hamiltonian(n, k) if kind == "ring" else ctx.clique_hamiltonian(n, k)).cpu().numpy()
+    st = oracle_mod.dicke_states(n, k)
+    D = len(st)
+    ref = np.stack([oracle_mod.hm_apply(n, np.eye(D)[i], kind, st) for i in range(D)], axis=1).real
+    np.testing.assert_array_equal(H, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "3xtf32"])
+@pytest.mark.parametrize("n,k,p", [(8, 4, 3), (10, 3, 2)])
+def test_clique_mixer_expectation_and_gradient(Q, oracle_mod, n, k, p, precision):
+    qg, ctx = Q
+    st, c, dc, mixer = problem(qg, ctx, oracle_mod, n, k, 90 + n, precision, "clique")
+    ang = uniform_angles(p, 91 + n)[0]
+    E, g = ctx.gradient(dc, mixer, ang)
+    E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, ang, "clique", st)
+    assert abs(E - E_ref) <= 1e-5 * max(abs(E_ref), sigma(c)), (E, E_ref)
+    np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-4 * max(np.abs(g_ref).max(), sigma(c)))
 
 
 PRECISIONS = ["fp32", "3xtf32"]
