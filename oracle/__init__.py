@@ -23,7 +23,8 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 MIXER_X = 0
 MIXER_RING = 1
 MIXER_CLIQUE = 2
-_MIXERS = {"x": MIXER_X, "ring": MIXER_RING, "clique": MIXER_CLIQUE}
+MIXER_GROVER = 3
+_MIXERS = {"x": MIXER_X, "ring": MIXER_RING, "clique": MIXER_CLIQUE, "grover": MIXER_GROVER}
 
 _lock = threading.Lock()
 _lib = None
@@ -61,6 +62,7 @@ def _load():
             "oracle_cost_maxcut": (None, [i32, i32, P, P, i64, P, P]),
             "oracle_cost_sk": (None, [i32, P, i64, P, P]),
             "oracle_cost_dks": (None, [i32, i32, P, i64, P, P]),
+            "oracle_cost_kvc": (None, [i32, i32, P, i64, P, P]),
             "oracle_qaoa_state": (i32, [i32, i32, i64, P, P, i32, P, P, P]),
             "oracle_qaoa_expectation": (f64, [i32, i32, i64, P, P, i32, P, P]),
             "oracle_qaoa_gradient": (i32, [i32, i32, i64, P, P, i32, P, P, P, P]),
@@ -135,15 +137,102 @@ def cost_dks(n, edges, states) -> np.ndarray:
     return out
 
 
+def cost_kvc(n, edges, states) -> np.ndarray:
+    dim, states = _states_dim(n, states)
+    e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+    out = np.empty(dim, dtype=np.float64)
+    _load().oracle_cost_kvc(n, e.shape[0], _ptr(e), dim, _ptr(states), _ptr(out))
+    return out
+
+
+def cost_degeneracy(n, edges, problem, k=None, n_bins=None, method=None) -> np.ndarray:
+    """Number of feasible states with each integer cost value 0..n_bins-1, by
+    brute force over every feasible state (Sec. 2.4: Grover-QAOA needs only
+    the distinct values and their degeneracies).  problem: "maxcut" (all 2^n
+    states), "dks" or "kvc" (the C(n, k) weight-k states).  Up to 64 qubits
+    from the oracle's cost vectors; above that (weight-k only) from all
+    k-subsets drawn with itertools, the cost counted from an adjacency matrix."""
+    import itertools
+
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    if method is None:
+        method = "states" if (problem == "maxcut" or n <= 40) else "subsets"
+    if method == "states":
+        if problem == "maxcut":
+            c = cost_maxcut(n, e)
+        else:
+            st = dicke_states(n, k)
+            c = cost_dks(n, e, st) if problem == "dks" else cost_kvc(n, e, st)
+    else:
+        if problem == "maxcut":
+            raise ValueError("brute force over 2^n states needs n <= 64")
+        A = np.zeros((n, n), dtype=np.int64)
+        A[e[:, 0], e[:, 1]] = 1
+        A[e[:, 1], e[:, 0]] = 1
+        deg = A.sum(axis=1)
+        chunks = []
+        it = itertools.combinations(range(n), k)
+        while True:
+            block = np.array(list(itertools.islice(it, 1 << 18)), dtype=np.int64).reshape(-1, k)
+            if block.shape[0] == 0:
+                break
+            inside = np.zeros(block.shape[0], dtype=np.int64)
+            for a in range(k):
+                for b in range(a + 1, k):
+                    inside += A[block[:, a], block[:, b]]
+            if problem == "dks":
+                chunks.append(inside)
+            else:  # covered edges = sum of degrees - edges counted twice
+                chunks.append(deg[block].sum(axis=1) - inside)
+        c = np.concatenate(chunks)
+    c = np.rint(c).astype(np.int64)
+    nb = int(c.max()) + 1 if n_bins is None else n_bins
+    return np.bincount(c, minlength=nb)[:nb].astype(np.int64)
+
+
+def grover_reduced_gradient(counts, angles, values=None):
+    """<C> and its 2p derivatives for QAOA with the Grover mixer and the
+    uniform initial state, on the distinct cost values (Sec. 2.4).
+
+    Fair sampling: every state of cost c_j keeps one amplitude, so the
+    weighted vector b_j = sqrt(d_j) a_j (d_j = degeneracy, N = sum d) evolves
+    as a QAOA on len(counts) states with cost diag(c_j), initial state
+    u_j = sqrt(d_j / N) and mixer H_G = u u^T.  Plain complex128 reverse mode,
+    the same recurrences as the full-state oracle."""
+    d = np.asarray(counts, dtype=np.float64)
+    c = np.arange(d.shape[0], dtype=np.float64) if values is None else np.asarray(values, dtype=np.float64)
+    a = np.asarray(angles, dtype=np.float64)
+    p = a.shape[0] // 2
+    u = np.sqrt(d / d.sum())
+
+    def mix(v, beta):
+        return v + (np.exp(-1j * beta) - 1.0) * np.dot(u, v) * u
+
+    psi = u.astype(np.complex128)
+    for k in range(p):
+        psi = np.exp(-1j * a[p + k] * c) * psi
+        psi = mix(psi, a[k])
+    E = float(np.sum(c * np.abs(psi) ** 2))
+    lam = c * psi
+    g = np.zeros(2 * p)
+    for k in range(p - 1, -1, -1):
+        g[k] = 2.0 * np.imag(np.conj(np.dot(u, lam)) * np.dot(u, psi))
+        lam, psi = mix(lam, -a[k]), mix(psi, -a[k])
+        g[p + k] = 2.0 * np.imag(np.sum(np.conj(lam) * c * psi))
+        ph = np.exp(1j * a[p + k] * c)
+        lam, psi = ph * lam, ph * psi
+    return E, g
+
+
 def _problem(mixer, n, cost, states):
     kind = _MIXERS[mixer]
     cost = _f64(cost)
-    if kind != MIXER_X:
+    if kind in (MIXER_RING, MIXER_CLIQUE):
         if states is None:
             raise ValueError(f"the {mixer} mixer needs the feasible states")
         states = np.ascontiguousarray(states, dtype=np.uint64)
     else:
-        states = None
+        states = None  # X: all 2^n states; Grover: whatever set the cost vector covers
     return kind, cost, states, cost.shape[0]
 
 

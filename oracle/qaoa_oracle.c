@@ -46,7 +46,7 @@
 
 typedef double complex cplx;
 
-enum { ORACLE_MIXER_X = 0, ORACLE_MIXER_RING = 1, ORACLE_MIXER_CLIQUE = 2 };
+enum { ORACLE_MIXER_X = 0, ORACLE_MIXER_RING = 1, ORACLE_MIXER_CLIQUE = 2, ORACLE_MIXER_GROVER = 3 };
 
 /* ------------------------------------------------------------------ threads */
 
@@ -145,10 +145,25 @@ void oracle_cost_dks(int n, int m, const int32_t *edges, int64_t dim,
     }
 }
 
+/* Max k-vertex cover (Sec. 2.1, a Hamming-weight-k problem): number of edges
+ * with at least one endpoint selected. */
+void oracle_cost_kvc(int n, int m, const int32_t *edges, int64_t dim,
+                     const uint64_t *states, double *out) {
+    (void)n;
+#pragma omp parallel for schedule(static)
+    for (int64_t a = 0; a < dim; a++) {
+        uint64_t x = state_at(states, a);
+        double c = 0.0;
+        for (int e = 0; e < m; e++)
+            if (bit(x, edges[2 * e]) || bit(x, edges[2 * e + 1])) c += 1.0;
+        out[a] = c;
+    }
+}
+
 /* ---------------------------------------------------------------- mixers */
 
 typedef struct {
-    int kind;               /* ORACLE_MIXER_X, _RING or _CLIQUE */
+    int kind;               /* ORACLE_MIXER_X, _RING, _CLIQUE or _GROVER */
     int n;
     int64_t dim;
     const uint64_t *states; /* ring, clique: the sorted Hamming-weight-k states */
@@ -173,9 +188,17 @@ static int64_t find_state(const mixer_t *mx, uint64_t s) {
  * matrix element 2 and annihilates |00>, |11>; so on a basis state it swaps
  * bits i and j with weight 2 when they differ.  The ring is read as periodic
  * (edge n-1 -- 0 included), coefficient 1 per edge.
- * Clique mixer (Sec. 2.1): the same two-qubit term on every pair i < j. */
+ * Clique mixer (Sec. 2.1): the same two-qubit term on every pair i < j.
+ * Grover mixer (Sec. 2.4): H_G = |u><u| with u the uniform superposition over
+ * the feasible set, so (H_G v)_a = (sum_b v_b) / dim. */
 static void hm_apply(const mixer_t *mx, const cplx *v, cplx *out) {
     const int n = mx->n;
+    if (mx->kind == ORACLE_MIXER_GROVER) {
+        cplx s = 0.0;
+        for (int64_t a = 0; a < mx->dim; a++) s += v[a];
+        for (int64_t a = 0; a < mx->dim; a++) out[a] = s / (double)mx->dim;
+        return;
+    }
     if (mx->kind == ORACLE_MIXER_X) {
 #pragma omp parallel for schedule(static)
         for (int64_t x = 0; x < mx->dim; x++) {
@@ -224,6 +247,14 @@ static void hm_apply(const mixer_t *mx, const cplx *v, cplx *out) {
  * for the clique (a weight-k state has k (n - k) pairs of differing bits). */
 static void mixer_apply(const mixer_t *mx, double beta, cplx *v, cplx *tmp1, cplx *tmp2) {
     const int64_t dim = mx->dim;
+    if (mx->kind == ORACLE_MIXER_GROVER) {
+        /* H_G is a projector: e^{-i beta H_G} = I + (e^{-i beta} - 1) |u><u| */
+        cplx s = 0.0;
+        for (int64_t a = 0; a < dim; a++) s += v[a];
+        const cplx d = (cexp(-I * beta) - 1.0) * s / (double)dim;
+        for (int64_t a = 0; a < dim; a++) v[a] += d;
+        return;
+    }
     if (mx->kind == ORACLE_MIXER_X) {
         const double c = cos(beta), s = sin(beta);
         for (int i = 0; i < mx->n; i++) {
@@ -286,6 +317,7 @@ static int make_mixer(mixer_t *mx, int kind, int n, int64_t dim, const uint64_t 
     if (kind == ORACLE_MIXER_X) return dim == ((int64_t)1 << n) ? 0 : -1;
     if (kind == ORACLE_MIXER_RING) return (states && n >= 3) ? 0 : -1;
     if (kind == ORACLE_MIXER_CLIQUE) return (states && n >= 2 && dim >= 1) ? 0 : -1;
+    if (kind == ORACLE_MIXER_GROVER) return dim >= 1 ? 0 : -1;
     return -1;
 }
 

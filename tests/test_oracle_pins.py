@@ -263,6 +263,103 @@ def test_clique_mixer_exponential(oracle_mod, n, k, beta):
     np.testing.assert_allclose(got, ref, atol=1e-11 * np.abs(v).max())
 
 
+# ------------------------------------------------ Grover mixer (Sec. 2.4)
+
+@pytest.mark.parametrize("space", ["full6", "dicke8_3"])
+def test_grover_mixer_is_projector_exponential(oracle_mod, space):
+    if space == "full6":
+        n, dim, st = 6, 64, None
+    else:
+        st = oracle_mod.dicke_states(8, 3)
+        n, dim = 8, len(st)
+    u = np.full(dim, 1 / math.sqrt(dim))
+    H = np.outer(u, u)
+    rng = np.random.default_rng(8)
+    v = rng.standard_normal(dim) + 1j * rng.standard_normal(dim)
+    np.testing.assert_allclose(oracle_mod.hm_apply(n, v, "grover", st), H @ v, atol=1e-13)
+    for beta in (0.3, -2.1):
+        np.testing.assert_allclose(oracle_mod.mixer_apply(n, v, beta, "grover", st),
+                                   sla.expm(-1j * beta * H) @ v, atol=1e-12)
+
+
+def _grover_cases(oracle_mod):
+    e10 = erdos_renyi(10, 0.5, 21)
+    st4 = oracle_mod.dicke_states(10, 4)
+    e9 = erdos_renyi(9, 0.4, 22)
+    st3 = oracle_mod.dicke_states(9, 3)
+    return {
+        "maxcut10": (10, oracle_mod.cost_maxcut(10, e10), None, ("maxcut", e10, None)),
+        "dks10_4": (10, oracle_mod.cost_dks(10, e10, st4), st4, ("dks", e10, 4)),
+        "kvc9_3": (9, oracle_mod.cost_kvc(9, e9, st3), st3, ("kvc", e9, 3)),
+    }
+
+
+@pytest.mark.parametrize("case", ["maxcut10", "dks10_4", "kvc9_3"])
+def test_grover_reduced_equals_full_state(oracle_mod, case):
+    """Fair sampling (Sec. 2.4): the reduced simulation on (value, degeneracy)
+    pairs gives the full-state <C> and gradient."""
+    n, cost, st, (prob, e, k) = _grover_cases(oracle_mod)[case]
+    counts = oracle_mod.cost_degeneracy(n, e, prob, k)
+    assert counts.sum() == len(cost)
+    ang = np.random.default_rng(9).random(6) * np.pi
+    E_full, g_full = oracle_mod.qaoa_gradient(n, cost, ang, "grover", st)
+    E_red, g_red = oracle_mod.grover_reduced_gradient(counts, ang)
+    assert E_red == pytest.approx(E_full, abs=1e-11)
+    np.testing.assert_allclose(g_red, g_full, atol=1e-10)
+
+
+def test_grover_p1_closed_form(oracle_mod):
+    """p = 1 by hand: after the phase, s = sum_j w_j e^{-i g c_j} (w_j = d_j / N)
+    is the overlap with the uniform state, and every state of value c_j has
+    amplitude (e^{-i g c_j} + (e^{-i b} - 1) s) / sqrt(N)."""
+    n, cost, st, (prob, e, k) = _grover_cases(oracle_mod)["maxcut10"]
+    counts = oracle_mod.cost_degeneracy(n, e, prob, k)
+    w = counts / counts.sum()
+    c = np.arange(len(counts))
+    for b, g in [(0.7, 0.4), (2.0, -1.3)]:
+        s = np.sum(w * np.exp(-1j * g * c))
+        ref = np.sum(w * np.abs(np.exp(-1j * g * c) + (np.exp(-1j * b) - 1) * s) ** 2 * c)
+        assert oracle_mod.qaoa_expectation(n, cost, [b, g], "grover") == pytest.approx(ref, abs=1e-11)
+        assert oracle_mod.grover_reduced_gradient(counts, [b, g])[0] == pytest.approx(ref, abs=1e-11)
+
+
+def test_kvc_cost_definition(oracle_mod):
+    n, k = 7, 3
+    e = erdos_renyi(n, 0.5, 23)
+    st = oracle_mod.dicke_states(n, k)
+    got = oracle_mod.cost_kvc(n, e, st)
+    for a, x in enumerate(st):
+        chosen = {i for i in range(n) if (int(x) >> i) & 1}
+        assert got[a] == sum(1 for u, v in e if u in chosen or v in chosen)
+
+
+@pytest.mark.parametrize("prob,n,k", [("dks", 12, 4), ("kvc", 11, 3), ("dks", 9, 9), ("kvc", 10, 1)])
+def test_degeneracy_two_enumerations_and_sum_rules(oracle_mod, prob, n, k):
+    e = erdos_renyi(n, 0.5, 24)
+    m = len(e)
+    a = oracle_mod.cost_degeneracy(n, e, prob, k, n_bins=m + 1, method="states")
+    b = oracle_mod.cost_degeneracy(n, e, prob, k, n_bins=m + 1, method="subsets")
+    np.testing.assert_array_equal(a, b)
+    N = math.comb(n, k)
+    assert a.sum() == N
+    mean = np.dot(np.arange(m + 1), a) / N
+    if prob == "dks":  # each edge lies inside a random k-set with prob C(n-2,k-2)/C(n,k)
+        ref = m * (math.comb(n - 2, k - 2) if k >= 2 else 0) / N
+    else:  # each edge is missed with prob C(n-2,k)/C(n,k)
+        ref = m * (1 - math.comb(n - 2, k) / N)
+    assert mean == pytest.approx(ref, rel=1e-12)
+
+
+def test_maxcut_degeneracy_sum_rule(oracle_mod):
+    n = 12
+    e = erdos_renyi(n, 0.5, 25)
+    d = oracle_mod.cost_degeneracy(n, e, "maxcut")
+    assert d.sum() == 1 << n
+    assert np.dot(np.arange(len(d)), d) / (1 << n) == pytest.approx(len(e) / 2, rel=1e-12)
+    # a cut and its complement have the same value: every count is even
+    assert np.all(d % 2 == 0)
+
+
 # -------------------------------------------------------- QAOA state, Eq. 1
 
 @pytest.mark.parametrize("n,p,seed", [(1, 1, 1), (3, 2, 2), (5, 3, 3), (8, 2, 4)])
@@ -406,9 +503,10 @@ def richardson_fd(f, x, h=1e-3):
     return g
 
 
-@pytest.mark.parametrize("case", ["maxcut_x", "sk_x", "dks_ring", "warm_x", "dks_clique"])
+@pytest.mark.parametrize("case", ["maxcut_x", "sk_x", "dks_ring", "warm_x", "dks_clique", "maxcut_grover"])
 def test_gradient_vs_finite_differences(oracle_mod, case):
-    rng = np.random.default_rng({"maxcut_x": 1, "sk_x": 2, "dks_ring": 3, "warm_x": 4, "dks_clique": 5}[case])
+    rng = np.random.default_rng({"maxcut_x": 1, "sk_x": 2, "dks_ring": 3, "warm_x": 4, "dks_clique": 5,
+                                 "maxcut_grover": 6}[case])
     psi0 = None
     if case == "maxcut_x":
         n, p, mix, st = 7, 3, "x", None
@@ -421,6 +519,9 @@ def test_gradient_vs_finite_differences(oracle_mod, case):
         cost = oracle_mod.cost_maxcut(n, erdos_renyi(n, 0.7, 5))
         psi0 = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
         psi0 /= np.linalg.norm(psi0)
+    elif case == "maxcut_grover":
+        n, p, mix, st = 7, 3, "grover", None
+        cost = oracle_mod.cost_maxcut(n, erdos_renyi(n, 0.5, 7))
     elif case == "dks_clique":
         n, k, p, mix = 7, 3, 2, "clique"
         st = oracle_mod.dicke_states(n, k)
