@@ -80,12 +80,15 @@ enum {
  *   SK     : C(x) = sum_{i<j} J_ij z_i z_j, z_i = 1 - 2 x_i; an arbitrary user
  *            cost, which the paper allows for any function of x (Sec. 3).
  *   DKS    : densest k-subgraph, C(x) = #{edges (u,v) : x_u = x_v = 1} on the
- *            Hamming-weight-k states (Sec. 2.1, Listing 2). */
+ *            Hamming-weight-k states (Sec. 2.1, Listing 2).
+ *   KVC    : max k-vertex cover, C(x) = #{edges (u,v) : x_u = 1 or x_v = 1} on
+ *            the Hamming-weight-k states (Sec. 2.1). */
 enum {
     QAOA_PROBLEM_MAXCUT = 0,
     QAOA_PROBLEM_WMAXCUT = 1,
     QAOA_PROBLEM_SK = 2,
-    QAOA_PROBLEM_DKS = 3
+    QAOA_PROBLEM_DKS = 3,
+    QAOA_PROBLEM_KVC = 4
 };
 
 /* Mixer kinds. */
@@ -285,6 +288,33 @@ qaoa_status qaoa_autotune_x(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, i
  * split 0, one adjoint buffer. */
 qaoa_status qaoa_set_xtune(qaoa_ctx *ctx, const qaoa_xtune *t);
 qaoa_status qaoa_get_xtune(qaoa_ctx *ctx, int n, int cost_dtype, qaoa_xtune *out);
+
+/* ------------------------------------------ Grover mixer on degeneracies */
+
+/* Degeneracies of an integer cost over the feasible set (Sec. 2.4): with the
+ * Grover mixer H_G = |u><u| (u the uniform superposition over the feasible
+ * set) and the uniform initial state, all states of equal cost keep equal
+ * amplitudes, so the QAOA needs only the distinct values and their counts.
+ *   prob      MAXCUT with k = -1 over all 2^n states (n <= 44), or DKS / KVC
+ *             over the Hamming-weight-k states (n <= 128, C(n, k) <= 2^44)
+ *   d_counts  device, n_bins int64: zeroed, then d_counts[c] = number of
+ *             feasible states with cost c; n_bins must exceed the edge count
+ *             (the largest possible cost) and be at most 4096
+ * Synchronous on the context stream.  Valid input never yields a cost outside
+ * [0, n_bins); the kernel checks it anyway and reports QAOA_ERR_CUDA. */
+qaoa_status qaoa_cost_degeneracy(qaoa_ctx *ctx, const qaoa_problem *prob, int64_t *d_counts, int n_bins);
+
+/* <C> (and, when d_grad != NULL, all 2p derivatives) of QAOA with the Grover
+ * mixer and the uniform initial state, for n_sets angle sets, from the
+ * degeneracies d_counts[0..n_bins) of the cost values 0..n_bins-1 (as written
+ * by qaoa_cost_degeneracy; other integer costs may be counted by the caller).
+ *   d_angles  device, n_sets x 2p float64 [beta_1..beta_p, gamma_1..gamma_p]
+ *   d_E       device output, n_sets float64
+ *   d_grad    device output, n_sets x 2p float64, or NULL
+ * Float64 throughout (the reduced vector holds one amplitude per value).
+ * Asynchronous on the context stream; a non-finite angle gives NaN results. */
+qaoa_status qaoa_grover_batched(qaoa_ctx *ctx, const int64_t *d_counts, int n_bins, int p, int n_sets,
+                                const double *d_angles, double *d_E, double *d_grad);
 
 /* ------------------------------------------------ allocation-free variant */
 

@@ -28,7 +28,7 @@ __all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError", "p
            "save_eigen_mixer", "load_eigen_mixer"]
 
 _PROBLEMS = {"maxcut": B.QAOA_PROBLEM_MAXCUT, "wmaxcut": B.QAOA_PROBLEM_WMAXCUT,
-             "sk": B.QAOA_PROBLEM_SK, "dks": B.QAOA_PROBLEM_DKS}
+             "sk": B.QAOA_PROBLEM_SK, "dks": B.QAOA_PROBLEM_DKS, "kvc": B.QAOA_PROBLEM_KVC}
 _GEMM = {"fp32": B.QAOA_GEMM_FP32_SIMT, "3xtf32": B.QAOA_GEMM_3XTF32, "bf16x3": B.QAOA_GEMM_BF16X3}
 
 
@@ -196,7 +196,7 @@ class Context:
         w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
         Jh = None if J is None else np.ascontiguousarray(J, dtype=np.float32).reshape(n, n)
         m = 0 if e is None else e.shape[0]
-        if kind == B.QAOA_PROBLEM_DKS:
+        if kind in (B.QAOA_PROBLEM_DKS, B.QAOA_PROBLEM_KVC):
             dim = int(np.round(np.prod([(n - i) / (i + 1) for i in range(k)]))) if k > 0 else 1
         else:
             dim = 1 << n
@@ -208,6 +208,35 @@ class Context:
         self._check(self._lib.qaoa_cost_precompute(self._h, ctypes.byref(prob), _ptr(out),
                                                    _cost_dtype(out), dim))
         return out
+
+    def cost_degeneracy(self, problem: str, n: int, *, edges, k: int = -1, n_bins: int | None = None) -> torch.Tensor:
+        """Number of feasible states with each cost value 0..n_bins-1 as an
+        int64 CUDA tensor (qaoa_cost_degeneracy): "maxcut" over all 2^n states
+        (k = -1), "dks" / "kvc" over the weight-k states (n <= 128)."""
+        kind = _PROBLEMS[problem]
+        e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+        m = e.shape[0]
+        nb = m + 1 if n_bins is None else int(n_bins)
+        out = torch.empty(nb, dtype=torch.int64, device=f"cuda:{self.device}")
+        prob = B.QaoaProblem(kind, n, k, m, e.ctypes.data_as(ctypes.c_void_p), None, None)
+        self._check(self._lib.qaoa_cost_degeneracy(self._h, ctypes.byref(prob), _ptr(out), nb))
+        return out
+
+    def grover_batched(self, counts: torch.Tensor, angles: torch.Tensor, want_grad: bool = True):
+        """(E, grad) CUDA float64 tensors for QAOA with the Grover mixer on the
+        degeneracies `counts` (qaoa_grover_batched); angles: n_sets x 2p
+        float64 CUDA tensor.  Asynchronous on the context stream."""
+        counts = _dev_tensor(counts, "counts")
+        A = _dev_tensor(angles, "angles")
+        if counts.dtype != torch.int64 or A.dtype != torch.float64:
+            raise TypeError("counts must be int64 and angles float64")
+        A = A.reshape(-1, A.shape[-1]).contiguous()
+        S, p2 = A.shape
+        E = torch.empty(S, dtype=torch.float64, device=A.device)
+        G = torch.empty(S, p2, dtype=torch.float64, device=A.device) if want_grad else None
+        self._check(self._lib.qaoa_grover_batched(self._h, _ptr(counts), counts.shape[0], p2 // 2, S, _ptr(A),
+                                                  _ptr(E), _ptr(G)))
+        return E, G
 
     def dicke_states(self, n: int, k: int) -> torch.Tensor:
         """Hamming-weight-k states in increasing order (int64 CUDA tensor)."""

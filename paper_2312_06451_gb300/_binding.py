@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "QAOA_OK", 1: "QAOA_ERR_INVALID", 2: "QAOA_ERR_OOM", 3: "QAOA
                 4: "QAOA_ERR_TIMEOUT", 5: "QAOA_ERR_UNSUPPORTED"}
 
 QAOA_COST_F32, QAOA_COST_U8 = 0, 1
-QAOA_PROBLEM_MAXCUT, QAOA_PROBLEM_WMAXCUT, QAOA_PROBLEM_SK, QAOA_PROBLEM_DKS = 0, 1, 2, 3
+QAOA_PROBLEM_MAXCUT, QAOA_PROBLEM_WMAXCUT, QAOA_PROBLEM_SK, QAOA_PROBLEM_DKS, QAOA_PROBLEM_KVC = 0, 1, 2, 3, 4
 QAOA_MIXER_X, QAOA_MIXER_EIGEN = 0, 1
 QAOA_GEMM_FP32_SIMT, QAOA_GEMM_3XTF32, QAOA_GEMM_BF16X3 = 0, 1, 2
 QAOA_CKPT_NONE, QAOA_CKPT_ROUND, QAOA_CKPT_PASS = 0, 1, 2
@@ -74,6 +74,8 @@ SIGNATURES = {
     "qaoa_gradient_small_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                             c_void_p]),
     "qaoa_set_checkpointing": (c_int, [c_void_p, c_int]),
+    "qaoa_cost_degeneracy": (c_int, [c_void_p, ctypes.POINTER(QaoaProblem), c_void_p, c_int]),
+    "qaoa_grover_batched": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "qaoa_pass_schedule": (c_int, [c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int]),
     "qaoa_autotune_x": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, ctypes.POINTER(QaoaXTune)]),
     "qaoa_set_xtune": (c_int, [c_void_p, ctypes.POINTER(QaoaXTune)]),

@@ -199,11 +199,24 @@ cudaError_t launch_cost_maxcut(int n, const uint64_t *nbr_hi_host, const float *
                                void *d_out, int dtype, cudaStream_t s);
 cudaError_t launch_cost_sk(int n, const int32_t *d_Jq, const double *d_Jd, int exact,
                            int64_t dim, float *d_out, cudaStream_t s);
-cudaError_t launch_cost_dks(int n, int k, const uint64_t *nbr_hi_host, int64_t dim, void *d_out,
-                            int dtype, cudaStream_t s);
+cudaError_t launch_cost_dks(int n, int k, const uint64_t *nbr_hi, int64_t dim, void *d_out, int dtype,
+                            int kvc, int m, cudaStream_t s);
 cudaError_t launch_dicke_states(int n, int k, int64_t dim, uint64_t *d_out, cudaStream_t s);
 cudaError_t launch_ring_hamiltonian(int n, int k, int64_t dim, double *d_H, cudaStream_t s);
 cudaError_t launch_clique_hamiltonian(int n, int k, int64_t dim, double *d_H, cudaStream_t s);
+
+// Grover-mixer QAOA on cost degeneracies (kernels_grover.cu).
+struct DegLaunch {
+    uint64_t up_lo[128], up_hi[128];  // weight-k problems: neighbours above u
+    uint64_t adj[64];                 // MaxCut: all neighbours
+    int deg[64];
+    int n, k, m, kind, comp, n_bins;  // kind 0 MaxCut (2^n states), 1 DkS, 2 k-vertex cover
+};
+int grover_max_bins();
+cudaError_t launch_degeneracy(const DegLaunch &L, const uint64_t *d_binom, uint64_t start, uint64_t count,
+                              unsigned long long *d_counts, int *d_err, cudaStream_t s);
+cudaError_t launch_grover_eval(const int64_t *d_counts, int nb, int p, int n_sets, const double *d_angles,
+                               double *d_E, double *d_grad, cudaStream_t s);
 int binom_table_max();
 cudaError_t upload_binom_table();
 

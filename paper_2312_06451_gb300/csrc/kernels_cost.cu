@@ -5,6 +5,7 @@
 //   MaxCut   C(x) = sum_u popcount(nbr_hi[u] & (x_u ? ~x : x)): every edge
 //            (u, v), v > u, is counted from its lower end when x_v != x_u.
 //   DkS      C(x) = sum_u x_u popcount(nbr_hi[u] & x) on weight-k states.
+//   k-VC     C(x) = m - (the DkS count of the complement of x).
 //   SK       C(x) = sum_{i<j} J_ij z_i z_j, z_i = 1 - 2 x_i.  When every
 //            J_ij is a multiple of 2^-20 the sum is carried exactly in int64
 //            (J scaled by 2^20) and rounded once to float32, so the result is
@@ -130,13 +131,18 @@ __global__ void cost_sk_f64_kernel(int n, const double *Jd, int64_t dim, float *
     }
 }
 
-__global__ void cost_dks_kernel(AdjParams A, int k, int64_t dim, void *out, int dtype) {
+// kvc = 0: edges inside the chosen set (densest k-subgraph); kvc = 1: edges
+// with an end in the set (k-vertex cover) = m - edges inside the complement.
+__global__ void cost_dks_kernel(AdjParams A, int k, int64_t dim, void *out, int dtype, int kvc, int m) {
+    const uint64_t full = A.n == 64 ? ~0ull : ((1ull << A.n) - 1);
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < dim;
          a += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t x = unrank_colex(a, A.n, k);
+        const uint64_t x0 = unrank_colex(a, A.n, k);
+        const uint64_t x = kvc ? (full ^ x0) : x0;
         int c = 0;
         for (int u = 0; u < A.n; u++)
             if ((x >> u) & 1) c += __popcll(A.nbr[u] & x);
+        if (kvc) c = m - c;
         if (dtype == 1)
             reinterpret_cast<unsigned char *>(out)[a] = (unsigned char)c;
         else
@@ -223,8 +229,8 @@ cudaError_t launch_cost_sk(int n, const int32_t *d_Jq, const double *d_Jd, int e
 }
 
 cudaError_t launch_cost_dks(int n, int k, const uint64_t *nbr_hi, int64_t dim, void *d_out, int dtype,
-                            cudaStream_t s) {
-    cost_dks_kernel<<<grid_for(dim, 256), 256, 0, s>>>(make_adj(n, nbr_hi), k, dim, d_out, dtype);
+                            int kvc, int m, cudaStream_t s) {
+    cost_dks_kernel<<<grid_for(dim, 256), 256, 0, s>>>(make_adj(n, nbr_hi), k, dim, d_out, dtype, kvc, m);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,319 @@
+// Grover-mixer QAOA on cost degeneracies (arXiv 2312.06451, Sec. 2.4).
+//
+// With the Grover mixer H_G = |u><u| (u the uniform superposition over the
+// feasible set) and the uniform initial state, every feasible state with the
+// same cost value keeps the same amplitude ("fair sampling"), so the QAOA
+// only needs the distinct cost values c_j and their degeneracies d_j.  The
+// heavy part is counting the degeneracies over 2^n (or C(n, k)) states; the
+// simulation then runs on a vector of at most a few thousand values.
+//
+//   degeneracy kernel  every thread walks a contiguous range of the feasible
+//                      states and adds one count per state to a per-warp
+//                      shared-memory histogram:
+//                      * all 2^n states (MaxCut) in Gray-code order: flipping
+//                        qubit i changes the cut by deg_i - 2 cut_i(x), where
+//                        cut_i(x) = popcount(adj_i & (x_i ? ~x : x)) counts
+//                        the cut edges at i, so a step costs one popcount;
+//                      * the weight-k states (densest k-subgraph, k-vertex
+//                        cover) in increasing integer order: the range start
+//                        by the combinatorial number system, the next state by
+//                        Gosper's hack (Sec. 2.4), on 128-bit masks (n <= 128);
+//                        k > n/2 enumerates the n-k clear bits instead.
+//   reduced simulation one CTA per angle set: b_j = sqrt(d_j) a_j evolves as a
+//                      QAOA on the values with initial state u_j = sqrt(d_j/N)
+//                      and mixer e^{-i beta H_G} = I + (e^{-i beta} - 1) u u^T;
+//                      forward, <C> = sum_j c_j |b_j|^2 and the adjoint
+//                      recurrences, in float64 (the vector is tiny).
+#include "common.cuh"
+
+#include <algorithm>
+#include <cstring>
+
+namespace qg {
+namespace {
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ int ctz128(u128 x) {
+    const uint64_t lo = (uint64_t)x;
+    return lo ? __ffsll((long long)lo) - 1 : 64 + __ffsll((long long)(uint64_t)(x >> 64)) - 1;
+}
+__device__ __forceinline__ int popc128(u128 x) {
+    return __popcll((uint64_t)x) + __popcll((uint64_t)(x >> 64));
+}
+
+// Next larger integer with the same number of set bits (Gosper's hack).
+__device__ __forceinline__ u128 gosper_next(u128 x) {
+    const u128 u = x & (~x + 1);
+    const u128 v = x + u;
+    return v | (((v ^ x) >> ctz128(u)) >> 2);
+}
+
+// Weight-k subset of rank r in increasing integer (colex) order; binom is the
+// (129 x 129) table of binomial coefficients, row = n, column = k.
+__device__ u128 unrank_colex128(uint64_t r, int n, int k, const uint64_t *__restrict__ binom) {
+    u128 x = 0;
+    int c = n - 1;
+    for (int i = k; i >= 1; i--) {
+        while (binom[c * 129 + i] > r) c--;
+        x |= (u128)1 << c;
+        r -= binom[c * 129 + i];
+        c--;
+    }
+    return x;
+}
+
+constexpr int kDegThreads = 256;
+constexpr int kDegWarps = kDegThreads / 32;
+
+// Edges inside the set x: every edge (u, v), u < v, counted at u.
+__device__ __forceinline__ int inside_edges(u128 x, const uint64_t *up_lo, const uint64_t *up_hi) {
+    int c = 0;
+    for (u128 y = x; y; y &= y - 1) {
+        const int u = ctz128(y);
+        c += __popcll(up_lo[u] & (uint64_t)x) + __popcll(up_hi[u] & (uint64_t)(x >> 64));
+    }
+    return c;
+}
+
+// Count one state of cost c; a cost outside the histogram (which valid
+// input never produces) is recorded instead of written.
+__device__ __forceinline__ void add_bin(uint32_t *h, int c, int n_bins, bool &bad) {
+    if ((unsigned)c < (unsigned)n_bins) atomicAdd(&h[c], 1u);
+    else bad = true;
+}
+
+struct DegParams {
+    uint64_t up_lo[128], up_hi[128];  // neighbours above u (weight-k problems)
+    uint64_t adj[64];                 // all neighbours (MaxCut, n <= 63)
+    int deg[64];
+    int n, k, m, kind;                // kind: 0 MaxCut, 1 DkS, 2 k-vertex cover
+    int comp;                         // weight-k: enumerate the clear bits
+};
+
+__global__ void __launch_bounds__(kDegThreads)
+degeneracy_kernel(const DegParams P, const uint64_t *__restrict__ binom, uint64_t start, uint64_t count,
+                  int n_bins, int copies, unsigned long long *__restrict__ counts, int *err) {
+    extern __shared__ uint32_t hist[];  // copies x n_bins
+    // adjacency in shared memory: threads index it with different vertices
+    __shared__ uint64_t s_up_lo[128], s_up_hi[128], s_adj[64];
+    __shared__ int s_deg[64];
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+        s_up_lo[i] = P.up_lo[i];
+        s_up_hi[i] = P.up_hi[i];
+        if (i < 64) {
+            s_adj[i] = P.adj[i];
+            s_deg[i] = P.deg[i];
+        }
+    }
+    for (int i = threadIdx.x; i < copies * n_bins; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    uint32_t *h = hist + (size_t)((threadIdx.x >> 5) % copies) * n_bins;
+
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t per = (count + T - 1) / T;
+    const uint64_t a0 = start + tid * per;
+    const uint64_t a1 = min(start + count, a0 + per);
+    if (a0 < a1) {
+        if (P.kind == 0) {
+            // Gray-code walk: state g(a) = a ^ (a >> 1); from a to a + 1 the
+            // qubit ctz(a + 1) flips
+            uint64_t x = a0 ^ (a0 >> 1);
+            int cut = 0;
+            for (int u = 0; u < P.n; u++)
+                if ((x >> u) & 1) cut += __popcll(s_adj[u] & ~x);
+            bool bad = false;
+            add_bin(h, cut, n_bins, bad);
+            for (uint64_t a = a0 + 1; a < a1; a++) {
+                const int i = __ffsll((long long)a) - 1;
+                const uint64_t side = ((x >> i) & 1) ? ~x : x;
+                cut += s_deg[i] - 2 * __popcll(s_adj[i] & side);
+                x ^= 1ull << i;
+                add_bin(h, cut, n_bins, bad);
+            }
+            if (bad) atomicOr(err, DERR_BAD_DESC);
+        } else {
+            const int kk = P.comp ? P.n - P.k : P.k;
+            const u128 full = P.n == 128 ? ~(u128)0 : (((u128)1 << P.n) - 1);
+            u128 y = unrank_colex128(a0, P.n, kk, binom);
+            bool bad = false;
+            for (uint64_t a = a0; a < a1; a++) {
+                const u128 x = P.comp ? (full ^ y) : y;
+                const int c = P.kind == 1 ? inside_edges(x, s_up_lo, s_up_hi)
+                                          : P.m - inside_edges(full ^ x, s_up_lo, s_up_hi);
+                add_bin(h, c, n_bins, bad);
+                if (kk > 0) y = gosper_next(y);
+            }
+            if (bad) atomicOr(err, DERR_BAD_DESC);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < n_bins; b += blockDim.x) {
+        unsigned long long s = 0;
+        for (int c = 0; c < copies; c++) s += hist[(size_t)c * n_bins + b];
+        if (s) atomicAdd(&counts[b], s);
+    }
+}
+
+// ------------------------------------------------------- reduced simulation
+constexpr int kGrThreads = 512;
+constexpr int kGrWarps = kGrThreads / 32;
+
+// Deterministic block sum of a complex float64 (fixed reduction order).
+__device__ double2 block_sum2(double2 v, double2 *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double2 t = make_double2(0.0, 0.0);
+    for (int w = 0; w < kGrWarps; w++) {
+        t.x += red[w].x;
+        t.y += red[w].y;
+    }
+    return t;  // every thread gets the total
+}
+
+__device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void __launch_bounds__(kGrThreads)
+grover_eval_kernel(const int64_t *__restrict__ counts, int nb, int p, const double *__restrict__ angles,
+                   double *__restrict__ E, double *__restrict__ grad) {
+    extern __shared__ double2 gsm[];
+    double2 *psi = gsm, *lam = gsm + nb, *red = gsm + 2 * nb;
+    const int set = blockIdx.x;
+    const double *a = angles + (size_t)set * 2 * p;
+    // N = sum of the degeneracies (exact in float64 below 2^53)
+    double2 nn = make_double2(0.0, 0.0);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) nn.x += (double)counts[j];
+    const double N = block_sum2(nn, red).x;
+    auto u_of = [&](int j) { return sqrt((double)counts[j] / N); };
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) psi[j] = make_double2(u_of(j), 0.0);
+    for (int k = 0; k < p; k++) {
+        const double g = a[p + k], b = a[k];
+        double2 s = make_double2(0.0, 0.0);
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+            double sn, cs;
+            sincos(g * (double)j, &sn, &cs);
+            psi[j] = cmuld(psi[j], make_double2(cs, -sn));
+            const double u = u_of(j);
+            s.x += u * psi[j].x;
+            s.y += u * psi[j].y;
+        }
+        s = block_sum2(s, red);
+        double sb, cb;
+        sincos(b, &sb, &cb);
+        const double2 d = cmuld(make_double2(cb - 1.0, -sb), s);
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+            const double u = u_of(j);
+            psi[j].x += d.x * u;
+            psi[j].y += d.y * u;
+        }
+    }
+    double2 e = make_double2(0.0, 0.0);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) e.x += (double)j * (psi[j].x * psi[j].x + psi[j].y * psi[j].y);
+    e = block_sum2(e, red);
+    if (threadIdx.x == 0) E[set] = e.x;
+    if (!grad) return;
+    double *g_out = grad + (size_t)set * 2 * p;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) lam[j] = make_double2((double)j * psi[j].x, (double)j * psi[j].y);
+    for (int k = p - 1; k >= 0; k--) {
+        const double g = a[p + k], b = a[k];
+        double2 sl = make_double2(0.0, 0.0), sp = make_double2(0.0, 0.0);
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+            const double u = u_of(j);
+            sl.x += u * lam[j].x;
+            sl.y += u * lam[j].y;
+            sp.x += u * psi[j].x;
+            sp.y += u * psi[j].y;
+        }
+        sl = block_sum2(sl, red);
+        sp = block_sum2(sp, red);
+        // dE/dbeta_k = 2 Im( conj(<u|lam>) <u|psi> )
+        if (threadIdx.x == 0) g_out[k] = 2.0 * (sl.x * sp.y - sl.y * sp.x);
+        double sb, cb;
+        sincos(b, &sb, &cb);
+        const double2 f = make_double2(cb - 1.0, sb);  // e^{+i b} - 1
+        const double2 dl = cmuld(f, sl), dp = cmuld(f, sp);
+        double2 gg = make_double2(0.0, 0.0);
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+            const double u = u_of(j);
+            lam[j].x += dl.x * u;
+            lam[j].y += dl.y * u;
+            psi[j].x += dp.x * u;
+            psi[j].y += dp.y * u;
+            // Im( conj(lam_j) c_j psi_j )
+            gg.x += (double)j * (lam[j].x * psi[j].y - lam[j].y * psi[j].x);
+            double sn, cs;
+            sincos(g * (double)j, &sn, &cs);
+            const double2 ph = make_double2(cs, sn);
+            lam[j] = cmuld(lam[j], ph);
+            psi[j] = cmuld(psi[j], ph);
+        }
+        gg = block_sum2(gg, red);
+        if (threadIdx.x == 0) g_out[p + k] = 2.0 * gg.x;
+    }
+}
+
+}  // namespace
+
+int grover_max_bins() { return 4096; }
+
+cudaError_t launch_degeneracy(const DegLaunch &L, const uint64_t *d_binom, uint64_t start, uint64_t count,
+                              unsigned long long *d_counts, int *d_err, cudaStream_t s) {
+    DegParams P;
+    memset(&P, 0, sizeof(P));
+    for (int i = 0; i < 128; i++) {
+        P.up_lo[i] = L.up_lo[i];
+        P.up_hi[i] = L.up_hi[i];
+    }
+    for (int i = 0; i < 64; i++) {
+        P.adj[i] = L.adj[i];
+        P.deg[i] = L.deg[i];
+    }
+    P.n = L.n;
+    P.k = L.k;
+    P.m = L.m;
+    P.kind = L.kind;
+    P.comp = L.comp;
+    int copies = (96 * 1024) / (4 * L.n_bins);
+    copies = std::max(1, std::min(kDegWarps, copies));
+    const size_t smem = (size_t)copies * L.n_bins * 4;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(degeneracy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             96 * 1024 + 4 * 4096);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (count + (uint64_t)kDegThreads * 64 - 1) / ((uint64_t)kDegThreads * 64);
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)nsm * 8));
+    degeneracy_kernel<<<grid, kDegThreads, smem, s>>>(P, d_binom, start, count, L.n_bins, copies, d_counts, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grover_eval(const int64_t *d_counts, int nb, int p, int n_sets, const double *d_angles,
+                               double *d_E, double *d_grad, cudaStream_t s) {
+    const size_t smem = (size_t)(2 * nb + kGrWarps) * sizeof(double2);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(grover_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((2 * 4096 + kGrWarps) * sizeof(double2)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    grover_eval_kernel<<<n_sets, kGrThreads, smem, s>>>(d_counts, nb, p, d_angles, d_E, d_grad);
+    return cudaGetLastError();
+}
+
+}  // namespace qg

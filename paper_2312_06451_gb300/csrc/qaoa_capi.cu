@@ -1339,7 +1339,7 @@ qaoa_status qaoa_cost_precompute(qaoa_ctx *ctx, const qaoa_problem *prob, void *
         const int n = prob->n;
         if (cost_dtype != QAOA_COST_F32 && cost_dtype != QAOA_COST_U8)
             return fail(ctx, QAOA_ERR_INVALID, "unknown cost dtype %d", cost_dtype);
-        const bool dks = prob->kind == QAOA_PROBLEM_DKS;
+        const bool dks = prob->kind == QAOA_PROBLEM_DKS || prob->kind == QAOA_PROBLEM_KVC;
         if (n < 1 || n > (dks ? binom_table_max() : 34))
             return fail(ctx, QAOA_ERR_INVALID, "n=%d out of range", n);
         int64_t want;
@@ -1386,7 +1386,8 @@ qaoa_status qaoa_cost_precompute(qaoa_ctx *ctx, const qaoa_problem *prob, void *
                 e = launch_cost_maxcut(n, nbr, static_cast<float *>(dw), static_cast<int32_t *>(de), prob->m, 1,
                                        dim, d_cost, cost_dtype, ctx->stream);
             } else if (dks) {
-                e = launch_cost_dks(n, prob->k, nbr, dim, d_cost, cost_dtype, ctx->stream);
+                e = launch_cost_dks(n, prob->k, nbr, dim, d_cost, cost_dtype, prob->kind == QAOA_PROBLEM_KVC ? 1 : 0,
+                                    prob->m, ctx->stream);
             } else {
                 e = launch_cost_maxcut(n, nbr, nullptr, nullptr, prob->m, 0, dim, d_cost, cost_dtype,
                                        ctx->stream);
@@ -1552,6 +1553,113 @@ qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *
     } catch (...) {
         return fail(ctx, QAOA_ERR_OOM, "host allocation failed");
     }
+}
+
+qaoa_status qaoa_cost_degeneracy(qaoa_ctx *ctx, const qaoa_problem *prob, int64_t *d_counts, int n_bins) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    try {
+        ctx->err.clear();
+        if (!prob || !d_counts) return fail(ctx, QAOA_ERR_INVALID, "problem and d_counts must be non-NULL");
+        const int n = prob->n, k = prob->k, m = prob->m;
+        const bool weighted_k = prob->kind == QAOA_PROBLEM_DKS || prob->kind == QAOA_PROBLEM_KVC;
+        if (!weighted_k && !(prob->kind == QAOA_PROBLEM_MAXCUT && k < 0))
+            return fail(ctx, QAOA_ERR_UNSUPPORTED, "degeneracies are counted for MAXCUT (k = -1), DKS and KVC");
+        if (n < 1 || n > (weighted_k ? 128 : 44))
+            return fail(ctx, QAOA_ERR_INVALID, "n=%d out of range (MAXCUT <= 44, DKS/KVC <= 128)", n);
+        if (weighted_k && (k < 0 || k > n)) return fail(ctx, QAOA_ERR_INVALID, "bad k=%d", k);
+        if (m < 0 || (m > 0 && !prob->edges)) return fail(ctx, QAOA_ERR_INVALID, "edge list missing");
+        if (n_bins <= m || n_bins > grover_max_bins())
+            return fail(ctx, QAOA_ERR_INVALID, "n_bins=%d must exceed the edge count %d and be <= %d", n_bins, m,
+                        grover_max_bins());
+        // feasible-set size, exactly, with a cap on the enumeration
+        const uint64_t kCap = 1ull << 44;
+        uint64_t N = 1;
+        if (weighted_k) {
+            const int kk = std::min(k, n - k);
+            long double b = 1;
+            for (int i = 0; i < kk; i++) b = b * (n - i) / (i + 1);
+            if (b > (long double)kCap) return fail(ctx, QAOA_ERR_UNSUPPORTED, "C(%d,%d) > 2^44 states", n, k);
+            N = (uint64_t)std::llround((double)b);
+        } else {
+            N = 1ull << n;
+        }
+        DegLaunch L;
+        std::memset(&L, 0, sizeof(L));
+        for (int e = 0; e < m; e++) {
+            int u = prob->edges[2 * e], v = prob->edges[2 * e + 1];
+            if (u < 0 || v < 0 || u >= n || v >= n || u == v)
+                return fail(ctx, QAOA_ERR_INVALID, "edge %d = (%d,%d) invalid for n=%d", e, u, v, n);
+            if (u > v) std::swap(u, v);
+            uint64_t &w = v < 64 ? L.up_lo[u] : L.up_hi[u];
+            const uint64_t bitv = 1ull << (v & 63);
+            if (w & bitv) return fail(ctx, QAOA_ERR_INVALID, "edge (%d,%d) repeated", u, v);
+            w |= bitv;
+            if (!weighted_k) {
+                L.adj[u] |= 1ull << v;
+                L.adj[v] |= 1ull << u;
+                L.deg[u]++;
+                L.deg[v]++;
+            }
+        }
+        L.n = n;
+        L.k = k;
+        L.m = m;
+        L.kind = prob->kind == QAOA_PROBLEM_MAXCUT ? 0 : (prob->kind == QAOA_PROBLEM_DKS ? 1 : 2);
+        L.comp = weighted_k && 2 * k > n ? 1 : 0;
+        L.n_bins = n_bins;
+        cudaSetDevice(ctx->device);
+        // binomial coefficients C(a, b), a, b <= 128, saturating at 2^64 - 1
+        void *d_binom = nullptr;
+        const bool fresh = !ctx->bufs.count("binom128");
+        qaoa_status st = scratch(ctx, "binom128", sizeof(uint64_t) * 129 * 129, &d_binom);
+        if (st) return st;
+        if (fresh) {
+            std::vector<uint64_t> h(129 * 129, 0);
+            for (int a = 0; a <= 128; a++)
+                for (int b = 0; b <= 128; b++) {
+                    uint64_t v;
+                    if (b == 0) v = 1;
+                    else if (a == 0) v = 0;
+                    else {
+                        const uint64_t x = h[(a - 1) * 129 + b - 1], y = h[(a - 1) * 129 + b];
+                        v = (x > ~0ull - y) ? ~0ull : x + y;
+                    }
+                    h[a * 129 + b] = v;
+                }
+            QG_CUDA(ctx, cudaMemcpyAsync(d_binom, h.data(), sizeof(uint64_t) * h.size(), cudaMemcpyHostToDevice,
+                                         ctx->stream),
+                    "binomial table upload");
+            QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "binomial table upload");
+        }
+        QG_CUDA(ctx, cudaMemsetAsync(d_counts, 0, sizeof(int64_t) * n_bins, ctx->stream), "counts clear");
+        const uint64_t slab = 1ull << 36;  // keeps every warp's 32-bit shared counters from wrapping
+        for (uint64_t s0 = 0; s0 < N; s0 += slab) {
+            const uint64_t cnt = std::min(slab, N - s0);
+            cudaError_t e = launch_degeneracy(L, static_cast<const uint64_t *>(d_binom), s0, cnt,
+                                              reinterpret_cast<unsigned long long *>(d_counts), ctx->d_err,
+                                              ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "degeneracy kernel launch");
+            ctx->launches++;
+        }
+        return read_dev_err(ctx);
+    } catch (...) {
+        return fail(ctx, QAOA_ERR_OOM, "host allocation failed");
+    }
+}
+
+qaoa_status qaoa_grover_batched(qaoa_ctx *ctx, const int64_t *d_counts, int n_bins, int p, int n_sets,
+                                const double *d_angles, double *d_E, double *d_grad) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    ctx->err.clear();
+    if (!d_counts || !d_angles || !d_E) return fail(ctx, QAOA_ERR_INVALID, "counts, angles and E must be non-NULL");
+    if (n_bins < 1 || n_bins > grover_max_bins())
+        return fail(ctx, QAOA_ERR_INVALID, "n_bins must be in [1, %d]", grover_max_bins());
+    if (p < 1 || n_sets < 1) return fail(ctx, QAOA_ERR_INVALID, "p and n_sets must be >= 1");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = launch_grover_eval(d_counts, n_bins, p, n_sets, d_angles, d_E, d_grad, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "Grover kernel launch");
+    ctx->launches++;
+    return QAOA_OK;
 }
 
 qaoa_status qaoa_set_checkpointing(qaoa_ctx *ctx, int mode) {
