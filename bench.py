@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -398,6 +399,93 @@ class Workload:
             "oracle gradient of 16 of the 512 instances (one angle set each), scaled per set")
 
 
+class GroverWorkload:
+    """Grover-mixer QAOA on cost degeneracies: one step counts every weight-k
+    subset of the 100-vertex graph by cost (the unit: feasible states counted)
+    and evaluates <C> and the gradient of 1024 angle sets on the distinct
+    values."""
+
+    def __init__(self, qg, ctx, dev, pool_steps):
+        import torch
+
+        from qaoa_inputs import WORKLOADS, workload_instance
+
+        self.idx, self.qg, self.ctx, self.dev = 6, qg, ctx, dev
+        spec = dict(WORKLOADS[6])
+        w = workload_instance(6, n_sets=spec["n_sets"] * pool_steps)
+        self.n, self.k, self.p, self.S = spec["n"], spec["k"], spec["p"], spec["n_sets"]
+        self.edges = w["edges"]
+        self.grad = True
+        self.name = spec["name"]
+        self.units = math.comb(self.n, self.k)
+        A = np.ascontiguousarray(w["angles"])
+        pool = torch.from_numpy(A).to(dev)
+        self.angles = pool[:self.S].clone()
+        self.pools = [(pool, self.S, self.n, A)]
+        self.counts = ctx.cost_degeneracy("dks", self.n, edges=self.edges, k=self.k)
+        self.E, self.G = ctx.grover_batched(self.counts, self.angles)
+        self.jobs = [{"E": self.E}]
+        self.deg_ms = []
+        self.config = {"workload": self.name, "problem": "densest k-subgraph, G(100,0.5), weight-6 subsets",
+                       "n": self.n, "k": self.k, "feasible_states": self.units, "p": self.p,
+                       "mixer": "Grover, on cost degeneracies", "angle_sets_per_step": self.S,
+                       "unit_note": "value counts feasible states enumerated per second",
+                       "state": "float64 reduced vector (one amplitude per cost value)",
+                       "l2": "no state in memory: integer enumeration"}
+
+    def autotune(self):
+        return {}
+
+    def load_angles(self, step):
+        s = (step * self.S) % self.pools[0][0].shape[0]
+        self.angles.copy_(self.pools[0][0][s:s + self.S], non_blocking=True)
+
+    def run(self):
+        import torch
+
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream()
+        a.record(st)
+        self.counts = self.ctx.cost_degeneracy("dks", self.n, edges=self.edges, k=self.k)
+        b.record(st)
+        self.E, self.G = self.ctx.grover_batched(self.counts, self.angles)
+        self.jobs[0]["E"] = self.E
+        self.deg_ms.append((a, b))
+
+    def e2e_step(self, step, pinned):
+        s = (step * self.S) % pinned[0].shape[0]
+        self.angles.copy_(pinned[0][s:s + self.S], non_blocking=True)
+        self.run()
+        outs = [self.E.to("cpu", non_blocking=True), self.G.to("cpu", non_blocking=True)]
+        import torch
+
+        torch.cuda.current_stream().synchronize()
+        return outs
+
+    def h2d_bytes(self):
+        return 8 * 2 * self.p * self.S
+
+    def d2h_bytes(self):
+        return 8 * self.S * (2 * self.p + 1)
+
+    def degeneracy_ms(self, last):
+        ev = self.deg_ms[-last:]
+        return sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+
+    def oracle_baseline(self):
+        """The oracle's brute-force count on the weight-3 subsets of the same
+        graph, per state, scaled to states/s."""
+        import oracle
+
+        oracle.build()
+        t = time.perf_counter()
+        oracle.cost_degeneracy(self.n, self.edges, "dks", 3, method="subsets")
+        dt = time.perf_counter() - t
+        return math.comb(self.n, 3) / dt, 1, (f"oracle brute-force degeneracy count of all weight-3 subsets "
+                                              f"of the same graph ({math.comb(self.n, 3)} states, numpy on one "
+                                              f"core), per state")
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def gpu_arm(args, ws, rank, local):
@@ -422,7 +510,10 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     import torch
 
     ctx = qg.Context(local, stream)
-    W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n, args.gemm)
+    if args.workload == 6:
+        W = GroverWorkload(qg, ctx, dev, args.steps + args.warmup)
+    else:
+        W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n, args.gemm)
     if not args.no_autotune:
         sched = W.autotune()
         if sched:
@@ -493,7 +584,7 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     e2e_value = rsum(args.steps * W.units) / e2e_s
 
     fd = None
-    if W.grad and ws == 1 and not args.no_fd:
+    if W.grad and ws == 1 and not args.no_fd and args.workload != 6:
         fd = fd_compare(W, stream, value)
 
     peaks = measured_peaks()
@@ -518,7 +609,21 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
                 "traffic": traffic_for(fam, W.name), "algo_bytes_per_launch": per_launch_bytes,
                 "launch_ms": per_launch_ms}
+    if args.workload == 6:
+        # integer enumeration: the bound is the SM's bit-count unit (16
+        # operations a clock per SM); a state of the sweep over the smallest
+        # vertex costs one population count per 64-bit word of |N(v) & T|
+        dms = W.degeneracy_ms(args.steps)
+        ops = 2
+        achieved = W.units / (dms * 1e-3) / 1e9
+        peak = 152 * 16 * 2.07e9 / ops / 1e9
+        roof = {"bound": "alu", "kernel": "degeneracy_kernel", "achieved": achieved, "peak": peak,
+                "unit": "Gstates/s", "frac": achieved / peak,
+                "peak_source": f"derived: 152 SM x 16 bit-count ops/clk x 2.07 GHz / {ops} ops per state",
+                "traffic": None, "launch_ms": dms}
     unit = UNIT if W.grad else "evals/s"
+    if args.workload == 6:
+        unit = "states/s"
     out = None
     if rank == 0:
         cfg = dict(W.config)
@@ -603,10 +708,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None,
                     help="override the qubit count (small cases for profiler captures)")
-    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[1, 2, 3, 4, 5],
+    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=[1, 2, 3, 4, 5, 6],
                     help="1: MaxCut n=12 p=3 forward; 2: SK n=28 p=8 gradient (default); "
                          "3: 3-regular n=24 p=10, 1024 angle sets; 4: densest 8-subgraph n=16 ring mixer "
-                         "(D=12870), 256 angle sets; 5: 512 uneven instances x 4 sets")
+                         "(D=12870), 256 angle sets; 5: 512 uneven instances x 4 sets; "
+                         "6: Grover mixer on cost degeneracies, densest 6-subgraph n=100")
     ap.add_argument("--gemm", default="3xtf32", choices=["fp32", "3xtf32"],
                     help="eigenbasis product precision (workload 4): tcgen05 3xTF32 or CUDA-core float32")
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")

@@ -298,8 +298,9 @@ qaoa_status qaoa_get_xtune(qaoa_ctx *ctx, int n, int cost_dtype, qaoa_xtune *out
  *   prob      MAXCUT with k = -1 over all 2^n states (n <= 44), or DKS / KVC
  *             over the Hamming-weight-k states (n <= 128, C(n, k) <= 2^44)
  *   d_counts  device, n_bins int64: zeroed, then d_counts[c] = number of
- *             feasible states with cost c; n_bins must exceed the edge count
- *             (the largest possible cost) and be at most 4096
+ *             feasible states with cost c; n_bins must exceed the largest
+ *             possible cost (the edge count; for DKS at most k(k-1)/2) and be
+ *             at most 4096
  * Synchronous on the context stream.  Valid input never yields a cost outside
  * [0, n_bins); the kernel checks it anyway and reports QAOA_ERR_CUDA. */
 qaoa_status qaoa_cost_degeneracy(qaoa_ctx *ctx, const qaoa_problem *prob, int64_t *d_counts, int n_bins);

@@ -216,7 +216,8 @@ class Context:
         kind = _PROBLEMS[problem]
         e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
         m = e.shape[0]
-        nb = m + 1 if n_bins is None else int(n_bins)
+        top = min(m, k * (k - 1) // 2) if problem == "dks" else m  # the largest possible cost
+        nb = top + 1 if n_bins is None else int(n_bins)
         out = torch.empty(nb, dtype=torch.int64, device=f"cuda:{self.device}")
         prob = B.QaoaProblem(kind, n, k, m, e.ctypes.data_as(ctypes.c_void_p), None, None)
         self._check(self._lib.qaoa_cost_degeneracy(self._h, ctypes.byref(prob), _ptr(out), nb))

@@ -207,7 +207,7 @@ cudaError_t launch_clique_hamiltonian(int n, int k, int64_t dim, double *d_H, cu
 
 // Grover-mixer QAOA on cost degeneracies (kernels_grover.cu).
 struct DegLaunch {
-    uint64_t up_lo[128], up_hi[128];  // weight-k problems: neighbours above u
+    uint64_t up_lo[128], up_hi[128];  // weight-k problems: all neighbours of u
     uint64_t adj[64];                 // MaxCut: all neighbours
     int deg[64];
     int n, k, m, kind, comp, n_bins;  // kind 0 MaxCut (2^n states), 1 DkS, 2 k-vertex cover

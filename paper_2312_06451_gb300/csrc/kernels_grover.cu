@@ -18,7 +18,11 @@
 //                        cover) in increasing integer order: the range start
 //                        by the combinatorial number system, the next state by
 //                        Gosper's hack (Sec. 2.4), on 128-bit masks (n <= 128);
-//                        k > n/2 enumerates the n-k clear bits instead.
+//                        k > n/2 enumerates the n-k clear bits instead.  The
+//                        states {v} u T, v < min(T), have consecutive ranks:
+//                        a thread fixes T and sweeps v with one two-word
+//                        popcount per state (counted in packed 8-bit register
+//                        fields when the cost depends on |N(v) & T| alone).
 //   reduced simulation one CTA per angle set: b_j = sqrt(d_j) a_j evolves as a
 //                      QAOA on the values with initial state u_j = sqrt(d_j/N)
 //                      and mixer e^{-i beta H_G} = I + (e^{-i beta} - 1) u u^T;
@@ -32,31 +36,40 @@
 namespace qg {
 namespace {
 
-typedef unsigned __int128 u128;
+// A set of up to 128 vertices as two 64-bit words (bit i of lo = vertex i,
+// bit i of hi = vertex 64 + i).
+struct Set2 {
+    uint64_t lo, hi;
+};
 
-__device__ __forceinline__ int ctz128(u128 x) {
-    const uint64_t lo = (uint64_t)x;
-    return lo ? __ffsll((long long)lo) - 1 : 64 + __ffsll((long long)(uint64_t)(x >> 64)) - 1;
-}
-__device__ __forceinline__ int popc128(u128 x) {
-    return __popcll((uint64_t)x) + __popcll((uint64_t)(x >> 64));
-}
-
-// Next larger integer with the same number of set bits (Gosper's hack).
-__device__ __forceinline__ u128 gosper_next(u128 x) {
-    const u128 u = x & (~x + 1);
-    const u128 v = x + u;
-    return v | (((v ^ x) >> ctz128(u)) >> 2);
+// Next larger set of the same size in increasing integer order (Gosper's
+// hack): with u the lowest set bit, v = x + u clears x's lowest block of b
+// ones and sets the bit above it; v ^ x is that run of b + 1 ones, and its
+// b - 1 = popcount(v ^ x) - 2 extra ones go to the bottom.
+__device__ __forceinline__ Set2 gosper_next(Set2 x) {
+    uint64_t vlo, vhi;
+    if (x.lo) {
+        vlo = x.lo + (x.lo & (0ull - x.lo));
+        vhi = x.hi + (vlo < x.lo ? 1ull : 0ull);
+    } else {
+        vlo = 0;
+        vhi = x.hi + (x.hi & (0ull - x.hi));
+    }
+    const int c = __popcll(vlo ^ x.lo) + __popcll(vhi ^ x.hi) - 2;
+    const uint64_t mlo = c >= 64 ? ~0ull : ((1ull << c) - 1ull);
+    const uint64_t mhi = c > 64 ? ((1ull << (c - 64)) - 1ull) : 0ull;
+    return {vlo | mlo, vhi | mhi};
 }
 
 // Weight-k subset of rank r in increasing integer (colex) order; binom is the
 // (129 x 129) table of binomial coefficients, row = n, column = k.
-__device__ u128 unrank_colex128(uint64_t r, int n, int k, const uint64_t *__restrict__ binom) {
-    u128 x = 0;
+__device__ Set2 unrank_colex128(uint64_t r, int n, int k, const uint64_t *__restrict__ binom) {
+    Set2 x = {0ull, 0ull};
     int c = n - 1;
     for (int i = k; i >= 1; i--) {
         while (binom[c * 129 + i] > r) c--;
-        x |= (u128)1 << c;
+        if (c < 64) x.lo |= 1ull << c;
+        else x.hi |= 1ull << (c - 64);
         r -= binom[c * 129 + i];
         c--;
     }
@@ -66,16 +79,6 @@ __device__ u128 unrank_colex128(uint64_t r, int n, int k, const uint64_t *__rest
 constexpr int kDegThreads = 256;
 constexpr int kDegWarps = kDegThreads / 32;
 
-// Edges inside the set x: every edge (u, v), u < v, counted at u.
-__device__ __forceinline__ int inside_edges(u128 x, const uint64_t *up_lo, const uint64_t *up_hi) {
-    int c = 0;
-    for (u128 y = x; y; y &= y - 1) {
-        const int u = ctz128(y);
-        c += __popcll(up_lo[u] & (uint64_t)x) + __popcll(up_hi[u] & (uint64_t)(x >> 64));
-    }
-    return c;
-}
-
 // Count one state of cost c; a cost outside the histogram (which valid
 // input never produces) is recorded instead of written.
 __device__ __forceinline__ void add_bin(uint32_t *h, int c, int n_bins, bool &bad) {
@@ -84,7 +87,7 @@ __device__ __forceinline__ void add_bin(uint32_t *h, int c, int n_bins, bool &ba
 }
 
 struct DegParams {
-    uint64_t up_lo[128], up_hi[128];  // neighbours above u (weight-k problems)
+    uint64_t up_lo[128], up_hi[128];  // all neighbours of u (weight-k problems)
     uint64_t adj[64];                 // all neighbours (MaxCut, n <= 63)
     int deg[64];
     int n, k, m, kind;                // kind: 0 MaxCut, 1 DkS, 2 k-vertex cover
@@ -97,10 +100,11 @@ degeneracy_kernel(const DegParams P, const uint64_t *__restrict__ binom, uint64_
     extern __shared__ uint32_t hist[];  // copies x n_bins
     // adjacency in shared memory: threads index it with different vertices
     __shared__ uint64_t s_up_lo[128], s_up_hi[128], s_adj[64];
-    __shared__ int s_deg[64];
+    __shared__ int s_deg[64], s_deg2[128];
     for (int i = threadIdx.x; i < 128; i += blockDim.x) {
         s_up_lo[i] = P.up_lo[i];
         s_up_hi[i] = P.up_hi[i];
+        s_deg2[i] = __popcll(P.up_lo[i]) + __popcll(P.up_hi[i]);
         if (i < 64) {
             s_adj[i] = P.adj[i];
             s_deg[i] = P.deg[i];
@@ -134,16 +138,77 @@ degeneracy_kernel(const DegParams P, const uint64_t *__restrict__ binom, uint64_
             }
             if (bad) atomicOr(err, DERR_BAD_DESC);
         } else {
+            // x = the chosen set; inside = edges within x, dsum = degrees summed
+            // over x (k-vertex cover: dsum - inside edges touch x).  Between
+            // consecutive states only the bits Gosper's step moves change:
+            // removing r lowers inside by |N(r) & x|, adding v raises it by
+            // |N(v) & x| (x without v).
+            // y = the enumerated set (x itself, or its complement when
+            // k > n/2), |y| = kk.  In increasing integer order the sets
+            // {v} u T with v < min(T) have consecutive ranks, so a thread fixes
+            // T, sweeps v, then moves T to its successor (Gosper).  With
+            // I = inside(y) = inside(T) + |N(v) & T| and D = degree sum of y:
+            //   DkS  x = y: I        x = ~y: m - D + I
+            //   kVC  x = y: D - I    x = ~y: m - I
             const int kk = P.comp ? P.n - P.k : P.k;
-            const u128 full = P.n == 128 ? ~(u128)0 : (((u128)1 << P.n) - 1);
-            u128 y = unrank_colex128(a0, P.n, kk, binom);
             bool bad = false;
-            for (uint64_t a = a0; a < a1; a++) {
-                const u128 x = P.comp ? (full ^ y) : y;
-                const int c = P.kind == 1 ? inside_edges(x, s_up_lo, s_up_hi)
-                                          : P.m - inside_edges(full ^ x, s_up_lo, s_up_hi);
+            if (kk == 0) {  // the single state: x = {} or x = all vertices
+                const int c = P.comp ? P.m : 0;  // no edge inside / touching {}, all m for all vertices
                 add_bin(h, c, n_bins, bad);
-                if (kk > 0) y = gosper_next(y);
+            } else {
+                Set2 T = unrank_colex128(a0, P.n, kk, binom);
+                int v = T.lo ? __ffsll((long long)T.lo) - 1 : 64 + __ffsll((long long)T.hi) - 1;
+                if (v < 64) T.lo ^= 1ull << v;
+                else T.hi ^= 1ull << (v - 64);
+                const bool by_inside = (P.kind == 1) != (P.comp != 0);  // cost = I or m - I
+                const bool packed = by_inside && kk <= 16;
+                uint64_t rem = a1 - a0;
+                for (;;) {
+                    const int lim = T.lo ? __ffsll((long long)T.lo) - 1
+                                         : (T.hi ? 64 + __ffsll((long long)T.hi) - 1 : P.n);
+                    int tin = 0, tds = 0;
+                    for (uint64_t z = T.lo; z; z &= z - 1) {
+                        const int u = __ffsll((long long)z) - 1;
+                        tin += __popcll(s_up_lo[u] & T.lo) + __popcll(s_up_hi[u] & T.hi);
+                        tds += s_deg2[u];
+                    }
+                    for (uint64_t z = T.hi; z; z &= z - 1) {
+                        const int u = 64 + __ffsll((long long)z) - 1;
+                        tin += __popcll(s_up_lo[u] & T.lo) + __popcll(s_up_hi[u] & T.hi);
+                        tds += s_deg2[u];
+                    }
+                    tin >>= 1;
+                    const uint64_t span = lim > v ? (uint64_t)(lim - v) : 0ull;
+                    const int cnt = (int)(span < rem ? span : rem);
+                    if (packed) {
+                        // |N(v) & T| < kk <= 16: counts in 8-bit fields (cnt < 128)
+                        uint64_t f0 = 0, f1 = 0;
+                        for (int i = 0; i < cnt; i++, v++) {
+                            const int pv = __popcll(s_up_lo[v] & T.lo) + __popcll(s_up_hi[v] & T.hi);
+                            if (pv < 8) f0 += 1ull << (8 * pv);
+                            else f1 += 1ull << (8 * (pv - 8));
+                        }
+                        for (int f = 0; f < kk; f++) {
+                            const uint32_t c = (uint32_t)(((f < 8 ? f0 : f1) >> (8 * (f & 7))) & 255u);
+                            if (c) {
+                                const int cost = P.comp ? P.m - (tin + f) : tin + f;
+                                if ((unsigned)cost < (unsigned)n_bins) atomicAdd(&h[cost], c);
+                                else bad = true;
+                            }
+                        }
+                    } else {
+                        for (int i = 0; i < cnt; i++, v++) {
+                            const int I = tin + __popcll(s_up_lo[v] & T.lo) + __popcll(s_up_hi[v] & T.hi);
+                            const int D = tds + s_deg2[v];
+                            const int cost = P.kind == 1 ? (P.comp ? P.m - D + I : I) : (P.comp ? P.m - I : D - I);
+                            add_bin(h, cost, n_bins, bad);
+                        }
+                    }
+                    rem -= (uint64_t)cnt;
+                    if (rem == 0 || kk == 1) break;
+                    T = gosper_next(T);
+                    v = 0;
+                }
             }
             if (bad) atomicOr(err, DERR_BAD_DESC);
         }

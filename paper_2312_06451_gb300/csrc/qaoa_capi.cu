@@ -1568,9 +1568,13 @@ qaoa_status qaoa_cost_degeneracy(qaoa_ctx *ctx, const qaoa_problem *prob, int64_
             return fail(ctx, QAOA_ERR_INVALID, "n=%d out of range (MAXCUT <= 44, DKS/KVC <= 128)", n);
         if (weighted_k && (k < 0 || k > n)) return fail(ctx, QAOA_ERR_INVALID, "bad k=%d", k);
         if (m < 0 || (m > 0 && !prob->edges)) return fail(ctx, QAOA_ERR_INVALID, "edge list missing");
-        if (n_bins <= m || n_bins > grover_max_bins())
-            return fail(ctx, QAOA_ERR_INVALID, "n_bins=%d must exceed the edge count %d and be <= %d", n_bins, m,
-                        grover_max_bins());
+        // the largest cost the problem can take: m edges, at most C(k, 2)
+        // inside a k-subset
+        int maxc = m;
+        if (prob->kind == QAOA_PROBLEM_DKS) maxc = std::min<int64_t>(m, (int64_t)k * (k - 1) / 2);
+        if (n_bins <= maxc || n_bins > grover_max_bins())
+            return fail(ctx, QAOA_ERR_INVALID, "n_bins=%d must exceed the largest possible cost %d and be <= %d",
+                        n_bins, maxc, grover_max_bins());
         // feasible-set size, exactly, with a cap on the enumeration
         const uint64_t kCap = 1ull << 44;
         uint64_t N = 1;
@@ -1594,6 +1598,7 @@ qaoa_status qaoa_cost_degeneracy(qaoa_ctx *ctx, const qaoa_problem *prob, int64_
             const uint64_t bitv = 1ull << (v & 63);
             if (w & bitv) return fail(ctx, QAOA_ERR_INVALID, "edge (%d,%d) repeated", u, v);
             w |= bitv;
+            (u < 64 ? L.up_lo[v] : L.up_hi[v]) |= 1ull << (u & 63);  // both directions
             if (!weighted_k) {
                 L.adj[u] |= 1ull << v;
                 L.adj[v] |= 1ull << u;

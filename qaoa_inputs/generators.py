@@ -127,6 +127,10 @@ WORKLOADS = {
             p_edge=0.5, mixer="ring", p=6, n_sets=256, grad=True),
     5: dict(name="uneven512_p6_s4", problem="maxcut", graph="uneven", n_instances=512,
             mixer="x", p=6, n_sets=4, grad=True),
+    # Grover mixer on cost degeneracies (Section 2.4: up to n = 100): all
+    # weight-6 subsets of 100 vertices counted by cost, then 1024 angle sets
+    6: dict(name="grover_dks_er100_k6_p10_b1024", problem="dks", graph="er", n=100, k=6,
+            p_edge=0.5, mixer="grover", p=10, n_sets=1024, grad=True),
 }
 
 

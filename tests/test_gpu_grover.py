@@ -117,7 +117,7 @@ def test_degeneracy_argument_checks(Q):
     qg, ctx = Q
     e = erdos_renyi(10, 0.5, 47)
     with pytest.raises(qg.QAOAError):
-        ctx.cost_degeneracy("dks", 10, edges=e, k=4, n_bins=len(e))  # the largest cost has no bin
+        ctx.cost_degeneracy("dks", 10, edges=e, k=4, n_bins=6)  # a 4-subset can hold 6 edges: no bin for 6
     with pytest.raises(qg.QAOAError):
         ctx.cost_degeneracy("sk", 10, edges=e)
     with pytest.raises(qg.QAOAError):
