@@ -68,6 +68,7 @@ def _load():
             "oracle_qaoa_gradient": (i32, [i32, i32, i64, P, P, i32, P, P, P, P]),
             "oracle_mixer_apply": (i32, [i32, i32, i64, P, f64, P]),
             "oracle_hm_apply": (i32, [i32, i32, i64, P, P, P]),
+            "oracle_qaoa_gradient_ma": (i32, [i32, P, i32, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -270,6 +271,23 @@ def qaoa_gradient(n, cost, angles, mixer="x", states=None, psi0=None):
                                      _ptr(_c128(psi0)), _ptr(E), _ptr(g))
     if r:
         raise RuntimeError(f"oracle_qaoa_gradient failed ({r})")
+    return float(E[0]), g
+
+
+def qaoa_gradient_ma(n, cost, angles, psi0=None):
+    """Multi-angle QAOA with one X angle per (round, qubit): angles =
+    [beta_{1,0..n-1}, ..., beta_{p,0..n-1}, gamma_1..gamma_p]; returns
+    (E, grad) in the same layout, exact reverse mode in complex128."""
+    cost = _f64(cost)
+    a = _f64(angles)
+    p = a.shape[0] // (n + 1)
+    if p * (n + 1) != a.shape[0]:
+        raise ValueError("multi-angle QAOA needs p (n + 1) angles")
+    E = np.zeros(1)
+    g = np.zeros(a.shape[0])
+    r = _load().oracle_qaoa_gradient_ma(n, _ptr(cost), p, _ptr(a), _ptr(_c128(psi0)), _ptr(E), _ptr(g))
+    if r:
+        raise RuntimeError(f"oracle_qaoa_gradient_ma failed ({r})")
     return float(E[0]), g
 
 

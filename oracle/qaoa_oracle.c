@@ -425,6 +425,65 @@ int oracle_qaoa_gradient(int kind, int n, int64_t dim, const uint64_t *states,
     return 0;
 }
 
+/* ------------------------------------------------------ multi-angle QAOA */
+
+/* Multi-angle QAOA (Sec. 3: several mixers per layer, each with its own
+ * angle): round k applies e^{-i gamma_k C}, then e^{-i beta_{k,q} X_q} for every
+ * qubit q (the X_q commute, so their order does not matter).  Angles:
+ * beta_{k,q} = angles[k n + q] (k < p, q < n), gamma_k = angles[p n + k];
+ * grad has the same layout.  X mixer on all 2^n states only.  Reverse mode
+ * as in oracle_qaoa_gradient, with one partial per (round, qubit):
+ *   dE/dbeta_{k,q} = 2 Im <lam| X_q |psi>. */
+static void rot_qubit(int64_t dim, int q, double beta, cplx *v) {
+    const double c = cos(beta), s = sin(beta);
+    const int64_t st = (int64_t)1 << q;
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < dim / 2; j++) {
+        int64_t lo = j & (st - 1);
+        int64_t x0 = ((j - lo) << 1) | lo, x1 = x0 | st;
+        cplx a = v[x0], b = v[x1];
+        v[x0] = c * a - I * s * b;
+        v[x1] = -I * s * a + c * b;
+    }
+}
+
+int oracle_qaoa_gradient_ma(int n, const double *cost, int p, const double *angles,
+                            const double *psi0, double *E, double *grad) {
+    const int64_t dim = (int64_t)1 << n;
+    if (p < 1 || n < 1 || n > 30) return -1;
+    cplx *psi = malloc(sizeof(cplx) * dim);
+    cplx *lam = malloc(sizeof(cplx) * dim);
+    if (!psi || !lam) { free(psi); free(lam); return -2; }
+    init_state(dim, psi0, psi);
+    for (int k = 0; k < p; k++) {
+        phase_apply(dim, cost, angles[p * n + k], psi);
+        for (int q = 0; q < n; q++) rot_qubit(dim, q, angles[k * n + q], psi);
+    }
+    *E = expect(dim, cost, psi);
+    for (int64_t a = 0; a < dim; a++) lam[a] = cost[a] * psi[a];
+    for (int k = p - 1; k >= 0; k--) {
+        for (int q = 0; q < n; q++) {
+            const int64_t st = (int64_t)1 << q;
+            double gb = 0.0;
+#pragma omp parallel for reduction(+ : gb) schedule(static)
+            for (int64_t a = 0; a < dim; a++) gb += cimag(conj(lam[a]) * psi[a ^ st]);
+            grad[k * n + q] = 2.0 * gb;
+        }
+        for (int q = 0; q < n; q++) {
+            rot_qubit(dim, q, -angles[k * n + q], lam);
+            rot_qubit(dim, q, -angles[k * n + q], psi);
+        }
+        double gg = 0.0;
+#pragma omp parallel for reduction(+ : gg) schedule(static)
+        for (int64_t a = 0; a < dim; a++) gg += cimag(conj(lam[a]) * cost[a] * psi[a]);
+        grad[p * n + k] = 2.0 * gg;
+        phase_apply(dim, cost, -angles[p * n + k], lam);
+        phase_apply(dim, cost, -angles[p * n + k], psi);
+    }
+    free(psi); free(lam);
+    return 0;
+}
+
 /* ------------------------------------------- single steps, for the tests */
 
 /* psi <- e^{-i beta H_M} psi (interleaved complex128, in place). */

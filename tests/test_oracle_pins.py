@@ -360,6 +360,48 @@ def test_maxcut_degeneracy_sum_rule(oracle_mod):
     assert np.all(d % 2 == 0)
 
 
+# ------------------------------------------------- multi-angle QAOA (Sec. 3)
+
+@pytest.mark.parametrize("n,p", [(3, 1), (5, 2), (6, 3)])
+def test_multi_angle_vs_dense_expm(oracle_mod, n, p):
+    """Round k applies e^{-i g_k C}, then e^{-i sum_q b_{kq} X_q} (the X_q
+    commute): a dense expm of the weighted Pauli sum."""
+    rng = np.random.default_rng(30 + n)
+    cost = oracle_mod.cost_maxcut(n, erdos_renyi(n, 0.6, 31 + n))
+    a = rng.random(p * (n + 1)) * np.pi
+    v = np.full(1 << n, 2 ** (-n / 2), dtype=np.complex128)
+    for k in range(p):
+        v = np.exp(-1j * a[p * n + k] * cost) * v
+        Hk = sum(a[k * n + q] * pauli_op(n, {q: PX}) for q in range(n))
+        v = sla.expm(-1j * Hk) @ v
+    E_ref = float(np.real(np.vdot(v, cost * v)))
+    E, _ = oracle_mod.qaoa_gradient_ma(n, cost, a)
+    assert E == pytest.approx(E_ref, abs=1e-12)
+
+
+def test_multi_angle_reduces_to_standard(oracle_mod):
+    """Equal angles on every qubit give the standard QAOA, and by the chain
+    rule the per-qubit beta partials of a round sum to dE/dbeta_k."""
+    n, p = 7, 3
+    cost = oracle_mod.cost_sk(n, sk_couplings(n, 32).astype(np.float64))
+    ang = np.random.default_rng(33).random(2 * p) * np.pi
+    a = np.concatenate([np.repeat(ang[:p], n), ang[p:]])
+    E, g = oracle_mod.qaoa_gradient_ma(n, cost, a)
+    E0, g0 = oracle_mod.qaoa_gradient(n, cost, ang)
+    assert E == pytest.approx(E0, abs=1e-12)
+    np.testing.assert_allclose(g[:p * n].reshape(p, n).sum(axis=1), g0[:p], atol=1e-10)
+    np.testing.assert_allclose(g[p * n:], g0[p:], atol=1e-10)
+
+
+def test_multi_angle_gradient_vs_finite_differences(oracle_mod):
+    n, p = 6, 2
+    cost = oracle_mod.cost_maxcut(n, erdos_renyi(n, 0.5, 34))
+    a = np.random.default_rng(35).random(p * (n + 1)) * np.pi
+    E, g = oracle_mod.qaoa_gradient_ma(n, cost, a)
+    fd = richardson_fd(lambda x: oracle_mod.qaoa_gradient_ma(n, cost, x)[0], a)
+    np.testing.assert_allclose(g, fd, atol=1e-8 * max(1.0, np.abs(g).max()))
+
+
 # -------------------------------------------------------- QAOA state, Eq. 1
 
 @pytest.mark.parametrize("n,p,seed", [(1, 1, 1), (3, 2, 2), (5, 3, 3), (8, 2, 4)])
