@@ -93,8 +93,13 @@ enum {
 
 /* Mixer kinds. */
 enum {
-    QAOA_MIXER_X = 0,    /* H_M = sum_i X_i on all 2^n states (Sec. 2.1, Eq. 2) */
-    QAOA_MIXER_EIGEN = 1 /* H_M = V diag(lambda) V^T on D feasible states (Sec. 2.1) */
+    QAOA_MIXER_X = 0,     /* H_M = sum_i X_i on all 2^n states (Sec. 2.1, Eq. 2) */
+    QAOA_MIXER_EIGEN = 1, /* H_M = V diag(lambda) V^T on D feasible states (Sec. 2.1) */
+    QAOA_MIXER_X_MA = 2   /* multi-angle QAOA (Sec. 3: one mixer per qubit per layer,
+                             each with its own angle): round k applies
+                             e^{-i beta_{k,q} X_q} to every qubit q.  An angle set is
+                             p (n + 1) values [beta_{1,0..n-1}, ..., beta_{p,0..n-1},
+                             gamma_1..gamma_p]; gradients use the same layout. */
 };
 
 /* Precision of the dense eigenbasis products for QAOA_MIXER_EIGEN. */
@@ -191,7 +196,8 @@ qaoa_status qaoa_clique_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, in
  *   d_cost, cost_dtype  cost vector over the mixer's feasible set
  *   d_init  device complex64 initial state (mixer->dim amplitudes) or NULL for
  *           the uniform superposition (Sec. 3, initial_state)
- *   p       rounds (>= 1); angles: host, 2p float64; E: host output.
+ *   p       rounds (>= 1); angles: host, 2p float64 (p (n + 1) for QAOA_MIXER_X_MA);
+ *           E: host output.
  * Synchronous on the context stream. */
 qaoa_status qaoa_expectation(qaoa_ctx *ctx, const void *d_cost, int cost_dtype,
                              const qaoa_mixer *mixer, const void *d_init, int p,
@@ -215,9 +221,10 @@ qaoa_status qaoa_gradient(qaoa_ctx *ctx, const void *d_cost, int cost_dtype,
                           const double *angles, double *E, double *grad, int ckpt);
 
 /* One batched job: n_sets angle sets evaluated on one cost vector and mixer.
- *   d_angles  device, n_sets x 2p float64 (row = one angle set)
+ *   d_angles  device, n_sets x 2p float64 (row = one angle set; p (n + 1) for
+ *             QAOA_MIXER_X_MA)
  *   d_E       device output, n_sets float64
- *   d_grad    device output, n_sets x 2p float64 (ignored unless want_grad)
+ *   d_grad    device output, n_sets rows like d_angles (ignored unless want_grad)
  *   d_init    device initial state shared by all sets, or NULL */
 typedef struct {
     const void *d_cost;

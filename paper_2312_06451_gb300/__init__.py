@@ -53,12 +53,23 @@ def _dev_tensor(t, name):
 
 
 class XMixer:
-    """Transverse-field mixer H_M = sum_i X_i on all 2^n states (Eq. 2)."""
+    """Transverse-field mixer H_M = sum_i X_i on all 2^n states (Eq. 2).
 
-    def __init__(self, n: int):
+    multi_angle=True: one angle per qubit and round (multi-angle QAOA, Sec. 3);
+    an angle set is then [beta_{1,0..n-1}, ..., beta_{p,0..n-1}, gamma_1..gamma_p]."""
+
+    def __init__(self, n: int, multi_angle: bool = False):
         self.n = int(n)
         self.dim = 1 << self.n
-        self.struct = B.QaoaMixer(B.QAOA_MIXER_X, self.n, self.dim, None, None, 0)
+        self.multi_angle = bool(multi_angle)
+        kind = B.QAOA_MIXER_X_MA if self.multi_angle else B.QAOA_MIXER_X
+        self.struct = B.QaoaMixer(kind, self.n, self.dim, None, None, 0)
+
+    def rounds(self, n_angles: int) -> int:
+        per = self.n + 1 if self.multi_angle else 2
+        if n_angles % per:
+            raise ValueError(f"{n_angles} angles do not make whole rounds of {per}")
+        return n_angles // per
 
 
 class EigenMixer:
@@ -268,7 +279,7 @@ class Context:
         a = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).ravel())
         E = ctypes.c_double()
         self._check(self._lib.qaoa_expectation(self._h, _ptr(cost), _cost_dtype(cost),
-                                               ctypes.byref(mixer.struct), _ptr(init), a.shape[0] // 2,
+                                               ctypes.byref(mixer.struct), _ptr(init), _rounds(mixer, a.shape[0]),
                                                a.ctypes.data_as(ctypes.c_void_p), ctypes.byref(E)))
         return E.value
 
@@ -282,7 +293,7 @@ class Context:
         E = ctypes.c_double()
         g = np.zeros(a.shape[0], dtype=np.float64)
         self._check(self._lib.qaoa_gradient(self._h, _ptr(cost), _cost_dtype(cost), ctypes.byref(mixer.struct),
-                                            _ptr(init), a.shape[0] // 2, a.ctypes.data_as(ctypes.c_void_p),
+                                            _ptr(init), _rounds(mixer, a.shape[0]), a.ctypes.data_as(ctypes.c_void_p),
                                             ctypes.byref(E), g.ctypes.data_as(ctypes.c_void_p),
                                             _ckpt_mode(ckpt)))
         return E.value, g
@@ -329,8 +340,8 @@ class Context:
             if ang.dtype != torch.float64 or E.dtype != torch.float64 or (G is not None and G.dtype != torch.float64):
                 raise TypeError("angles, E and grad must be float64")
             n_sets = ang.shape[0] if ang.dim() == 2 else 1
-            p = ang.shape[-1] // 2
             mx = j["mixer"]
+            p = _rounds(mx, ang.shape[-1])
             keep.append(mx)
             arr[i] = B.QaoaJob(cost.data_ptr(), _cost_dtype(cost), ctypes.pointer(mx.struct), p, n_sets,
                                ang.data_ptr(), E.data_ptr(), None if G is None else G.data_ptr(),
@@ -358,6 +369,13 @@ class Context:
 
     def scratch_bytes(self) -> int:
         return int(self._lib.qaoa_scratch_bytes(self._h))
+
+
+def _rounds(mixer, n_angles: int) -> int:
+    """p from the length of one angle set."""
+    if hasattr(mixer, "rounds"):
+        return mixer.rounds(n_angles)
+    return n_angles // 2
 
 
 def _ckpt_mode(m) -> int:

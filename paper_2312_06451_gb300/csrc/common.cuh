@@ -98,22 +98,24 @@ constexpr int kPassTileBits = 12;
 struct SmallDesc {
     const void *cost;
     const float2 *init;
-    const RoundCoef *coef;   // p entries
+    const RoundCoef *coef;   // p entries (p n for multi-angle)
     const float2 *table;     // p * kPhaseTable entries (uint8 costs)
     double *E_out;
     double *grad_out;        // 2p entries or nullptr
     int n;
     int p;
     float amp0;
-    int pad;
+    int nq;                  // multi-angle: n coefficients per round (else 0)
 };
 
 struct PrepDesc {
-    const double *angles;  // 2p
-    RoundCoef *coef;       // p
+    const double *angles;  // p (nq or 1) betas, then p gammas
+    RoundCoef *coef;       // p (nq or 1) entries
     float2 *table;         // p * kPhaseTable, or nullptr
     int p;
     int tsize;             // table entries used (<= kPhaseTable)
+    int nq;                // multi-angle: one beta per qubit (n), else 0
+    int pad;
 };
 
 // Two-level deterministic reduction of the per-(tile, warp) partial sums.
@@ -188,7 +190,7 @@ cudaError_t launch_reduce(const RedChunk *d_chunks, int nchunks, double *d_level
 cudaError_t launch_small(const SmallDesc *d_descs, int ndesc, int cost_dtype, int want_grad,
                          int max_n, int *d_err, cudaStream_t s);
 // bwd: 0 forward, 1 adjoint.  Persistent launch over total_tiles tiles.
-cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, const PassDesc *d_descs,
+cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int ma, const PassDesc *d_descs,
                          const uint32_t *d_tile_begin, int ndesc, uint32_t total_tiles,
                          int *d_err, cudaStream_t s);
 int small_max_n();

@@ -162,6 +162,35 @@ __device__ __forceinline__ void stage_rot(float2 (&a)[16], float2 (&l)[16], uint
     }
 }
 
+// Multi-angle rotations (one angle per qubit, direct form): register bit j
+// of the stage carries local bit Lj, rotated by rot[Lj] = (cos b, +-sin b);
+// the adjoint's pair terms go to one accumulator per local bit.
+template <int BWD, int L0, int L1, int L2, int L3>
+__device__ __forceinline__ void stage_rot_ma(float2 (&a)[16], float2 (&l)[16], uint32_t on, const float2 *rot,
+                                             float (&bq)[12], bool rot_psi) {
+    Rot R0, R1, R2, R3;
+    R0.c = rot[L0].x, R0.s = rot[L0].y;
+    R1.c = rot[L1].x, R1.s = rot[L1].y;
+    R2.c = rot[L2].x, R2.s = rot[L2].y;
+    R3.c = rot[L3].x, R3.s = rot[L3].y;
+    if (BWD) {
+        if (on & 1u) bq[L0] += pair_dot<0>(l, a);
+        if (on & 2u) bq[L1] += pair_dot<1>(l, a);
+        if (on & 4u) bq[L2] += pair_dot<2>(l, a);
+        if (on & 8u) bq[L3] += pair_dot<3>(l, a);
+        if (on & 1u) rot_pairs<0, 2>(l, R0);
+        if (on & 2u) rot_pairs<1, 2>(l, R1);
+        if (on & 4u) rot_pairs<2, 2>(l, R2);
+        if (on & 8u) rot_pairs<3, 2>(l, R3);
+    }
+    if (!BWD || rot_psi) {
+        if (on & 1u) rot_pairs<0, 2>(a, R0);
+        if (on & 2u) rot_pairs<1, 2>(a, R1);
+        if (on & 4u) rot_pairs<2, 2>(a, R2);
+        if (on & 8u) rot_pairs<3, 2>(a, R3);
+    }
+}
+
 // Register bits of the stage whose local bits are b0..b3, from the pass's
 // active-qubit mask.
 __device__ __forceinline__ uint32_t stage_mask(uint32_t active, int b0, int b1, int b2, int b3) {
@@ -429,8 +458,9 @@ struct PassConst {
 // copies of this body so the common one stays compact in the instruction
 // cache.  Optional work (initial state, phase, epilogue) sits in loops of its
 // own that are skipped as a whole when a pass does not need them.
-template <int BWD, int COST, int NBUF, int MODE>
+template <int BWD, int COST, int NBUF, int MODE, int MA>
 __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D, const float2 *stab,
+                                          const float2 *s_rot,
                                           unsigned char *bufs, int b, uint32_t bar, uint32_t t, uint32_t stride,
                                           uint32_t total, uint32_t base, uint32_t tl, TileInfo *tinfo,
                                           const PassDesc *__restrict__ descs,
@@ -450,6 +480,9 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     float2 a[16];
     float2 l[16];
     float pscale = 1.f, bacc = 0.f;
+    float bq[12];  // multi-angle: pair terms per local bit
+#pragma unroll
+    for (int j = 0; j < 12; j++) bq[j] = 0.f;
 
     // ---------------- stage 1: read the landed tile
     if (!BWD && (flags & PF_GEN_INIT)) {
@@ -511,7 +544,8 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
             }
         }
     }
-    stage_rot<BWD, MODE>(a, l, stage_mask(active, 0, 9, 10, 11), K.R, pscale, bacc, true);
+    if (MA) stage_rot_ma<BWD, 0, 9, 10, 11>(a, l, stage_mask(active, 0, 9, 10, 11), s_rot, bq, true);
+    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 0, 9, 10, 11), K.R, pscale, bacc, true);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs1);
         pscale = 1.f;
@@ -532,7 +566,8 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
         a[i] = sp[p2 ^ ((uint32_t)i << 1)];
         if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
     }
-    stage_rot<BWD, MODE>(a, l, stage_mask(active, 1, 2, 3, 4), K.R, pscale, bacc, true);
+    if (MA) stage_rot_ma<BWD, 1, 2, 3, 4>(a, l, stage_mask(active, 1, 2, 3, 4), s_rot, bq, true);
+    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 1, 2, 3, 4), K.R, pscale, bacc, true);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs2);
         pscale = 1.f;
@@ -596,7 +631,8 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     // psi after the last stage is needed only when it is stored or meets the
     // phase epilogue (the adjoint with per-pass checkpoints stores lambda only)
     const bool psi_live = !BWD || D.psi_out != nullptr || (flags & PF_PHASE);
-    stage_rot<BWD, MODE>(a, l, stage_mask(active, 5, 6, 7, 8), K.R, pscale, bacc, psi_live);
+    if (MA) stage_rot_ma<BWD, 5, 6, 7, 8>(a, l, stage_mask(active, 5, 6, 7, 8), s_rot, bq, psi_live);
+    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 5, 6, 7, 8), K.R, pscale, bacc, psi_live);
     scale_all<BWD>(a, l, K.rescale ? K.fs3 : K.fse);
 
     // ---------------- stage 3: fused epilogue, coalesced store
@@ -636,8 +672,17 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     }
     // per-warp partial sums: slot tile * 8 + warp (no block barrier)
     if (BWD) {
-        const double tb = warp_sum(bacc);
-        if (lane == 0 && D.part_beta) D.part_beta[tl * kNW + warp] = tb;
+        if (MA) {  // slot (local bit j, tile, warp)
+#pragma unroll
+            for (int j = 0; j < 12; j++) {
+                if (!((active >> j) & 1u)) continue;
+                const double tb = warp_sum(bq[j]);
+                if (lane == 0 && D.part_beta) D.part_beta[((size_t)j * D.ntiles + tl) * kNW + warp] = tb;
+            }
+        } else {
+            const double tb = warp_sum(bacc);
+            if (lane == 0 && D.part_beta) D.part_beta[tl * kNW + warp] = tb;
+        }
         if (flags & PF_PHASE) {
             const double tg = warp_sum(eacc);
             if (lane == 0 && D.part_gamma) D.part_gamma[tl * kNW + warp] = tg;
@@ -648,7 +693,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     }
 }
 
-template <int BWD, int COST, int NBUF>
+template <int BWD, int COST, int NBUF, int MA>
 __global__ void __launch_bounds__(kNT, (BWD && NBUF > 1) ? 1 : 2)
 xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ tile_begin, int ndesc,
              uint32_t total, int *err) {
@@ -659,6 +704,7 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
     float2 *stab = reinterpret_cast<float2 *>(smem_raw + 256);
     unsigned char *bufs = smem_raw + G::kHead;
     __shared__ PassDesc D;
+    __shared__ float2 s_rot[12];  // multi-angle: (cos, +-sin) per local bit
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -736,15 +782,28 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
             for (int k = 0; k < 4; k++) K.rs3[k] = 1u << D.gpos[5 + k];
             if (COST == 1 && (K.flags & PF_PHASE))
                 for (int i = tid; i < kPhaseTable; i += kNT) stab[i] = D.table[i];
+            if (MA) {
+                // per-qubit rotations: D.coef is this round's n entries, indexed
+                // by global qubit; the direct form needs no rescaling
+                if (tid < kT) {
+                    const RoundCoef q = D.coef[D.gpos[tid]];
+                    s_rot[tid] = make_float2(q.cb, sgn * q.sb);
+                }
+                K.rescale = 0;
+                K.fs1 = K.fs2 = K.fs3 = K.fse = 1.f;
+            }
             __syncthreads();
             cur = di;
         }
-        if (K.R.mode == 0)
-            tile_body<BWD, COST, NBUF, 0>(K, D, stab, bufs, b, bar, t, stride, total, ti.base, ti.tl, tinfo, descs,
-                                          tile_begin, ndesc, cursor);
+        if (MA)
+            tile_body<BWD, COST, NBUF, 2, 1>(K, D, stab, s_rot, bufs, b, bar, t, stride, total, ti.base, ti.tl,
+                                             tinfo, descs, tile_begin, ndesc, cursor);
+        else if (K.R.mode == 0)
+            tile_body<BWD, COST, NBUF, 0, 0>(K, D, stab, s_rot, bufs, b, bar, t, stride, total, ti.base, ti.tl,
+                                             tinfo, descs, tile_begin, ndesc, cursor);
         else
-            tile_body<BWD, COST, NBUF, 2>(K, D, stab, bufs, b, bar, t, stride, total, ti.base, ti.tl, tinfo, descs,
-                                          tile_begin, ndesc, cursor);
+            tile_body<BWD, COST, NBUF, 2, 0>(K, D, stab, s_rot, bufs, b, bar, t, stride, total, ti.base, ti.tl,
+                                             tinfo, descs, tile_begin, ndesc, cursor);
     }
 }
 
@@ -795,16 +854,20 @@ small_kernel(const SmallDesc *__restrict__ descs, int *err) {
         }
     };
 
+    // coefficients of round k: one entry, or one per qubit (multi-angle)
+    const int nb = D.nq ? D.nq : 1;
+    auto qcoef = [&](int k, int q) -> const RoundCoef & { return D.coef[k * nb + (D.nq ? q : 0)]; };
+
     for (int x = tid; x < N; x += kSmallThreads)
         psi[x] = D.init ? D.init[x] : make_float2(D.amp0, 0.f);
     for (int k = 0; k < p; k++) {
-        const RoundCoef cf = D.coef[k];
+        const RoundCoef cf = D.coef[k * nb];
         __syncthreads();
         load_table(k);
         for (int x = tid; x < N; x += kSmallThreads) psi[x] = cmul(psi[x], phase(x, cf));
         for (int q = 0; q < n; q++) {
             __syncthreads();
-            mix(psi, q, cf.cb, cf.sb);
+            mix(psi, q, qcoef(k, q).cb, qcoef(k, q).sb);
         }
     }
     __syncthreads();
@@ -819,23 +882,32 @@ small_kernel(const SmallDesc *__restrict__ descs, int *err) {
         lam[x] = make_float2(c * psi[x].x, c * psi[x].y);
     }
     for (int k = p - 1; k >= 0; k--) {
-        const RoundCoef cf = D.coef[k];
+        const RoundCoef cf = D.coef[k * nb];
         __syncthreads();
         float gb = 0.f;
         for (int q = 0; q < n; q++) {
+            float gq = 0.f;
             for (int j = tid; j < H; j += kSmallThreads) {
                 const int lo = j & ((1 << q) - 1);
                 const int x0 = ((j - lo) << 1) | lo, x1 = x0 | (1 << q);
                 const float2 l0 = lam[x0], l1 = lam[x1], a0 = psi[x0], a1 = psi[x1];
-                gb += l0.x * a1.y - l0.y * a1.x + l1.x * a0.y - l1.y * a0.x;
+                gq += l0.x * a1.y - l0.y * a1.x + l1.x * a0.y - l1.y * a0.x;
+            }
+            if (D.nq) {  // one partial per qubit
+                const double GQ = block_sum<kSmallThreads / 32>(gq, s_red);
+                if (tid == 0) D.grad_out[k * n + q] = 2.0 * GQ;
+            } else {
+                gb += gq;
             }
         }
-        const double GB = block_sum<kSmallThreads / 32>(gb, s_red);
-        if (tid == 0) D.grad_out[k] = 2.0 * GB;
+        if (!D.nq) {
+            const double GB = block_sum<kSmallThreads / 32>(gb, s_red);
+            if (tid == 0) D.grad_out[k] = 2.0 * GB;
+        }
         for (int q = 0; q < n; q++) {
             __syncthreads();
-            mix(lam, q, cf.cb, -cf.sb);
-            mix(psi, q, cf.cb, -cf.sb);
+            mix(lam, q, qcoef(k, q).cb, -qcoef(k, q).sb);
+            mix(psi, q, qcoef(k, q).cb, -qcoef(k, q).sb);
         }
         __syncthreads();
         load_table(k);
@@ -845,7 +917,7 @@ small_kernel(const SmallDesc *__restrict__ descs, int *err) {
             gg = fmaf(costv(x), l.x * a.y - l.y * a.x, gg);
         }
         const double GG = block_sum<kSmallThreads / 32>(gg, s_red);
-        if (tid == 0) D.grad_out[p + k] = 2.0 * GG;
+        if (tid == 0) D.grad_out[p * nb + k] = 2.0 * GG;
         for (int x = tid; x < N; x += kSmallThreads) {
             const float2 ph = phase(x, cf);
             lam[x] = cmul_conj(lam[x], ph);
@@ -859,8 +931,12 @@ small_kernel(const SmallDesc *__restrict__ descs, int *err) {
 // Angles -> per-round coefficients and uint8 phase tables (float64 math).
 __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ descs, int *err) {
     const PrepDesc D = descs[blockIdx.x];
-    for (int k = threadIdx.x; k < D.p; k += blockDim.x) {
-        const double be = D.angles[k], ga = D.angles[D.p + k];
+    // nb angles per round's mixer (nq qubits for multi-angle, else 1):
+    // beta_{k,q} = angles[k nb + q], gamma_k = angles[p nb + k]
+    const int nb = D.nq ? D.nq : 1;
+    for (int e = threadIdx.x; e < D.p * nb; e += blockDim.x) {
+        const int k = e / nb;
+        const double be = D.angles[e], ga = D.angles[D.p * nb + k];
         if (!isfinite(be) || !isfinite(ga)) atomicOr(err, DERR_BAD_ANGLE);
         const double cb = cos(be), sb = sin(be);
         RoundCoef c;
@@ -883,7 +959,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ 
         c.b_hi = (float)bb;
         c.b_lo = (float)(bb - (double)c.b_hi);
         c.pad = 0.f;
-        D.coef[k] = c;
+        D.coef[e] = c;
     }
     if (D.table) {
         const int tot = D.p * D.tsize;
@@ -891,7 +967,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ 
             const int k = e / D.tsize, cst = e - k * D.tsize;
             // e^{-i gamma c}: the turn fraction of gamma c / (2 pi) in float64
             // (exact integer part removed), then sin/cos of pi * 2f in float32
-            const double t = D.angles[D.p + k] / kTwoPi * (double)cst;
+            const double t = D.angles[D.p * nb + k] / kTwoPi * (double)cst;
             const float f = (float)(t - rint(t));
             float s, c;
             sincospif(2.f * f, &s, &c);
@@ -926,25 +1002,25 @@ __global__ void __launch_bounds__(32) reduce2_kernel(const RedOut *__restrict__ 
     if (threadIdx.x == 0) *O.out = O.scale * acc;
 }
 
-template <int BWD, int COST, int NBUF>
+template <int BWD, int COST, int NBUF, int MA>
 cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t tiles, int *err,
                        cudaStream_t s) {
     using G = PassGeom<BWD, COST>;
     const size_t smem = G::kHead + (size_t)NBUF * G::kBufB + G::kStashB;
     static int grid_cap = 0;
     if (!grid_cap) {
-        cudaError_t e = cudaFuncSetAttribute(xpass_kernel<BWD, COST, NBUF>,
+        cudaError_t e = cudaFuncSetAttribute(xpass_kernel<BWD, COST, NBUF, MA>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, nsm = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xpass_kernel<BWD, COST, NBUF>, kNT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xpass_kernel<BWD, COST, NBUF, MA>, kNT, smem);
         if (e != cudaSuccess) return e;
         grid_cap = std::max(1, nsm * std::max(1, per_sm));
     }
     const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)grid_cap);
-    xpass_kernel<BWD, COST, NBUF><<<grid, kNT, smem, s>>>(d, tb, nd, tiles, err);
+    xpass_kernel<BWD, COST, NBUF, MA><<<grid, kNT, smem, s>>>(d, tb, nd, tiles, err);
     return cudaGetLastError();
 }
 
@@ -952,18 +1028,25 @@ cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t t
 
 int small_max_n() { return kSmallMaxN; }
 
-cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, const PassDesc *d, const uint32_t *tb, int nd,
-                         uint32_t tiles, int *err, cudaStream_t s) {
-    if (tiles == 0) return cudaSuccess;
-    if (!bwd) return cost_dtype == 0 ? launch_one<0, 0, 2>(d, tb, nd, tiles, err, s)
-                                     : launch_one<0, 1, 2>(d, tb, nd, tiles, err, s);
+template <int MA>
+cudaError_t launch_xpass_t(int bwd, int cost_dtype, int nbuf, const PassDesc *d, const uint32_t *tb, int nd,
+                           uint32_t tiles, int *err, cudaStream_t s) {
+    if (!bwd) return cost_dtype == 0 ? launch_one<0, 0, 2, MA>(d, tb, nd, tiles, err, s)
+                                     : launch_one<0, 1, 2, MA>(d, tb, nd, tiles, err, s);
     // adjoint: one tile buffer and two CTAs per SM (128 registers a thread),
     // or two buffers and one CTA per SM (no register cap below 255)
     if (nbuf == 2)
-        return cost_dtype == 0 ? launch_one<1, 0, 2>(d, tb, nd, tiles, err, s)
-                               : launch_one<1, 1, 2>(d, tb, nd, tiles, err, s);
-    return cost_dtype == 0 ? launch_one<1, 0, 1>(d, tb, nd, tiles, err, s)
-                           : launch_one<1, 1, 1>(d, tb, nd, tiles, err, s);
+        return cost_dtype == 0 ? launch_one<1, 0, 2, MA>(d, tb, nd, tiles, err, s)
+                               : launch_one<1, 1, 2, MA>(d, tb, nd, tiles, err, s);
+    return cost_dtype == 0 ? launch_one<1, 0, 1, MA>(d, tb, nd, tiles, err, s)
+                           : launch_one<1, 1, 1, MA>(d, tb, nd, tiles, err, s);
+}
+
+cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int ma, const PassDesc *d, const uint32_t *tb, int nd,
+                         uint32_t tiles, int *err, cudaStream_t s) {
+    if (tiles == 0) return cudaSuccess;
+    return ma ? launch_xpass_t<1>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, s)
+              : launch_xpass_t<0>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, s);
 }
 
 cudaError_t launch_small(const SmallDesc *d, int nd, int cost_dtype, int want_grad, int max_n,

@@ -59,13 +59,14 @@ struct Unit {
     const float *V;        // eigenbasis mixer: D x D eigenvectors
     const double *lam;     // eigenbasis mixer: D eigenvalues
     int gemm_precision;
+    int ma;                // X mixer with one angle per (round, qubit)
 };
 
 enum LaunchKind { LK_PREP, LK_SMALL, LK_XPASS, LK_REDUCE, LK_EIG_INIT, LK_EIG_GEMM };
 
 struct LaunchRec {
     int kind;
-    int T = 0, bwd = 0, cost_dtype = 0, nbuf = 1;
+    int T = 0, bwd = 0, cost_dtype = 0, nbuf = 1, ma = 0;
     size_t desc_off = 0, tb_off = 0;
     int ndesc = 0;
     uint32_t tiles = 0;
@@ -376,7 +377,8 @@ UnitLayout layout_for(const qaoa_ctx *ctx, const Unit &u, bool grad, int ckpt) {
     L.gb = L.gf;  // per-pass checkpoints pair forward and adjoint passes one to one
     L.tiles_f = 1u << (u.n - L.T_f);
     L.tiles_b = 1u << (u.n - L.T_b);
-    L.stride = std::max<int64_t>(L.tiles_f, (int64_t)L.gb.size() * L.tiles_b) * kPassWarps;
+    L.stride = std::max<int64_t>(L.tiles_f, (int64_t)L.gb.size() * (u.ma ? kPassTileBits : 1) * L.tiles_b) *
+               kPassWarps;
     L.ckpt = grad ? ckpt : QAOA_CKPT_NONE;
     L.vecs = layout_vecs(L, u.p, grad);
     L.nb_bc = t.nbuf_bwd_contig;
@@ -432,6 +434,8 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
     const int Pf = (int)L.gf.size(), Pb = (int)L.gb.size();
     const float amp0 = (float)(1.0 / std::sqrt(std::ldexp(1.0, u.n)));
     const int ckpt = L.ckpt;
+    const int nbq = u.ma ? u.n : 1;                               // coefficients per round
+    const int64_t bslot = (u.ma ? kPassTileBits : 1) * (int64_t)L.tiles_b * kPassWarps;  // beta partials per pass
     auto ck = [&](int k) { return CK + (int64_t)k * N; };
     auto pk = [&](int k, int g) { return CK + ((int64_t)k * Pf + g) * N; };
     if (grad && ckpt == QAOA_CKPT_PASS) {
@@ -441,7 +445,7 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
                 std::memset(&d, 0, sizeof(d));
                 fill_geometry(d, u.n, L.T_f, L.gf[g]);
                 d.cost = u.cost;
-                d.coef = coef + k;
+                d.coef = coef + (int64_t)k * nbq;
                 d.table = table ? table + (int64_t)k * kPhaseTable : nullptr;
                 d.amp0 = amp0;
                 if (g == 0) {
@@ -476,7 +480,7 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
                 std::memset(&d, 0, sizeof(d));
                 fill_geometry(d, u.n, L.T_b, L.gb[g]);
                 d.cost = u.cost;
-                d.coef = coef + k;
+                d.coef = coef + (int64_t)k * nbq;
                 d.table = table ? table + (int64_t)k * kPhaseTable : nullptr;
                 d.amp0 = amp0;
                 d.psi_in = pk(k, g);
@@ -489,7 +493,7 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
                 } else {
                     d.lam_out = Lam;
                 }
-                d.part_beta = part + (int64_t)(1 + k) * L.stride + (int64_t)q * L.tiles_b * kPassWarps;
+                d.part_beta = part + (int64_t)(1 + k) * L.stride + (int64_t)q * bslot;
                 bwd.push_back(d);
             }
         }
@@ -501,7 +505,7 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
             std::memset(&d, 0, sizeof(d));
             fill_geometry(d, u.n, L.T_f, L.gf[g]);
             d.cost = u.cost;
-            d.coef = coef + k;
+            d.coef = coef + (int64_t)k * nbq;
             d.table = table ? table + (int64_t)k * kPhaseTable : nullptr;
             d.amp0 = amp0;
             const bool first = g == 0, last = g == Pf - 1;
@@ -543,7 +547,7 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
             std::memset(&d, 0, sizeof(d));
             fill_geometry(d, u.n, L.T_b, L.gb[g]);
             d.cost = u.cost;
-            d.coef = coef + k;
+            d.coef = coef + (int64_t)k * nbq;
             d.table = table ? table + (int64_t)k * kPhaseTable : nullptr;
             d.amp0 = amp0;
             const bool first_round = k == p - 1;
@@ -568,7 +572,7 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
                 d.psi_out = W;
                 d.lam_out = Lam;
             }
-            d.part_beta = part + (int64_t)(1 + k) * L.stride + (int64_t)q * L.tiles_b * kPassWarps;
+            d.part_beta = part + (int64_t)(1 + k) * L.stride + (int64_t)q * bslot;
             bwd.push_back(d);
         }
     }
@@ -597,7 +601,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         // job are consecutive, so their rounds form a [set][round] array)
         for (int i = 0; i < nu; i++) {
             off_coef[i] = meta;
-            meta += sizeof(RoundCoef) * units[i].p;
+            meta += sizeof(RoundCoef) * units[i].p * (units[i].ma ? units[i].n : 1);
         }
         meta = align_up(meta);
         for (int i = 0; i < nu; i++) {
@@ -617,10 +621,10 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
 
         // ---- state memory: pass units grouped by launch shape, admitted in waves
         struct GKey {
-            int Tf, Tb, Pf, Pb, p, dt, nbc, nbg;
+            int Tf, Tb, Pf, Pb, p, dt, nbc, nbg, ma;
             bool operator<(const GKey &o) const {
-                return std::tie(Tf, Tb, Pf, Pb, p, dt, nbc, nbg) <
-                       std::tie(o.Tf, o.Tb, o.Pf, o.Pb, o.p, o.dt, o.nbc, o.nbg);
+                return std::tie(Tf, Tb, Pf, Pb, p, dt, nbc, nbg, ma) <
+                       std::tie(o.Tf, o.Tb, o.Pf, o.Pb, o.p, o.dt, o.nbc, o.nbg, o.ma);
             }
         };
         std::map<GKey, std::vector<int>> groups;
@@ -628,7 +632,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             if (units[i].mixer_kind != QAOA_MIXER_X || units[i].n <= smax) continue;
             const UnitLayout &L = lay[i];
             groups[{L.T_f, L.T_b, (int)L.gf.size(), (int)L.gb.size(), units[i].p, units[i].cost_dtype, L.nb_bc,
-                    L.nb_bg}]
+                    L.nb_bg, units[i].ma}]
                 .push_back(i);
         }
         size_t free_b = 0, total_b = 0;
@@ -697,6 +701,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             prep[i].table = u.cost_dtype == QAOA_COST_U8 ? reinterpret_cast<float2 *>(mb + off_tab[i]) : nullptr;
             prep[i].p = u.p;
             prep[i].tsize = u.tsize;
+            prep[i].nq = u.ma ? u.n : 0;
         }
         {
             LaunchRec r;
@@ -723,6 +728,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 s.grad_out = grad ? u.grad : nullptr;
                 s.n = u.n;
                 s.p = u.p;
+                s.nq = u.ma ? u.n : 0;
                 s.amp0 = 1.0f / std::sqrt((float)(1u << u.n));
                 sd.push_back(s);
                 maxn = std::max(maxn, u.n);
@@ -815,12 +821,24 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                     const int64_t S = lay[i].stride;
                     add_reduction(part, (int64_t)lay[i].tiles_f * kPassWarps, u.E, 1.0);
                     if (grad) {
+                        const int64_t tw = (int64_t)lay[i].tiles_b * kPassWarps;
+                        const int Pb = (int)lay[i].gb.size();
+                        const int nbq = u.ma ? u.n : 1;
                         for (int k = 0; k < u.p; k++) {
-                            add_reduction(part + (1 + k) * S,
-                                          (int64_t)lay[i].gb.size() * lay[i].tiles_b * kPassWarps, u.grad + k,
-                                          2.0);
-                            add_reduction(part + (1 + u.p + k) * S, (int64_t)lay[i].tiles_b * kPassWarps,
-                                          u.grad + u.p + k, 2.0);
+                            if (u.ma) {
+                                // qubit of local bit j in adjoint pass q (group Pb - 1 - q)
+                                for (int q = 0; q < Pb; q++) {
+                                    const Group &G = lay[i].gb[Pb - 1 - q];
+                                    for (int j = (G.c >= kPassTileBits ? 0 : G.c); j < kPassTileBits; j++) {
+                                        const int qb = G.c >= kPassTileBits ? j : G.lo + (j - G.c);
+                                        add_reduction(part + (1 + k) * S + ((int64_t)q * kPassTileBits + j) * tw, tw,
+                                                      u.grad + (int64_t)k * u.n + qb, 2.0);
+                                    }
+                                }
+                            } else {
+                                add_reduction(part + (1 + k) * S, (int64_t)Pb * tw, u.grad + k, 2.0);
+                            }
+                            add_reduction(part + (1 + u.p + k) * S, tw, u.grad + (int64_t)u.p * nbq + k, 2.0);
                         }
                     }
                 }
@@ -842,6 +860,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 r.bwd = bwd;
                 r.cost_dtype = gk.dt;
                 r.nbuf = bwd ? (steps[s][0].c >= kPassTileBits ? gk.nbc : gk.nbg) : 2;
+                r.ma = gk.ma;
                 r.desc_off = put(steps[s].data(), sizeof(PassDesc) * steps[s].size());
                 xpass_descs.push_back({r.desc_off, (int)steps[s].size()});
                 r.tb_off = put(tb.data(), sizeof(uint32_t) * tb.size());
@@ -850,7 +869,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 r.bytes = bytes;
                 char nm[64];
                 const int c0 = steps[s][0].c;
-                snprintf(nm, sizeof(nm), "xpass_%s_%s_%s", bwd ? "bwd" : "fwd",
+                snprintf(nm, sizeof(nm), "xpass%s_%s_%s_%s", gk.ma ? "_ma" : "", bwd ? "bwd" : "fwd",
                          c0 >= kPassTileBits ? "contig" : (c0 >= 6 ? "gather_wide" : "gather"),
                          dtype_name(gk.dt));
                 r.fam = family(ctx, nm);
@@ -1128,7 +1147,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                              r.small_grad, r.small_maxn, ctx->d_err, ctx->stream);
             break;
         case LK_XPASS:
-            e = launch_xpass(r.bwd, r.cost_dtype, r.nbuf, reinterpret_cast<const PassDesc *>(db + r.desc_off),
+            e = launch_xpass(r.bwd, r.cost_dtype, r.nbuf, r.ma, reinterpret_cast<const PassDesc *>(db + r.desc_off),
                              reinterpret_cast<const uint32_t *>(db + r.tb_off), r.ndesc, r.tiles,
                              ctx->d_err, ctx->stream);
             break;
@@ -1179,7 +1198,8 @@ qaoa_status check_args(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
         if (d_init && ((uintptr_t)d_init & 7)) return fail(ctx, QAOA_ERR_INVALID, "d_init must be 8-byte aligned");
         return QAOA_OK;
     }
-    if (mx->kind != QAOA_MIXER_X) return fail(ctx, QAOA_ERR_INVALID, "unknown mixer kind %d", mx->kind);
+    if (mx->kind != QAOA_MIXER_X && mx->kind != QAOA_MIXER_X_MA)
+        return fail(ctx, QAOA_ERR_INVALID, "unknown mixer kind %d", mx->kind);
     if (mx->n < 1 || mx->n > kMaxXQubits)
         return fail(ctx, QAOA_ERR_INVALID, "X mixer needs 1 <= n <= %d (got %d)", kMaxXQubits, mx->n);
     if (mx->dim != (1ll << mx->n))
@@ -1216,9 +1236,11 @@ qaoa_status scalar_run(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
     if (st) return st;
     if (!angles || !E || (grad == nullptr) != (ckpt < 0))
         return fail(ctx, QAOA_ERR_INVALID, "angles and result pointers must be non-NULL");
-    for (int i = 0; i < 2 * p; i++)
+    const int ma = mixer->kind == QAOA_MIXER_X_MA;
+    const int na = ma ? p * (mixer->n + 1) : 2 * p;  // angles (and partials) per set
+    for (int i = 0; i < na; i++)
         if (!std::isfinite(angles[i])) return fail(ctx, QAOA_ERR_INVALID, "angle %d is not finite", i);
-    const size_t cnt = (size_t)4 * p + 1;
+    const size_t cnt = (size_t)2 * na + 1;
     void *d_io = nullptr;
     st = scratch(ctx, "io", cnt * sizeof(double), &d_io);
     if (st) return st;
@@ -1233,9 +1255,9 @@ qaoa_status scalar_run(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
                 "cudaMallocHost");
         ctx->h_io_count = cnt;
     }
-    std::memcpy(ctx->h_io, angles, sizeof(double) * 2 * p);
+    std::memcpy(ctx->h_io, angles, sizeof(double) * na);
     double *io = static_cast<double *>(d_io);
-    QG_CUDA(ctx, cudaMemcpyAsync(io, ctx->h_io, sizeof(double) * 2 * p, cudaMemcpyHostToDevice, ctx->stream),
+    QG_CUDA(ctx, cudaMemcpyAsync(io, ctx->h_io, sizeof(double) * na, cudaMemcpyHostToDevice, ctx->stream),
             "angle upload");
     Unit u;
     std::memset(&u, 0, sizeof(u));
@@ -1244,11 +1266,12 @@ qaoa_status scalar_run(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
     u.n = mixer->n;
     u.p = p;
     u.angles = io;
-    u.E = io + 2 * p;
-    u.grad = grad ? io + 2 * p + 1 : nullptr;
+    u.E = io + na;
+    u.grad = grad ? io + na + 1 : nullptr;
     u.init = static_cast<const float2 *>(d_init);
     u.tsize = kPhaseTable;
-    u.mixer_kind = mixer->kind;
+    u.mixer_kind = ma ? QAOA_MIXER_X : mixer->kind;
+    u.ma = ma;
     u.dim = mixer->dim;
     u.V = mixer->d_V;
     u.lam = mixer->d_lambda;
@@ -1256,14 +1279,14 @@ qaoa_status scalar_run(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
     std::vector<Unit> us(1, u);
     st = run_units(ctx, us, grad != nullptr, grad ? ckpt : 0);
     if (st) return st;
-    const size_t nout = grad ? (size_t)2 * p + 1 : 1;
-    QG_CUDA(ctx, cudaMemcpyAsync(ctx->h_io + 2 * p, io + 2 * p, sizeof(double) * nout, cudaMemcpyDeviceToHost,
+    const size_t nout = grad ? (size_t)na + 1 : 1;
+    QG_CUDA(ctx, cudaMemcpyAsync(ctx->h_io + na, io + na, sizeof(double) * nout, cudaMemcpyDeviceToHost,
                                  ctx->stream),
             "result download");
     st = read_dev_err(ctx);
     if (st) return st;
-    *E = ctx->h_io[2 * p];
-    if (grad) std::memcpy(grad, ctx->h_io + 2 * p + 1, sizeof(double) * 2 * p);
+    *E = ctx->h_io[na];
+    if (grad) std::memcpy(grad, ctx->h_io + na + 1, sizeof(double) * na);
     return QAOA_OK;
 }
 
@@ -1528,6 +1551,8 @@ qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *
             if (st) return st;
             if (jb.n_sets < 1 || !jb.d_angles || !jb.d_E || (want_grad && !jb.d_grad))
                 return fail(ctx, QAOA_ERR_INVALID, "job %d: bad sets or output pointers", j);
+            const int ma = jb.mixer->kind == QAOA_MIXER_X_MA;
+            const int64_t na = ma ? (int64_t)jb.p * (jb.mixer->n + 1) : 2 * (int64_t)jb.p;
             for (int s = 0; s < jb.n_sets; s++) {
                 Unit u;
                 std::memset(&u, 0, sizeof(u));
@@ -1535,12 +1560,13 @@ qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *
                 u.cost_dtype = jb.cost_dtype;
                 u.n = jb.mixer->n;
                 u.p = jb.p;
-                u.angles = jb.d_angles + (int64_t)s * 2 * jb.p;
+                u.angles = jb.d_angles + (int64_t)s * na;
                 u.E = jb.d_E + s;
-                u.grad = want_grad ? jb.d_grad + (int64_t)s * 2 * jb.p : nullptr;
+                u.grad = want_grad ? jb.d_grad + (int64_t)s * na : nullptr;
                 u.init = static_cast<const float2 *>(jb.d_init);
                 u.tsize = kPhaseTable;
-                u.mixer_kind = jb.mixer->kind;
+                u.mixer_kind = ma ? QAOA_MIXER_X : jb.mixer->kind;
+                u.ma = ma;
                 u.job = j;
                 u.dim = jb.mixer->dim;
                 u.V = jb.mixer->d_V;
