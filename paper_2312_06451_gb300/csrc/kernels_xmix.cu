@@ -165,9 +165,9 @@ __device__ __forceinline__ void stage_rot(float2 (&a)[16], float2 (&l)[16], uint
 // Multi-angle rotations (one angle per qubit, direct form): register bit j
 // of the stage carries local bit Lj, rotated by rot[Lj] = (cos b, +-sin b);
 // the adjoint's pair terms go to one accumulator per local bit.
-template <int BWD, int L0, int L1, int L2, int L3>
+template <int BWD, int L0, int L1, int L2, int L3, int NQ>
 __device__ __forceinline__ void stage_rot_ma(float2 (&a)[16], float2 (&l)[16], uint32_t on, const float2 *rot,
-                                             float (&bq)[12], bool rot_psi) {
+                                             float (&bq)[NQ], bool rot_psi) {
     Rot R0, R1, R2, R3;
     R0.c = rot[L0].x, R0.s = rot[L0].y;
     R1.c = rot[L1].x, R1.s = rot[L1].y;
@@ -480,9 +480,9 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     float2 a[16];
     float2 l[16];
     float pscale = 1.f, bacc = 0.f;
-    float bq[12];  // multi-angle: pair terms per local bit
+    float bq[MA ? 12 : 1];  // multi-angle: pair terms per local bit
 #pragma unroll
-    for (int j = 0; j < 12; j++) bq[j] = 0.f;
+    for (int j = 0; j < (MA ? 12 : 1); j++) bq[j] = 0.f;
 
     // ---------------- stage 1: read the landed tile
     if (!BWD && (flags & PF_GEN_INIT)) {
@@ -544,7 +544,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
             }
         }
     }
-    if (MA) stage_rot_ma<BWD, 0, 9, 10, 11>(a, l, stage_mask(active, 0, 9, 10, 11), s_rot, bq, true);
+    if constexpr (MA) stage_rot_ma<BWD, 0, 9, 10, 11>(a, l, stage_mask(active, 0, 9, 10, 11), s_rot, bq, true);
     else stage_rot<BWD, MODE>(a, l, stage_mask(active, 0, 9, 10, 11), K.R, pscale, bacc, true);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs1);
@@ -566,7 +566,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
         a[i] = sp[p2 ^ ((uint32_t)i << 1)];
         if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
     }
-    if (MA) stage_rot_ma<BWD, 1, 2, 3, 4>(a, l, stage_mask(active, 1, 2, 3, 4), s_rot, bq, true);
+    if constexpr (MA) stage_rot_ma<BWD, 1, 2, 3, 4>(a, l, stage_mask(active, 1, 2, 3, 4), s_rot, bq, true);
     else stage_rot<BWD, MODE>(a, l, stage_mask(active, 1, 2, 3, 4), K.R, pscale, bacc, true);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs2);
@@ -631,7 +631,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     // psi after the last stage is needed only when it is stored or meets the
     // phase epilogue (the adjoint with per-pass checkpoints stores lambda only)
     const bool psi_live = !BWD || D.psi_out != nullptr || (flags & PF_PHASE);
-    if (MA) stage_rot_ma<BWD, 5, 6, 7, 8>(a, l, stage_mask(active, 5, 6, 7, 8), s_rot, bq, psi_live);
+    if constexpr (MA) stage_rot_ma<BWD, 5, 6, 7, 8>(a, l, stage_mask(active, 5, 6, 7, 8), s_rot, bq, psi_live);
     else stage_rot<BWD, MODE>(a, l, stage_mask(active, 5, 6, 7, 8), K.R, pscale, bacc, psi_live);
     scale_all<BWD>(a, l, K.rescale ? K.fs3 : K.fse);
 
@@ -672,7 +672,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     }
     // per-warp partial sums: slot tile * 8 + warp (no block barrier)
     if (BWD) {
-        if (MA) {  // slot (local bit j, tile, warp)
+        if constexpr (MA) {  // slot (local bit j, tile, warp)
 #pragma unroll
             for (int j = 0; j < 12; j++) {
                 if (!((active >> j) & 1u)) continue;
