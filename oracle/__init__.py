@@ -69,6 +69,8 @@ def _load():
             "oracle_mixer_apply": (i32, [i32, i32, i64, P, f64, P]),
             "oracle_hm_apply": (i32, [i32, i32, i64, P, P, P]),
             "oracle_qaoa_gradient_ma": (i32, [i32, P, i32, P, P, P, P]),
+            "oracle_qaoa_gradient_general": (i32, [i32, P, P, i32, P, P, P, P]),
+            "oracle_general_mixer_apply": (i32, [i32, P, f64, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -289,6 +291,44 @@ def qaoa_gradient_ma(n, cost, angles, psi0=None):
     if r:
         raise RuntimeError(f"oracle_qaoa_gradient_ma failed ({r})")
     return float(E[0]), g
+
+
+def krawtchouk_weights(n, coeffs) -> np.ndarray:
+    """d_w = sum_k c_k K_k(w) for w = 0..n: the Hadamard-basis eigenvalues of
+    f(X) = sum_S c_{|S|} prod_{i in S} X_i (Sec. 2.1); coeffs maps the term
+    order k to c_k."""
+    import math
+
+    d = np.zeros(n + 1)
+    for w in range(n + 1):
+        for k, ck in coeffs.items():
+            d[w] += ck * sum((-1) ** j * math.comb(w, j) * math.comb(n - w, k - j) for j in range(0, k + 1))
+    return d
+
+
+def qaoa_gradient_general(n, d, cost, angles, psi0=None):
+    """(E, grad) of QAOA with the general X mixer H^n diag(d_|z|) H^n."""
+    dd = _f64(d)
+    if dd.shape[0] != n + 1:
+        raise ValueError("d needs n + 1 entries")
+    cost = _f64(cost)
+    a = _f64(angles)
+    p = a.shape[0] // 2
+    E = np.zeros(1)
+    g = np.zeros(2 * p)
+    r = _load().oracle_qaoa_gradient_general(n, _ptr(dd), _ptr(cost), p, _ptr(a), _ptr(_c128(psi0)), _ptr(E),
+                                             _ptr(g))
+    if r:
+        raise RuntimeError(f"oracle_qaoa_gradient_general failed ({r})")
+    return float(E[0]), g
+
+
+def general_mixer_apply(n, d, psi, beta) -> np.ndarray:
+    v = _c128(psi).copy()
+    r = _load().oracle_general_mixer_apply(n, _ptr(_f64(d)), float(beta), _ptr(v))
+    if r:
+        raise RuntimeError(f"oracle_general_mixer_apply failed ({r})")
+    return v
 
 
 def mixer_apply(n, psi, beta, mixer="x", states=None) -> np.ndarray:

@@ -484,6 +484,90 @@ int oracle_qaoa_gradient_ma(int n, const double *cost, int p, const double *angl
     return 0;
 }
 
+/* ----------------------------------------- general X mixers (Sec. 2.1) */
+
+/* Mixers written as sums of products of Pauli X: H_M = f(X) with
+ * f(X) = sum_S c_{|S|} prod_{i in S} X_i (Sec. 2.1: e^{-i beta f(X_i)} =
+ * H^n e^{-i beta f(Z_i)} H^n, with the diagonal form precomputed).  On the
+ * Hadamard-basis state |z> of weight w, prod_{i in S} Z_i has eigenvalue
+ * (-1)^{|S & z|}, so f(Z) = d_w with d_w = sum_k c_k K_k(w), K_k the
+ * Krawtchouk polynomial sum_j (-1)^j C(w, j) C(n - w, k - j).  The oracle
+ * takes d[0..n] and applies e^{-i beta H_M} literally: a Walsh-Hadamard
+ * transform (n Hadamard butterflies), the weight phases, the transform again.
+ * The Grover mixer |+><+| is c_k = 2^-n for all k, i.e. d_w = [w = 0]. */
+static void hadamard_all(int n, cplx *v) {
+    const int64_t dim = (int64_t)1 << n;
+    const double r = 1.0 / sqrt(2.0);
+    for (int q = 0; q < n; q++) {
+        const int64_t st = (int64_t)1 << q;
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < dim / 2; j++) {
+            int64_t lo = j & (st - 1);
+            int64_t x0 = ((j - lo) << 1) | lo, x1 = x0 | st;
+            cplx a = v[x0], b = v[x1];
+            v[x0] = r * (a + b);
+            v[x1] = r * (a - b);
+        }
+    }
+}
+
+static void general_mixer(int n, const double *d, double beta, cplx *v) {
+    const int64_t dim = (int64_t)1 << n;
+    hadamard_all(n, v);
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < dim; x++) v[x] *= cexp(-I * beta * d[__builtin_popcountll((uint64_t)x)]);
+    hadamard_all(n, v);
+}
+
+/* out = H_M v = H^n diag(d_w) H^n v. */
+static void general_hm(int n, const double *d, const cplx *v, cplx *out) {
+    const int64_t dim = (int64_t)1 << n;
+    memcpy(out, v, sizeof(cplx) * dim);
+    hadamard_all(n, out);
+    for (int64_t x = 0; x < dim; x++) out[x] *= d[__builtin_popcountll((uint64_t)x)];
+    hadamard_all(n, out);
+}
+
+/* <C> and its 2p derivatives (angle layout of Listing 1) for the general X
+ * mixer with Hadamard-basis weights d[0..n]; reverse mode as in
+ * oracle_qaoa_gradient. */
+int oracle_qaoa_gradient_general(int n, const double *d, const double *cost, int p, const double *angles,
+                                 const double *psi0, double *E, double *grad) {
+    const int64_t dim = (int64_t)1 << n;
+    if (p < 1 || n < 1 || n > 30) return -1;
+    cplx *psi = malloc(sizeof(cplx) * dim), *lam = malloc(sizeof(cplx) * dim), *hv = malloc(sizeof(cplx) * dim);
+    if (!psi || !lam || !hv) { free(psi); free(lam); free(hv); return -2; }
+    init_state(dim, psi0, psi);
+    for (int k = 0; k < p; k++) {
+        phase_apply(dim, cost, angles[p + k], psi);
+        general_mixer(n, d, angles[k], psi);
+    }
+    *E = expect(dim, cost, psi);
+    for (int64_t a = 0; a < dim; a++) lam[a] = cost[a] * psi[a];
+    for (int k = p - 1; k >= 0; k--) {
+        general_hm(n, d, psi, hv);
+        double gb = 0.0;
+        for (int64_t a = 0; a < dim; a++) gb += cimag(conj(lam[a]) * hv[a]);
+        grad[k] = 2.0 * gb;
+        general_mixer(n, d, -angles[k], lam);
+        general_mixer(n, d, -angles[k], psi);
+        double gg = 0.0;
+        for (int64_t a = 0; a < dim; a++) gg += cimag(conj(lam[a]) * cost[a] * psi[a]);
+        grad[p + k] = 2.0 * gg;
+        phase_apply(dim, cost, -angles[p + k], lam);
+        phase_apply(dim, cost, -angles[p + k], psi);
+    }
+    free(psi); free(lam); free(hv);
+    return 0;
+}
+
+/* psi <- e^{-i beta H_M} psi for the general X mixer (interleaved complex128). */
+int oracle_general_mixer_apply(int n, const double *d, double beta, double *psi) {
+    if (n < 1 || n > 30) return -1;
+    general_mixer(n, d, beta, (cplx *)psi);
+    return 0;
+}
+
 /* ------------------------------------------- single steps, for the tests */
 
 /* psi <- e^{-i beta H_M} psi (interleaved complex128, in place). */

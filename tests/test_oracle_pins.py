@@ -402,6 +402,63 @@ def test_multi_angle_gradient_vs_finite_differences(oracle_mod):
     np.testing.assert_allclose(g, fd, atol=1e-8 * max(1.0, np.abs(g).max()))
 
 
+# ---------------------------------------------- general X mixers (Sec. 2.1)
+
+def dense_x_products(n, coeffs):
+    H = 0
+    for k, ck in coeffs.items():
+        for S in itertools.combinations(range(n), k):
+            H = H + ck * pauli_op(n, {q: PX for q in S})
+    return H
+
+
+@pytest.mark.parametrize("coeffs", [{1: 1.0}, {2: 1.0}, {1: 1.0, 2: 0.5}, {3: -0.7, 1: 0.2}, {0: 0.3, 4: 1.0}])
+def test_general_mixer_vs_dense_pauli_products(oracle_mod, coeffs):
+    n = 5
+    d = oracle_mod.krawtchouk_weights(n, coeffs)
+    H = dense_x_products(n, coeffs)
+    rng = np.random.default_rng(40)
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    for beta in (0.6, -1.9):
+        np.testing.assert_allclose(oracle_mod.general_mixer_apply(n, d, v, beta), sla.expm(-1j * beta * H) @ v,
+                                   atol=1e-11 * np.abs(v).max())
+
+
+def test_grover_mixer_weights(oracle_mod):
+    """|+><+| = prod (1 + X_i)/2: c_k = 2^-n for every k, so d_w = [w = 0]."""
+    n = 6
+    d = oracle_mod.krawtchouk_weights(n, {k: 2.0 ** -n for k in range(n + 1)})
+    np.testing.assert_allclose(d, [1.0] + [0.0] * n, atol=1e-14)
+    cost = oracle_mod.cost_maxcut(n, erdos_renyi(n, 0.5, 41))
+    ang = np.random.default_rng(42).random(4) * np.pi
+    E, g = oracle_mod.qaoa_gradient_general(n, d, cost, ang)
+    E2, g2 = oracle_mod.qaoa_gradient(n, cost, ang, "grover")
+    assert E == pytest.approx(E2, abs=1e-12)
+    np.testing.assert_allclose(g, g2, atol=1e-10)
+
+
+def test_general_mixer_single_x_is_transverse_field(oracle_mod):
+    n, p = 7, 3
+    cost = oracle_mod.cost_sk(n, sk_couplings(n, 43).astype(np.float64))
+    ang = np.random.default_rng(44).random(2 * p) * np.pi
+    d = oracle_mod.krawtchouk_weights(n, {1: 1.0})
+    np.testing.assert_allclose(d, n - 2 * np.arange(n + 1), atol=1e-14)
+    E, g = oracle_mod.qaoa_gradient_general(n, d, cost, ang)
+    E0, g0 = oracle_mod.qaoa_gradient(n, cost, ang)
+    assert E == pytest.approx(E0, abs=1e-12)
+    np.testing.assert_allclose(g, g0, atol=1e-10)
+
+
+def test_general_mixer_gradient_vs_finite_differences(oracle_mod):
+    n, p = 6, 2
+    cost = oracle_mod.cost_maxcut(n, erdos_renyi(n, 0.5, 45))
+    d = oracle_mod.krawtchouk_weights(n, {1: 0.4, 2: 1.0, 3: -0.3})
+    ang = np.random.default_rng(46).random(2 * p) * np.pi
+    E, g = oracle_mod.qaoa_gradient_general(n, d, cost, ang)
+    fd = richardson_fd(lambda x: oracle_mod.qaoa_gradient_general(n, d, cost, x)[0], ang)
+    np.testing.assert_allclose(g, fd, atol=1e-8 * max(1.0, np.abs(g).max()))
+
+
 # -------------------------------------------------------- QAOA state, Eq. 1
 
 @pytest.mark.parametrize("n,p,seed", [(1, 1, 1), (3, 2, 2), (5, 3, 3), (8, 2, 4)])
