@@ -95,11 +95,17 @@ enum {
 enum {
     QAOA_MIXER_X = 0,     /* H_M = sum_i X_i on all 2^n states (Sec. 2.1, Eq. 2) */
     QAOA_MIXER_EIGEN = 1, /* H_M = V diag(lambda) V^T on D feasible states (Sec. 2.1) */
-    QAOA_MIXER_X_MA = 2   /* multi-angle QAOA (Sec. 3: one mixer per qubit per layer,
+    QAOA_MIXER_X_MA = 2,  /* multi-angle QAOA (Sec. 3: one mixer per qubit per layer,
                              each with its own angle): round k applies
                              e^{-i beta_{k,q} X_q} to every qubit q.  An angle set is
                              p (n + 1) values [beta_{1,0..n-1}, ..., beta_{p,0..n-1},
                              gamma_1..gamma_p]; gradients use the same layout. */
+    QAOA_MIXER_X_GENERAL = 3 /* a sum of products of Pauli X (Sec. 2.1),
+                             f(X) = sum_S c_|S| prod_{i in S} X_i on all 2^n states,
+                             given by its Hadamard-basis eigenvalues: d_lambda holds
+                             n + 1 float64 values d_w = sum_k c_k K_k(w) (K_k the
+                             Krawtchouk polynomial); d_w = [w = 0] is the Grover
+                             mixer |+><+|.  Angles and gradients as for X. */
 };
 
 /* Precision of the dense eigenbasis products for QAOA_MIXER_EIGEN. */
@@ -131,7 +137,7 @@ typedef struct {
  *   dim    feasible-set size: 2^n for X, D for EIGEN
  *   d_V    EIGEN: D x D float32, row-major, real orthogonal eigenvectors as
  *          columns (H_M V = V diag(lambda))
- *   d_lambda EIGEN: D float64 eigenvalues
+ *   d_lambda EIGEN: D float64 eigenvalues; X_GENERAL: n + 1 float64 weights
  *   gemm_precision EIGEN: one of QAOA_GEMM_* */
 typedef struct {
     int kind;

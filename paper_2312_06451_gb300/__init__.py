@@ -25,7 +25,8 @@ from ._binding import QAOAError  # noqa: F401
 __all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError", "pass_schedule",
            "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched",
            "qaoa_gradient_small_noalloc", "ring_eigen_mixer", "clique_eigen_mixer", "xy_eigen_mixer",
-           "save_eigen_mixer", "load_eigen_mixer"]
+           "save_eigen_mixer", "load_eigen_mixer", "GeneralXMixer", "x_terms_mixer", "grover_x_mixer",
+           "krawtchouk_weights"]
 
 _PROBLEMS = {"maxcut": B.QAOA_PROBLEM_MAXCUT, "wmaxcut": B.QAOA_PROBLEM_WMAXCUT,
              "sk": B.QAOA_PROBLEM_SK, "dks": B.QAOA_PROBLEM_DKS, "kvc": B.QAOA_PROBLEM_KVC}
@@ -70,6 +71,45 @@ class XMixer:
         if n_angles % per:
             raise ValueError(f"{n_angles} angles do not make whole rounds of {per}")
         return n_angles // per
+
+
+class GeneralXMixer:
+    """A sum of products of Pauli X, f(X) = sum_S c_|S| prod_{i in S} X_i, on
+    all 2^n states (Sec. 2.1), given by its Hadamard-basis eigenvalues d_w for
+    w = 0..n (e^{-i b f(X)} = H^n e^{-i b f(Z)} H^n, f(Z) = d_|z|)."""
+
+    def __init__(self, n: int, weights, device: int = 0):
+        w = torch.as_tensor(np.asarray(weights, dtype=np.float64))
+        if w.shape != (n + 1,):
+            raise ValueError(f"need n + 1 = {n + 1} weights")
+        self.n = int(n)
+        self.dim = 1 << self.n
+        self.weights = w.to(f"cuda:{device}").contiguous()
+        self.struct = B.QaoaMixer(B.QAOA_MIXER_X_GENERAL, self.n, self.dim, None, self.weights.data_ptr(), 0)
+
+
+def krawtchouk_weights(n: int, coeffs: dict) -> np.ndarray:
+    """Hadamard-basis eigenvalues d_w = sum_k c_k K_k(w), w = 0..n, of
+    f(X) = sum_S c_|S| prod X_i, where K_k(w) = sum_j (-1)^j C(w, j) C(n-w, k-j)
+    (the value of sum_{|S|=k} prod_{i in S} Z_i on a weight-w state)."""
+    import math
+
+    d = np.zeros(n + 1)
+    for w in range(n + 1):
+        for k, ck in coeffs.items():
+            d[w] += ck * sum((-1) ** j * math.comb(w, j) * math.comb(n - w, k - j) for j in range(k + 1))
+    return d
+
+
+def x_terms_mixer(n: int, coeffs: dict, device: int = 0) -> GeneralXMixer:
+    """mixer_X-style sums (Sec. 3): coeffs maps the term order k to c_k, e.g.
+    {1: 1, 2: 1} for sum_i X_i + sum_{i<j} X_i X_j."""
+    return GeneralXMixer(n, krawtchouk_weights(n, coeffs), device)
+
+
+def grover_x_mixer(n: int, device: int = 0) -> GeneralXMixer:
+    """Grover mixer |+><+| on all 2^n states (Sec. 2.4): d_w = [w = 0]."""
+    return GeneralXMixer(n, [1.0] + [0.0] * n, device)
 
 
 class EigenMixer:

@@ -53,7 +53,9 @@ enum PassFlags : uint32_t {
     PF_LAM_FROM_C = 4u,  // bwd: lambda = C psi (first adjoint pass)
     PF_GEN_INIT = 8u,    // fwd: psi = amp0 everywhere instead of a load
     PF_UNPHASE_PSI = 16u, // bwd: also undo the phase on psi (psi_out written)
-    PF_TWIST_IN = 32u    // fwd: psi_in is a user state in the plain basis
+    PF_TWIST_IN = 32u,   // fwd: psi_in is a user state in the plain basis
+    PF_WDIAG = 64u       // general X mixer: fwd: e^{-i b G(|x|)} on load; bwd: its
+                         // beta partial and its undo after the rotations
 };
 
 // Per-warp partial sums per tile of the pass kernel.
@@ -70,6 +72,7 @@ struct PassDesc {
     const void *cost;
     const RoundCoef *coef;
     const float2 *table;  // uint8 costs: this round's phase table
+    const float4 *wtab;   // PF_WDIAG: per weight w (cos, -sin of b G(w), G(w), 0)
     double *part_beta;    // [tile] partial sums, this pass
     double *part_gamma;   // [tile]
     double *part_E;       // [tile]
@@ -106,16 +109,20 @@ struct SmallDesc {
     int p;
     float amp0;
     int nq;                  // multi-angle: n coefficients per round (else 0)
+    const double *wts;       // general X mixer: Hadamard-basis weights d_0..d_n (else nullptr)
+    const double *angles_beta;  // general X mixer: beta_1..beta_p (the unit's angles)
 };
 
 struct PrepDesc {
     const double *angles;  // p (nq or 1) betas, then p gammas
-    RoundCoef *coef;       // p (nq or 1) entries
+    RoundCoef *coef;       // p (nq or 1) entries; general X mixer: 2 per round
     float2 *table;         // p * kPhaseTable, or nullptr
     int p;
     int tsize;             // table entries used (<= kPhaseTable)
     int nq;                // multi-angle: one beta per qubit (n), else 0
-    int pad;
+    int gm_n;              // general X mixer: qubits n (else 0)
+    const double *wts;     // general X mixer: Hadamard-basis weights d_0..d_n
+    float4 *wtab;          // general X mixer: p x (n + 1) weight phases
 };
 
 // Two-level deterministic reduction of the per-(tile, warp) partial sums.
@@ -190,7 +197,8 @@ cudaError_t launch_reduce(const RedChunk *d_chunks, int nchunks, double *d_level
 cudaError_t launch_small(const SmallDesc *d_descs, int ndesc, int cost_dtype, int want_grad,
                          int max_n, int *d_err, cudaStream_t s);
 // bwd: 0 forward, 1 adjoint.  Persistent launch over total_tiles tiles.
-cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int ma, const PassDesc *d_descs,
+// var: 0 transverse field, 1 multi-angle, 2 general X mixer (half rounds)
+cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int var, const PassDesc *d_descs,
                          const uint32_t *d_tile_begin, int ndesc, uint32_t total_tiles,
                          int *d_err, cudaStream_t s);
 int small_max_n();

@@ -140,14 +140,16 @@ __device__ __forceinline__ float pair_dot(const float2 (&l)[16], const float2 (&
 // and psi only when rot_psi is set (its later values are not always needed).
 template <int BWD, int MODE>
 __device__ __forceinline__ void stage_rot(float2 (&a)[16], float2 (&l)[16], uint32_t on, const Rot &R,
-                                          float &pscale, float &bacc, bool rot_psi) {
+                                          float &pscale, float &bacc, bool rot_psi, bool pairs = true) {
     if (BWD) {
-        float s = 0.f;
-        if (on & 1u) s += pair_dot<0>(l, a);
-        if (on & 2u) s += pair_dot<1>(l, a);
-        if (on & 4u) s += pair_dot<2>(l, a);
-        if (on & 8u) s += pair_dot<3>(l, a);
-        bacc = fmaf(s, pscale, bacc);
+        if (pairs) {
+            float s = 0.f;
+            if (on & 1u) s += pair_dot<0>(l, a);
+            if (on & 2u) s += pair_dot<1>(l, a);
+            if (on & 4u) s += pair_dot<2>(l, a);
+            if (on & 8u) s += pair_dot<3>(l, a);
+            bacc = fmaf(s, pscale, bacc);
+        }
         for (uint32_t m = on; m; m &= m - 1u) pscale *= R.psc;
         if (on & 1u) rot_pairs<0, MODE>(l, R);
         if (on & 2u) rot_pairs<1, MODE>(l, R);
@@ -458,9 +460,9 @@ struct PassConst {
 // copies of this body so the common one stays compact in the instruction
 // cache.  Optional work (initial state, phase, epilogue) sits in loops of its
 // own that are skipped as a whole when a pass does not need them.
-template <int BWD, int COST, int NBUF, int MODE, int MA>
+template <int BWD, int COST, int NBUF, int MODE, int VAR>
 __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D, const float2 *stab,
-                                          const float2 *s_rot,
+                                          const float2 *s_rot, const float4 *s_w,
                                           unsigned char *bufs, int b, uint32_t bar, uint32_t t, uint32_t stride,
                                           uint32_t total, uint32_t base, uint32_t tl, TileInfo *tinfo,
                                           const PassDesc *__restrict__ descs,
@@ -480,18 +482,25 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     float2 a[16];
     float2 l[16];
     float pscale = 1.f, bacc = 0.f;
-    float bq[MA ? 12 : 1];  // multi-angle: pair terms per local bit
+    constexpr bool MA = VAR == 1;  // multi-angle
+    constexpr bool GM = VAR == 2;  // general X mixer: fixed half-round rotations, no pair terms
+    float bq[MA ? 12 : 1];         // multi-angle: pair terms per local bit
 #pragma unroll
     for (int j = 0; j < (MA ? 12 : 1); j++) bq[j] = 0.f;
 
     // ---------------- stage 1: read the landed tile
     if (!BWD && (flags & PF_GEN_INIT)) {
-        // uniform state in the twisted basis: amp0 * (-i)^{|x|}, |x| = |base| + |local|
-        const float2 a0 = twist(make_float2(K.amp0, 0.f), __popc(base) + __popc(l1));
+        if (GM) {  // the general mixer's passes keep plain amplitudes
 #pragma unroll
-        for (int r = 0; r < 8; r++) {
-            a[2 * r] = twist(a0, __popc(r));
-            a[2 * r + 1] = twist(a0, __popc(r) + 1);
+            for (int i = 0; i < 16; i++) a[i] = make_float2(K.amp0, 0.f);
+        } else {
+            // uniform state in the twisted basis: amp0 * (-i)^{|x|}, |x| = |base| + |local|
+            const float2 a0 = twist(make_float2(K.amp0, 0.f), __popc(base) + __popc(l1));
+#pragma unroll
+            for (int r = 0; r < 8; r++) {
+                a[2 * r] = twist(a0, __popc(r));
+                a[2 * r + 1] = twist(a0, __popc(r) + 1);
+            }
         }
     } else {
 #pragma unroll
@@ -500,7 +509,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
             a[2 * r] = make_float2(v.x, v.y);
             a[2 * r + 1] = make_float2(v.z, v.w);
         }
-        if (!BWD && (flags & PF_TWIST_IN)) {
+        if (!GM && !BWD && (flags & PF_TWIST_IN)) {
             const float2 w0 = twist(make_float2(1.f, 0.f), __popc(base) + __popc(l1));
 #pragma unroll
             for (int r = 0; r < 8; r++) {
@@ -544,8 +553,21 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
             }
         }
     }
+    if (GM && !BWD && (flags & PF_WDIAG)) {
+        // general X mixer: e^{-i b G(|x|)} on the global index x of every
+        // amplitude (local bits below c stay, the others start at qubit lo)
+        const int c = D.c, lo = c < kT ? D.gpos[c] : 0;
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const uint32_t lq = l1 | ((uint32_t)r << 9);
+            const uint32_t x = base + (c >= kT ? lq : ((lq & ((1u << c) - 1u)) | ((lq >> c) << lo)));
+            const float4 t0 = s_w[__popc(x)], t1 = s_w[__popc(x | 1u)];
+            a[2 * r] = cmul(a[2 * r], make_float2(t0.x, t0.y));
+            a[2 * r + 1] = cmul(a[2 * r + 1], make_float2(t1.x, t1.y));
+        }
+    }
     if constexpr (MA) stage_rot_ma<BWD, 0, 9, 10, 11>(a, l, stage_mask(active, 0, 9, 10, 11), s_rot, bq, true);
-    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 0, 9, 10, 11), K.R, pscale, bacc, true);
+    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 0, 9, 10, 11), K.R, pscale, bacc, true, !GM);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs1);
         pscale = 1.f;
@@ -567,7 +589,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
         if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
     }
     if constexpr (MA) stage_rot_ma<BWD, 1, 2, 3, 4>(a, l, stage_mask(active, 1, 2, 3, 4), s_rot, bq, true);
-    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 1, 2, 3, 4), K.R, pscale, bacc, true);
+    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 1, 2, 3, 4), K.R, pscale, bacc, true, !GM);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs2);
         pscale = 1.f;
@@ -630,10 +652,26 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     }
     // psi after the last stage is needed only when it is stored or meets the
     // phase epilogue (the adjoint with per-pass checkpoints stores lambda only)
-    const bool psi_live = !BWD || D.psi_out != nullptr || (flags & PF_PHASE);
+    const bool psi_live = !BWD || D.psi_out != nullptr || (flags & PF_PHASE) || (GM && (flags & PF_WDIAG));
     if constexpr (MA) stage_rot_ma<BWD, 5, 6, 7, 8>(a, l, stage_mask(active, 5, 6, 7, 8), s_rot, bq, psi_live);
-    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 5, 6, 7, 8), K.R, pscale, bacc, psi_live);
+    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 5, 6, 7, 8), K.R, pscale, bacc, psi_live, !GM);
     scale_all<BWD>(a, l, K.rescale ? K.fs3 : K.fse);
+    if (GM && BWD && (flags & PF_WDIAG)) {
+        // general X mixer: the beta partial sum_x G(|x|) Im(conj(lam) psi) in
+        // the frame between the two half rounds, then the diagonal undone
+        const uint32_t g0 = base + K.g3;
+        float wacc = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const uint32_t x = g0 + (((i & 1) ? K.rs3[0] : 0) + ((i & 2) ? K.rs3[1] : 0) + ((i & 4) ? K.rs3[2] : 0) +
+                                     ((i & 8) ? K.rs3[3] : 0));
+            const float4 t = s_w[__popc(x)];
+            wacc = fmaf(t.z, fmaf(l[i].x, a[i].y, -l[i].y * a[i].x), wacc);
+            l[i] = cmul_conj(l[i], make_float2(t.x, t.y));
+            if (D.psi_out) a[i] = cmul_conj(a[i], make_float2(t.x, t.y));
+        }
+        bacc += wacc;
+    }
 
     // ---------------- stage 3: fused epilogue, coalesced store
     float eacc = 0.f;
@@ -693,7 +731,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     }
 }
 
-template <int BWD, int COST, int NBUF, int MA>
+template <int BWD, int COST, int NBUF, int VAR>
 __global__ void __launch_bounds__(kNT, (BWD && NBUF > 1) ? 1 : 2)
 xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ tile_begin, int ndesc,
              uint32_t total, int *err) {
@@ -705,6 +743,7 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
     unsigned char *bufs = smem_raw + G::kHead;
     __shared__ PassDesc D;
     __shared__ float2 s_rot[12];  // multi-angle: (cos, +-sin) per local bit
+    __shared__ float4 s_w[33];    // general X mixer: weight phases and G(w)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -782,7 +821,9 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
             for (int k = 0; k < 4; k++) K.rs3[k] = 1u << D.gpos[5 + k];
             if (COST == 1 && (K.flags & PF_PHASE))
                 for (int i = tid; i < kPhaseTable; i += kNT) stab[i] = D.table[i];
-            if (MA) {
+            if (VAR == 2 && (K.flags & PF_WDIAG))
+                for (int i = tid; i <= D.n; i += kNT) s_w[i] = D.wtab[i];
+            if (VAR == 1) {
                 // per-qubit rotations: D.coef is this round's n entries, indexed
                 // by global qubit; the direct form needs no rescaling
                 if (tid < kT) {
@@ -795,14 +836,14 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
             __syncthreads();
             cur = di;
         }
-        if (MA)
-            tile_body<BWD, COST, NBUF, 2, 1>(K, D, stab, s_rot, bufs, b, bar, t, stride, total, ti.base, ti.tl,
+        if (VAR == 1)
+            tile_body<BWD, COST, NBUF, 2, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
                                              tinfo, descs, tile_begin, ndesc, cursor);
         else if (K.R.mode == 0)
-            tile_body<BWD, COST, NBUF, 0, 0>(K, D, stab, s_rot, bufs, b, bar, t, stride, total, ti.base, ti.tl,
+            tile_body<BWD, COST, NBUF, 0, VAR>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
                                              tinfo, descs, tile_begin, ndesc, cursor);
         else
-            tile_body<BWD, COST, NBUF, 2, 0>(K, D, stab, s_rot, bufs, b, bar, t, stride, total, ti.base, ti.tl,
+            tile_body<BWD, COST, NBUF, 2, VAR>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
                                              tinfo, descs, tile_begin, ndesc, cursor);
     }
 }
@@ -854,17 +895,51 @@ small_kernel(const SmallDesc *__restrict__ descs, int *err) {
         }
     };
 
-    // coefficients of round k: one entry, or one per qubit (multi-angle)
+    // general X mixer (plain basis here): H^n diag(e^{-i b d_|x|}) H^n
+    __shared__ float2 s_gph[kSmallMaxN + 1];
+    auto hadamard_all = [&](float2 *v) {
+        const float r = 0.70710678118654752f;
+        for (int q = 0; q < n; q++) {
+            __syncthreads();
+            for (int j = tid; j < H; j += kSmallThreads) {
+                const int lo = j & ((1 << q) - 1);
+                const int x0 = ((j - lo) << 1) | lo, x1 = x0 | (1 << q);
+                const float2 u = v[x0], w = v[x1];
+                v[x0] = make_float2(r * (u.x + w.x), r * (u.y + w.y));
+                v[x1] = make_float2(r * (u.x - w.x), r * (u.y - w.y));
+            }
+        }
+        __syncthreads();
+    };
+    auto weight_phases = [&](double b) {  // s_gph[w] = e^{-i b d_w}
+        __syncthreads();
+        if (tid <= n) {
+            double sn, cs;
+            sincos(b * D.wts[tid], &sn, &cs);
+            s_gph[tid] = make_float2((float)cs, (float)-sn);
+        }
+        __syncthreads();
+    };
+    // coefficients of round k: one entry, one per qubit (multi-angle) or two
+    // (general X mixer); nb angles per round's mixer
     const int nb = D.nq ? D.nq : 1;
-    auto qcoef = [&](int k, int q) -> const RoundCoef & { return D.coef[k * nb + (D.nq ? q : 0)]; };
+    const int cs = D.nq ? D.nq : (D.wts ? 2 : 1);
+    auto qcoef = [&](int k, int q) -> const RoundCoef & { return D.coef[k * cs + (D.nq ? q : 0)]; };
 
     for (int x = tid; x < N; x += kSmallThreads)
         psi[x] = D.init ? D.init[x] : make_float2(D.amp0, 0.f);
     for (int k = 0; k < p; k++) {
-        const RoundCoef cf = D.coef[k * nb];
+        const RoundCoef cf = D.coef[k * cs];
         __syncthreads();
         load_table(k);
         for (int x = tid; x < N; x += kSmallThreads) psi[x] = cmul(psi[x], phase(x, cf));
+        if (D.wts) {
+            weight_phases(D.angles_beta[k]);
+            hadamard_all(psi);
+            for (int x = tid; x < N; x += kSmallThreads) psi[x] = cmul(psi[x], s_gph[__popc(x)]);
+            hadamard_all(psi);
+            continue;
+        }
         for (int q = 0; q < n; q++) {
             __syncthreads();
             mix(psi, q, qcoef(k, q).cb, qcoef(k, q).sb);
@@ -882,10 +957,27 @@ small_kernel(const SmallDesc *__restrict__ descs, int *err) {
         lam[x] = make_float2(c * psi[x].x, c * psi[x].y);
     }
     for (int k = p - 1; k >= 0; k--) {
-        const RoundCoef cf = D.coef[k * nb];
+        const RoundCoef cf = D.coef[k * cs];
         __syncthreads();
         float gb = 0.f;
-        for (int q = 0; q < n; q++) {
+        if (D.wts) {
+            // in the Hadamard frame: beta partial sum_z d_|z| Im(conj(lam) psi),
+            // then the diagonal undone and the frame left again
+            weight_phases(D.angles_beta[k]);
+            hadamard_all(lam);
+            hadamard_all(psi);
+            for (int x = tid; x < N; x += kSmallThreads) {
+                const float2 l = lam[x], a = psi[x];
+                gb = fmaf((float)D.wts[__popc(x)], l.x * a.y - l.y * a.x, gb);
+                lam[x] = cmul_conj(l, s_gph[__popc(x)]);
+                psi[x] = cmul_conj(a, s_gph[__popc(x)]);
+            }
+            const double GB = block_sum<kSmallThreads / 32>(gb, s_red);
+            if (tid == 0) D.grad_out[k] = 2.0 * GB;
+            hadamard_all(lam);
+            hadamard_all(psi);
+        }
+        for (int q = 0; q < (D.wts ? 0 : n); q++) {
             float gq = 0.f;
             for (int j = tid; j < H; j += kSmallThreads) {
                 const int lo = j & ((1 << q) - 1);
@@ -900,11 +992,11 @@ small_kernel(const SmallDesc *__restrict__ descs, int *err) {
                 gb += gq;
             }
         }
-        if (!D.nq) {
+        if (!D.nq && !D.wts) {
             const double GB = block_sum<kSmallThreads / 32>(gb, s_red);
             if (tid == 0) D.grad_out[k] = 2.0 * GB;
         }
-        for (int q = 0; q < n; q++) {
+        for (int q = 0; q < (D.wts ? 0 : n); q++) {
             __syncthreads();
             mix(lam, q, qcoef(k, q).cb, -qcoef(k, q).sb);
             mix(psi, q, qcoef(k, q).cb, -qcoef(k, q).sb);
@@ -934,7 +1026,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ 
     // nb angles per round's mixer (nq qubits for multi-angle, else 1):
     // beta_{k,q} = angles[k nb + q], gamma_k = angles[p nb + k]
     const int nb = D.nq ? D.nq : 1;
-    for (int e = threadIdx.x; e < D.p * nb; e += blockDim.x) {
+    for (int e = threadIdx.x; e < (D.gm_n ? 0 : D.p * nb); e += blockDim.x) {
         const int k = e / nb;
         const double be = D.angles[e], ga = D.angles[D.p * nb + k];
         if (!isfinite(be) || !isfinite(ga)) atomicOr(err, DERR_BAD_ANGLE);
@@ -960,6 +1052,37 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ 
         c.b_lo = (float)(bb - (double)c.b_hi);
         c.pad = 0.f;
         D.coef[e] = c;
+    }
+    if (D.gm_n) {
+        // general X mixer: its passes keep plain (untwisted) amplitudes, on
+        // which the real rotation [[c, s], [-s, c]] is e^{i t Y}; e^{i (pi/4) Y}
+        // on every qubit takes X_S to Z_S, so e^{-i b f(X)} is the rotation by
+        // t = pi/4 (coefficient 2k, with gamma_k), e^{-i b d_|x|}, and the
+        // rotation by t = -pi/4 (coefficient 2k + 1)
+        const int n = D.gm_n;
+        for (int e = threadIdx.x; e < 2 * D.p; e += blockDim.x) {
+            const int k = e >> 1;
+            const double be = (e & 1) ? -kTwoPi / 8 : kTwoPi / 8, ga = D.angles[D.p + k];
+            if (!isfinite(D.angles[k]) || !isfinite(ga)) atomicOr(err, DERR_BAD_ANGLE);
+            RoundCoef c;
+            c.cb = (float)cos(be);
+            c.sb = (float)sin(be);
+            c.bmode = 2;
+            c.bt = 0.f;
+            c.rescale = 0;
+            const double g = ga / kTwoPi;
+            c.g_hi = (float)g;
+            c.g_lo = (float)(g - (double)c.g_hi);
+            c.b_hi = c.b_lo = c.pad = 0.f;
+            D.coef[e] = c;
+        }
+        for (int e = threadIdx.x; e < D.p * (n + 1); e += blockDim.x) {
+            const int k = e / (n + 1), w = e - k * (n + 1);
+            const double G = D.wts[w];
+            double sn, cs;
+            sincos(D.angles[k] * G, &sn, &cs);
+            D.wtab[e] = make_float4((float)cs, (float)-sn, (float)G, 0.f);
+        }
     }
     if (D.table) {
         const int tot = D.p * D.tsize;
@@ -1002,25 +1125,25 @@ __global__ void __launch_bounds__(32) reduce2_kernel(const RedOut *__restrict__ 
     if (threadIdx.x == 0) *O.out = O.scale * acc;
 }
 
-template <int BWD, int COST, int NBUF, int MA>
+template <int BWD, int COST, int NBUF, int VAR>
 cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t tiles, int *err,
                        cudaStream_t s) {
     using G = PassGeom<BWD, COST>;
     const size_t smem = G::kHead + (size_t)NBUF * G::kBufB + G::kStashB;
     static int grid_cap = 0;
     if (!grid_cap) {
-        cudaError_t e = cudaFuncSetAttribute(xpass_kernel<BWD, COST, NBUF, MA>,
+        cudaError_t e = cudaFuncSetAttribute(xpass_kernel<BWD, COST, NBUF, VAR>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, nsm = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xpass_kernel<BWD, COST, NBUF, MA>, kNT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xpass_kernel<BWD, COST, NBUF, VAR>, kNT, smem);
         if (e != cudaSuccess) return e;
         grid_cap = std::max(1, nsm * std::max(1, per_sm));
     }
     const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)grid_cap);
-    xpass_kernel<BWD, COST, NBUF, MA><<<grid, kNT, smem, s>>>(d, tb, nd, tiles, err);
+    xpass_kernel<BWD, COST, NBUF, VAR><<<grid, kNT, smem, s>>>(d, tb, nd, tiles, err);
     return cudaGetLastError();
 }
 
@@ -1028,25 +1151,26 @@ cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t t
 
 int small_max_n() { return kSmallMaxN; }
 
-template <int MA>
+template <int VAR>
 cudaError_t launch_xpass_t(int bwd, int cost_dtype, int nbuf, const PassDesc *d, const uint32_t *tb, int nd,
                            uint32_t tiles, int *err, cudaStream_t s) {
-    if (!bwd) return cost_dtype == 0 ? launch_one<0, 0, 2, MA>(d, tb, nd, tiles, err, s)
-                                     : launch_one<0, 1, 2, MA>(d, tb, nd, tiles, err, s);
+    if (!bwd) return cost_dtype == 0 ? launch_one<0, 0, 2, VAR>(d, tb, nd, tiles, err, s)
+                                     : launch_one<0, 1, 2, VAR>(d, tb, nd, tiles, err, s);
     // adjoint: one tile buffer and two CTAs per SM (128 registers a thread),
     // or two buffers and one CTA per SM (no register cap below 255)
     if (nbuf == 2)
-        return cost_dtype == 0 ? launch_one<1, 0, 2, MA>(d, tb, nd, tiles, err, s)
-                               : launch_one<1, 1, 2, MA>(d, tb, nd, tiles, err, s);
-    return cost_dtype == 0 ? launch_one<1, 0, 1, MA>(d, tb, nd, tiles, err, s)
-                           : launch_one<1, 1, 1, MA>(d, tb, nd, tiles, err, s);
+        return cost_dtype == 0 ? launch_one<1, 0, 2, VAR>(d, tb, nd, tiles, err, s)
+                               : launch_one<1, 1, 2, VAR>(d, tb, nd, tiles, err, s);
+    return cost_dtype == 0 ? launch_one<1, 0, 1, VAR>(d, tb, nd, tiles, err, s)
+                           : launch_one<1, 1, 1, VAR>(d, tb, nd, tiles, err, s);
 }
 
-cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int ma, const PassDesc *d, const uint32_t *tb, int nd,
-                         uint32_t tiles, int *err, cudaStream_t s) {
+cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int var, const PassDesc *d, const uint32_t *tb,
+                         int nd, uint32_t tiles, int *err, cudaStream_t s) {
     if (tiles == 0) return cudaSuccess;
-    return ma ? launch_xpass_t<1>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, s)
-              : launch_xpass_t<0>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, s);
+    if (var == 1) return launch_xpass_t<1>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, s);
+    if (var == 2) return launch_xpass_t<2>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, s);
+    return launch_xpass_t<0>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, s);
 }
 
 cudaError_t launch_small(const SmallDesc *d, int nd, int cost_dtype, int want_grad, int max_n,

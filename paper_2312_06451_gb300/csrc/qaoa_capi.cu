@@ -60,13 +60,15 @@ struct Unit {
     const double *lam;     // eigenbasis mixer: D eigenvalues
     int gemm_precision;
     int ma;                // X mixer with one angle per (round, qubit)
+    int gm;                // general X mixer (Hadamard-basis weights wts)
+    const double *wts;     // general X mixer: n + 1 weights
 };
 
 enum LaunchKind { LK_PREP, LK_SMALL, LK_XPASS, LK_REDUCE, LK_EIG_INIT, LK_EIG_GEMM };
 
 struct LaunchRec {
     int kind;
-    int T = 0, bwd = 0, cost_dtype = 0, nbuf = 1, ma = 0;
+    int T = 0, bwd = 0, cost_dtype = 0, nbuf = 1, var = 0;
     size_t desc_off = 0, tb_off = 0;
     int ndesc = 0;
     uint32_t tiles = 0;
@@ -374,12 +376,16 @@ UnitLayout layout_for(const qaoa_ctx *ctx, const Unit &u, bool grad, int ckpt) {
     L.T_f = kPassTileBits;
     L.T_b = kPassTileBits;
     L.gf = make_groups(u.n, L.T_f, t.cmin, t.split);
+    if (u.gm) {  // general X mixer: two half rounds of the same passes
+        const std::vector<Group> h = L.gf;
+        L.gf.insert(L.gf.end(), h.begin(), h.end());
+    }
     L.gb = L.gf;  // per-pass checkpoints pair forward and adjoint passes one to one
     L.tiles_f = 1u << (u.n - L.T_f);
     L.tiles_b = 1u << (u.n - L.T_b);
     L.stride = std::max<int64_t>(L.tiles_f, (int64_t)L.gb.size() * (u.ma ? kPassTileBits : 1) * L.tiles_b) *
                kPassWarps;
-    L.ckpt = grad ? ckpt : QAOA_CKPT_NONE;
+    L.ckpt = grad ? (u.gm ? QAOA_CKPT_PASS : ckpt) : QAOA_CKPT_NONE;  // general mixer: per-pass only
     L.vecs = layout_vecs(L, u.p, grad);
     L.nb_bc = t.nbuf_bwd_contig;
     L.nb_bg = t.nbuf_bwd_gather;
@@ -427,8 +433,8 @@ double pass_bytes(const PassDesc &d, int bwd, int cost_bytes) {
 // after round k (0-based, k < p-1) with per-round checkpoints; with per-pass
 // checkpoints CK[k Pf + g] = output of forward pass g of round k (W unused).
 void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float2 *Lam, float2 *CK,
-                 const RoundCoef *coef, const float2 *table, double *part, std::vector<PassDesc> &fwd,
-                 std::vector<PassDesc> &bwd) {
+                 const RoundCoef *coef, const float2 *table, const float4 *wtab, double *part,
+                 std::vector<PassDesc> &fwd, std::vector<PassDesc> &bwd) {
     const int p = u.p;
     const int64_t N = 1ll << u.n;
     const int Pf = (int)L.gf.size(), Pb = (int)L.gb.size();
@@ -438,6 +444,64 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
     const int64_t bslot = (u.ma ? kPassTileBits : 1) * (int64_t)L.tiles_b * kPassWarps;  // beta partials per pass
     auto ck = [&](int k) { return CK + (int64_t)k * N; };
     auto pk = [&](int k, int g) { return CK + ((int64_t)k * Pf + g) * N; };
+    if (u.gm) {
+        // general X mixer: passes j = 0..2P-1 of round k are the half rounds
+        // e^{-i (pi/4) X} (j < P, coefficient 2k, phase on the first) and
+        // e^{+i (pi/4) X} (j >= P, coefficient 2k + 1), the weight phases
+        // e^{-i b_k G} on the load of pass P
+        const int P = Pf / 2;
+        const int64_t nw = u.n + 1;
+        auto fwd_desc = [&](int k, int j) {
+            PassDesc d;
+            std::memset(&d, 0, sizeof(d));
+            fill_geometry(d, u.n, L.T_f, L.gf[j]);
+            d.cost = u.cost;
+            d.coef = coef + 2 * k + (j >= P ? 1 : 0);
+            d.table = table ? table + (int64_t)k * kPhaseTable : nullptr;
+            d.wtab = wtab + (int64_t)k * nw;
+            d.amp0 = amp0;
+            if (j == 0) d.flags |= PF_PHASE;
+            if (j == P) d.flags |= PF_WDIAG;
+            return d;
+        };
+        for (int k = 0; k < p; k++) {
+            for (int j = 0; j < Pf; j++) {
+                PassDesc d = fwd_desc(k, j);
+                const bool first = k == 0 && j == 0, last = k == p - 1 && j == Pf - 1;
+                if (first) {
+                    if (u.init) {
+                        d.psi_in = u.init;
+                        d.flags |= PF_TWIST_IN;
+                    } else {
+                        d.flags |= PF_GEN_INIT;
+                    }
+                } else {
+                    d.psi_in = grad ? (j == 0 ? pk(k - 1, Pf - 1) : pk(k, j - 1)) : W;
+                }
+                if (last) {
+                    d.flags |= PF_E;
+                    d.part_E = part;
+                }
+                d.psi_out = grad ? pk(k, j) : (last ? nullptr : W);
+                fwd.push_back(d);
+            }
+        }
+        if (!grad) return;
+        for (int k = p - 1; k >= 0; k--) {
+            for (int j = Pf - 1; j >= 0; j--) {
+                PassDesc d = fwd_desc(k, j);
+                d.flags &= PF_PHASE | PF_WDIAG;
+                d.psi_in = pk(k, j);
+                if (k == p - 1 && j == Pf - 1) d.flags |= PF_LAM_FROM_C;
+                else d.lam_in = Lam;
+                d.lam_out = (k == 0 && j == 0) ? nullptr : Lam;
+                if (j == P) d.part_beta = part + (int64_t)(1 + k) * L.stride;
+                if (j == 0) d.part_gamma = part + (int64_t)(1 + p + k) * L.stride;
+                bwd.push_back(d);
+            }
+        }
+        return;
+    }
     if (grad && ckpt == QAOA_CKPT_PASS) {
         for (int k = 0; k < p; k++) {
             for (int g = 0; g < Pf; g++) {
@@ -599,13 +663,18 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         size_t meta = 0;
         // coefficients of all units back to back (the sets of one eigenbasis
         // job are consecutive, so their rounds form a [set][round] array)
+        std::vector<size_t> off_w(nu, 0);
         for (int i = 0; i < nu; i++) {
             off_coef[i] = meta;
-            meta += sizeof(RoundCoef) * units[i].p * (units[i].ma ? units[i].n : 1);
+            meta += sizeof(RoundCoef) * units[i].p * (units[i].ma ? units[i].n : (units[i].gm ? 2 : 1));
         }
         meta = align_up(meta);
         for (int i = 0; i < nu; i++) {
             const Unit &u = units[i];
+            if (u.gm) {  // weight phases of the general X mixer, p x (n + 1)
+                off_w[i] = meta;
+                meta = align_up(meta + sizeof(float4) * u.p * (u.n + 1));
+            }
             off_tab[i] = meta;
             if (u.cost_dtype == QAOA_COST_U8) meta = align_up(meta + sizeof(float2) * kPhaseTable * u.p);
             off_part[i] = meta;
@@ -621,10 +690,10 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
 
         // ---- state memory: pass units grouped by launch shape, admitted in waves
         struct GKey {
-            int Tf, Tb, Pf, Pb, p, dt, nbc, nbg, ma;
+            int Tf, Tb, Pf, Pb, p, dt, nbc, nbg, var;  // var: 0 X, 1 multi-angle, 2 general X mixer
             bool operator<(const GKey &o) const {
-                return std::tie(Tf, Tb, Pf, Pb, p, dt, nbc, nbg, ma) <
-                       std::tie(o.Tf, o.Tb, o.Pf, o.Pb, o.p, o.dt, o.nbc, o.nbg, o.ma);
+                return std::tie(Tf, Tb, Pf, Pb, p, dt, nbc, nbg, var) <
+                       std::tie(o.Tf, o.Tb, o.Pf, o.Pb, o.p, o.dt, o.nbc, o.nbg, o.var);
             }
         };
         std::map<GKey, std::vector<int>> groups;
@@ -632,7 +701,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             if (units[i].mixer_kind != QAOA_MIXER_X || units[i].n <= smax) continue;
             const UnitLayout &L = lay[i];
             groups[{L.T_f, L.T_b, (int)L.gf.size(), (int)L.gb.size(), units[i].p, units[i].cost_dtype, L.nb_bc,
-                    L.nb_bg, units[i].ma}]
+                    L.nb_bg, units[i].ma ? 1 : (units[i].gm ? 2 : 0)}]
                 .push_back(i);
         }
         size_t free_b = 0, total_b = 0;
@@ -655,7 +724,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             for (int i : kv.second) {
                 size_t need = align_up((size_t)lay[i].vecs * (sizeof(float2) << units[i].n));
                 // fewer checkpoints when one angle set's scratch does not fit
-                while (need > budget && lay[i].ckpt > QAOA_CKPT_NONE) {
+                while (need > budget && lay[i].ckpt > QAOA_CKPT_NONE && !units[i].gm) {
                     lay[i].ckpt--;
                     lay[i].vecs = layout_vecs(lay[i], units[i].p, grad);
                     need = align_up((size_t)lay[i].vecs * (sizeof(float2) << units[i].n));
@@ -702,6 +771,9 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             prep[i].p = u.p;
             prep[i].tsize = u.tsize;
             prep[i].nq = u.ma ? u.n : 0;
+            prep[i].gm_n = u.gm ? u.n : 0;
+            prep[i].wts = u.gm ? u.wts : nullptr;
+            prep[i].wtab = u.gm ? reinterpret_cast<float4 *>(mb + off_w[i]) : nullptr;
         }
         {
             LaunchRec r;
@@ -729,6 +801,8 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 s.n = u.n;
                 s.p = u.p;
                 s.nq = u.ma ? u.n : 0;
+                s.wts = u.gm ? u.wts : nullptr;
+                s.angles_beta = u.angles;
                 s.amp0 = 1.0f / std::sqrt((float)(1u << u.n));
                 sd.push_back(s);
                 maxn = std::max(maxn, u.n);
@@ -810,7 +884,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                     W = nullptr;
                 }
                 std::vector<PassDesc> f, b;
-                unit_passes(u, lay[i], grad, W, Lam, CK, prep[i].coef, prep[i].table,
+                unit_passes(u, lay[i], grad, W, Lam, CK, prep[i].coef, prep[i].table, prep[i].wtab,
                             reinterpret_cast<double *>(mb + off_part[i]), f, b);
                 std::vector<PassDesc> all = f;
                 all.insert(all.end(), b.begin(), b.end());
@@ -825,7 +899,9 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                         const int Pb = (int)lay[i].gb.size();
                         const int nbq = u.ma ? u.n : 1;
                         for (int k = 0; k < u.p; k++) {
-                            if (u.ma) {
+                            if (u.gm) {  // the weight-diagonal pass holds the whole beta partial
+                                add_reduction(part + (1 + k) * S, tw, u.grad + k, 2.0);
+                            } else if (u.ma) {
                                 // qubit of local bit j in adjoint pass q (group Pb - 1 - q)
                                 for (int q = 0; q < Pb; q++) {
                                     const Group &G = lay[i].gb[Pb - 1 - q];
@@ -860,7 +936,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 r.bwd = bwd;
                 r.cost_dtype = gk.dt;
                 r.nbuf = bwd ? (steps[s][0].c >= kPassTileBits ? gk.nbc : gk.nbg) : 2;
-                r.ma = gk.ma;
+                r.var = gk.var;
                 r.desc_off = put(steps[s].data(), sizeof(PassDesc) * steps[s].size());
                 xpass_descs.push_back({r.desc_off, (int)steps[s].size()});
                 r.tb_off = put(tb.data(), sizeof(uint32_t) * tb.size());
@@ -869,7 +945,8 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 r.bytes = bytes;
                 char nm[64];
                 const int c0 = steps[s][0].c;
-                snprintf(nm, sizeof(nm), "xpass%s_%s_%s_%s", gk.ma ? "_ma" : "", bwd ? "bwd" : "fwd",
+                snprintf(nm, sizeof(nm), "xpass%s_%s_%s_%s", gk.var == 1 ? "_ma" : (gk.var == 2 ? "_gm" : ""),
+                         bwd ? "bwd" : "fwd",
                          c0 >= kPassTileBits ? "contig" : (c0 >= 6 ? "gather_wide" : "gather"),
                          dtype_name(gk.dt));
                 r.fam = family(ctx, nm);
@@ -1147,7 +1224,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                              r.small_grad, r.small_maxn, ctx->d_err, ctx->stream);
             break;
         case LK_XPASS:
-            e = launch_xpass(r.bwd, r.cost_dtype, r.nbuf, r.ma, reinterpret_cast<const PassDesc *>(db + r.desc_off),
+            e = launch_xpass(r.bwd, r.cost_dtype, r.nbuf, r.var, reinterpret_cast<const PassDesc *>(db + r.desc_off),
                              reinterpret_cast<const uint32_t *>(db + r.tb_off), r.ndesc, r.tiles,
                              ctx->d_err, ctx->stream);
             break;
@@ -1198,8 +1275,10 @@ qaoa_status check_args(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
         if (d_init && ((uintptr_t)d_init & 7)) return fail(ctx, QAOA_ERR_INVALID, "d_init must be 8-byte aligned");
         return QAOA_OK;
     }
-    if (mx->kind != QAOA_MIXER_X && mx->kind != QAOA_MIXER_X_MA)
+    if (mx->kind != QAOA_MIXER_X && mx->kind != QAOA_MIXER_X_MA && mx->kind != QAOA_MIXER_X_GENERAL)
         return fail(ctx, QAOA_ERR_INVALID, "unknown mixer kind %d", mx->kind);
+    if (mx->kind == QAOA_MIXER_X_GENERAL && (!mx->d_lambda || ((uintptr_t)mx->d_lambda & 7)))
+        return fail(ctx, QAOA_ERR_INVALID, "general X mixer needs its n + 1 weights in d_lambda");
     if (mx->n < 1 || mx->n > kMaxXQubits)
         return fail(ctx, QAOA_ERR_INVALID, "X mixer needs 1 <= n <= %d (got %d)", kMaxXQubits, mx->n);
     if (mx->dim != (1ll << mx->n))
@@ -1270,8 +1349,10 @@ qaoa_status scalar_run(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
     u.grad = grad ? io + na + 1 : nullptr;
     u.init = static_cast<const float2 *>(d_init);
     u.tsize = kPhaseTable;
-    u.mixer_kind = ma ? QAOA_MIXER_X : mixer->kind;
+    u.mixer_kind = (ma || mixer->kind == QAOA_MIXER_X_GENERAL) ? QAOA_MIXER_X : mixer->kind;
     u.ma = ma;
+    u.gm = mixer->kind == QAOA_MIXER_X_GENERAL;
+    u.wts = u.gm ? mixer->d_lambda : nullptr;
     u.dim = mixer->dim;
     u.V = mixer->d_V;
     u.lam = mixer->d_lambda;
@@ -1565,8 +1646,10 @@ qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *
                 u.grad = want_grad ? jb.d_grad + (int64_t)s * na : nullptr;
                 u.init = static_cast<const float2 *>(jb.d_init);
                 u.tsize = kPhaseTable;
-                u.mixer_kind = ma ? QAOA_MIXER_X : jb.mixer->kind;
+                u.mixer_kind = (ma || jb.mixer->kind == QAOA_MIXER_X_GENERAL) ? QAOA_MIXER_X : jb.mixer->kind;
                 u.ma = ma;
+                u.gm = jb.mixer->kind == QAOA_MIXER_X_GENERAL;
+                u.wts = u.gm ? jb.mixer->d_lambda : nullptr;
                 u.job = j;
                 u.dim = jb.mixer->dim;
                 u.V = jb.mixer->d_V;

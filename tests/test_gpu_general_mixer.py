@@ -1,0 +1,92 @@
+"""General X mixers f(X) = sum_S c_|S| prod X_i (Sec. 2.1) and the Grover
+mixer on all 2^n states against the oracle (which applies them as Hadamard
+transform, weight phases, Hadamard transform).  The library runs them as two
+fixed half rounds of X rotations around a popcount-indexed diagonal, on chip
+for n <= 12 and through the pass kernels above.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from qaoa_inputs import erdos_renyi, sk_couplings, uniform_angles
+
+pytestmark = pytest.mark.gpu
+
+TERMS = {"x": {1: 1.0}, "xx": {2: 1.0}, "x_xx": {1: 1.0, 2: 0.5}, "mixed": {1: 0.3, 3: -0.7, 4: 0.2}}
+
+
+@pytest.fixture(scope="module")
+def Q():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2312_06451_gb300 as qg
+
+    ctx = qg.Context(0)
+    yield qg, ctx
+    ctx.close()
+
+
+def sigma(c):
+    return float(np.sqrt(np.mean(np.asarray(c, dtype=np.float64) ** 2)))
+
+
+def check(E, g, E_ref, g_ref, c):
+    sig = sigma(c)
+    assert abs(E - E_ref) <= 1e-5 * max(abs(E_ref), sig), (E, E_ref)
+    np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-4 * max(np.abs(g_ref).max(), sig))
+
+
+def problem(ctx, oracle_mod, n, seed, f32):
+    if f32:
+        J = sk_couplings(n, seed)
+        return ctx.cost_precompute("sk", n, J=J, dtype=torch.float32), oracle_mod.cost_sk(n, J.astype(np.float64))
+    e = erdos_renyi(n, 0.4, seed)
+    return ctx.cost_precompute("maxcut", n, edges=e, dtype=torch.uint8), oracle_mod.cost_maxcut(n, e)
+
+
+@pytest.mark.parametrize("terms", ["x", "xx", "x_xx", "mixed", "grover"])
+@pytest.mark.parametrize("n,p,f32", [(8, 3, False), (16, 2, True), (21, 2, False)])
+def test_general_mixer_gradient(Q, oracle_mod, terms, n, p, f32):
+    qg, ctx = Q
+    cost, c = problem(ctx, oracle_mod, n, 500 + n, f32)
+    mixer = qg.grover_x_mixer(n) if terms == "grover" else qg.x_terms_mixer(n, TERMS[terms])
+    d = mixer.weights.cpu().numpy()
+    np.testing.assert_allclose(d, [1.0] + [0.0] * n if terms == "grover" else
+                               oracle_mod.krawtchouk_weights(n, TERMS[terms]), atol=1e-12)
+    ang = uniform_angles(p, 600 + n)[0]
+    E, g = ctx.gradient(cost, mixer, ang, ckpt="pass")
+    E_ref, g_ref = oracle_mod.qaoa_gradient_general(n, d, c, ang)
+    check(E, g, E_ref, g_ref, c)
+    assert ctx.expectation(cost, mixer, ang) == pytest.approx(E_ref, abs=1e-5 * max(abs(E_ref), sigma(c)))
+
+
+def test_single_x_term_equals_transverse_field(Q, oracle_mod):
+    qg, ctx = Q
+    n, p = 18, 3
+    cost, c = problem(ctx, oracle_mod, n, 7, True)
+    ang = uniform_angles(p, 8)[0]
+    E, g = ctx.gradient(cost, qg.x_terms_mixer(n, {1: 1.0}), ang)
+    E0, g0 = ctx.gradient(cost, qg.XMixer(n), ang)
+    check(E, g, E0, g0, c)
+
+
+def test_batched_general_and_standard(Q, oracle_mod):
+    qg, ctx = Q
+    n, p, S = 17, 2, 3
+    cost, c = problem(ctx, oracle_mod, n, 9, False)
+    mixers = [qg.x_terms_mixer(n, TERMS["x_xx"]), qg.grover_x_mixer(n), qg.XMixer(n)]
+    A = uniform_angles(p, 10, S)
+    jobs = [{"cost": cost, "mixer": m, "angles": torch.from_numpy(A).cuda(),
+             "E": torch.zeros(S, dtype=torch.float64, device="cuda"),
+             "grad": torch.zeros(S, 2 * p, dtype=torch.float64, device="cuda")} for m in mixers]
+    ctx.expectation_batched(jobs, want_grad=True)
+    torch.cuda.synchronize()
+    refs = [oracle_mod.krawtchouk_weights(n, TERMS["x_xx"]), np.array([1.0] + [0.0] * n), None]
+    for j, d in zip(jobs, refs):
+        for s in (0, S - 1):
+            if d is None:
+                E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, A[s])
+            else:
+                E_ref, g_ref = oracle_mod.qaoa_gradient_general(n, d, c, A[s])
+            check(j["E"][s].item(), j["grad"][s].cpu().numpy(), E_ref, g_ref, c)
