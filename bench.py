@@ -223,7 +223,7 @@ class Workload:
     copied into the job buffers from a device pool first (a 2p-double copy per
     set, so every step evaluates fresh angles)."""
 
-    def __init__(self, qg, ctx, idx, dev, pool_steps, n_override=None, gemm="fp32"):
+    def __init__(self, qg, ctx, idx, dev, pool_steps, n_override=None, gemm="fp32", mixer="x"):
         import torch
 
         from qaoa_inputs import BASE_SEED, sk_couplings, uneven_batch_recipe, uniform_angles, workload_instance
@@ -272,6 +272,18 @@ class Workload:
             w = workload_instance(idx, n_sets=spec["n_sets"] * pool_steps)
             n = n_override or spec["n"]
             self.grad = bool(spec["grad"])
+            # mixer variant: transverse field, multi-angle, sum of X and XX
+            # terms (mixer_X([1, 2])), or the Grover mixer on all 2^n states
+            self.mixer_variant = mixer
+            if mixer == "ma":
+                from qaoa_inputs import uniform_angles_ma
+
+                w["angles"] = uniform_angles_ma(p, n, BASE_SEED + idx + 1000, spec["n_sets"] * pool_steps)
+                self.x_mixer = qg.XMixer(n, multi_angle=True)
+            elif mixer == "terms":
+                self.x_mixer = qg.x_terms_mixer(n, {1: 1.0, 2: 1.0})
+            elif mixer == "grover":
+                self.x_mixer = qg.grover_x_mixer(n)
             if spec["problem"] == "sk":
                 J = w["J"] if n == spec["n"] else sk_couplings(n, BASE_SEED + idx)
                 cost = ctx.cost_precompute("sk", n, J=J, dtype=torch.float32)
@@ -281,8 +293,13 @@ class Workload:
                 prob = "MaxCut " + ("G(12,0.5)" if idx == 1 else "random 3-regular")
             self._add_job(cost, n, w["angles"], spec["n_sets"])
             self.name = spec["name"] if n == spec["n"] else f"{spec['name']}_n{n}"
+            if mixer != "x":
+                self.name += f"_{mixer}"
             self.units = spec["n_sets"]
-            self.config = {"workload": self.name, "problem": prob, "n": n, "p": p, "mixer": "X (transverse field)",
+            mix_desc = {"x": "X (transverse field)", "ma": "multi-angle X (one angle per qubit and round)",
+                        "terms": "sum_i X_i + sum_{i<j} X_i X_j (half rounds around a weight diagonal)",
+                        "grover": "Grover |+><+| on all 2^n states (half rounds around a weight diagonal)"}[mixer]
+            self.config = {"workload": self.name, "problem": prob, "n": n, "p": p, "mixer": mix_desc,
                            "angle_sets_per_step": spec["n_sets"],
                            "cost_dtype": "f32" if spec["problem"] == "sk" else "u8"}
             self.config["l2"] = (f"state {2 ** n * 8 / 2 ** 30:.2f} GiB per set vs 129 MB L2; no flush"
@@ -314,7 +331,7 @@ class Workload:
         ang = pool[:n_sets].clone()
         E = torch.zeros(n_sets, dtype=torch.float64, device=self.dev)
         G = torch.zeros(n_sets, 2 * self.p, dtype=torch.float64, device=self.dev)
-        mixer = getattr(self, "eig_mixer", None) or self.qg.XMixer(n)
+        mixer = getattr(self, "eig_mixer", None) or getattr(self, "x_mixer", None) or self.qg.XMixer(n)
         self.jobs.append({"cost": cost, "mixer": mixer, "angles": ang, "E": E, "grad": G})
         self.pools.append((pool, n_sets, n, np.ascontiguousarray(A)))
 
@@ -360,8 +377,14 @@ class Workload:
             J = w["J"] if n == 28 else sk_couplings(n, BASE_SEED + 2)
             cost = oracle.cost_sk(n, J.astype(np.float64))
             a = self.pools[0][3][0]
+            var = getattr(self, "mixer_variant", "x")
             t = time.perf_counter()
-            oracle.qaoa_gradient(n, cost, np.array([a[0], a[p]]))
+            if var == "ma":
+                oracle.qaoa_gradient_ma(n, cost, np.concatenate([a[:n], a[p * n:p * n + 1]]))
+            elif var in ("terms", "grover"):
+                oracle.qaoa_gradient_general(n, self.x_mixer.weights.cpu().numpy(), cost, np.array([a[0], a[p]]))
+            else:
+                oracle.qaoa_gradient(n, cost, np.array([a[0], a[p]]))
             dt = (time.perf_counter() - t) * p
             return 1.0 / dt, oracle.get_threads(), (f"oracle gradient of one round (p=1) at n={n}, "
                                                      f"scaled x{p} to the p={p} unit")
@@ -513,7 +536,7 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     if args.workload == 6:
         W = GroverWorkload(qg, ctx, dev, args.steps + args.warmup)
     else:
-        W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n, args.gemm)
+        W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n, args.gemm, args.mixer)
     if not args.no_autotune:
         sched = W.autotune()
         if sched:
@@ -584,7 +607,7 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     e2e_value = rsum(args.steps * W.units) / e2e_s
 
     fd = None
-    if W.grad and ws == 1 and not args.no_fd and args.workload != 6:
+    if W.grad and ws == 1 and not args.no_fd and args.workload != 6 and args.mixer == "x":
         fd = fd_compare(W, stream, value)
 
     peaks = measured_peaks()
@@ -630,7 +653,7 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
         cfg.update({"units_per_step_per_rank": W.units, "parallelism": f"replicas x{ws}",
                     "timing": "CUDA graph replay" if graph is not None else "direct launches"})
         out = {
-            "metric": METRIC if args.workload == 2 and not args.n else f"QAOA {unit} ({W.name})",
+            "metric": METRIC if args.workload == 2 and not args.n and args.mixer == "x" else f"QAOA {unit} ({W.name})",
             "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -716,6 +739,8 @@ def main():
     ap.add_argument("--gemm", default="3xtf32", choices=["fp32", "3xtf32"],
                     help="eigenbasis product precision (workload 4): tcgen05 3xTF32 or CUDA-core float32")
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
+    ap.add_argument("--mixer", default="x", choices=["x", "ma", "terms", "grover"],
+                    help="X-mixer workloads (1-3): transverse field, multi-angle, X + XX terms, or Grover")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default X-mixer pass schedule instead of tuning it before the warm-up")
     ap.add_argument("--no-fd", action="store_true",

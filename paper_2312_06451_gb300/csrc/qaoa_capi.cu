@@ -680,7 +680,8 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             off_part[i] = meta;
             if (u.mixer_kind == QAOA_MIXER_X && u.n > smax) {
                 lay[i] = layout_for(ctx, u, grad, ckpt);
-                meta = align_up(meta + sizeof(double) * (2 * u.p + 1) * lay[i].stride);
+                // partial slots: <C>, and with gradients every beta_k and gamma_k
+                meta = align_up(meta + sizeof(double) * (grad ? 2 * u.p + 1 : 1) * lay[i].stride);
             }
         }
         void *d_meta = nullptr;

@@ -11,6 +11,7 @@ from .generators import (  # noqa: F401
     random_regular3,
     sk_couplings,
     uniform_angles,
+    uniform_angles_ma,
     uneven_batch_recipe,
     WORKLOADS,
     workload_instance,

@@ -90,6 +90,13 @@ def uniform_angles(p: int, seed: int, n_sets: int = 1, high: float = np.pi) -> n
     return rng.random((n_sets, 2 * p)) * high
 
 
+def uniform_angles_ma(p: int, n: int, seed: int, n_sets: int = 1, high: float = np.pi) -> np.ndarray:
+    """Multi-angle sets: n_sets vectors of p (n + 1) entries ~ U[0, high)
+    (p rounds of n per-qubit betas, then p gammas), float64."""
+    rng = _rng(seed)
+    return rng.random((n_sets, p * (n + 1))) * high
+
+
 def uneven_batch_recipe(n_instances: int, seed: int, n_lo: int = 14, n_hi: int = 22):
     """Instances of the uneven angle-finding batch.
 
