@@ -381,12 +381,17 @@ __device__ __forceinline__ uint32_t tile_base(uint32_t tl, int c, int lo) {
 
 // Warp 0: start the loads of tile t into buffer buf (all 32 lanes call).
 template <int BWD, int COST>
+// The descriptor the CTA is working on sits in shared memory (Ds) with its
+// tile range and index in s_tr = {first tile, end tile, index}; a next tile in
+// that range (the common case) needs no global load at all.
 __device__ __forceinline__ void issue_tile(uint32_t t, unsigned char *buf, uint32_t bar, TileInfo *info,
                                            const PassDesc *__restrict__ descs,
-                                           const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor) {
+                                           const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor,
+                                           const PassDesc *Ds, const uint32_t *s_tr) {
     using G = PassGeom<BWD, COST>;
     const int lane = threadIdx.x & 31;
-    const int di = next_desc(tile_begin, ndesc, t, cursor);
+    const bool here = Ds && t >= s_tr[0] && t < s_tr[1];
+    const int di = here ? (int)s_tr[2] : next_desc(tile_begin, ndesc, t, cursor);
     fence_proxy_async();
     if (di < 0) {
         if (lane == 0) {
@@ -395,10 +400,10 @@ __device__ __forceinline__ void issue_tile(uint32_t t, unsigned char *buf, uint3
         }
         return;
     }
-    const PassDesc *Dg = descs + di;
+    const PassDesc *Dg = here ? Ds : descs + di;
     const uint32_t flags = Dg->flags;
     const int c = Dg->c;
-    const uint32_t tl = t - tile_begin[di];
+    const uint32_t tl = t - (here ? s_tr[0] : tile_begin[di]);
     const uint32_t base = tile_base(tl, c, Dg->gpos[c < kT ? c : 0]);
     const bool ld_psi = BWD || !(flags & PF_GEN_INIT);
     const bool ld_lam = BWD && !(flags & PF_LAM_FROM_C);
@@ -466,7 +471,8 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
                                           unsigned char *bufs, int b, uint32_t bar, uint32_t t, uint32_t stride,
                                           uint32_t total, uint32_t base, uint32_t tl, TileInfo *tinfo,
                                           const PassDesc *__restrict__ descs,
-                                          const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor) {
+                                          const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor,
+                                          const uint32_t *s_tr) {
     using G = PassGeom<BWD, COST>;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t l1 = ((uint32_t)lane << 1) | ((uint32_t)warp << 6);
@@ -648,7 +654,8 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     if (warp == 0) {
         const uint32_t tn = t + (uint32_t)NBUF * stride;
         if (tn < total)
-            issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc, cursor);
+            issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc, cursor, &D,
+                                  s_tr);
     }
     // psi after the last stage is needed only when it is stored or meets the
     // phase epilogue (the adjoint with per-pass checkpoints stores lambda only)
@@ -744,6 +751,7 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
     __shared__ PassDesc D;
     __shared__ float2 s_rot[12];  // multi-angle: (cos, +-sin) per local bit
     __shared__ float4 s_w[33];    // general X mixer: weight phases and G(w)
+    __shared__ uint32_t s_tr[3];  // D's first tile, end tile and index
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -758,7 +766,7 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
             const uint32_t t = blockIdx.x + (uint32_t)k * stride;
             if (t < total)
                 issue_tile<BWD, COST>(t, bufs + k * G::kBufB, smem_u32(&bars[k]), &tinfo[k], descs, tile_begin,
-                                      ndesc, cursor);
+                                      ndesc, cursor, nullptr, nullptr);
         }
     }
     const uint32_t l3 = (uint32_t)lane | ((uint32_t)warp << 9);
@@ -788,6 +796,11 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
             const uint32_t *src = reinterpret_cast<const uint32_t *>(descs + di);
             uint32_t *dst = reinterpret_cast<uint32_t *>(&D);
             for (int i = tid; i < (int)(sizeof(PassDesc) / 4); i += kNT) dst[i] = src[i];
+            if (tid == 0) {
+                s_tr[0] = tile_begin[di];
+                s_tr[1] = tile_begin[di + 1];
+                s_tr[2] = (uint32_t)di;
+            }
             __syncthreads();
             const RoundCoef cf = *D.coef;
             K.flags = D.flags;
@@ -838,13 +851,13 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
         }
         if (VAR == 1)
             tile_body<BWD, COST, NBUF, 2, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
-                                             tinfo, descs, tile_begin, ndesc, cursor);
+                                             tinfo, descs, tile_begin, ndesc, cursor, s_tr);
         else if (K.R.mode == 0)
             tile_body<BWD, COST, NBUF, 0, VAR>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
-                                             tinfo, descs, tile_begin, ndesc, cursor);
+                                             tinfo, descs, tile_begin, ndesc, cursor, s_tr);
         else
             tile_body<BWD, COST, NBUF, 2, VAR>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
-                                             tinfo, descs, tile_begin, ndesc, cursor);
+                                             tinfo, descs, tile_begin, ndesc, cursor, s_tr);
     }
 }
 
