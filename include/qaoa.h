@@ -358,6 +358,16 @@ qaoa_status qaoa_gradient_small_noalloc(const void *d_cost, int cost_dtype, int 
                                         const double *d_angles, double *d_E, double *d_grad,
                                         void *cuda_stream);
 
+/* ------------------------------------------------------------- diagnostics */
+
+/* Runs the library's bounded device-side wait (the one every TMA / mbarrier
+ * wait of the kernels uses) on a barrier that nothing ever completes.  The
+ * wait gives up after one second of GPU time, the kernel records it
+ * in the context's error word and returns, and the call reports
+ * QAOA_ERR_TIMEOUT; the context and the device stay usable.  For tests of the
+ * failure path; the paper has no counterpart.  Synchronous. */
+qaoa_status qaoa_check_bounded_wait(qaoa_ctx *ctx);
+
 /* ------------------------------------------------------------ measurement */
 
 /* Per-kernel-family launch statistics, collected when profiling is on: each

@@ -388,6 +388,11 @@ class Context:
                                None if init is None else init.data_ptr())
         self._check(self._lib.qaoa_expectation_batched(self._h, len(jobs), arr, 1 if want_grad else 0))
 
+    def check_bounded_wait(self):
+        """qaoa_check_bounded_wait: raises QAOAError with status
+        QAOA_ERR_TIMEOUT when the device-side wait gave up as designed."""
+        self._check(self._lib.qaoa_check_bounded_wait(self._h))
+
     # --------------------------------------------------------- measurement
     def set_profiling(self, on: bool = True):
         self._check(self._lib.qaoa_set_profiling(self._h, 1 if on else 0))

@@ -74,6 +74,7 @@ SIGNATURES = {
     "qaoa_gradient_small_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                             c_void_p]),
     "qaoa_set_checkpointing": (c_int, [c_void_p, c_int]),
+    "qaoa_check_bounded_wait": (c_int, [c_void_p]),
     "qaoa_cost_degeneracy": (c_int, [c_void_p, ctypes.POINTER(QaoaProblem), c_void_p, c_int]),
     "qaoa_grover_batched": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "qaoa_pass_schedule": (c_int, [c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int]),

@@ -45,6 +45,16 @@ struct RoundCoef {
 // Phase table entries per (unit, round) for uint8 costs: T[c] = e^{-i gamma c}.
 constexpr int kPhaseTable = 256;
 
+// Device-side waits give up after this much wall-clock time (nanoseconds of
+// the GPU's global timer); a completed copy or barrier takes microseconds.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // -------------------------------------------------- pass descriptors (X)
 enum PassFlags : uint32_t {
     PF_PHASE = 1u,       // fwd: e^{-i g C} before the rotations; bwd: gamma
@@ -202,6 +212,8 @@ cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int var, const PassD
                          const uint32_t *d_tile_begin, int ndesc, uint32_t total_tiles,
                          int *d_err, cudaStream_t s);
 int small_max_n();
+// Diagnostic: a bounded wait on a barrier nothing completes (sets DERR_TIMEOUT).
+cudaError_t launch_wait_probe(int *d_err, cudaStream_t s);
 
 // Cost precompute (kernels_cost.cu).
 cudaError_t launch_cost_maxcut(int n, const uint64_t *nbr_hi_host, const float *d_w_edges,

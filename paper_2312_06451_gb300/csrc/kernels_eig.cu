@@ -288,7 +288,9 @@ __device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// Bounded wait: gives up after kWaitLimitNs of global time (or kSpin polls).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    uint64_t t0 = 0;
     for (uint32_t i = 0; i < kSpin; i++) {
         uint32_t ok;
         asm volatile(
@@ -298,6 +300,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if (i == 0) t0 = global_ns();
+        else if ((i & 15u) == 0u && global_ns() - t0 > kWaitLimitNs) return false;
     }
     return false;
 }

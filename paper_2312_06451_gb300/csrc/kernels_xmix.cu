@@ -282,11 +282,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after kSpinLimit polls (seconds), never hangs.
+// Bounded wait: gives up after kWaitLimitNs of global time (or kSpinLimit
+// polls), never hangs.
 constexpr uint32_t kSpinLimit = 1u << 22;
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
     for (uint32_t i = 0; i < kSpinLimit; i++) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 15u) == 15u && global_ns() - t0 > kWaitLimitNs) return false;
         __nanosleep(32);
     }
     return false;
@@ -1160,7 +1164,23 @@ cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t t
     return cudaGetLastError();
 }
 
+// One thread waits, with the pass kernels' bounded wait, for a barrier phase
+// that no thread and no copy ever completes: the wait gives up, the error word
+// records it, and the kernel returns.
+__global__ void wait_probe_kernel(int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(smem_u32(&bar), 1);
+    fence_mbar_init();
+    if (!mbar_wait(smem_u32(&bar), 0u)) atomicOr(err, DERR_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(int *err, cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(err);
+    return cudaGetLastError();
+}
 
 int small_max_n() { return kSmallMaxN; }
 

@@ -1777,6 +1777,16 @@ qaoa_status qaoa_grover_batched(qaoa_ctx *ctx, const int64_t *d_counts, int n_bi
     return QAOA_OK;
 }
 
+qaoa_status qaoa_check_bounded_wait(qaoa_ctx *ctx) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    ctx->err.clear();
+    cudaSetDevice(ctx->device);
+    cudaError_t e = launch_wait_probe(ctx->d_err, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "wait probe launch");
+    ctx->launches++;
+    return read_dev_err(ctx);
+}
+
 qaoa_status qaoa_set_checkpointing(qaoa_ctx *ctx, int mode) {
     if (!ctx) return QAOA_ERR_INVALID;
     if (mode < QAOA_CKPT_NONE || mode > QAOA_CKPT_PASS)
