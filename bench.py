@@ -244,15 +244,17 @@ class Workload:
             self.grad = True
             cost = ctx.cost_precompute("dks", n, edges=w["edges"], k=k, dtype=torch.uint8)
             t0 = time.perf_counter()
-            mixer = qg.ring_eigen_mixer(ctx, n, k, precision=gemm)
+            xy = "clique" if mixer == "clique" else "ring"
+            mixer = qg.xy_eigen_mixer(ctx, xy, n, k, precision=gemm)
             torch.cuda.synchronize()
             self.precompute_s = time.perf_counter() - t0
             self.eig_mixer = mixer
+            self.xy = xy
             self._add_job(cost, n, w["angles"], spec["n_sets"])
-            self.name = spec["name"]
+            self.name = spec["name"] if xy == "ring" else spec["name"].replace("_ring_", "_clique_")
             self.units = spec["n_sets"]
-            self.config = {"workload": spec["name"], "problem": "densest k-subgraph, G(16,0.5)", "n": n, "k": k,
-                           "feasible_states": int(mixer.dim), "p": p, "mixer": f"ring XY via V diag(e^-ib lambda) V^T",
+            self.config = {"workload": self.name, "problem": "densest k-subgraph, G(16,0.5)", "n": n, "k": k,
+                           "feasible_states": int(mixer.dim), "p": p, "mixer": f"{xy} XY via V diag(e^-ib lambda) V^T",
                            "gemm": gemm, "angle_sets_per_step": spec["n_sets"], "cost_dtype": "u8",
                            "eig_precompute_s": round(self.precompute_s, 2)}
         elif idx == 5:
@@ -395,10 +397,10 @@ class Workload:
             cost = oracle.cost_dks(n, w["edges"], st)
             a = w["angles"][0]
             t = time.perf_counter()
-            oracle.qaoa_gradient(n, cost, np.array([a[0], a[p]]), "ring", st)
+            oracle.qaoa_gradient(n, cost, np.array([a[0], a[p]]), self.xy, st)
             dt = (time.perf_counter() - t) * p
             return 1.0 / dt, oracle.get_threads(), (f"oracle gradient of one round (p=1) of one angle set, "
-                                                     f"power-series ring mixer on D={len(st)}, scaled x{p}")
+                                                     f"power-series {self.xy} mixer on D={len(st)}, scaled x{p}")
         if self.idx in (1, 3):
             w = workload_instance(self.idx, n_sets=2)
             n = self.pools[0][2]
@@ -607,7 +609,7 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     e2e_value = rsum(args.steps * W.units) / e2e_s
 
     fd = None
-    if W.grad and ws == 1 and not args.no_fd and args.workload != 6 and args.mixer == "x":
+    if W.grad and ws == 1 and not args.no_fd and args.workload != 6 and args.mixer in ("x", "clique"):
         fd = fd_compare(W, stream, value)
 
     peaks = measured_peaks()
@@ -739,8 +741,9 @@ def main():
     ap.add_argument("--gemm", default="3xtf32", choices=["fp32", "3xtf32"],
                     help="eigenbasis product precision (workload 4): tcgen05 3xTF32 or CUDA-core float32")
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
-    ap.add_argument("--mixer", default="x", choices=["x", "ma", "terms", "grover"],
-                    help="X-mixer workloads (1-3): transverse field, multi-angle, X + XX terms, or Grover")
+    ap.add_argument("--mixer", default="x", choices=["x", "ma", "terms", "grover", "clique"],
+                    help="X-mixer workloads (1-3): transverse field, multi-angle, X + XX terms, or Grover; "
+                         "workload 4: clique instead of ring XY mixer")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default X-mixer pass schedule instead of tuning it before the warm-up")
     ap.add_argument("--no-fd", action="store_true",
