@@ -212,6 +212,10 @@ cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int var, const PassD
                          const uint32_t *d_tile_begin, int ndesc, uint32_t total_tiles,
                          int *d_err, cudaStream_t s);
 int small_max_n();
+// n = 12, transverse-field mixer: one CTA per angle set keeps the whole state
+// as one register-staged tile (descriptors as for launch_small).
+cudaError_t launch_tile12(const SmallDesc *d_descs, int ndesc, int cost_dtype, int want_grad, int *d_err,
+                          cudaStream_t s);
 // Diagnostic: a bounded wait on a barrier nothing completes (sets DERR_TIMEOUT).
 cudaError_t launch_wait_probe(int *d_err, cudaStream_t s);
 

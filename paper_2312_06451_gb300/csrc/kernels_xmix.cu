@@ -40,7 +40,6 @@ namespace qg {
 namespace {
 
 constexpr float kTwoPiF = 6.2831853071795864769f;
-constexpr double kTwoPi = 6.2831853071795864769;
 
 // XOR swizzle of a tile-local amplitude index into shared memory.  Bits 1..3
 // are flipped by a fold of bits 6..14, bit 0 is kept so that the amplitude
@@ -73,6 +72,52 @@ __device__ __forceinline__ float2 phase_f32(float C, float ghi, float glo) {
     float s, c;
     __sincosf(kTwoPiF * f, &s, &c);
     return make_float2(c, -s);
+}
+
+// (sin, cos) of 2 pi t for a float64 turn count t, without float64
+// transcendentals (slow on this part): t = q/4 + r with the nearest quarter
+// turn q/4 removed in float64, |r| <= 1/8 to the float32 sincospi, then the
+// quarter turns applied exactly.  Values near zero keep their relative accuracy.
+__device__ __forceinline__ void sincos_turns(double t, float *s, float *c) {
+    const double q = rint(4.0 * t);
+    const float r = (float)(t - 0.25 * q);
+    float sr, cr;
+    sincospif(2.f * r, &sr, &cr);
+    switch ((int)((long long)q & 3)) {
+    case 0: *s = sr; *c = cr; break;
+    case 1: *s = cr; *c = -sr; break;
+    case 2: *s = -sr; *c = -cr; break;
+    default: *s = -cr; *c = sr; break;
+    }
+}
+
+constexpr double kInvTwoPi = 0.15915494309189533577;  // 1 / (2 pi)
+
+// Round coefficients from one beta (rotation) and the round's gamma.
+__device__ __forceinline__ RoundCoef make_coef(double be, double ga) {
+    const double bb = be * kInvTwoPi;
+    float sb, cb;
+    sincos_turns(bb, &sb, &cb);
+    RoundCoef c;
+    c.cb = cb;
+    c.sb = sb;
+    // tan form unless cos b is so small that the running 1/cos factors or
+    // the pair-term scale would leave float32 range (then: direct form)
+    if (fabsf(cb) >= 2.44140625e-4f) {
+        c.bmode = 0;
+        c.bt = sb / cb;
+    } else {
+        c.bmode = 2;
+        c.bt = 0.f;
+    }
+    c.rescale = fabsf(cb) < 0.25f ? 1 : 0;
+    const double g = ga * kInvTwoPi;
+    c.g_hi = (float)g;
+    c.g_lo = (float)(g - (double)c.g_hi);
+    c.b_hi = (float)bb;
+    c.b_lo = (float)(bb - (double)c.b_hi);
+    c.pad = 0.f;
+    return c;
 }
 
 // ----------------------------------------------------------------------------
@@ -931,9 +976,9 @@ small_kernel(const SmallDesc *__restrict__ descs, int *err) {
     auto weight_phases = [&](double b) {  // s_gph[w] = e^{-i b d_w}
         __syncthreads();
         if (tid <= n) {
-            double sn, cs;
-            sincos(b * D.wts[tid], &sn, &cs);
-            s_gph[tid] = make_float2((float)cs, (float)-sn);
+            float sn, cs;
+            sincos_turns(b * D.wts[tid] * kInvTwoPi, &sn, &cs);
+            s_gph[tid] = make_float2(cs, -sn);
         }
         __syncthreads();
     };
@@ -1037,7 +1082,249 @@ small_kernel(const SmallDesc *__restrict__ descs, int *err) {
 }
 
 // --------------------------------------------------------------------------
+// n = 12: the whole state is one tile of the pass kernels (256 threads x 16
+// amplitudes), so one CTA per angle set runs every round with the pass
+// kernels' three register stages and two swizzled transposes; between rounds
+// the state waits in shared memory in natural order, never in global memory.
+// Same twisted basis as the pass kernels (every qubit is a tile bit, so the
+// stage masks are full).  The adjoint undoes each round on psi as well.
+struct Round12 {
+    Rot R;
+    int rescale;
+    float fs, fse;  // cos factors: per stage (4 rotations), per round (12)
+    float ghi, glo;
+};
+
+__device__ __forceinline__ Round12 round12(const RoundCoef &cf, float sgn) {
+    Round12 r;
+    r.R.mode = cf.bmode;
+    r.R.tt = make_float2(sgn * cf.bt, sgn * cf.bt);
+    r.R.ntt = make_float2(-sgn * cf.bt, -sgn * cf.bt);
+    r.R.c = cf.cb;
+    r.R.s = sgn * cf.sb;
+    r.R.psc = cf.bmode == 0 ? cf.cb * cf.cb : 1.f;
+    r.rescale = (cf.bmode == 0 && cf.rescale) ? 1 : 0;
+    const float c = cf.bmode == 0 ? cf.cb : 1.f;
+    r.fs = c * c * c * c;
+    r.fse = r.rescale ? 1.f : r.fs * r.fs * r.fs;
+    r.ghi = cf.g_hi;
+    r.glo = cf.g_lo;
+    return r;
+}
+
+// One round on the state in shared memory (natural order in and out).
+// Forward: phase on load (initial state generated or twisted in when first),
+// rotations; last: <C> partial, and (GRAD) lambda = C psi written to sl.
+// Adjoint: rotations of lambda and psi undone with the pair terms, then the
+// gamma partial and the phase undone on both.
+template <int BWD, int COST, int MODE>
+__device__ void tile12_round(float2 *sp, float2 *sl, const float2 *stab, const void *scost, const SmallDesc &D,
+                             const Round12 &rc, bool first, bool last, bool grad, float &bacc, float &eacc) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t l1 = ((uint32_t)lane << 1) | ((uint32_t)warp << 6);
+    const uint32_t l2 = ((uint32_t)lane & 1u) | ((((uint32_t)lane >> 1) & 7u) << 6) |
+                        ((((uint32_t)lane >> 4) & 1u) << 5) | ((uint32_t)warp << 9);
+    const uint32_t l3 = (uint32_t)lane | ((uint32_t)warp << 9);
+    const uint32_t p1 = swz(l1), p2 = swz(l2), p3 = swz(l3);
+    auto costv = [&](uint32_t x) -> float {  // the cost vector, copied to shared memory
+        if (COST == 0) return reinterpret_cast<const float *>(scost)[x];
+        return (float)reinterpret_cast<const unsigned char *>(scost)[x];
+    };
+    auto phase = [&](uint32_t x) -> float2 {
+        if (COST == 0) return phase_f32(costv(x), rc.ghi, rc.glo);
+        return stab[reinterpret_cast<const unsigned char *>(scost)[x]];
+    };
+    float2 a[16], l[16];
+    float pscale = 1.f;
+    // ---- stage 1: local bits {0, 9, 10, 11} in registers
+    if (!BWD && first && !D.init) {
+        const float2 a0 = twist(make_float2(D.amp0, 0.f), __popc(l1));
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            a[2 * r] = twist(a0, __popc(r));
+            a[2 * r + 1] = twist(a0, __popc(r) + 1);
+        }
+    } else {
+        const float2 *src = (!BWD && first) ? D.init : sp;
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const float4 v = *reinterpret_cast<const float4 *>(src + (l1 | ((uint32_t)r << 9)));
+            a[2 * r] = make_float2(v.x, v.y);
+            a[2 * r + 1] = make_float2(v.z, v.w);
+        }
+        if (!BWD && first) {
+            const float2 w0 = twist(make_float2(1.f, 0.f), __popc(l1));
+#pragma unroll
+            for (int r = 0; r < 8; r++) {
+                a[2 * r] = cmul(twist(a[2 * r], __popc(r)), w0);
+                a[2 * r + 1] = cmul(twist(a[2 * r + 1], __popc(r) + 1), w0);
+            }
+        }
+    }
+    if (BWD) {
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const float4 v = *reinterpret_cast<const float4 *>(sl + (l1 | ((uint32_t)r << 9)));
+            l[2 * r] = make_float2(v.x, v.y);
+            l[2 * r + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const uint32_t x = l1 | ((uint32_t)r << 9);
+            a[2 * r] = cmul(a[2 * r], phase(x));
+            a[2 * r + 1] = cmul(a[2 * r + 1], phase(x | 1u));
+        }
+    }
+    stage_rot<BWD, MODE>(a, l, 0xFu, rc.R, pscale, bacc, true);
+    if (rc.rescale) {
+        scale_all<BWD>(a, l, rc.fs);
+        pscale = 1.f;
+    }
+    // ---- stage 1 -> 2 (in place, swizzled; crosses warps)
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        const uint32_t idx = p1 ^ swz((uint32_t)r << 9);
+        *reinterpret_cast<float4 *>(sp + idx) = make_float4(a[2 * r].x, a[2 * r].y, a[2 * r + 1].x, a[2 * r + 1].y);
+        if (BWD)
+            *reinterpret_cast<float4 *>(sl + idx) = make_float4(l[2 * r].x, l[2 * r].y, l[2 * r + 1].x, l[2 * r + 1].y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        a[i] = sp[p2 ^ ((uint32_t)i << 1)];
+        if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
+    }
+    stage_rot<BWD, MODE>(a, l, 0xFu, rc.R, pscale, bacc, true);
+    if (rc.rescale) {
+        scale_all<BWD>(a, l, rc.fs);
+        pscale = 1.f;
+    }
+    // ---- stage 2 -> 3 (inside each warp's 512-amplitude block)
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        sp[p2 ^ ((uint32_t)i << 1)] = a[i];
+        if (BWD) sl[p2 ^ ((uint32_t)i << 1)] = l[i];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        const uint32_t idx = p3 ^ swz((uint32_t)i << 5);
+        a[i] = sp[idx];
+        if (BWD) l[i] = sl[idx];
+    }
+    stage_rot<BWD, MODE>(a, l, 0xFu, rc.R, pscale, bacc, true);
+    scale_all<BWD>(a, l, rc.rescale ? rc.fs : rc.fse);
+    // ---- epilogue and natural-order store (still this warp's block)
+    if (BWD) {
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const uint32_t x = l3 | ((uint32_t)i << 5);
+            const float C = costv(x);
+            const float2 ph = phase(x);
+            eacc = fmaf(C, fmaf(l[i].x, a[i].y, -l[i].y * a[i].x), eacc);
+            l[i] = cmul_conj(l[i], ph);
+            a[i] = cmul_conj(a[i], ph);
+        }
+    } else if (last) {
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const float C = costv(l3 | ((uint32_t)i << 5));
+            eacc = fmaf(C, fmaf(a[i].x, a[i].x, a[i].y * a[i].y), eacc);
+            if (grad) l[i] = make_float2(C * a[i].x, C * a[i].y);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        sp[l3 | ((uint32_t)i << 5)] = a[i];
+        if (BWD || (last && grad)) sl[l3 | ((uint32_t)i << 5)] = l[i];
+    }
+    __syncthreads();
+}
+
+template <int COST, int GRAD>
+__global__ void __launch_bounds__(kNT) tile12_kernel(const SmallDesc *__restrict__ descs, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2 *sp = reinterpret_cast<float2 *>(smem_raw);
+    float2 *sl = sp + kTile;
+    float2 *stab = sl + kTile;
+    unsigned char *scost = reinterpret_cast<unsigned char *>(stab + kPhaseTable);
+    __shared__ double s_red[2][kNW];
+    const SmallDesc D = descs[blockIdx.x];
+    const int p = D.p, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    {  // cost vector to shared memory (16-byte words)
+        const int words = kTile * (COST == 0 ? 4 : 1) / 16;
+        for (int i = tid; i < words; i += kNT)
+            reinterpret_cast<uint4 *>(scost)[i] = __ldg(reinterpret_cast<const uint4 *>(D.cost) + i);
+        __syncthreads();
+    }
+    // coefficients and the uint8 phase table come from the angles here (no
+    // separate preparation launch); every thread forms the round's coefficients
+    const double *ang = D.angles_beta;
+    if (tid < 2 * p && !isfinite(ang[tid])) atomicOr(err, DERR_BAD_ANGLE);
+    auto load_table = [&](int k) {  // the previous round ended with a block barrier
+        if (COST == 1) {
+            for (int i = tid; i < kPhaseTable; i += kNT) {
+                float sn, cs;
+                sincos_turns(ang[p + k] * kInvTwoPi * (double)i, &sn, &cs);
+                stab[i] = make_float2(cs, -sn);
+            }
+            __syncthreads();
+        }
+    };
+    // fixed-order block sums of two per-thread values, in float64
+    auto block_sum2 = [&](float x, float y, double &X, double &Y) {
+        const double dx = warp_sum(x), dy = warp_sum(y);
+        if (lane == 0) {
+            s_red[0][warp] = dx;
+            s_red[1][warp] = dy;
+        }
+        __syncthreads();
+        X = 0.0;
+        Y = 0.0;
+        for (int w = 0; w < kNW; w++) {
+            X += s_red[0][w];
+            Y += s_red[1][w];
+        }
+        __syncthreads();
+    };
+    float bacc = 0.f, eacc = 0.f;
+    for (int k = 0; k < p; k++) {
+        const Round12 rc = round12(make_coef(ang[k], ang[p + k]), 1.f);
+        load_table(k);
+        if (rc.R.mode == 0)
+            tile12_round<0, COST, 0>(sp, sl, stab, scost, D, rc, k == 0, k == p - 1, GRAD != 0, bacc, eacc);
+        else
+            tile12_round<0, COST, 2>(sp, sl, stab, scost, D, rc, k == 0, k == p - 1, GRAD != 0, bacc, eacc);
+    }
+    double E, unused;
+    block_sum2(eacc, 0.f, E, unused);
+    if (tid == 0) *D.E_out = E;
+    if constexpr (GRAD) {
+        for (int k = p - 1; k >= 0; k--) {
+            const Round12 rc = round12(make_coef(ang[k], ang[p + k]), -1.f);
+            load_table(k);
+            float b = 0.f, g = 0.f;
+            if (rc.R.mode == 0)
+                tile12_round<1, COST, 0>(sp, sl, stab, scost, D, rc, false, false, true, b, g);
+            else
+                tile12_round<1, COST, 2>(sp, sl, stab, scost, D, rc, false, false, true, b, g);
+            double B, Gm;
+            block_sum2(b, g, B, Gm);
+            if (tid == 0) {
+                D.grad_out[k] = 2.0 * B;
+                D.grad_out[p + k] = 2.0 * Gm;
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
 // Angles -> per-round coefficients and uint8 phase tables (float64 math).
+
 __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ descs, int *err) {
     const PrepDesc D = descs[blockIdx.x];
     // nb angles per round's mixer (nq qubits for multi-angle, else 1):
@@ -1047,27 +1334,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ 
         const int k = e / nb;
         const double be = D.angles[e], ga = D.angles[D.p * nb + k];
         if (!isfinite(be) || !isfinite(ga)) atomicOr(err, DERR_BAD_ANGLE);
-        const double cb = cos(be), sb = sin(be);
-        RoundCoef c;
-        c.cb = (float)cb;
-        c.sb = (float)sb;
-        // tan form unless cos b is so small that the running 1/cos factors or
-        // the pair-term scale would leave float32 range (then: direct form)
-        if (fabs(cb) >= 2.44140625e-4) {
-            c.bmode = 0;
-            c.bt = (float)(sb / cb);
-        } else {
-            c.bmode = 2;
-            c.bt = 0.f;
-        }
-        c.rescale = fabs(cb) < 0.25 ? 1 : 0;
-        const double g = ga / kTwoPi;
-        c.g_hi = (float)g;
-        c.g_lo = (float)(g - (double)c.g_hi);
-        const double bb = be / kTwoPi;
-        c.b_hi = (float)bb;
-        c.b_lo = (float)(bb - (double)c.b_hi);
-        c.pad = 0.f;
+        const RoundCoef c = make_coef(be, ga);
         D.coef[e] = c;
     }
     if (D.gm_n) {
@@ -1079,15 +1346,14 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ 
         const int n = D.gm_n;
         for (int e = threadIdx.x; e < 2 * D.p; e += blockDim.x) {
             const int k = e >> 1;
-            const double be = (e & 1) ? -kTwoPi / 8 : kTwoPi / 8, ga = D.angles[D.p + k];
+            const double ga = D.angles[D.p + k];
             if (!isfinite(D.angles[k]) || !isfinite(ga)) atomicOr(err, DERR_BAD_ANGLE);
             RoundCoef c;
-            c.cb = (float)cos(be);
-            c.sb = (float)sin(be);
+            sincos_turns((e & 1) ? -0.125 : 0.125, &c.sb, &c.cb);  // t = -+pi/4
             c.bmode = 2;
             c.bt = 0.f;
             c.rescale = 0;
-            const double g = ga / kTwoPi;
+            const double g = ga * kInvTwoPi;
             c.g_hi = (float)g;
             c.g_lo = (float)(g - (double)c.g_hi);
             c.b_hi = c.b_lo = c.pad = 0.f;
@@ -1096,21 +1362,18 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepDesc *__restrict__ 
         for (int e = threadIdx.x; e < D.p * (n + 1); e += blockDim.x) {
             const int k = e / (n + 1), w = e - k * (n + 1);
             const double G = D.wts[w];
-            double sn, cs;
-            sincos(D.angles[k] * G, &sn, &cs);
-            D.wtab[e] = make_float4((float)cs, (float)-sn, (float)G, 0.f);
+            float sn, cs;
+            sincos_turns(D.angles[k] * G * kInvTwoPi, &sn, &cs);
+            D.wtab[e] = make_float4(cs, -sn, (float)G, 0.f);
         }
     }
     if (D.table) {
         const int tot = D.p * D.tsize;
         for (int e = threadIdx.x; e < tot; e += blockDim.x) {
             const int k = e / D.tsize, cst = e - k * D.tsize;
-            // e^{-i gamma c}: the turn fraction of gamma c / (2 pi) in float64
-            // (exact integer part removed), then sin/cos of pi * 2f in float32
-            const double t = D.angles[D.p * nb + k] / kTwoPi * (double)cst;
-            const float f = (float)(t - rint(t));
+            // e^{-i gamma c} from the turn count gamma c / (2 pi)
             float s, c;
-            sincospif(2.f * f, &s, &c);
+            sincos_turns(D.angles[D.p * nb + k] * kInvTwoPi * (double)cst, &s, &c);
             D.table[k * kPhaseTable + cst] = make_float2(c, -s);
         }
     }
@@ -1225,6 +1488,23 @@ cudaError_t launch_small(const SmallDesc *d, int nd, int cost_dtype, int want_gr
     };
     if (cost_dtype == 0) return want_grad ? go(small_kernel<0, 1>, 0) : go(small_kernel<0, 0>, 1);
     return want_grad ? go(small_kernel<1, 1>, 2) : go(small_kernel<1, 0>, 3);
+}
+
+cudaError_t launch_tile12(const SmallDesc *d, int nd, int cost_dtype, int want_grad, int *err, cudaStream_t s) {
+    const size_t smem = (size_t)2 * kTile * sizeof(float2) + kPhaseTable * sizeof(float2) +
+                        (size_t)kTile * (cost_dtype == 0 ? 4 : 1);
+    auto go = [&](auto kern, int slot) -> cudaError_t {
+        static bool attr[4] = {false, false, false, false};
+        if (!attr[slot]) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr[slot] = true;
+        }
+        kern<<<nd, kNT, smem, s>>>(d, err);
+        return cudaGetLastError();
+    };
+    if (cost_dtype == 0) return want_grad ? go(tile12_kernel<0, 1>, 0) : go(tile12_kernel<0, 0>, 1);
+    return want_grad ? go(tile12_kernel<1, 1>, 2) : go(tile12_kernel<1, 0>, 3);
 }
 
 cudaError_t launch_prep(const PrepDesc *d, int nd, int *err, cudaStream_t s) {

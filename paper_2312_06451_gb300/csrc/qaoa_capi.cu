@@ -72,7 +72,7 @@ struct LaunchRec {
     size_t desc_off = 0, tb_off = 0;
     int ndesc = 0;
     uint32_t tiles = 0;
-    int small_maxn = 0, small_grad = 0;
+    int small_maxn = 0, small_grad = 0, t12 = 0;
     int fam = 0;
     double bytes = 0.0;
     double flops = 0.0;
@@ -777,20 +777,32 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             prep[i].wtab = u.gm ? reinterpret_cast<float4 *>(mb + off_w[i]) : nullptr;
         }
         {
-            LaunchRec r;
-            r.kind = LK_PREP;
-            r.desc_off = put(prep.data(), sizeof(PrepDesc) * nu);
-            r.ndesc = nu;
-            r.fam = family(ctx, "prep_coefficients");
-            L.push_back(r);
+            // the n = 12 tile kernel forms its coefficients itself
+            std::vector<PrepDesc> todo;
+            for (int i = 0; i < nu; i++) {
+                const Unit &u = units[i];
+                if (!(u.mixer_kind == QAOA_MIXER_X && u.n == kPassTileBits && !u.ma && !u.gm)) todo.push_back(prep[i]);
+            }
+            if (!todo.empty()) {
+                LaunchRec r;
+                r.kind = LK_PREP;
+                r.desc_off = put(todo.data(), sizeof(PrepDesc) * todo.size());
+                r.ndesc = (int)todo.size();
+                r.fam = family(ctx, "prep_coefficients");
+                L.push_back(r);
+            }
         }
-        for (int dt = 0; dt < 2; dt++) {
+        // on-chip units: n = 12 with the transverse field as one register-staged
+        // tile (t12), every other n <= 12 unit in the generic kernel
+        for (int combo = 0; combo < 4; combo++) {
+            const int dt = combo & 1, t12 = combo >> 1;
             std::vector<SmallDesc> sd;
             int maxn = 0;
             double bytes = 0;
             for (int i = 0; i < nu; i++) {
                 const Unit &u = units[i];
                 if (u.mixer_kind != QAOA_MIXER_X || u.n > smax || u.cost_dtype != dt) continue;
+                if ((u.n == kPassTileBits && !u.ma && !u.gm) != (t12 != 0)) continue;
                 SmallDesc s;
                 std::memset(&s, 0, sizeof(s));
                 s.cost = u.cost;
@@ -817,8 +829,9 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             r.ndesc = (int)sd.size();
             r.small_maxn = maxn;
             r.small_grad = grad ? 1 : 0;
+            r.t12 = t12;
             r.bytes = bytes;
-            r.fam = family(ctx, std::string(grad ? "small_grad_" : "small_fwd_") + dtype_name(dt));
+            r.fam = family(ctx, std::string(t12 ? "tile12_" : "small_") + (grad ? "grad_" : "fwd_") + dtype_name(dt));
             L.push_back(r);
         }
         std::vector<RedChunk> rchunks;
@@ -1221,8 +1234,12 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                             ctx->stream);
             break;
         case LK_SMALL:
-            e = launch_small(reinterpret_cast<const SmallDesc *>(db + r.desc_off), r.ndesc, r.cost_dtype,
-                             r.small_grad, r.small_maxn, ctx->d_err, ctx->stream);
+            if (r.t12)
+                e = launch_tile12(reinterpret_cast<const SmallDesc *>(db + r.desc_off), r.ndesc, r.cost_dtype,
+                                  r.small_grad, ctx->d_err, ctx->stream);
+            else
+                e = launch_small(reinterpret_cast<const SmallDesc *>(db + r.desc_off), r.ndesc, r.cost_dtype,
+                                 r.small_grad, r.small_maxn, ctx->d_err, ctx->stream);
             break;
         case LK_XPASS:
             e = launch_xpass(r.bwd, r.cost_dtype, r.nbuf, r.var, reinterpret_cast<const PassDesc *>(db + r.desc_off),

@@ -148,7 +148,7 @@ def test_gradient_matches_oracle(Q, oracle_mod, n, kind, ckpt):
     assert_grad(g, g_ref, c)
 
 
-@pytest.mark.parametrize("n", [4, 13, 16])
+@pytest.mark.parametrize("n", [4, 12, 13, 16])
 def test_custom_initial_state(Q, oracle_mod, n):
     """Warm start (initial_state of Sec. 3): a normalised complex psi_0."""
     import paper_2312_06451_gb300 as qg
@@ -166,6 +166,30 @@ def test_custom_initial_state(Q, oracle_mod, n):
     E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, ang, psi0=psi0)
     assert_E(E, E_ref, c)
     assert_grad(g, g_ref, c)
+
+
+@pytest.mark.parametrize("kind", ["maxcut_u8", "sk_f32"])
+def test_n12_rotation_regimes(Q, oracle_mod, kind):
+    """n = 12 runs as one register-staged tile; betas in every rotation form:
+    tan form (beta = 0.1, 2.9), tan form with per-stage rescaling
+    (|cos beta| < 1/4 at beta = 1.4) and the direct form (beta = pi / 2)."""
+    import paper_2312_06451_gb300 as qg
+
+    n = 12
+    if kind == "maxcut_u8":
+        e = erdos_renyi(n, 0.5, 31)
+        c = oracle_mod.cost_maxcut(n, e)
+        dc = Q.cost_precompute("maxcut", n, edges=e, dtype=torch.uint8)
+    else:
+        J = sk_couplings(n, 32)
+        c = oracle_mod.cost_sk(n, J.astype(np.float64))
+        dc = Q.cost_precompute("sk", n, J=J, dtype=torch.float32)
+    ang = np.array([0.1, 1.4, np.pi / 2, 2.9, 0.7, 1.9, 0.3, 2.5])
+    E, g = Q.gradient(dc, qg.XMixer(n), ang)
+    E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, ang)
+    assert_E(E, E_ref, c)
+    assert_grad(g, g_ref, c)
+    assert_E(Q.expectation(dc, qg.XMixer(n), ang), E_ref, c)
 
 
 def test_many_rounds(Q, oracle_mod):
