@@ -209,32 +209,44 @@ __device__ __forceinline__ void stage_rot(float2 (&a)[16], float2 (&l)[16], uint
     }
 }
 
-// Multi-angle rotations (one angle per qubit, direct form): register bit j
-// of the stage carries local bit Lj, rotated by rot[Lj] = (cos b, +-sin b);
-// the adjoint's pair terms go to one accumulator per local bit.
-template <int BWD, int L0, int L1, int L2, int L3, int NQ>
-__device__ __forceinline__ void stage_rot_ma(float2 (&a)[16], float2 (&l)[16], uint32_t on, const float2 *rot,
-                                             float (&bq)[NQ], bool rot_psi) {
-    Rot R0, R1, R2, R3;
-    R0.c = rot[L0].x, R0.s = rot[L0].y;
-    R1.c = rot[L1].x, R1.s = rot[L1].y;
-    R2.c = rot[L2].x, R2.s = rot[L2].y;
-    R3.c = rot[L3].x, R3.s = rot[L3].y;
+// Multi-angle rotations (one angle per qubit): register bit j of the stage
+// carries local bit Lj, with rot[Lj] = (cos b, +-sin b, +-tan b, cos^2 b).
+// MODE 0 is the tan form (the cosines are applied per stage or per pass like
+// the single-angle path, pscale tracks them for the pair terms), MODE 2 the
+// direct form.  The adjoint's pair terms go to one accumulator per local bit.
+template <int BWD, int MODE, int L0, int L1, int L2, int L3, int NQ>
+__device__ __forceinline__ void stage_rot_ma(float2 (&a)[16], float2 (&l)[16], uint32_t on, const float4 *rot,
+                                             float (&bq)[NQ], float &pscale, bool rot_psi) {
+    Rot R[4];
+    const int Ls[4] = {L0, L1, L2, L3};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const float4 q = rot[Ls[j]];
+        R[j].c = q.x;
+        R[j].s = q.y;
+        R[j].tt = make_float2(q.z, q.z);
+        R[j].ntt = make_float2(-q.z, -q.z);
+    }
     if (BWD) {
-        if (on & 1u) bq[L0] += pair_dot<0>(l, a);
-        if (on & 2u) bq[L1] += pair_dot<1>(l, a);
-        if (on & 4u) bq[L2] += pair_dot<2>(l, a);
-        if (on & 8u) bq[L3] += pair_dot<3>(l, a);
-        if (on & 1u) rot_pairs<0, 2>(l, R0);
-        if (on & 2u) rot_pairs<1, 2>(l, R1);
-        if (on & 4u) rot_pairs<2, 2>(l, R2);
-        if (on & 8u) rot_pairs<3, 2>(l, R3);
+        if (on & 1u) bq[L0] = fmaf(pair_dot<0>(l, a), pscale, bq[L0]);
+        if (on & 2u) bq[L1] = fmaf(pair_dot<1>(l, a), pscale, bq[L1]);
+        if (on & 4u) bq[L2] = fmaf(pair_dot<2>(l, a), pscale, bq[L2]);
+        if (on & 8u) bq[L3] = fmaf(pair_dot<3>(l, a), pscale, bq[L3]);
+        if (MODE == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (on & (1u << j)) pscale *= rot[Ls[j]].w;
+        }
+        if (on & 1u) rot_pairs<0, MODE>(l, R[0]);
+        if (on & 2u) rot_pairs<1, MODE>(l, R[1]);
+        if (on & 4u) rot_pairs<2, MODE>(l, R[2]);
+        if (on & 8u) rot_pairs<3, MODE>(l, R[3]);
     }
     if (!BWD || rot_psi) {
-        if (on & 1u) rot_pairs<0, 2>(a, R0);
-        if (on & 2u) rot_pairs<1, 2>(a, R1);
-        if (on & 4u) rot_pairs<2, 2>(a, R2);
-        if (on & 8u) rot_pairs<3, 2>(a, R3);
+        if (on & 1u) rot_pairs<0, MODE>(a, R[0]);
+        if (on & 2u) rot_pairs<1, MODE>(a, R[1]);
+        if (on & 4u) rot_pairs<2, MODE>(a, R[2]);
+        if (on & 8u) rot_pairs<3, MODE>(a, R[3]);
     }
 }
 
@@ -516,7 +528,7 @@ struct PassConst {
 // own that are skipped as a whole when a pass does not need them.
 template <int BWD, int COST, int NBUF, int MODE, int VAR>
 __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D, const float2 *stab,
-                                          const float2 *s_rot, const float4 *s_w,
+                                          const float4 *s_rot, const float4 *s_w,
                                           unsigned char *bufs, int b, uint32_t bar, uint32_t t, uint32_t stride,
                                           uint32_t total, uint32_t base, uint32_t tl, TileInfo *tinfo,
                                           const PassDesc *__restrict__ descs,
@@ -621,7 +633,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
             a[2 * r + 1] = cmul(a[2 * r + 1], make_float2(t1.x, t1.y));
         }
     }
-    if constexpr (MA) stage_rot_ma<BWD, 0, 9, 10, 11>(a, l, stage_mask(active, 0, 9, 10, 11), s_rot, bq, true);
+    if constexpr (MA) stage_rot_ma<BWD, MODE, 0, 9, 10, 11>(a, l, stage_mask(active, 0, 9, 10, 11), s_rot, bq, pscale, true);
     else stage_rot<BWD, MODE>(a, l, stage_mask(active, 0, 9, 10, 11), K.R, pscale, bacc, true, !GM);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs1);
@@ -643,7 +655,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
         a[i] = sp[p2 ^ ((uint32_t)i << 1)];
         if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
     }
-    if constexpr (MA) stage_rot_ma<BWD, 1, 2, 3, 4>(a, l, stage_mask(active, 1, 2, 3, 4), s_rot, bq, true);
+    if constexpr (MA) stage_rot_ma<BWD, MODE, 1, 2, 3, 4>(a, l, stage_mask(active, 1, 2, 3, 4), s_rot, bq, pscale, true);
     else stage_rot<BWD, MODE>(a, l, stage_mask(active, 1, 2, 3, 4), K.R, pscale, bacc, true, !GM);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs2);
@@ -709,7 +721,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     // psi after the last stage is needed only when it is stored or meets the
     // phase epilogue (the adjoint with per-pass checkpoints stores lambda only)
     const bool psi_live = !BWD || D.psi_out != nullptr || (flags & PF_PHASE) || (GM && (flags & PF_WDIAG));
-    if constexpr (MA) stage_rot_ma<BWD, 5, 6, 7, 8>(a, l, stage_mask(active, 5, 6, 7, 8), s_rot, bq, psi_live);
+    if constexpr (MA) stage_rot_ma<BWD, MODE, 5, 6, 7, 8>(a, l, stage_mask(active, 5, 6, 7, 8), s_rot, bq, pscale, psi_live);
     else stage_rot<BWD, MODE>(a, l, stage_mask(active, 5, 6, 7, 8), K.R, pscale, bacc, psi_live, !GM);
     scale_all<BWD>(a, l, K.rescale ? K.fs3 : K.fse);
     if (GM && BWD && (flags & PF_WDIAG)) {
@@ -798,7 +810,7 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
     float2 *stab = reinterpret_cast<float2 *>(smem_raw + 256);
     unsigned char *bufs = smem_raw + G::kHead;
     __shared__ PassDesc D;
-    __shared__ float2 s_rot[12];  // multi-angle: (cos, +-sin) per local bit
+    __shared__ float4 s_rot[12];  // multi-angle: (cos, +-sin, +-tan, cos^2) per local bit
     __shared__ float4 s_w[33];    // general X mixer: weight phases and G(w)
     __shared__ uint32_t s_tr[3];  // D's first tile, end tile and index
 
@@ -887,18 +899,40 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
                 for (int i = tid; i <= D.n; i += kNT) s_w[i] = D.wtab[i];
             if (VAR == 1) {
                 // per-qubit rotations: D.coef is this round's n entries, indexed
-                // by global qubit; the direct form needs no rescaling
+                // by global qubit.  The tan form when every rotated qubit allows
+                // it, with the cosines per stage (rescale: any |cos| < 1/4) or
+                // once per pass, else the direct form.
+                bool tan_ok = true, resc = false;
                 if (tid < kT) {
                     const RoundCoef q = D.coef[D.gpos[tid]];
-                    s_rot[tid] = make_float2(q.cb, sgn * q.sb);
+                    s_rot[tid] = make_float4(q.cb, sgn * q.sb, sgn * q.bt, q.cb * q.cb);
+                    const bool on = (K.active >> tid) & 1u;
+                    tan_ok = !on || q.bmode == 0;
+                    resc = on && q.rescale;
                 }
-                K.rescale = 0;
-                K.fs1 = K.fs2 = K.fs3 = K.fse = 1.f;
+                tan_ok = __syncthreads_and(tan_ok);
+                resc = __syncthreads_or(resc) && tan_ok;
+                auto prod = [&](int b0, int b1, int b2, int b3) {
+                    float f = 1.f;
+                    const int bs[4] = {b0, b1, b2, b3};
+                    for (int j = 0; j < 4; j++)
+                        if ((K.active >> bs[j]) & 1u) f *= s_rot[bs[j]].x;
+                    return tan_ok ? f : 1.f;
+                };
+                K.R.mode = tan_ok ? 0 : 2;
+                K.rescale = resc ? 1 : 0;
+                K.fs1 = prod(0, 9, 10, 11);
+                K.fs2 = prod(1, 2, 3, 4);
+                K.fs3 = prod(5, 6, 7, 8);
+                K.fse = K.rescale ? 1.f : K.fs1 * K.fs2 * K.fs3;
             }
             __syncthreads();
             cur = di;
         }
-        if (VAR == 1)
+        if (VAR == 1 && K.R.mode == 0)
+            tile_body<BWD, COST, NBUF, 0, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
+                                             tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+        else if (VAR == 1)
             tile_body<BWD, COST, NBUF, 2, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
                                              tinfo, descs, tile_begin, ndesc, cursor, s_tr);
         else if (K.R.mode == 0)
