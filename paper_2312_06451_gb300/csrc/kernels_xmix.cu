@@ -277,19 +277,55 @@ __device__ __forceinline__ float2 twist(float2 v, int k) {
     }
 }
 
-// Warp sum of one float per lane in float64 (fixed order); valid in lane 0.
-__device__ __forceinline__ double warp_sum(float v) {
-    double d = (double)v;
+// Float64 arithmetic runs at a small fraction of the float32 rate on this
+// part, so the per-tile partial sums below are summed across a warp in
+// float32 (a fixed shuffle tree, so still bitwise reproducible) and only the
+// warp totals are widened to float64 for the sums over tiles and warps.
+// Each thread's share is itself a float32 sum of a few hundred terms, so the
+// warp step adds an error of the same order (~1e-7 of the sum of magnitudes).
+
+// Warp sum of one float per lane; every lane gets the total.
+__device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-    return d;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// Deterministic block sum of one float per thread, accumulated in float64;
-// the result is valid in thread 0.
+// Warp sums of two floats per lane in one tree: the total of x lands in
+// lanes 0..15, the total of y in lanes 16..31.
+__device__ __forceinline__ float warp_sum2_f(float x, float y) {
+    const bool hi = (threadIdx.x & 16u) != 0;
+    float v = (hi ? y : x) + __shfl_xor_sync(0xffffffffu, hi ? x : y, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Warp sums of 16 floats per lane as a reduce-scatter: each step halves the
+// values a lane keeps and trades the other half with its partner, so value
+// j's total lands in lanes 2j and 2j + 1 after 16 shuffles (not 80).
+__device__ __forceinline__ float warp_sum16_f(const float (&v)[16]) {
+    const uint32_t lane = threadIdx.x & 31u;
+    float w8[8], w4[4], w2[2];
+    const bool h4 = lane & 16u, h3 = lane & 8u, h2 = lane & 4u, h1 = lane & 2u;
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+        w8[k] = (h4 ? v[k + 8] : v[k]) + __shfl_xor_sync(0xffffffffu, h4 ? v[k] : v[k + 8], 16);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        w4[k] = (h3 ? w8[k + 4] : w8[k]) + __shfl_xor_sync(0xffffffffu, h3 ? w8[k] : w8[k + 4], 8);
+#pragma unroll
+    for (int k = 0; k < 2; k++)
+        w2[k] = (h2 ? w4[k + 2] : w4[k]) + __shfl_xor_sync(0xffffffffu, h2 ? w4[k] : w4[k + 2], 4);
+    float w = (h1 ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, h1 ? w2[0] : w2[1], 2);
+    return w + __shfl_xor_sync(0xffffffffu, w, 1);
+}
+
+// Deterministic block sum of one float per thread: float32 within each
+// warp, float64 across warps; the result is valid in thread 0.
 template <int NW>
 __device__ __forceinline__ double block_sum(float v, double *red) {
-    double d = warp_sum(v);
+    double d = (double)warp_sum_f(v);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = d;
     __syncthreads();
@@ -778,24 +814,26 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     }
     // per-warp partial sums: slot tile * 8 + warp (no block barrier)
     if (BWD) {
-        if constexpr (MA) {  // slot (local bit j, tile, warp)
+        if constexpr (MA) {  // slot (local bit j, tile, warp); j's total in lane 2j
+            float v[16];
 #pragma unroll
-            for (int j = 0; j < 12; j++) {
-                if (!((active >> j) & 1u)) continue;
-                const double tb = warp_sum(bq[j]);
-                if (lane == 0 && D.part_beta) D.part_beta[((size_t)j * D.ntiles + tl) * kNW + warp] = tb;
+            for (int j = 0; j < 16; j++) v[j] = j < 12 ? bq[j < 12 ? j : 0] : 0.f;
+            const float tb = warp_sum16_f(v);
+            const uint32_t j = (uint32_t)lane >> 1;
+            if (!(lane & 1) && j < 12u && ((active >> j) & 1u) && D.part_beta)
+                D.part_beta[((size_t)j * D.ntiles + tl) * kNW + warp] = (double)tb;
+            if (flags & PF_PHASE) {
+                const float tg = warp_sum_f(eacc);
+                if (lane == 0 && D.part_gamma) D.part_gamma[tl * kNW + warp] = (double)tg;
             }
-        } else {
-            const double tb = warp_sum(bacc);
-            if (lane == 0 && D.part_beta) D.part_beta[tl * kNW + warp] = tb;
-        }
-        if (flags & PF_PHASE) {
-            const double tg = warp_sum(eacc);
-            if (lane == 0 && D.part_gamma) D.part_gamma[tl * kNW + warp] = tg;
+        } else {  // beta's total in lane 0, gamma's in lane 16
+            const float t = warp_sum2_f(bacc, eacc);
+            if (lane == 0 && D.part_beta) D.part_beta[tl * kNW + warp] = (double)t;
+            if ((flags & PF_PHASE) && lane == 16 && D.part_gamma) D.part_gamma[tl * kNW + warp] = (double)t;
         }
     } else if (flags & PF_E) {
-        const double te = warp_sum(eacc);
-        if (lane == 0 && D.part_E) D.part_E[tl * kNW + warp] = te;
+        const float te = warp_sum_f(eacc);
+        if (lane == 0 && D.part_E) D.part_E[tl * kNW + warp] = (double)te;
     }
 }
 
@@ -1309,13 +1347,12 @@ __global__ void __launch_bounds__(kNT) tile12_kernel(const SmallDesc *__restrict
             __syncthreads();
         }
     };
-    // fixed-order block sums of two per-thread values, in float64
+    // fixed-order block sums of two per-thread values: float32 within a
+    // warp (x in lanes 0..15, y in 16..31), float64 across warps
     auto block_sum2 = [&](float x, float y, double &X, double &Y) {
-        const double dx = warp_sum(x), dy = warp_sum(y);
-        if (lane == 0) {
-            s_red[0][warp] = dx;
-            s_red[1][warp] = dy;
-        }
+        const float t = warp_sum2_f(x, y);
+        if (lane == 0) s_red[0][warp] = (double)t;
+        if (lane == 16) s_red[1][warp] = (double)t;
         __syncthreads();
         X = 0.0;
         Y = 0.0;
