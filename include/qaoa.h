@@ -325,6 +325,7 @@ qaoa_status qaoa_cost_degeneracy(qaoa_ctx *ctx, const qaoa_problem *prob, int64_
  *   d_angles  device, n_sets x 2p float64 [beta_1..beta_p, gamma_1..gamma_p]
  *   d_E       device output, n_sets float64
  *   d_grad    device output, n_sets x 2p float64, or NULL
+ *   p         1 .. 1024 rounds
  * Float64 throughout (the reduced vector holds one amplitude per value).
  * Asynchronous on the context stream; a non-finite angle gives NaN results. */
 qaoa_status qaoa_grover_batched(qaoa_ctx *ctx, const int64_t *d_counts, int n_bins, int p, int n_sets,

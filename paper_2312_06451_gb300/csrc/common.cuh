@@ -239,6 +239,13 @@ struct DegLaunch {
     int n, k, m, kind, comp, n_bins;  // kind 0 MaxCut (2^n states), 1 DkS, 2 k-vertex cover
 };
 int grover_max_bins();
+// Size of the enumerated set for the bit-sliced weight-k count (2..8), or 0
+// when that kernel does not apply (MaxCut, degree-dependent costs, other sizes).
+int degeneracy_sliced_kk(const DegLaunch &L);
+// Counts the weight-KK sets {v} u T, v < min(T), for the (KK-1)-sets T of
+// colex ranks [t_start, t_start + t_count).
+cudaError_t launch_degeneracy_sliced(const DegLaunch &L, const uint64_t *d_binom, uint64_t t_start,
+                                     uint64_t t_count, unsigned long long *d_counts, int *d_err, cudaStream_t s);
 cudaError_t launch_degeneracy(const DegLaunch &L, const uint64_t *d_binom, uint64_t start, uint64_t count,
                               unsigned long long *d_counts, int *d_err, cudaStream_t s);
 cudaError_t launch_grover_eval(const int64_t *d_counts, int nb, int p, int n_sets, const double *d_angles,

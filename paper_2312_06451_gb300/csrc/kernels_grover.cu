@@ -221,65 +221,231 @@ degeneracy_kernel(const DegParams P, const uint64_t *__restrict__ binom, uint64_
     }
 }
 
-// ------------------------------------------------------- reduced simulation
-constexpr int kGrThreads = 512;
-constexpr int kGrWarps = kGrThreads / 32;
+// ------------------------------------------------- bit-sliced weight-k count
+// Weight-k problems whose cost is a function of I = |edges inside y| alone
+// (densest k-subgraph with y = x, k-vertex cover with y = the complement),
+// |y| = KK in 2..8.  The sets y = {v} u T with v < min(T) are counted per
+// (KK-1)-set T at once: I = inside(T) + a(v) with a(v) = |N(v) & T|, and
+// a(v) for all 128 vertices is the bitwise sum of the neighbour masks of T's
+// members, held as three bit planes (a <= 7).  The histogram of a over
+// v < min(T) is then a popcount per value of a.  T itself is T2 u {w} with
+// w < min(T2): the planes of T2 are built once per T2 (a carry-save adder
+// tree), and each T adds one mask to them.  Threads take equal ranges of T's
+// colex ranks, so every thread does the same work.
+struct Planes {
+    uint64_t b0l, b0h, b1l, b1h, b2l, b2h;
+};
 
-// Deterministic block sum of a complex float64 (fixed reduction order).
+__device__ __forceinline__ void csa(uint64_t a, uint64_t b, uint64_t c, uint64_t &sum, uint64_t &carry) {
+    sum = a ^ b ^ c;
+    carry = (a & b) | (c & (a ^ b));
+}
+
+// a + m for one more mask m (no overflow: a <= 7 by construction)
+__device__ __forceinline__ Planes planes_add(const Planes &P, uint64_t ml, uint64_t mh) {
+    Planes Q;
+    const uint64_t c0l = P.b0l & ml, c0h = P.b0h & mh;
+    Q.b0l = P.b0l ^ ml;
+    Q.b0h = P.b0h ^ mh;
+    const uint64_t c1l = P.b1l & c0l, c1h = P.b1h & c0h;
+    Q.b1l = P.b1l ^ c0l;
+    Q.b1h = P.b1h ^ c0h;
+    Q.b2l = P.b2l ^ c1l;
+    Q.b2h = P.b2h ^ c1h;
+    return Q;
+}
+
+// bits [0, x) of a 128-bit mask, 0 <= x <= 128
+__device__ __forceinline__ void below128(int x, uint64_t &lo, uint64_t &hi) {
+    lo = x >= 64 ? ~0ull : ((1ull << x) - 1ull);
+    hi = x <= 64 ? 0ull : (x >= 128 ? ~0ull : ((1ull << (x - 64)) - 1ull));
+}
+
+__device__ __forceinline__ int lowest128(uint64_t lo, uint64_t hi, int none) {
+    return lo ? __ffsll((long long)lo) - 1 : (hi ? 64 + __ffsll((long long)hi) - 1 : none);
+}
+
+template <int KK>
+__global__ void __launch_bounds__(kDegThreads)
+degeneracy_sliced_kernel(const DegParams P, const uint64_t *__restrict__ binom, uint64_t t_start, uint64_t t_count,
+                         int n_bins, unsigned long long *__restrict__ counts, int *err) {
+    constexpr int kNb = KK * (KK - 1) / 2 + 1;  // I = 0 .. C(KK, 2)
+    extern __shared__ uint32_t hpriv[];          // [kNb][kDegThreads]: one column per thread
+    __shared__ ulonglong2 s_up[128];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < 128; i += blockDim.x) s_up[i] = make_ulonglong2(P.up_lo[i], P.up_hi[i]);
+    for (int i = tid; i < kNb * kDegThreads; i += blockDim.x) hpriv[i] = 0u;
+    __syncthreads();
+    uint32_t *h = hpriv + tid;
+    const int n = P.n;
+
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + tid;
+    const uint64_t per = (t_count + nthr - 1) / nthr;
+    const uint64_t r0 = t_start + g * per;
+    const uint64_t r1 = min(t_start + t_count, r0 + per);
+    if (r0 < r1) {
+        // T of rank r0: w = its smallest member, T2 = the rest
+        Set2 T2 = unrank_colex128(r0, n, KK - 1, binom);
+        int w = lowest128(T2.lo, T2.hi, n);
+        if (w < 64) T2.lo ^= 1ull << w;
+        else T2.hi ^= 1ull << (w - 64);
+        Planes B2;
+        int tin2 = 0, lim = n;
+        auto build_t2 = [&]() {
+            // planes of a(v) = |N(v) & T2| by a carry-save tree over T2's KK-2 members
+            uint64_t ml[6], mh[6];
+            uint64_t zl = T2.lo, zh = T2.hi;
+#pragma unroll
+            for (int j = 0; j < 6; j++) {
+                ml[j] = mh[j] = 0ull;
+                if (j < KK - 2) {
+                    const int u = lowest128(zl, zh, 0);
+                    if (u < 64) zl &= zl - 1;
+                    else zh &= zh - 1;
+                    const ulonglong2 m = s_up[u];
+                    ml[j] = m.x;
+                    mh[j] = m.y;
+                }
+            }
+            uint64_t s1l, c1l, s2l, c2l, s1h, c1h, s2h, c2h;
+            csa(ml[0], ml[1], ml[2], s1l, c1l);
+            csa(ml[3], ml[4], ml[5], s2l, c2l);
+            csa(mh[0], mh[1], mh[2], s1h, c1h);
+            csa(mh[3], mh[4], mh[5], s2h, c2h);
+            B2.b0l = s1l ^ s2l;
+            B2.b0h = s1h ^ s2h;
+            csa(c1l, c2l, s1l & s2l, B2.b1l, B2.b2l);
+            csa(c1h, c2h, s1h & s2h, B2.b1h, B2.b2h);
+            // inside(T2) = (sum over members u of a(u)) / 2
+            tin2 = (__popcll(B2.b0l & T2.lo) + __popcll(B2.b0h & T2.hi) +
+                    2 * (__popcll(B2.b1l & T2.lo) + __popcll(B2.b1h & T2.hi)) +
+                    4 * (__popcll(B2.b2l & T2.lo) + __popcll(B2.b2h & T2.hi))) >> 1;
+            lim = KK > 2 ? lowest128(T2.lo, T2.hi, n) : n;
+        };
+        build_t2();
+        for (uint64_t r = r0; r < r1; r++) {
+            // T = T2 u {w}: its planes, inside(T) = inside(T2) + a_T2(w)
+            const ulonglong2 m = s_up[w];
+            const Planes B = planes_add(B2, m.x, m.y);
+            const bool wh = w >= 64;
+            const uint64_t wb = 1ull << (w & 63);
+            const int aw = (((wh ? B2.b0h : B2.b0l) & wb) ? 1 : 0) + (((wh ? B2.b1h : B2.b1l) & wb) ? 2 : 0) +
+                           (((wh ? B2.b2h : B2.b2l) & wb) ? 4 : 0);
+            const int tin = tin2 + aw;
+            // histogram of a_T(v) over v < w
+            uint64_t Rl, Rh;
+            below128(w, Rl, Rh);
+            const uint64_t x0l = B.b0l & Rl, x0h = B.b0h & Rh, x1l = B.b1l & Rl, x1h = B.b1h & Rh,
+                           x2l = B.b2l & Rl, x2h = B.b2h & Rh;
+            int rest = w;
+#pragma unroll
+            for (int f = 1; f < KK; f++) {
+                const uint64_t fl = ((f & 1) ? x0l : ~x0l) & ((f & 2) ? x1l : ~x1l) & ((f & 4) ? x2l : ~x2l);
+                const uint64_t fh = ((f & 1) ? x0h : ~x0h) & ((f & 2) ? x1h : ~x1h) & ((f & 4) ? x2h : ~x2h);
+                const int c = __popcll(fl) + __popcll(fh);
+                rest -= c;
+                h[(tin + f) * kDegThreads] += (uint32_t)c;
+            }
+            h[tin * kDegThreads] += (uint32_t)rest;
+            if (++w >= lim) {
+                // next T2 with a vertex below it (a T2 holding vertex 0 has no T)
+                if (KK > 2 && r + 1 < r1) {
+                    do {
+                        T2 = gosper_next(T2);
+                        build_t2();
+                    } while (lim == 0);
+                }
+                w = 0;
+            }
+        }
+    }
+    __syncthreads();
+    // bins: one warp per value of I, fixed order
+    for (int I = warp; I < kNb; I += kDegWarps) {
+        unsigned long long sacc = 0;
+        for (int t = lane; t < kDegThreads; t += 32) sacc += hpriv[I * kDegThreads + t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+        if (lane == 0 && sacc) {
+            const int cost = P.kind == 1 ? I : P.m - I;
+            if ((unsigned)cost < (unsigned)n_bins) atomicAdd(&counts[cost], sacc);
+            else atomicOr(err, DERR_BAD_DESC);
+        }
+    }
+}
+
+// ------------------------------------------------------- reduced simulation
+// One CTA per angle set, as many threads as values (a warp at least, 512 at
+// most).  Float64 runs at a small fraction of the float32 rate here, so the
+// per-value constants sqrt(d_j / N) and the mixer's cos / sin are computed
+// once per set, not in every loop.
+constexpr int kGrMaxThreads = 512;
+constexpr int kGrMaxWarps = kGrMaxThreads / 32;
+
+// Deterministic block sum of a complex float64 (fixed reduction order);
+// every thread gets the total.
 __device__ double2 block_sum2(double2 v, double2 *red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
     }
+    const int nw = blockDim.x >> 5;
+    if (nw == 1) return v;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) red[warp] = v;
     __syncthreads();
     double2 t = make_double2(0.0, 0.0);
-    for (int w = 0; w < kGrWarps; w++) {
+    for (int w = 0; w < nw; w++) {
         t.x += red[w].x;
         t.y += red[w].y;
     }
-    return t;  // every thread gets the total
+    return t;
 }
 
 __device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__global__ void __launch_bounds__(kGrThreads)
+__global__ void __launch_bounds__(kGrMaxThreads)
 grover_eval_kernel(const int64_t *__restrict__ counts, int nb, int p, const double *__restrict__ angles,
                    double *__restrict__ E, double *__restrict__ grad) {
     extern __shared__ double2 gsm[];
-    double2 *psi = gsm, *lam = gsm + nb, *red = gsm + 2 * nb;
+    double2 *psi = gsm, *lam = gsm + nb, *red = gsm + 2 * nb, *trig = red + kGrMaxWarps;
+    double *u = reinterpret_cast<double *>(trig + p);
     const int set = blockIdx.x;
     const double *a = angles + (size_t)set * 2 * p;
     // N = sum of the degeneracies (exact in float64 below 2^53)
     double2 nn = make_double2(0.0, 0.0);
     for (int j = threadIdx.x; j < nb; j += blockDim.x) nn.x += (double)counts[j];
     const double N = block_sum2(nn, red).x;
-    auto u_of = [&](int j) { return sqrt((double)counts[j] / N); };
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) psi[j] = make_double2(u_of(j), 0.0);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        u[j] = sqrt((double)counts[j] / N);
+        psi[j] = make_double2(u[j], 0.0);
+    }
+    for (int k = threadIdx.x; k < p; k += blockDim.x) {
+        double sb, cb;
+        sincos(a[k], &sb, &cb);
+        trig[k] = make_double2(cb, sb);
+    }
+    __syncthreads();
     for (int k = 0; k < p; k++) {
-        const double g = a[p + k], b = a[k];
+        const double g = a[p + k];
         double2 s = make_double2(0.0, 0.0);
         for (int j = threadIdx.x; j < nb; j += blockDim.x) {
             double sn, cs;
             sincos(g * (double)j, &sn, &cs);
             psi[j] = cmuld(psi[j], make_double2(cs, -sn));
-            const double u = u_of(j);
-            s.x += u * psi[j].x;
-            s.y += u * psi[j].y;
+            s.x += u[j] * psi[j].x;
+            s.y += u[j] * psi[j].y;
         }
         s = block_sum2(s, red);
-        double sb, cb;
-        sincos(b, &sb, &cb);
-        const double2 d = cmuld(make_double2(cb - 1.0, -sb), s);
+        const double2 d = cmuld(make_double2(trig[k].x - 1.0, -trig[k].y), s);  // (e^{-i b} - 1) <u|psi>
         for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-            const double u = u_of(j);
-            psi[j].x += d.x * u;
-            psi[j].y += d.y * u;
+            psi[j].x += d.x * u[j];
+            psi[j].y += d.y * u[j];
         }
     }
     double2 e = make_double2(0.0, 0.0);
@@ -290,30 +456,26 @@ grover_eval_kernel(const int64_t *__restrict__ counts, int nb, int p, const doub
     double *g_out = grad + (size_t)set * 2 * p;
     for (int j = threadIdx.x; j < nb; j += blockDim.x) lam[j] = make_double2((double)j * psi[j].x, (double)j * psi[j].y);
     for (int k = p - 1; k >= 0; k--) {
-        const double g = a[p + k], b = a[k];
+        const double g = a[p + k];
         double2 sl = make_double2(0.0, 0.0), sp = make_double2(0.0, 0.0);
         for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-            const double u = u_of(j);
-            sl.x += u * lam[j].x;
-            sl.y += u * lam[j].y;
-            sp.x += u * psi[j].x;
-            sp.y += u * psi[j].y;
+            sl.x += u[j] * lam[j].x;
+            sl.y += u[j] * lam[j].y;
+            sp.x += u[j] * psi[j].x;
+            sp.y += u[j] * psi[j].y;
         }
         sl = block_sum2(sl, red);
         sp = block_sum2(sp, red);
         // dE/dbeta_k = 2 Im( conj(<u|lam>) <u|psi> )
         if (threadIdx.x == 0) g_out[k] = 2.0 * (sl.x * sp.y - sl.y * sp.x);
-        double sb, cb;
-        sincos(b, &sb, &cb);
-        const double2 f = make_double2(cb - 1.0, sb);  // e^{+i b} - 1
+        const double2 f = make_double2(trig[k].x - 1.0, trig[k].y);  // e^{+i b} - 1
         const double2 dl = cmuld(f, sl), dp = cmuld(f, sp);
         double2 gg = make_double2(0.0, 0.0);
         for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-            const double u = u_of(j);
-            lam[j].x += dl.x * u;
-            lam[j].y += dl.y * u;
-            psi[j].x += dp.x * u;
-            psi[j].y += dp.y * u;
+            lam[j].x += dl.x * u[j];
+            lam[j].y += dl.y * u[j];
+            psi[j].x += dp.x * u[j];
+            psi[j].y += dp.y * u[j];
             // Im( conj(lam_j) c_j psi_j )
             gg.x += (double)j * (lam[j].x * psi[j].y - lam[j].y * psi[j].x);
             double sn, cs;
@@ -331,8 +493,7 @@ grover_eval_kernel(const int64_t *__restrict__ counts, int nb, int p, const doub
 
 int grover_max_bins() { return 4096; }
 
-cudaError_t launch_degeneracy(const DegLaunch &L, const uint64_t *d_binom, uint64_t start, uint64_t count,
-                              unsigned long long *d_counts, int *d_err, cudaStream_t s) {
+static DegParams deg_params(const DegLaunch &L) {
     DegParams P;
     memset(&P, 0, sizeof(P));
     for (int i = 0; i < 128; i++) {
@@ -348,6 +509,52 @@ cudaError_t launch_degeneracy(const DegLaunch &L, const uint64_t *d_binom, uint6
     P.m = L.m;
     P.kind = L.kind;
     P.comp = L.comp;
+    return P;
+}
+
+int degeneracy_sliced_kk(const DegLaunch &L) {
+    if (L.kind == 0) return 0;
+    const int kk = L.comp ? L.n - L.k : L.k;
+    const bool by_inside = (L.kind == 1) != (L.comp != 0);  // cost = I (DkS) or m - I (cover, complement)
+    return by_inside && kk >= 2 && kk <= 8 ? kk : 0;
+}
+
+template <int KK>
+static cudaError_t go_sliced(const DegParams &P, const uint64_t *d_binom, uint64_t t_start, uint64_t t_count,
+                             int n_bins, unsigned long long *d_counts, int *d_err, cudaStream_t s) {
+    constexpr int nb = KK * (KK - 1) / 2 + 1;
+    const size_t smem = (size_t)nb * kDegThreads * 4;
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, degeneracy_sliced_kernel<KK>, kDegThreads,
+                                                                  smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t want = (t_count + (uint64_t)kDegThreads * 8 - 1) / ((uint64_t)kDegThreads * 8);
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)nsm * std::max(1, occ)));
+    degeneracy_sliced_kernel<KK><<<grid, kDegThreads, smem, s>>>(P, d_binom, t_start, t_count, n_bins, d_counts,
+                                                                 d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_degeneracy_sliced(const DegLaunch &L, const uint64_t *d_binom, uint64_t t_start,
+                                     uint64_t t_count, unsigned long long *d_counts, int *d_err, cudaStream_t s) {
+    const DegParams P = deg_params(L);
+    switch (degeneracy_sliced_kk(L)) {
+    case 2: return go_sliced<2>(P, d_binom, t_start, t_count, L.n_bins, d_counts, d_err, s);
+    case 3: return go_sliced<3>(P, d_binom, t_start, t_count, L.n_bins, d_counts, d_err, s);
+    case 4: return go_sliced<4>(P, d_binom, t_start, t_count, L.n_bins, d_counts, d_err, s);
+    case 5: return go_sliced<5>(P, d_binom, t_start, t_count, L.n_bins, d_counts, d_err, s);
+    case 6: return go_sliced<6>(P, d_binom, t_start, t_count, L.n_bins, d_counts, d_err, s);
+    case 7: return go_sliced<7>(P, d_binom, t_start, t_count, L.n_bins, d_counts, d_err, s);
+    case 8: return go_sliced<8>(P, d_binom, t_start, t_count, L.n_bins, d_counts, d_err, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_degeneracy(const DegLaunch &L, const uint64_t *d_binom, uint64_t start, uint64_t count,
+                              unsigned long long *d_counts, int *d_err, cudaStream_t s) {
+    DegParams P = deg_params(L);
     int copies = (96 * 1024) / (4 * L.n_bins);
     copies = std::max(1, std::min(kDegWarps, copies));
     const size_t smem = (size_t)copies * L.n_bins * 4;
@@ -369,15 +576,17 @@ cudaError_t launch_degeneracy(const DegLaunch &L, const uint64_t *d_binom, uint6
 
 cudaError_t launch_grover_eval(const int64_t *d_counts, int nb, int p, int n_sets, const double *d_angles,
                                double *d_E, double *d_grad, cudaStream_t s) {
-    const size_t smem = (size_t)(2 * nb + kGrWarps) * sizeof(double2);
+    const size_t smem = (size_t)(2 * nb + kGrMaxWarps + p) * sizeof(double2) + (size_t)nb * sizeof(double);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(grover_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((2 * 4096 + kGrWarps) * sizeof(double2)));
+                                             200 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    grover_eval_kernel<<<n_sets, kGrThreads, smem, s>>>(d_counts, nb, p, d_angles, d_E, d_grad);
+    const int threads = std::min(kGrMaxThreads, std::max(32, (nb + 31) / 32 * 32));
+    grover_eval_kernel<<<n_sets, threads, smem, s>>>(d_counts, nb, p, d_angles, d_E, d_grad);
     return cudaGetLastError();
 }
 

@@ -1764,6 +1764,22 @@ qaoa_status qaoa_cost_degeneracy(qaoa_ctx *ctx, const qaoa_problem *prob, int64_
             QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "binomial table upload");
         }
         QG_CUDA(ctx, cudaMemsetAsync(d_counts, 0, sizeof(int64_t) * n_bins, ctx->stream), "counts clear");
+        if (const int kk = degeneracy_sliced_kk(L)) {
+            // bit-sliced count: all (kk-1)-sets T, each with the v < min(T)
+            uint64_t NT = 1;
+            for (int i = 0; i < kk - 1; i++) NT = NT * (uint64_t)(n - i) / (uint64_t)(i + 1);
+            // each T adds at most 127 to one thread's 32-bit counter per value
+            const uint64_t tslab = 1ull << 34;
+            for (uint64_t t0 = 0; t0 < NT; t0 += tslab) {
+                cudaError_t e = launch_degeneracy_sliced(L, static_cast<const uint64_t *>(d_binom), t0,
+                                                         std::min(tslab, NT - t0),
+                                                         reinterpret_cast<unsigned long long *>(d_counts),
+                                                         ctx->d_err, ctx->stream);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "degeneracy kernel launch");
+                ctx->launches++;
+            }
+            return read_dev_err(ctx);
+        }
         const uint64_t slab = 1ull << 36;  // keeps every warp's 32-bit shared counters from wrapping
         for (uint64_t s0 = 0; s0 < N; s0 += slab) {
             const uint64_t cnt = std::min(slab, N - s0);
@@ -1786,7 +1802,8 @@ qaoa_status qaoa_grover_batched(qaoa_ctx *ctx, const int64_t *d_counts, int n_bi
     if (!d_counts || !d_angles || !d_E) return fail(ctx, QAOA_ERR_INVALID, "counts, angles and E must be non-NULL");
     if (n_bins < 1 || n_bins > grover_max_bins())
         return fail(ctx, QAOA_ERR_INVALID, "n_bins must be in [1, %d]", grover_max_bins());
-    if (p < 1 || n_sets < 1) return fail(ctx, QAOA_ERR_INVALID, "p and n_sets must be >= 1");
+    if (p < 1 || p > 1024 || n_sets < 1)
+        return fail(ctx, QAOA_ERR_INVALID, "p must be in [1, 1024] and n_sets >= 1 (p=%d, n_sets=%d)", p, n_sets);
     cudaSetDevice(ctx->device);
     cudaError_t e = launch_grover_eval(d_counts, n_bins, p, n_sets, d_angles, d_E, d_grad, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "Grover kernel launch");

@@ -34,6 +34,10 @@ def Q():
     ("dks", 20, 7, 0.5), ("dks", 20, 13, 0.5), ("dks", 16, 0, 0.5), ("dks", 16, 16, 0.5),
     ("kvc", 16, 5, 0.4), ("kvc", 18, 12, 0.3),
     ("dks", 100, 3, 0.5), ("kvc", 128, 2, 0.1), ("dks", 70, 67, 0.2),
+    # bit-sliced count (cost a function of the inside edges, set size 2..8):
+    # one and two 64-bit words, set sizes 2 and 8, the complement form
+    ("dks", 28, 8, 0.4), ("dks", 90, 2, 0.5), ("dks", 64, 4, 0.3), ("dks", 66, 4, 0.3),
+    ("dks", 128, 3, 0.3), ("kvc", 24, 22, 0.3), ("kvc", 26, 19, 0.3),
 ])
 def test_degeneracies_match_brute_force(Q, oracle_mod, prob, n, k, p_edge):
     qg, ctx = Q
@@ -54,6 +58,29 @@ def test_degeneracies_two_slabs(Q):
     assert sum(got) == 1 << n
     assert sum(c * v for c, v in enumerate(got)) * 2 == len(e) * (1 << n)
     assert all(v % 2 == 0 for v in got)
+
+
+def test_degeneracies_full_size_moments(Q):
+    """All weight-6 subsets of the 100-vertex benchmark graph (1.19e9 states):
+    the count and the first two moments of the inside-edge count are fixed by
+    the graph alone, exactly.  sum_S I(S)^2 counts ordered edge pairs inside S:
+    equal pairs C(n-2, k-2) times, pairs sharing one vertex C(n-3, k-3) times,
+    disjoint pairs C(n-4, k-4) times."""
+    from qaoa_inputs import WORKLOADS, workload_instance
+
+    qg, ctx = Q
+    spec = WORKLOADS[6]
+    n, k = spec["n"], spec["k"]
+    e = np.asarray(workload_instance(6, n_sets=1)["edges"]).reshape(-1, 2)
+    m = len(e)
+    deg = np.bincount(e.ravel(), minlength=n).astype(object)
+    share = sum(d * (d - 1) for d in deg)
+    got = [int(v) for v in ctx.cost_degeneracy("dks", n, edges=e, k=k).cpu().numpy()]
+    assert sum(got) == math.comb(n, k)
+    assert sum(c * v for c, v in enumerate(got)) == m * math.comb(n - 2, k - 2)
+    second = m * math.comb(n - 2, k - 2) + share * math.comb(n - 3, k - 3) + \
+        (m * (m - 1) - share) * math.comb(n - 4, k - 4)
+    assert sum(c * c * v for c, v in enumerate(got)) == second
 
 
 def test_kvc_cost_vector(Q, oracle_mod):
