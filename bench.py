@@ -637,11 +637,12 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     if args.workload == 6:
         # integer enumeration: the bound is the SM's bit-count unit (16
         # 32-bit population counts a clock per SM).  The bit-sliced count
-        # takes, per (k-1)-set T, one 128-bit population count (4 x 32-bit)
-        # for each value 1..k-1 of |N(v) & T|, and T covers (n-k+1)/k
-        # states on average: 4k(k-1)/(n-k+1) counts per state.
+        # takes, per (k-1)-set T, one 64-bit population count (2 x 32-bit)
+        # per plane combination 1..k-1 (the swept vertices v < w lie in the
+        # low word for all but 0.5% of the T), and T covers (n-k+1)/k
+        # states on average: 2k(k-1)/(n-k+1) counts per state.
         dms = W.degeneracy_ms(args.steps)
-        ops = 4 * W.k * (W.k - 1) / (W.n - W.k + 1)
+        ops = 2 * W.k * (W.k - 1) / (W.n - W.k + 1)
         achieved = W.units / (dms * 1e-3) / 1e9
         peak = 152 * 16 * 2.07e9 / ops / 1e9
         roof = {"bound": "alu", "kernel": "degeneracy_sliced_kernel", "achieved": achieved, "peak": peak,

@@ -228,10 +228,12 @@ degeneracy_kernel(const DegParams P, const uint64_t *__restrict__ binom, uint64_
 // (KK-1)-set T at once: I = inside(T) + a(v) with a(v) = |N(v) & T|, and
 // a(v) for all 128 vertices is the bitwise sum of the neighbour masks of T's
 // members, held as three bit planes (a <= 7).  The histogram of a over
-// v < min(T) is then a popcount per value of a.  T itself is T2 u {w} with
-// w < min(T2): the planes of T2 are built once per T2 (a carry-save adder
-// tree), and each T adds one mask to them.  Threads take equal ranges of T's
-// colex ranks, so every thread does the same work.
+// v < min(T) is then a popcount per value of a.  T itself is T3 u {a, w}
+// with w < a < min(T3): the planes of T3 are built once per T3 (a carry-save
+// adder tree), those of T2 = T3 u {a} by one mask added per a, and those of T
+// by one more per w.  A thread's change of T2 is then short, so the lanes of
+// a warp, which change T2 at different times, stay together.  Threads take
+// equal ranges of T's colex ranks, so every thread does the same work.
 struct Planes {
     uint64_t b0l, b0h, b1l, b1h, b2l, b2h;
 };
@@ -255,14 +257,34 @@ __device__ __forceinline__ Planes planes_add(const Planes &P, uint64_t ml, uint6
     return Q;
 }
 
-// bits [0, x) of a 128-bit mask, 0 <= x <= 128
-__device__ __forceinline__ void below128(int x, uint64_t &lo, uint64_t &hi) {
-    lo = x >= 64 ? ~0ull : ((1ull << x) - 1ull);
-    hi = x <= 64 ? 0ull : (x >= 128 ? ~0ull : ((1ull << (x - 64)) - 1ull));
-}
-
 __device__ __forceinline__ int lowest128(uint64_t lo, uint64_t hi, int none) {
     return lo ? __ffsll((long long)lo) - 1 : (hi ? 64 + __ffsll((long long)hi) - 1 : none);
+}
+
+// p[S] += the number of v whose plane bits include S (S = 1..7 as a set of
+// planes); an S above KK - 1 has no v (every |N(v) & T| <= KK - 1).
+template <int KK>
+__device__ __forceinline__ void plane_popcounts(uint64_t x0, uint64_t x1, uint64_t x2, int (&p)[8]) {
+#pragma unroll
+    for (int S = 1; S < 8; S++) {
+        if (S > KK - 1) continue;
+        uint64_t m = ~0ull;
+        if (S & 1) m &= x0;
+        if (S & 2) m &= x1;
+        if (S & 4) m &= x2;
+        p[S] += __popcll(m);
+    }
+}
+
+// The number of v with value exactly f, by inclusion-exclusion over the
+// plane sets that contain f's bits.
+template <int KK>
+__device__ __forceinline__ int value_count(const int (&p)[8], int f) {
+    int c = 0;
+#pragma unroll
+    for (int S = 1; S < 8; S++)
+        if (S <= KK - 1 && (S & f) == f) c += (__popc((unsigned)(S ^ f)) & 1) ? -p[S] : p[S];
+    return c;
 }
 
 template <int KK>
@@ -285,21 +307,27 @@ degeneracy_sliced_kernel(const DegParams P, const uint64_t *__restrict__ binom, 
     const uint64_t r0 = t_start + g * per;
     const uint64_t r1 = min(t_start + t_count, r0 + per);
     if (r0 < r1) {
-        // T of rank r0: w = its smallest member, T2 = the rest
-        Set2 T2 = unrank_colex128(r0, n, KK - 1, binom);
-        int w = lowest128(T2.lo, T2.hi, n);
-        if (w < 64) T2.lo ^= 1ull << w;
-        else T2.hi ^= 1ull << (w - 64);
-        Planes B2;
-        int tin2 = 0, lim = n;
-        auto build_t2 = [&]() {
-            // planes of a(v) = |N(v) & T2| by a carry-save tree over T2's KK-2 members
+        // T of rank r0 = T3 u {a, w}, w < a < min(T3); with KK = 2, T = {w}
+        Set2 T3 = unrank_colex128(r0, n, KK - 1, binom);
+        int w = lowest128(T3.lo, T3.hi, n);
+        if (w < 64) T3.lo ^= 1ull << w;
+        else T3.hi ^= 1ull << (w - 64);
+        int a = n;
+        if (KK >= 3) {
+            a = lowest128(T3.lo, T3.hi, n);
+            if (a < 64) T3.lo ^= 1ull << a;
+            else T3.hi ^= 1ull << (a - 64);
+        }
+        Planes B3, B2;
+        int tin3 = 0, lim3 = n, tin2 = 0;
+        auto build_t3 = [&]() {
+            // planes of |N(v) & T3| by a carry-save tree over T3's KK-3 members
             uint64_t ml[6], mh[6];
-            uint64_t zl = T2.lo, zh = T2.hi;
+            uint64_t zl = T3.lo, zh = T3.hi;
 #pragma unroll
             for (int j = 0; j < 6; j++) {
                 ml[j] = mh[j] = 0ull;
-                if (j < KK - 2) {
+                if (j < KK - 3) {
                     const int u = lowest128(zl, zh, 0);
                     if (u < 64) zl &= zl - 1;
                     else zh &= zh - 1;
@@ -313,50 +341,71 @@ degeneracy_sliced_kernel(const DegParams P, const uint64_t *__restrict__ binom, 
             csa(ml[3], ml[4], ml[5], s2l, c2l);
             csa(mh[0], mh[1], mh[2], s1h, c1h);
             csa(mh[3], mh[4], mh[5], s2h, c2h);
-            B2.b0l = s1l ^ s2l;
-            B2.b0h = s1h ^ s2h;
-            csa(c1l, c2l, s1l & s2l, B2.b1l, B2.b2l);
-            csa(c1h, c2h, s1h & s2h, B2.b1h, B2.b2h);
-            // inside(T2) = (sum over members u of a(u)) / 2
-            tin2 = (__popcll(B2.b0l & T2.lo) + __popcll(B2.b0h & T2.hi) +
-                    2 * (__popcll(B2.b1l & T2.lo) + __popcll(B2.b1h & T2.hi)) +
-                    4 * (__popcll(B2.b2l & T2.lo) + __popcll(B2.b2h & T2.hi))) >> 1;
-            lim = KK > 2 ? lowest128(T2.lo, T2.hi, n) : n;
+            B3.b0l = s1l ^ s2l;
+            B3.b0h = s1h ^ s2h;
+            csa(c1l, c2l, s1l & s2l, B3.b1l, B3.b2l);
+            csa(c1h, c2h, s1h & s2h, B3.b1h, B3.b2h);
+            // inside(T3) = (sum over members u of |N(u) & T3|) / 2
+            tin3 = (__popcll(B3.b0l & T3.lo) + __popcll(B3.b0h & T3.hi) +
+                    2 * (__popcll(B3.b1l & T3.lo) + __popcll(B3.b1h & T3.hi)) +
+                    4 * (__popcll(B3.b2l & T3.lo) + __popcll(B3.b2h & T3.hi))) >> 1;
+            lim3 = KK >= 4 ? lowest128(T3.lo, T3.hi, n) : n;
         };
-        build_t2();
+        // T2 = T3 u {a}: one more mask, inside(T2) = inside(T3) + |N(a) & T3|
+        auto set_t2 = [&]() {
+            if (KK >= 3) {
+                const ulonglong2 m = s_up[a];
+                B2 = planes_add(B3, m.x, m.y);
+                tin2 = tin3 + __popcll(m.x & T3.lo) + __popcll(m.y & T3.hi);
+            } else {
+                B2 = B3;
+                tin2 = 0;
+            }
+        };
+        build_t3();
+        set_t2();
         for (uint64_t r = r0; r < r1; r++) {
-            // T = T2 u {w}: its planes, inside(T) = inside(T2) + a_T2(w)
-            const ulonglong2 m = s_up[w];
-            const Planes B = planes_add(B2, m.x, m.y);
-            const bool wh = w >= 64;
-            const uint64_t wb = 1ull << (w & 63);
-            const int aw = (((wh ? B2.b0h : B2.b0l) & wb) ? 1 : 0) + (((wh ? B2.b1h : B2.b1l) & wb) ? 2 : 0) +
-                           (((wh ? B2.b2h : B2.b2l) & wb) ? 4 : 0);
+            // T = T2 u {w}: its planes, inside(T) = inside(T2) + a_T2(w), and
+            // the planes' popcounts over v < w
+            int p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            int aw;
+            if (w < 64) {  // every v < w in the low word (nearly every T)
+                const uint64_t ml = s_up[w].x, R = (1ull << w) - 1ull;
+                const uint64_t c0 = B2.b0l & ml, c1 = B2.b1l & c0;
+                plane_popcounts<KK>((B2.b0l ^ ml) & R, (B2.b1l ^ c0) & R, (B2.b2l ^ c1) & R, p);
+                aw = (int)((B2.b0l >> w) & 1ull) + 2 * (int)((B2.b1l >> w) & 1ull) + 4 * (int)((B2.b2l >> w) & 1ull);
+            } else {
+                const ulonglong2 m = s_up[w];
+                const Planes B = planes_add(B2, m.x, m.y);
+                const uint64_t Rh = (1ull << (w - 64)) - 1ull;
+                plane_popcounts<KK>(B.b0l, B.b1l, B.b2l, p);
+                plane_popcounts<KK>(B.b0h & Rh, B.b1h & Rh, B.b2h & Rh, p);
+                const int sh = w - 64;
+                aw = (int)((B2.b0h >> sh) & 1ull) + 2 * (int)((B2.b1h >> sh) & 1ull) + 4 * (int)((B2.b2h >> sh) & 1ull);
+            }
             const int tin = tin2 + aw;
-            // histogram of a_T(v) over v < w
-            uint64_t Rl, Rh;
-            below128(w, Rl, Rh);
-            const uint64_t x0l = B.b0l & Rl, x0h = B.b0h & Rh, x1l = B.b1l & Rl, x1h = B.b1h & Rh,
-                           x2l = B.b2l & Rl, x2h = B.b2h & Rh;
             int rest = w;
 #pragma unroll
             for (int f = 1; f < KK; f++) {
-                const uint64_t fl = ((f & 1) ? x0l : ~x0l) & ((f & 2) ? x1l : ~x1l) & ((f & 4) ? x2l : ~x2l);
-                const uint64_t fh = ((f & 1) ? x0h : ~x0h) & ((f & 2) ? x1h : ~x1h) & ((f & 4) ? x2h : ~x2h);
-                const int c = __popcll(fl) + __popcll(fh);
+                const int c = value_count<KK>(p, f);
                 rest -= c;
                 h[(tin + f) * kDegThreads] += (uint32_t)c;
             }
             h[tin * kDegThreads] += (uint32_t)rest;
-            if (++w >= lim) {
-                // next T2 with a vertex below it (a T2 holding vertex 0 has no T)
-                if (KK > 2 && r + 1 < r1) {
-                    do {
-                        T2 = gosper_next(T2);
-                        build_t2();
-                    } while (lim == 0);
-                }
+            // next T: w + 1 below a, else a + 1 below min(T3), else the next
+            // T3 with at least two vertices below it (a >= 1 and w < a)
+            if (++w >= a && KK >= 3 && r + 1 < r1) {
                 w = 0;
+                if (++a >= lim3) {
+                    if (KK >= 4) {
+                        do {
+                            T3 = gosper_next(T3);
+                            build_t3();
+                        } while (lim3 < 2);
+                    }
+                    a = 1;
+                }
+                set_t2();
             }
         }
     }
