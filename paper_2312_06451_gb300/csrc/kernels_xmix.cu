@@ -437,6 +437,9 @@ struct PassGeom {
     static constexpr uint32_t kCostB = kTile * (COST == 0 ? 4 : 1);
     static constexpr uint32_t kBufB = kPsiB * (BWD ? 2 : 1) + kCostB;
     static constexpr uint32_t kStashB = (BWD && COST == 0) ? kTile * 4 : 0;  // after the buffers
+    // single-buffered adjoint with float costs: buffer 0's cost slot and the
+    // stash make one vector's worth of transpose space (see tile_body)
+    static constexpr bool kEarly = BWD && COST == 0 && kCostB + kStashB == kPsiB;
     static constexpr uint32_t kHead = 256 + kPhaseTable * 8;  // barriers, tile info, phase table
 };
 
@@ -691,6 +694,20 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
         a[i] = sp[p2 ^ ((uint32_t)i << 1)];
         if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
     }
+    // A single-buffered adjoint tile that reads no cost hands its buffer back
+    // here, after the stage-2 read, and runs the warp-private stage 2 -> 3
+    // transpose through buffer 0's cost slot and the float-cost stash (32 KB),
+    // which no load writes while the next tile belongs to the same
+    // descriptor (it reads no cost either).  The next tile's loads then run
+    // under stages 2 and 3 instead of stage 3 alone.
+    const uint32_t tn = t + (uint32_t)NBUF * stride;
+    const bool early = G::kEarly && NBUF == 1 && !needs_cost<BWD>(flags) && (tn >= total || tn < s_tr[1]);
+    if (early) {
+        __syncthreads();
+        if (warp == 0 && tn < total)
+            issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc, cursor, &D,
+                                  s_tr);
+    }
     if constexpr (MA) stage_rot_ma<BWD, MODE, 1, 2, 3, 4>(a, l, stage_mask(active, 1, 2, 3, 4), s_rot, bq, pscale, true);
     else stage_rot<BWD, MODE>(a, l, stage_mask(active, 1, 2, 3, 4), K.R, pscale, bacc, true, !GM);
     if (K.rescale) {
@@ -701,18 +718,35 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     // ---------------- stage 2 -> 3: local bits 9..11 are the warp index in
     // both layouts and the swizzle moves bits 1..3 only, so each warp reads
     // back just what it wrote: a warp barrier is enough
-    __syncwarp();
+    if (G::kEarly && NBUF == 1 && early) {
+        // one vector at a time through the 32 KB behind buffer 0's vectors
+        float2 *scr = reinterpret_cast<float2 *>(bufs + 2 * G::kPsiB);
+        __syncwarp();
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
-        sp[p2 ^ ((uint32_t)i << 1)] = a[i];
-        if (BWD) sl[p2 ^ ((uint32_t)i << 1)] = l[i];
-    }
-    __syncwarp();
+        for (int i = 0; i < 16; i++) scr[p2 ^ ((uint32_t)i << 1)] = a[i];
+        __syncwarp();
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
-        const uint32_t idx = p3 ^ swz((uint32_t)i << 5);
-        a[i] = sp[idx];
-        if (BWD) l[i] = sl[idx];
+        for (int i = 0; i < 16; i++) a[i] = scr[p3 ^ swz((uint32_t)i << 5)];
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 16; i++) scr[p2 ^ ((uint32_t)i << 1)] = l[i];
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 16; i++) l[i] = scr[p3 ^ swz((uint32_t)i << 5)];
+    } else {
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            sp[p2 ^ ((uint32_t)i << 1)] = a[i];
+            if (BWD) sl[p2 ^ ((uint32_t)i << 1)] = l[i];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const uint32_t idx = p3 ^ swz((uint32_t)i << 5);
+            a[i] = sp[idx];
+            if (BWD) l[i] = sl[idx];
+        }
     }
     // Cost values of this thread's stage-3 amplitudes, read before the buffer
     // goes back to the loader: uint8 costs packed four to a register; float
@@ -747,10 +781,9 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
         return cst[i];
     };
     // the buffer is consumed: start the tile NBUF ahead
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t tn = t + (uint32_t)NBUF * stride;
-        if (tn < total)
+    if (!early) {
+        __syncthreads();
+        if (warp == 0 && tn < total)
             issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc, cursor, &D,
                                   s_tr);
     }
