@@ -208,9 +208,11 @@ cudaError_t launch_small(const SmallDesc *d_descs, int ndesc, int cost_dtype, in
                          int max_n, int *d_err, cudaStream_t s);
 // bwd: 0 forward, 1 adjoint.  Persistent launch over total_tiles tiles.
 // var: 0 transverse field, 1 multi-angle, 2 general X mixer (half rounds)
+// d_sched: this launch's tile counter, zero when the launch starts.
+// cost_free: no descriptor of the launch reads the cost vector.
 cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int var, const PassDesc *d_descs,
                          const uint32_t *d_tile_begin, int ndesc, uint32_t total_tiles,
-                         int *d_err, cudaStream_t s);
+                         int *d_err, uint32_t *d_sched, int cost_free, cudaStream_t s);
 int small_max_n();
 // n = 12, transverse-field mixer: one CTA per angle set keeps the whole state
 // as one register-staged tile (descriptors as for launch_small).

@@ -550,6 +550,21 @@ __device__ __forceinline__ void issue_tile(uint32_t t, unsigned char *buf, uint3
     }
 }
 
+// Tiles are handed out dynamically: the first NBUF per CTA statically
+// (blockIdx + k gridDim), the rest from a per-launch counter in the order CTAs
+// ask for them, so CTAs that run faster take more tiles and the launch ends
+// with every CTA within about one tile of the others.  Partial sums sit in
+// per-tile slots, so the results do not depend on which CTA took a tile.
+// A claim past the last tile posts an end marker through the buffer's barrier.
+constexpr int kTileEnd = -2;
+
+__device__ __forceinline__ void post_end(uint32_t bar, TileInfo *info) {
+    if ((threadIdx.x & 31) == 0) {
+        info->di = kTileEnd;
+        mbar_arrive_tx(bar, 0);
+    }
+}
+
 // Constants of the descriptor currently being processed.
 struct PassConst {
     Rot R;
@@ -568,7 +583,7 @@ struct PassConst {
 template <int BWD, int COST, int NBUF, int MODE, int VAR>
 __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D, const float2 *stab,
                                           const float4 *s_rot, const float4 *s_w,
-                                          unsigned char *bufs, int b, uint32_t bar, uint32_t t, uint32_t stride,
+                                          unsigned char *bufs, int b, uint32_t bar, uint32_t *sched, int cost_free,
                                           uint32_t total, uint32_t base, uint32_t tl, TileInfo *tinfo,
                                           const PassDesc *__restrict__ descs,
                                           const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor,
@@ -581,6 +596,17 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     const uint32_t l3 = (uint32_t)lane | ((uint32_t)warp << 9);
     const uint32_t p1 = swz(l1), p2 = swz(l2), p3 = swz(l3);
     const uint32_t flags = K.flags, active = K.active;
+    // warp 0: claim the next tile for this buffer and start its loads
+    auto claim_issue = [&]() {
+        uint32_t tn = 0;
+        if (lane == 0) tn = (uint32_t)NBUF * gridDim.x + atomicAdd(sched, 1u);
+        tn = __shfl_sync(0xffffffffu, tn, 0);
+        if (tn < total)
+            issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc, cursor, &D,
+                                  s_tr);
+        else
+            post_end(bar, &tinfo[b]);
+    };
 
     float2 *sp = reinterpret_cast<float2 *>(bufs + b * G::kBufB);
     float2 *sl = sp + kTile;
@@ -697,16 +723,13 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     // A single-buffered adjoint tile that reads no cost hands its buffer back
     // here, after the stage-2 read, and runs the warp-private stage 2 -> 3
     // transpose through buffer 0's cost slot and the float-cost stash (32 KB),
-    // which no load writes while the next tile belongs to the same
-    // descriptor (it reads no cost either).  The next tile's loads then run
-    // under stages 2 and 3 instead of stage 3 alone.
-    const uint32_t tn = t + (uint32_t)NBUF * stride;
-    const bool early = G::kEarly && NBUF == 1 && !needs_cost<BWD>(flags) && (tn >= total || tn < s_tr[1]);
+    // which no load writes while the launch reads no cost at all (cost_free).
+    // The next tile's loads then run under stages 2 and 3 instead of stage 3
+    // alone.
+    const bool early = G::kEarly && NBUF == 1 && cost_free && !needs_cost<BWD>(flags);
     if (early) {
         __syncthreads();
-        if (warp == 0 && tn < total)
-            issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc, cursor, &D,
-                                  s_tr);
+        if (warp == 0) claim_issue();
     }
     if constexpr (MA) stage_rot_ma<BWD, MODE, 1, 2, 3, 4>(a, l, stage_mask(active, 1, 2, 3, 4), s_rot, bq, pscale, true);
     else stage_rot<BWD, MODE>(a, l, stage_mask(active, 1, 2, 3, 4), K.R, pscale, bacc, true, !GM);
@@ -783,9 +806,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     // the buffer is consumed: start the tile NBUF ahead
     if (!early) {
         __syncthreads();
-        if (warp == 0 && tn < total)
-            issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc, cursor, &D,
-                                  s_tr);
+        if (warp == 0) claim_issue();
     }
     // psi after the last stage is needed only when it is stored or meets the
     // phase epilogue (the adjoint with per-pass checkpoints stores lambda only)
@@ -873,7 +894,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
 template <int BWD, int COST, int NBUF, int VAR>
 __global__ void __launch_bounds__(kNT, (BWD && NBUF > 1) ? 1 : 2)
 xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ tile_begin, int ndesc,
-             uint32_t total, int *err) {
+             uint32_t total, int *err, uint32_t *__restrict__ sched, int cost_free) {
     using G = PassGeom<BWD, COST>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
@@ -899,6 +920,8 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
             if (t < total)
                 issue_tile<BWD, COST>(t, bufs + k * G::kBufB, smem_u32(&bars[k]), &tinfo[k], descs, tile_begin,
                                       ndesc, cursor, nullptr, nullptr);
+            else
+                post_end(smem_u32(&bars[k]), &tinfo[k]);
         }
     }
     const uint32_t l3 = (uint32_t)lane | ((uint32_t)warp << 9);
@@ -906,22 +929,20 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
     PassConst K;
 
     for (uint32_t it = 0;; it++) {
-        const uint32_t t = blockIdx.x + it * stride;
-        if (t >= total) break;
         const int b = (int)(it % NBUF);
         const uint32_t bar = smem_u32(&bars[b]);
         const bool ok = mbar_wait(bar, (it / NBUF) & 1u);
         const TileInfo ti = tinfo[b];
+        if (ok && ti.di == kTileEnd) break;  // uniform; later claims are end markers too
         const int di = ok ? ti.di : -1;
         if (di != cur) {  // uniform: every thread read the same tile info
             __syncthreads();  // the previous tile's epilogue is done with D / stab
             if (di < 0) {
                 if (tid == 0) atomicOr(err, ok ? DERR_BAD_DESC : DERR_TIMEOUT);
                 // let every load this CTA started land before the block exits
-                for (int k = 1; k < NBUF; k++) {
-                    const uint32_t tk = t + (uint32_t)k * stride;
-                    if (tk < total) mbar_wait(smem_u32(&bars[(it + k) % NBUF]), ((it + k) / NBUF) & 1u);
-                }
+                // (each of the other buffers holds a claimed tile or an end marker)
+                for (int k = 1; k < NBUF; k++)
+                    mbar_wait(smem_u32(&bars[(it + k) % NBUF]), ((it + k) / NBUF) & 1u);
                 if (!ok) mbar_wait(bar, (it / NBUF) & 1u);
                 return;
             }
@@ -1001,16 +1022,16 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
             cur = di;
         }
         if (VAR == 1 && K.R.mode == 0)
-            tile_body<BWD, COST, NBUF, 0, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
+            tile_body<BWD, COST, NBUF, 0, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base, ti.tl,
                                              tinfo, descs, tile_begin, ndesc, cursor, s_tr);
         else if (VAR == 1)
-            tile_body<BWD, COST, NBUF, 2, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
+            tile_body<BWD, COST, NBUF, 2, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base, ti.tl,
                                              tinfo, descs, tile_begin, ndesc, cursor, s_tr);
         else if (K.R.mode == 0)
-            tile_body<BWD, COST, NBUF, 0, VAR>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
+            tile_body<BWD, COST, NBUF, 0, VAR>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base, ti.tl,
                                              tinfo, descs, tile_begin, ndesc, cursor, s_tr);
         else
-            tile_body<BWD, COST, NBUF, 2, VAR>(K, D, stab, s_rot, s_w, bufs, b, bar, t, stride, total, ti.base, ti.tl,
+            tile_body<BWD, COST, NBUF, 2, VAR>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base, ti.tl,
                                              tinfo, descs, tile_begin, ndesc, cursor, s_tr);
     }
 }
@@ -1510,8 +1531,8 @@ __global__ void __launch_bounds__(32) reduce2_kernel(const RedOut *__restrict__ 
 }
 
 template <int BWD, int COST, int NBUF, int VAR>
-cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t tiles, int *err,
-                       cudaStream_t s) {
+cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t tiles, int *err, uint32_t *sched,
+                       int cost_free, cudaStream_t s) {
     using G = PassGeom<BWD, COST>;
     const size_t smem = G::kHead + (size_t)NBUF * G::kBufB + G::kStashB;
     static int grid_cap = 0;
@@ -1527,7 +1548,7 @@ cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t t
         grid_cap = std::max(1, nsm * std::max(1, per_sm));
     }
     const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)grid_cap);
-    xpass_kernel<BWD, COST, NBUF, VAR><<<grid, kNT, smem, s>>>(d, tb, nd, tiles, err);
+    xpass_kernel<BWD, COST, NBUF, VAR><<<grid, kNT, smem, s>>>(d, tb, nd, tiles, err, sched, cost_free);
     return cudaGetLastError();
 }
 
@@ -1553,24 +1574,25 @@ int small_max_n() { return kSmallMaxN; }
 
 template <int VAR>
 cudaError_t launch_xpass_t(int bwd, int cost_dtype, int nbuf, const PassDesc *d, const uint32_t *tb, int nd,
-                           uint32_t tiles, int *err, cudaStream_t s) {
-    if (!bwd) return cost_dtype == 0 ? launch_one<0, 0, 2, VAR>(d, tb, nd, tiles, err, s)
-                                     : launch_one<0, 1, 2, VAR>(d, tb, nd, tiles, err, s);
+                           uint32_t tiles, int *err, uint32_t *sched, int cf, cudaStream_t s) {
+    if (!bwd) return cost_dtype == 0 ? launch_one<0, 0, 2, VAR>(d, tb, nd, tiles, err, sched, cf, s)
+                                     : launch_one<0, 1, 2, VAR>(d, tb, nd, tiles, err, sched, cf, s);
     // adjoint: one tile buffer and two CTAs per SM (128 registers a thread),
     // or two buffers and one CTA per SM (no register cap below 255)
     if (nbuf == 2)
-        return cost_dtype == 0 ? launch_one<1, 0, 2, VAR>(d, tb, nd, tiles, err, s)
-                               : launch_one<1, 1, 2, VAR>(d, tb, nd, tiles, err, s);
-    return cost_dtype == 0 ? launch_one<1, 0, 1, VAR>(d, tb, nd, tiles, err, s)
-                           : launch_one<1, 1, 1, VAR>(d, tb, nd, tiles, err, s);
+        return cost_dtype == 0 ? launch_one<1, 0, 2, VAR>(d, tb, nd, tiles, err, sched, cf, s)
+                               : launch_one<1, 1, 2, VAR>(d, tb, nd, tiles, err, sched, cf, s);
+    return cost_dtype == 0 ? launch_one<1, 0, 1, VAR>(d, tb, nd, tiles, err, sched, cf, s)
+                           : launch_one<1, 1, 1, VAR>(d, tb, nd, tiles, err, sched, cf, s);
 }
 
 cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int var, const PassDesc *d, const uint32_t *tb,
-                         int nd, uint32_t tiles, int *err, cudaStream_t s) {
+                         int nd, uint32_t tiles, int *err, uint32_t *sched, int cost_free, cudaStream_t s) {
     if (tiles == 0) return cudaSuccess;
-    if (var == 1) return launch_xpass_t<1>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, s);
-    if (var == 2) return launch_xpass_t<2>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, s);
-    return launch_xpass_t<0>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, s);
+    if (!sched) return cudaErrorInvalidValue;
+    if (var == 1) return launch_xpass_t<1>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, sched, cost_free, s);
+    if (var == 2) return launch_xpass_t<2>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, sched, cost_free, s);
+    return launch_xpass_t<0>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, sched, cost_free, s);
 }
 
 cudaError_t launch_small(const SmallDesc *d, int nd, int cost_dtype, int want_grad, int max_n,

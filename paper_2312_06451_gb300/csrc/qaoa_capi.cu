@@ -85,12 +85,15 @@ struct LaunchRec {
     float iamp0 = 0.f;
     int tc = 0;        // tensor-core product (tensor maps below)
     CUtensorMap tm[4];  // A_hi, A_lo, B_hi, B_lo
+    int sched_idx = -1;  // pass launches: tile counter slot
+    int cost_free = 0;   // pass launches: no descriptor reads the cost
 };
 
 struct Plan {
     uint64_t key = 0;
     bool valid = false;
     std::vector<LaunchRec> launches;
+    int n_sched = 0;  // pass launches (one tile counter each, zeroed per call)
 };
 
 // Global-bit layout of one pass: local bits 0..c-1 are global bits 0..c-1,
@@ -857,6 +860,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         std::vector<CUtensorMap> maps;
         std::map<std::tuple<const void *, int, int, int, int>, size_t> map_index;
         std::vector<std::pair<size_t, int>> xpass_descs;  // (image offset, count)
+        int n_sched = 0;
         auto map_for = [&](const void *basep, int n, int c, int lo, int elsz) -> const void * {
             const auto key = std::make_tuple(basep, n, c, lo, elsz);
             auto it = map_index.find(key);
@@ -957,6 +961,13 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 r.ndesc = (int)steps[s].size();
                 r.tiles = tb.back();
                 r.bytes = bytes;
+                r.sched_idx = n_sched++;
+                {
+                    const uint32_t cost_flags = bwd ? (PF_LAM_FROM_C | PF_PHASE) : (PF_PHASE | PF_E);
+                    r.cost_free = 1;
+                    for (const PassDesc &pd : steps[s])
+                        if (pd.flags & cost_flags) r.cost_free = 0;
+                }
                 char nm[64];
                 const int c0 = steps[s][0].c;
                 snprintf(nm, sizeof(nm), "xpass%s_%s_%s_%s", gk.var == 1 ? "_ma" : (gk.var == 2 ? "_gm" : ""),
@@ -1212,13 +1223,25 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         QG_CUDA(ctx, cudaMemcpyAsync(d_desc, ctx->h_stage, host.size(), cudaMemcpyHostToDevice, ctx->stream),
                 "descriptor upload");
         QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "descriptor upload");
+        if (n_sched > 0) {
+            void *d_sched = nullptr;
+            st = scratch(ctx, "sched", sizeof(uint32_t) * n_sched, &d_sched);
+            if (st) return st;
+        }
         ctx->plan.launches = L;
+        ctx->plan.n_sched = n_sched;
         ctx->plan.key = key;
         ctx->plan.valid = true;
     }
 
     // ---- enqueue
     char *db = static_cast<char *>(ctx->bufs["desc"].p);
+    uint32_t *d_sched = nullptr;
+    if (ctx->plan.n_sched > 0) {
+        d_sched = static_cast<uint32_t *>(ctx->bufs["sched"].p);
+        QG_CUDA(ctx, cudaMemsetAsync(d_sched, 0, sizeof(uint32_t) * ctx->plan.n_sched, ctx->stream),
+                "tile counters clear");
+    }
     const bool prof = ctx->profiling && !capturing(ctx);
     for (const LaunchRec &r : ctx->plan.launches) {
         cudaEvent_t ea = nullptr, eb = nullptr;
@@ -1244,7 +1267,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         case LK_XPASS:
             e = launch_xpass(r.bwd, r.cost_dtype, r.nbuf, r.var, reinterpret_cast<const PassDesc *>(db + r.desc_off),
                              reinterpret_cast<const uint32_t *>(db + r.tb_off), r.ndesc, r.tiles,
-                             ctx->d_err, ctx->stream);
+                             ctx->d_err, d_sched + r.sched_idx, r.cost_free, ctx->stream);
             break;
         case LK_EIG_INIT:
             e = launch_eig_init(r.iX, r.iX_lo, r.ick0, r.ep.M, r.ep.ld, r.ep.nsets, r.ep.cost, r.ep.cost_dtype,
