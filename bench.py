@@ -223,7 +223,7 @@ class Workload:
     copied into the job buffers from a device pool first (a 2p-double copy per
     set, so every step evaluates fresh angles)."""
 
-    def __init__(self, qg, ctx, idx, dev, pool_steps, n_override=None, gemm="fp32", mixer="x"):
+    def __init__(self, qg, ctx, idx, dev, pool_steps, n_override=None, gemm="fp32", mixer="x", eig_cache=None):
         import torch
 
         from qaoa_inputs import BASE_SEED, sk_couplings, uneven_batch_recipe, uniform_angles, workload_instance
@@ -245,7 +245,7 @@ class Workload:
             cost = ctx.cost_precompute("dks", n, edges=w["edges"], k=k, dtype=torch.uint8)
             t0 = time.perf_counter()
             xy = "clique" if mixer == "clique" else "ring"
-            mixer = qg.xy_eigen_mixer(ctx, xy, n, k, precision=gemm)
+            mixer = qg.xy_eigen_mixer(ctx, xy, n, k, precision=gemm, cache_file=eig_cache)
             torch.cuda.synchronize()
             self.precompute_s = time.perf_counter() - t0
             self.eig_mixer = mixer
@@ -538,7 +538,8 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     if args.workload == 6:
         W = GroverWorkload(qg, ctx, dev, args.steps + args.warmup)
     else:
-        W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n, args.gemm, args.mixer)
+        W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n, args.gemm, args.mixer,
+                     args.eig_cache)
     if not args.no_autotune:
         sched = W.autotune()
         if sched:
@@ -741,6 +742,8 @@ def main():
                          "3: 3-regular n=24 p=10, 1024 angle sets; 4: densest 8-subgraph n=16 ring mixer "
                          "(D=12870), 256 angle sets; 5: 512 uneven instances x 4 sets; "
                          "6: Grover mixer on cost degeneracies, densest 6-subgraph n=100")
+    ap.add_argument("--eig-cache", default=None,
+                    help="workload 4: load the mixer's eigendecomposition from this file, or save it there")
     ap.add_argument("--gemm", default="3xtf32", choices=["fp32", "3xtf32"],
                     help="eigenbasis product precision (workload 4): tcgen05 3xTF32 or CUDA-core float32")
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")

@@ -264,14 +264,17 @@ gemm_simt_kernel(const float *__restrict__ A, const float *__restrict__ B, int K
 //
 // 128 x 128 output tile per CTA, STAGES-deep TMA ring of 128-byte-swizzled
 // K-major tiles.  Warp 0 lane 0 issues TMA loads, warp 1 lane 0 the MMAs;
-// warps 2..5 (one per quarter of the accumulator rows) drain the chunks and
-// run the fused epilogue.
+// warps 2..17 drain the chunks and run the fused epilogue, four per quarter
+// of the accumulator rows (a warp reaches only its quarter of tensor memory),
+// 32 columns each.  Four accumulator buffers (all 512 tensor-memory columns)
+// let the MMAs run up to three chunks ahead of the drain.
 namespace tc {
-constexpr int BM = 128, BN = 128, BKF = 32, STAGES = 3, NT = 192;
+constexpr int NACC = 4, NDRAIN = 16;  // accumulator buffers, draining warps
+constexpr int BM = 128, BN = 128, BKF = 32, STAGES = 3, NT = 32 * (2 + NDRAIN);
 constexpr uint32_t kTileA = BM * 128, kTileB = BN * 128;
 constexpr uint32_t kStage = 2 * kTileA + 2 * kTileB;  // A_hi, A_lo, B_hi, B_lo
 constexpr uint32_t kSmem = STAGES * kStage + 1024;      // + alignment slack
-constexpr uint32_t kTmemCols = 256;                     // two 128-column accumulators
+constexpr uint32_t kTmemCols = NACC * BN;               // four 128-column accumulators
 constexpr uint32_t kSpin = 1u << 24;
 // instruction descriptor: D f32, A/B tf32, both K-major, N = 128, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -361,7 +364,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf[2], acce[2];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf[tc::NACC], acce[tc::NACC];
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     __shared__ float red[4][TBN / 2];
@@ -381,9 +384,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
             tc::mbar_init(tc::su32(&full[s]), 1);
             tc::mbar_init(tc::su32(&empty[s]), 1);
         }
-        for (int b = 0; b < 2; b++) {
+        for (int b = 0; b < tc::NACC; b++) {
             tc::mbar_init(tc::su32(&accf[b]), 1);
-            tc::mbar_init(tc::su32(&acce[b]), 4);  // one arrive per draining warp
+            tc::mbar_init(tc::su32(&acce[b]), tc::NDRAIN);  // one arrive per draining warp
         }
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -393,7 +396,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
     tc::fence_after();
     const uint32_t tmem = tmem_base;
     int issued = 0;  // stages the producer has started (for a clean exit on timeout)
-    float acc[TBN];  // drained accumulator row (draining warps)
+    constexpr int kCols = TBN / (tc::NDRAIN / 4);  // accumulator columns per draining warp
+    float acc[kCols];               // its part of one accumulator row
 
     if (warp == 0) {
         if (lane == 0) {
@@ -416,8 +420,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
     } else if (warp == 1) {
         if (lane == 0) {
             for (int kb = 0; kb < nk; kb++) {
-                const int s = kb % STAGES, b = kb & 1;
-                if (kb >= 2 && !tc::mbar_wait(tc::su32(&acce[b]), ((kb >> 1) & 1) ^ 1)) {
+                const int s = kb % STAGES, b = kb % tc::NACC;
+                if (kb >= tc::NACC && !tc::mbar_wait(tc::su32(&acce[b]), ((kb / tc::NACC) & 1) ^ 1)) {
                     atomicExch(&s_fail, 1);
                     break;
                 }
@@ -443,26 +447,28 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
         }
     } else {
         // draining warps: warp w reads accumulator rows (TMEM lanes) 32 (w % 4) ..
+        // and columns kCols * ch .. (ch = which of the quarter's warps)
         const uint32_t lrow = (uint32_t)((warp & 3) * 32) << 16;
+        const int ch = (warp - 2) >> 2;
 #pragma unroll
-        for (int c = 0; c < TBN; c++) acc[c] = 0.f;
+        for (int c = 0; c < kCols; c++) acc[c] = 0.f;
         for (int kb = 0; kb < nk; kb++) {
-            const int b = kb & 1;
-            if (!tc::mbar_wait(tc::su32(&accf[b]), (kb >> 1) & 1)) {
+            const int b = kb % tc::NACC;
+            if (!tc::mbar_wait(tc::su32(&accf[b]), (kb / tc::NACC) & 1)) {
                 atomicExch(&s_fail, 1);
                 break;
             }
             tc::fence_after();
+            {
+                uint32_t r[kCols / 16][16];
 #pragma unroll
-            for (int h = 0; h < TBN; h += 64) {
-                uint32_t r[4][16];
-#pragma unroll
-                for (int q = 0; q < 4; q++) tc::tmem_ld16(tmem + lrow + (uint32_t)(b * TBN + h + 16 * q), r[q]);
+                for (int q = 0; q < kCols / 16; q++)
+                    tc::tmem_ld16(tmem + lrow + (uint32_t)(b * TBN + ch * kCols + 16 * q), r[q]);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < 4; q++)
+                for (int q = 0; q < kCols / 16; q++)
 #pragma unroll
-                    for (int i = 0; i < 16; i++) acc[h + 16 * q + i] += __uint_as_float(r[q][i]);
+                    for (int i = 0; i < 16; i++) acc[16 * q + i] += __uint_as_float(r[q][i]);
             }
             tc::fence_before();
             __syncwarp();
@@ -477,17 +483,18 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
             for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; kb++)
                 tc::mbar_wait(tc::su32(&full[kb % STAGES]), (kb / STAGES) & 1);
     } else if (warp >= 2) {
-        const int rq = warp & 3;
+        const int rq = warp & 3, ch = (warp - 2) >> 2;
         const int m = m0 + rq * 32 + lane;
 #pragma unroll
-        for (int q = 0; q < TBN / 2; q++) {
-            const int s = n0 / 2 + q;
+        for (int q = 0; q < kCols / 2; q++) {
+            const int qq = ch * (kCols / 2) + q;  // set within the tile
+            const int s = n0 / 2 + qq;
             float contrib = 0.f;
             if (m < E.M && s < E.nsets) contrib = epi_elem(E, m, s, make_float2(acc[2 * q], acc[2 * q + 1]));
             if (E.part) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, o);
-                if (lane == 0) red[rq][q] = contrib;
+                if (lane == 0) red[rq][qq] = contrib;
             }
         }
     }
