@@ -230,6 +230,39 @@ def test_batched_uneven_jobs(Q, oracle_mod):
             assert_grad(j["grad"][s].cpu().numpy(), g_ref, c)
 
 
+def test_batched_uneven_sk_gradients_repeat_bitwise(Q, oracle_mod):
+    """Float costs in one batched call over uneven n (13..21 qubits): a step
+    launch mixes descriptors that read the cost (the first adjoint pass of one
+    job, the phase pass of another) with ones that do not, and tiles are
+    claimed dynamically.  Gradients match the oracle, and a repeat of the call
+    gives bitwise the same E and gradients (every partial sum has its slot)."""
+    import paper_2312_06451_gb300 as qg
+
+    p, S = 3, 2
+    jobs, refs = [], []
+    for i, n in enumerate([13, 21, 16, 19, 14]):
+        J = sk_couplings(n, 60 + i)
+        c = oracle_mod.cost_sk(n, J.astype(np.float64))
+        dc = Q.cost_precompute("sk", n, J=J, dtype=torch.float32)
+        A = uniform_angles(p, 70 + i, S)
+        jobs.append({"cost": dc, "mixer": qg.XMixer(n), "angles": torch.from_numpy(A).cuda(),
+                     "E": torch.zeros(S, dtype=torch.float64, device="cuda"),
+                     "grad": torch.zeros(S, 2 * p, dtype=torch.float64, device="cuda")})
+        refs.append((n, c, A))
+    Q.expectation_batched(jobs, want_grad=True)
+    torch.cuda.synchronize()
+    first = [(j["E"].clone(), j["grad"].clone()) for j in jobs]
+    for j, (n, c, A) in zip(jobs, refs):
+        for s in range(S):
+            E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, A[s])
+            assert_E(j["E"][s].item(), E_ref, c)
+            assert_grad(j["grad"][s].cpu().numpy(), g_ref, c)
+    Q.expectation_batched(jobs, want_grad=True)
+    torch.cuda.synchronize()
+    for j, (E0, g0) in zip(jobs, first):
+        assert torch.equal(j["E"], E0) and torch.equal(j["grad"], g0)
+
+
 def test_batched_expectation_only_and_replay(Q, oracle_mod):
     """A repeated identical batched call reuses its plan and gives bitwise
     identical results; new angles in the same buffers are picked up."""
