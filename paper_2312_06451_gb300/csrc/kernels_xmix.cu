@@ -455,15 +455,23 @@ __device__ __forceinline__ bool needs_cost(uint32_t flags) {
     return BWD ? (flags & (PF_LAM_FROM_C | PF_PHASE)) != 0 : (flags & (PF_PHASE | PF_E)) != 0;
 }
 
-// Descriptor of tile t for the loader.  A CTA issues its tiles in
+// Descriptor of tile t for the loader.  A CTA claims its tiles in
 // increasing order, so the search walks forward from the previous answer
-// (`cursor`, warp 0's own) instead of bisecting tile_begin every time.
+// (`cursor`, warp 0's own) for a few descriptors, and bisects when the claim
+// jumped further (small descriptors: a CTA's claims are about a grid apart).
 __device__ __forceinline__ int next_desc(const uint32_t *__restrict__ tile_begin, int ndesc, uint32_t t,
                                          int &cursor) {
     int di = cursor;
-    if (di < 0 || di >= ndesc || t < tile_begin[di]) di = find_desc(tile_begin, ndesc, t);
-    else
-        while (di < ndesc && t >= tile_begin[di + 1]) di++;
+    if (di < 0 || di >= ndesc || t < tile_begin[di]) {
+        di = find_desc(tile_begin, ndesc, t);
+    } else {
+        int steps = 0;
+        while (di < ndesc && t >= tile_begin[di + 1] && steps < 4) {
+            di++;
+            steps++;
+        }
+        if (di < ndesc && t >= tile_begin[di + 1]) di = find_desc(tile_begin, ndesc, t);
+    }
     if (di >= ndesc) di = -1;
     if (di >= 0) cursor = di;
     return di;
