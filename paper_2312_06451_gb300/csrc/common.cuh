@@ -192,10 +192,16 @@ cudaError_t launch_eig_init(float *X, float *X_lo, float *ck0, int D, int ld, in
 cudaError_t launch_eig_gemm_simt(const float *A, const float *B, int Mp, int Np, int Kp, const EigEpiParams &P,
                                  cudaStream_t s);
 // tcgen05 3xTF32 product with the same epilogues; tensor maps (2-d, K-major,
-// 32-float boxes x 128 rows, 128-byte swizzle) of the operand planes.
+// 32-float boxes x 128 rows, 128-byte swizzle) of the operand planes.  The
+// tiles of a last, partial wave may be split along K: d_ws holds
+// eig_split_max_tail() x kEigMaxSeg partial 128 x 128 float tiles and d_cnt
+// eig_split_max_tail() counters, zero before the first product of a call
+// (each product leaves them zero).  d_ws = nullptr: no split.
+constexpr int kEigMaxSeg = 4;
+int eig_split_max_tail();
 cudaError_t launch_eig_gemm_tc(const CUtensorMap &a_hi, const CUtensorMap &a_lo, const CUtensorMap &b_hi,
-                               const CUtensorMap &b_lo, int Mp, int Np, int Kp, const EigEpiParams &P, int *err,
-                               cudaStream_t s);
+                               const CUtensorMap &b_lo, int Mp, int Np, int Kp, const EigEpiParams &P, float *d_ws,
+                               unsigned *d_cnt, int *err, cudaStream_t s);
 constexpr int kEigTile = 128;   // M and N tile of the eigenbasis products
 constexpr int kEigSetTile = 64; // sets per N tile
 

@@ -268,6 +268,14 @@ gemm_simt_kernel(const float *__restrict__ A, const float *__restrict__ B, int K
 // of the accumulator rows (a warp reaches only its quarter of tensor memory),
 // 32 columns each.  Four accumulator buffers (all 512 tensor-memory columns)
 // let the MMAs run up to three chunks ahead of the drain.
+// Split of the last, partial wave of tiles along K (see gemm_tc_kernel).
+struct SplitArgs {
+    int full;       // tiles computed whole, by blocks 0 .. full-1
+    int nseg;       // K segments of each remaining tile (1: none)
+    float *ws;      // [remaining tile][segment][128 x 128] partial accumulators
+    unsigned *cnt;  // [remaining tile] segments finished; zero between products
+};
+
 namespace tc {
 constexpr int NACC = 4, NDRAIN = 16;  // accumulator buffers, draining warps
 constexpr int BM = 128, BN = 128, BKF = 32, STAGES = 3, NT = 32 * (2 + NDRAIN);
@@ -354,7 +362,7 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __global__ void __launch_bounds__(tc::NT, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int Kp, int ntn,
-               EpiArgs E, int *err) {
+               EpiArgs E, SplitArgs SP, int *err) {
     using tc::BKF;
     using tc::kStage;
     using tc::kTileA;
@@ -368,10 +376,22 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     __shared__ float red[4][TBN / 2];
+    __shared__ int s_last;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int mt = blockIdx.x / ntn, nt = blockIdx.x % ntn;
+    // blocks below SP.full take a whole tile; the rest take one K segment of
+    // one of the remaining tiles
+    int tile = blockIdx.x, seg = 0, nsegs = 1;
+    if ((int)blockIdx.x >= SP.full) {
+        const int u = blockIdx.x - SP.full;
+        tile = SP.full + u / SP.nseg;
+        seg = u % SP.nseg;
+        nsegs = SP.nseg;
+    }
+    const int mt = tile / ntn, nt = tile % ntn;
     const int m0 = mt * TBM, n0 = nt * TBN;
-    const int nk = Kp / BKF;
+    const int nk_all = Kp / BKF;
+    const int kb0 = (int)((int64_t)nk_all * seg / nsegs);
+    const int nk = (int)((int64_t)nk_all * (seg + 1) / nsegs) - kb0;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&tmem_base)),
@@ -410,10 +430,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
                 const uint32_t base = tc::su32(smem + s * kStage);
                 const uint32_t fb = tc::su32(&full[s]);
                 tc::mbar_expect(fb, kStage);
-                tc::tma_2d(base, &tmAh, kb * BKF, m0, fb);
-                tc::tma_2d(base + kTileA, &tmAl, kb * BKF, m0, fb);
-                tc::tma_2d(base + 2 * kTileA, &tmBh, kb * BKF, n0, fb);
-                tc::tma_2d(base + 2 * kTileA + kTileB, &tmBl, kb * BKF, n0, fb);
+                const int kx = (kb0 + kb) * BKF;
+                tc::tma_2d(base, &tmAh, kx, m0, fb);
+                tc::tma_2d(base + kTileA, &tmAl, kx, m0, fb);
+                tc::tma_2d(base + 2 * kTileA, &tmBh, kx, n0, fb);
+                tc::tma_2d(base + 2 * kTileA + kTileB, &tmBl, kx, n0, fb);
                 issued = kb + 1;
             }
         }
@@ -476,13 +497,47 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
         }
     }
     __syncwarp();
-    if (__syncthreads_or(s_fail)) {
+    const bool failed = __syncthreads_or(s_fail) != 0;
+    bool do_epi = !failed;
+    if (failed) {
         if (tid == 0) atomicOr(err, DERR_TIMEOUT);
         // let started loads land before the block exits
         if (warp == 0 && lane == 0)
             for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; kb++)
                 tc::mbar_wait(tc::su32(&full[kb % STAGES]), (kb / STAGES) & 1);
-    } else if (warp >= 2) {
+    } else if (nsegs > 1) {
+        // K segment of a split tile: store the partial accumulator; the
+        // segment that finishes last adds all partials in segment order (the
+        // same sum whichever finishes last) and runs the epilogue.  No block
+        // ever waits for another.
+        const int ti = tile - SP.full;
+        float *slots = SP.ws + (size_t)ti * nsegs * (TBM * TBN);
+        const int r = (warp & 3) * 32 + lane, c0 = ((warp - 2) >> 2) * kCols;
+        if (warp >= 2) {
+            float *dst = slots + (size_t)seg * (TBM * TBN) + (size_t)r * TBN + c0;
+#pragma unroll
+            for (int c = 0; c < kCols; c++) dst[c] = acc[c];
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned prev = atomicAdd(&SP.cnt[ti], 1u);
+            s_last = prev == (unsigned)(nsegs - 1) ? 1 : 0;
+            if (s_last) atomicExch(&SP.cnt[ti], 0u);  // ready for the next product
+        }
+        __syncthreads();
+        do_epi = s_last != 0;
+        if (do_epi && warp >= 2) {
+            __threadfence();
+#pragma unroll
+            for (int c = 0; c < kCols; c++) {
+                float v = 0.f;
+                for (int g = 0; g < nsegs; g++) v += __ldcg(slots + (size_t)g * (TBM * TBN) + (size_t)r * TBN + c0 + c);
+                acc[c] = v;
+            }
+        }
+    }
+    if (do_epi && warp >= 2) {
         const int rq = warp & 3, ch = (warp - 2) >> 2;
         const int m = m0 + rq * 32 + lane;
 #pragma unroll
@@ -498,7 +553,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
             }
         }
     }
-    if (E.part && !s_fail) {
+    if (E.part && do_epi) {
         __syncthreads();
         if (tid < TBN / 2) {
             const int s = n0 / 2 + tid;
@@ -606,9 +661,16 @@ cudaError_t launch_eig_gemm_simt(const float *A, const float *B, int Mp, int Np,
     return cudaGetLastError();
 }
 
+int eig_split_max_tail() {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return nsm > 0 ? nsm : 1;
+}
+
 cudaError_t launch_eig_gemm_tc(const CUtensorMap &a_hi, const CUtensorMap &a_lo, const CUtensorMap &b_hi,
-                               const CUtensorMap &b_lo, int Mp, int Np, int Kp, const EigEpiParams &P, int *err,
-                               cudaStream_t s) {
+                               const CUtensorMap &b_lo, int Mp, int Np, int Kp, const EigEpiParams &P, float *d_ws,
+                               unsigned *d_cnt, int *err, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -617,7 +679,26 @@ cudaError_t launch_eig_gemm_tc(const CUtensorMap &a_hi, const CUtensorMap &a_lo,
         attr = true;
     }
     const int ntn = Np / tc::BN;
-    gemm_tc_kernel<<<(Mp / tc::BM) * ntn, tc::NT, tc::kSmem, s>>>(a_hi, a_lo, b_hi, b_lo, Kp, ntn, to_args(P), err);
+    const int tiles = (Mp / tc::BM) * ntn;
+    // One block per SM: with W whole waves and R < nsm tiles left over, the
+    // R tiles run as S K-segments each when that ends sooner, W + ceil(R S /
+    // nsm) / S waves against W + 1 (S = 2..kMaxSeg).
+    const int nsm = eig_split_max_tail();
+    SplitArgs sp{tiles, 1, d_ws, d_cnt};
+    const int W = tiles / nsm, R = tiles - W * nsm;
+    if (d_ws && d_cnt && W >= 1 && R > 0 && R <= eig_split_max_tail()) {
+        double best = 1.0;  // the unsplit tail: one more wave
+        for (int S = 2; S <= kEigMaxSeg; S++) {
+            const double t = (double)((R * S + nsm - 1) / nsm) / S;
+            if (t < best - 1e-9 && Kp / tc::BKF >= 8 * S) {
+                best = t;
+                sp.nseg = S;
+            }
+        }
+        if (sp.nseg > 1) sp.full = W * nsm;
+    }
+    const int grid = sp.full + (tiles - sp.full) * sp.nseg;
+    gemm_tc_kernel<<<grid, tc::NT, tc::kSmem, s>>>(a_hi, a_lo, b_hi, b_lo, Kp, ntn, to_args(P), sp, err);
     return cudaGetLastError();
 }
 

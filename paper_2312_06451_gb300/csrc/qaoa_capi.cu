@@ -94,6 +94,7 @@ struct Plan {
     bool valid = false;
     std::vector<LaunchRec> launches;
     int n_sched = 0;  // pass launches (one tile counter each, zeroed per call)
+    bool eig_tc = false;  // tensor-core eigenbasis products (split-K tail workspace)
 };
 
 // Global-bit layout of one pass: local bits 0..c-1 are global bits 0..c-1,
@@ -238,6 +239,13 @@ bool capturing(qaoa_ctx *ctx) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(ctx->stream, &cs);
     return cs != cudaStreamCaptureStatusNone;
+}
+
+// Split-K tail of the tensor-core eigenbasis products: counters, then the
+// partial tiles (see launch_eig_gemm_tc).
+size_t eig_split_cnt_bytes() { return ((size_t)eig_split_max_tail() * sizeof(unsigned) + 255) / 256 * 256; }
+size_t eig_split_bytes() {
+    return eig_split_cnt_bytes() + (size_t)eig_split_max_tail() * kEigMaxSeg * kEigTile * kEigTile * sizeof(float);
 }
 
 // Device scratch by name; grows (never shrinks) and invalidates the cached
@@ -861,6 +869,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         std::map<std::tuple<const void *, int, int, int, int>, size_t> map_index;
         std::vector<std::pair<size_t, int>> xpass_descs;  // (image offset, count)
         int n_sched = 0;
+        bool any_eig_tc = false;
         auto map_for = [&](const void *basep, int n, int c, int lo, int elsz) -> const void * {
             const auto key = std::make_tuple(basep, n, c, lo, elsz);
             auto it = map_index.find(key);
@@ -1101,6 +1110,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                         r.fam = fam_g;
                         if (tcp) {
                             r.tc = 1;
+                            any_eig_tc = true;
                             const float *Al = A == Vp ? Vpl : Vtpl;
                             map_ok = map_ok && encode_kmajor_map(&r.tm[0], A, ld, ld) &&
                                      encode_kmajor_map(&r.tm[1], Al, ld, ld) &&
@@ -1228,8 +1238,14 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             st = scratch(ctx, "sched", sizeof(uint32_t) * n_sched, &d_sched);
             if (st) return st;
         }
+        if (any_eig_tc) {
+            void *d_split = nullptr;
+            st = scratch(ctx, "eig_split", eig_split_bytes(), &d_split);
+            if (st) return st;
+        }
         ctx->plan.launches = L;
         ctx->plan.n_sched = n_sched;
+        ctx->plan.eig_tc = any_eig_tc;
         ctx->plan.key = key;
         ctx->plan.valid = true;
     }
@@ -1241,6 +1257,14 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         d_sched = static_cast<uint32_t *>(ctx->bufs["sched"].p);
         QG_CUDA(ctx, cudaMemsetAsync(d_sched, 0, sizeof(uint32_t) * ctx->plan.n_sched, ctx->stream),
                 "tile counters clear");
+    }
+    float *d_split_ws = nullptr;
+    unsigned *d_split_cnt = nullptr;
+    if (ctx->plan.eig_tc) {
+        char *b = static_cast<char *>(ctx->bufs["eig_split"].p);
+        d_split_cnt = reinterpret_cast<unsigned *>(b);
+        d_split_ws = reinterpret_cast<float *>(b + eig_split_cnt_bytes());
+        QG_CUDA(ctx, cudaMemsetAsync(d_split_cnt, 0, eig_split_cnt_bytes(), ctx->stream), "split counters clear");
     }
     const bool prof = ctx->profiling && !capturing(ctx);
     for (const LaunchRec &r : ctx->plan.launches) {
@@ -1274,8 +1298,8 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                                 r.ep.coef, r.ep.coef_stride, r.iinit, r.iamp0, ctx->stream);
             break;
         case LK_EIG_GEMM:
-            e = r.tc ? launch_eig_gemm_tc(r.tm[0], r.tm[1], r.tm[2], r.tm[3], r.Mp, r.Np, r.Kp, r.ep, ctx->d_err,
-                                          ctx->stream)
+            e = r.tc ? launch_eig_gemm_tc(r.tm[0], r.tm[1], r.tm[2], r.tm[3], r.Mp, r.Np, r.Kp, r.ep, d_split_ws,
+                                          d_split_cnt, ctx->d_err, ctx->stream)
                      : launch_eig_gemm_simt(r.gA, r.gB, r.Mp, r.Np, r.Kp, r.ep, ctx->stream);
             break;
         case LK_REDUCE:
