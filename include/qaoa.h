@@ -350,8 +350,10 @@ qaoa_status qaoa_grover_batched(qaoa_ctx *ctx, const int64_t *d_counts, int n_bi
  * fixed 256 KiB file-scope device array that every device loading the library
  * keeps until exit; sizes beyond n = 12 or p = 96 are rejected with
  * QAOA_ERR_INVALID.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) once; make that first call before any stream
- * capture.  The call is synchronous on cuda_stream.  All calls share the one
+ * address (cudaGetSymbolAddress) once and keeps it; make that first call
+ * before any stream capture, and do not call the entry point on a device after
+ * cudaDeviceReset there (the array may then sit at another address).  The
+ * caller must pass buffers of the stated sizes: they are not checked.  The call is synchronous on cuda_stream.  All calls share the one
  * array: calls that overlap on the GPU (other threads or streams) race, so
  * serialise them.  No other context or state is needed.  A non-finite angle
  * returns QAOA_ERR_INVALID; a CUDA failure QAOA_ERR_CUDA. */

@@ -472,16 +472,46 @@ def qaoa_gradient_small_noalloc(cost: torch.Tensor, n: int, angles: torch.Tensor
     that allocates no device memory (for callers that cannot allocate: the
     library keeps a fixed device array instead).  angles, E, grad: float64 CUDA
     tensors (2p, 1, 2p); results land in E and grad.  Synchronous."""
+    n, p = _check_noalloc_args(cost, n, angles, E, grad)
     lib = B.load()
-    cost = _dev_tensor(cost, "cost")
-    angles = _dev_tensor(angles, "angles")
-    E = _dev_tensor(E, "E")
-    grad = _dev_tensor(grad, "grad")
-    s = stream if stream is not None else torch.cuda.current_stream(cost.device)
-    st = lib.qaoa_gradient_small_noalloc(_ptr(cost), _cost_dtype(cost), int(n), angles.numel() // 2,
-                                         _ptr(angles), _ptr(E), _ptr(grad), ctypes.c_void_p(s.cuda_stream))
+    with torch.cuda.device(cost.device):
+        s = stream if stream is not None else torch.cuda.current_stream(cost.device)
+        st = lib.qaoa_gradient_small_noalloc(_ptr(cost), _cost_dtype(cost), n, p, _ptr(angles), _ptr(E),
+                                             _ptr(grad), ctypes.c_void_p(s.cuda_stream))
     if st != B.QAOA_OK:
         raise QAOAError(st, "qaoa_gradient_small_noalloc failed")
+
+
+def _check_noalloc_args(cost, n, angles, E, grad):
+    """Shapes, dtypes and devices of a qaoa_gradient_small_noalloc call,
+    checked on the host before anything reaches the device: the C entry point
+    trusts the sizes it is given, so a short or mistyped buffer here would
+    turn into an out-of-bounds device access.  Returns (n, p)."""
+    n = int(n)
+    for name, t in (("cost", cost), ("angles", angles), ("E", E)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+    if grad is not None and not isinstance(grad, torch.Tensor):
+        raise ValueError("grad must be a torch tensor or None")
+    if cost.dtype not in (torch.uint8, torch.float32):
+        raise ValueError(f"cost must be uint8 or float32, got {cost.dtype}")
+    for name, t in (("angles", angles), ("E", E), ("grad", grad)):
+        if t is not None and t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64, got {t.dtype}")
+    if not 1 <= n <= 62 or cost.numel() != 1 << n:
+        raise ValueError(f"cost must hold 2^n = 2^{n} values, has {cost.numel()}")
+    if angles.numel() < 2 or angles.numel() % 2:
+        raise ValueError(f"angles must hold 2p values (p >= 1), has {angles.numel()}")
+    if E.numel() < 1:
+        raise ValueError("E must hold at least one value")
+    if grad is not None and grad.numel() != angles.numel():
+        raise ValueError(f"grad must hold {angles.numel()} values like angles, has {grad.numel()}")
+    for name, t in (("cost", cost), ("angles", angles), ("E", E), ("grad", grad)):
+        if t is not None and not (t.is_cuda and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if t is not None and t.device != cost.device:
+            raise ValueError(f"{name} is on {t.device}, cost on {cost.device}")
+    return n, angles.numel() // 2
 
 
 class QAOAExpectation(torch.autograd.Function):

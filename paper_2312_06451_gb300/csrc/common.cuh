@@ -205,6 +205,25 @@ cudaError_t launch_eig_gemm_tc(const CUtensorMap &a_hi, const CUtensorMap &a_lo,
 constexpr int kEigTile = 128;   // M and N tile of the eigenbasis products
 constexpr int kEigSetTile = 64; // sets per N tile
 
+// --------------------------------------------- per-device launch settings
+// Kernel attributes (the opt-in shared-memory size) belong to one device's
+// context, so each device raises them for itself, the first time a launch on
+// it needs them.  `done` holds one entry per device index: the size set so
+// far.  Concurrent first calls both set the same value, which is harmless.
+constexpr int kMaxDevices = 64;
+
+template <typename Kern>
+cudaError_t smem_attr_once(Kern kern, int bytes, int *done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (__atomic_load_n(&done[dev], __ATOMIC_ACQUIRE) >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) __atomic_store_n(&done[dev], bytes, __ATOMIC_RELEASE);
+    return e;
+}
+
 // ------------------------------------------------------- launch wrappers
 // Each returns the cudaError_t of the launch.
 cudaError_t launch_prep(const PrepDesc *d_descs, int ndesc, int *d_err, cudaStream_t s);

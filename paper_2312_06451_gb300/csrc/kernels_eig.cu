@@ -671,12 +671,10 @@ int eig_split_max_tail() {
 cudaError_t launch_eig_gemm_tc(const CUtensorMap &a_hi, const CUtensorMap &a_lo, const CUtensorMap &b_hi,
                                const CUtensorMap &b_lo, int Mp, int Np, int Kp, const EigEpiParams &P, float *d_ws,
                                unsigned *d_cnt, int *err, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tc::kSmem);
+    static int attr_done[kMaxDevices];
+    {
+        cudaError_t e = smem_attr_once(gemm_tc_kernel, (int)tc::kSmem, attr_done);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int ntn = Np / tc::BN;
     const int tiles = (Mp / tc::BM) * ntn;

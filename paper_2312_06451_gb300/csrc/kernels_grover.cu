@@ -607,12 +607,10 @@ cudaError_t launch_degeneracy(const DegLaunch &L, const uint64_t *d_binom, uint6
     int copies = (96 * 1024) / (4 * L.n_bins);
     copies = std::max(1, std::min(kDegWarps, copies));
     const size_t smem = (size_t)copies * L.n_bins * 4;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(degeneracy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             96 * 1024 + 4 * 4096);
+    static int attr_done[kMaxDevices];
+    {
+        cudaError_t e = smem_attr_once(degeneracy_kernel, 96 * 1024 + 4 * 4096, attr_done);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
@@ -627,12 +625,10 @@ cudaError_t launch_grover_eval(const int64_t *d_counts, int nb, int p, int n_set
                                double *d_E, double *d_grad, cudaStream_t s) {
     const size_t smem = (size_t)(2 * nb + kGrMaxWarps + p) * sizeof(double2) + (size_t)nb * sizeof(double);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(grover_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
+    static int attr_done[kMaxDevices];
+    {
+        cudaError_t e = smem_attr_once(grover_eval_kernel, 200 * 1024, attr_done);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int threads = std::min(kGrMaxThreads, std::max(32, (nb + 31) / 32 * 32));
     grover_eval_kernel<<<n_sets, threads, smem, s>>>(d_counts, nb, p, d_angles, d_E, d_grad);

@@ -1543,17 +1543,23 @@ cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t t
                        int cost_free, cudaStream_t s) {
     using G = PassGeom<BWD, COST>;
     const size_t smem = G::kHead + (size_t)NBUF * G::kBufB + G::kStashB;
-    static int grid_cap = 0;
+    // per device: the shared-memory attribute and the persistent grid size
+    static int attr_done[kMaxDevices];
+    static int grid_caps[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    e = smem_attr_once(xpass_kernel<BWD, COST, NBUF, VAR>, (int)smem, attr_done);
+    if (e != cudaSuccess) return e;
+    int grid_cap = __atomic_load_n(&grid_caps[dev], __ATOMIC_ACQUIRE);
     if (!grid_cap) {
-        cudaError_t e = cudaFuncSetAttribute(xpass_kernel<BWD, COST, NBUF, VAR>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, nsm = 0, per_sm = 0;
-        cudaGetDevice(&dev);
+        int nsm = 0, per_sm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xpass_kernel<BWD, COST, NBUF, VAR>, kNT, smem);
         if (e != cudaSuccess) return e;
         grid_cap = std::max(1, nsm * std::max(1, per_sm));
+        __atomic_store_n(&grid_caps[dev], grid_cap, __ATOMIC_RELEASE);
     }
     const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)grid_cap);
     xpass_kernel<BWD, COST, NBUF, VAR><<<grid, kNT, smem, s>>>(d, tb, nd, tiles, err, sched, cost_free);
@@ -1610,13 +1616,9 @@ cudaError_t launch_small(const SmallDesc *d, int nd, int cost_dtype, int want_gr
     // size any call needs (n <= kSmallMaxN)
     const size_t smem_max = (size_t)2 * (1u << kSmallMaxN) * sizeof(float2) + kPhaseTable * sizeof(float2);
     auto go = [&](auto kern, int slot) -> cudaError_t {
-        static bool attr[4] = {false, false, false, false};
-        if (!attr[slot]) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem_max);
-            if (e != cudaSuccess) return e;
-            attr[slot] = true;
-        }
+        static int attr_done[4][kMaxDevices];
+        cudaError_t e = smem_attr_once(kern, (int)smem_max, attr_done[slot]);
+        if (e != cudaSuccess) return e;
         kern<<<nd, kSmallThreads, smem, s>>>(d, err);
         return cudaGetLastError();
     };
@@ -1628,12 +1630,9 @@ cudaError_t launch_tile12(const SmallDesc *d, int nd, int cost_dtype, int want_g
     const size_t smem = (size_t)2 * kTile * sizeof(float2) + kPhaseTable * sizeof(float2) +
                         (size_t)kTile * (cost_dtype == 0 ? 4 : 1);
     auto go = [&](auto kern, int slot) -> cudaError_t {
-        static bool attr[4] = {false, false, false, false};
-        if (!attr[slot]) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr[slot] = true;
-        }
+        static int attr_done[4][kMaxDevices];
+        cudaError_t e = smem_attr_once(kern, (int)smem, attr_done[slot]);
+        if (e != cudaSuccess) return e;
         kern<<<nd, kNT, smem, s>>>(d, err);
         return cudaGetLastError();
     };

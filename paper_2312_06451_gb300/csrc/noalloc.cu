@@ -37,17 +37,19 @@ static_assert(kOffTable + sizeof(float2) * qg::kPhaseTable * kNoAllocMaxP <= kNo
 static_assert(sizeof(qg::PrepDesc) <= kOffSmall - kOffPrep, "descriptor layout");
 static_assert(sizeof(qg::SmallDesc) <= kOffCoef - kOffSmall, "descriptor layout");
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char *g_dev_ptr[kMaxDevices] = {nullptr};
+unsigned char *g_dev_ptr[qg::kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (the array's name is only a host-side stand-in).
+// per device (the array's name is only a host-side stand-in).  The address is
+// kept for the life of the process: after cudaDeviceReset the module is loaded
+// again and the array may move, so the entry point must not be used after a
+// reset of a device it has already run on.
 cudaError_t scratch_address(unsigned char **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (dev < 0 || dev >= qg::kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_dev_ptr[dev]) {
         void *p = nullptr;
