@@ -105,6 +105,33 @@ def test_weighted_maxcut(oracle_mod):
     assert c.max() <= w.sum() + 1e-12
 
 
+@pytest.mark.parametrize("n,seed", [(5, 21), (9, 22), (12, 23)])
+def test_weighted_maxcut_laplacian_form(oracle_mod, n, seed):
+    """Weighted cut = x^T L x with the weighted graph Laplacian L = D - W
+    (each edge adds w_uv (x_u - x_v)^2), and = (1/2) sum_uv w_uv (1 - z_u z_v)
+    over edges with z = 1 - 2x.  Distinct random weights make any mix-up of
+    weights and edges (a permutation, a transposed pair) change the values;
+    a single set bit cuts exactly the edges at that vertex, its weighted
+    degree."""
+    e = erdos_renyi(n, 0.5, seed)
+    w = np.random.default_rng(seed).uniform(0.1, 3.0, len(e))
+    c = oracle_mod.cost_maxcut(n, e, weights=w)
+    W = np.zeros((n, n))
+    np.add.at(W, (e[:, 0], e[:, 1]), w)
+    np.add.at(W, (e[:, 1], e[:, 0]), w)
+    L = np.diag(W.sum(1)) - W
+    x = bits_matrix(n).astype(np.float64)
+    np.testing.assert_allclose(c, np.einsum("xi,ij,xj->x", x, L, x), rtol=0, atol=1e-12)
+    z = 1 - 2 * x
+    zz = z[:, e[:, 0]] * z[:, e[:, 1]]
+    np.testing.assert_allclose(c, 0.5 * ((1 - zz) @ w), rtol=0, atol=1e-12)
+    for v in range(n):
+        assert c[1 << v] == pytest.approx(W[v].sum(), abs=1e-12)
+    # a permutation of the weights over the edges gives another cost vector
+    perm = np.roll(np.arange(len(e)), 1)
+    assert not np.allclose(oracle_mod.cost_maxcut(n, e, weights=w[perm]), c)
+
+
 @pytest.mark.parametrize("n,seed", [(2, 5), (6, 6), (11, 7)])
 def test_sk_cost_quadratic_form(oracle_mod, n, seed):
     """C = z^T J z / 2 for symmetric zero-diagonal J; mean over all x is 0,
