@@ -188,6 +188,13 @@ def traffic_for(family: str, workload: str):
     return ent.get("dram_bytes_per_launch_full_size")
 
 
+def headline_config(n, p):
+    """Workload description of the headline line (the same for both arms)."""
+    return {"workload": "sk28_p8_grad", "problem": "SK, J_ij~N(0,1) on 2^-20 grid", "n": n, "p": p,
+            "mixer": "X (transverse field)", "angle_sets_per_step": 1, "cost_dtype": "f32",
+            "l2": f"state {2 ** n * 8 / 2 ** 30:.2f} GiB per set vs 129 MB L2; no flush"}
+
+
 # ------------------------------------------------------------- CPU oracle
 
 def oracle_sample(threads: int | None = None):
@@ -266,9 +273,13 @@ class Workload:
                 A = uniform_angles(p, BASE_SEED + 5 + 1000 + i, spec["n_sets"] * pool_steps)
                 self._add_job(cost, n, A, spec["n_sets"])
             self.name = spec["name"]
+            self.inst = inst
             self.config = {"workload": spec["name"], "problem": "MaxCut, 3-regular (even i) / G(n,0.3) (odd i)",
                            "instances": len(inst), "n_range": [14, 22], "p": p, "angle_sets_per_instance":
-                           spec["n_sets"], "mixer": "X", "cost_dtype": "u8"}
+                           spec["n_sets"], "mixer": "X", "cost_dtype": "u8",
+                           "amplitudes_per_step": int(sum(spec["n_sets"] << it["n"] for it in inst)),
+                           "l2": "each step evaluates all 2048 angle sets, states of 15 GB in all vs 129 MB "
+                                 "L2; no flush"}
             self.units = len(inst) * spec["n_sets"]
         else:
             w = workload_instance(idx, n_sets=spec["n_sets"] * pool_steps)
@@ -306,13 +317,14 @@ class Workload:
                            "cost_dtype": "f32" if spec["problem"] == "sk" else "u8"}
             self.config["l2"] = (f"state {2 ** n * 8 / 2 ** 30:.2f} GiB per set vs 129 MB L2; no flush"
                                  if n >= 24 else "on-chip state (whole state in shared memory)")
-        self.config["state"] = "complex64"
+        # how this implementation runs the workload (not part of the workload)
+        self.run_info = {"state": "complex64"}
         if not self.grad:
-            self.config["ckpt"] = "none (forward only)"
+            self.run_info["ckpt"] = "none (forward only)"
         elif idx == 4:
-            self.config["ckpt"] = "per-round state checkpoints"
+            self.run_info["ckpt"] = "per-round state checkpoints"
         else:
-            self.config["ckpt"] = "per-pass state checkpoints (the adjoint writes lambda only)"
+            self.run_info["ckpt"] = "per-pass state checkpoints (the adjoint writes lambda only)"
 
     def autotune(self):
         """Pick the pass schedule of every X-mixer problem size in the workload
@@ -367,9 +379,11 @@ class Workload:
 
     def oracle_baseline(self):
         """Time the CPU oracle on a bounded sample of this workload; returns
-        (units/s, cores, description)."""
+        (units/s, cores, description, extra).  extra may carry more baseline
+        fields ("baseline") and, where the sample's results can be compared
+        with the GPU's, the error record ("oracle_error")."""
         import oracle
-        from qaoa_inputs import BASE_SEED, sk_couplings, uneven_batch_recipe, workload_instance
+        from qaoa_inputs import BASE_SEED, sk_couplings, workload_instance
 
         oracle.build()
         p = self.p
@@ -380,16 +394,43 @@ class Workload:
             cost = oracle.cost_sk(n, J.astype(np.float64))
             a = self.pools[0][3][0]
             var = getattr(self, "mixer_variant", "x")
+
+            def one_round(nn, cc):
+                if var == "ma":
+                    oracle.qaoa_gradient_ma(nn, cc, np.concatenate([a[:nn], a[p * nn:p * nn + 1]]))
+                elif var in ("terms", "grover"):
+                    w_ = self.x_mixer.weights.cpu().numpy() if nn == n else None
+                    if w_ is None:
+                        return None
+                    oracle.qaoa_gradient_general(nn, w_, cc, np.array([a[0], a[p]]))
+                else:
+                    oracle.qaoa_gradient(nn, cc, np.array([a[0], a[p]]))
+                return True
+
             t = time.perf_counter()
-            if var == "ma":
-                oracle.qaoa_gradient_ma(n, cost, np.concatenate([a[:n], a[p * n:p * n + 1]]))
-            elif var in ("terms", "grover"):
-                oracle.qaoa_gradient_general(n, self.x_mixer.weights.cpu().numpy(), cost, np.array([a[0], a[p]]))
-            else:
-                oracle.qaoa_gradient(n, cost, np.array([a[0], a[p]]))
+            one_round(n, cost)
             dt = (time.perf_counter() - t) * p
-            return 1.0 / dt, oracle.get_threads(), (f"oracle gradient of one round (p=1) at n={n}, "
-                                                     f"scaled x{p} to the p={p} unit")
+            cores = oracle.get_threads()
+            del cost
+            extra = {}
+            if var == "x" and n >= 25:
+                # one thread, on one round at n - 3 (an eighth of the state),
+                # scaled by the mixer's n 2^n work to the full unit
+                n1 = n - 3
+                c1 = oracle.cost_sk(n1, sk_couplings(n1, BASE_SEED + 2).astype(np.float64))
+                oracle.set_threads(1)
+                try:
+                    t = time.perf_counter()
+                    one_round(n1, c1)
+                    dt1 = (time.perf_counter() - t) * p * (n * 2.0 ** n) / (n1 * 2.0 ** n1)
+                finally:
+                    oracle.set_threads(cores)
+                extra["baseline"] = {"single_thread": {
+                    "value": 1.0 / dt1, "unit": UNIT, "cores": 1,
+                    "sample": f"oracle gradient of one round (p=1) at n={n1} on one thread, scaled x{p} rounds "
+                              f"and x{(n * 2.0 ** n) / (n1 * 2.0 ** n1):.2f} (n 2^n work) to the n={n}, p={p} unit"}}
+            return 1.0 / dt, cores, (f"oracle gradient of one round (p=1) at n={n}, scaled x{p} to the p={p} "
+                                     f"unit"), extra
         if self.idx == 4:
             w = workload_instance(4, n_sets=1)
             n, k = 16, 8
@@ -400,7 +441,7 @@ class Workload:
             oracle.qaoa_gradient(n, cost, np.array([a[0], a[p]]), self.xy, st)
             dt = (time.perf_counter() - t) * p
             return 1.0 / dt, oracle.get_threads(), (f"oracle gradient of one round (p=1) of one angle set, "
-                                                     f"power-series {self.xy} mixer on D={len(st)}, scaled x{p}")
+                                                     f"power-series {self.xy} mixer on D={len(st)}, scaled x{p}"), {}
         if self.idx in (1, 3):
             w = workload_instance(self.idx, n_sets=2)
             n = self.pools[0][2]
@@ -414,14 +455,36 @@ class Workload:
                 else:
                     oracle.qaoa_expectation(n, cost, a)
             return k / (time.perf_counter() - t), oracle.get_threads(), (
-                f"oracle on {k} of the workload's angle sets at n={n}, scaled per set")
-        inst = uneven_batch_recipe(512, BASE_SEED + 5)[:16]
-        t = time.perf_counter()
-        for it in inst:
+                f"oracle on {k} of the workload's angle sets at n={n}, scaled per set"), {}
+        # uneven batch: the first angle set of 16 of the 512 instances, timed;
+        # their results are compared with the GPU's for the same angles
+        import torch
+
+        n_s = 16
+        res, t_tot = [], 0.0
+        for i in range(n_s):
+            it = self.inst[i]
             c = oracle.cost_maxcut(it["n"], it["edges"])
-            oracle.qaoa_gradient(it["n"], c, self.pools[0][3][0])
-        return 16 / (time.perf_counter() - t), oracle.get_threads(), (
-            "oracle gradient of 16 of the 512 instances (one angle set each), scaled per set")
+            a = self.pools[i][3][0]
+            t = time.perf_counter()
+            E, g = oracle.qaoa_gradient(it["n"], c, a)
+            t_tot += time.perf_counter() - t
+            res.append((E, g, float(np.sqrt(np.mean(c ** 2)))))
+        self.load_angles(0)
+        self.run()
+        torch.cuda.synchronize()
+        worst_E, worst_g = 0.0, 0.0
+        for i, (E, g, sig) in enumerate(res):
+            Eg = float(self.jobs[i]["E"][0].item())
+            gg = self.jobs[i]["grad"][0].cpu().numpy()
+            worst_E = max(worst_E, abs(Eg - E) / max(abs(E), sig))
+            worst_g = max(worst_g, float(np.max(np.abs(gg - g)) / np.max(np.abs(g))))
+        err = {"reference": "CPU oracle (complex128, exact reverse mode), run here",
+               "sets": f"first angle set of instances 0..{n_s - 1} (n = "
+                       f"{sorted({self.inst[i]['n'] for i in range(n_s)})})",
+               "max_abs_dE_over_max_absE_sigmaC": worst_E, "max_abs_dg_over_max_abs_g": worst_g}
+        return n_s / t_tot, oracle.get_threads(), (
+            f"oracle gradient of the first angle set of {n_s} of the 512 instances, per set"), {"oracle_error": err}
 
 
 class GroverWorkload:
@@ -451,6 +514,7 @@ class GroverWorkload:
         self.E, self.G = ctx.grover_batched(self.counts, self.angles)
         self.jobs = [{"E": self.E}]
         self.deg_ms = []
+        self.run_info = {}
         self.config = {"workload": self.name, "problem": "densest k-subgraph, G(100,0.5), weight-6 subsets",
                        "n": self.n, "k": self.k, "feasible_states": self.units, "p": self.p,
                        "mixer": "Grover, on cost degeneracies", "angle_sets_per_step": self.S,
@@ -508,7 +572,7 @@ class GroverWorkload:
         dt = time.perf_counter() - t
         return math.comb(self.n, 3) / dt, 1, (f"oracle brute-force degeneracy count of all weight-3 subsets "
                                               f"of the same graph ({math.comb(self.n, 3)} states, numpy on one "
-                                              f"core), per state")
+                                              f"core), per state"), {}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -540,35 +604,77 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     else:
         W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n, args.gemm, args.mixer,
                      args.eig_cache)
+    out = measure(args, W, qg, ctx, stream, dist, ws, rank, local, dev, graph_mode=args.graph,
+                  steps=args.steps, warmup=args.warmup)
+    headline = args.workload == WORKLOAD and not args.n and args.mixer == "x"
+    if rank == 0 and out is not None:
+        out["metric"] = METRIC if headline else f"QAOA {out['unit']} ({W.name})"
+        if headline:
+            err = oracle_error_golden(W)
+            if err is not None:
+                out["oracle_error"] = err
+    del W
+    ctx.close()
+    if headline and not args.no_batched:
+        # the batched half of the metric: the uneven angle-finding batch
+        # (512 instances, n = 14..22, 4 angle sets each, p = 6), every step
+        # replayed from one captured CUDA graph, in a context of its own
+        torch.cuda.empty_cache()
+        ctx5 = qg.Context(local, stream)
+        W5 = Workload(qg, ctx5, 5, dev, args.steps + args.warmup)
+        b = measure(args, W5, qg, ctx5, stream, dist, ws, rank, local, dev, graph_mode=True,
+                    steps=args.steps, warmup=args.warmup)
+        if rank == 0 and b is not None:
+            b["metric"] = f"QAOA {b['unit']} ({W5.name})"
+            out["batched"] = b
+        del W5
+        ctx5.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def measure(args, W, qg, ctx, stream, dist, ws, rank, local, dev, graph_mode, steps, warmup):
+    """Time `steps` steps of workload W after `warmup` untimed ones.
+
+    value: CUDA events on the library's stream around the steps, with no
+    per-kernel events inside (graph replay when graph_mode).  Per-kernel
+    family times for the roofline come from a separate repeat of the same
+    steps as direct launches, each bracketed by CUDA events.  e2e: the same
+    steps end to end from pinned host angles to host results."""
+    import torch
+
     if not args.no_autotune:
         sched = W.autotune()
         if sched:
-            W.config["schedule"] = sched if len(sched) > 1 else next(iter(sched.values()))
+            W.run_info["schedule"] = sched if len(sched) > 1 else next(iter(sched.values()))
 
-    graph = None
-    if args.graph:
+    graph, launches_per_step = None, None
+    if graph_mode:
         # capture one step (angle copies + batched call) after a plan-building call
         W.load_angles(0)
         W.run()
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
+        l0 = ctx.launch_count()
         with torch.cuda.graph(graph, stream=stream):
             W.run()
+        launches_per_step = ctx.launch_count() - l0
 
-    def step(i):
+    def step(i, replay=True):
         W.load_angles(i)
-        if graph is not None:
+        if graph is not None and replay:
             graph.replay()
         else:
             W.run()
 
-    for i in range(args.warmup):
+    for i in range(warmup):
         step(i)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ctx.reset_stats()
-    ctx.set_profiling(graph is None)
+    ctx.set_profiling(False)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -576,22 +682,33 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     l0 = ctx.launch_count()
     torch.cuda.synchronize()
     e0.record(stream)
-    for i in range(args.steps):
-        step(args.warmup + i)
+    for i in range(steps):
+        step(warmup + i)
     e1.record(stream)
     torch.cuda.synchronize()
-    launches = ctx.launch_count() - l0
-    if graph is not None:  # the library counted one step's launches at capture
-        launches = None
+    launches = launches_per_step * steps if graph is not None else ctx.launch_count() - l0
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    ctx.set_profiling(False)
-    stats = ctx.kernel_stats()
     clk = clocks.stop()
 
+    # per-family kernel times: the same steps again, direct launches, each
+    # launch bracketed by CUDA events on the library's stream
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    p0.record(stream)
+    for i in range(steps):
+        step(warmup + i, replay=False)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ctx.set_profiling(False)
+    prof_ms = p0.elapsed_time(p1)
+    stats = ctx.kernel_stats()
+
     rmax, rsum = reducers(dist, dev)
-    value, tmax, units = aggregate(ms / 1e3, args.steps * W.units, ws, rmax, rsum)
+    value, tmax, units = aggregate(ms / 1e3, steps * W.units, ws, rmax, rsum)
     E_last = float(W.jobs[0]["E"][0].item())
 
     # end to end through the public API: host angles from pinned memory copied
@@ -603,31 +720,89 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    for i in range(args.steps):
-        outs = W.e2e_step(args.warmup + i, pinned)
+    for i in range(steps):
+        outs = W.e2e_step(warmup + i, pinned)
     torch.cuda.synchronize()
     e2e_s = rmax(time.perf_counter() - t0)
-    e2e_value = rsum(args.steps * W.units) / e2e_s
+    e2e_value = rsum(steps * W.units) / e2e_s
 
     fd = None
-    if W.grad and ws == 1 and not args.no_fd and args.workload != 6 and args.mixer in ("x", "clique"):
+    if W.grad and ws == 1 and not args.no_fd and W.idx != 6 and getattr(W, "mixer_variant", "x") in ("x", "clique"):
         fd = fd_compare(W, stream, value)
 
+    roof = roofline(W, stats, args.gemm if W.idx == 4 else None, steps)
+    unit = UNIT if W.grad else "evals/s"
+    if W.idx == 6:
+        unit = "states/s"
+    out = None
+    if rank == 0:
+        cfg = dict(W.config)
+        cfg.update({"units_per_step_per_rank": W.units, "parallelism": f"replicas x{ws}"})
+        run = dict(W.run_info)
+        run.update({"timing": "CUDA graph replay" if graph is not None else "direct launches",
+                    "kernel_times": "a second run of the same steps, direct launches, one CUDA event pair "
+                                    "per launch on the library's stream",
+                    "profiled_ms_per_step": prof_ms / steps})
+        out = {
+            "metric": None, "value": value, "unit": unit, "n_gpus": ws, "steps": steps,
+            "warmup": warmup, "ms_per_step": tmax * 1e3 / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": cfg, "run": run,
+            "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": W.h2d_bytes(),
+                    "d2h_bytes_per_step": W.d2h_bytes()},
+            "roofline": roof,
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 4),
+                            "GBps": round(v["algo_bytes"] / v["total_ms"] / 1e6, 1) if v["total_ms"] else None}
+                        for k, v in stats.items() if v["launches"]},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "result_check": {"E_first_set_last_step": E_last, "e2e_E0": float(outs[0][0])},
+        }
+        if fd is not None:
+            out["fd_baseline"] = fd
+        if ws == 1 and not args.no_cpu_baseline:
+            v, cores, desc, extra = W.oracle_baseline()
+            out["cpu_baseline"] = {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": desc}
+            out["cpu_baseline"].update(extra.get("baseline", {}))
+            if "oracle_error" in extra:
+                out["oracle_error"] = extra["oracle_error"]
+    return out
+
+
+def roofline(W, stats, gemm, steps):
+    """Roofline of the dominant kernel family (most device time): its
+    algorithmic bytes (or useful flops) per launch over its average launch
+    time from the profiled steps."""
     peaks = measured_peaks()
-    roof = None
     fams = [k for k in stats if stats[k]["launches"] and stats[k]["total_ms"] > 0]
-    if fams and stats[max(fams, key=lambda k: stats[k]["total_ms"])]["algo_flops"] > 0:
-        fam = max(fams, key=lambda k: stats[k]["total_ms"])
-        st = stats[fam]
+    roof = None
+    if W.idx == 6:
+        # integer enumeration: the bound is the SM's bit-count unit (16
+        # 32-bit population counts a clock per SM).  The bit-sliced count
+        # takes, per (k-1)-set T, one 64-bit population count (2 x 32-bit)
+        # per plane combination 1..k-1 (the swept vertices v < w lie in the
+        # low word for all but 0.5% of the T), and T covers (n-k+1)/k
+        # states on average: 2k(k-1)/(n-k+1) counts per state.
+        dms = W.degeneracy_ms(steps)
+        ops = 2 * W.k * (W.k - 1) / (W.n - W.k + 1)
+        achieved = W.units / (dms * 1e-3) / 1e9
+        peak = 152 * 16 * 2.07e9 / ops / 1e9
+        return {"bound": "alu", "kernel": "degeneracy_sliced_kernel", "achieved": achieved, "peak": peak,
+                "unit": "Gstates/s", "frac": achieved / peak,
+                "peak_source": f"derived: 152 SM x 16 bit-count ops/clk x 2.07 GHz / {ops:.3f} counts per state",
+                "traffic": None, "launch_ms": dms}
+    if not fams:
+        return None
+    fam = max(fams, key=lambda k: stats[k]["total_ms"])
+    st = stats[fam]
+    if st["algo_flops"] > 0:
         achieved = st["algo_flops"] / (st["total_ms"] * 1e-3) / 1e12
-        pk = gemm_peak(args.gemm)
+        pk = gemm_peak(gemm or "3xtf32")
         roof = {"bound": pk["bound"], "kernel": fam, "achieved": achieved, "peak": pk["peak"], "unit": "TFLOP/s",
                 "frac": achieved / pk["peak"], "peak_source": pk["source"], "traffic": traffic_for(fam, W.name),
                 "algo_flops_per_launch": st["algo_flops"] / st["launches"],
                 "launch_ms": st["total_ms"] / st["launches"]}
-    elif fams:
-        fam = max(fams, key=lambda k: stats[k]["total_ms"])
-        st = stats[fam]
+    else:
         per_launch_bytes = st["algo_bytes"] / st["launches"]
         per_launch_ms = st["total_ms"] / st["launches"]
         achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
@@ -635,55 +810,44 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
                 "traffic": traffic_for(fam, W.name), "algo_bytes_per_launch": per_launch_bytes,
                 "launch_ms": per_launch_ms}
-    if args.workload == 6:
-        # integer enumeration: the bound is the SM's bit-count unit (16
-        # 32-bit population counts a clock per SM).  The bit-sliced count
-        # takes, per (k-1)-set T, one 64-bit population count (2 x 32-bit)
-        # per plane combination 1..k-1 (the swept vertices v < w lie in the
-        # low word for all but 0.5% of the T), and T covers (n-k+1)/k
-        # states on average: 2k(k-1)/(n-k+1) counts per state.
-        dms = W.degeneracy_ms(args.steps)
-        ops = 2 * W.k * (W.k - 1) / (W.n - W.k + 1)
-        achieved = W.units / (dms * 1e-3) / 1e9
-        peak = 152 * 16 * 2.07e9 / ops / 1e9
-        roof = {"bound": "alu", "kernel": "degeneracy_sliced_kernel", "achieved": achieved, "peak": peak,
-                "unit": "Gstates/s", "frac": achieved / peak,
-                "peak_source": f"derived: 152 SM x 16 bit-count ops/clk x 2.07 GHz / {ops:.3f} counts per state",
-                "traffic": None, "launch_ms": dms}
-    unit = UNIT if W.grad else "evals/s"
-    if args.workload == 6:
-        unit = "states/s"
-    out = None
-    if rank == 0:
-        cfg = dict(W.config)
-        cfg.update({"units_per_step_per_rank": W.units, "parallelism": f"replicas x{ws}",
-                    "timing": "CUDA graph replay" if graph is not None else "direct launches"})
-        out = {
-            "metric": METRIC if args.workload == 2 and not args.n and args.mixer == "x" else f"QAOA {unit} ({W.name})",
-            "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": cfg,
-            "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": W.h2d_bytes(),
-                    "d2h_bytes_per_step": W.d2h_bytes()},
-            "roofline": roof,
-            "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 4),
-                            "GBps": round(v["algo_bytes"] / v["total_ms"] / 1e6, 1) if v["total_ms"] else None}
-                        for k, v in stats.items() if v["launches"]},
-            "gpu_launches": launches if launches is not None else "graph",
-            "clocks": clk,
-            "result_check": {"E_first_set_last_step": E_last, "e2e_E0": float(outs[0][0])},
-        }
-        if fd is not None:
-            out["fd_baseline"] = fd
-        if ws == 1 and not args.no_cpu_baseline:
-            v, cores, desc = W.oracle_baseline()
-            out["cpu_baseline"] = {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": desc}
-    ctx.close()
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
-    return out
+    tot = sum(stats[k]["total_ms"] for k in fams)
+    roof["share_of_kernel_time"] = st["total_ms"] / tot if tot else None
+    return roof
+
+
+def oracle_error_golden(W):
+    """Error of the timed path against the CPU oracle (complex128) on the
+    stored oracle values of the headline workload: the first angle set of the
+    timed pool and a linear-ramp schedule where |<C>| is several sigma_C.
+    Runs the same batched call as the timed steps, outside the timed region."""
+    import torch
+
+    path = os.path.join(ROOT, "tests", "golden", "oracle_fullsize.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        gold = json.load(f)["workloads"]
+    job = W.jobs[0]
+    rows = []
+    for key, label in (("2", "first angle set of the timed pool (U[0, pi))"),
+                       ("2ramp", "linear ramp beta_k = 0.6 (1 - t_k), gamma_k = -0.12 t_k")):
+        g = gold.get(key)
+        if g is None:
+            continue
+        job["angles"][0].copy_(torch.tensor(g["angles"], dtype=torch.float64))
+        W.run()
+        torch.cuda.synchronize()
+        E = float(job["E"][0].item())
+        G = job["grad"][0].cpu().numpy()
+        gref = np.array(g["grad"])
+        sig = g["cost_rms"]
+        rows.append({"set": label, "E_oracle": g["E"], "E_gpu": E, "abs_dE": abs(E - g["E"]),
+                     "abs_dE_over_sigma_C": abs(E - g["E"]) / sig,
+                     "rel_dE": abs(E - g["E"]) / abs(g["E"]) if g["E"] else None,
+                     "max_abs_dg_over_max_abs_g": float(np.max(np.abs(G - gref)) / np.max(np.abs(gref))),
+                     "max_rel_dg_per_component": float(np.max(np.abs(G - gref) / np.abs(gref)))})
+    return {"reference": "tests/golden/oracle_fullsize.json (CPU oracle, complex128, exact reverse mode)",
+            "sets": rows, "sigma_C": gold["2"]["cost_rms"]}
 
 
 def fd_compare(W, stream, adjoint_value, h=1e-3, reps=3, max_jobs=8):
@@ -752,6 +916,8 @@ def main():
                          "workload 4: clique instead of ring XY mixer")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default X-mixer pass schedule instead of tuning it before the warm-up")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default workload only: skip the batched sub-record (uneven 512-instance batch)")
     ap.add_argument("--no-fd", action="store_true",
                     help="skip the central finite-difference comparison on the same GPU")
     args = ap.parse_args()
@@ -767,14 +933,18 @@ def main():
         for _ in range(args.warmup):
             run()
         ts = [run() for _ in range(args.steps)]
-        t_round = sum(ts) / len(ts)
-        value = 1.0 / (t_round * p)
+        t_unit = sum(ts) / len(ts) * p  # one round timed, p rounds per gradient
+        value = 1.0 / t_unit
+        cfg = headline_config(n, p)
+        cfg.update({"units_per_step_per_rank": 1, "parallelism": f"replicas x{ws}"})
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_round * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_unit * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "sk28_p8_grad", "n": n, "p": p, "parallelism": "host cores"},
+            "data": "synthetic", "config": cfg,
+            "run": {"state": "complex128", "timing": "host wall clock per step",
+                    "step": f"one round (p=1) of the n={n} gradient, timed; ms_per_step and value are per "
+                            f"p={p} gradient (x{p})"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"each step: oracle gradient of one round (p=1) at n={n}, "
                                        f"scaled x{p} to the p={p} unit"},

@@ -8,6 +8,7 @@ no mixers), so that the oracle and the GPU implementation stay independent.
 from .generators import (  # noqa: F401
     BASE_SEED,
     erdos_renyi,
+    ramp_angles,
     random_regular3,
     sk_couplings,
     uniform_angles,

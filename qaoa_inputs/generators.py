@@ -90,6 +90,17 @@ def uniform_angles(p: int, seed: int, n_sets: int = 1, high: float = np.pi) -> n
     return rng.random((n_sets, 2 * p)) * high
 
 
+def ramp_angles(p: int, beta0: float = 0.6, gamma1: float = -0.12) -> np.ndarray:
+    """One deterministic annealing-like schedule (the kind of smooth angle
+    pattern the paper's angle-finding discussion starts from, Sec. 2.3):
+    beta_k = beta0 (1 - t_k), gamma_k = gamma1 t_k with t_k = (k - 1/2) / p.
+    Unlike uniform random angles it drives <C> far from the uniform mean, so
+    a relative error bound on <C> is tested at |<C>| of several sigma_C.
+    Returns float64 (1, 2p)."""
+    t = (np.arange(p) + 0.5) / p
+    return np.concatenate([beta0 * (1.0 - t), gamma1 * t])[None, :].astype(np.float64)
+
+
 def uniform_angles_ma(p: int, n: int, seed: int, n_sets: int = 1, high: float = np.pi) -> np.ndarray:
     """Multi-angle sets: n_sets vectors of p (n + 1) entries ~ U[0, high)
     (p rounds of n per-qubit betas, then p gammas), float64."""

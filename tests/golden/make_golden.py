@@ -19,7 +19,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 import oracle  # noqa: E402
-from qaoa_inputs import workload_instance  # noqa: E402
+from qaoa_inputs import ramp_angles, workload_instance  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_fullsize.json")
 
@@ -32,6 +32,10 @@ def main():
             res = json.load(f)
     if "4" not in res["workloads"]:
         workload4(res)
+        with open(OUT, "w") as f:
+            json.dump(res, f, indent=1)
+    if "2ramp" not in res["workloads"]:
+        workload2_ramp(res)
         with open(OUT, "w") as f:
             json.dump(res, f, indent=1)
     if "2" in res["workloads"] and "3" in res["workloads"]:
@@ -70,6 +74,23 @@ def main():
     print("workload 3 done", res["workloads"]["3"]["oracle_seconds"])
     with open(OUT, "w") as f:
         json.dump(res, f, indent=1)
+
+
+def workload2_ramp(res):
+    """SK n=28, p=8 on a linear-ramp schedule (ramp_angles), where <C> sits
+    several sigma_C from the mean: E and the gradient."""
+    w = workload_instance(2)
+    n, p = w["spec"]["n"], w["spec"]["p"]
+    a = ramp_angles(p)[0]
+    t = time.time()
+    cost = oracle.cost_sk(n, w["J"].astype(np.float64))
+    E, g = oracle.qaoa_gradient(n, cost, a)
+    res["workloads"]["2ramp"] = {
+        "name": w["spec"]["name"] + "_ramp", "n": n, "p": p, "angles": a.tolist(), "E": E, "grad": g.tolist(),
+        "cost_rms": float(np.sqrt(np.mean(cost ** 2))), "oracle_seconds": time.time() - t,
+        "oracle_threads": oracle.get_threads(),
+    }
+    print("workload 2 ramp done", res["workloads"]["2ramp"]["oracle_seconds"], E)
 
 
 def workload4(res):

@@ -62,7 +62,7 @@ def test_sk28_p8_gradient_full_size(Q, golden):
     sig = g["cost_rms"]
     E, G = batched_grad(qg, ctx, cost, n, np.array(g["angles"]))
     assert abs(E[0] - g["E"]) <= 1e-5 * max(abs(g["E"]), sig), (E[0], g["E"])
-    tol = 1e-4 * max(np.abs(g["grad"]).max(), sig)
+    tol = 1e-4 * np.abs(g["grad"]).max()
     np.testing.assert_allclose(G[0], g["grad"], rtol=0, atol=tol)
     # the host-pointer entry point without checkpoints (states recovered by undoing rounds)
     E2, G2 = ctx.gradient(cost, qg.XMixer(n), np.array(g["angles"]), ckpt=False)
@@ -83,6 +83,21 @@ def test_sk28_p8_gradient_full_size(Q, golden):
         Ef, _ = batched_grad(qg, ctx, cost, n, A, want_grad=False)
         fd = (Ef[0] - Ef[1]) / (2 * h)
         assert abs(fd - G[0][j]) <= 2e-3 * max(np.abs(g["grad"]).max(), sig), (j, fd, G[0][j], g["grad"][j])
+
+
+def test_sk28_p8_ramp_schedule_full_size(Q, golden):
+    """SK n=28, p=8 on a linear-ramp schedule where <C> lies about three
+    sigma_C below the mean, so the 1e-5 bound on <C> is relative to |<C>|
+    itself; every derivative within 1e-4 of the largest one."""
+    qg, ctx = Q
+    g = golden["2ramp"]
+    w = workload_instance(2)
+    n = w["spec"]["n"]
+    cost = ctx.cost_precompute("sk", n, J=w["J"], dtype=torch.float32)
+    assert abs(g["E"]) > g["cost_rms"]
+    E, G = batched_grad(qg, ctx, cost, n, np.array(g["angles"]))
+    assert abs(E[0] - g["E"]) <= 1e-5 * abs(g["E"]), (E[0], g["E"])
+    np.testing.assert_allclose(G[0], g["grad"], rtol=0, atol=1e-4 * np.abs(g["grad"]).max())
 
 
 def test_maxcut_3reg24_p10_batched(Q, golden):
@@ -108,7 +123,7 @@ def test_maxcut_3reg24_p10_batched(Q, golden):
     for s in range(2):
         ref = g["sets"][s]
         assert abs(E[s] - ref["E"]) <= 1e-5 * max(abs(ref["E"]), sig)
-        np.testing.assert_allclose(G[s], ref["grad"], rtol=0, atol=1e-4 * max(np.abs(ref["grad"]).max(), sig))
+        np.testing.assert_allclose(G[s], ref["grad"], rtol=0, atol=1e-4 * np.abs(ref["grad"]).max())
 
 
 def test_maxcut_er12_p3_forward(Q):
@@ -153,7 +168,7 @@ def test_uneven_batch_sample(Q):
             E_ref, g_ref = oracle.qaoa_gradient(n, c, A[s])
             assert abs(j["E"][s].item() - E_ref) <= 1e-5 * max(abs(E_ref), sig)
             np.testing.assert_allclose(j["grad"][s].cpu().numpy(), g_ref, rtol=0,
-                                       atol=1e-4 * max(np.abs(g_ref).max(), sig))
+                                       atol=1e-4 * np.abs(g_ref).max())
 
 
 @pytest.mark.parametrize("precision", ["fp32", "3xtf32"])
@@ -180,7 +195,7 @@ def test_dks16_k8_ring_p6_full_size(Q, golden, precision):
         ref = g["sets"][s]
         assert abs(E[s].item() - ref["E"]) <= 1e-5 * max(abs(ref["E"]), sig), (E[s].item(), ref["E"])
         np.testing.assert_allclose(G[s].cpu().numpy(), ref["grad"], rtol=0,
-                                   atol=1e-4 * max(np.abs(ref["grad"]).max(), sig))
+                                   atol=1e-4 * np.abs(ref["grad"]).max())
     # every set: <C> within the cost range
     Eh = E.cpu().numpy()
     assert np.all(np.isfinite(Eh)) and Eh.min() >= 0 and Eh.max() <= len(w["edges"])

@@ -31,7 +31,7 @@ def sigma(c):
 def check(E, g, E_ref, g_ref, c):
     sig = sigma(c)
     assert abs(E - E_ref) <= 1e-5 * max(abs(E_ref), sig), (E, E_ref)
-    np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-4 * max(np.abs(g_ref).max(), sig))
+    np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-4 * np.abs(g_ref).max())
 
 
 def problem(ctx, oracle_mod, kind, n, seed):
@@ -65,7 +65,7 @@ def test_equal_angles_match_standard_path(Q, oracle_mod):
     E0, g0 = ctx.gradient(cost, qg.XMixer(n), ang)
     assert abs(E - E0) <= 1e-5 * max(abs(E0), sigma(c))
     np.testing.assert_allclose(g[:p * n].reshape(p, n).sum(axis=1), g0[:p], rtol=0,
-                               atol=1e-4 * max(np.abs(g0).max(), sigma(c)))
+                               atol=1e-4 * np.abs(g0).max())
 
 
 def test_batched_next_to_standard_jobs(Q, oracle_mod):

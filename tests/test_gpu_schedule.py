@@ -33,7 +33,7 @@ def setup(oracle_mod):
 
 def _check(E, g, E_ref, g_ref, sig):
     assert abs(E - E_ref) <= 1e-5 * max(abs(E_ref), sig), (E, E_ref)
-    np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-4 * max(np.abs(g_ref).max(), sig))
+    np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-4 * np.abs(g_ref).max())
 
 
 SCHEDULES = sorted({tuple(s) for s in [(cm, sp) for cm in range(4, 9) for sp in range(3)]})
