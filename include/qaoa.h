@@ -108,6 +108,18 @@ enum {
                              mixer |+><+|.  Angles and gradients as for X. */
 };
 
+/* Hadamard-basis weights of a general X mixer (Sec. 2.1: a mixer written as a
+ * sum of products of Pauli X is diagonal after H^n, with the diagonal
+ * precomputed): for f(X) = sum_{k=0..kmax} c_k sum_{|S| = k} prod_{i in S} X_i
+ * on n qubits, d[w] = sum_k c_k K_k(w) for w = 0..n, K_k(w) the Krawtchouk
+ * polynomial (the value of sum_{|S|=k} prod Z_i on a weight-w state).  These
+ * are the n + 1 values a QAOA_MIXER_X_GENERAL mixer's d_lambda holds.
+ *   c  host, kmax + 1 float64 coefficients (c[0] multiplies the identity)
+ *   d  host output, n + 1 float64
+ * 1 <= n <= 62, 0 <= kmax <= n; otherwise QAOA_ERR_INVALID.  Host-only; no
+ * context or device is needed. */
+qaoa_status qaoa_x_mixer_weights(int n, int kmax, const double *c, double *d);
+
 /* Precision of the dense eigenbasis products for QAOA_MIXER_EIGEN. */
 enum {
     QAOA_GEMM_FP32_SIMT = 0, /* complex64 CUDA-core products, fp32 accumulate */
@@ -258,6 +270,15 @@ qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *
  * QAOA_CKPT_PASS).  Per unit the planner steps down PASS -> ROUND -> NONE
  * when one angle set's scratch would not fit in free device memory. */
 qaoa_status qaoa_set_checkpointing(qaoa_ctx *ctx, int mode);
+
+/* Cap on the device memory a call may plan for state scratch (work states,
+ * checkpoints and eigenbasis state matrices), in bytes; negative = no cap
+ * beyond the device's free memory.  Planning happens on the host before any
+ * launch: an angle set whose states cannot fit under the cap even without
+ * checkpoints makes the call fail with QAOA_ERR_OOM, launching nothing; the
+ * context stays usable.  Lets a caller share the device with other work, and
+ * lets tests drive the refusal without exhausting the device.  Host-only. */
+qaoa_status qaoa_set_state_limit(qaoa_ctx *ctx, int64_t bytes);
 
 /* ------------------------------------------ X-mixer pass schedule tuning */
 

@@ -89,15 +89,17 @@ class GeneralXMixer:
 
 
 def krawtchouk_weights(n: int, coeffs: dict) -> np.ndarray:
-    """Hadamard-basis eigenvalues d_w = sum_k c_k K_k(w), w = 0..n, of
-    f(X) = sum_S c_|S| prod X_i, where K_k(w) = sum_j (-1)^j C(w, j) C(n-w, k-j)
-    (the value of sum_{|S|=k} prod_{i in S} Z_i on a weight-w state)."""
-    import math
-
-    d = np.zeros(n + 1)
-    for w in range(n + 1):
-        for k, ck in coeffs.items():
-            d[w] += ck * sum((-1) ** j * math.comb(w, j) * math.comb(n - w, k - j) for j in range(k + 1))
+    """Hadamard-basis eigenvalues d_w, w = 0..n, of f(X) = sum_S c_|S| prod X_i
+    (qaoa_x_mixer_weights); coeffs maps the term order k to c_k."""
+    kmax = max(coeffs) if coeffs else 0
+    c = np.zeros(kmax + 1, dtype=np.float64)
+    for k, ck in coeffs.items():
+        c[int(k)] = float(ck)
+    d = np.zeros(n + 1, dtype=np.float64)
+    st = B.load().qaoa_x_mixer_weights(int(n), kmax, c.ctypes.data_as(ctypes.c_void_p),
+                                       d.ctypes.data_as(ctypes.c_void_p))
+    if st != B.QAOA_OK:
+        raise QAOAError(st, f"qaoa_x_mixer_weights(n={n}, kmax={kmax}) failed")
     return d
 
 
@@ -337,6 +339,11 @@ class Context:
                                             ctypes.byref(E), g.ctypes.data_as(ctypes.c_void_p),
                                             _ckpt_mode(ckpt)))
         return E.value, g
+
+    def set_state_limit(self, nbytes: int | None):
+        """Cap the state scratch a call may plan (qaoa_set_state_limit); None
+        removes the cap."""
+        self._check(self._lib.qaoa_set_state_limit(self._h, -1 if nbytes is None else int(nbytes)))
 
     def set_checkpointing(self, mode):
         """Checkpointing of batched gradients: "none", "round" or "pass" (default)."""

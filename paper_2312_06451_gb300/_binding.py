@@ -74,6 +74,8 @@ SIGNATURES = {
     "qaoa_gradient_small_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                             c_void_p]),
     "qaoa_set_checkpointing": (c_int, [c_void_p, c_int]),
+    "qaoa_set_state_limit": (c_int, [c_void_p, c_int64]),
+    "qaoa_x_mixer_weights": (c_int, [c_int, c_int, c_void_p, c_void_p]),
     "qaoa_check_bounded_wait": (c_int, [c_void_p]),
     "qaoa_cost_degeneracy": (c_int, [c_void_p, ctypes.POINTER(QaoaProblem), c_void_p, c_int]),
     "qaoa_grover_batched": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),

@@ -92,6 +92,11 @@ struct PassDesc {
     const void *tm_psi;
     const void *tm_lam;
     const void *tm_cost;
+    // adjoint: the constant c0 subtracted from C wherever the adjoint uses the
+    // cost as an operator (lambda_p = (C - c0) psi_p and the gamma partials);
+    // nullptr = 0.  The gradient does not depend on c0; c0 = <C> keeps lambda
+    // free of the large common component c0 psi.
+    const double *c0;
     float amp0;
     uint32_t active;      // local bits rotated in this pass
     uint32_t flags;
@@ -179,11 +184,14 @@ struct EigEpiParams {
     int part_stride;
     float *out_lo;  // tensor-core path: remainder planes of split outputs
     float *out2_lo;
+    const double *c0;  // adjoint epilogues: cost shift (lambda_p = (C - c0) psi_p, gamma partials)
 };
 
 // Vp_lo / Vtp_lo non-null: Vp / Vtp get the tf32 heads, *_lo the remainders.
 cudaError_t launch_eig_prepare(const float *V, int D, int ld, float *Vp, float *Vtp, float *Vp_lo, float *Vtp_lo,
                                const double *lam, float *lam_hi, float *lam_lo, cudaStream_t s);
+// Mean of a cost vector (D entries) into *out, fixed summation order; one block.
+cudaError_t launch_cost_mean(const void *cost, int cost_dtype, int D, double *out, cudaStream_t s);
 cudaError_t launch_eig_init(float *X, float *X_lo, float *ck0, int D, int ld, int nsets, const void *cost,
                             int cost_dtype, const RoundCoef *coef, int coef_stride, const float2 *init, float amp0,
                             cudaStream_t s);

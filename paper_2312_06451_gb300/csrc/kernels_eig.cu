@@ -66,6 +66,7 @@ struct EpiArgs {
     int part_stride;      // = number of M tiles
     float *out_lo;        // split outputs for tensor-core operands: out holds the
     float *out2_lo;       // tf32 head, out_lo the float32 remainder (or nullptr)
+    const double *c0;     // cost shift of the adjoint (C - c0), or nullptr
 };
 
 // Store v to out (and its tf32 split when out_lo is set).  The head is v
@@ -114,7 +115,7 @@ __device__ __forceinline__ float epi_elem(const EpiArgs &E, int j, int s, float2
         put(E.out, E.out_lo, o_im, w.y);
         break;
     }
-    case EPI_FWD_LAST: {  // psi_p: <C> partial, store psi_p and lambda_p = C psi_p
+    case EPI_FWD_LAST: {  // psi_p: <C> partial, store psi_p and lambda_p = (C - c0) psi_p
         const float C = cost_at(E, j);
         contrib = C * fmaf(v.x, v.x, v.y * v.y);
         if (E.out) {
@@ -122,8 +123,9 @@ __device__ __forceinline__ float epi_elem(const EpiArgs &E, int j, int s, float2
             E.out[o_im] = v.y;
         }
         if (E.out2) {
-            put(E.out2, E.out2_lo, o_re, C * v.x);
-            put(E.out2, E.out2_lo, o_im, C * v.y);
+            const float Cs = C - (E.c0 ? (float)__ldg(E.c0) : 0.f);
+            put(E.out2, E.out2_lo, o_re, Cs * v.x);
+            put(E.out2, E.out2_lo, o_im, Cs * v.y);
         }
         break;
     }
@@ -142,7 +144,7 @@ __device__ __forceinline__ float epi_elem(const EpiArgs &E, int j, int s, float2
         const float C = cost_at(E, j);
         const float2 ph = turn_phase(cf.g_hi, cf.g_lo, C, 0.f);
         const float2 phi = cmul(make_float2(E.ck_in[o_re], E.ck_in[o_im]), ph);
-        contrib = C * (v.x * phi.y - v.y * phi.x);
+        contrib = (C - (E.c0 ? (float)__ldg(E.c0) : 0.f)) * (v.x * phi.y - v.y * phi.x);
         if (E.out) {
             const float2 w = make_float2(fmaf(v.x, ph.x, v.y * ph.y), fmaf(v.y, ph.x, -v.x * ph.y));
             put(E.out, E.out_lo, o_re, w.x);
@@ -592,6 +594,27 @@ __global__ void eig_init_kernel(float *X, float *X_lo, float *ck0, int D, int ld
     }
 }
 
+// Mean of the D cost values in a fixed order (one block): the shift c0 of the
+// adjoint sweep.  Any constant gives the same gradient, because
+// <mu_k|phi_k> = <lambda_p|psi_p> = <C> is real; the mean removes the
+// component of lambda_p along psi_p that would otherwise dominate it.
+__global__ void __launch_bounds__(256) cost_mean_kernel(const void *cost, int cost_dtype, int D, double *out) {
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < D; j += 256)
+        acc += cost_dtype == 0 ? (double)reinterpret_cast<const float *>(cost)[j]
+                               : (double)reinterpret_cast<const unsigned char *>(cost)[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; w++) t += red[w];
+        *out = t / (double)D;
+    }
+}
+
 // Padded copies of V (row-major D x D) and V^T, and lambda split into two floats.
 __global__ void eig_prepare_kernel(const float *V, int D, int ld, float *Vp, float *Vtp, float *Vp_lo,
                                    float *Vtp_lo, const double *lam, float *lam_hi, float *lam_lo) {
@@ -616,6 +639,11 @@ __global__ void eig_prepare_kernel(const float *V, int D, int ld, float *Vp, flo
 cudaError_t launch_eig_prepare(const float *V, int D, int ld, float *Vp, float *Vtp, float *Vp_lo, float *Vtp_lo,
                                const double *lam, float *lam_hi, float *lam_lo, cudaStream_t s) {
     eig_prepare_kernel<<<152 * 16, 256, 0, s>>>(V, D, ld, Vp, Vtp, Vp_lo, Vtp_lo, lam, lam_hi, lam_lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost_mean(const void *cost, int cost_dtype, int D, double *out, cudaStream_t s) {
+    cost_mean_kernel<<<1, 256, 0, s>>>(cost, cost_dtype, D, out);
     return cudaGetLastError();
 }
 
@@ -650,6 +678,7 @@ EpiArgs to_args(const EigEpiParams &P) {
     E.part_stride = P.part_stride;
     E.out_lo = P.out_lo;
     E.out2_lo = P.out2_lo;
+    E.c0 = P.c0;
     return E;
 }
 }  // namespace

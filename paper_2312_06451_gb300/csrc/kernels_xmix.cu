@@ -577,6 +577,7 @@ __device__ __forceinline__ void post_end(uint32_t bar, TileInfo *info) {
 struct PassConst {
     Rot R;
     float ghi, glo, amp0;
+    float c0;                  // adjoint: cost shift (C - c0 as the operator)
     float fs1, fs2, fs3, fse;  // cos b factors per stage / per pass
     uint32_t flags, active, g3;
     uint32_t rs3[4];
@@ -685,8 +686,9 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
                 }
             }
             if (BWD) {
-                l[2 * r] = __fmul2_rn(make_float2(c0, c0), a[2 * r]);
-                l[2 * r + 1] = __fmul2_rn(make_float2(c1, c1), a[2 * r + 1]);
+                const float d0 = c0 - K.c0, d1 = c1 - K.c0;
+                l[2 * r] = __fmul2_rn(make_float2(d0, d0), a[2 * r]);
+                l[2 * r + 1] = __fmul2_rn(make_float2(d1, d1), a[2 * r + 1]);
             } else if (COST == 0) {
                 a[2 * r] = cmul(a[2 * r], phase_f32(c0, K.ghi, K.glo));
                 a[2 * r + 1] = cmul(a[2 * r + 1], phase_f32(c1, K.ghi, K.glo));
@@ -851,7 +853,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
             for (int i = 0; i < 16; i++) {
                 const float C = cost_at(i);
                 const float2 ph = COST == 0 ? phase_f32(C, K.ghi, K.glo) : stab[(int)C];
-                eacc = fmaf(C, fmaf(l[i].x, a[i].y, -l[i].y * a[i].x), eacc);
+                eacc = fmaf(C - K.c0, fmaf(l[i].x, a[i].y, -l[i].y * a[i].x), eacc);
                 l[i] = cmul_conj(l[i], ph);
                 if (un_psi) a[i] = cmul_conj(a[i], ph);
             }
@@ -988,6 +990,7 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
             }
             K.ghi = cf.g_hi;
             K.glo = cf.g_lo;
+            K.c0 = (BWD && D.c0 && (K.flags & (PF_LAM_FROM_C | PF_PHASE))) ? (float)*D.c0 : 0.f;
             K.g3 = 0;
             for (int j = 0; j < kT; j++)
                 if ((l3 >> j) & 1u) K.g3 += 1u << D.gpos[j];
@@ -1148,8 +1151,14 @@ small_kernel(const SmallDesc *__restrict__ descs, int *err) {
     const double E = block_sum<kSmallThreads / 32>(e, s_red);
     if (tid == 0) *D.E_out = E;
     if constexpr (GRAD) {
+    // the adjoint uses C - <C>: the same gradient, without the common
+    // component <C> psi in lambda
+    __shared__ float s_c0;
+    if (tid == 0) s_c0 = (float)E;
+    __syncthreads();
+    const float c0 = s_c0;
     for (int x = tid; x < N; x += kSmallThreads) {
-        const float c = costv(x);
+        const float c = costv(x) - c0;
         lam[x] = make_float2(c * psi[x].x, c * psi[x].y);
     }
     for (int k = p - 1; k >= 0; k--) {
@@ -1202,7 +1211,7 @@ small_kernel(const SmallDesc *__restrict__ descs, int *err) {
         float gg = 0.f;
         for (int x = tid; x < N; x += kSmallThreads) {
             const float2 l = lam[x], a = psi[x];
-            gg = fmaf(costv(x), l.x * a.y - l.y * a.x, gg);
+            gg = fmaf(costv(x) - c0, l.x * a.y - l.y * a.x, gg);
         }
         const double GG = block_sum<kSmallThreads / 32>(gg, s_red);
         if (tid == 0) D.grad_out[p * nb + k] = 2.0 * GG;
@@ -1253,7 +1262,7 @@ __device__ __forceinline__ Round12 round12(const RoundCoef &cf, float sgn) {
 // gamma partial and the phase undone on both.
 template <int BWD, int COST, int MODE>
 __device__ void tile12_round(float2 *sp, float2 *sl, const float2 *stab, const void *scost, const SmallDesc &D,
-                             const Round12 &rc, bool first, bool last, bool grad, float &bacc, float &eacc) {
+                             const Round12 &rc, bool first, bool last, float c0, float &bacc, float &eacc) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t l1 = ((uint32_t)lane << 1) | ((uint32_t)warp << 6);
     const uint32_t l2 = ((uint32_t)lane & 1u) | ((((uint32_t)lane >> 1) & 7u) << 6) |
@@ -1358,7 +1367,7 @@ __device__ void tile12_round(float2 *sp, float2 *sl, const float2 *stab, const v
             const uint32_t x = l3 | ((uint32_t)i << 5);
             const float C = costv(x);
             const float2 ph = phase(x);
-            eacc = fmaf(C, fmaf(l[i].x, a[i].y, -l[i].y * a[i].x), eacc);
+            eacc = fmaf(C - c0, fmaf(l[i].x, a[i].y, -l[i].y * a[i].x), eacc);
             l[i] = cmul_conj(l[i], ph);
             a[i] = cmul_conj(a[i], ph);
         }
@@ -1367,14 +1376,13 @@ __device__ void tile12_round(float2 *sp, float2 *sl, const float2 *stab, const v
         for (int i = 0; i < 16; i++) {
             const float C = costv(l3 | ((uint32_t)i << 5));
             eacc = fmaf(C, fmaf(a[i].x, a[i].x, a[i].y * a[i].y), eacc);
-            if (grad) l[i] = make_float2(C * a[i].x, C * a[i].y);
         }
     }
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < 16; i++) {
         sp[l3 | ((uint32_t)i << 5)] = a[i];
-        if (BWD || (last && grad)) sl[l3 | ((uint32_t)i << 5)] = l[i];
+        if (BWD) sl[l3 | ((uint32_t)i << 5)] = l[i];
     }
     __syncthreads();
 }
@@ -1429,22 +1437,33 @@ __global__ void __launch_bounds__(kNT) tile12_kernel(const SmallDesc *__restrict
         const Round12 rc = round12(make_coef(ang[k], ang[p + k]), 1.f);
         load_table(k);
         if (rc.R.mode == 0)
-            tile12_round<0, COST, 0>(sp, sl, stab, scost, D, rc, k == 0, k == p - 1, GRAD != 0, bacc, eacc);
+            tile12_round<0, COST, 0>(sp, sl, stab, scost, D, rc, k == 0, k == p - 1, 0.f, bacc, eacc);
         else
-            tile12_round<0, COST, 2>(sp, sl, stab, scost, D, rc, k == 0, k == p - 1, GRAD != 0, bacc, eacc);
+            tile12_round<0, COST, 2>(sp, sl, stab, scost, D, rc, k == 0, k == p - 1, 0.f, bacc, eacc);
     }
     double E, unused;
     block_sum2(eacc, 0.f, E, unused);
     if (tid == 0) *D.E_out = E;
     if constexpr (GRAD) {
+        // lambda_p = (C - <C>) psi_p: the adjoint with the cost shifted by its
+        // expectation gives the same gradient without the common component
+        // <C> psi in lambda (every thread holds E after block_sum2)
+        const float c0 = (float)E;
+        for (int x = tid; x < kTile; x += kNT) {
+            const float C = COST == 0 ? reinterpret_cast<const float *>(scost)[x]
+                                      : (float)reinterpret_cast<const unsigned char *>(scost)[x];
+            const float2 v = sp[x];
+            sl[x] = make_float2((C - c0) * v.x, (C - c0) * v.y);
+        }
+        __syncthreads();
         for (int k = p - 1; k >= 0; k--) {
             const Round12 rc = round12(make_coef(ang[k], ang[p + k]), -1.f);
             load_table(k);
             float b = 0.f, g = 0.f;
             if (rc.R.mode == 0)
-                tile12_round<1, COST, 0>(sp, sl, stab, scost, D, rc, false, false, true, b, g);
+                tile12_round<1, COST, 0>(sp, sl, stab, scost, D, rc, false, false, c0, b, g);
             else
-                tile12_round<1, COST, 2>(sp, sl, stab, scost, D, rc, false, false, true, b, g);
+                tile12_round<1, COST, 2>(sp, sl, stab, scost, D, rc, false, false, c0, b, g);
             double B, Gm;
             block_sum2(b, g, B, Gm);
             if (tid == 0) {

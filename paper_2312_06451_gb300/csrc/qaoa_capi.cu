@@ -64,7 +64,7 @@ struct Unit {
     const double *wts;     // general X mixer: n + 1 weights
 };
 
-enum LaunchKind { LK_PREP, LK_SMALL, LK_XPASS, LK_REDUCE, LK_EIG_INIT, LK_EIG_GEMM };
+enum LaunchKind { LK_PREP, LK_SMALL, LK_XPASS, LK_REDUCE, LK_EIG_INIT, LK_EIG_GEMM, LK_COST_MEAN };
 
 struct LaunchRec {
     int kind;
@@ -87,6 +87,7 @@ struct LaunchRec {
     CUtensorMap tm[4];  // A_hi, A_lo, B_hi, B_lo
     int sched_idx = -1;  // pass launches: tile counter slot
     int cost_free = 0;   // pass launches: no descriptor reads the cost
+    double *mean_out = nullptr;  // LK_COST_MEAN: where the cost mean goes
 };
 
 struct Plan {
@@ -184,6 +185,7 @@ struct qaoa_ctx {
     std::map<std::pair<int, int>, qaoa_xtune> xtune;  // X-mixer schedules by (n, cost dtype)
     uint64_t tune_epoch = 0;                          // bumped on every schedule change
     int ckpt_mode = QAOA_CKPT_PASS;                   // checkpointing of batched gradients
+    int64_t state_limit = -1;                         // caller's cap on state scratch (-1: none)
 };
 
 namespace {
@@ -720,7 +722,8 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         cudaMemGetInfo(&free_b, &total_b);
         const size_t held = ctx->bufs.count("state") ? ctx->bufs["state"].bytes : 0;
         const double budget_d = (double)(free_b + held) * 0.92 - 1.0 * (1ull << 30);
-        const size_t budget = budget_d > 0 ? (size_t)budget_d : 0;
+        size_t budget = budget_d > 0 ? (size_t)budget_d : 0;
+        if (ctx->state_limit >= 0) budget = std::min(budget, (size_t)ctx->state_limit);
         // waves: consecutive units of a group whose states fit the budget together
         struct Wave {
             GKey gk;
@@ -847,21 +850,26 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         }
         std::vector<RedChunk> rchunks;
         std::vector<RedOut> routs;
+        size_t level2_need = 0;  // chunks of the largest reduction launch
         // partials of unit quantity q: cnt values at src -> chunks + one output
-        auto add_reduction = [&](const double *src, int64_t cnt, double *out, double scale) {
+        auto add_reduction_to = [&](std::vector<RedChunk> &chunks, std::vector<RedOut> &outs, const double *src,
+                                    int64_t cnt, double *out, double scale) {
             RedOut o;
-            o.first = (int)rchunks.size();
+            o.first = (int)chunks.size();
             for (int64_t j = 0; j < cnt; j += kRedChunk) {
                 RedChunk ch;
                 ch.src = src + j;
                 ch.cnt = (int)std::min<int64_t>(kRedChunk, cnt - j);
                 ch.pad = 0;
-                rchunks.push_back(ch);
+                chunks.push_back(ch);
             }
-            o.n = (int)rchunks.size() - o.first;
+            o.n = (int)chunks.size() - o.first;
             o.out = out;
             o.scale = scale;
-            routs.push_back(o);
+            outs.push_back(o);
+        };
+        auto add_reduction = [&](const double *src, int64_t cnt, double *out, double scale) {
+            add_reduction_to(rchunks, routs, src, cnt, out, scale);
         };
         // tensor maps of gathered tiles with short runs (< 2^kTmaSegBits elements),
         // deduplicated; PassDesc.tm_* temporarily hold (index + 1)
@@ -899,6 +907,10 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         for (const Wave &w : waves) {
             const GKey &gk = w.gk;
             std::vector<std::vector<PassDesc>> steps;
+            // <C> of every unit of the wave, reduced between the forward and
+            // the adjoint sweep: the adjoint shifts the cost by it
+            std::vector<RedChunk> mchunks;
+            std::vector<RedOut> mouts;
             for (size_t wi = 0; wi < w.us.size(); wi++) {
                 const int i = w.us[wi];
                 const Unit &u = units[i];
@@ -913,6 +925,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 std::vector<PassDesc> f, b;
                 unit_passes(u, lay[i], grad, W, Lam, CK, prep[i].coef, prep[i].table, prep[i].wtab,
                             reinterpret_cast<double *>(mb + off_part[i]), f, b);
+                for (PassDesc &d : b) d.c0 = u.E;
                 std::vector<PassDesc> all = f;
                 all.insert(all.end(), b.begin(), b.end());
                 if (steps.size() < all.size()) steps.resize(all.size());
@@ -920,7 +933,10 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 {
                     const double *part = reinterpret_cast<const double *>(mb + off_part[i]);
                     const int64_t S = lay[i].stride;
-                    add_reduction(part, (int64_t)lay[i].tiles_f * kPassWarps, u.E, 1.0);
+                    if (grad)
+                        add_reduction_to(mchunks, mouts, part, (int64_t)lay[i].tiles_f * kPassWarps, u.E, 1.0);
+                    else
+                        add_reduction(part, (int64_t)lay[i].tiles_f * kPassWarps, u.E, 1.0);
                     if (grad) {
                         const int64_t tw = (int64_t)lay[i].tiles_b * kPassWarps;
                         const int Pb = (int)lay[i].gb.size();
@@ -985,6 +1001,17 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                          dtype_name(gk.dt));
                 r.fam = family(ctx, nm);
                 L.push_back(r);
+                if (grad && (int)s == nfwd - 1 && !mouts.empty()) {
+                    LaunchRec m;
+                    m.kind = LK_REDUCE;
+                    m.desc_off = put(mchunks.data(), sizeof(RedChunk) * mchunks.size());
+                    m.tb_off = put(mouts.data(), sizeof(RedOut) * mouts.size());
+                    m.ndesc = (int)mchunks.size();
+                    m.tiles = (uint32_t)mouts.size();
+                    m.fam = family(ctx, "reduce_expectation");
+                    level2_need = std::max(level2_need, mchunks.size());
+                    L.push_back(m);
+                }
             }
         }
         // ---- eigenbasis-mixer jobs: one GEMM pipeline per job, the job's angle
@@ -992,7 +1019,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         {
             struct EG {
                 int u0, S, Spad, ld, nmt;
-                size_t st_off, part_off;
+                size_t st_off, part_off, c0_off;
             };
             std::vector<EG> eg;
             size_t st_bytes = 0, part_bytes = 0;
@@ -1022,10 +1049,16 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 st_bytes += align_up(mat * nmat);
                 g.part_off = part_bytes;
                 part_bytes += align_up(sizeof(double) * (1 + 2 * u.p) * g.Spad * g.nmt);
+                g.c0_off = part_bytes;  // the job's cost mean (shift of the adjoint)
+                part_bytes += align_up(sizeof(double));
                 eg.push_back(g);
                 i = j;
             }
             if (!eg.empty()) {
+                if (ctx->state_limit >= 0 && st_bytes > (size_t)ctx->state_limit)
+                    return fail(ctx, QAOA_ERR_OOM,
+                                "eigenbasis state matrices need %.3f GiB, the context's limit is %.3f GiB",
+                                st_bytes / 1073741824.0, ctx->state_limit / 1073741824.0);
                 void *d_est = nullptr, *d_epart = nullptr;
                 st = scratch(ctx, "eigstate", st_bytes, &d_est);
                 if (st) return st;
@@ -1091,6 +1124,16 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                     ep.coef = coef;
                     ep.coef_stride = p;
                     ep.part_stride = g.nmt;
+                    double *c0 = reinterpret_cast<double *>(static_cast<char *>(d_epart) + g.c0_off);
+                    ep.c0 = grad ? c0 : nullptr;
+                    if (grad) {
+                        LaunchRec r;
+                        r.kind = LK_COST_MEAN;
+                        r.ep = ep;
+                        r.mean_out = c0;
+                        r.fam = family(ctx, "cost_mean");
+                        L.push_back(r);
+                    }
                     const double gflops = 2.0 * D * (double)D * 2.0 * g.S;
                     const int fam_g = family(ctx, tcp ? "eig_gemm_tc_3xtf32" : "eig_gemm_simt");
                     // B operand planes of each state matrix (hi = the matrix itself on the tensor path)
@@ -1200,9 +1243,10 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             r.fam = family(ctx, "reduce_partials");
             L.push_back(r);
         }
-        if (!rchunks.empty()) {
+        level2_need = std::max(level2_need, rchunks.size());
+        if (level2_need) {
             void *d_l2 = nullptr;
-            st = scratch(ctx, "level2", sizeof(double) * rchunks.size(), &d_l2);
+            st = scratch(ctx, "level2", sizeof(double) * level2_need, &d_l2);
             if (st) return st;
         }
         // ---- tensor maps at the end of the image (128-byte aligned), then
@@ -1301,6 +1345,9 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             e = r.tc ? launch_eig_gemm_tc(r.tm[0], r.tm[1], r.tm[2], r.tm[3], r.Mp, r.Np, r.Kp, r.ep, d_split_ws,
                                           d_split_cnt, ctx->d_err, ctx->stream)
                      : launch_eig_gemm_simt(r.gA, r.gB, r.Mp, r.Np, r.Kp, r.ep, ctx->stream);
+            break;
+        case LK_COST_MEAN:
+            e = launch_cost_mean(r.ep.cost, r.ep.cost_dtype, r.ep.M, r.mean_out, ctx->stream);
             break;
         case LK_REDUCE:
             e = launch_reduce(reinterpret_cast<const RedChunk *>(db + r.desc_off), r.ndesc,
@@ -1873,6 +1920,41 @@ qaoa_status qaoa_set_checkpointing(qaoa_ctx *ctx, int mode) {
     if (mode < QAOA_CKPT_NONE || mode > QAOA_CKPT_PASS)
         return fail(ctx, QAOA_ERR_INVALID, "checkpoint mode must be 0, 1 or 2 (got %d)", mode);
     ctx->ckpt_mode = mode;
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_x_mixer_weights(int n, int kmax, const double *c, double *d) {
+    if (n < 1 || n > 62 || kmax < 0 || kmax > n || !c || !d) return QAOA_ERR_INVALID;
+    // binomials of n <= 62 in exact 64-bit integers (largest C(62, 31) < 2^63)
+    std::vector<std::vector<int64_t>> B(n + 1, std::vector<int64_t>(n + 1, 0));
+    for (int a = 0; a <= n; a++) {
+        B[a][0] = 1;
+        for (int b = 1; b <= a; b++) B[a][b] = B[a - 1][b - 1] + (b <= a - 1 ? B[a - 1][b] : 0);
+    }
+    for (int w = 0; w <= n; w++) {
+        double acc = 0.0;
+        for (int k = 0; k <= kmax; k++) {
+            if (c[k] == 0.0) continue;
+            // K_k(w): the value of sum_{|S| = k} prod_{i in S} Z_i on a weight-w
+            // basis state; its terms alternate, so it is summed exactly in integers
+            // (|K_k(w)| <= C(n, k)) before the one rounding to double
+            int64_t K = 0;
+            for (int j = 0; j <= k && j <= w; j++) {
+                if (k - j > n - w) continue;
+                const int64_t t = B[w][j] * B[n - w][k - j];
+                K += (j & 1) ? -t : t;
+            }
+            acc += c[k] * (double)K;
+        }
+        d[w] = acc;
+    }
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_set_state_limit(qaoa_ctx *ctx, int64_t bytes) {
+    if (!ctx) return QAOA_ERR_INVALID;
+    ctx->state_limit = bytes < 0 ? -1 : bytes;
+    ctx->plan.valid = false;  // the next call re-plans its waves under the new cap
     return QAOA_OK;
 }
 
