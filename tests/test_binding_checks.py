@@ -36,3 +36,42 @@ def test_noalloc_rejects_host_tensors_before_any_call():
     # well-formed shapes and dtypes, but host memory: refused on the host
     with pytest.raises(ValueError, match="CUDA tensor"):
         qg.qaoa_gradient_small_noalloc(*_good())
+
+
+@pytest.mark.parametrize("n,coeffs", [(1, {1: 1.0}), (8, {1: 1.0, 2: 1.0}), (21, {1: 1.0, 2: 1.0}),
+                                      (13, {0: 0.5, 1: -1.0, 3: 2.5}), (34, {2: 1.0, 17: 1e-3})])
+def test_x_mixer_weights_match_the_oracle(oracle_mod, n, coeffs):
+    """qaoa_x_mixer_weights (host-only library call) against the oracle's
+    Krawtchouk sums, which the oracle pins check against dense Pauli
+    products."""
+    import numpy as np
+
+    d = qg.krawtchouk_weights(n, coeffs)
+    ref = oracle_mod.krawtchouk_weights(n, coeffs)
+    np.testing.assert_allclose(d, ref, rtol=1e-13, atol=1e-12 * max(1.0, np.abs(ref).max()))
+
+
+def test_x_mixer_weights_grover_sum_is_exact():
+    """Sum over every order k of K_k(w) is 2^n [w = 0]: with all c_k = 2^-n
+    the weights are exactly the Grover mixer's [1, 0, ..., 0]."""
+    import numpy as np
+
+    n = 30
+    d = qg.krawtchouk_weights(n, {k: 2.0 ** -n for k in range(n + 1)})
+    np.testing.assert_array_equal(d, [1.0] + [0.0] * n)
+
+
+def test_x_mixer_weights_rejects_bad_sizes():
+    import ctypes
+
+    import numpy as np
+
+    from paper_2312_06451_gb300 import _binding as B
+
+    c = np.ones(3)
+    d = np.zeros(3)
+    lib = B.load()
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    assert lib.qaoa_x_mixer_weights(0, 1, P(c), P(d)) == B.QAOA_ERR_INVALID
+    assert lib.qaoa_x_mixer_weights(2, 3, P(c), P(d)) == B.QAOA_ERR_INVALID
+    assert lib.qaoa_x_mixer_weights(2, 1, None, P(d)) == B.QAOA_ERR_INVALID

@@ -32,9 +32,15 @@ def sigma(c):
 
 
 def check(E, g, E_ref, g_ref, c):
+    """<C> within 1e-5 max(|E|, sigma_C); gradients within 1e-4 of the largest
+    component, but not below 1e-7 sigma_C: the full-space Grover mixer barely
+    moves the state off |+>, its gradient can sit 1e6 below the cost scale,
+    and the 2n quarter-turn rotation layers around its diagonal leave
+    complex64 rounding of about that size (1e-7 sigma_C is 2 float32 unit
+    roundoffs on the cost scale)."""
     sig = sigma(c)
     assert abs(E - E_ref) <= 1e-5 * max(abs(E_ref), sig), (E, E_ref)
-    np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-4 * np.abs(g_ref).max())
+    np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-4 * max(np.abs(g_ref).max(), 1e-3 * sig))
 
 
 def problem(ctx, oracle_mod, n, seed, f32):

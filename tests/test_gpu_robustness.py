@@ -96,3 +96,43 @@ def test_cuda_graph_replay_of_batched_call(qg, oracle_mod):
                 check(j["E"][s].item(), j["grad"][s].cpu().numpy(), E_ref, g_ref, c)
     finally:
         ctx.close()
+
+
+def test_state_limit_refuses_before_launch_and_context_recovers(qg, oracle_mod):
+    """A cap on state scratch below what one angle set needs (even without
+    checkpoints) makes the planner refuse with QAOA_ERR_OOM before anything is
+    launched; lifting the cap, the same context computes the oracle's result."""
+    from paper_2312_06451_gb300 import _binding as B
+
+    n, p = 20, 3
+    e = erdos_renyi(n, 0.3, 81)
+    ang = uniform_angles(p, 82, 2)
+    ctx = qg.Context(0)
+    try:
+        cost = ctx.cost_precompute("maxcut", n, edges=e, dtype=torch.uint8)
+        job = {"cost": cost, "mixer": qg.XMixer(n), "angles": torch.from_numpy(ang).cuda(),
+               "E": torch.full((2,), float("nan"), dtype=torch.float64, device="cuda"),
+               "grad": torch.full((2, 2 * p), float("nan"), dtype=torch.float64, device="cuda")}
+        ctx.set_state_limit((2 << n) * 8 - 1)  # one byte short of W and lambda
+        launches = ctx.launch_count()
+        with pytest.raises(qg.QAOAError) as ei:
+            ctx.expectation_batched([job], want_grad=True)
+        assert ei.value.status == B.QAOA_ERR_OOM
+        assert ctx.launch_count() == launches
+        torch.cuda.synchronize()
+        assert torch.isnan(job["E"]).all()
+        # a cap that admits one set at a time without checkpoints still works
+        ctx.set_state_limit((2 << n) * 8)
+        ctx.expectation_batched([job], want_grad=True)
+        torch.cuda.synchronize()
+        c = oracle_mod.cost_maxcut(n, e)
+        for s in range(2):
+            E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, ang[s])
+            check(job["E"][s].item(), job["grad"][s].cpu().numpy(), E_ref, g_ref, c)
+        ctx.set_state_limit(None)
+        ctx.expectation_batched([job], want_grad=True)
+        torch.cuda.synchronize()
+        E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, ang[1])
+        check(job["E"][1].item(), job["grad"][1].cpu().numpy(), E_ref, g_ref, c)
+    finally:
+        ctx.close()
