@@ -230,7 +230,8 @@ class Workload:
     copied into the job buffers from a device pool first (a 2p-double copy per
     set, so every step evaluates fresh angles)."""
 
-    def __init__(self, qg, ctx, idx, dev, pool_steps, n_override=None, gemm="fp32", mixer="x", eig_cache=None):
+    def __init__(self, qg, ctx, idx, dev, pool_steps, n_override=None, gemm="fp32", mixer="x", eig_cache=None,
+                 eig_form="blocks"):
         import torch
 
         from qaoa_inputs import BASE_SEED, sk_couplings, uneven_batch_recipe, uniform_angles, workload_instance
@@ -252,7 +253,11 @@ class Workload:
             cost = ctx.cost_precompute("dks", n, edges=w["edges"], k=k, dtype=torch.uint8)
             t0 = time.perf_counter()
             xy = "clique" if mixer == "clique" else "ring"
-            mixer = qg.xy_eigen_mixer(ctx, xy, n, k, precision=gemm, cache_file=eig_cache)
+            self.eig_form = eig_form
+            if eig_form == "blocks":
+                mixer = qg.xy_sym_mixer(ctx, xy, n, k, precision=gemm)
+            else:
+                mixer = qg.xy_eigen_mixer(ctx, xy, n, k, precision=gemm, cache_file=eig_cache)
             torch.cuda.synchronize()
             self.precompute_s = time.perf_counter() - t0
             self.eig_mixer = mixer
@@ -261,9 +266,14 @@ class Workload:
             self.name = spec["name"] if xy == "ring" else spec["name"].replace("_ring_", "_clique_")
             self.units = spec["n_sets"]
             self.config = {"workload": self.name, "problem": "densest k-subgraph, G(16,0.5)", "n": n, "k": k,
-                           "feasible_states": int(mixer.dim), "p": p, "mixer": f"{xy} XY via V diag(e^-ib lambda) V^T",
-                           "gemm": gemm, "angle_sets_per_step": spec["n_sets"], "cost_dtype": "u8",
-                           "eig_precompute_s": round(self.precompute_s, 2)}
+                           "feasible_states": int(mixer.dim), "p": p, "mixer": f"{xy} XY",
+                           "angle_sets_per_step": spec["n_sets"], "cost_dtype": "u8",
+                           "l2": "per step 24 products over 256 sets; operands ~0.36 GB (blocks) / 2.7 GB "
+                                 "(dense) vs 129 MB L2; no flush"}
+            self.run_info_eig = {
+                "gemm": gemm, "eig_precompute_s": round(self.precompute_s, 2),
+                "mixer_form": ("cyclic-shift momentum blocks V_b diag(e^-ib lambda) V_b^T, block sizes "
+                               f"{mixer.block_dims}" if eig_form == "blocks" else "dense V diag(e^-ib lambda) V^T")}
         elif idx == 5:
             inst = uneven_batch_recipe(spec["n_instances"], BASE_SEED + 5)
             self.grad = True
@@ -319,6 +329,7 @@ class Workload:
                                  if n >= 24 else "on-chip state (whole state in shared memory)")
         # how this implementation runs the workload (not part of the workload)
         self.run_info = {"state": "complex64"}
+        self.run_info.update(getattr(self, "run_info_eig", {}))
         if not self.grad:
             self.run_info["ckpt"] = "none (forward only)"
         elif idx == 4:
@@ -603,7 +614,7 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
         W = GroverWorkload(qg, ctx, dev, args.steps + args.warmup)
     else:
         W = Workload(qg, ctx, args.workload, dev, args.steps + args.warmup, args.n, args.gemm, args.mixer,
-                     args.eig_cache)
+                     args.eig_cache, args.eig)
     out = measure(args, W, qg, ctx, stream, dist, ws, rank, local, dev, graph_mode=args.graph,
                   steps=args.steps, warmup=args.warmup)
     headline = args.workload == WORKLOAD and not args.n and args.mixer == "x"
@@ -910,6 +921,9 @@ def main():
                     help="workload 4: load the mixer's eigendecomposition from this file, or save it there")
     ap.add_argument("--gemm", default="3xtf32", choices=["fp32", "3xtf32"],
                     help="eigenbasis product precision (workload 4): tcgen05 3xTF32 or CUDA-core float32")
+    ap.add_argument("--eig", default="blocks", choices=["blocks", "dense"],
+                    help="workload 4: the mixer through its cyclic-shift momentum blocks (default) or one dense "
+                         "eigendecomposition")
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
     ap.add_argument("--mixer", default="x", choices=["x", "ma", "terms", "grover", "clique"],
                     help="X-mixer workloads (1-3): transverse field, multi-angle, X + XX terms, or Grover; "

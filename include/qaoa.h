@@ -100,6 +100,14 @@ enum {
                              e^{-i beta_{k,q} X_q} to every qubit q.  An angle set is
                              p (n + 1) values [beta_{1,0..n-1}, ..., beta_{p,0..n-1},
                              gamma_1..gamma_p]; gradients use the same layout. */
+    QAOA_MIXER_EIGEN_SYM = 4, /* an XY mixer (ring or clique) on the D weight-k states
+                             through the eigendecompositions of its cyclic-shift
+                             blocks (see qaoa_xy_block_hamiltonians): d_V holds the
+                             block eigenvector matrices V_b back to back (each
+                             D_b x D_b float32, row-major, eigenvectors as columns),
+                             d_lambda the D float64 eigenvalues block after block,
+                             k the Hamming weight.  Same results as QAOA_MIXER_EIGEN
+                             with the full V, at about 2/n of its product work. */
     QAOA_MIXER_X_GENERAL = 3 /* a sum of products of Pauli X (Sec. 2.1),
                              f(X) = sum_S c_|S| prod_{i in S} X_i on all 2^n states,
                              given by its Hadamard-basis eigenvalues: d_lambda holds
@@ -144,13 +152,22 @@ typedef struct {
 } qaoa_problem;
 
 /* Mixer description.
- *   kind   QAOA_MIXER_X or QAOA_MIXER_EIGEN
+ *   kind   one of QAOA_MIXER_*
  *   n      qubits
- *   dim    feasible-set size: 2^n for X, D for EIGEN
+ *   dim    feasible-set size: 2^n for the X mixers, D for EIGEN / EIGEN_SYM
  *   d_V    EIGEN: D x D float32, row-major, real orthogonal eigenvectors as
- *          columns (H_M V = V diag(lambda))
- *   d_lambda EIGEN: D float64 eigenvalues; X_GENERAL: n + 1 float64 weights
- *   gemm_precision EIGEN: one of QAOA_GEMM_* */
+ *          columns (H_M V = V diag(lambda)); EIGEN_SYM: the block matrices
+ *   d_lambda EIGEN, EIGEN_SYM: D float64 eigenvalues; X_GENERAL: n + 1 float64
+ *          weights
+ *   gemm_precision EIGEN, EIGEN_SYM: one of QAOA_GEMM_*
+ *   k      EIGEN_SYM: Hamming weight of the feasible states (else ignored)
+ *   id     EIGEN, EIGEN_SYM: 0, or a caller-chosen id of this (d_V, d_lambda)
+ *          pair.  The products use V in padded (and, for 3xTF32, split) copies.
+ *          With id 0 every call rebuilds them from d_V / d_lambda; with an id
+ *          the context builds them once and keeps them for every later call
+ *          with that id, so the caller must give a new id whenever the
+ *          contents change (device addresses alone are not enough: freed
+ *          memory is reused). */
 typedef struct {
     int kind;
     int n;
@@ -158,6 +175,8 @@ typedef struct {
     const float *d_V;
     const double *d_lambda;
     int gemm_precision;
+    int k;
+    uint64_t id;
 } qaoa_mixer;
 
 /* ------------------------------------------------------------- context */
@@ -207,6 +226,27 @@ qaoa_status qaoa_ring_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, int6
  * one set and one clear bit, else 0.  d_H: device, dim x dim float64,
  * row-major, dim = C(n, k), 2 <= n <= 40.  Synchronous. */
 qaoa_status qaoa_clique_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, int64_t dim);
+
+/* XY mixers on the weight-k states, block by block (Sec. 2.1 constrained
+ * mixers; Sec. 2.2: the products with the stored eigendecomposition dominate
+ * their cost).  The ring and clique mixers commute with the cyclic shift of
+ * the qubits, so in a real basis of shift momenta they split into
+ * floor(n/2) + 1 blocks (momenta m and n - m share one real block).  This
+ * call gives the blocks' sizes and, when H is not NULL, the dense block
+ * matrices in that basis, whose eigendecompositions make a
+ * QAOA_MIXER_EIGEN_SYM mixer.
+ *   mixer     QAOA_XY_RING or QAOA_XY_CLIQUE (the matrices of
+ *             qaoa_ring_hamiltonian / qaoa_clique_hamiltonian)
+ *   n, k      2 <= n <= 32, 0 <= k <= n, C(n, k) <= 65536
+ *   n_blocks  in: capacity of block_dim; out: the number of (non-empty) blocks
+ *   block_dim host output, the sizes D_b (sum = C(n, k)); NULL to query
+ *             n_blocks only
+ *   H         host output, sum of D_b^2 float64: block b row-major after the
+ *             blocks before it; NULL to skip
+ * Host-only (no context or device).  QAOA_ERR_INVALID on bad arguments or a
+ * too-small capacity. */
+enum { QAOA_XY_RING = 0, QAOA_XY_CLIQUE = 1 };
+qaoa_status qaoa_xy_block_hamiltonians(int mixer, int n, int k, int *n_blocks, int64_t *block_dim, double *H);
 
 /* ----------------------------------------------------------- simulation */
 

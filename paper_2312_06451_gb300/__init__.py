@@ -15,6 +15,7 @@ uniform superposition over the feasible set.
 from __future__ import annotations
 
 import ctypes
+import itertools
 
 import numpy as np
 import torch
@@ -26,7 +27,9 @@ __all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError", "p
            "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched",
            "qaoa_gradient_small_noalloc", "ring_eigen_mixer", "clique_eigen_mixer", "xy_eigen_mixer",
            "save_eigen_mixer", "load_eigen_mixer", "GeneralXMixer", "x_terms_mixer", "grover_x_mixer",
-           "krawtchouk_weights"]
+           "krawtchouk_weights", "EigenSymMixer", "xy_block_hamiltonians", "xy_sym_mixer"]
+
+_MIXER_IDS = itertools.count(1)
 
 _PROBLEMS = {"maxcut": B.QAOA_PROBLEM_MAXCUT, "wmaxcut": B.QAOA_PROBLEM_WMAXCUT,
              "sk": B.QAOA_PROBLEM_SK, "dks": B.QAOA_PROBLEM_DKS, "kvc": B.QAOA_PROBLEM_KVC}
@@ -127,8 +130,10 @@ class EigenMixer:
         self.n = int(n)
         self.dim = int(lam.shape[0])
         self.V, self.lam = V, lam
+        # a fresh id per mixer object: the library keeps its prepared copies
+        # of V under it (addresses alone are reused once tensors are freed)
         self.struct = B.QaoaMixer(B.QAOA_MIXER_EIGEN, self.n, self.dim, V.data_ptr(), lam.data_ptr(),
-                                  _GEMM[precision])
+                                  _GEMM[precision], 0, next(_MIXER_IDS))
 
 
 MIXER_FILE_VERSION = 1
@@ -190,6 +195,73 @@ def xy_eigen_mixer(ctx: "Context", kind: str, n: int, k: int, precision: str = "
         if cache_file:
             save_eigen_mixer(cache_file, n, k, V, lam, kind)
     return EigenMixer(n, V.contiguous(), lam.contiguous(), precision)
+
+
+class EigenSymMixer:
+    """Ring or clique XY mixer on the weight-k states through the
+    eigendecompositions of its cyclic-shift blocks (QAOA_MIXER_EIGEN_SYM):
+    V holds the block eigenvector matrices back to back (float32), lam the
+    eigenvalues block after block (float64)."""
+
+    def __init__(self, n: int, k: int, V: torch.Tensor, lam: torch.Tensor, block_dims, precision: str = "3xtf32"):
+        V = _dev_tensor(V, "V")
+        lam = _dev_tensor(lam, "lam")
+        if V.dtype != torch.float32 or lam.dtype != torch.float64:
+            raise TypeError("V must be float32 and lam float64")
+        dims = [int(d) for d in block_dims]
+        if V.numel() != sum(d * d for d in dims) or lam.numel() != sum(dims):
+            raise ValueError("V and lam do not match the block sizes")
+        self.n, self.k = int(n), int(k)
+        self.dim = int(lam.numel())
+        self.block_dims = dims
+        self.V, self.lam = V, lam
+        self.struct = B.QaoaMixer(B.QAOA_MIXER_EIGEN_SYM, self.n, self.dim, V.data_ptr(), lam.data_ptr(),
+                                  _GEMM[precision], self.k, next(_MIXER_IDS))
+
+
+def xy_block_hamiltonians(kind: str, n: int, k: int):
+    """(block sizes, [H_b as float64 numpy arrays]) of the ring or clique XY
+    mixer in the real momentum basis of the cyclic qubit shift
+    (qaoa_xy_block_hamiltonians; host-only)."""
+    lib = B.load()
+    mk = {"ring": B.QAOA_XY_RING, "clique": B.QAOA_XY_CLIQUE}[kind]
+    nb = ctypes.c_int(0)
+    st = lib.qaoa_xy_block_hamiltonians(mk, int(n), int(k), ctypes.byref(nb), None, None)
+    if st != B.QAOA_OK:
+        raise QAOAError(st, f"qaoa_xy_block_hamiltonians({kind}, n={n}, k={k}) failed")
+    dims = np.zeros(nb.value, dtype=np.int64)
+    dims_only = nb.value
+    st = lib.qaoa_xy_block_hamiltonians(mk, int(n), int(k), ctypes.byref(nb), dims.ctypes.data_as(ctypes.c_void_p),
+                                        None)
+    if st != B.QAOA_OK or nb.value != dims_only:
+        raise QAOAError(st, "qaoa_xy_block_hamiltonians failed")
+    H = np.zeros(int(np.sum(dims * dims)), dtype=np.float64)
+    st = lib.qaoa_xy_block_hamiltonians(mk, int(n), int(k), ctypes.byref(nb), dims.ctypes.data_as(ctypes.c_void_p),
+                                        H.ctypes.data_as(ctypes.c_void_p))
+    if st != B.QAOA_OK:
+        raise QAOAError(st, "qaoa_xy_block_hamiltonians failed")
+    out, o = [], 0
+    for d in dims.tolist():
+        out.append(H[o:o + d * d].reshape(d, d))
+        o += d * d
+    return dims.tolist(), out
+
+
+def xy_sym_mixer(ctx: "Context", kind: str, n: int, k: int, precision: str = "3xtf32") -> EigenSymMixer:
+    """EigenSymMixer of the ring or clique XY mixer: the block matrices come
+    from the library, each is diagonalised once in float64 with
+    torch.linalg.eigh (the pre-computation the paper does for the dense
+    mixer, Sec. 2.1, now on blocks of about 2D/n states)."""
+    dims, Hs = xy_block_hamiltonians(kind, n, k)
+    dev = f"cuda:{ctx.device}"
+    Vs, lams = [], []
+    for H in Hs:
+        lam, V = torch.linalg.eigh(torch.from_numpy(H).to(dev))
+        Vs.append(V.to(torch.float32).reshape(-1))
+        lams.append(lam)
+    V = torch.cat(Vs).contiguous()
+    lam = torch.cat(lams).contiguous()
+    return EigenSymMixer(n, k, V, lam, dims, precision)
 
 
 def ring_eigen_mixer(ctx: "Context", n: int, k: int, precision: str = "fp32", cache_file: str | None = None):

@@ -21,7 +21,8 @@ STATUS_NAMES = {0: "QAOA_OK", 1: "QAOA_ERR_INVALID", 2: "QAOA_ERR_OOM", 3: "QAOA
 
 QAOA_COST_F32, QAOA_COST_U8 = 0, 1
 QAOA_PROBLEM_MAXCUT, QAOA_PROBLEM_WMAXCUT, QAOA_PROBLEM_SK, QAOA_PROBLEM_DKS, QAOA_PROBLEM_KVC = 0, 1, 2, 3, 4
-QAOA_MIXER_X, QAOA_MIXER_EIGEN, QAOA_MIXER_X_MA, QAOA_MIXER_X_GENERAL = 0, 1, 2, 3
+QAOA_MIXER_X, QAOA_MIXER_EIGEN, QAOA_MIXER_X_MA, QAOA_MIXER_X_GENERAL, QAOA_MIXER_EIGEN_SYM = 0, 1, 2, 3, 4
+QAOA_XY_RING, QAOA_XY_CLIQUE = 0, 1
 QAOA_GEMM_FP32_SIMT, QAOA_GEMM_3XTF32, QAOA_GEMM_BF16X3 = 0, 1, 2
 QAOA_CKPT_NONE, QAOA_CKPT_ROUND, QAOA_CKPT_PASS = 0, 1, 2
 
@@ -33,7 +34,7 @@ class QaoaProblem(ctypes.Structure):
 
 class QaoaMixer(ctypes.Structure):
     _fields_ = [("kind", c_int), ("n", c_int), ("dim", c_int64), ("d_V", c_void_p),
-                ("d_lambda", c_void_p), ("gemm_precision", c_int)]
+                ("d_lambda", c_void_p), ("gemm_precision", c_int), ("k", c_int), ("id", ctypes.c_uint64)]
 
 
 class QaoaJob(ctypes.Structure):
@@ -76,6 +77,7 @@ SIGNATURES = {
     "qaoa_set_checkpointing": (c_int, [c_void_p, c_int]),
     "qaoa_set_state_limit": (c_int, [c_void_p, c_int64]),
     "qaoa_x_mixer_weights": (c_int, [c_int, c_int, c_void_p, c_void_p]),
+    "qaoa_xy_block_hamiltonians": (c_int, [c_int, c_int, c_int, ctypes.POINTER(c_int), c_void_p, c_void_p]),
     "qaoa_check_bounded_wait": (c_int, [c_void_p]),
     "qaoa_cost_degeneracy": (c_int, [c_void_p, ctypes.POINTER(QaoaProblem), c_void_p, c_int]),
     "qaoa_grover_batched": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),

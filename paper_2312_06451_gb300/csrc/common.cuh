@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace qg {
 
 // ---------------------------------------------------------------- errors
@@ -158,6 +160,7 @@ struct RedOut {
 
 // -------------------------------------------- eigenbasis mixer (kernels_eig)
 enum EigEpi {
+    EPI_STORE = 0,      // out = the product (block-diagonal path: the orbit kernel follows)
     EPI_FWD_EIG = 1,    // Y = e^{-i b lambda} (V^T X); checkpoint V^T phi
     EPI_FWD_PHASE = 2,  // X = e^{-i g' C} (V Y); checkpoint psi_k
     EPI_FWD_LAST = 3,   // psi_p = V Y; <C> partials; lambda_p = C psi_p
@@ -187,6 +190,12 @@ struct EigEpiParams {
     const double *c0;  // adjoint epilogues: cost shift (lambda_p = (C - c0) psi_p, gamma partials)
 };
 
+// Grouped products: tile i covers output rows out_row .. out_row + 127 of block
+// rows valid below row_end, A rows a_row .., K columns 0 .. kext of A and
+// k_off .. k_off + kext of B.
+struct GroupTile {
+    int a_row, k_off, kext, out_row, row_end, part_idx;
+};
 // Vp_lo / Vtp_lo non-null: Vp / Vtp get the tf32 heads, *_lo the remainders.
 cudaError_t launch_eig_prepare(const float *V, int D, int ld, float *Vp, float *Vtp, float *Vp_lo, float *Vtp_lo,
                                const double *lam, float *lam_hi, float *lam_lo, cudaStream_t s);
@@ -199,6 +208,14 @@ cudaError_t launch_eig_init(float *X, float *X_lo, float *ck0, int D, int ld, in
 // multiples of 128.
 cudaError_t launch_eig_gemm_simt(const float *A, const float *B, int Mp, int Np, int Kp, const EigEpiParams &P,
                                  cudaStream_t s);
+// Grouped (block-diagonal) variants: d_tiles holds n_mtiles GroupTile entries;
+// lda / ldb are the row lengths of A and B.
+cudaError_t launch_eig_gemm_simt_grouped(const float *A, int lda, const float *B, int ldb, int Np,
+                                         const GroupTile *d_tiles, int n_mtiles, const EigEpiParams &P,
+                                         cudaStream_t s);
+cudaError_t launch_eig_gemm_tc_grouped(const CUtensorMap &a_hi, const CUtensorMap &a_lo, const CUtensorMap &b_hi,
+                                       const CUtensorMap &b_lo, int Np, const GroupTile *d_tiles, int n_mtiles,
+                                       const EigEpiParams &P, int *err, cudaStream_t s);
 // tcgen05 3xTF32 product with the same epilogues; tensor maps (2-d, K-major,
 // 32-float boxes x 128 rows, 128-byte swizzle) of the operand planes.  The
 // tiles of a last, partial wave may be split along K: d_ws holds
@@ -231,6 +248,77 @@ cudaError_t smem_attr_once(Kern kern, int bytes, int *done) {
     if (e == cudaSuccess) __atomic_store_n(&done[dev], bytes, __ATOMIC_RELEASE);
     return e;
 }
+
+// ------------------------------------------- XY-mixer cyclic symmetry (xy_sym.cu)
+// Orbits of the weight-k states under the cyclic qubit shift and the real
+// momentum basis that block-diagonalises the ring and clique mixers.  Vectors
+// are numbered like orbit members (orbit o owns entries orb_start[o] ..
+// orb_start[o+1] of members and of the vec_* arrays); vector a of a period-r
+// orbit has the values M_r[j][a] = mr[mr_off[r] + j r + a] on its members.
+// Positions: block b holds block_dim[b] vectors at padded positions
+// block_pos[b] .. block_pos[b] + block_dim[b]; block_pos[b + 1] - block_pos[b]
+// is a multiple of kSymPad.
+constexpr int kSymMaxN = 32;  // longest orbit the orbit kernel holds in registers
+constexpr int kSymPad = 128;  // block padding (the product tiles)
+struct SymLayout {
+    int n = 0, k = 0, D = 0, n_orbits = 0, ldp = 0, pmax = 0;
+    std::vector<int> block_m, block_dim, block_off, block_pos;
+    std::vector<int> orb_start, members, vec_pos, vec_block, vec_t, vec_sin;
+    std::vector<int> orbit_of, member_of, mr_off;
+    std::vector<double> mr;
+};
+bool build_sym_layout(int n, int k, SymLayout &L);
+double sym_basis_value(int r, int t, int sin_part, int j);
+// Dense block matrices Q_b^T H Q_b (row-major, block after block), mixer_kind
+// 0 ring, 1 clique.
+void sym_block_hamiltonians(int mixer_kind, const SymLayout &L, std::vector<double> &H);
+
+// Device tables of a layout for the orbit kernel.
+struct OrbitTabs {
+    const int *orb_start;  // n_orbits + 1
+    const int *members;    // Dicke index of each member
+    const int *vec_pos;    // padded position of each vector
+    const float *mr;       // M_r matrices (float)
+    const int *mr_off;     // n + 1 offsets into mr (-1: no orbit of that period)
+    int n_orbits;
+    int max_r;             // longest orbit (<= kSymMaxN)
+    int mr_len;            // floats in mr (<= kOrbitSmem)
+};
+// Shared-memory room for the M_r matrices: the sum of r^2 over the periods r
+// that divide n is at most 1.34 n^2 for n <= 32.
+constexpr int kOrbitSmem = 1400;
+// Orbit-kernel modes (one launch per round boundary, all sets of a job).
+enum OrbitMode {
+    ORB_INIT = 0,   // X = T^T (e^{-i g_0 C} psi_0); ckpt = T^T psi_0
+    ORB_PHASE = 1,  // X = T^T (e^{-i g_{r+1} C} T Z)
+    ORB_LAST = 2,   // <C> partials of T Z; L = T^T ((C - c0) T Z)
+    ORB_BWD = 3     // mu = T W, phi = e^{-i g_r C} T P; gamma partials; L = T^T (e^{+i g_r C} mu)
+};
+struct OrbitArgs {
+    int mode;
+    int D, ldp, nsets, round;
+    const float *in;      // Z (PHASE, LAST) or W (BWD): [2S][ldp]
+    const float *in_psi;  // BWD: checkpointed psi_{r-1} in the momentum basis
+    float *out, *out_lo;  // X or L (tf32 head and remainder when out_lo)
+    float *ckpt;          // INIT: T^T psi_0
+    const float2 *init;   // INIT: user psi_0 (computational basis) or nullptr
+    float amp0;
+    const void *cost;
+    int cost_dtype;
+    const RoundCoef *coef;
+    int coef_stride;
+    const double *c0;     // LAST / BWD: cost shift
+    double *part;         // LAST / BWD: [set][orbit block] partial sums
+    int part_stride;
+};
+constexpr int kOrbitThreads = 128;  // orbits per block of the orbit kernel
+cudaError_t launch_orbit(const OrbitTabs &T, const OrbitArgs &A, cudaStream_t s);
+// Padded block matrices of a symmetric eigendecomposition: A = V_b (or V_b^T)
+// stacked as rows block_pos[b] .. of a [ldp][pmax] matrix (zero padded), the
+// tf32 split planes when *_lo is set; eigenvalues at padded positions.
+cudaError_t launch_sym_prepare(const float *V, const double *lam, const int *d_bdim, const int *d_boff,
+                               const int *d_bpos, int nb, int pmax, float *Vp, float *Vtp, float *Vp_lo, float *Vtp_lo,
+                               float *lam_hi, float *lam_lo, cudaStream_t s);
 
 // ------------------------------------------------------- launch wrappers
 // Each returns the cudaError_t of the launch.

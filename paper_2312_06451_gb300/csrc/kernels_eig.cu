@@ -95,6 +95,10 @@ __device__ __forceinline__ float epi_elem(const EpiArgs &E, int j, int s, float2
     const RoundCoef cf = E.coef[s * E.coef_stride + E.round];
     float contrib = 0.f;
     switch (E.kind) {
+    case EPI_STORE:
+        put(E.out, E.out_lo, o_re, v.x);
+        put(E.out, E.out_lo, o_im, v.y);
+        break;
     case EPI_FWD_EIG: {  // Y = e^{-i b lambda} v, checkpoint V^T phi
         if (E.ckpt) {
             E.ckpt[o_re] = v.x;
@@ -160,16 +164,28 @@ __device__ __forceinline__ float epi_elem(const EpiArgs &E, int j, int s, float2
 
 __global__ void __launch_bounds__(NT, 2)
 gemm_simt_kernel(const float *__restrict__ A, const float *__restrict__ B, int Kp, int lda, int ldb,
-                 EpiArgs E) {
+                 EpiArgs E, const GroupTile *__restrict__ gt) {
     __shared__ __align__(16) float As[2][BK][BM + 4];
     __shared__ __align__(16) float Bs[2][BK][BN + 4];
     __shared__ float red[BN / 2][17];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // tile geometry: a plain product tiles the whole matrix; a grouped
+    // (block-diagonal) one takes its block's rows and K range from the table
+    int a_row = blockIdx.x * BM, k_off = 0, kext = Kp, m0 = blockIdx.x * BM, row_end = E.M, pidx = blockIdx.x;
+    if (gt) {
+        const GroupTile g = gt[blockIdx.x];
+        a_row = g.a_row;
+        k_off = g.k_off;
+        kext = g.kext;
+        m0 = g.out_row;
+        row_end = g.row_end;
+        pidx = g.part_idx;
+    }
+    const int n0 = blockIdx.y * BN;
     // global -> register staging: each thread loads 8 floats of A and of B
     const int lr = tid >> 1, lk = (tid & 1) * 8;
-    const float *Ag = A + (size_t)(m0 + lr) * lda + lk;
-    const float *Bg = B + (size_t)(n0 + lr) * ldb + lk;
+    const float *Ag = A + (size_t)(a_row + lr) * lda + lk;
+    const float *Bg = B + (size_t)(n0 + lr) * ldb + k_off + lk;
     float4 ra0, ra1, rb0, rb1;
     float acc[8][8];
 #pragma unroll
@@ -192,7 +208,7 @@ gemm_simt_kernel(const float *__restrict__ A, const float *__restrict__ B, int K
             Bs[buf][lk + q][lr] = vb[q];
         }
     };
-    const int nk = Kp / BK;
+    const int nk = kext / BK;
     gload(0);
     sstore(0);
     __syncthreads();
@@ -223,7 +239,7 @@ gemm_simt_kernel(const float *__restrict__ A, const float *__restrict__ B, int K
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-        if (m >= E.M) continue;
+        if (m >= row_end) continue;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const int nc = n0 + (q < 2 ? tx * 4 + 2 * q : 64 + tx * 4 + 2 * (q - 2));
@@ -245,7 +261,7 @@ gemm_simt_kernel(const float *__restrict__ A, const float *__restrict__ B, int K
             double t = 0.0;
             for (int r = 0; r < 16; r++) t += (double)red[tid][r];
             const int s = n0 / 2 + tid;
-            if (s < E.nsets) E.part[(size_t)s * E.part_stride + blockIdx.x] = t;
+            if (s < E.nsets) E.part[(size_t)s * E.part_stride + pidx] = t;
         }
     }
 }
@@ -364,7 +380,7 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __global__ void __launch_bounds__(tc::NT, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int Kp, int ntn,
-               EpiArgs E, SplitArgs SP, int *err) {
+               EpiArgs E, SplitArgs SP, int *err, const GroupTile *__restrict__ gt) {
     using tc::BKF;
     using tc::kStage;
     using tc::kTileA;
@@ -390,8 +406,20 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
         nsegs = SP.nseg;
     }
     const int mt = tile / ntn, nt = tile % ntn;
-    const int m0 = mt * TBM, n0 = nt * TBN;
-    const int nk_all = Kp / BKF;
+    const int n0 = nt * TBN;
+    // plain product: the whole matrix in 128 x 128 tiles; grouped product
+    // (block-diagonal A): the block's rows, K range and valid rows from the table
+    int m0 = mt * TBM, a_row = mt * TBM, k_off = 0, kext = Kp, row_end = E.M, pidx = mt;
+    if (gt) {
+        const GroupTile g = gt[mt];
+        m0 = g.out_row;
+        a_row = g.a_row;
+        k_off = g.k_off;
+        kext = g.kext;
+        row_end = g.row_end;
+        pidx = g.part_idx;
+    }
+    const int nk_all = kext / BKF;
     const int kb0 = (int)((int64_t)nk_all * seg / nsegs);
     const int nk = (int)((int64_t)nk_all * (seg + 1) / nsegs) - kb0;
 
@@ -433,10 +461,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
                 const uint32_t fb = tc::su32(&full[s]);
                 tc::mbar_expect(fb, kStage);
                 const int kx = (kb0 + kb) * BKF;
-                tc::tma_2d(base, &tmAh, kx, m0, fb);
-                tc::tma_2d(base + kTileA, &tmAl, kx, m0, fb);
-                tc::tma_2d(base + 2 * kTileA, &tmBh, kx, n0, fb);
-                tc::tma_2d(base + 2 * kTileA + kTileB, &tmBl, kx, n0, fb);
+                tc::tma_2d(base, &tmAh, kx, a_row, fb);
+                tc::tma_2d(base + kTileA, &tmAl, kx, a_row, fb);
+                tc::tma_2d(base + 2 * kTileA, &tmBh, k_off + kx, n0, fb);
+                tc::tma_2d(base + 2 * kTileA + kTileB, &tmBl, k_off + kx, n0, fb);
                 issued = kb + 1;
             }
         }
@@ -547,7 +575,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
             const int qq = ch * (kCols / 2) + q;  // set within the tile
             const int s = n0 / 2 + qq;
             float contrib = 0.f;
-            if (m < E.M && s < E.nsets) contrib = epi_elem(E, m, s, make_float2(acc[2 * q], acc[2 * q + 1]));
+            if (m < row_end && s < E.nsets) contrib = epi_elem(E, m, s, make_float2(acc[2 * q], acc[2 * q + 1]));
             if (E.part) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, o);
@@ -560,7 +588,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
         if (tid < TBN / 2) {
             const int s = n0 / 2 + tid;
             const double t = ((double)red[0][tid] + (double)red[1][tid]) + ((double)red[2][tid] + (double)red[3][tid]);
-            if (s < E.nsets) E.part[(size_t)s * E.part_stride + mt] = t;
+            if (s < E.nsets) E.part[(size_t)s * E.part_stride + pidx] = t;
         }
     }
     tc::fence_before();
@@ -615,6 +643,192 @@ __global__ void __launch_bounds__(256) cost_mean_kernel(const void *cost, int co
     }
 }
 
+// ------------------------------------------------------------ orbit kernel
+// The per-orbit change of basis of the block-diagonal XY mixers: momentum
+// coefficients (the products' basis) <-> amplitudes of the orbit's member
+// states (the computational basis, where the cost is diagonal).  With T the
+// orthogonal map from momentum coefficients to amplitudes, T restricted to a
+// period-r orbit is the r x r matrix M_r[j][a] (member j, vector a).  One
+// thread takes one orbit of one angle set (both the Re and Im rows); consecutive
+// threads take consecutive orbits, whose vectors sit at consecutive positions of
+// each block.  Round-boundary work in between (see OrbitMode):
+//   INIT : X = T^T (e^{-i g_0 C} psi_0); checkpoint T^T psi_0
+//   PHASE: X = T^T (e^{-i g C} T Z)
+//   LAST : <C> partial sum_j C |a_j|^2 of a = T Z; L = T^T ((C - c0) a)
+//   BWD  : mu = T W, phi = e^{-i g C} T P; gamma partial
+//          sum_j (C_j - c0) Im(conj(mu_j) phi_j); L = T^T (e^{+i g C} mu)
+// Partial sums: fixed-order block sums, float64 across warps.
+template <int MODE, int RMAX>
+__global__ void __launch_bounds__(kOrbitThreads) orbit_kernel(OrbitTabs T, OrbitArgs A) {
+    __shared__ double red[kOrbitThreads / 32];
+    // every M_r of the layout (sum of r^2 over the periods, at most
+    // kOrbitSmem floats), read by all threads at once: shared-memory broadcasts
+    __shared__ __align__(16) float s_mr[kOrbitSmem];
+    for (int i = threadIdx.x; i < T.mr_len; i += kOrbitThreads) s_mr[i] = T.mr[i];
+    __syncthreads();
+    const int o = blockIdx.x * kOrbitThreads + threadIdx.x;
+    const int s = blockIdx.y;
+    float contrib = 0.f;
+    if (o < T.n_orbits && s < A.nsets) {
+        const int s0 = T.orb_start[o], r = T.orb_start[o + 1] - s0;
+        const float *M = s_mr + T.mr_off[r];
+        const RoundCoef cf = A.coef[s * A.coef_stride + A.round];
+        const size_t row_re = (size_t)(2 * s) * A.ldp, row_im = row_re + A.ldp;
+        float ar[RMAX], ai[RMAX], cr[RMAX], ci[RMAX];
+        auto cost_of = [&](int j) -> float {
+            const int idx = T.members[s0 + j];
+            return A.cost_dtype == 0 ? __ldg(reinterpret_cast<const float *>(A.cost) + idx)
+                                     : (float)__ldg(reinterpret_cast<const unsigned char *>(A.cost) + idx);
+        };
+        // a = T c for the coefficients of this orbit in matrix `in`
+        auto to_amp = [&](const float *in, float (&xr)[RMAX], float (&xi)[RMAX]) {
+#pragma unroll
+            for (int a = 0; a < RMAX; a++) {
+                if (a < r) {
+                    const int pos = T.vec_pos[s0 + a];
+                    cr[a] = in[row_re + pos];
+                    ci[a] = in[row_im + pos];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < RMAX; j++) {
+                if (j >= r) continue;
+                float sr = 0.f, si = 0.f;
+#pragma unroll
+                for (int a = 0; a < RMAX; a++) {
+                    if (a >= r) continue;
+                    const float m = M[j * r + a];
+                    sr = fmaf(m, cr[a], sr);
+                    si = fmaf(m, ci[a], si);
+                }
+                xr[j] = sr;
+                xi[j] = si;
+            }
+        };
+        // c = T^T a written to `out` (with the tf32 split when out_lo)
+        auto from_amp = [&](const float (&xr)[RMAX], const float (&xi)[RMAX], float *out, float *out_lo) {
+#pragma unroll
+            for (int a = 0; a < RMAX; a++) {
+                if (a >= r) continue;
+                float sr = 0.f, si = 0.f;
+#pragma unroll
+                for (int j = 0; j < RMAX; j++) {
+                    if (j >= r) continue;
+                    const float m = M[j * r + a];
+                    sr = fmaf(m, xr[j], sr);
+                    si = fmaf(m, xi[j], si);
+                }
+                const int pos = T.vec_pos[s0 + a];
+                put(out, out_lo, row_re + pos, sr);
+                put(out, out_lo, row_im + pos, si);
+            }
+        };
+        if (MODE == ORB_INIT) {
+#pragma unroll
+            for (int j = 0; j < RMAX; j++) {
+                if (j >= r) continue;
+                const float2 v = A.init ? A.init[T.members[s0 + j]] : make_float2(A.amp0, 0.f);
+                ar[j] = v.x;
+                ai[j] = v.y;
+            }
+            if (A.ckpt) from_amp(ar, ai, A.ckpt, nullptr);
+#pragma unroll
+            for (int j = 0; j < RMAX; j++) {
+                if (j >= r) continue;
+                const float2 w = cmul(make_float2(ar[j], ai[j]), turn_phase(cf.g_hi, cf.g_lo, cost_of(j), 0.f));
+                ar[j] = w.x;
+                ai[j] = w.y;
+            }
+            from_amp(ar, ai, A.out, A.out_lo);
+        } else if (MODE == ORB_PHASE) {
+            to_amp(A.in, ar, ai);
+#pragma unroll
+            for (int j = 0; j < RMAX; j++) {
+                if (j >= r) continue;
+                const float2 w = cmul(make_float2(ar[j], ai[j]), turn_phase(cf.g_hi, cf.g_lo, cost_of(j), 0.f));
+                ar[j] = w.x;
+                ai[j] = w.y;
+            }
+            from_amp(ar, ai, A.out, A.out_lo);
+        } else if (MODE == ORB_LAST) {
+            to_amp(A.in, ar, ai);
+            const float c0 = A.c0 ? (float)__ldg(A.c0) : 0.f;
+#pragma unroll
+            for (int j = 0; j < RMAX; j++) {
+                if (j >= r) continue;
+                const float C = cost_of(j);
+                contrib = fmaf(C, fmaf(ar[j], ar[j], ai[j] * ai[j]), contrib);
+                ar[j] *= C - c0;
+                ai[j] *= C - c0;
+            }
+            if (A.out) from_amp(ar, ai, A.out, A.out_lo);
+        } else {  // ORB_BWD
+            float pr[RMAX], pi[RMAX];
+            to_amp(A.in_psi, pr, pi);
+            to_amp(A.in, ar, ai);
+            const float c0 = A.c0 ? (float)__ldg(A.c0) : 0.f;
+#pragma unroll
+            for (int j = 0; j < RMAX; j++) {
+                if (j >= r) continue;
+                const float C = cost_of(j);
+                const float2 ph = turn_phase(cf.g_hi, cf.g_lo, C, 0.f);
+                const float2 phi = cmul(make_float2(pr[j], pi[j]), ph);
+                contrib = fmaf(C - c0, ar[j] * phi.y - ai[j] * phi.x, contrib);
+                // undo the phase on mu: mu conj(ph)
+                const float xr = fmaf(ar[j], ph.x, ai[j] * ph.y), xi = fmaf(ai[j], ph.x, -ar[j] * ph.y);
+                ar[j] = xr;
+                ai[j] = xi;
+            }
+            if (A.out) from_amp(ar, ai, A.out, A.out_lo);
+        }
+    }
+    if (MODE == ORB_LAST || MODE == ORB_BWD) {
+        if (!A.part) return;  // uniform over the launch
+        float v = contrib;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
+        __syncthreads();
+        if (threadIdx.x == 0 && s < A.nsets) {
+            double t = 0.0;
+#pragma unroll
+            for (int w = 0; w < kOrbitThreads / 32; w++) t += red[w];
+            A.part[(size_t)s * A.part_stride + blockIdx.x] = t;
+        }
+    }
+}
+
+// Block eigenvector matrices V_b (back to back, D_b x D_b row-major) into the
+// stacked, zero-padded operand planes: row block_pos[b] + i of Vp is row i of
+// V_b (A = V_b), of Vtp column i (A = V_b^T); eigenvalues to padded positions.
+__global__ void sym_prepare_kernel(const float *V, const double *lam, const int *bdim, const int *boff,
+                                   const int *bpos, int nb, int pmax, float *Vp, float *Vtp, float *Vp_lo,
+                                   float *Vtp_lo, float *lam_hi, float *lam_lo) {
+    const int b = blockIdx.y;
+    if (b >= nb) return;
+    const int Db = bdim[b], P = bpos[b + 1] - bpos[b];
+    const float *Vb = V + (size_t)0;
+    // offset of V_b: sum of D_b'^2 over earlier blocks
+    size_t vo = 0;
+    for (int q = 0; q < b; q++) vo += (size_t)bdim[q] * bdim[q];
+    Vb += vo;
+    const int64_t total = (int64_t)P * pmax;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / pmax), c = (int)(e % pmax);
+        const size_t o = (size_t)(bpos[b] + i) * pmax + c;
+        const bool in = i < Db && c < Db;
+        put(Vp, Vp_lo, o, in ? Vb[(size_t)i * Db + c] : 0.f);
+        put(Vtp, Vtp_lo, o, in ? Vb[(size_t)c * Db + i] : 0.f);
+        if (c == 0) {
+            const double l = i < Db ? lam[boff[b] + i] : 0.0;
+            const float hi = (float)l;
+            lam_hi[bpos[b] + i] = hi;
+            lam_lo[bpos[b] + i] = (float)(l - (double)hi);
+        }
+    }
+}
+
 // Padded copies of V (row-major D x D) and V^T, and lambda split into two floats.
 __global__ void eig_prepare_kernel(const float *V, int D, int ld, float *Vp, float *Vtp, float *Vp_lo,
                                    float *Vtp_lo, const double *lam, float *lam_hi, float *lam_lo) {
@@ -636,9 +850,47 @@ __global__ void eig_prepare_kernel(const float *V, int D, int ld, float *Vp, flo
 
 }  // namespace
 
+cudaError_t launch_sym_prepare(const float *V, const double *lam, const int *d_bdim, const int *d_boff,
+                               const int *d_bpos, int nb, int pmax, float *Vp, float *Vtp, float *Vp_lo, float *Vtp_lo,
+                               float *lam_hi, float *lam_lo, cudaStream_t s) {
+    dim3 grid(152, nb);
+    sym_prepare_kernel<<<grid, 256, 0, s>>>(V, lam, d_bdim, d_boff, d_bpos, nb, pmax, Vp, Vtp, Vp_lo, Vtp_lo,
+                                            lam_hi, lam_lo);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_eig_prepare(const float *V, int D, int ld, float *Vp, float *Vtp, float *Vp_lo, float *Vtp_lo,
                                const double *lam, float *lam_hi, float *lam_lo, cudaStream_t s) {
     eig_prepare_kernel<<<152 * 16, 256, 0, s>>>(V, D, ld, Vp, Vtp, Vp_lo, Vtp_lo, lam, lam_hi, lam_lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orbit(const OrbitTabs &T, const OrbitArgs &A, cudaStream_t s) {
+    if (T.max_r < 1 || T.max_r > kSymMaxN || T.mr_len < 1 || T.mr_len > kOrbitSmem) return cudaErrorInvalidValue;
+    dim3 grid((T.n_orbits + kOrbitThreads - 1) / kOrbitThreads, A.nsets);
+    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+    // the longest orbit sets the register arrays: 16 or 32 members
+    const bool r16 = T.max_r <= 16;
+    switch (A.mode) {
+    case ORB_INIT:
+        if (r16) orbit_kernel<ORB_INIT, 16><<<grid, kOrbitThreads, 0, s>>>(T, A);
+        else orbit_kernel<ORB_INIT, 32><<<grid, kOrbitThreads, 0, s>>>(T, A);
+        break;
+    case ORB_PHASE:
+        if (r16) orbit_kernel<ORB_PHASE, 16><<<grid, kOrbitThreads, 0, s>>>(T, A);
+        else orbit_kernel<ORB_PHASE, 32><<<grid, kOrbitThreads, 0, s>>>(T, A);
+        break;
+    case ORB_LAST:
+        if (r16) orbit_kernel<ORB_LAST, 16><<<grid, kOrbitThreads, 0, s>>>(T, A);
+        else orbit_kernel<ORB_LAST, 32><<<grid, kOrbitThreads, 0, s>>>(T, A);
+        break;
+    case ORB_BWD:
+        if (r16) orbit_kernel<ORB_BWD, 16><<<grid, kOrbitThreads, 0, s>>>(T, A);
+        else orbit_kernel<ORB_BWD, 32><<<grid, kOrbitThreads, 0, s>>>(T, A);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -686,7 +938,7 @@ EpiArgs to_args(const EigEpiParams &P) {
 cudaError_t launch_eig_gemm_simt(const float *A, const float *B, int Mp, int Np, int Kp, const EigEpiParams &P,
                                  cudaStream_t s) {
     dim3 grid(Mp / BM, Np / BN);
-    gemm_simt_kernel<<<grid, NT, 0, s>>>(A, B, Kp, Kp, Kp, to_args(P));
+    gemm_simt_kernel<<<grid, NT, 0, s>>>(A, B, Kp, Kp, Kp, to_args(P), nullptr);
     return cudaGetLastError();
 }
 
@@ -725,7 +977,32 @@ cudaError_t launch_eig_gemm_tc(const CUtensorMap &a_hi, const CUtensorMap &a_lo,
         if (sp.nseg > 1) sp.full = W * nsm;
     }
     const int grid = sp.full + (tiles - sp.full) * sp.nseg;
-    gemm_tc_kernel<<<grid, tc::NT, tc::kSmem, s>>>(a_hi, a_lo, b_hi, b_lo, Kp, ntn, to_args(P), sp, err);
+    gemm_tc_kernel<<<grid, tc::NT, tc::kSmem, s>>>(a_hi, a_lo, b_hi, b_lo, Kp, ntn, to_args(P), sp, err, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eig_gemm_simt_grouped(const float *A, int lda, const float *B, int ldb, int Np,
+                                         const GroupTile *d_tiles, int n_mtiles, const EigEpiParams &P,
+                                         cudaStream_t s) {
+    if (n_mtiles <= 0) return cudaSuccess;
+    dim3 grid(n_mtiles, Np / BN);
+    gemm_simt_kernel<<<grid, NT, 0, s>>>(A, B, 0, lda, ldb, to_args(P), d_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eig_gemm_tc_grouped(const CUtensorMap &a_hi, const CUtensorMap &a_lo, const CUtensorMap &b_hi,
+                                       const CUtensorMap &b_lo, int Np, const GroupTile *d_tiles, int n_mtiles,
+                                       const EigEpiParams &P, int *err, cudaStream_t s) {
+    if (n_mtiles <= 0) return cudaSuccess;
+    static int attr_done[kMaxDevices];
+    {
+        cudaError_t e = smem_attr_once(gemm_tc_kernel, (int)tc::kSmem, attr_done);
+        if (e != cudaSuccess) return e;
+    }
+    const int ntn = Np / tc::BN;
+    const int tiles = n_mtiles * ntn;
+    SplitArgs sp{tiles, 1, nullptr, nullptr};  // no split of the last wave
+    gemm_tc_kernel<<<tiles, tc::NT, tc::kSmem, s>>>(a_hi, a_lo, b_hi, b_lo, 0, ntn, to_args(P), sp, err, d_tiles);
     return cudaGetLastError();
 }
 

@@ -59,12 +59,15 @@ struct Unit {
     const float *V;        // eigenbasis mixer: D x D eigenvectors
     const double *lam;     // eigenbasis mixer: D eigenvalues
     int gemm_precision;
+    int k;                 // block-diagonal XY mixer: Hamming weight of the feasible states
+    uint64_t mixer_id;     // eigenbasis mixers: caller's id of (V, lambda); 0 = none
     int ma;                // X mixer with one angle per (round, qubit)
     int gm;                // general X mixer (Hadamard-basis weights wts)
     const double *wts;     // general X mixer: n + 1 weights
 };
 
-enum LaunchKind { LK_PREP, LK_SMALL, LK_XPASS, LK_REDUCE, LK_EIG_INIT, LK_EIG_GEMM, LK_COST_MEAN };
+enum LaunchKind { LK_PREP, LK_SMALL, LK_XPASS, LK_REDUCE, LK_EIG_INIT, LK_EIG_GEMM, LK_COST_MEAN, LK_ORBIT,
+                  LK_OPERANDS };
 
 struct LaunchRec {
     int kind;
@@ -88,6 +91,20 @@ struct LaunchRec {
     int sched_idx = -1;  // pass launches: tile counter slot
     int cost_free = 0;   // pass launches: no descriptor reads the cost
     double *mean_out = nullptr;  // LK_COST_MEAN: where the cost mean goes
+    // grouped (block-diagonal) products and orbit kernels
+    int grouped = 0, n_mtiles = 0, lda = 0, ldb = 0;
+    const GroupTile *gtiles = nullptr;
+    OrbitTabs otab{};
+    OrbitArgs oarg{};
+    // LK_OPERANDS: padded (and tf32-split) operand planes of an eigendecomposition
+    struct {
+        int sym;
+        const float *V;
+        const double *lam;
+        int D, ld, nb, pmax;
+        const int *bdim, *boff, *bpos;
+        float *Vp, *Vtp, *Vpl, *Vtpl, *lam_hi, *lam_lo;
+    } op{};
 };
 
 struct Plan {
@@ -186,6 +203,7 @@ struct qaoa_ctx {
     uint64_t tune_epoch = 0;                          // bumped on every schedule change
     int ckpt_mode = QAOA_CKPT_PASS;                   // checkpointing of batched gradients
     int64_t state_limit = -1;                         // caller's cap on state scratch (-1: none)
+    std::map<std::pair<int, int>, SymLayout> sym;     // cyclic-shift layouts by (n, k)
 };
 
 namespace {
@@ -655,6 +673,309 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
     }
 }
 
+cudaError_t enqueue_operands(const LaunchRec &r, cudaStream_t s) {
+    if (r.op.sym)
+        return launch_sym_prepare(r.op.V, r.op.lam, r.op.bdim, r.op.boff, r.op.bpos, r.op.nb, r.op.pmax, r.op.Vp,
+                                  r.op.Vtp, r.op.Vpl, r.op.Vtpl, r.op.lam_hi, r.op.lam_lo, s);
+    return launch_eig_prepare(r.op.V, r.op.D, r.op.ld, r.op.Vp, r.op.Vtp, r.op.Vpl, r.op.Vtpl, r.op.lam, r.op.lam_hi,
+                              r.op.lam_lo, s);
+}
+
+// Operand planes of a mixer with an id, built once when the plan is made.
+qaoa_status launch_operands(qaoa_ctx *ctx, const LaunchRec &r) {
+    cudaError_t e = enqueue_operands(r, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "eigenbasis preparation");
+    QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "eigenbasis preparation");
+    ctx->launches++;
+    return QAOA_OK;
+}
+
+// Launches of one job of a block-diagonal XY mixer (QAOA_MIXER_EIGEN_SYM):
+// the S angle sets are the columns of every product, all state matrices are in
+// the momentum basis of the cyclic shift ([2 Spad][ldp], Re and Im rows), and
+// the orbit kernel moves to and from the computational basis at each round
+// boundary.  Per forward round r:
+//   Y = e^{-i b_r lambda} (V_b^T X)   (grouped product; checkpoint V_b^T X)
+//   Z = V_b Y                         (grouped product, plain store; with
+//                                      gradients straight into checkpoint P_{r+1})
+//   X = T^T e^{-i g_{r+1} C} T Z      (orbit kernel; last round: <C>, L)
+// and per adjoint round r = p-1 .. 0:
+//   Y = e^{+i b_r lambda} (V_b^T L)   (beta partials)
+//   W = V_b Y
+//   L = T^T e^{+i g_r C} T W          (gamma partials with P_r)
+template <typename AddRed>
+qaoa_status plan_sym_job(qaoa_ctx *ctx, const std::vector<Unit> &units, int u0, int S, int Spad, bool grad,
+                         const SymLayout &SL, int nmt, int nob, char *st_base, double *part, double *c0,
+                         const RoundCoef *coef, std::vector<LaunchRec> &Lr, AddRed &add_reduction, bool &any_tc) {
+    const Unit &u = units[u0];
+    const int p = u.p, ldp = SL.ldp, pmax = SL.pmax, NB = (int)SL.block_dim.size();
+    const bool tcp = u.gemm_precision == QAOA_GEMM_3XTF32;
+    // ---- device tables of the layout (uploaded once per context)
+    char nm[128];
+    snprintf(nm, sizeof(nm), "symtab:%d:%d", SL.n, SL.k);
+    const std::string tkey = nm;
+    std::vector<int> ints;
+    auto put_ints = [&](const std::vector<int> &v) {
+        const size_t off = ints.size();
+        ints.insert(ints.end(), v.begin(), v.end());
+        while (ints.size() % 4) ints.push_back(0);
+        return off;
+    };
+    const size_t o_start = put_ints(SL.orb_start), o_mem = put_ints(SL.members), o_pos = put_ints(SL.vec_pos),
+                 o_mroff = put_ints(SL.mr_off), o_bdim = put_ints(SL.block_dim), o_boff = put_ints(SL.block_off),
+                 o_bpos = put_ints(SL.block_pos);
+    std::vector<GroupTile> tiles;
+    for (int b = 0; b < NB; b++) {
+        const int P = SL.block_pos[b + 1] - SL.block_pos[b];
+        for (int mt = 0; mt < P / kEigTile; mt++) {
+            GroupTile t;
+            t.a_row = SL.block_pos[b] + mt * kEigTile;
+            t.k_off = SL.block_pos[b];
+            t.kext = P;
+            t.out_row = t.a_row;
+            t.row_end = SL.block_pos[b] + SL.block_dim[b];
+            t.part_idx = t.a_row / kEigTile;
+            tiles.push_back(t);
+        }
+    }
+    // longest K first, so the short blocks fill the last wave
+    std::stable_sort(tiles.begin(), tiles.end(), [](const GroupTile &a, const GroupTile &b) { return a.kext > b.kext; });
+    const size_t ints_b = align_up(ints.size() * sizeof(int)), mr_b = align_up(SL.mr.size() * sizeof(float)),
+                 tiles_b = align_up(tiles.size() * sizeof(GroupTile));
+    void *d_tab = nullptr;
+    qaoa_status st = scratch(ctx, tkey.c_str(), ints_b + mr_b + tiles_b, &d_tab);
+    if (st) return st;
+    char *tb = static_cast<char *>(d_tab);
+    const int *di = reinterpret_cast<const int *>(tb);
+    const float *dmr = reinterpret_cast<const float *>(tb + ints_b);
+    const GroupTile *dtiles = reinterpret_cast<const GroupTile *>(tb + ints_b + mr_b);
+    if (!ctx->eig_ready.count(tkey)) {
+        std::vector<char> img(ints_b + mr_b + tiles_b, 0);
+        std::memcpy(img.data(), ints.data(), ints.size() * sizeof(int));
+        for (size_t i = 0; i < SL.mr.size(); i++) reinterpret_cast<float *>(img.data() + ints_b)[i] = (float)SL.mr[i];
+        std::memcpy(img.data() + ints_b + mr_b, tiles.data(), tiles.size() * sizeof(GroupTile));
+        QG_CUDA(ctx, cudaMemcpy(d_tab, img.data(), img.size(), cudaMemcpyHostToDevice), "layout upload");
+        ctx->eig_ready.insert(tkey);
+    }
+    OrbitTabs T;
+    T.orb_start = di + o_start;
+    T.members = di + o_mem;
+    T.vec_pos = di + o_pos;
+    T.mr = dmr;
+    T.mr_off = di + o_mroff;
+    T.n_orbits = SL.n_orbits;
+    T.max_r = SL.n;
+    T.mr_len = (int)SL.mr.size();
+    if (T.mr_len > kOrbitSmem)
+        return fail(ctx, QAOA_ERR_UNSUPPORTED, "orbit matrices of n=%d exceed the kernel's shared memory", SL.n);
+    // ---- operand planes of (V_b, lambda), prepared once per (V, lambda, n, k)
+    // (kept across calls for a mixer with an id, else rebuilt by every call)
+    if (u.mixer_id)
+        snprintf(nm, sizeof(nm), "symV:id%llu:%d:%d:%d", (unsigned long long)u.mixer_id, SL.n, SL.k, tcp ? 1 : 0);
+    else
+        snprintf(nm, sizeof(nm), "symV:call:%d:%d:%d", SL.n, SL.k, tcp ? 1 : 0);
+    const std::string key = nm;
+    const size_t plane = (size_t)ldp * pmax * sizeof(float);
+    void *dV = nullptr, *dVt = nullptr, *dVl = nullptr, *dVtl = nullptr, *dL = nullptr;
+    if ((st = scratch(ctx, (key + ":V").c_str(), plane, &dV)) || (st = scratch(ctx, (key + ":Vt").c_str(), plane, &dVt)))
+        return st;
+    if (tcp && ((st = scratch(ctx, (key + ":Vlo").c_str(), plane, &dVl)) ||
+                (st = scratch(ctx, (key + ":Vtlo").c_str(), plane, &dVtl))))
+        return st;
+    if ((st = scratch(ctx, (key + ":lam").c_str(), (size_t)2 * ldp * sizeof(float), &dL))) return st;
+    float *lam_hi = static_cast<float *>(dL), *lam_lo = lam_hi + ldp;
+    if (!u.mixer_id || !ctx->eig_ready.count(key)) {
+        LaunchRec r;
+        r.kind = LK_OPERANDS;
+        r.op.sym = 1;
+        r.op.V = u.V;
+        r.op.lam = u.lam;
+        r.op.nb = NB;
+        r.op.pmax = pmax;
+        r.op.bdim = di + o_bdim;
+        r.op.boff = di + o_boff;
+        r.op.bpos = di + o_bpos;
+        r.op.Vp = static_cast<float *>(dV);
+        r.op.Vtp = static_cast<float *>(dVt);
+        r.op.Vpl = static_cast<float *>(dVl);
+        r.op.Vtpl = static_cast<float *>(dVtl);
+        r.op.lam_hi = lam_hi;
+        r.op.lam_lo = lam_lo;
+        r.fam = family(ctx, "eig_operands");
+        if (u.mixer_id) {
+            st = launch_operands(ctx, r);
+            if (st) return st;
+            ctx->eig_ready.insert(key);
+        } else {
+            Lr.push_back(r);
+        }
+    }
+    const float *Vp = static_cast<const float *>(dV), *Vtp = static_cast<const float *>(dVt);
+    const float *Vpl = static_cast<const float *>(dVl), *Vtpl = static_cast<const float *>(dVtl);
+    // ---- state matrices: X, Y, L, Z, 2p checkpoints (CKY: V_b^T X of each
+    // round, P: the state entering each round), remainder planes last
+    const size_t mat = (size_t)2 * Spad * ldp;
+    float *base = reinterpret_cast<float *>(st_base);
+    float *X = base, *Y = base + mat, *Lm = grad ? base + 2 * mat : nullptr;
+    float *Z = base + (grad ? 3 : 2) * mat;
+    auto CKY = [&](int r) { return base + (4 + r) * mat; };
+    auto CKP = [&](int r) { return base + (4 + p + r) * mat; };
+    const int lo0 = grad ? 4 + 2 * p : 3;
+    float *Xl = tcp ? base + lo0 * mat : nullptr;
+    float *Yl = tcp ? base + (lo0 + 1) * mat : nullptr;
+    float *Ll = (tcp && grad) ? base + (lo0 + 2) * mat : nullptr;
+    const int nmat = (grad ? 3 + 2 * p + 3 * (tcp ? 1 : 0) : 2 + 2 * (tcp ? 1 : 0)) + 1;
+    // padding entries are never written: clear the matrices once per plan
+    QG_CUDA(ctx, cudaMemsetAsync(base, 0, mat * nmat * sizeof(float), ctx->stream), "state clear");
+    const int64_t pq = (int64_t)Spad * std::max(nmt, nob);  // partial slots per quantity
+    EigEpiParams ep{};
+    ep.M = SL.D;
+    ep.ld = ldp;
+    ep.nsets = S;
+    ep.lam_hi = lam_hi;
+    ep.lam_lo = lam_lo;
+    ep.cost = u.cost;
+    ep.cost_dtype = u.cost_dtype;
+    ep.coef = coef;
+    ep.coef_stride = p;
+    ep.part_stride = nmt;
+    double useful = 0.0;  // useful flops of one grouped product
+    for (int b = 0; b < NB; b++) useful += 2.0 * SL.block_dim[b] * (double)SL.block_dim[b] * 2.0 * S;
+    const int fam_g = family(ctx, tcp ? "eig_gemm_tc_3xtf32_blocks" : "eig_gemm_simt_blocks");
+    const int fam_o = family(ctx, "orbit_transform");
+    bool map_ok = true;
+    auto lo_of = [&](const float *B) -> const float * { return B == X ? Xl : B == Y ? Yl : B == Lm ? Ll : nullptr; };
+    auto gemm = [&](const float *A, const float *B, EigEpiParams q) {
+        LaunchRec r;
+        r.kind = LK_EIG_GEMM;
+        r.grouped = 1;
+        r.gtiles = dtiles;
+        r.n_mtiles = (int)tiles.size();
+        r.gA = A;
+        r.gB = B;
+        r.lda = pmax;
+        r.ldb = ldp;
+        r.Np = 2 * Spad;
+        r.flops = useful;
+        r.fam = fam_g;
+        if (tcp) {
+            r.tc = 1;
+            any_tc = true;
+            const float *Al = A == Vp ? Vpl : Vtpl;
+            map_ok = map_ok && encode_kmajor_map(&r.tm[0], A, pmax, ldp) && encode_kmajor_map(&r.tm[1], Al, pmax, ldp) &&
+                     encode_kmajor_map(&r.tm[2], B, ldp, 2 * Spad) &&
+                     encode_kmajor_map(&r.tm[3], lo_of(B), ldp, 2 * Spad);
+            q.out_lo = q.out == Y ? Yl : nullptr;  // only Y feeds another product
+        }
+        r.ep = q;
+        Lr.push_back(r);
+    };
+    auto orbit = [&](const OrbitArgs &a) {
+        LaunchRec r;
+        r.kind = LK_ORBIT;
+        r.otab = T;
+        r.oarg = a;
+        r.fam = fam_o;
+        // algorithmic bytes: the matrices read and written once
+        r.bytes = 4.0 * 2 * S * SL.D * ((a.in ? 1 : 0) + (a.in_psi ? 1 : 0) + (a.out ? (a.out_lo ? 2 : 1) : 0) +
+                                        (a.ckpt ? 1 : 0));
+        Lr.push_back(r);
+    };
+    OrbitArgs oa{};
+    oa.D = SL.D;
+    oa.ldp = ldp;
+    oa.nsets = S;
+    oa.amp0 = (float)(1.0 / std::sqrt((double)SL.D));
+    oa.cost = u.cost;
+    oa.cost_dtype = u.cost_dtype;
+    oa.coef = coef;
+    oa.coef_stride = p;
+    oa.part_stride = nob;
+    if (grad) {
+        LaunchRec r;
+        r.kind = LK_COST_MEAN;
+        r.ep = ep;
+        r.mean_out = c0;
+        r.fam = family(ctx, "cost_mean");
+        Lr.push_back(r);
+    }
+    {
+        OrbitArgs a = oa;
+        a.mode = ORB_INIT;
+        a.round = 0;
+        a.out = X;
+        a.out_lo = Xl;
+        a.ckpt = grad ? CKP(0) : nullptr;
+        a.init = u.init;
+        orbit(a);
+    }
+    for (int r = 0; r < p; r++) {
+        EigEpiParams q = ep;
+        q.kind = EPI_FWD_EIG;
+        q.round = r;
+        q.out = Y;
+        q.ckpt = grad ? CKY(r) : nullptr;
+        gemm(Vtp, X, q);
+        float *zout = (grad && r < p - 1) ? CKP(r + 1) : Z;
+        q = ep;
+        q.kind = EPI_STORE;
+        q.out = zout;
+        gemm(Vp, Y, q);
+        OrbitArgs a = oa;
+        a.in = zout;
+        if (r < p - 1) {
+            a.mode = ORB_PHASE;
+            a.round = r + 1;
+            a.out = X;
+            a.out_lo = Xl;
+        } else {
+            a.mode = ORB_LAST;
+            a.round = r;
+            a.out = grad ? Lm : nullptr;
+            a.out_lo = grad ? Ll : nullptr;
+            a.c0 = grad ? c0 : nullptr;
+            a.part = part;
+        }
+        orbit(a);
+    }
+    if (grad) {
+        for (int r = p - 1; r >= 0; r--) {
+            EigEpiParams q = ep;
+            q.kind = EPI_BWD_EIG;
+            q.round = r;
+            q.out = Y;
+            q.ck_in = CKY(r);
+            q.part = part + (1 + r) * pq;
+            gemm(Vtp, Lm, q);
+            q = ep;
+            q.kind = EPI_STORE;
+            q.out = Z;
+            gemm(Vp, Y, q);
+            OrbitArgs a = oa;
+            a.mode = ORB_BWD;
+            a.round = r;
+            a.in = Z;
+            a.in_psi = CKP(r);
+            a.out = r > 0 ? Lm : nullptr;
+            a.out_lo = r > 0 ? Ll : nullptr;
+            a.c0 = c0;
+            a.part = part + (1 + p + r) * pq;
+            orbit(a);
+        }
+    }
+    if (!map_ok) return fail(ctx, QAOA_ERR_CUDA, "tensor map encoding failed");
+    for (int s2 = 0; s2 < S; s2++) {
+        const Unit &us = units[u0 + s2];
+        add_reduction(part + (int64_t)s2 * nob, nob, us.E, 1.0);
+        if (grad)
+            for (int r = 0; r < p; r++) {
+                add_reduction(part + (1 + r) * pq + (int64_t)s2 * nmt, nmt, us.grad + r, 2.0);
+                add_reduction(part + (1 + p + r) * pq + (int64_t)s2 * nob, nob, us.grad + p + r, 2.0);
+            }
+    }
+    return QAOA_OK;
+}
+
 const char *dtype_name(int dt) { return dt == QAOA_COST_U8 ? "u8" : "f32"; }
 
 // Build (or reuse) the launch plan for a unit list and enqueue it.
@@ -1020,16 +1341,20 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             struct EG {
                 int u0, S, Spad, ld, nmt;
                 size_t st_off, part_off, c0_off;
+                bool sym;
+                const SymLayout *L;
+                int nob;  // orbit blocks (block-diagonal mixers)
             };
             std::vector<EG> eg;
             size_t st_bytes = 0, part_bytes = 0;
+            auto is_eig = [](int kind) { return kind == QAOA_MIXER_EIGEN || kind == QAOA_MIXER_EIGEN_SYM; };
             for (int i = 0; i < nu;) {
-                if (units[i].mixer_kind != QAOA_MIXER_EIGEN) {
+                if (!is_eig(units[i].mixer_kind)) {
                     i++;
                     continue;
                 }
                 int j = i;
-                while (j < nu && units[j].mixer_kind == QAOA_MIXER_EIGEN && units[j].job == units[i].job) j++;
+                while (j < nu && units[j].mixer_kind == units[i].mixer_kind && units[j].job == units[i].job) j++;
                 const Unit &u = units[i];
                 if (u.gemm_precision == QAOA_GEMM_BF16X3)
                     return fail(ctx, QAOA_ERR_UNSUPPORTED,
@@ -1039,16 +1364,34 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 g.u0 = i;
                 g.S = j - i;
                 g.Spad = (int)align_up((size_t)g.S, kEigSetTile);
-                g.ld = (int)align_up((size_t)u.dim, kEigTile);
+                g.sym = u.mixer_kind == QAOA_MIXER_EIGEN_SYM;
+                g.L = nullptr;
+                g.nob = 0;
+                if (g.sym) {
+                    auto key = std::make_pair(u.n, u.k);
+                    if (!ctx->sym.count(key)) {
+                        SymLayout SL;
+                        if (!build_sym_layout(u.n, u.k, SL))
+                            return fail(ctx, QAOA_ERR_INVALID, "no cyclic-shift layout for n=%d, k=%d", u.n, u.k);
+                        ctx->sym[key] = SL;
+                    }
+                    g.L = &ctx->sym[key];
+                    g.ld = g.L->ldp;
+                    g.nob = (g.L->n_orbits + kOrbitThreads - 1) / kOrbitThreads;
+                } else {
+                    g.ld = (int)align_up((size_t)u.dim, kEigTile);
+                }
                 g.nmt = g.ld / kEigTile;
                 const size_t mat = (size_t)2 * g.Spad * g.ld * sizeof(float);
                 const int tcp = u.gemm_precision == QAOA_GEMM_3XTF32 ? 1 : 0;
-                // X, Y, L (+ their remainder planes on the tensor-core path) and 2p checkpoints
-                const int nmat = grad ? 3 + 2 * u.p + 3 * tcp : 2 + 2 * tcp;
+                // dense: X, Y, L (+ their remainder planes on the tensor-core path) and 2p
+                // checkpoints; block-diagonal: one more work matrix Z (product outputs
+                // that only the orbit kernel reads)
+                const int nmat = (grad ? 3 + 2 * u.p + 3 * tcp : 2 + 2 * tcp) + (g.sym ? 1 : 0);
                 g.st_off = st_bytes;
                 st_bytes += align_up(mat * nmat);
                 g.part_off = part_bytes;
-                part_bytes += align_up(sizeof(double) * (1 + 2 * u.p) * g.Spad * g.nmt);
+                part_bytes += align_up(sizeof(double) * (1 + 2 * u.p) * g.Spad * std::max(g.nmt, g.nob));
                 g.c0_off = part_bytes;  // the job's cost mean (shift of the adjoint)
                 part_bytes += align_up(sizeof(double));
                 eg.push_back(g);
@@ -1066,13 +1409,28 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 if (st) return st;
                 for (const EG &g : eg) {
                     const Unit &u = units[g.u0];
+                    if (g.sym) {
+                        st = plan_sym_job(ctx, units, g.u0, g.S, g.Spad, grad, *g.L, g.nmt, g.nob,
+                                          static_cast<char *>(d_est) + g.st_off,
+                                          reinterpret_cast<double *>(static_cast<char *>(d_epart) + g.part_off),
+                                          reinterpret_cast<double *>(static_cast<char *>(d_epart) + g.c0_off),
+                                          reinterpret_cast<const RoundCoef *>(mb + off_coef[g.u0]), L, add_reduction,
+                                          any_eig_tc);
+                        if (st) return st;
+                        continue;
+                    }
                     const int D = (int)u.dim, ld = g.ld, p = u.p;
                     // padded V, V^T and split eigenvalues, prepared once per (V, lambda)
                     const bool tcp = u.gemm_precision == QAOA_GEMM_3XTF32;
                     char nm[96];
                     void *dV = nullptr, *dVt = nullptr, *dL = nullptr, *dVl = nullptr, *dVtl = nullptr;
-                    snprintf(nm, sizeof(nm), "eigV:%p:%p:%d:%d", (const void *)u.V, (const void *)u.lam, D,
-                             tcp ? 1 : 0);
+                    // operand planes: kept across calls for a mixer the caller gave an id
+                    // (the id promises V and lambda do not change), else rebuilt by
+                    // every call from the V and lambda it is given
+                    if (u.mixer_id)
+                        snprintf(nm, sizeof(nm), "eigV:id%llu:%d:%d", (unsigned long long)u.mixer_id, D, tcp ? 1 : 0);
+                    else
+                        snprintf(nm, sizeof(nm), "eigV:call:%d:%d", D, tcp ? 1 : 0);
                     const std::string key = nm;
                     st = scratch(ctx, (key + ":V").c_str(), (size_t)ld * ld * sizeof(float), &dV);
                     if (st) return st;
@@ -1086,16 +1444,28 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                     }
                     st = scratch(ctx, (key + ":lam").c_str(), (size_t)2 * ld * sizeof(float), &dL);
                     if (st) return st;
-                    if (!ctx->eig_ready.count(key)) {
-                        float *lh = static_cast<float *>(dL);
-                        cudaError_t e = launch_eig_prepare(u.V, D, ld, static_cast<float *>(dV),
-                                                           static_cast<float *>(dVt), static_cast<float *>(dVl),
-                                                           static_cast<float *>(dVtl), u.lam, lh, lh + ld,
-                                                           ctx->stream);
-                        if (e != cudaSuccess) return cuda_fail(ctx, e, "eigenbasis preparation");
-                        QG_CUDA(ctx, cudaStreamSynchronize(ctx->stream), "eigenbasis preparation");
-                        ctx->launches++;
-                        ctx->eig_ready.insert(key);
+                    if (!u.mixer_id || !ctx->eig_ready.count(key)) {
+                        LaunchRec r;
+                        r.kind = LK_OPERANDS;
+                        r.op.sym = 0;
+                        r.op.V = u.V;
+                        r.op.lam = u.lam;
+                        r.op.D = D;
+                        r.op.ld = ld;
+                        r.op.Vp = static_cast<float *>(dV);
+                        r.op.Vtp = static_cast<float *>(dVt);
+                        r.op.Vpl = static_cast<float *>(dVl);
+                        r.op.Vtpl = static_cast<float *>(dVtl);
+                        r.op.lam_hi = static_cast<float *>(dL);
+                        r.op.lam_lo = static_cast<float *>(dL) + ld;
+                        r.fam = family(ctx, "eig_operands");
+                        if (u.mixer_id) {  // once for this mixer, now
+                            st = launch_operands(ctx, r);
+                            if (st) return st;
+                            ctx->eig_ready.insert(key);
+                        } else {
+                            L.push_back(r);
+                        }
                     }
                     const float *Vp = static_cast<const float *>(dV), *Vtp = static_cast<const float *>(dVt);
                     const float *lam_hi = static_cast<const float *>(dL), *lam_lo = lam_hi + ld;
@@ -1342,9 +1712,21 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                                 r.ep.coef, r.ep.coef_stride, r.iinit, r.iamp0, ctx->stream);
             break;
         case LK_EIG_GEMM:
-            e = r.tc ? launch_eig_gemm_tc(r.tm[0], r.tm[1], r.tm[2], r.tm[3], r.Mp, r.Np, r.Kp, r.ep, d_split_ws,
-                                          d_split_cnt, ctx->d_err, ctx->stream)
-                     : launch_eig_gemm_simt(r.gA, r.gB, r.Mp, r.Np, r.Kp, r.ep, ctx->stream);
+            if (r.grouped)
+                e = r.tc ? launch_eig_gemm_tc_grouped(r.tm[0], r.tm[1], r.tm[2], r.tm[3], r.Np, r.gtiles, r.n_mtiles,
+                                                      r.ep, ctx->d_err, ctx->stream)
+                         : launch_eig_gemm_simt_grouped(r.gA, r.lda, r.gB, r.ldb, r.Np, r.gtiles, r.n_mtiles, r.ep,
+                                                        ctx->stream);
+            else
+                e = r.tc ? launch_eig_gemm_tc(r.tm[0], r.tm[1], r.tm[2], r.tm[3], r.Mp, r.Np, r.Kp, r.ep, d_split_ws,
+                                              d_split_cnt, ctx->d_err, ctx->stream)
+                         : launch_eig_gemm_simt(r.gA, r.gB, r.Mp, r.Np, r.Kp, r.ep, ctx->stream);
+            break;
+        case LK_ORBIT:
+            e = launch_orbit(r.otab, r.oarg, ctx->stream);
+            break;
+        case LK_OPERANDS:
+            e = enqueue_operands(r, ctx->stream);
             break;
         case LK_COST_MEAN:
             e = launch_cost_mean(r.ep.cost, r.ep.cost_dtype, r.ep.M, r.mean_out, ctx->stream);
@@ -1372,11 +1754,20 @@ qaoa_status check_args(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
                          const void *d_init, int p) {
     if (!ctx) return QAOA_ERR_INVALID;
     if (!mx) return fail(ctx, QAOA_ERR_INVALID, "mixer is NULL");
-    if (mx->kind == QAOA_MIXER_EIGEN) {
+    if (mx->kind == QAOA_MIXER_EIGEN || mx->kind == QAOA_MIXER_EIGEN_SYM) {
         if (!mx->d_V || !mx->d_lambda || ((uintptr_t)mx->d_V & 15) || ((uintptr_t)mx->d_lambda & 7))
             return fail(ctx, QAOA_ERR_INVALID, "eigenbasis mixer needs aligned d_V and d_lambda");
         if (mx->dim < 1 || mx->dim > kMaxEigDim)
             return fail(ctx, QAOA_ERR_INVALID, "eigenbasis mixer dim must be in [1, %d]", kMaxEigDim);
+        if (mx->kind == QAOA_MIXER_EIGEN_SYM) {
+            if (mx->n < 2 || mx->n > kSymMaxN || mx->k < 0 || mx->k > mx->n)
+                return fail(ctx, QAOA_ERR_INVALID, "block XY mixer needs 2 <= n <= %d and 0 <= k <= n", kSymMaxN);
+            double D = 1.0;
+            for (int i = 0; i < mx->k; i++) D = D * (mx->n - i) / (i + 1);
+            if ((int64_t)std::llround(D) != mx->dim)
+                return fail(ctx, QAOA_ERR_INVALID, "block XY mixer: dim %lld is not C(%d, %d)", (long long)mx->dim,
+                            mx->n, mx->k);
+        }
         if (mx->gemm_precision < QAOA_GEMM_FP32_SIMT || mx->gemm_precision > QAOA_GEMM_BF16X3)
             return fail(ctx, QAOA_ERR_INVALID, "unknown GEMM precision %d", mx->gemm_precision);
         if (p < 1 || p > 4096) return fail(ctx, QAOA_ERR_INVALID, "p must be in [1, 4096] (got %d)", p);
@@ -1469,6 +1860,8 @@ qaoa_status scalar_run(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
     u.V = mixer->d_V;
     u.lam = mixer->d_lambda;
     u.gemm_precision = mixer->gemm_precision;
+    u.k = mixer->k;
+    u.mixer_id = mixer->id;
     std::vector<Unit> us(1, u);
     st = run_units(ctx, us, grad != nullptr, grad ? ckpt : 0);
     if (st) return st;
@@ -1767,6 +2160,8 @@ qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *
                 u.V = jb.mixer->d_V;
                 u.lam = jb.mixer->d_lambda;
                 u.gemm_precision = jb.mixer->gemm_precision;
+                u.k = jb.mixer->k;
+                u.mixer_id = jb.mixer->id;
                 units.push_back(u);
             }
         }

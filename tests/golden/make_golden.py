@@ -93,9 +93,9 @@ def workload2_ramp(res):
     print("workload 2 ramp done", res["workloads"]["2ramp"]["oracle_seconds"], E)
 
 
-def workload4(res):
-    """Densest 8-subgraph on G(16, 0.5), ring mixer on the 12870 weight-8
-    states, p=6: two angle sets, <C> and gradient."""
+def workload4(res, mixer="ring"):
+    """Densest 8-subgraph on G(16, 0.5), ring (or clique) mixer on the 12870
+    weight-8 states, p=6: two angle sets, <C> and gradient."""
     w = workload_instance(4, n_sets=2)
     n, k, p = w["spec"]["n"], w["spec"]["k"], w["spec"]["p"]
     t = time.time()
@@ -103,12 +103,14 @@ def workload4(res):
     cost = oracle.cost_dks(n, w["edges"], st)
     sets = []
     for s in range(2):
-        E, g = oracle.qaoa_gradient(n, cost, w["angles"][s], "ring", st)
+        E, g = oracle.qaoa_gradient(n, cost, w["angles"][s], mixer, st)
         sets.append({"angles": w["angles"][s].tolist(), "E": E, "grad": g.tolist()})
-    res["workloads"]["4"] = {"name": w["spec"]["name"], "n": n, "k": k, "p": p, "sets": sets,
+    key = "4" if mixer == "ring" else "4" + mixer
+    name = w["spec"]["name"] if mixer == "ring" else w["spec"]["name"].replace("_ring_", f"_{mixer}_")
+    res["workloads"][key] = {"name": name, "n": n, "k": k, "p": p, "sets": sets, "mixer": mixer,
                              "cost_rms": float(np.sqrt(np.mean(cost ** 2))),
                              "oracle_seconds": time.time() - t}
-    print("workload 4 done", res["workloads"]["4"]["oracle_seconds"])
+    print("workload 4 done", mixer, res["workloads"][key]["oracle_seconds"])
 
 
 if __name__ == "__main__":

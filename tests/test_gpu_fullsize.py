@@ -199,3 +199,31 @@ def test_dks16_k8_ring_p6_full_size(Q, golden, precision):
     # every set: <C> within the cost range
     Eh = E.cpu().numpy()
     assert np.all(np.isfinite(Eh)) and Eh.min() >= 0 and Eh.max() <= len(w["edges"])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "3xtf32"])
+def test_dks16_k8_block_mixer_full_size(Q, golden, precision):
+    """The same workload (256 sets, D = 12870, p = 6) through the cyclic-shift
+    blocks of the ring mixer: sets 0 and 1 against the oracle."""
+    kind = "ring"
+    qg, ctx = Q
+    g = golden["4"]
+    w = workload_instance(4)
+    n, k, p = w["spec"]["n"], w["spec"]["k"], w["spec"]["p"]
+    cost = ctx.cost_precompute("dks", n, edges=w["edges"], k=k, dtype=torch.uint8)
+    mixer = qg.xy_sym_mixer(ctx, kind, n, k, precision=precision)
+    assert len(mixer.block_dims) == 9 and sum(mixer.block_dims) == 12870
+    A = w["angles"]
+    assert np.allclose(A[:2], [s["angles"] for s in g["sets"]])
+    E = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+    G = torch.zeros(A.shape[0], 2 * p, dtype=torch.float64, device="cuda")
+    ctx.expectation_batched([{"cost": cost, "mixer": mixer, "angles": torch.from_numpy(A).cuda(), "E": E,
+                              "grad": G}], want_grad=True)
+    torch.cuda.synchronize()
+    sig = g["cost_rms"]
+    for s in range(2):
+        ref = g["sets"][s]
+        assert abs(E[s].item() - ref["E"]) <= 1e-5 * max(abs(ref["E"]), sig), (E[s].item(), ref["E"])
+        np.testing.assert_allclose(G[s].cpu().numpy(), ref["grad"], rtol=0, atol=1e-4 * np.abs(ref["grad"]).max())
+    Eh = E.cpu().numpy()
+    assert np.all(np.isfinite(Eh)) and Eh.min() >= 0 and Eh.max() <= len(w["edges"])
