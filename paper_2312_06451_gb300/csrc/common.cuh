@@ -66,8 +66,13 @@ enum PassFlags : uint32_t {
     PF_GEN_INIT = 8u,    // fwd: psi = amp0 everywhere instead of a load
     PF_UNPHASE_PSI = 16u, // bwd: also undo the phase on psi (psi_out written)
     PF_TWIST_IN = 32u,   // fwd: psi_in is a user state in the plain basis
-    PF_WDIAG = 64u       // general X mixer: fwd: e^{-i b G(|x|)} on load; bwd: its
+    PF_WDIAG = 64u,      // general X mixer: fwd: e^{-i b G(|x|)} on load; bwd: its
                          // beta partial and its undo after the rotations
+    PF_FUSED = 128u      // round boundary: the tile bits are the last group of round
+                         // k (coef) and the first of round k+1 (coef2).  fwd: rotations
+                         // of round k, e^{-i g_{k+1} C}, rotations of round k+1; bwd:
+                         // undo round k+1 (beta partial -> part_beta), gamma_{k+1}
+                         // partial and phase undo, undo round k (-> part_beta2)
 };
 
 // Per-warp partial sums per tile of the pass kernel.
@@ -88,6 +93,8 @@ struct PassDesc {
     double *part_beta;    // [tile] partial sums, this pass
     double *part_gamma;   // [tile]
     double *part_E;       // [tile]
+    const RoundCoef *coef2;  // PF_FUSED: round k+1 (coef: round k)
+    double *part_beta2;      // PF_FUSED adjoint: round k's beta partials
     // TMA tensor maps (CUtensorMap, 64-byte aligned, device memory) of the
     // gathered tile of psi_in / lam_in / cost, or nullptr: then the tile is
     // fetched as 2^(T-c) one-dimensional bulk copies of 2^c elements.
@@ -331,9 +338,10 @@ cudaError_t launch_small(const SmallDesc *d_descs, int ndesc, int cost_dtype, in
 // var: 0 transverse field, 1 multi-angle, 2 general X mixer (half rounds)
 // d_sched: this launch's tile counter, zero when the launch starts.
 // cost_free: no descriptor of the launch reads the cost vector.
+// fused: every descriptor is a round-boundary pass (PF_FUSED; var 0 only).
 cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int var, const PassDesc *d_descs,
                          const uint32_t *d_tile_begin, int ndesc, uint32_t total_tiles,
-                         int *d_err, uint32_t *d_sched, int cost_free, cudaStream_t s);
+                         int *d_err, uint32_t *d_sched, int cost_free, int fused, cudaStream_t s);
 int small_max_n();
 // n = 12, transverse-field mixer: one CTA per angle set keeps the whole state
 // as one register-staged tile (descriptors as for launch_small).

@@ -452,7 +452,7 @@ struct TileInfo {
 
 template <int BWD>
 __device__ __forceinline__ bool needs_cost(uint32_t flags) {
-    return BWD ? (flags & (PF_LAM_FROM_C | PF_PHASE)) != 0 : (flags & (PF_PHASE | PF_E)) != 0;
+    return BWD ? (flags & (PF_LAM_FROM_C | PF_PHASE | PF_FUSED)) != 0 : (flags & (PF_PHASE | PF_E | PF_FUSED)) != 0;
 }
 
 // Descriptor of tile t for the loader.  A CTA claims its tiles in
@@ -579,8 +579,8 @@ struct PassConst {
     float ghi, glo, amp0;
     float c0;                  // adjoint: cost shift (C - c0 as the operator)
     float fs1, fs2, fs3, fse;  // cos b factors per stage / per pass
-    uint32_t flags, active, g3;
-    uint32_t rs3[4];
+    uint32_t flags, active, g3, g1;
+    uint32_t rs3[4], rs1[3];
     int rescale;
 };
 
@@ -901,7 +901,214 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     }
 }
 
-template <int BWD, int COST, int NBUF, int VAR>
+// Rotation and phase constants of one round for the tiles of a descriptor
+// (K.active must be set): rotation form, the cos factors per stage / per pass.
+__device__ __forceinline__ void set_round(PassConst &K, const RoundCoef &cf, float sgn) {
+    K.R.mode = cf.bmode;
+    K.R.tt = make_float2(sgn * cf.bt, sgn * cf.bt);
+    K.R.ntt = make_float2(-sgn * cf.bt, -sgn * cf.bt);
+    K.R.c = cf.cb;
+    K.R.s = sgn * cf.sb;
+    K.R.psc = cf.bmode == 0 ? cf.cb * cf.cb : 1.f;
+    K.rescale = (cf.bmode == 0 && cf.rescale) ? 1 : 0;
+    const float c = cf.bmode == 0 ? cf.cb : 1.f;
+    const int k1 = __popc(K.active & 0xE01u), k2 = __popc(K.active & 0x1Eu), k3 = __popc(K.active & 0x1E0u);
+    K.fs1 = K.fs2 = K.fs3 = 1.f;
+    for (int k = 0; k < k1; k++) K.fs1 *= c;
+    for (int k = 0; k < k2; k++) K.fs2 *= c;
+    for (int k = 0; k < k3; k++) K.fs3 *= c;
+    K.fse = K.rescale ? 1.f : K.fs1 * K.fs2 * K.fs3;
+    K.ghi = cf.g_hi;
+    K.glo = cf.g_lo;
+}
+
+// Round-boundary tile (PF_FUSED).  The tile's bits are the last qubit group
+// of round k and the first of round k+1, so one pass applies round k's
+// rotations, the phase of round k+1 and round k+1's rotations (forward), or
+// undoes them in reverse order with both rounds' pair terms and the gamma
+// partial in between (adjoint).  The register stages run 1 -> 2 -> 3, the
+// phase at stage 3 (cost values in the tile buffer, natural order), then back
+// 3 -> 2 -> 1 through the inverse transposes, and the result is stored from
+// the stage-1 (load) layout as 16-byte pairs.  KA is the round applied first
+// (forward: k; adjoint: k+1), KB the second; KP holds the phase (round k+1).
+template <int BWD, int COST, int NBUF, int MA, int MB>
+__device__ __forceinline__ void tile_body_fused(const PassConst &KA, const PassConst &KB, const PassConst &KP,
+                                                uint32_t g1, const uint32_t (&rs1)[3],
+                                                const PassDesc &D, const float2 *stab, unsigned char *bufs, int b,
+                                                uint32_t bar, uint32_t *sched, uint32_t total, uint32_t base,
+                                                uint32_t tl, TileInfo *tinfo, const PassDesc *__restrict__ descs,
+                                                const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor,
+                                                const uint32_t *s_tr) {
+    using G = PassGeom<BWD, COST>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t l1 = ((uint32_t)lane << 1) | ((uint32_t)warp << 6);
+    const uint32_t l2 = ((uint32_t)lane & 1u) | ((((uint32_t)lane >> 1) & 7u) << 6) |
+                        ((((uint32_t)lane >> 4) & 1u) << 5) | ((uint32_t)warp << 9);
+    const uint32_t l3 = (uint32_t)lane | ((uint32_t)warp << 9);
+    const uint32_t p1 = swz(l1), p2 = swz(l2), p3 = swz(l3);
+    const uint32_t active = KA.active;
+    float2 *sp = reinterpret_cast<float2 *>(bufs + b * G::kBufB);
+    float2 *sl = sp + kTile;
+    const unsigned char *scost = bufs + b * G::kBufB + G::kPsiB * (BWD ? 2 : 1);
+    float2 a[16], l[16];
+    float pscale = 1.f, bA = 0.f, bB = 0.f, eacc = 0.f;
+    const uint32_t m1 = stage_mask(active, 0, 9, 10, 11), m2 = stage_mask(active, 1, 2, 3, 4),
+                   m3 = stage_mask(active, 5, 6, 7, 8);
+
+    // ---------------- stage 1: read the landed tile
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        const float4 v = *reinterpret_cast<const float4 *>(sp + (l1 | ((uint32_t)r << 9)));
+        a[2 * r] = make_float2(v.x, v.y);
+        a[2 * r + 1] = make_float2(v.z, v.w);
+        if (BWD) {
+            const float4 w = *reinterpret_cast<const float4 *>(sl + (l1 | ((uint32_t)r << 9)));
+            l[2 * r] = make_float2(w.x, w.y);
+            l[2 * r + 1] = make_float2(w.z, w.w);
+        }
+    }
+    // ---------------- round A, stages 1 -> 2 -> 3
+    stage_rot<BWD, MA>(a, l, m1, KA.R, pscale, bA, true);
+    if (KA.rescale) {
+        scale_all<BWD>(a, l, KA.fs1);
+        pscale = 1.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        const uint32_t idx = p1 ^ swz((uint32_t)r << 9);
+        *reinterpret_cast<float4 *>(sp + idx) = make_float4(a[2 * r].x, a[2 * r].y, a[2 * r + 1].x, a[2 * r + 1].y);
+        if (BWD)
+            *reinterpret_cast<float4 *>(sl + idx) = make_float4(l[2 * r].x, l[2 * r].y, l[2 * r + 1].x, l[2 * r + 1].y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        a[i] = sp[p2 ^ ((uint32_t)i << 1)];
+        if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
+    }
+    stage_rot<BWD, MA>(a, l, m2, KA.R, pscale, bA, true);
+    if (KA.rescale) {
+        scale_all<BWD>(a, l, KA.fs2);
+        pscale = 1.f;
+    }
+    // stage 2 -> 3 inside each warp's 512 amplitudes
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        sp[p2 ^ ((uint32_t)i << 1)] = a[i];
+        if (BWD) sl[p2 ^ ((uint32_t)i << 1)] = l[i];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        const uint32_t idx = p3 ^ swz((uint32_t)i << 5);
+        a[i] = sp[idx];
+        if (BWD) l[i] = sl[idx];
+    }
+    stage_rot<BWD, MA>(a, l, m3, KA.R, pscale, bA, true);
+    scale_all<BWD>(a, l, KA.rescale ? KA.fs3 : KA.fse);
+    pscale = 1.f;
+
+    // ---------------- the phase of round k+1 between the two rounds
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        const uint32_t ci = l3 | ((uint32_t)i << 5);
+        const float C = COST == 0 ? reinterpret_cast<const float *>(scost)[ci] : (float)scost[ci];
+        const float2 ph = COST == 0 ? phase_f32(C, KP.ghi, KP.glo) : stab[scost[ci]];
+        if (BWD) {
+            eacc = fmaf(C - KP.c0, fmaf(l[i].x, a[i].y, -l[i].y * a[i].x), eacc);
+            l[i] = cmul_conj(l[i], ph);
+            a[i] = cmul_conj(a[i], ph);
+        } else {
+            a[i] = cmul(a[i], ph);
+        }
+    }
+
+    // ---------------- round B, stages 3 -> 2 -> 1
+    stage_rot<BWD, MB>(a, l, m3, KB.R, pscale, bB, true);
+    if (KB.rescale) {
+        scale_all<BWD>(a, l, KB.fs3);
+        pscale = 1.f;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        const uint32_t idx = p3 ^ swz((uint32_t)i << 5);
+        sp[idx] = a[i];
+        if (BWD) sl[idx] = l[i];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        a[i] = sp[p2 ^ ((uint32_t)i << 1)];
+        if (BWD) l[i] = sl[p2 ^ ((uint32_t)i << 1)];
+    }
+    stage_rot<BWD, MB>(a, l, m2, KB.R, pscale, bB, true);
+    if (KB.rescale) {
+        scale_all<BWD>(a, l, KB.fs2);
+        pscale = 1.f;
+    }
+    // stage 2 -> 1: each warp rewrites its own 512 amplitudes, then all read across warps
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        sp[p2 ^ ((uint32_t)i << 1)] = a[i];
+        if (BWD) sl[p2 ^ ((uint32_t)i << 1)] = l[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        const uint32_t idx = p1 ^ swz((uint32_t)r << 9);
+        const float4 v = *reinterpret_cast<const float4 *>(sp + idx);
+        a[2 * r] = make_float2(v.x, v.y);
+        a[2 * r + 1] = make_float2(v.z, v.w);
+        if (BWD) {
+            const float4 w = *reinterpret_cast<const float4 *>(sl + idx);
+            l[2 * r] = make_float2(w.x, w.y);
+            l[2 * r + 1] = make_float2(w.z, w.w);
+        }
+    }
+    // the buffer is consumed: start the tile NBUF ahead
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t tn = 0;
+        if (lane == 0) tn = (uint32_t)NBUF * gridDim.x + atomicAdd(sched, 1u);
+        tn = __shfl_sync(0xffffffffu, tn, 0);
+        if (tn < total)
+            issue_tile<BWD, COST>(tn, bufs + b * G::kBufB, bar, &tinfo[b], descs, tile_begin, ndesc, cursor, &D,
+                                  s_tr);
+        else
+            post_end(bar, &tinfo[b]);
+    }
+    // psi is dead after the last adjoint stage
+    stage_rot<BWD, MB>(a, l, m1, KB.R, pscale, bB, !BWD);
+    scale_all<BWD>(a, l, KB.rescale ? KB.fs1 : KB.fse);
+
+    // ---------------- store from the stage-1 layout: 16-byte amplitude pairs
+    {
+        float2 *out = BWD ? D.lam_out : D.psi_out;
+        if (out) {
+            const float2 *v = BWD ? l : a;
+            out += base + g1;
+#pragma unroll
+            for (int r = 0; r < 8; r++) {
+                const uint32_t o = ((r & 1) ? rs1[0] : 0u) + ((r & 2) ? rs1[1] : 0u) + ((r & 4) ? rs1[2] : 0u);
+                __stcs(reinterpret_cast<float4 *>(out + o),
+                       make_float4(v[2 * r].x, v[2 * r].y, v[2 * r + 1].x, v[2 * r + 1].y));
+            }
+        }
+    }
+    if (BWD) {  // round k+1's beta total in lane 0, round k's in lane 16; gamma by its own tree
+        const float t = warp_sum2_f(bA, bB);
+        if (lane == 0 && D.part_beta) D.part_beta[tl * kNW + warp] = (double)t;
+        if (lane == 16 && D.part_beta2) D.part_beta2[tl * kNW + warp] = (double)t;
+        const float tg = warp_sum_f(eacc);
+        if (lane == 0 && D.part_gamma) D.part_gamma[tl * kNW + warp] = (double)tg;
+    }
+}
+
+template <int BWD, int COST, int NBUF, int VAR, int FUSED>
 __global__ void __launch_bounds__(kNT, (BWD && NBUF > 1) ? 1 : 2)
 xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ tile_begin, int ndesc,
              uint32_t total, int *err, uint32_t *__restrict__ sched, int cost_free) {
@@ -915,6 +1122,7 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
     __shared__ float4 s_rot[12];  // multi-angle: (cos, +-sin, +-tan, cos^2) per local bit
     __shared__ float4 s_w[33];    // general X mixer: weight phases and G(w)
     __shared__ uint32_t s_tr[3];  // D's first tile, end tile and index
+    __shared__ PassConst s_kf[2];  // round-boundary launches: rounds k and k+1 (uniform fields)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -965,38 +1173,33 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
                 s_tr[2] = (uint32_t)di;
             }
             __syncthreads();
-            const RoundCoef cf = *D.coef;
             K.flags = D.flags;
             K.active = D.active;
             K.amp0 = D.amp0;
             // undoing a round (adjoint) uses the coefficients of -b
             const float sgn = BWD ? -1.f : 1.f;
-            K.R.mode = cf.bmode;
-            K.R.tt = make_float2(sgn * cf.bt, sgn * cf.bt);
-            K.R.ntt = make_float2(-sgn * cf.bt, -sgn * cf.bt);
-            K.R.c = cf.cb;
-            K.R.s = sgn * cf.sb;
-            K.R.psc = cf.bmode == 0 ? cf.cb * cf.cb : 1.f;
-            K.rescale = (cf.bmode == 0 && cf.rescale) ? 1 : 0;
-            {
-                const float c = cf.bmode == 0 ? cf.cb : 1.f;
-                const int k1 = __popc(K.active & 0xE01u), k2 = __popc(K.active & 0x1Eu),
-                          k3 = __popc(K.active & 0x1E0u);
-                K.fs1 = K.fs2 = K.fs3 = 1.f;
-                for (int k = 0; k < k1; k++) K.fs1 *= c;
-                for (int k = 0; k < k2; k++) K.fs2 *= c;
-                for (int k = 0; k < k3; k++) K.fs3 *= c;
-                K.fse = K.rescale ? 1.f : K.fs1 * K.fs2 * K.fs3;
-            }
-            K.ghi = cf.g_hi;
-            K.glo = cf.g_lo;
-            K.c0 = (BWD && D.c0 && (K.flags & (PF_LAM_FROM_C | PF_PHASE))) ? (float)*D.c0 : 0.f;
+            set_round(K, *D.coef, sgn);
+            K.c0 = (BWD && D.c0 && (K.flags & (PF_LAM_FROM_C | PF_PHASE | PF_FUSED))) ? (float)*D.c0 : 0.f;
             K.g3 = 0;
             for (int j = 0; j < kT; j++)
                 if ((l3 >> j) & 1u) K.g3 += 1u << D.gpos[j];
 #pragma unroll
             for (int k = 0; k < 4; k++) K.rs3[k] = 1u << D.gpos[5 + k];
-            if (COST == 1 && (K.flags & PF_PHASE))
+            if (FUSED) {  // stage-1 store offsets (round-boundary passes)
+                const uint32_t l1s = ((uint32_t)lane << 1) | ((uint32_t)warp << 6);
+                K.g1 = 0;
+                for (int j = 1; j < 9; j++)
+                    if ((l1s >> j) & 1u) K.g1 += 1u << D.gpos[j];
+#pragma unroll
+                for (int k = 0; k < 3; k++) K.rs1[k] = 1u << D.gpos[9 + k];
+            }
+            if (FUSED && tid == 0) {  // both rounds of a boundary pass, for every thread
+                PassConst K2 = K;
+                set_round(K2, *D.coef2, sgn);
+                s_kf[0] = K;
+                s_kf[1] = K2;
+            }
+            if (COST == 1 && (K.flags & (PF_PHASE | PF_FUSED)))
                 for (int i = tid; i < kPhaseTable; i += kNT) stab[i] = D.table[i];
             if (VAR == 2 && (K.flags & PF_WDIAG))
                 for (int i = tid; i <= D.n; i += kNT) s_w[i] = D.wtab[i];
@@ -1032,7 +1235,23 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
             __syncthreads();
             cur = di;
         }
-        if (VAR == 1 && K.R.mode == 0)
+        if constexpr (FUSED) {
+            // forward: round k then round k+1; adjoint: k+1 first; the phase is round k+1's
+            const PassConst &KA = s_kf[BWD ? 1 : 0], &KB = s_kf[BWD ? 0 : 1], &KP = s_kf[1];
+            const int mk = (KA.R.mode == 0 ? 0 : 1) | (KB.R.mode == 0 ? 0 : 2);
+            if (mk == 0)
+                tile_body_fused<BWD, COST, NBUF, 0, 0>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched, total,
+                                                       ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+            else if (mk == 1)
+                tile_body_fused<BWD, COST, NBUF, 2, 0>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched, total,
+                                                       ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+            else if (mk == 2)
+                tile_body_fused<BWD, COST, NBUF, 0, 2>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched, total,
+                                                       ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+            else
+                tile_body_fused<BWD, COST, NBUF, 2, 2>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched, total,
+                                                       ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+        } else if (VAR == 1 && K.R.mode == 0)
             tile_body<BWD, COST, NBUF, 0, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base, ti.tl,
                                              tinfo, descs, tile_begin, ndesc, cursor, s_tr);
         else if (VAR == 1)
@@ -1557,7 +1776,7 @@ __global__ void __launch_bounds__(32) reduce2_kernel(const RedOut *__restrict__ 
     if (threadIdx.x == 0) *O.out = O.scale * acc;
 }
 
-template <int BWD, int COST, int NBUF, int VAR>
+template <int BWD, int COST, int NBUF, int VAR, int FUSED>
 cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t tiles, int *err, uint32_t *sched,
                        int cost_free, cudaStream_t s) {
     using G = PassGeom<BWD, COST>;
@@ -1569,19 +1788,19 @@ cudaError_t launch_one(const PassDesc *d, const uint32_t *tb, int nd, uint32_t t
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    e = smem_attr_once(xpass_kernel<BWD, COST, NBUF, VAR>, (int)smem, attr_done);
+    e = smem_attr_once(xpass_kernel<BWD, COST, NBUF, VAR, FUSED>, (int)smem, attr_done);
     if (e != cudaSuccess) return e;
     int grid_cap = __atomic_load_n(&grid_caps[dev], __ATOMIC_ACQUIRE);
     if (!grid_cap) {
         int nsm = 0, per_sm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xpass_kernel<BWD, COST, NBUF, VAR>, kNT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xpass_kernel<BWD, COST, NBUF, VAR, FUSED>, kNT, smem);
         if (e != cudaSuccess) return e;
         grid_cap = std::max(1, nsm * std::max(1, per_sm));
         __atomic_store_n(&grid_caps[dev], grid_cap, __ATOMIC_RELEASE);
     }
     const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)grid_cap);
-    xpass_kernel<BWD, COST, NBUF, VAR><<<grid, kNT, smem, s>>>(d, tb, nd, tiles, err, sched, cost_free);
+    xpass_kernel<BWD, COST, NBUF, VAR, FUSED><<<grid, kNT, smem, s>>>(d, tb, nd, tiles, err, sched, cost_free);
     return cudaGetLastError();
 }
 
@@ -1605,27 +1824,31 @@ cudaError_t launch_wait_probe(int *err, cudaStream_t s) {
 
 int small_max_n() { return kSmallMaxN; }
 
-template <int VAR>
+template <int VAR, int FUSED>
 cudaError_t launch_xpass_t(int bwd, int cost_dtype, int nbuf, const PassDesc *d, const uint32_t *tb, int nd,
                            uint32_t tiles, int *err, uint32_t *sched, int cf, cudaStream_t s) {
-    if (!bwd) return cost_dtype == 0 ? launch_one<0, 0, 2, VAR>(d, tb, nd, tiles, err, sched, cf, s)
-                                     : launch_one<0, 1, 2, VAR>(d, tb, nd, tiles, err, sched, cf, s);
+    if (!bwd) return cost_dtype == 0 ? launch_one<0, 0, 2, VAR, FUSED>(d, tb, nd, tiles, err, sched, cf, s)
+                                     : launch_one<0, 1, 2, VAR, FUSED>(d, tb, nd, tiles, err, sched, cf, s);
     // adjoint: one tile buffer and two CTAs per SM (128 registers a thread),
     // or two buffers and one CTA per SM (no register cap below 255)
     if (nbuf == 2)
-        return cost_dtype == 0 ? launch_one<1, 0, 2, VAR>(d, tb, nd, tiles, err, sched, cf, s)
-                               : launch_one<1, 1, 2, VAR>(d, tb, nd, tiles, err, sched, cf, s);
-    return cost_dtype == 0 ? launch_one<1, 0, 1, VAR>(d, tb, nd, tiles, err, sched, cf, s)
-                           : launch_one<1, 1, 1, VAR>(d, tb, nd, tiles, err, sched, cf, s);
+        return cost_dtype == 0 ? launch_one<1, 0, 2, VAR, FUSED>(d, tb, nd, tiles, err, sched, cf, s)
+                               : launch_one<1, 1, 2, VAR, FUSED>(d, tb, nd, tiles, err, sched, cf, s);
+    return cost_dtype == 0 ? launch_one<1, 0, 1, VAR, FUSED>(d, tb, nd, tiles, err, sched, cf, s)
+                           : launch_one<1, 1, 1, VAR, FUSED>(d, tb, nd, tiles, err, sched, cf, s);
 }
 
 cudaError_t launch_xpass(int bwd, int cost_dtype, int nbuf, int var, const PassDesc *d, const uint32_t *tb,
-                         int nd, uint32_t tiles, int *err, uint32_t *sched, int cost_free, cudaStream_t s) {
+                         int nd, uint32_t tiles, int *err, uint32_t *sched, int cost_free, int fused, cudaStream_t s) {
     if (tiles == 0) return cudaSuccess;
     if (!sched) return cudaErrorInvalidValue;
-    if (var == 1) return launch_xpass_t<1>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, sched, cost_free, s);
-    if (var == 2) return launch_xpass_t<2>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, sched, cost_free, s);
-    return launch_xpass_t<0>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, sched, cost_free, s);
+    if (fused) {  // round-boundary passes: transverse field only
+        if (var != 0) return cudaErrorInvalidValue;
+        return launch_xpass_t<0, 1>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, sched, cost_free, s);
+    }
+    if (var == 1) return launch_xpass_t<1, 0>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, sched, cost_free, s);
+    if (var == 2) return launch_xpass_t<2, 0>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, sched, cost_free, s);
+    return launch_xpass_t<0, 0>(bwd, cost_dtype, nbuf, d, tb, nd, tiles, err, sched, cost_free, s);
 }
 
 cudaError_t launch_small(const SmallDesc *d, int nd, int cost_dtype, int want_grad, int max_n,

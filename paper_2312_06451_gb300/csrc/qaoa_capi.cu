@@ -90,6 +90,7 @@ struct LaunchRec {
     CUtensorMap tm[4];  // A_hi, A_lo, B_hi, B_lo
     int sched_idx = -1;  // pass launches: tile counter slot
     int cost_free = 0;   // pass launches: no descriptor reads the cost
+    int fused = 0;       // pass launches: round-boundary passes (PF_FUSED)
     double *mean_out = nullptr;  // LK_COST_MEAN: where the cost mean goes
     // grouped (block-diagonal) products and orbit kernels
     int grouped = 0, n_mtiles = 0, lda = 0, ldb = 0;
@@ -173,6 +174,20 @@ int env_int(const char *name, int dflt, int lo, int hi) {
     const int x = std::atoi(v);
     return (x < lo || x > hi) ? dflt : x;
 }
+// Round-boundary fusion of the X-mixer passes (QAOA_FUSE=0 turns it off, for
+// comparison runs).
+bool fusion_enabled() {
+    static const int v = env_int("QAOA_FUSE", 1, 0, 1);
+    return v != 0;
+}
+
+// Tile buffers of the round-boundary adjoint passes (QAOA_FUSED_NBUF overrides
+// it for tuning sweeps: 1 or 2).
+int fused_bwd_nbuf() {
+    static const int v = env_int("QAOA_FUSED_NBUF", 1, 1, 2);
+    return v;
+}
+
 int min_contig() {
     static const int c = env_int("QAOA_MIN_CONTIG", kCminDefault, 4, 8);
     return c;
@@ -375,6 +390,7 @@ struct UnitLayout {
     int ckpt;        // QAOA_CKPT_* actually used
     int vecs;        // state vectors held in scratch
     int nb_bc, nb_bg;  // adjoint tile buffers (contiguous / gathered passes)
+    bool fused;      // round-boundary passes fused (alternating group order)
 };
 
 qaoa_xtune default_xtune(int n, int dt) {
@@ -394,9 +410,16 @@ qaoa_xtune tune_for(const qaoa_ctx *ctx, int n, int dt) {
     return it != ctx->xtune.end() ? it->second : default_xtune(n, dt);
 }
 
+// Forward passes of a unit: P per round, one fewer per round boundary when
+// the boundary passes are fused.
+int forward_passes(const UnitLayout &L, int p) {
+    const int P = (int)L.gf.size();
+    return L.fused ? p * P - (p - 1) : p * P;
+}
+
 int layout_vecs(const UnitLayout &L, int p, bool grad) {
     if (!grad) return 1;
-    if (L.ckpt == QAOA_CKPT_PASS) return 1 + p * (int)L.gf.size();
+    if (L.ckpt == QAOA_CKPT_PASS) return 1 + forward_passes(L, p);
     if (L.ckpt == QAOA_CKPT_ROUND) return 2 + (p - 1);
     return 2;
 }
@@ -417,6 +440,9 @@ UnitLayout layout_for(const qaoa_ctx *ctx, const Unit &u, bool grad, int ckpt) {
     L.stride = std::max<int64_t>(L.tiles_f, (int64_t)L.gb.size() * (u.ma ? kPassTileBits : 1) * L.tiles_b) *
                kPassWarps;
     L.ckpt = grad ? (u.gm ? QAOA_CKPT_PASS : ckpt) : QAOA_CKPT_NONE;  // general mixer: per-pass only
+    // fused round boundaries: transverse field, per-pass checkpoints (or no gradient)
+    L.fused = fusion_enabled() && !u.ma && !u.gm && L.gf.size() >= 2 && u.p >= 2 &&
+              (!grad || L.ckpt == QAOA_CKPT_PASS);
     L.vecs = layout_vecs(L, u.p, grad);
     L.nb_bc = t.nbuf_bwd_contig;
     L.nb_bg = t.nbuf_bwd_gather;
@@ -446,13 +472,13 @@ double pass_bytes(const PassDesc &d, int bwd, int cost_bytes) {
     if (!bwd) {
         if (!(d.flags & PF_GEN_INIT)) b += 8;
         if (d.psi_out) b += 8;
-        if (d.flags & PF_PHASE) b += cost_bytes;
+        if (d.flags & (PF_PHASE | PF_FUSED)) b += cost_bytes;
         if (d.flags & PF_E) b += cost_bytes;
     } else {
         b += 8;  // psi
         if (!(d.flags & PF_LAM_FROM_C)) b += 8;
         else b += cost_bytes;
-        if (d.flags & PF_PHASE) b += cost_bytes;
+        if (d.flags & (PF_PHASE | PF_FUSED)) b += cost_bytes;
         if (d.psi_out) b += 8;
         if (d.lam_out) b += 8;
     }
@@ -530,6 +556,84 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
                 if (j == 0) d.part_gamma = part + (int64_t)(1 + p + k) * L.stride;
                 bwd.push_back(d);
             }
+        }
+        return;
+    }
+    if (L.fused) {
+        // Alternating group order: even rounds run groups 0 .. P-1, odd rounds
+        // P-1 .. 0, so round k ends on the group round k+1 starts with and the
+        // two meet in one round-boundary pass (PF_FUSED), which also applies
+        // round k+1's phase.  Forward pass j writes checkpoint j (gradients)
+        // or works in place on W (expectation only).
+        struct FP {
+            int g, k, fused;  // group, round (fused: rounds k and k+1)
+        };
+        std::vector<FP> seq;
+        auto group_at = [&](int k, int q) { return (k & 1) ? Pf - 1 - q : q; };  // q-th group of round k
+        for (int k = 0; k < p; k++)
+            for (int q = (k == 0 ? 0 : 1); q < Pf; q++)
+                seq.push_back({group_at(k, q), k, (q == Pf - 1 && k < p - 1) ? 1 : 0});
+        const int J = (int)seq.size();
+        auto pj = [&](int j) { return CK + (int64_t)j * N; };
+        auto slot = [&](int k, int g) {  // round k's beta partial slot of group g
+            const int q = (k & 1) ? Pf - 1 - g : g;
+            return part + (int64_t)(1 + k) * L.stride + (int64_t)q * bslot;
+        };
+        auto base_desc = [&](const FP &f) {
+            PassDesc d;
+            std::memset(&d, 0, sizeof(d));
+            fill_geometry(d, u.n, L.T_f, L.gf[f.g]);
+            d.cost = u.cost;
+            d.coef = coef + (int64_t)f.k * nbq;
+            const int tk = f.fused ? f.k + 1 : f.k;  // the round whose phase the pass applies
+            d.table = table ? table + (int64_t)tk * kPhaseTable : nullptr;
+            d.amp0 = amp0;
+            if (f.fused) {
+                d.flags |= PF_FUSED;
+                d.coef2 = coef + (int64_t)(f.k + 1) * nbq;
+            }
+            return d;
+        };
+        for (int j = 0; j < J; j++) {
+            PassDesc d = base_desc(seq[j]);
+            if (j == 0) {
+                d.flags |= PF_PHASE;
+                if (u.init) {
+                    d.psi_in = u.init;
+                    d.flags |= PF_TWIST_IN;
+                } else {
+                    d.flags |= PF_GEN_INIT;
+                }
+            } else {
+                d.psi_in = grad ? pj(j - 1) : W;
+            }
+            if (j == J - 1) {
+                d.flags |= PF_E;
+                d.part_E = part;
+            }
+            d.psi_out = grad ? pj(j) : (j == J - 1 ? nullptr : W);
+            fwd.push_back(d);
+        }
+        if (!grad) return;
+        for (int j = J - 1; j >= 0; j--) {
+            const FP &f = seq[j];
+            PassDesc d = base_desc(f);
+            d.psi_in = pj(j);
+            if (j == J - 1) d.flags |= PF_LAM_FROM_C;
+            else d.lam_in = Lam;
+            d.lam_out = j > 0 ? Lam : nullptr;
+            if (f.fused) {
+                d.part_beta = slot(f.k + 1, f.g);
+                d.part_beta2 = slot(f.k, f.g);
+                d.part_gamma = part + (int64_t)(1 + p + f.k + 1) * L.stride;
+            } else {
+                d.part_beta = slot(f.k, f.g);
+            }
+            if (j == 0) {
+                d.flags |= PF_PHASE;
+                d.part_gamma = part + (int64_t)(1 + p) * L.stride;
+            }
+            bwd.push_back(d);
         }
         return;
     }
@@ -1026,25 +1130,36 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         // ---- state memory: pass units grouped by launch shape, admitted in waves
         struct GKey {
             int Tf, Tb, Pf, Pb, p, dt, nbc, nbg, var;  // var: 0 X, 1 multi-angle, 2 general X mixer
+            int fused;
             bool operator<(const GKey &o) const {
-                return std::tie(Tf, Tb, Pf, Pb, p, dt, nbc, nbg, var) <
-                       std::tie(o.Tf, o.Tb, o.Pf, o.Pb, o.p, o.dt, o.nbc, o.nbg, o.var);
+                return std::tie(Tf, Tb, Pf, Pb, p, dt, nbc, nbg, var, fused) <
+                       std::tie(o.Tf, o.Tb, o.Pf, o.Pb, o.p, o.dt, o.nbc, o.nbg, o.var, o.fused);
             }
         };
-        std::map<GKey, std::vector<int>> groups;
-        for (int i = 0; i < nu; i++) {
-            if (units[i].mixer_kind != QAOA_MIXER_X || units[i].n <= smax) continue;
-            const UnitLayout &L = lay[i];
-            groups[{L.T_f, L.T_b, (int)L.gf.size(), (int)L.gb.size(), units[i].p, units[i].cost_dtype, L.nb_bc,
-                    L.nb_bg, units[i].ma ? 1 : (units[i].gm ? 2 : 0)}]
-                .push_back(i);
-        }
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
         const size_t held = ctx->bufs.count("state") ? ctx->bufs["state"].bytes : 0;
         const double budget_d = (double)(free_b + held) * 0.92 - 1.0 * (1ull << 30);
         size_t budget = budget_d > 0 ? (size_t)budget_d : 0;
         if (ctx->state_limit >= 0) budget = std::min(budget, (size_t)ctx->state_limit);
+        // fused round boundaries need per-pass checkpoints: a unit whose
+        // checkpoints do not fit runs the unfused schedule (and may then step
+        // down to fewer checkpoints below)
+        for (int i = 0; i < nu; i++) {
+            if (units[i].mixer_kind != QAOA_MIXER_X || units[i].n <= smax || !lay[i].fused || !grad) continue;
+            if (align_up((size_t)lay[i].vecs * (sizeof(float2) << units[i].n)) > budget) {
+                lay[i].fused = false;
+                lay[i].vecs = layout_vecs(lay[i], units[i].p, grad);
+            }
+        }
+        std::map<GKey, std::vector<int>> groups;
+        for (int i = 0; i < nu; i++) {
+            if (units[i].mixer_kind != QAOA_MIXER_X || units[i].n <= smax) continue;
+            const UnitLayout &L = lay[i];
+            groups[{L.T_f, L.T_b, (int)L.gf.size(), (int)L.gb.size(), units[i].p, units[i].cost_dtype, L.nb_bc,
+                    L.nb_bg, units[i].ma ? 1 : (units[i].gm ? 2 : 0), L.fused ? 1 : 0}]
+                .push_back(i);
+        }
         // waves: consecutive units of a group whose states fit the budget together
         struct Wave {
             GKey gk;
@@ -1220,7 +1335,8 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             const int cb = dt == QAOA_COST_U8 ? 1 : 4;
             const bool ld_psi = bwd || !(d.flags & PF_GEN_INIT);
             const bool ld_lam = bwd && !(d.flags & PF_LAM_FROM_C);
-            const bool ld_cost = bwd ? (d.flags & (PF_LAM_FROM_C | PF_PHASE)) : (d.flags & (PF_PHASE | PF_E));
+            const bool ld_cost = bwd ? (d.flags & (PF_LAM_FROM_C | PF_PHASE | PF_FUSED))
+                                     : (d.flags & (PF_PHASE | PF_E | PF_FUSED));
             if (ld_psi) d.tm_psi = map_for(d.psi_in, d.n, d.c, lo, 8);
             if (ld_lam) d.tm_lam = map_for(d.lam_in, d.n, d.c, lo, 8);
             if (ld_cost) d.tm_cost = map_for(d.cost, d.n, d.c, lo, cb);
@@ -1283,7 +1399,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                     }
                 }
             }
-            const int nfwd = gk.p * gk.Pf;
+            const int nfwd = gk.fused ? gk.p * gk.Pf - (gk.p - 1) : gk.p * gk.Pf;
             for (size_t s = 0; s < steps.size(); s++) {
                 const bool bwd = (int)s >= nfwd;
                 const int T = bwd ? gk.Tb : gk.Tf;
@@ -1300,6 +1416,10 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 r.bwd = bwd;
                 r.cost_dtype = gk.dt;
                 r.nbuf = bwd ? (steps[s][0].c >= kPassTileBits ? gk.nbc : gk.nbg) : 2;
+                // round-boundary adjoint passes: one buffer and two CTAs per SM
+                // (measured at n = 28: 2.72 ms a launch against 3.22 with two
+                // buffers and one CTA; they are bound by SM latency, not loads)
+                if (bwd && (steps[s][0].flags & PF_FUSED)) r.nbuf = fused_bwd_nbuf();
                 r.var = gk.var;
                 r.desc_off = put(steps[s].data(), sizeof(PassDesc) * steps[s].size());
                 xpass_descs.push_back({r.desc_off, (int)steps[s].size()});
@@ -1308,16 +1428,18 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 r.tiles = tb.back();
                 r.bytes = bytes;
                 r.sched_idx = n_sched++;
+                r.fused = (steps[s][0].flags & PF_FUSED) ? 1 : 0;
                 {
-                    const uint32_t cost_flags = bwd ? (PF_LAM_FROM_C | PF_PHASE) : (PF_PHASE | PF_E);
+                    const uint32_t cost_flags =
+                        bwd ? (PF_LAM_FROM_C | PF_PHASE | PF_FUSED) : (PF_PHASE | PF_E | PF_FUSED);
                     r.cost_free = 1;
                     for (const PassDesc &pd : steps[s])
                         if (pd.flags & cost_flags) r.cost_free = 0;
                 }
                 char nm[64];
                 const int c0 = steps[s][0].c;
-                snprintf(nm, sizeof(nm), "xpass%s_%s_%s_%s", gk.var == 1 ? "_ma" : (gk.var == 2 ? "_gm" : ""),
-                         bwd ? "bwd" : "fwd",
+                snprintf(nm, sizeof(nm), "xpass%s_%s%s_%s_%s", gk.var == 1 ? "_ma" : (gk.var == 2 ? "_gm" : ""),
+                         bwd ? "bwd" : "fwd", (steps[s][0].flags & PF_FUSED) ? "_fused" : "",
                          c0 >= kPassTileBits ? "contig" : (c0 >= 6 ? "gather_wide" : "gather"),
                          dtype_name(gk.dt));
                 r.fam = family(ctx, nm);
@@ -1705,7 +1827,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         case LK_XPASS:
             e = launch_xpass(r.bwd, r.cost_dtype, r.nbuf, r.var, reinterpret_cast<const PassDesc *>(db + r.desc_off),
                              reinterpret_cast<const uint32_t *>(db + r.tb_off), r.ndesc, r.tiles,
-                             ctx->d_err, d_sched + r.sched_idx, r.cost_free, ctx->stream);
+                             ctx->d_err, d_sched + r.sched_idx, r.cost_free, r.fused, ctx->stream);
             break;
         case LK_EIG_INIT:
             e = launch_eig_init(r.iX, r.iX_lo, r.ick0, r.ep.M, r.ep.ld, r.ep.nsets, r.ep.cost, r.ep.cost_dtype,
