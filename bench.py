@@ -823,6 +823,14 @@ def roofline(W, stats, gemm, steps):
                 "launch_ms": per_launch_ms}
     tot = sum(stats[k]["total_ms"] for k in fams)
     roof["share_of_kernel_time"] = st["total_ms"] / tot if tot else None
+    if roof["bound"] == "hbm":
+        # the whole step: every kernel's algorithmic bytes over the profiled
+        # step time (kernel times summed; launch gaps excluded)
+        step_bytes = sum(stats[k]["algo_bytes"] for k in fams) / steps
+        step_ms = tot / steps
+        roof["step"] = {"algo_bytes": step_bytes, "kernel_ms": step_ms,
+                        "achieved": step_bytes / (step_ms * 1e-3) / 1e9,
+                        "frac": step_bytes / (step_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
     return roof
 
 
