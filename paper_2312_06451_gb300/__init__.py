@@ -27,7 +27,7 @@ __all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError", "p
            "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched",
            "qaoa_gradient_small_noalloc", "ring_eigen_mixer", "clique_eigen_mixer", "xy_eigen_mixer",
            "save_eigen_mixer", "load_eigen_mixer", "GeneralXMixer", "x_terms_mixer", "grover_x_mixer",
-           "krawtchouk_weights", "EigenSymMixer", "xy_block_hamiltonians", "xy_sym_mixer"]
+           "krawtchouk_weights", "EigenSymMixer", "xy_block_hamiltonians", "xy_sym_mixer", "BatchedCall"]
 
 _MIXER_IDS = itertools.count(1)
 
@@ -448,6 +448,15 @@ class Context:
         jobs: list of dicts with keys cost, mixer, angles (n_sets x 2p float64
         CUDA tensor), E (n_sets float64 CUDA tensor), grad (n_sets x 2p, when
         want_grad) and optionally init.  Asynchronous on the context stream."""
+        self.batched_call(jobs, want_grad).run()
+
+    def batched_call(self, jobs, want_grad: bool = False) -> "BatchedCall":
+        """The same call with its job list marshalled once: run() re-issues it
+        on the same tensors (new angles copied into them in place), which
+        takes the per-call argument handling off small problems."""
+        return BatchedCall(self, jobs, want_grad)
+
+    def _job_array(self, jobs):
         arr = (B.QaoaJob * len(jobs))()
         keep = []
         for i, j in enumerate(jobs):
@@ -465,7 +474,8 @@ class Context:
             arr[i] = B.QaoaJob(cost.data_ptr(), _cost_dtype(cost), ctypes.pointer(mx.struct), p, n_sets,
                                ang.data_ptr(), E.data_ptr(), None if G is None else G.data_ptr(),
                                None if init is None else init.data_ptr())
-        self._check(self._lib.qaoa_expectation_batched(self._h, len(jobs), arr, 1 if want_grad else 0))
+            keep.extend([ang, E, G, cost, init])
+        return arr, keep
 
     def check_bounded_wait(self):
         """qaoa_check_bounded_wait: raises QAOAError with status
@@ -493,6 +503,22 @@ class Context:
 
     def scratch_bytes(self) -> int:
         return int(self._lib.qaoa_scratch_bytes(self._h))
+
+
+class BatchedCall:
+    """A qaoa_expectation_batched call prepared once (Context.batched_call):
+    the job structs point at the given tensors, which it keeps alive; run()
+    enqueues the call again.  Asynchronous on the context stream."""
+
+    def __init__(self, ctx: Context, jobs, want_grad: bool = False):
+        self._ctx = ctx
+        self._arr, self._keep = ctx._job_array(jobs)
+        self._n = len(jobs)
+        self._grad = 1 if want_grad else 0
+
+    def run(self):
+        c = self._ctx
+        c._check(c._lib.qaoa_expectation_batched(c._h, self._n, self._arr, self._grad))
 
 
 def _rounds(mixer, n_angles: int) -> int:

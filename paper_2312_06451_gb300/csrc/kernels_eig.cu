@@ -598,6 +598,207 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__
                      : "memory");
 }
 
+// Persistent grouped (block-diagonal) variant: one CTA per SM walks the tile
+// table (tiles c, c + grid, ...; the table is sorted by K extent) with the
+// same TMA ring, MMA chain and per-chunk drain as gemm_tc_kernel.  TMEM is
+// allocated once and the barrier phases run on across tiles, so the TMA and
+// MMA warps start the next tile while the draining warps run this tile's
+// epilogue; the epilogue's per-set sums use a named barrier of the draining
+// warps only.
+namespace tc {
+// barrier of the draining warps only (named barrier 1)
+__device__ __forceinline__ void drain_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * NDRAIN) : "memory"); }
+// the same barrier, returning whether any draining thread passed true
+__device__ __forceinline__ bool drain_sync_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(32 * NDRAIN)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ bool failed(const int *f) { return *reinterpret_cast<const volatile int *>(f) != 0; }
+}  // namespace tc
+
+__global__ void __launch_bounds__(tc::NT, 1)
+gemm_tc_grouped_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                       const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int ntn,
+                       int ntiles, EpiArgs E, const GroupTile *__restrict__ gt, int *err) {
+    using tc::BKF;
+    using tc::kStage;
+    using tc::kTileA;
+    using tc::kTileB;
+    using tc::STAGES;
+    constexpr int TBN = tc::BN;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf[tc::NACC], acce[tc::NACC];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    __shared__ float red[4][TBN / 2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&tmem_base)),
+                     "r"(tc::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        for (int st = 0; st < STAGES; st++) {
+            tc::mbar_init(tc::su32(&full[st]), 1);
+            tc::mbar_init(tc::su32(&empty[st]), 1);
+        }
+        for (int b = 0; b < tc::NACC; b++) {
+            tc::mbar_init(tc::su32(&accf[b]), 1);
+            tc::mbar_init(tc::su32(&acce[b]), tc::NDRAIN);
+        }
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_base;
+    int issued = 0;  // producer: chunks whose loads were started
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int g = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !tc::failed(&s_fail); tile += gridDim.x) {
+                const GroupTile G = gt[tile / ntn];
+                const int n0 = (tile % ntn) * TBN, nk = G.kext / BKF;
+                for (int kb = 0; kb < nk; kb++, g++) {
+                    const int st = g % STAGES;
+                    if (g >= STAGES && !tc::mbar_wait(tc::su32(&empty[st]), ((g / STAGES) & 1) ^ 1)) {
+                        atomicExch(&s_fail, 1);
+                        break;
+                    }
+                    const uint32_t base = tc::su32(smem + st * kStage);
+                    const uint32_t fb = tc::su32(&full[st]);
+                    tc::mbar_expect(fb, kStage);
+                    const int kx = kb * BKF;
+                    tc::tma_2d(base, &tmAh, kx, G.a_row, fb);
+                    tc::tma_2d(base + kTileA, &tmAl, kx, G.a_row, fb);
+                    tc::tma_2d(base + 2 * kTileA, &tmBh, G.k_off + kx, n0, fb);
+                    tc::tma_2d(base + 2 * kTileA + kTileB, &tmBl, G.k_off + kx, n0, fb);
+                    issued = g + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int g = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !tc::failed(&s_fail); tile += gridDim.x) {
+                const int nk = gt[tile / ntn].kext / BKF;
+                for (int kb = 0; kb < nk; kb++, g++) {
+                    const int st = g % STAGES, b = g % tc::NACC;
+                    if (g >= tc::NACC && !tc::mbar_wait(tc::su32(&acce[b]), ((g / tc::NACC) & 1) ^ 1)) {
+                        atomicExch(&s_fail, 1);
+                        break;
+                    }
+                    if (!tc::mbar_wait(tc::su32(&full[st]), (g / STAGES) & 1)) {
+                        atomicExch(&s_fail, 1);
+                        break;
+                    }
+                    tc::fence_after();
+                    const uint32_t base = tc::su32(smem + st * kStage);
+                    const uint32_t d = tmem + (uint32_t)(b * TBN);
+#pragma unroll
+                    for (int kk = 0; kk < BKF / 8; kk++) {
+                        const uint64_t ah = tc::sdesc(base + kk * 32), al = tc::sdesc(base + kTileA + kk * 32);
+                        const uint64_t bh = tc::sdesc(base + 2 * kTileA + kk * 32),
+                                       bl = tc::sdesc(base + 2 * kTileA + kTileB + kk * 32);
+                        tc::mma_tf32(d, al, bh, tc::kIdesc, kk ? 1u : 0u);
+                        tc::mma_tf32(d, ah, bl, tc::kIdesc, 1u);
+                        tc::mma_tf32(d, ah, bh, tc::kIdesc, 1u);
+                    }
+                    tc::mma_commit(tc::su32(&empty[st]));
+                    tc::mma_commit(tc::su32(&accf[b]));
+                }
+            }
+        }
+    } else {
+        // draining warps: warp w reads accumulator rows (TMEM lanes) 32 (w % 4) ..
+        // and columns kCols * ch .. (ch = which of the quarter's warps)
+        constexpr int kCols = TBN / (tc::NDRAIN / 4);
+        const uint32_t lrow = (uint32_t)((warp & 3) * 32) << 16;
+        const int ch = (warp - 2) >> 2, rq = warp & 3, dt = tid - 64;
+        int g = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const GroupTile G = gt[tile / ntn];
+            const int n0 = (tile % ntn) * TBN, nk = G.kext / BKF;
+            float acc[kCols];
+#pragma unroll
+            for (int c = 0; c < kCols; c++) acc[c] = 0.f;
+            bool ok = !tc::failed(&s_fail);
+            for (int kb = 0; kb < nk && ok; kb++, g++) {
+                const int b = g % tc::NACC;
+                if (!tc::mbar_wait(tc::su32(&accf[b]), (g / tc::NACC) & 1)) {
+                    atomicExch(&s_fail, 1);
+                    ok = false;
+                    break;
+                }
+                tc::fence_after();
+                uint32_t r[kCols / 16][16];
+#pragma unroll
+                for (int q = 0; q < kCols / 16; q++)
+                    tc::tmem_ld16(tmem + lrow + (uint32_t)(b * TBN + ch * kCols + 16 * q), r[q]);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < kCols / 16; q++)
+#pragma unroll
+                    for (int i = 0; i < 16; i++) acc[16 * q + i] += __uint_as_float(r[q][i]);
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(tc::su32(&acce[b]));
+            }
+            // the draining warps agree on whether the tile completed
+            if (tc::drain_sync_or(!ok || tc::failed(&s_fail))) break;
+            const int m = G.out_row + rq * 32 + lane;
+#pragma unroll
+            for (int q = 0; q < kCols / 2; q++) {
+                const int qq = ch * (kCols / 2) + q;  // set within the tile
+                const int s = n0 / 2 + qq;
+                float contrib = 0.f;
+                if (m < G.row_end && s < E.nsets) contrib = epi_elem(E, m, s, make_float2(acc[2 * q], acc[2 * q + 1]));
+                if (E.part) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, o);
+                    if (lane == 0) red[rq][qq] = contrib;
+                }
+            }
+            if (E.part) {
+                tc::drain_sync();
+                if (dt < TBN / 2) {
+                    const int s = n0 / 2 + dt;
+                    const double t =
+                        ((double)red[0][dt] + (double)red[1][dt]) + ((double)red[2][dt] + (double)red[3][dt]);
+                    if (s < E.nsets) E.part[(size_t)s * E.part_stride + G.part_idx] = t;
+                }
+                tc::drain_sync();  // red is free for the next tile
+            }
+        }
+    }
+    __syncwarp();
+    const bool failed = __syncthreads_or(s_fail) != 0;
+    if (failed) {
+        if (tid == 0) atomicOr(err, DERR_TIMEOUT);
+        // let started loads land before the block exits
+        if (warp == 0 && lane == 0)
+            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; kb++)
+                tc::mbar_wait(tc::su32(&full[kb % STAGES]), (kb / STAGES) & 1);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::kTmemCols)
+                     : "memory");
+}
+
 // Initial state of every set with the first phase separator applied:
 // X = e^{-i g_1 C} psi_0 (psi_0 uniform 1/sqrt(D) or a user complex64 state);
 // also keeps psi_0 as checkpoint 0.
@@ -675,6 +876,7 @@ __global__ void __launch_bounds__(kOrbitThreads) orbit_kernel(OrbitTabs T, Orbit
         const RoundCoef cf = A.coef[s * A.coef_stride + A.round];
         const size_t row_re = (size_t)(2 * s) * A.ldp, row_im = row_re + A.ldp;
         float ar[RMAX], ai[RMAX], cr[RMAX], ci[RMAX];
+        auto vpos = [&](int a) -> int { return T.vec_pos[s0 + a]; };
         auto cost_of = [&](int j) -> float {
             const int idx = T.members[s0 + j];
             return A.cost_dtype == 0 ? __ldg(reinterpret_cast<const float *>(A.cost) + idx)
@@ -685,42 +887,48 @@ __global__ void __launch_bounds__(kOrbitThreads) orbit_kernel(OrbitTabs T, Orbit
 #pragma unroll
             for (int a = 0; a < RMAX; a++) {
                 if (a < r) {
-                    const int pos = T.vec_pos[s0 + a];
+                    const int pos = vpos(a);
                     cr[a] = in[row_re + pos];
                     ci[a] = in[row_im + pos];
                 }
             }
+            // member sums accumulated side by side (independent FMA chains)
 #pragma unroll
-            for (int j = 0; j < RMAX; j++) {
-                if (j >= r) continue;
-                float sr = 0.f, si = 0.f;
-#pragma unroll
-                for (int a = 0; a < RMAX; a++) {
-                    if (a >= r) continue;
-                    const float m = M[j * r + a];
-                    sr = fmaf(m, cr[a], sr);
-                    si = fmaf(m, ci[a], si);
-                }
-                xr[j] = sr;
-                xi[j] = si;
-            }
-        };
-        // c = T^T a written to `out` (with the tf32 split when out_lo)
-        auto from_amp = [&](const float (&xr)[RMAX], const float (&xi)[RMAX], float *out, float *out_lo) {
+            for (int j = 0; j < RMAX; j++) xr[j] = xi[j] = 0.f;
 #pragma unroll
             for (int a = 0; a < RMAX; a++) {
                 if (a >= r) continue;
-                float sr = 0.f, si = 0.f;
 #pragma unroll
                 for (int j = 0; j < RMAX; j++) {
                     if (j >= r) continue;
                     const float m = M[j * r + a];
-                    sr = fmaf(m, xr[j], sr);
-                    si = fmaf(m, xi[j], si);
+                    xr[j] = fmaf(m, cr[a], xr[j]);
+                    xi[j] = fmaf(m, ci[a], xi[j]);
                 }
-                const int pos = T.vec_pos[s0 + a];
-                put(out, out_lo, row_re + pos, sr);
-                put(out, out_lo, row_im + pos, si);
+            }
+        };
+        // c = T^T a written to `out` (with the tf32 split when out_lo)
+        auto from_amp = [&](const float (&xr)[RMAX], const float (&xi)[RMAX], float *out, float *out_lo) {
+            // coefficient sums accumulated side by side in cr / ci (free here)
+#pragma unroll
+            for (int a = 0; a < RMAX; a++) cr[a] = ci[a] = 0.f;
+#pragma unroll
+            for (int j = 0; j < RMAX; j++) {
+                if (j >= r) continue;
+#pragma unroll
+                for (int a = 0; a < RMAX; a++) {
+                    if (a >= r) continue;
+                    const float m = M[j * r + a];
+                    cr[a] = fmaf(m, xr[j], cr[a]);
+                    ci[a] = fmaf(m, xi[j], ci[a]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < RMAX; a++) {
+                if (a >= r) continue;
+                const int pos = vpos(a);
+                put(out, out_lo, row_re + pos, cr[a]);
+                put(out, out_lo, row_im + pos, ci[a]);
             }
         };
         if (MODE == ORB_INIT) {
@@ -763,6 +971,15 @@ __global__ void __launch_bounds__(kOrbitThreads) orbit_kernel(OrbitTabs T, Orbit
             }
             if (A.out) from_amp(ar, ai, A.out, A.out_lo);
         } else {  // ORB_BWD
+            // two matrices to read: start the second one's lines toward L2
+            // while the first is fetched and transformed
+#pragma unroll
+            for (int a = 0; a < RMAX; a++) {
+                if (a >= r) continue;
+                const int pos = vpos(a);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.in + row_re + pos));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.in + row_im + pos));
+            }
             float pr[RMAX], pi[RMAX];
             to_amp(A.in_psi, pr, pi);
             to_amp(A.in, ar, ai);
@@ -999,10 +1216,16 @@ cudaError_t launch_eig_gemm_tc_grouped(const CUtensorMap &a_hi, const CUtensorMa
         cudaError_t e = smem_attr_once(gemm_tc_kernel, (int)tc::kSmem, attr_done);
         if (e != cudaSuccess) return e;
     }
+    static int attr_done_p[kMaxDevices];
+    {
+        cudaError_t e = smem_attr_once(gemm_tc_grouped_kernel, (int)tc::kSmem, attr_done_p);
+        if (e != cudaSuccess) return e;
+    }
     const int ntn = Np / tc::BN;
     const int tiles = n_mtiles * ntn;
-    SplitArgs sp{tiles, 1, nullptr, nullptr};  // no split of the last wave
-    gemm_tc_kernel<<<tiles, tc::NT, tc::kSmem, s>>>(a_hi, a_lo, b_hi, b_lo, 0, ntn, to_args(P), sp, err, d_tiles);
+    const int grid = std::min(tiles, eig_split_max_tail());  // one CTA per SM
+    gemm_tc_grouped_kernel<<<grid, tc::NT, tc::kSmem, s>>>(a_hi, a_lo, b_hi, b_lo, ntn, tiles, to_args(P), d_tiles,
+                                                           err);
     return cudaGetLastError();
 }
 
