@@ -108,12 +108,24 @@ enum {
                              d_lambda the D float64 eigenvalues block after block,
                              k the Hamming weight.  Same results as QAOA_MIXER_EIGEN
                              with the full V, at about 2/n of its product work. */
-    QAOA_MIXER_X_GENERAL = 3 /* a sum of products of Pauli X (Sec. 2.1),
+    QAOA_MIXER_X_GENERAL = 3, /* a sum of products of Pauli X (Sec. 2.1),
                              f(X) = sum_S c_|S| prod_{i in S} X_i on all 2^n states,
                              given by its Hadamard-basis eigenvalues: d_lambda holds
                              n + 1 float64 values d_w = sum_k c_k K_k(w) (K_k the
                              Krawtchouk polynomial); d_w = [w = 0] is the Grover
                              mixer |+><+|.  Angles and gradients as for X. */
+    QAOA_MIXER_GROVER = 5    /* the Grover mixer H_M = |u><u| (Sec. 2.4), u the uniform
+                             superposition over the dim states the cost vector lists
+                             (all 2^n, the binom(n, k) weight-k states, or any other
+                             feasible set), applied as the rank-one update
+                             e^{-i b H_M} phi = phi + (e^{-i b} - 1) <u|phi> u: one
+                             streaming pass per round and direction.  dim >= 1; n is
+                             informational; d_V, d_lambda, k, id unused.  d_init,
+                             when given, must be 16-byte aligned.  Angles and
+                             gradients as for X.  Gradient runs keep p + 1 state
+                             vectors when they fit (QAOA_CKPT_ROUND or _PASS), else
+                             two (QAOA_CKPT_NONE: each adjoint pass also undoes the
+                             forward round on the state). */
 };
 
 /* Hadamard-basis weights of a general X mixer (Sec. 2.1: a mixer written as a

@@ -15,6 +15,7 @@ uniform superposition over the feasible set.
 from __future__ import annotations
 
 import ctypes
+import math
 import itertools
 
 import numpy as np
@@ -26,7 +27,7 @@ from ._binding import QAOAError  # noqa: F401
 __all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError", "pass_schedule",
            "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched",
            "qaoa_gradient_small_noalloc", "ring_eigen_mixer", "clique_eigen_mixer", "xy_eigen_mixer",
-           "save_eigen_mixer", "load_eigen_mixer", "GeneralXMixer", "x_terms_mixer", "grover_x_mixer",
+           "save_eigen_mixer", "load_eigen_mixer", "GeneralXMixer", "x_terms_mixer", "grover_x_mixer", "GroverMixer",
            "krawtchouk_weights", "EigenSymMixer", "xy_block_hamiltonians", "xy_sym_mixer", "BatchedCall"]
 
 _MIXER_IDS = itertools.count(1)
@@ -115,6 +116,31 @@ def x_terms_mixer(n: int, coeffs: dict, device: int = 0) -> GeneralXMixer:
 def grover_x_mixer(n: int, device: int = 0) -> GeneralXMixer:
     """Grover mixer |+><+| on all 2^n states (Sec. 2.4): d_w = [w = 0]."""
     return GeneralXMixer(n, [1.0] + [0.0] * n, device)
+
+
+class GroverMixer:
+    """Grover mixer |u><u| (Sec. 2.4), u the uniform superposition over the dim
+    states a cost vector lists: all 2^n states, the binom(n, k) weight-k states,
+    or any other feasible set.  Applied as the rank-one update
+    phi + (e^{-i b} - 1) <u|phi> u, one streaming pass per round
+    (QAOA_MIXER_GROVER); n only labels the problem."""
+
+    def __init__(self, dim: int, n: int = 0):
+        self.dim = int(dim)
+        if self.dim < 1:
+            raise ValueError("a Grover mixer needs at least one feasible state")
+        self.n = int(n)
+        self.struct = B.QaoaMixer(B.QAOA_MIXER_GROVER, self.n, self.dim, None, None, 0)
+
+    @classmethod
+    def full(cls, n: int) -> "GroverMixer":
+        """On all 2^n states (u = |+>^n)."""
+        return cls(1 << int(n), n)
+
+    @classmethod
+    def dicke(cls, n: int, k: int) -> "GroverMixer":
+        """On the binom(n, k) Hamming-weight-k states (u = the Dicke state)."""
+        return cls(math.comb(int(n), int(k)), n)
 
 
 class EigenMixer:

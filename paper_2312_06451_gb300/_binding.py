@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "QAOA_OK", 1: "QAOA_ERR_INVALID", 2: "QAOA_ERR_OOM", 3: "QAOA
 QAOA_COST_F32, QAOA_COST_U8 = 0, 1
 QAOA_PROBLEM_MAXCUT, QAOA_PROBLEM_WMAXCUT, QAOA_PROBLEM_SK, QAOA_PROBLEM_DKS, QAOA_PROBLEM_KVC = 0, 1, 2, 3, 4
 QAOA_MIXER_X, QAOA_MIXER_EIGEN, QAOA_MIXER_X_MA, QAOA_MIXER_X_GENERAL, QAOA_MIXER_EIGEN_SYM = 0, 1, 2, 3, 4
+QAOA_MIXER_GROVER = 5
 QAOA_XY_RING, QAOA_XY_CLIQUE = 0, 1
 QAOA_GEMM_FP32_SIMT, QAOA_GEMM_3XTF32, QAOA_GEMM_BF16X3 = 0, 1, 2
 QAOA_CKPT_NONE, QAOA_CKPT_ROUND, QAOA_CKPT_PASS = 0, 1, 2

@@ -362,6 +362,38 @@ cudaError_t launch_dicke_states(int n, int k, int64_t dim, uint64_t *d_out, cuda
 cudaError_t launch_ring_hamiltonian(int n, int k, int64_t dim, double *d_H, cudaStream_t s);
 cudaError_t launch_clique_hamiltonian(int n, int k, int64_t dim, double *d_H, cudaStream_t s);
 
+// Grover mixer as a rank-one update on a stored state vector (kernels_rank1.cu).
+enum R1Mode { R1_FWD = 0, R1_LAST = 1, R1_BWD = 2 };
+enum R1ScalarMode { R1_SFWD = 0, R1_SLAST = 1, R1_SBWD = 2 };
+struct R1Desc {
+    const void *cost;
+    const float2 *init;     // user psi_0 (16-byte aligned) or nullptr: amp0 everywhere
+    const RoundCoef *coef;  // p entries (the round's gamma as g_hi + g_lo)
+    const float2 *table;    // uint8 costs: p * kPhaseTable entries e^{-i gamma_r c}
+    const double *angles;   // beta_0..beta_{p-1}, gamma_0..gamma_{p-1}
+    float2 *phi;            // ckpt: phi_0..phi_{p-1} at stride ld; else one vector
+    float2 *lam;            // gradient runs: the adjoint vector
+    double *part;           // [slot][3] per-block sums (min(tiles, grid) slots)
+    double *scal;           // 4 p + 3 scalars (layout in kernels_rank1.cu)
+    double *E;
+    double *grad;           // 2p, or nullptr
+    int64_t dim;
+    int64_t ld;             // vector stride (even, >= dim)
+    int p;
+    int ckpt;
+    float amp0;
+    int pad;
+};
+int r1_tile_amps();
+uint32_t r1_max_grid();                       // upper bound of r1_grid over modes
+uint32_t r1_grid(int mode, int cost_dtype);   // resident blocks of one pass kernel
+// grid: blocks of the pass (the same value for every pass and scalar launch
+// over one descriptor list: it fixes the slot layout of the partials).
+cudaError_t launch_r1_pass(int mode, int cost_dtype, const R1Desc *d, const uint32_t *tb, int nd, uint32_t tiles,
+                           uint32_t grid, int round, cudaStream_t s);
+cudaError_t launch_r1_scalar(int mode, const R1Desc *d, const uint32_t *tb, int nd, uint32_t grid, int round,
+                             cudaStream_t s);
+
 // Grover-mixer QAOA on cost degeneracies (kernels_grover.cu).
 struct DegLaunch {
     uint64_t up_lo[128], up_hi[128];  // weight-k problems: all neighbours of u

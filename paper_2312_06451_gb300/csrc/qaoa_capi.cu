@@ -53,7 +53,7 @@ struct Unit {
     double *grad;          // device, 2p (gradient runs)
     const float2 *init;    // device or nullptr
     int tsize;             // phase-table entries (uint8 costs)
-    int mixer_kind;        // QAOA_MIXER_X or QAOA_MIXER_EIGEN
+    int mixer_kind;        // QAOA_MIXER_X, _EIGEN, _EIGEN_SYM or _GROVER
     int job;               // job index (eigenbasis sets of one job form one GEMM group)
     int64_t dim;           // feasible-set size
     const float *V;        // eigenbasis mixer: D x D eigenvectors
@@ -67,7 +67,7 @@ struct Unit {
 };
 
 enum LaunchKind { LK_PREP, LK_SMALL, LK_XPASS, LK_REDUCE, LK_EIG_INIT, LK_EIG_GEMM, LK_COST_MEAN, LK_ORBIT,
-                  LK_OPERANDS };
+                  LK_OPERANDS, LK_R1_PASS, LK_R1_SCALAR };
 
 struct LaunchRec {
     int kind;
@@ -92,6 +92,10 @@ struct LaunchRec {
     int cost_free = 0;   // pass launches: no descriptor reads the cost
     int fused = 0;       // pass launches: round-boundary passes (PF_FUSED)
     double *mean_out = nullptr;  // LK_COST_MEAN: where the cost mean goes
+    // Grover-mixer (rank-one) launches: mode, round and the pass grid, which
+    // fixes the slot layout the following scalar launch reads
+    int r1mode = 0, r1round = 0;
+    uint32_t r1grid = 0;
     // grouped (block-diagonal) products and orbit kernels
     int grouped = 0, n_mtiles = 0, lda = 0, ldb = 0;
     const GroupTile *gtiles = nullptr;
@@ -124,6 +128,7 @@ struct Group {
 
 constexpr int kMaxXQubits = 32;   // 32-bit element offsets in the pass kernel
 constexpr int kMaxEigDim = 1 << 16; // feasible states of an eigenbasis mixer
+constexpr int64_t kMaxGroverDim = 1ll << 36;  // feasible states of a Grover (rank-one) mixer
 constexpr int kCminDefault = 4;   // >= 16 contiguous amplitudes = one 128-byte line
 constexpr int kTmaSegBits = 8;    // shorter runs are fetched through a TMA tensor map
 constexpr size_t kAlign = 256;
@@ -1457,6 +1462,166 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                 }
             }
         }
+        // ---- Grover-mixer units: the rank-one update as streaming passes, one
+        // launch per pass over all units of one (p, cost dtype), admitted in
+        // waves under the memory left next to the X-mixer states
+        {
+            std::map<std::pair<int, int>, std::vector<int>> rgroups;
+            for (int i = 0; i < nu; i++)
+                if (units[i].mixer_kind == QAOA_MIXER_GROVER)
+                    rgroups[{units[i].p, units[i].cost_dtype}].push_back(i);
+            if (!rgroups.empty()) {
+                const int64_t tile = r1_tile_amps();
+                const uint32_t gmax = r1_max_grid();
+                const size_t held_r1 = ctx->bufs.count("r1state") ? ctx->bufs["r1state"].bytes : 0;
+                const double rb = (double)(free_b + held + held_r1) * 0.92 - 1.0 * (1ull << 30);
+                size_t r1_budget = rb > 0 ? (size_t)rb : 0;
+                if (ctx->state_limit >= 0) r1_budget = std::min(r1_budget, (size_t)ctx->state_limit);
+                r1_budget = r1_budget > state_need ? r1_budget - state_need : 0;
+                struct RUnit {
+                    int i;
+                    int64_t ld;
+                    int ck;
+                    uint32_t nt;
+                    size_t soff, part_off, scal_off;
+                };
+                struct RWave {
+                    int p, dt;
+                    std::vector<RUnit> us;
+                };
+                std::vector<RWave> rwaves;
+                size_t r1_need = 0, r1_meta = 0;
+                for (auto &kv : rgroups) {
+                    RWave w;
+                    w.p = kv.first.first;
+                    w.dt = kv.first.second;
+                    size_t used = 0;
+                    uint64_t wtiles = 0;
+                    for (int i : kv.second) {
+                        const Unit &u = units[i];
+                        RUnit ru;
+                        ru.i = i;
+                        ru.ld = (u.dim + 63) / 64 * 64;
+                        ru.nt = (uint32_t)((u.dim + tile - 1) / tile);
+                        const size_t vb = (size_t)ru.ld * sizeof(float2);
+                        // p + 1 vectors (phi_0..phi_{p-1} and lambda) with checkpoints,
+                        // else phi and lambda, the adjoint undoing each round on phi
+                        ru.ck = grad && ckpt != QAOA_CKPT_NONE ? 1 : 0;
+                        size_t need = align_up(vb * (grad ? (ru.ck ? u.p + 1 : 2) : 1));
+                        if (need > r1_budget && ru.ck) {
+                            ru.ck = 0;
+                            need = align_up(vb * 2);
+                        }
+                        if (need > r1_budget)
+                            return fail(ctx, QAOA_ERR_OOM,
+                                        "one Grover-mixer angle set of %lld states needs %.2f GiB of state scratch, "
+                                        "%.2f GiB available",
+                                        (long long)u.dim, need / 1073741824.0, r1_budget / 1073741824.0);
+                        if (!w.us.empty() && (used + need > r1_budget || wtiles + ru.nt >= (1ull << 31))) {
+                            rwaves.push_back(w);
+                            w.us.clear();
+                            used = 0;
+                            wtiles = 0;
+                        }
+                        ru.soff = used;
+                        used += need;
+                        wtiles += ru.nt;
+                        ru.part_off = r1_meta;
+                        r1_meta = align_up(r1_meta + sizeof(double) * 3 * std::min<uint32_t>(ru.nt, gmax));
+                        ru.scal_off = r1_meta;
+                        r1_meta = align_up(r1_meta + sizeof(double) * (4 * u.p + 3));
+                        w.us.push_back(ru);
+                        r1_need = std::max(r1_need, used);
+                    }
+                    if (!w.us.empty()) rwaves.push_back(w);
+                }
+                void *d_r1 = nullptr, *d_r1m = nullptr;
+                st = scratch(ctx, "r1state", r1_need, &d_r1);
+                if (st) return st;
+                st = scratch(ctx, "r1meta", r1_meta, &d_r1m);
+                if (st) return st;
+                for (const RWave &w : rwaves) {
+                    std::vector<R1Desc> ds;
+                    std::vector<uint32_t> tb(1, 0);
+                    for (const RUnit &ru : w.us) {
+                        const Unit &u = units[ru.i];
+                        R1Desc d;
+                        std::memset(&d, 0, sizeof(d));
+                        d.cost = u.cost;
+                        d.init = u.init;
+                        d.coef = prep[ru.i].coef;
+                        d.table = prep[ru.i].table;
+                        d.angles = u.angles;
+                        float2 *base = reinterpret_cast<float2 *>(static_cast<char *>(d_r1) + ru.soff);
+                        d.phi = base;
+                        d.lam = grad ? base + (ru.ck ? (int64_t)u.p * ru.ld : ru.ld) : nullptr;
+                        d.part = reinterpret_cast<double *>(static_cast<char *>(d_r1m) + ru.part_off);
+                        d.scal = reinterpret_cast<double *>(static_cast<char *>(d_r1m) + ru.scal_off);
+                        d.E = u.E;
+                        d.grad = grad ? u.grad : nullptr;
+                        d.dim = u.dim;
+                        d.ld = ru.ld;
+                        d.p = u.p;
+                        d.ckpt = ru.ck;
+                        d.amp0 = (float)(1.0 / std::sqrt((double)u.dim));
+                        ds.push_back(d);
+                        tb.push_back(tb.back() + ru.nt);
+                    }
+                    const size_t doff = put(ds.data(), sizeof(R1Desc) * ds.size());
+                    const size_t toff = put(tb.data(), sizeof(uint32_t) * tb.size());
+                    const double cb = w.dt == QAOA_COST_U8 ? 1.0 : 4.0;
+                    // algorithmic bytes of one pass over every unit of the wave
+                    auto pass_bytes_r1 = [&](int mode, int round) {
+                        double b = 0;
+                        for (const RUnit &ru : w.us) {
+                            const Unit &u = units[ru.i];
+                            const double N = (double)u.dim;
+                            double per = cb;  // the cost value
+                            if (mode == R1_FWD) per += (round == 0 && !u.init) ? 8 : 16;
+                            else if (mode == R1_LAST) per += 8;
+                            else {
+                                per += 8 + (round == w.p - 1 ? 0 : 8);  // phi, lambda
+                                if (round > 0) per += 8 + (ru.ck ? 0 : 8);  // lambda (and phi) out
+                            }
+                            b += N * per;
+                        }
+                        return b;
+                    };
+                    const char *mname[3] = {"fwd", "last", "bwd"};
+                    auto add = [&](int mode, int round) {
+                        LaunchRec r;
+                        r.kind = LK_R1_PASS;
+                        r.cost_dtype = w.dt;
+                        r.desc_off = doff;
+                        r.tb_off = toff;
+                        r.ndesc = (int)ds.size();
+                        r.tiles = tb.back();
+                        r.r1mode = mode;
+                        r.r1round = round;
+                        r.r1grid = std::min<uint32_t>(tb.back(), r1_grid(mode, w.dt));
+                        r.bytes = pass_bytes_r1(mode, round);
+                        char nm[48];
+                        snprintf(nm, sizeof(nm), "grover_r1_%s_%s", mname[mode], dtype_name(w.dt));
+                        r.fam = family(ctx, nm);
+                        L.push_back(r);
+                        LaunchRec q;
+                        q.kind = LK_R1_SCALAR;
+                        q.desc_off = doff;
+                        q.tb_off = toff;
+                        q.ndesc = (int)ds.size();
+                        q.r1mode = mode == R1_FWD ? R1_SFWD : (mode == R1_LAST ? R1_SLAST : R1_SBWD);
+                        q.r1round = round;
+                        q.r1grid = r.r1grid;
+                        q.fam = family(ctx, "grover_r1_scalar");
+                        L.push_back(q);
+                    };
+                    for (int k = 0; k < w.p; k++) add(R1_FWD, k);
+                    add(R1_LAST, w.p - 1);
+                    if (grad)
+                        for (int k = w.p - 1; k >= 0; k--) add(R1_BWD, k);
+                }
+            }
+        }
         // ---- eigenbasis-mixer jobs: one GEMM pipeline per job, the job's angle
         // sets as the columns of every product
         {
@@ -1850,6 +2015,16 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         case LK_OPERANDS:
             e = enqueue_operands(r, ctx->stream);
             break;
+        case LK_R1_PASS:
+            e = launch_r1_pass(r.r1mode, r.cost_dtype, reinterpret_cast<const R1Desc *>(db + r.desc_off),
+                               reinterpret_cast<const uint32_t *>(db + r.tb_off), r.ndesc, r.tiles, r.r1grid,
+                               r.r1round, ctx->stream);
+            break;
+        case LK_R1_SCALAR:
+            e = launch_r1_scalar(r.r1mode, reinterpret_cast<const R1Desc *>(db + r.desc_off),
+                                 reinterpret_cast<const uint32_t *>(db + r.tb_off), r.ndesc, r.r1grid, r.r1round,
+                                 ctx->stream);
+            break;
         case LK_COST_MEAN:
             e = launch_cost_mean(r.ep.cost, r.ep.cost_dtype, r.ep.M, r.mean_out, ctx->stream);
             break;
@@ -1898,6 +2073,18 @@ qaoa_status check_args(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const 
         if (!d_cost || ((uintptr_t)d_cost & 15))
             return fail(ctx, QAOA_ERR_INVALID, "d_cost must be a 16-byte aligned device pointer");
         if (d_init && ((uintptr_t)d_init & 7)) return fail(ctx, QAOA_ERR_INVALID, "d_init must be 8-byte aligned");
+        return QAOA_OK;
+    }
+    if (mx->kind == QAOA_MIXER_GROVER) {
+        if (mx->dim < 1 || mx->dim > kMaxGroverDim)
+            return fail(ctx, QAOA_ERR_INVALID, "Grover mixer dim must be in [1, 2^36] (got %lld)", (long long)mx->dim);
+        if (p < 1 || p > 4096) return fail(ctx, QAOA_ERR_INVALID, "p must be in [1, 4096] (got %d)", p);
+        if (cost_dtype != QAOA_COST_F32 && cost_dtype != QAOA_COST_U8)
+            return fail(ctx, QAOA_ERR_INVALID, "unknown cost dtype %d", cost_dtype);
+        if (!d_cost || ((uintptr_t)d_cost & 15))
+            return fail(ctx, QAOA_ERR_INVALID, "d_cost must be a 16-byte aligned device pointer");
+        if (d_init && ((uintptr_t)d_init & 15))
+            return fail(ctx, QAOA_ERR_INVALID, "d_init must be 16-byte aligned");
         return QAOA_OK;
     }
     if (mx->kind != QAOA_MIXER_X && mx->kind != QAOA_MIXER_X_MA && mx->kind != QAOA_MIXER_X_GENERAL)
