@@ -386,11 +386,12 @@ struct R1Desc {
 };
 int r1_tile_amps();
 uint32_t r1_max_grid();                       // upper bound of r1_grid over modes
-uint32_t r1_grid(int mode, int cost_dtype);   // resident blocks of one pass kernel
+uint32_t r1_grid(int mode, int cost_dtype);   // blocks of one pass kernel (persistent: a multiple of the SMs)
 // grid: blocks of the pass (the same value for every pass and scalar launch
 // over one descriptor list: it fixes the slot layout of the partials).
+// err: the device error word (DERR_TIMEOUT when a bounded copy wait gives up).
 cudaError_t launch_r1_pass(int mode, int cost_dtype, const R1Desc *d, const uint32_t *tb, int nd, uint32_t tiles,
-                           uint32_t grid, int round, cudaStream_t s);
+                           uint32_t grid, int round, int *err, cudaStream_t s);
 cudaError_t launch_r1_scalar(int mode, const R1Desc *d, const uint32_t *tb, int nd, uint32_t grid, int round,
                              cudaStream_t s);
 

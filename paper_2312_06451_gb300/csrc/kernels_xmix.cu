@@ -31,6 +31,7 @@
 //   * Partial sums are per tile in float32, combined in float64 in a fixed
 //     order, so results are bitwise reproducible.
 #include "common.cuh"
+#include "bulk.cuh"
 
 #include <math.h>
 
@@ -355,46 +356,7 @@ __device__ __forceinline__ int find_desc(const uint32_t *__restrict__ tile_begin
 }
 
 // ----------------------------------------------------------- TMA / mbarrier
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: gives up after kWaitLimitNs of global time (or kSpinLimit
-// polls), never hangs.
-constexpr uint32_t kSpinLimit = 1u << 22;
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t i = 0; i < kSpinLimit; i++) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 15u) == 15u && global_ns() - t0 > kWaitLimitNs) return false;
-        __nanosleep(32);
-    }
-    return false;
-}
-// One bulk (TMA) copy global -> shared, completing on mbarrier `bar`.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
+// (mbarrier and bulk-copy wrappers: bulk.cuh)
 // One TMA tensor copy of a 4-d box (coordinates c0..c3) global -> shared.
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3,
                                             uint32_t bar) {
@@ -403,12 +365,6 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int 
         "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
         "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
         : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
 // --------------------------------------------------------------------------

@@ -2018,7 +2018,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
         case LK_R1_PASS:
             e = launch_r1_pass(r.r1mode, r.cost_dtype, reinterpret_cast<const R1Desc *>(db + r.desc_off),
                                reinterpret_cast<const uint32_t *>(db + r.tb_off), r.ndesc, r.tiles, r.r1grid,
-                               r.r1round, ctx->stream);
+                               r.r1round, ctx->d_err, ctx->stream);
             break;
         case LK_R1_SCALAR:
             e = launch_r1_scalar(r.r1mode, reinterpret_cast<const R1Desc *>(db + r.desc_off),
