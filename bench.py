@@ -297,6 +297,7 @@ class Workload:
             self.grad = bool(spec["grad"])
             # mixer variant: transverse field, multi-angle, sum of X and XX
             # terms (mixer_X([1, 2])), or the Grover mixer on all 2^n states
+            # (as the rank-one update, or through the general X-mixer passes)
             self.mixer_variant = mixer
             if mixer == "ma":
                 from qaoa_inputs import uniform_angles_ma
@@ -306,6 +307,8 @@ class Workload:
             elif mixer == "terms":
                 self.x_mixer = qg.x_terms_mixer(n, {1: 1.0, 2: 1.0})
             elif mixer == "grover":
+                self.x_mixer = qg.GroverMixer.full(n)
+            elif mixer == "grover_x":
                 self.x_mixer = qg.grover_x_mixer(n)
             if spec["problem"] == "sk":
                 J = w["J"] if n == spec["n"] else sk_couplings(n, BASE_SEED + idx)
@@ -321,7 +324,8 @@ class Workload:
             self.units = spec["n_sets"]
             mix_desc = {"x": "X (transverse field)", "ma": "multi-angle X (one angle per qubit and round)",
                         "terms": "sum_i X_i + sum_{i<j} X_i X_j (half rounds around a weight diagonal)",
-                        "grover": "Grover |+><+| on all 2^n states (half rounds around a weight diagonal)"}[mixer]
+                        "grover": "Grover |+><+| on all 2^n states (rank-one update, one pass per round)",
+                        "grover_x": "Grover |+><+| on all 2^n states (half rounds around a weight diagonal)"}[mixer]
             self.config = {"workload": self.name, "problem": prob, "n": n, "p": p, "mixer": mix_desc,
                            "angle_sets_per_step": spec["n_sets"],
                            "cost_dtype": "f32" if spec["problem"] == "sk" else "u8"}
@@ -332,6 +336,8 @@ class Workload:
         self.run_info.update(getattr(self, "run_info_eig", {}))
         if not self.grad:
             self.run_info["ckpt"] = "none (forward only)"
+        elif getattr(self, "mixer_variant", "x") == "grover":
+            self.run_info["ckpt"] = "every round's phase-separated state phi_r (p + 1 vectors)"
         elif idx == 4:
             self.run_info["ckpt"] = "per-round state checkpoints"
         else:
@@ -412,7 +418,9 @@ class Workload:
             def one_round(nn, cc):
                 if var == "ma":
                     oracle.qaoa_gradient_ma(nn, cc, np.concatenate([a[:nn], a[p * nn:p * nn + 1]]))
-                elif var in ("terms", "grover"):
+                elif var == "grover":
+                    oracle.qaoa_gradient(nn, cc, np.array([a[0], a[p]]), "grover")
+                elif var in ("terms", "grover_x"):
                     w_ = self.x_mixer.weights.cpu().numpy() if nn == n else None
                     if w_ is None:
                         return None
@@ -936,8 +944,9 @@ def main():
                     help="workload 4: the mixer through its cyclic-shift momentum blocks (default) or one dense "
                          "eigendecomposition")
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
-    ap.add_argument("--mixer", default="x", choices=["x", "ma", "terms", "grover", "clique"],
-                    help="X-mixer workloads (1-3): transverse field, multi-angle, X + XX terms, or Grover; "
+    ap.add_argument("--mixer", default="x", choices=["x", "ma", "terms", "grover", "grover_x", "clique"],
+                    help="X-mixer workloads (1-3): transverse field, multi-angle, X + XX terms, Grover (rank-one "
+                         "update) or Grover through the general X-mixer passes; "
                          "workload 4: clique instead of ring XY mixer")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default X-mixer pass schedule instead of tuning it before the warm-up")
