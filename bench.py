@@ -3,9 +3,12 @@
 Default workload (one unit = one gradient of <C> with respect to all 2p
 angles, forward + adjoint sweep): Sherrington-Kirkpatrick cost on n = 28
 qubits (2^28 complex64 amplitudes, 2 GiB state), transverse-field mixer,
-p = 8 rounds, per-round state checkpoints, J_ij ~ N(0,1) from the seeded
+p = 8 rounds, per-pass state checkpoints, J_ij ~ N(0,1) from the seeded
 generator.  The state (2 GiB) is larger than L2, so no flush is needed
-between steps.
+between steps.  Two sub-records ride on the default line: `batched`, the
+uneven 512-instance batch (n = 14..22, p = 6, 4 angle sets each) replayed from
+a captured CUDA graph, and `grover`, the same n = 28 workload with the Grover
+mixer applied as a rank-one update.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -651,6 +654,21 @@ def _gpu_arm_on_stream(args, ws, rank, local, dist, dev, stream, qg):
             out["batched"] = b
         del W5
         ctx5.close()
+    if headline and not args.no_grover:
+        # the same workload with the Grover mixer of Sec. 2.4 as the rank-one
+        # update (one streaming pass per round and direction), direct launches
+        torch.cuda.empty_cache()
+        ctxg = qg.Context(local, stream)
+        Wg = Workload(qg, ctxg, WORKLOAD, dev, args.steps + args.warmup, mixer="grover")
+        gargs = argparse.Namespace(**vars(args))
+        gargs.no_cpu_baseline = True
+        g = measure(gargs, Wg, qg, ctxg, stream, dist, ws, rank, local, dev, graph_mode=False,
+                    steps=args.steps, warmup=args.warmup)
+        if rank == 0 and g is not None:
+            g["metric"] = f"QAOA {g['unit']} ({Wg.name})"
+            out["grover"] = g
+        del Wg
+        ctxg.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -952,6 +970,9 @@ def main():
                     help="keep the default X-mixer pass schedule instead of tuning it before the warm-up")
     ap.add_argument("--no-batched", action="store_true",
                     help="default workload only: skip the batched sub-record (uneven 512-instance batch)")
+    ap.add_argument("--no-grover", action="store_true",
+                    help="default workload only: skip the sub-record of the same workload with the Grover mixer "
+                         "(rank-one update)")
     ap.add_argument("--no-fd", action="store_true",
                     help="skip the central finite-difference comparison on the same GPU")
     args = ap.parse_args()

@@ -75,3 +75,22 @@ def test_x_mixer_weights_rejects_bad_sizes():
     assert lib.qaoa_x_mixer_weights(0, 1, P(c), P(d)) == B.QAOA_ERR_INVALID
     assert lib.qaoa_x_mixer_weights(2, 3, P(c), P(d)) == B.QAOA_ERR_INVALID
     assert lib.qaoa_x_mixer_weights(2, 1, None, P(d)) == B.QAOA_ERR_INVALID
+
+
+def test_grover_mixer_struct():
+    """GroverMixer: dimensions of the full space and the weight-k subspace,
+    the mixer kind the library sees, and no empty feasible set."""
+    import math
+
+    import pytest
+
+    import paper_2312_06451_gb300 as qg
+    from paper_2312_06451_gb300 import _binding as B
+
+    m = qg.GroverMixer.full(10)
+    assert (m.dim, m.n, m.struct.kind, m.struct.dim) == (1024, 10, B.QAOA_MIXER_GROVER, 1024)
+    d = qg.GroverMixer.dicke(20, 9)
+    assert d.dim == math.comb(20, 9) == d.struct.dim
+    assert qg.GroverMixer(3).dim == 3
+    with pytest.raises(ValueError):
+        qg.GroverMixer(0)
