@@ -28,7 +28,7 @@ __all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError", "p
            "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched",
            "qaoa_gradient_small_noalloc", "ring_eigen_mixer", "clique_eigen_mixer", "xy_eigen_mixer",
            "save_eigen_mixer", "load_eigen_mixer", "GeneralXMixer", "x_terms_mixer", "grover_x_mixer", "GroverMixer",
-           "krawtchouk_weights", "EigenSymMixer", "xy_block_hamiltonians", "xy_sym_mixer", "BatchedCall"]
+           "write_tuning_file", "read_tuning_file", "krawtchouk_weights", "EigenSymMixer", "xy_block_hamiltonians", "xy_sym_mixer", "BatchedCall"]
 
 _MIXER_IDS = itertools.count(1)
 
@@ -300,6 +300,62 @@ def clique_eigen_mixer(ctx: "Context", n: int, k: int, precision: str = "fp32", 
     return xy_eigen_mixer(ctx, "clique", n, k, precision, cache_file)
 
 
+TUNING_FILE_FORMAT = "qaoa-gb300-xtune"
+TUNING_FILE_VERSION = 1
+_XTUNE_KEYS = ("n", "cost_dtype", "cmin", "split", "nbuf_bwd_contig", "nbuf_bwd_gather")
+
+
+def _tuning_digest(entries) -> str:
+    import hashlib
+    import json
+
+    return hashlib.sha256(json.dumps(entries, sort_keys=True).encode()).hexdigest()
+
+
+def write_tuning_file(path: str, entries, gpu: str = "") -> None:
+    """Store X-mixer pass schedules (autotune() results) for re-use: a JSON
+    file with a format tag and version, the GPU they were tuned on and a
+    SHA-256 of the entries.  Written to a temporary name and renamed, so a
+    crash never leaves a half-written file under `path`."""
+    import json
+    import os
+
+    ents = [dict({k: int(e[k]) for k in _XTUNE_KEYS}, ms=float(e.get("ms", 0.0))) for e in entries]
+    doc = {"format": TUNING_FILE_FORMAT, "version": TUNING_FILE_VERSION, "gpu": gpu, "entries": ents,
+           "sha256": _tuning_digest(ents)}
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(doc, f, indent=1)
+    os.replace(tmp, path)
+
+
+def read_tuning_file(path: str, gpu: str | None = None) -> list:
+    """Entries of a file written by write_tuning_file.  Raises ValueError for a
+    damaged or altered file, another format or version, or (gpu given) a file
+    tuned on another GPU.  The values are checked again by the library when
+    installed (qaoa_set_xtune)."""
+    import json
+
+    try:
+        with open(path) as f:
+            doc = json.load(f)
+    except (OSError, ValueError) as e:
+        raise ValueError(f"unreadable tuning file {path}: {e}") from e
+    if not isinstance(doc, dict) or doc.get("format") != TUNING_FILE_FORMAT:
+        raise ValueError(f"{path} is not a pass-schedule tuning file")
+    if doc.get("version") != TUNING_FILE_VERSION:
+        raise ValueError(f"tuning file {path} has version {doc.get('version')}, wanted {TUNING_FILE_VERSION}")
+    ents = doc.get("entries")
+    if not isinstance(ents, list) or _tuning_digest(ents) != doc.get("sha256"):
+        raise ValueError(f"tuning file {path} fails its checksum")
+    for e in ents:
+        if not isinstance(e, dict) or any(not isinstance(e.get(k), int) for k in _XTUNE_KEYS):
+            raise ValueError(f"tuning file {path} holds a malformed entry")
+    if gpu is not None and doc.get("gpu") != gpu:
+        raise ValueError(f"tuning file {path} was tuned on {doc.get('gpu')!r}, this is {gpu!r}")
+    return ents
+
+
 class Context:
     """A library context bound to one device and one CUDA stream."""
 
@@ -314,6 +370,7 @@ class Context:
         if st != B.QAOA_OK:
             raise QAOAError(st, "qaoa_create failed")
         self._h = h
+        self._tuned = {}  # (n, cost dtype) -> schedule installed by autotune() / set_tuning()
 
     # ------------------------------------------------------------ plumbing
     def close(self):
@@ -455,13 +512,30 @@ class Context:
         t = B.QaoaXTune()
         self._check(self._lib.qaoa_autotune_x(self._h, _ptr(cost), _cost_dtype(cost), n, p, 1 if want_grad else 0,
                                               ctypes.byref(t)))
-        return _xtune_dict(t)
+        d = _xtune_dict(t)
+        self._tuned[(d["n"], d["cost_dtype"])] = d
+        return d
 
     def set_tuning(self, t: dict):
         """Install a schedule (e.g. one saved from autotune())."""
         st = B.QaoaXTune(*(int(t[k]) for k in ("n", "cost_dtype", "cmin", "split", "nbuf_bwd_contig",
                                                "nbuf_bwd_gather")), float(t.get("ms", 0.0)))
         self._check(self._lib.qaoa_set_xtune(self._h, ctypes.byref(st)))
+        self._tuned[(int(t["n"]), int(t["cost_dtype"]))] = dict(t)
+
+    def save_tuning(self, path: str) -> None:
+        """Write every schedule this context tuned or was given to `path`
+        (write_tuning_file), for a later run to load instead of re-tuning."""
+        write_tuning_file(path, list(self._tuned.values()), torch.cuda.get_device_name(self.device))
+
+    def load_tuning(self, path: str) -> int:
+        """Install the schedules of a tuning file written on the same GPU model;
+        returns how many.  A damaged, altered or foreign file raises
+        ValueError and installs nothing."""
+        ents = read_tuning_file(path, torch.cuda.get_device_name(self.device))
+        for e in ents:
+            self.set_tuning(e)
+        return len(ents)
 
     def get_tuning(self, n: int, cost_dtype: int) -> dict:
         t = B.QaoaXTune()

@@ -8,6 +8,7 @@
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -24,6 +25,16 @@
 using namespace qg;
 
 namespace {
+
+// NVTX range for the duration of a scope: entry points and kernel launches
+// show up by name in a timeline tool; with no tool attached a push or pop is
+// a pointer check.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct Buf {
     void *p = nullptr;
@@ -1969,6 +1980,8 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
     }
     const bool prof = ctx->profiling && !capturing(ctx);
     for (const LaunchRec &r : ctx->plan.launches) {
+        NvtxRange nvtx_launch(r.fam >= 0 && r.fam < (int)ctx->fam_names.size() ? ctx->fam_names[r.fam].c_str()
+                                                                              : "qaoa_launch");
         cudaEvent_t ea = nullptr, eb = nullptr;
         if (prof) {
             ea = take_event(ctx);
@@ -2250,6 +2263,7 @@ int64_t qaoa_scratch_bytes(const qaoa_ctx *ctx) {
 
 qaoa_status qaoa_cost_precompute(qaoa_ctx *ctx, const qaoa_problem *prob, void *d_cost, int cost_dtype,
                                  int64_t dim) {
+    NvtxRange nvtx_range("qaoa_cost_precompute");
     if (!ctx) return QAOA_ERR_INVALID;
     try {
         ctx->err.clear();
@@ -2356,6 +2370,7 @@ qaoa_status qaoa_cost_precompute(qaoa_ctx *ctx, const qaoa_problem *prob, void *
 }
 
 qaoa_status qaoa_dicke_states(qaoa_ctx *ctx, int n, int k, uint64_t *d_states, int64_t dim) {
+    NvtxRange nvtx_range("qaoa_dicke_states");
     if (!ctx) return QAOA_ERR_INVALID;
     ctx->err.clear();
     if (n < 1 || n > binom_table_max() || k < 0 || k > n || !d_states)
@@ -2372,6 +2387,7 @@ qaoa_status qaoa_dicke_states(qaoa_ctx *ctx, int n, int k, uint64_t *d_states, i
 }
 
 qaoa_status qaoa_ring_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, int64_t dim) {
+    NvtxRange nvtx_range("qaoa_ring_hamiltonian");
     if (!ctx) return QAOA_ERR_INVALID;
     ctx->err.clear();
     if (n < 3 || n > binom_table_max() || k < 0 || k > n || !d_H)
@@ -2389,6 +2405,7 @@ qaoa_status qaoa_ring_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, int6
 }
 
 qaoa_status qaoa_clique_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, int64_t dim) {
+    NvtxRange nvtx_range("qaoa_clique_hamiltonian");
     if (!ctx) return QAOA_ERR_INVALID;
     ctx->err.clear();
     if (n < 2 || n > binom_table_max() || k < 0 || k > n || !d_H)
@@ -2407,6 +2424,7 @@ qaoa_status qaoa_clique_hamiltonian(qaoa_ctx *ctx, int n, int k, double *d_H, in
 
 qaoa_status qaoa_expectation(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const qaoa_mixer *mixer,
                              const void *d_init, int p, const double *angles, double *E) {
+    NvtxRange nvtx_range("qaoa_expectation");
     if (!ctx) return QAOA_ERR_INVALID;
     try {
         ctx->err.clear();
@@ -2420,6 +2438,7 @@ qaoa_status qaoa_expectation(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, 
 qaoa_status qaoa_gradient(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, const qaoa_mixer *mixer,
                           const void *d_init, int p, const double *angles, double *E, double *grad,
                           int ckpt) {
+    NvtxRange nvtx_range("qaoa_gradient");
     if (!ctx) return QAOA_ERR_INVALID;
     try {
         ctx->err.clear();
@@ -2434,6 +2453,7 @@ qaoa_status qaoa_gradient(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, con
 }
 
 qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *jobs, int want_grad) {
+    NvtxRange nvtx_range("qaoa_expectation_batched");
     if (!ctx) return QAOA_ERR_INVALID;
     try {
         ctx->err.clear();
@@ -2481,6 +2501,7 @@ qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *
 }
 
 qaoa_status qaoa_cost_degeneracy(qaoa_ctx *ctx, const qaoa_problem *prob, int64_t *d_counts, int n_bins) {
+    NvtxRange nvtx_range("qaoa_cost_degeneracy");
     if (!ctx) return QAOA_ERR_INVALID;
     try {
         ctx->err.clear();
@@ -2595,6 +2616,7 @@ qaoa_status qaoa_cost_degeneracy(qaoa_ctx *ctx, const qaoa_problem *prob, int64_
 
 qaoa_status qaoa_grover_batched(qaoa_ctx *ctx, const int64_t *d_counts, int n_bins, int p, int n_sets,
                                 const double *d_angles, double *d_E, double *d_grad) {
+    NvtxRange nvtx_range("qaoa_grover_batched");
     if (!ctx) return QAOA_ERR_INVALID;
     ctx->err.clear();
     if (!d_counts || !d_angles || !d_E) return fail(ctx, QAOA_ERR_INVALID, "counts, angles and E must be non-NULL");
@@ -2691,6 +2713,7 @@ qaoa_status qaoa_get_xtune(qaoa_ctx *ctx, int n, int cost_dtype, qaoa_xtune *out
 
 qaoa_status qaoa_autotune_x(qaoa_ctx *ctx, const void *d_cost, int cost_dtype, int n, int p, int want_grad,
                             qaoa_xtune *out) {
+    NvtxRange nvtx_range("qaoa_autotune_x");
     if (!ctx) return QAOA_ERR_INVALID;
     try {
         ctx->err.clear();

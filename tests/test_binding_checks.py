@@ -94,3 +94,40 @@ def test_grover_mixer_struct():
     assert qg.GroverMixer(3).dim == 3
     with pytest.raises(ValueError):
         qg.GroverMixer(0)
+
+
+def test_tuning_file_round_trip_and_damage(tmp_path):
+    """The pass-schedule tuning file: what is written reads back; a changed
+    value, a truncated file, another version or another GPU are refused."""
+    import json
+
+    import pytest
+
+    import paper_2312_06451_gb300 as qg
+
+    ents = [{"n": 24, "cost_dtype": 1, "cmin": 5, "split": 1, "nbuf_bwd_contig": 2, "nbuf_bwd_gather": 1,
+             "ms": 3.25},
+            {"n": 28, "cost_dtype": 0, "cmin": 4, "split": 0, "nbuf_bwd_contig": 1, "nbuf_bwd_gather": 1,
+             "ms": 48.0}]
+    path = str(tmp_path / "tune.json")
+    qg.write_tuning_file(path, ents, "GPU A")
+    assert qg.read_tuning_file(path, "GPU A") == ents
+    assert qg.read_tuning_file(path) == ents
+    with pytest.raises(ValueError, match="tuned on"):
+        qg.read_tuning_file(path, "GPU B")
+    doc = json.load(open(path))
+    doc["entries"][0]["cmin"] = 6  # altered without a new checksum
+    json.dump(doc, open(path, "w"))
+    with pytest.raises(ValueError, match="checksum"):
+        qg.read_tuning_file(path)
+    qg.write_tuning_file(path, ents)
+    text = open(path).read()
+    open(path, "w").write(text[: len(text) // 2])
+    with pytest.raises(ValueError, match="unreadable"):
+        qg.read_tuning_file(path)
+    qg.write_tuning_file(path, ents)
+    doc = json.load(open(path))
+    doc["version"] = 99
+    json.dump(doc, open(path, "w"))
+    with pytest.raises(ValueError, match="version"):
+        qg.read_tuning_file(path)

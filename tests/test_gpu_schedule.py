@@ -74,6 +74,20 @@ def test_autotune_then_batched_gradient(setup):
         _check(E[s].item(), G[s].cpu().numpy(), E_ref, g_ref, sig)
 
 
+def test_tuning_saved_and_restored(setup, tmp_path):
+    """A tuned schedule written to a file (the autotuner's cache) and loaded
+    into a fresh context is the schedule the fresh context uses."""
+    qg, ctx, cost, *_ = setup
+    t = ctx.autotune(cost, N, p=2, want_grad=True)
+    path = str(tmp_path / "xtune.json")
+    ctx.save_tuning(path)
+    with qg.Context(0) as fresh:
+        assert fresh.load_tuning(path) >= 1
+        got = fresh.get_tuning(N, 1)
+        assert {k: got[k] for k in ("cmin", "split", "nbuf_bwd_contig", "nbuf_bwd_gather")} == \
+            {k: t[k] for k in ("cmin", "split", "nbuf_bwd_contig", "nbuf_bwd_gather")}
+
+
 def test_bad_tuning_and_mode_are_rejected(setup):
     qg, ctx, *_ = setup
     with pytest.raises(qg.QAOAError):
