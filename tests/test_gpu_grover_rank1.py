@@ -292,3 +292,30 @@ def test_full_size_against_degeneracies(Q, oracle_mod):
     E_ref, g_ref = oracle_mod.grover_reduced_gradient(counts, A[0])
     assert abs(E2 - E_ref) <= 1e-5 * max(abs(E_ref), sig)
     np.testing.assert_allclose(g2, g_ref, rtol=0, atol=1e-4 * np.abs(g_ref).max())
+
+
+def test_state_limit_steps_down_then_refuses(Q, oracle_mod):
+    """Under a state cap the rank-one path keeps two vectors instead of p + 1
+    (each adjoint pass then undoes its round on the state) and still matches
+    the oracle; below two vectors the call fails with QAOA_ERR_OOM before any
+    launch, and the context works again once the cap is lifted."""
+    qg, ctx = Q
+    n, p = 20, 4
+    cost, c = full_problem(ctx, oracle_mod, n, 810, False)
+    mixer = qg.GroverMixer.full(n)
+    ang = ramp_angles(p)[0]
+    E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, ang, "grover")
+    vec = (1 << n) * 8
+    with qg.Context(0) as cx:
+        cx.set_state_limit(int(2.5 * vec))  # two vectors fit, p + 1 = 5 do not
+        E, g = cx.gradient(cost, mixer, ang, ckpt="round")
+        check(E, g, E_ref, g_ref, c)
+        cx.set_state_limit(vec)  # not even two
+        with pytest.raises(qg.QAOAError) as ei:
+            cx.gradient(cost, mixer, ang, ckpt="round")
+        from paper_2312_06451_gb300 import _binding as B
+
+        assert ei.value.status == B.QAOA_ERR_OOM
+        cx.set_state_limit(None)
+        E, g = cx.gradient(cost, mixer, ang, ckpt="round")
+        check(E, g, E_ref, g_ref, c)
