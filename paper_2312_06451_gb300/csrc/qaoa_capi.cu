@@ -190,11 +190,14 @@ int env_int(const char *name, int dflt, int lo, int hi) {
     const int x = std::atoi(v);
     return (x < lo || x > hi) ? dflt : x;
 }
-// Round-boundary fusion of the X-mixer passes (QAOA_FUSE=0 turns it off, for
-// comparison runs).
-bool fusion_enabled() {
-    static const int v = env_int("QAOA_FUSE", 1, 0, 1);
-    return v != 0;
+// Round-boundary fusion of the X-mixer passes, as a mask of the boundary
+// kinds fused: bit 0 boundaries on the contiguous group, bit 1 boundaries on
+// a gathered group.  QAOA_FUSE selects 0 none, 1 all (default), 2 contiguous
+// only, 3 gathered only, for comparison runs.
+int fusion_mask() {
+    static const int v = env_int("QAOA_FUSE", 1, 0, 3);
+    static const int masks[4] = {0, 3, 1, 2};
+    return masks[v];
 }
 
 // Tile buffers of the round-boundary adjoint passes (QAOA_FUSED_NBUF overrides
@@ -406,8 +409,17 @@ struct UnitLayout {
     int ckpt;        // QAOA_CKPT_* actually used
     int vecs;        // state vectors held in scratch
     int nb_bc, nb_bg;  // adjoint tile buffers (contiguous / gathered passes)
-    bool fused;      // round-boundary passes fused (alternating group order)
+    bool fused;      // alternating group order, some round boundaries fused (fuse_mask)
+    int fuse_mask;   // boundary kinds fused: bit 0 contiguous group, bit 1 gathered
 };
+
+// Whether the boundary between rounds k and k+1 is one fused pass.  With the
+// alternating order round k ends on group P-1 (k even) or group 0 (k odd).
+bool boundary_fused(const UnitLayout &L, int k) {
+    if (!L.fused) return false;
+    const int g = (k & 1) ? 0 : (int)L.gf.size() - 1;
+    return (L.fuse_mask & (L.gf[g].c >= kPassTileBits ? 1 : 2)) != 0;
+}
 
 qaoa_xtune default_xtune(int n, int dt) {
     qaoa_xtune t;
@@ -426,11 +438,11 @@ qaoa_xtune tune_for(const qaoa_ctx *ctx, int n, int dt) {
     return it != ctx->xtune.end() ? it->second : default_xtune(n, dt);
 }
 
-// Forward passes of a unit: P per round, one fewer per round boundary when
-// the boundary passes are fused.
+// Forward passes of a unit: P per round, one fewer per fused round boundary.
 int forward_passes(const UnitLayout &L, int p) {
-    const int P = (int)L.gf.size();
-    return L.fused ? p * P - (p - 1) : p * P;
+    int n = p * (int)L.gf.size();
+    for (int k = 0; k + 1 < p; k++) n -= boundary_fused(L, k) ? 1 : 0;
+    return n;
 }
 
 int layout_vecs(const UnitLayout &L, int p, bool grad) {
@@ -457,7 +469,8 @@ UnitLayout layout_for(const qaoa_ctx *ctx, const Unit &u, bool grad, int ckpt) {
                kPassWarps;
     L.ckpt = grad ? (u.gm ? QAOA_CKPT_PASS : ckpt) : QAOA_CKPT_NONE;  // general mixer: per-pass only
     // fused round boundaries: transverse field, per-pass checkpoints (or no gradient)
-    L.fused = fusion_enabled() && !u.ma && !u.gm && L.gf.size() >= 2 && u.p >= 2 &&
+    L.fuse_mask = fusion_mask();
+    L.fused = L.fuse_mask != 0 && !u.ma && !u.gm && L.gf.size() >= 2 && u.p >= 2 &&
               (!grad || L.ckpt == QAOA_CKPT_PASS);
     L.vecs = layout_vecs(L, u.p, grad);
     L.nb_bc = t.nbuf_bwd_contig;
@@ -583,12 +596,16 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
         // or works in place on W (expectation only).
         struct FP {
             int g, k, fused;  // group, round (fused: rounds k and k+1)
+            int first;        // the first pass of round k (not fused): applies / undoes its phase
         };
         std::vector<FP> seq;
         auto group_at = [&](int k, int q) { return (k & 1) ? Pf - 1 - q : q; };  // q-th group of round k
-        for (int k = 0; k < p; k++)
-            for (int q = (k == 0 ? 0 : 1); q < Pf; q++)
-                seq.push_back({group_at(k, q), k, (q == Pf - 1 && k < p - 1) ? 1 : 0});
+        for (int k = 0; k < p; k++) {
+            const int q0 = (k > 0 && boundary_fused(L, k - 1)) ? 1 : 0;
+            for (int q = q0; q < Pf; q++)
+                seq.push_back({group_at(k, q), k, (q == Pf - 1 && k < p - 1 && boundary_fused(L, k)) ? 1 : 0,
+                               q == 0 ? 1 : 0});
+        }
         const int J = (int)seq.size();
         auto pj = [&](int j) { return CK + (int64_t)j * N; };
         auto slot = [&](int k, int g) {  // round k's beta partial slot of group g
@@ -612,8 +629,8 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
         };
         for (int j = 0; j < J; j++) {
             PassDesc d = base_desc(seq[j]);
+            if (seq[j].first) d.flags |= PF_PHASE;
             if (j == 0) {
-                d.flags |= PF_PHASE;
                 if (u.init) {
                     d.psi_in = u.init;
                     d.flags |= PF_TWIST_IN;
@@ -645,9 +662,9 @@ void unit_passes(const Unit &u, const UnitLayout &L, bool grad, float2 *W, float
             } else {
                 d.part_beta = slot(f.k, f.g);
             }
-            if (j == 0) {
+            if (f.first) {
                 d.flags |= PF_PHASE;
-                d.part_gamma = part + (int64_t)(1 + p) * L.stride;
+                d.part_gamma = part + (int64_t)(1 + p + f.k) * L.stride;
             }
             bwd.push_back(d);
         }
@@ -1173,7 +1190,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
             if (units[i].mixer_kind != QAOA_MIXER_X || units[i].n <= smax) continue;
             const UnitLayout &L = lay[i];
             groups[{L.T_f, L.T_b, (int)L.gf.size(), (int)L.gb.size(), units[i].p, units[i].cost_dtype, L.nb_bc,
-                    L.nb_bg, units[i].ma ? 1 : (units[i].gm ? 2 : 0), L.fused ? 1 : 0}]
+                    L.nb_bg, units[i].ma ? 1 : (units[i].gm ? 2 : 0), L.fused ? L.fuse_mask : 0}]
                 .push_back(i);
         }
         // waves: consecutive units of a group whose states fit the budget together
@@ -1415,7 +1432,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                     }
                 }
             }
-            const int nfwd = gk.fused ? gk.p * gk.Pf - (gk.p - 1) : gk.p * gk.Pf;
+            const int nfwd = forward_passes(lay[w.us[0]], gk.p);
             for (size_t s = 0; s < steps.size(); s++) {
                 const bool bwd = (int)s >= nfwd;
                 const int T = bwd ? gk.Tb : gk.Tf;
