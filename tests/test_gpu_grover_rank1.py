@@ -319,3 +319,69 @@ def test_state_limit_steps_down_then_refuses(Q, oracle_mod):
         cx.set_state_limit(None)
         E, g = cx.gradient(cost, mixer, ang, ckpt="round")
         check(E, g, E_ref, g_ref, c)
+
+
+def test_autograd_with_grover_mixer(Q, oracle_mod):
+    """QAOAExpectation (the torch.autograd.Function) over the rank-one Grover
+    path: backward gives the oracle's gradient, and a few plain gradient-ascent
+    steps raise <C> (the angle-finding use of Sec. 2.3)."""
+    qg, ctx = Q
+    n, p = 14, 3
+    cost, c = full_problem(ctx, oracle_mod, n, 820, False)
+    mixer = qg.GroverMixer.full(n)
+    a0 = ramp_angles(p)[0]
+    ang = torch.tensor(a0, dtype=torch.float64, requires_grad=True)
+    E = qg.QAOAExpectation.apply(ang, ctx, cost, mixer)
+    E.backward()
+    E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, a0, "grover")
+    check(E.item(), ang.grad.numpy(), E_ref, g_ref, c)
+    x = torch.tensor(a0, dtype=torch.float64, requires_grad=True)
+    E_first = None
+    for _ in range(5):
+        x.grad = None
+        Ex = qg.QAOAExpectation.apply(x, ctx, cost, mixer)
+        E_first = Ex.item() if E_first is None else E_first
+        Ex.backward()
+        with torch.no_grad():
+            x += 0.01 * x.grad / max(1.0, float(x.grad.abs().max()))
+    assert qg.QAOAExpectation.apply(x.detach(), ctx, cost, mixer).item() > E_first
+
+
+def test_mixed_batch_with_x_mixer_graph_replay(Q, oracle_mod):
+    """One batched call holding an X-mixer job and Grover-mixer jobs (full
+    space and Dicke), captured in a CUDA graph and replayed with new angles."""
+    qg, ctx = Q
+    S, p = 2, 3
+    cx, c = full_problem(ctx, oracle_mod, 16, 830, True)
+    cd, cdk = dicke_problem(ctx, oracle_mod, 14, 6, 831)
+    specs = [(16, cx, c, qg.XMixer(16), None), (16, cx, c, qg.GroverMixer.full(16), "grover"),
+             (14, cd, cdk, qg.GroverMixer.dicke(14, 6), "grover")]
+    jobs = []
+    for j, (n, cost, cc, mixer, kind) in enumerate(specs):
+        A = scaled_angles(p, 840 + j, cc, S) if kind else uniform_angles(p, 840 + j, S)
+        jobs.append({"cost": cost, "mixer": mixer, "angles": torch.from_numpy(A).cuda(),
+                     "E": torch.zeros(S, dtype=torch.float64, device="cuda"),
+                     "grad": torch.zeros(S, 2 * p, dtype=torch.float64, device="cuda")})
+    s = torch.cuda.Stream()
+    qctx = qg.Context(0, s)
+    try:
+        with torch.cuda.stream(s):
+            qctx.expectation_batched(jobs, want_grad=True)
+            s.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s):
+                qctx.expectation_batched(jobs, want_grad=True)
+            new = []
+            for j, (n, cost, cc, mixer, kind) in enumerate(specs):
+                A = scaled_angles(p, 850 + j, cc, S) if kind else uniform_angles(p, 850 + j, S)
+                jobs[j]["angles"].copy_(torch.from_numpy(A))
+                new.append(A)
+            graph.replay()
+        s.synchronize()
+        for (n, cost, cc, mixer, kind), jb, A in zip(specs, jobs, new):
+            for i in range(S):
+                E_ref, g_ref = (oracle_mod.qaoa_gradient(n, cc, A[i], kind) if kind
+                                else oracle_mod.qaoa_gradient(n, cc, A[i]))
+                check(jb["E"][i].item(), jb["grad"][i].cpu().numpy(), E_ref, g_ref, cc)
+    finally:
+        qctx.close()
