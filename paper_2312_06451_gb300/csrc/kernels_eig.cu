@@ -16,6 +16,8 @@
 // direction as well, thanks to checkpoints of V^T phi_k and psi_{k-1}.
 #include "common.cuh"
 
+#include <type_traits>
+
 #include <cuda.h>
 #include <math.h>
 
@@ -865,138 +867,198 @@ __global__ void __launch_bounds__(kOrbitThreads) orbit_kernel(OrbitTabs T, Orbit
     // every M_r of the layout (sum of r^2 over the periods, at most
     // kOrbitSmem floats), read by all threads at once: shared-memory broadcasts
     __shared__ __align__(16) float s_mr[kOrbitSmem];
+    // the full-period matrix M_RMAX and its transpose, 16-byte aligned, so
+    // that both transforms read four consecutive entries at once
+    constexpr int kF = RMAX <= 16 ? RMAX : 1;
+    __shared__ __align__(16) float s_mf[kF * kF];
+    __shared__ __align__(16) float s_mft[kF * kF];
     for (int i = threadIdx.x; i < T.mr_len; i += kOrbitThreads) s_mr[i] = T.mr[i];
+    const int off_full = RMAX <= 16 ? T.mr_off[RMAX] : -1;
+    if (off_full >= 0)
+        for (int i = threadIdx.x; i < kF * kF; i += kOrbitThreads) {
+            const float m = T.mr[off_full + i];
+            s_mf[i] = m;
+            s_mft[(i % kF) * kF + i / kF] = m;
+        }
     __syncthreads();
     const int o = blockIdx.x * kOrbitThreads + threadIdx.x;
     const int s = blockIdx.y;
     float contrib = 0.f;
     if (o < T.n_orbits && s < A.nsets) {
         const int s0 = T.orb_start[o], r = T.orb_start[o + 1] - s0;
-        const float *M = s_mr + T.mr_off[r];
         const RoundCoef cf = A.coef[s * A.coef_stride + A.round];
         const size_t row_re = (size_t)(2 * s) * A.ldp, row_im = row_re + A.ldp;
-        float ar[RMAX], ai[RMAX], cr[RMAX], ci[RMAX];
         auto vpos = [&](int a) -> int { return T.vec_pos[s0 + a]; };
         auto cost_of = [&](int j) -> float {
             const int idx = T.members[s0 + j];
             return A.cost_dtype == 0 ? __ldg(reinterpret_cast<const float *>(A.cost) + idx)
                                      : (float)__ldg(reinterpret_cast<const unsigned char *>(A.cost) + idx);
         };
-        // a = T c for the coefficients of this orbit in matrix `in`
-        auto to_amp = [&](const float *in, float (&xr)[RMAX], float (&xi)[RMAX]) {
-#pragma unroll
-            for (int a = 0; a < RMAX; a++) {
-                if (a < r) {
-                    const int pos = vpos(a);
-                    cr[a] = in[row_re + pos];
-                    ci[a] = in[row_im + pos];
-                }
-            }
-            // member sums accumulated side by side (independent FMA chains)
-#pragma unroll
-            for (int j = 0; j < RMAX; j++) xr[j] = xi[j] = 0.f;
-#pragma unroll
-            for (int a = 0; a < RMAX; a++) {
-                if (a >= r) continue;
-#pragma unroll
-                for (int j = 0; j < RMAX; j++) {
-                    if (j >= r) continue;
-                    const float m = M[j * r + a];
-                    xr[j] = fmaf(m, cr[a], xr[j]);
-                    xi[j] = fmaf(m, ci[a], xi[j]);
-                }
-            }
-        };
-        // c = T^T a written to `out` (with the tf32 split when out_lo)
-        auto from_amp = [&](const float (&xr)[RMAX], const float (&xi)[RMAX], float *out, float *out_lo) {
-            // coefficient sums accumulated side by side in cr / ci (free here)
-#pragma unroll
-            for (int a = 0; a < RMAX; a++) cr[a] = ci[a] = 0.f;
-#pragma unroll
-            for (int j = 0; j < RMAX; j++) {
-                if (j >= r) continue;
+        // Full-period orbits (all but a few; they come first in orbit order)
+        // take a copy of the body with the period known at compile time: no
+        // bound tests, M_r rows read as float4.  The sums run over the same
+        // index order in both copies, so the results agree bit for bit.
+        auto body = [&](auto full_tag) {
+            constexpr bool FULL = decltype(full_tag)::value;
+            const int R = FULL ? RMAX : r;
+            const float *M = FULL ? s_mf : s_mr + T.mr_off[r];
+            static_assert(!FULL || RMAX == kF, "full-period copy only for the 16-wide kernel");
+            float ar[RMAX], ai[RMAX], cr[RMAX], ci[RMAX];
+            // a = T c for the coefficients of this orbit in matrix `in`
+            auto to_amp = [&](const float *in, float (&xr)[RMAX], float (&xi)[RMAX]) {
 #pragma unroll
                 for (int a = 0; a < RMAX; a++) {
-                    if (a >= r) continue;
-                    const float m = M[j * r + a];
-                    cr[a] = fmaf(m, xr[j], cr[a]);
-                    ci[a] = fmaf(m, xi[j], ci[a]);
+                    if (a < R) {
+                        const int pos = vpos(a);
+                        cr[a] = in[row_re + pos];
+                        ci[a] = in[row_im + pos];
+                    }
                 }
-            }
+                // member sums accumulated side by side (independent FMA chains)
 #pragma unroll
-            for (int a = 0; a < RMAX; a++) {
-                if (a >= r) continue;
-                const int pos = vpos(a);
-                put(out, out_lo, row_re + pos, cr[a]);
-                put(out, out_lo, row_im + pos, ci[a]);
+                for (int j = 0; j < RMAX; j++) xr[j] = xi[j] = 0.f;
+#pragma unroll
+                for (int a = 0; a < RMAX; a++) {
+                    if (a >= R) continue;
+                    if constexpr (FULL) {  // row a of M^T: M[j][a], j = 4q .. 4q + 3
+                        const float4 *MT4 = reinterpret_cast<const float4 *>(s_mft) + a * (RMAX / 4);
+#pragma unroll
+                        for (int q = 0; q < RMAX / 4; q++) {
+                            const float4 m = MT4[q];
+                            xr[4 * q] = fmaf(m.x, cr[a], xr[4 * q]);
+                            xi[4 * q] = fmaf(m.x, ci[a], xi[4 * q]);
+                            xr[4 * q + 1] = fmaf(m.y, cr[a], xr[4 * q + 1]);
+                            xi[4 * q + 1] = fmaf(m.y, ci[a], xi[4 * q + 1]);
+                            xr[4 * q + 2] = fmaf(m.z, cr[a], xr[4 * q + 2]);
+                            xi[4 * q + 2] = fmaf(m.z, ci[a], xi[4 * q + 2]);
+                            xr[4 * q + 3] = fmaf(m.w, cr[a], xr[4 * q + 3]);
+                            xi[4 * q + 3] = fmaf(m.w, ci[a], xi[4 * q + 3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < RMAX; j++) {
+                            if (j >= R) continue;
+                            const float m = M[j * R + a];
+                            xr[j] = fmaf(m, cr[a], xr[j]);
+                            xi[j] = fmaf(m, ci[a], xi[j]);
+                        }
+                    }
+                }
+            };
+            // c = T^T a written to `out` (with the tf32 split when out_lo)
+            auto from_amp = [&](const float (&xr)[RMAX], const float (&xi)[RMAX], float *out, float *out_lo) {
+                // coefficient sums accumulated side by side in cr / ci (free here)
+#pragma unroll
+                for (int a = 0; a < RMAX; a++) cr[a] = ci[a] = 0.f;
+#pragma unroll
+                for (int j = 0; j < RMAX; j++) {
+                    if (j >= R) continue;
+                    if constexpr (FULL) {
+                        const float4 *M4 = reinterpret_cast<const float4 *>(M) + j * (RMAX / 4);
+#pragma unroll
+                        for (int q = 0; q < RMAX / 4; q++) {
+                            const float4 m = M4[q];
+                            cr[4 * q] = fmaf(m.x, xr[j], cr[4 * q]);
+                            ci[4 * q] = fmaf(m.x, xi[j], ci[4 * q]);
+                            cr[4 * q + 1] = fmaf(m.y, xr[j], cr[4 * q + 1]);
+                            ci[4 * q + 1] = fmaf(m.y, xi[j], ci[4 * q + 1]);
+                            cr[4 * q + 2] = fmaf(m.z, xr[j], cr[4 * q + 2]);
+                            ci[4 * q + 2] = fmaf(m.z, xi[j], ci[4 * q + 2]);
+                            cr[4 * q + 3] = fmaf(m.w, xr[j], cr[4 * q + 3]);
+                            ci[4 * q + 3] = fmaf(m.w, xi[j], ci[4 * q + 3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < RMAX; a++) {
+                            if (a >= R) continue;
+                            const float m = M[j * R + a];
+                            cr[a] = fmaf(m, xr[j], cr[a]);
+                            ci[a] = fmaf(m, xi[j], ci[a]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < RMAX; a++) {
+                    if (a >= R) continue;
+                    const int pos = vpos(a);
+                    put(out, out_lo, row_re + pos, cr[a]);
+                    put(out, out_lo, row_im + pos, ci[a]);
+                }
+            };
+            if (MODE == ORB_INIT) {
+#pragma unroll
+                for (int j = 0; j < RMAX; j++) {
+                    if (j >= R) continue;
+                    const float2 v = A.init ? A.init[T.members[s0 + j]] : make_float2(A.amp0, 0.f);
+                    ar[j] = v.x;
+                    ai[j] = v.y;
+                }
+                if (A.ckpt) from_amp(ar, ai, A.ckpt, nullptr);
+#pragma unroll
+                for (int j = 0; j < RMAX; j++) {
+                    if (j >= R) continue;
+                    const float2 w = cmul(make_float2(ar[j], ai[j]), turn_phase(cf.g_hi, cf.g_lo, cost_of(j), 0.f));
+                    ar[j] = w.x;
+                    ai[j] = w.y;
+                }
+                from_amp(ar, ai, A.out, A.out_lo);
+            } else if (MODE == ORB_PHASE) {
+                to_amp(A.in, ar, ai);
+#pragma unroll
+                for (int j = 0; j < RMAX; j++) {
+                    if (j >= R) continue;
+                    const float2 w = cmul(make_float2(ar[j], ai[j]), turn_phase(cf.g_hi, cf.g_lo, cost_of(j), 0.f));
+                    ar[j] = w.x;
+                    ai[j] = w.y;
+                }
+                from_amp(ar, ai, A.out, A.out_lo);
+            } else if (MODE == ORB_LAST) {
+                to_amp(A.in, ar, ai);
+                const float c0 = A.c0 ? (float)__ldg(A.c0) : 0.f;
+#pragma unroll
+                for (int j = 0; j < RMAX; j++) {
+                    if (j >= R) continue;
+                    const float C = cost_of(j);
+                    contrib = fmaf(C, fmaf(ar[j], ar[j], ai[j] * ai[j]), contrib);
+                    ar[j] *= C - c0;
+                    ai[j] *= C - c0;
+                }
+                if (A.out) from_amp(ar, ai, A.out, A.out_lo);
+            } else {  // ORB_BWD
+                // two matrices to read: start the second one's lines toward L2
+                // while the first is fetched and transformed
+#pragma unroll
+                for (int a = 0; a < RMAX; a++) {
+                    if (a >= R) continue;
+                    const int pos = vpos(a);
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.in + row_re + pos));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.in + row_im + pos));
+                }
+                float pr[RMAX], pi[RMAX];
+                to_amp(A.in_psi, pr, pi);
+                to_amp(A.in, ar, ai);
+                const float c0 = A.c0 ? (float)__ldg(A.c0) : 0.f;
+#pragma unroll
+                for (int j = 0; j < RMAX; j++) {
+                    if (j >= R) continue;
+                    const float C = cost_of(j);
+                    const float2 ph = turn_phase(cf.g_hi, cf.g_lo, C, 0.f);
+                    const float2 phi = cmul(make_float2(pr[j], pi[j]), ph);
+                    contrib = fmaf(C - c0, ar[j] * phi.y - ai[j] * phi.x, contrib);
+                    // undo the phase on mu: mu conj(ph)
+                    const float xr = fmaf(ar[j], ph.x, ai[j] * ph.y), xi = fmaf(ai[j], ph.x, -ar[j] * ph.y);
+                    ar[j] = xr;
+                    ai[j] = xi;
+                }
+                if (A.out) from_amp(ar, ai, A.out, A.out_lo);
             }
         };
-        if (MODE == ORB_INIT) {
-#pragma unroll
-            for (int j = 0; j < RMAX; j++) {
-                if (j >= r) continue;
-                const float2 v = A.init ? A.init[T.members[s0 + j]] : make_float2(A.amp0, 0.f);
-                ar[j] = v.x;
-                ai[j] = v.y;
-            }
-            if (A.ckpt) from_amp(ar, ai, A.ckpt, nullptr);
-#pragma unroll
-            for (int j = 0; j < RMAX; j++) {
-                if (j >= r) continue;
-                const float2 w = cmul(make_float2(ar[j], ai[j]), turn_phase(cf.g_hi, cf.g_lo, cost_of(j), 0.f));
-                ar[j] = w.x;
-                ai[j] = w.y;
-            }
-            from_amp(ar, ai, A.out, A.out_lo);
-        } else if (MODE == ORB_PHASE) {
-            to_amp(A.in, ar, ai);
-#pragma unroll
-            for (int j = 0; j < RMAX; j++) {
-                if (j >= r) continue;
-                const float2 w = cmul(make_float2(ar[j], ai[j]), turn_phase(cf.g_hi, cf.g_lo, cost_of(j), 0.f));
-                ar[j] = w.x;
-                ai[j] = w.y;
-            }
-            from_amp(ar, ai, A.out, A.out_lo);
-        } else if (MODE == ORB_LAST) {
-            to_amp(A.in, ar, ai);
-            const float c0 = A.c0 ? (float)__ldg(A.c0) : 0.f;
-#pragma unroll
-            for (int j = 0; j < RMAX; j++) {
-                if (j >= r) continue;
-                const float C = cost_of(j);
-                contrib = fmaf(C, fmaf(ar[j], ar[j], ai[j] * ai[j]), contrib);
-                ar[j] *= C - c0;
-                ai[j] *= C - c0;
-            }
-            if (A.out) from_amp(ar, ai, A.out, A.out_lo);
-        } else {  // ORB_BWD
-            // two matrices to read: start the second one's lines toward L2
-            // while the first is fetched and transformed
-#pragma unroll
-            for (int a = 0; a < RMAX; a++) {
-                if (a >= r) continue;
-                const int pos = vpos(a);
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.in + row_re + pos));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.in + row_im + pos));
-            }
-            float pr[RMAX], pi[RMAX];
-            to_amp(A.in_psi, pr, pi);
-            to_amp(A.in, ar, ai);
-            const float c0 = A.c0 ? (float)__ldg(A.c0) : 0.f;
-#pragma unroll
-            for (int j = 0; j < RMAX; j++) {
-                if (j >= r) continue;
-                const float C = cost_of(j);
-                const float2 ph = turn_phase(cf.g_hi, cf.g_lo, C, 0.f);
-                const float2 phi = cmul(make_float2(pr[j], pi[j]), ph);
-                contrib = fmaf(C - c0, ar[j] * phi.y - ai[j] * phi.x, contrib);
-                // undo the phase on mu: mu conj(ph)
-                const float xr = fmaf(ar[j], ph.x, ai[j] * ph.y), xi = fmaf(ai[j], ph.x, -ar[j] * ph.y);
-                ar[j] = xr;
-                ai[j] = xi;
-            }
-            if (A.out) from_amp(ar, ai, A.out, A.out_lo);
+        // (the 32-wide copy would not fit the registers next to the generic one)
+        if constexpr (RMAX <= 16) {
+            if (r == RMAX && off_full >= 0) body(std::integral_constant<bool, true>());
+            else body(std::integral_constant<bool, false>());
+        } else {
+            body(std::integral_constant<bool, false>());
         }
     }
     if (MODE == ORB_LAST || MODE == ORB_BWD) {
