@@ -318,7 +318,8 @@ struct OrbitArgs {
     double *part;         // LAST / BWD: [set][orbit block] partial sums
     int part_stride;
 };
-constexpr int kOrbitThreads = 128;  // orbits per block of the orbit kernel
+constexpr int kOrbitThreads = 128;                   // threads per block of the orbit kernel
+constexpr int kOrbitsPerBlock = kOrbitThreads / 2;  // two threads (real, imaginary rows) per orbit
 cudaError_t launch_orbit(const OrbitTabs &T, const OrbitArgs &A, cudaStream_t s);
 // Padded block matrices of a symmetric eigendecomposition: A = V_b (or V_b^T)
 // stacked as rows block_pos[b] .. of a [ldp][pmax] matrix (zero padded), the

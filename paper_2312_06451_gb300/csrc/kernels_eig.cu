@@ -881,19 +881,24 @@ __global__ void __launch_bounds__(kOrbitThreads) orbit_kernel(OrbitTabs T, Orbit
             s_mft[(i % kF) * kF + i / kF] = m;
         }
     __syncthreads();
-    const int o = blockIdx.x * kOrbitThreads + threadIdx.x;
+    // Two adjacent lanes per (orbit, set): part 0 holds the real rows, part 1
+    // the imaginary ones.  M_r is real, so each row transforms on its own;
+    // the phase and the gamma term take the partner's values by a shuffle.
+    const int part = threadIdx.x & 1;
+    const unsigned pair_mask = 3u << ((threadIdx.x & 31) & ~1);
+    const int o = blockIdx.x * kOrbitsPerBlock + (threadIdx.x >> 1);
     const int s = blockIdx.y;
     float contrib = 0.f;
-    if (o < T.n_orbits && s < A.nsets) {
+    if (o < T.n_orbits && s < A.nsets) {  // the same for both lanes of a pair
         const int s0 = T.orb_start[o], r = T.orb_start[o + 1] - s0;
         const RoundCoef cf = A.coef[s * A.coef_stride + A.round];
-        const size_t row_re = (size_t)(2 * s) * A.ldp, row_im = row_re + A.ldp;
-        auto vpos = [&](int a) -> int { return T.vec_pos[s0 + a]; };
-        auto cost_of = [&](int j) -> float {
-            const int idx = T.members[s0 + j];
-            return A.cost_dtype == 0 ? __ldg(reinterpret_cast<const float *>(A.cost) + idx)
-                                     : (float)__ldg(reinterpret_cast<const unsigned char *>(A.cost) + idx);
+        const size_t row = (size_t)(2 * s + part) * A.ldp;
+        // (re, im) of a member from this lane's part and the partner's
+        auto pair_of = [&](float v) -> float2 {
+            const float w = __shfl_xor_sync(pair_mask, v, 1);
+            return part ? make_float2(w, v) : make_float2(v, w);
         };
+        auto take = [&](float2 z) -> float { return part ? z.y : z.x; };
         // Full-period orbits (all but a few; they come first in orbit order)
         // take a copy of the body with the period known at compile time: no
         // bound tests, M_r rows read as float4.  The sums run over the same
@@ -902,21 +907,45 @@ __global__ void __launch_bounds__(kOrbitThreads) orbit_kernel(OrbitTabs T, Orbit
             constexpr bool FULL = decltype(full_tag)::value;
             const int R = FULL ? RMAX : r;
             const float *M = FULL ? s_mf : s_mr + T.mr_off[r];
-            static_assert(!FULL || RMAX == kF, "full-period copy only for the 16-wide kernel");
-            float ar[RMAX], ai[RMAX], cr[RMAX], ci[RMAX];
-            // a = T c for the coefficients of this orbit in matrix `in`
-            auto to_amp = [&](const float *in, float (&xr)[RMAX], float (&xi)[RMAX]) {
+            float c[RMAX];
+            // full-period orbits start on a multiple of 16 members: their vector
+            // positions and member indices are read once, 16 bytes at a time
+            int pos[FULL ? RMAX : 1], mem[FULL ? RMAX : 1];
+            if constexpr (FULL) {
+                const int4 *vp = reinterpret_cast<const int4 *>(T.vec_pos + s0);
+                const int4 *mp = reinterpret_cast<const int4 *>(T.members + s0);
 #pragma unroll
-                for (int a = 0; a < RMAX; a++) {
-                    if (a < R) {
-                        const int pos = vpos(a);
-                        cr[a] = in[row_re + pos];
-                        ci[a] = in[row_im + pos];
-                    }
+                for (int q = 0; q < RMAX / 4; q++) {
+                    const int4 v = __ldg(vp + q), w = __ldg(mp + q);
+                    pos[4 * q] = v.x;
+                    pos[4 * q + 1] = v.y;
+                    pos[4 * q + 2] = v.z;
+                    pos[4 * q + 3] = v.w;
+                    mem[4 * q] = w.x;
+                    mem[4 * q + 1] = w.y;
+                    mem[4 * q + 2] = w.z;
+                    mem[4 * q + 3] = w.w;
                 }
+            }
+            auto vpos = [&](int a) -> int {
+                if constexpr (FULL) return pos[a];
+                else return T.vec_pos[s0 + a];
+            };
+            auto cost_of = [&](int j) -> float {
+                int idx;
+                if constexpr (FULL) idx = mem[j];
+                else idx = T.members[s0 + j];
+                return A.cost_dtype == 0 ? __ldg(reinterpret_cast<const float *>(A.cost) + idx)
+                                         : (float)__ldg(reinterpret_cast<const unsigned char *>(A.cost) + idx);
+            };
+            // x = T c for this lane's row of the orbit's coefficients in `in`
+            auto to_amp = [&](const float *in, float (&x)[RMAX]) {
+#pragma unroll
+                for (int a = 0; a < RMAX; a++)
+                    if (a < R) c[a] = in[row + vpos(a)];
                 // member sums accumulated side by side (independent FMA chains)
 #pragma unroll
-                for (int j = 0; j < RMAX; j++) xr[j] = xi[j] = 0.f;
+                for (int j = 0; j < RMAX; j++) x[j] = 0.f;
 #pragma unroll
                 for (int a = 0; a < RMAX; a++) {
                     if (a >= R) continue;
@@ -925,31 +954,24 @@ __global__ void __launch_bounds__(kOrbitThreads) orbit_kernel(OrbitTabs T, Orbit
 #pragma unroll
                         for (int q = 0; q < RMAX / 4; q++) {
                             const float4 m = MT4[q];
-                            xr[4 * q] = fmaf(m.x, cr[a], xr[4 * q]);
-                            xi[4 * q] = fmaf(m.x, ci[a], xi[4 * q]);
-                            xr[4 * q + 1] = fmaf(m.y, cr[a], xr[4 * q + 1]);
-                            xi[4 * q + 1] = fmaf(m.y, ci[a], xi[4 * q + 1]);
-                            xr[4 * q + 2] = fmaf(m.z, cr[a], xr[4 * q + 2]);
-                            xi[4 * q + 2] = fmaf(m.z, ci[a], xi[4 * q + 2]);
-                            xr[4 * q + 3] = fmaf(m.w, cr[a], xr[4 * q + 3]);
-                            xi[4 * q + 3] = fmaf(m.w, ci[a], xi[4 * q + 3]);
+                            x[4 * q] = fmaf(m.x, c[a], x[4 * q]);
+                            x[4 * q + 1] = fmaf(m.y, c[a], x[4 * q + 1]);
+                            x[4 * q + 2] = fmaf(m.z, c[a], x[4 * q + 2]);
+                            x[4 * q + 3] = fmaf(m.w, c[a], x[4 * q + 3]);
                         }
                     } else {
 #pragma unroll
                         for (int j = 0; j < RMAX; j++) {
                             if (j >= R) continue;
-                            const float m = M[j * R + a];
-                            xr[j] = fmaf(m, cr[a], xr[j]);
-                            xi[j] = fmaf(m, ci[a], xi[j]);
+                            x[j] = fmaf(M[j * R + a], c[a], x[j]);
                         }
                     }
                 }
             };
-            // c = T^T a written to `out` (with the tf32 split when out_lo)
-            auto from_amp = [&](const float (&xr)[RMAX], const float (&xi)[RMAX], float *out, float *out_lo) {
-                // coefficient sums accumulated side by side in cr / ci (free here)
+            // c = T^T x written to this lane's row of `out` (tf32 split when out_lo)
+            auto from_amp = [&](const float (&x)[RMAX], float *out, float *out_lo) {
 #pragma unroll
-                for (int a = 0; a < RMAX; a++) cr[a] = ci[a] = 0.f;
+                for (int a = 0; a < RMAX; a++) c[a] = 0.f;
 #pragma unroll
                 for (int j = 0; j < RMAX; j++) {
                     if (j >= R) continue;
@@ -958,104 +980,91 @@ __global__ void __launch_bounds__(kOrbitThreads) orbit_kernel(OrbitTabs T, Orbit
 #pragma unroll
                         for (int q = 0; q < RMAX / 4; q++) {
                             const float4 m = M4[q];
-                            cr[4 * q] = fmaf(m.x, xr[j], cr[4 * q]);
-                            ci[4 * q] = fmaf(m.x, xi[j], ci[4 * q]);
-                            cr[4 * q + 1] = fmaf(m.y, xr[j], cr[4 * q + 1]);
-                            ci[4 * q + 1] = fmaf(m.y, xi[j], ci[4 * q + 1]);
-                            cr[4 * q + 2] = fmaf(m.z, xr[j], cr[4 * q + 2]);
-                            ci[4 * q + 2] = fmaf(m.z, xi[j], ci[4 * q + 2]);
-                            cr[4 * q + 3] = fmaf(m.w, xr[j], cr[4 * q + 3]);
-                            ci[4 * q + 3] = fmaf(m.w, xi[j], ci[4 * q + 3]);
+                            c[4 * q] = fmaf(m.x, x[j], c[4 * q]);
+                            c[4 * q + 1] = fmaf(m.y, x[j], c[4 * q + 1]);
+                            c[4 * q + 2] = fmaf(m.z, x[j], c[4 * q + 2]);
+                            c[4 * q + 3] = fmaf(m.w, x[j], c[4 * q + 3]);
                         }
                     } else {
 #pragma unroll
                         for (int a = 0; a < RMAX; a++) {
                             if (a >= R) continue;
-                            const float m = M[j * R + a];
-                            cr[a] = fmaf(m, xr[j], cr[a]);
-                            ci[a] = fmaf(m, xi[j], ci[a]);
+                            c[a] = fmaf(M[j * R + a], x[j], c[a]);
                         }
                     }
                 }
 #pragma unroll
                 for (int a = 0; a < RMAX; a++) {
                     if (a >= R) continue;
-                    const int pos = vpos(a);
-                    put(out, out_lo, row_re + pos, cr[a]);
-                    put(out, out_lo, row_im + pos, ci[a]);
+                    put(out, out_lo, row + vpos(a), c[a]);
                 }
             };
+            float x[RMAX];
             if (MODE == ORB_INIT) {
 #pragma unroll
                 for (int j = 0; j < RMAX; j++) {
                     if (j >= R) continue;
-                    const float2 v = A.init ? A.init[T.members[s0 + j]] : make_float2(A.amp0, 0.f);
-                    ar[j] = v.x;
-                    ai[j] = v.y;
+                    int mj;
+                    if constexpr (FULL) mj = mem[j];
+                    else mj = T.members[s0 + j];
+                    const float2 v = A.init ? A.init[mj] : make_float2(A.amp0, 0.f);
+                    x[j] = part ? v.y : v.x;
                 }
-                if (A.ckpt) from_amp(ar, ai, A.ckpt, nullptr);
+                if (A.ckpt) from_amp(x, A.ckpt, nullptr);
 #pragma unroll
                 for (int j = 0; j < RMAX; j++) {
                     if (j >= R) continue;
-                    const float2 w = cmul(make_float2(ar[j], ai[j]), turn_phase(cf.g_hi, cf.g_lo, cost_of(j), 0.f));
-                    ar[j] = w.x;
-                    ai[j] = w.y;
+                    x[j] = take(cmul(pair_of(x[j]), turn_phase(cf.g_hi, cf.g_lo, cost_of(j), 0.f)));
                 }
-                from_amp(ar, ai, A.out, A.out_lo);
+                from_amp(x, A.out, A.out_lo);
             } else if (MODE == ORB_PHASE) {
-                to_amp(A.in, ar, ai);
+                to_amp(A.in, x);
 #pragma unroll
                 for (int j = 0; j < RMAX; j++) {
                     if (j >= R) continue;
-                    const float2 w = cmul(make_float2(ar[j], ai[j]), turn_phase(cf.g_hi, cf.g_lo, cost_of(j), 0.f));
-                    ar[j] = w.x;
-                    ai[j] = w.y;
+                    x[j] = take(cmul(pair_of(x[j]), turn_phase(cf.g_hi, cf.g_lo, cost_of(j), 0.f)));
                 }
-                from_amp(ar, ai, A.out, A.out_lo);
+                from_amp(x, A.out, A.out_lo);
             } else if (MODE == ORB_LAST) {
-                to_amp(A.in, ar, ai);
+                to_amp(A.in, x);
                 const float c0 = A.c0 ? (float)__ldg(A.c0) : 0.f;
 #pragma unroll
                 for (int j = 0; j < RMAX; j++) {
                     if (j >= R) continue;
                     const float C = cost_of(j);
-                    contrib = fmaf(C, fmaf(ar[j], ar[j], ai[j] * ai[j]), contrib);
-                    ar[j] *= C - c0;
-                    ai[j] *= C - c0;
+                    contrib = fmaf(C, x[j] * x[j], contrib);  // C |x|^2 over the two lanes
+                    x[j] *= C - c0;
                 }
-                if (A.out) from_amp(ar, ai, A.out, A.out_lo);
+                if (A.out) from_amp(x, A.out, A.out_lo);
             } else {  // ORB_BWD
                 // two matrices to read: start the second one's lines toward L2
                 // while the first is fetched and transformed
 #pragma unroll
                 for (int a = 0; a < RMAX; a++) {
                     if (a >= R) continue;
-                    const int pos = vpos(a);
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.in + row_re + pos));
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.in + row_im + pos));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.in + row + vpos(a)));
                 }
-                float pr[RMAX], pi[RMAX];
-                to_amp(A.in_psi, pr, pi);
-                to_amp(A.in, ar, ai);
+                float pv[RMAX];
+                to_amp(A.in_psi, pv);
+                to_amp(A.in, x);
                 const float c0 = A.c0 ? (float)__ldg(A.c0) : 0.f;
 #pragma unroll
                 for (int j = 0; j < RMAX; j++) {
                     if (j >= R) continue;
                     const float C = cost_of(j);
                     const float2 ph = turn_phase(cf.g_hi, cf.g_lo, C, 0.f);
-                    const float2 phi = cmul(make_float2(pr[j], pi[j]), ph);
-                    contrib = fmaf(C - c0, ar[j] * phi.y - ai[j] * phi.x, contrib);
+                    const float2 phi = cmul(pair_of(pv[j]), ph);
+                    const float2 mu = pair_of(x[j]);
+                    if (part == 0) contrib = fmaf(C - c0, mu.x * phi.y - mu.y * phi.x, contrib);
                     // undo the phase on mu: mu conj(ph)
-                    const float xr = fmaf(ar[j], ph.x, ai[j] * ph.y), xi = fmaf(ai[j], ph.x, -ar[j] * ph.y);
-                    ar[j] = xr;
-                    ai[j] = xi;
+                    x[j] = take(make_float2(fmaf(mu.x, ph.x, mu.y * ph.y), fmaf(mu.y, ph.x, -mu.x * ph.y)));
                 }
-                if (A.out) from_amp(ar, ai, A.out, A.out_lo);
+                if (A.out) from_amp(x, A.out, A.out_lo);
             }
         };
         // (the 32-wide copy would not fit the registers next to the generic one)
         if constexpr (RMAX <= 16) {
-            if (r == RMAX && off_full >= 0) body(std::integral_constant<bool, true>());
+            if (r == RMAX && off_full >= 0 && (s0 & 3) == 0) body(std::integral_constant<bool, true>());
             else body(std::integral_constant<bool, false>());
         } else {
             body(std::integral_constant<bool, false>());
@@ -1146,7 +1155,7 @@ cudaError_t launch_eig_prepare(const float *V, int D, int ld, float *Vp, float *
 
 cudaError_t launch_orbit(const OrbitTabs &T, const OrbitArgs &A, cudaStream_t s) {
     if (T.max_r < 1 || T.max_r > kSymMaxN || T.mr_len < 1 || T.mr_len > kOrbitSmem) return cudaErrorInvalidValue;
-    dim3 grid((T.n_orbits + kOrbitThreads - 1) / kOrbitThreads, A.nsets);
+    dim3 grid((T.n_orbits + kOrbitsPerBlock - 1) / kOrbitsPerBlock, A.nsets);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     // the longest orbit sets the register arrays: 16 or 32 members
     const bool r16 = T.max_r <= 16;

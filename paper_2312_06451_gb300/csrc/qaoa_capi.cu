@@ -1692,7 +1692,7 @@ qaoa_status run_units(qaoa_ctx *ctx, const std::vector<Unit> &units, bool grad, 
                     }
                     g.L = &ctx->sym[key];
                     g.ld = g.L->ldp;
-                    g.nob = (g.L->n_orbits + kOrbitThreads - 1) / kOrbitThreads;
+                    g.nob = (g.L->n_orbits + kOrbitsPerBlock - 1) / kOrbitsPerBlock;
                 } else {
                     g.ld = (int)align_up((size_t)u.dim, kEigTile);
                 }
