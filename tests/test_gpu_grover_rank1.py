@@ -385,3 +385,36 @@ def test_mixed_batch_with_x_mixer_graph_replay(Q, oracle_mod):
                 check(jb["E"][i].item(), jb["grad"][i].cpu().numpy(), E_ref, g_ref, cc)
     finally:
         qctx.close()
+
+
+@pytest.mark.parametrize("n,k,p,mode", [(15, 7, 3, "none"), (15, 7, 1, "round"), (15, 7, 1, "none"),
+                                        (13, 6, 4, "none")])
+def test_uncompute_and_single_round(Q, oracle_mod, n, k, p, mode):
+    """Odd Dicke dimensions (C(15, 7) = 6435, C(13, 6) = 1716: a lone last
+    amplitude in the last tile) with a warm start, without checkpoints (the
+    adjoint undoes each round on the state in place) and at p = 1 (the
+    adjoint writes no lambda)."""
+    qg, ctx = Q
+    cost, c = dicke_problem(ctx, oracle_mod, n, k, 860 + n + p)
+    mixer = qg.GroverMixer.dicke(n, k)
+    rng = np.random.default_rng(861 + p)
+    psi0 = rng.standard_normal(mixer.dim) + 1j * rng.standard_normal(mixer.dim)
+    psi0 = (psi0 / np.linalg.norm(psi0)).astype(np.complex64)
+    init = torch.view_as_real(torch.from_numpy(psi0).cuda()).contiguous()
+    for ang in angle_sets(p, 862 + n, c):
+        E, g = ctx.gradient(cost, mixer, ang, init=init, ckpt=mode)
+        E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, ang, "grover", psi0=psi0.astype(np.complex128))
+        check(E, g, E_ref, g_ref, c)
+
+
+def test_tiny_set_without_checkpoints(Q, oracle_mod):
+    """Five feasible states (less than one tile, an odd count) without
+    checkpoints, float32 costs, several rounds."""
+    qg, ctx = Q
+    c = np.array([3.0, -1.0, 4.0, 1.5, -2.5])
+    cost = torch.tensor(c, dtype=torch.float32, device="cuda")
+    mixer = qg.GroverMixer(5, 3)
+    for ang in angle_sets(4, 870, c):
+        E, g = ctx.gradient(cost, mixer, ang, ckpt="none")
+        E_ref, g_ref = oracle_mod.qaoa_gradient(3, c, ang, "grover")
+        check(E, g, E_ref, g_ref, c)
