@@ -888,7 +888,7 @@ __device__ __forceinline__ void set_round(PassConst &K, const RoundCoef &cf, flo
 // the stage-1 (load) layout as 16-byte pairs.  KA is the round applied first
 // (forward: k; adjoint: k+1), KB the second; KP holds the phase (round k+1).
 template <int BWD, int COST, int NBUF, int MA, int MB>
-__device__ __forceinline__ void tile_body_fused(const PassConst &KA, const PassConst &KB, const PassConst &KP,
+__device__ __forceinline__ void tile_body_fused_impl(const PassConst &KA, const PassConst &KB, const PassConst &KP,
                                                 uint32_t g1, const uint32_t (&rs1)[3],
                                                 const PassDesc &D, const float2 *stab, unsigned char *bufs, int b,
                                                 uint32_t bar, uint32_t *sched, uint32_t total, uint32_t base,
@@ -1064,6 +1064,32 @@ __device__ __forceinline__ void tile_body_fused(const PassConst &KA, const PassC
     }
 }
 
+// The common case (both rounds in the tan form) inline; the direct form
+// (|cos b| tiny, rare) out of line, so that its extra registers do not set
+// the register allocation of the common path.
+template <int BWD, int COST, int NBUF, int MA, int MB>
+__device__ __forceinline__ void tile_body_fused(const PassConst &KA, const PassConst &KB, const PassConst &KP,
+                                                uint32_t g1, const uint32_t (&rs1)[3],
+                                                const PassDesc &D, const float2 *stab, unsigned char *bufs, int b,
+                                                uint32_t bar, uint32_t *sched, uint32_t total, uint32_t base,
+                                                uint32_t tl, TileInfo *tinfo, const PassDesc *__restrict__ descs,
+                                                const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor,
+                                                const uint32_t *s_tr) {
+    tile_body_fused_impl<BWD, COST, NBUF, MA, MB>(KA, KB, KP, g1, rs1, D, stab, bufs, b, bar, sched, total, base, tl,
+                                                  tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+}
+template <int BWD, int COST, int NBUF, int MA, int MB>
+__device__ __noinline__ void tile_body_fused_rare(const PassConst &KA, const PassConst &KB, const PassConst &KP,
+                                                  uint32_t g1, const uint32_t (&rs1)[3],
+                                                  const PassDesc &D, const float2 *stab, unsigned char *bufs, int b,
+                                                  uint32_t bar, uint32_t *sched, uint32_t total, uint32_t base,
+                                                  uint32_t tl, TileInfo *tinfo, const PassDesc *__restrict__ descs,
+                                                  const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor,
+                                                  const uint32_t *s_tr) {
+    tile_body_fused_impl<BWD, COST, NBUF, MA, MB>(KA, KB, KP, g1, rs1, D, stab, bufs, b, bar, sched, total, base, tl,
+                                                  tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+}
+
 template <int BWD, int COST, int NBUF, int VAR, int FUSED>
 __global__ void __launch_bounds__(kNT, (BWD && NBUF > 1) ? 1 : 2)
 xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ tile_begin, int ndesc,
@@ -1199,14 +1225,17 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
                 tile_body_fused<BWD, COST, NBUF, 0, 0>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched, total,
                                                        ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
             else if (mk == 1)
-                tile_body_fused<BWD, COST, NBUF, 2, 0>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched, total,
-                                                       ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+                tile_body_fused_rare<BWD, COST, NBUF, 2, 0>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched,
+                                                            total, ti.base, ti.tl, tinfo, descs, tile_begin, ndesc,
+                                                            cursor, s_tr);
             else if (mk == 2)
-                tile_body_fused<BWD, COST, NBUF, 0, 2>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched, total,
-                                                       ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+                tile_body_fused_rare<BWD, COST, NBUF, 0, 2>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched,
+                                                            total, ti.base, ti.tl, tinfo, descs, tile_begin, ndesc,
+                                                            cursor, s_tr);
             else
-                tile_body_fused<BWD, COST, NBUF, 2, 2>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched, total,
-                                                       ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+                tile_body_fused_rare<BWD, COST, NBUF, 2, 2>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched,
+                                                            total, ti.base, ti.tl, tinfo, descs, tile_begin, ndesc,
+                                                            cursor, s_tr);
         } else if (VAR == 1 && K.R.mode == 0)
             tile_body<BWD, COST, NBUF, 0, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base, ti.tl,
                                              tinfo, descs, tile_begin, ndesc, cursor, s_tr);

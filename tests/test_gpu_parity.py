@@ -192,6 +192,30 @@ def test_n12_rotation_regimes(Q, oracle_mod, kind):
     assert_E(Q.expectation(dc, qg.XMixer(n), ang), E_ref, c)
 
 
+@pytest.mark.parametrize("n,kind", [(18, "maxcut_u8"), (22, "sk_f32")])
+def test_pass_rotation_regimes(Q, oracle_mod, n, kind):
+    """The pass kernels with fused round boundaries in every combination of
+    rotation forms: betas 0.1 (tan form), pi/2 (direct form: |cos b| tiny),
+    pi/2, 1.4 (tan form with per-stage rescaling), 2.9, so the boundaries
+    see tan-direct, direct-direct, direct-tan and tan-tan."""
+    import paper_2312_06451_gb300 as qg
+
+    if kind == "maxcut_u8":
+        e = erdos_renyi(n, 0.4, 41)
+        c = oracle_mod.cost_maxcut(n, e)
+        dc = Q.cost_precompute("maxcut", n, edges=e, dtype=torch.uint8)
+    else:
+        J = sk_couplings(n, 42)
+        c = oracle_mod.cost_sk(n, J.astype(np.float64))
+        dc = Q.cost_precompute("sk", n, J=J, dtype=torch.float32)
+    ang = np.array([0.1, np.pi / 2, np.pi / 2, 1.4, 2.9, 0.7, 1.9, 0.3, 2.5, 1.1])
+    E, g = Q.gradient(dc, qg.XMixer(n), ang, ckpt="pass")
+    E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, ang)
+    assert_E(E, E_ref, c)
+    assert_grad(g, g_ref, c)
+    assert_E(Q.expectation(dc, qg.XMixer(n), ang), E_ref, c)
+
+
 def test_many_rounds(Q, oracle_mod):
     import paper_2312_06451_gb300 as qg
 
