@@ -629,10 +629,11 @@ def richardson_fd(f, x, h=1e-3):
     return g
 
 
-@pytest.mark.parametrize("case", ["maxcut_x", "sk_x", "dks_ring", "warm_x", "dks_clique", "maxcut_grover"])
+@pytest.mark.parametrize("case", ["maxcut_x", "sk_x", "dks_ring", "warm_x", "dks_clique", "maxcut_grover",
+                                  "dks_grover_warm", "grover_small_set"])
 def test_gradient_vs_finite_differences(oracle_mod, case):
     rng = np.random.default_rng({"maxcut_x": 1, "sk_x": 2, "dks_ring": 3, "warm_x": 4, "dks_clique": 5,
-                                 "maxcut_grover": 6}[case])
+                                 "maxcut_grover": 6, "dks_grover_warm": 7, "grover_small_set": 8}[case])
     psi0 = None
     if case == "maxcut_x":
         n, p, mix, st = 7, 3, "x", None
@@ -648,6 +649,16 @@ def test_gradient_vs_finite_differences(oracle_mod, case):
     elif case == "maxcut_grover":
         n, p, mix, st = 7, 3, "grover", None
         cost = oracle_mod.cost_maxcut(n, erdos_renyi(n, 0.5, 7))
+    elif case == "dks_grover_warm":
+        # the Grover mixer on the weight-3 states (u = the Dicke state), warm start
+        n, p, mix, st = 8, 3, "grover", None
+        cost = oracle_mod.cost_dks(n, erdos_renyi(n, 0.5, 9), oracle_mod.dicke_states(n, 3))
+        psi0 = rng.standard_normal(len(cost)) + 1j * rng.standard_normal(len(cost))
+        psi0 /= np.linalg.norm(psi0)
+    elif case == "grover_small_set":
+        # any listed feasible set: five states with real costs
+        n, p, mix, st = 3, 4, "grover", None
+        cost = np.array([3.0, -1.0, 4.0, 1.5, -2.5])
     elif case == "dks_clique":
         n, k, p, mix = 7, 3, 2, "clique"
         st = oracle_mod.dicke_states(n, k)
