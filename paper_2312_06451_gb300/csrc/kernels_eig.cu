@@ -298,11 +298,20 @@ struct SplitArgs {
 
 namespace tc {
 constexpr int NACC = 4, NDRAIN = 16;  // accumulator buffers, draining warps
+// Grouped product: GNACC buffers, each a pair of TMEM accumulators (the
+// A_hi B_hi products, and the two small cross terms apart, so the large sum
+// takes only one truncating add per 8-wide K step), drained into the float32
+// registers (round to nearest) every DGRP K chunks.  The truncating adds bias
+// <C> low in proportion to the adds between drains: on DkS n=16, k=8 (block
+// ring mixer, p=6) the error relative to max(|E|, rms C) is about -2.3e-6 -
+// 1.45e-6 DGRP; a single accumulator drained every chunk gave -5.9e-6.
+constexpr int GNACC = 2, DGRP = 3;
 constexpr int BM = 128, BN = 128, BKF = 32, STAGES = 3, NT = 32 * (2 + NDRAIN);
 constexpr uint32_t kTileA = BM * 128, kTileB = BN * 128;
 constexpr uint32_t kStage = 2 * kTileA + 2 * kTileB;  // A_hi, A_lo, B_hi, B_lo
 constexpr uint32_t kSmem = STAGES * kStage + 1024;      // + alignment slack
 constexpr uint32_t kTmemCols = NACC * BN;               // four 128-column accumulators
+static_assert(GNACC * 2 * BN <= (int)kTmemCols, "accumulator pairs exceed the TMEM allocation");
 constexpr uint32_t kSpin = 1u << 24;
 // instruction descriptor: D f32, A/B tf32, both K-major, N = 128, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -624,6 +633,115 @@ __device__ __forceinline__ bool drain_sync_or(bool v) {
 __device__ __forceinline__ bool failed(const int *f) { return *reinterpret_cast<const volatile int *>(f) != 0; }
 }  // namespace tc
 
+// The angle pair an epilogue kind turns by: beta for the eigenvalue phases,
+// gamma for the cost phases (both in turns, as float32 head and tail).
+__device__ __forceinline__ float2 epi_angle(const EpiArgs &E, int s) {
+    const RoundCoef &cf = E.coef[s * E.coef_stride + E.round];
+    return (E.kind == EPI_FWD_EIG || E.kind == EPI_BWD_EIG) ? make_float2(cf.b_hi, cf.b_lo)
+                                                            : make_float2(cf.g_hi, cf.g_lo);
+}
+
+// Sums v[q] over the warp's 32 lanes for each of 16 sets with 16 shuffles:
+// every exchange halves the values a lane holds (a transposed butterfly).
+// Lanes 2i and 2i+1 return the total of set i.
+__device__ __forceinline__ float warp_sum16(float (&v)[16], int lane) {
+    float w[8];
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+        w[i] = (b4 ? v[i + 8] : v[i]) + __shfl_xor_sync(0xffffffffu, b4 ? v[i] : v[i + 8], 16);
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        w[i] = (b3 ? w[i + 4] : w[i]) + __shfl_xor_sync(0xffffffffu, b3 ? w[i] : w[i + 4], 8);
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+        w[i] = (b2 ? w[i + 2] : w[i]) + __shfl_xor_sync(0xffffffffu, b2 ? w[i] : w[i + 2], 4);
+    float t = (b1 ? w[1] : w[0]) + __shfl_xor_sync(0xffffffffu, b1 ? w[0] : w[1], 2);
+    return t + __shfl_xor_sync(0xffffffffu, t, 1);
+}
+
+// Epilogue of one draining thread in the grouped product: row m, the 16 sets
+// s0 .. s0+15 (complex values acc[2q], acc[2q+1]), the same element arithmetic
+// as epi_elem.  The row's eigenvalue or cost is loaded once, the angles come
+// from shared memory, and the adjoint's checkpoint values are loaded 4 sets at
+// a time before those sets' stores, so the thread waits for four round trips to
+// memory, not one per set.  c[q] receives set q's partial-sum term.
+template <int KIND>
+__device__ __forceinline__ void epi_row16(const EpiArgs &E, int m, int s0, int nq, const float2 *ang,
+                                          const float *acc, float (&c)[16]) {
+    constexpr bool kEig = KIND == EPI_FWD_EIG || KIND == EPI_BWD_EIG;
+    constexpr bool kBwd = KIND == EPI_BWD_EIG || KIND == EPI_BWD_PHASE;
+    constexpr bool kShift = KIND == EPI_FWD_LAST || KIND == EPI_BWD_PHASE;
+    float xh = 0.f, xl = 0.f, c0 = 0.f;
+    if (nq <= 0) {  // row past the block, or no valid set
+#pragma unroll
+        for (int q = 0; q < 16; q++) c[q] = 0.f;
+        return;
+    }
+    if (kEig) {
+        xh = __ldg(E.lam_hi + m);
+        xl = __ldg(E.lam_lo + m);
+    } else if (KIND != EPI_STORE) {
+        xh = cost_at(E, m);
+    }
+    if (kShift && E.c0) c0 = (float)__ldg(E.c0);
+    // groups of kGrp sets: the adjoint's checkpoint values of a group are loaded
+    // together (groups of 8 spill at this kernel's register cap and measured slower)
+    constexpr int kGrp = 4;
+#pragma unroll
+    for (int h = 0; h < 16; h += kGrp) {
+        float2 y[kGrp];
+        if (kBwd) {
+#pragma unroll
+            for (int i = 0; i < kGrp; i++) {
+                const size_t o = (size_t)(2 * (s0 + h + i)) * E.ld + m;
+                y[i] = h + i < nq ? make_float2(__ldcg(E.ck_in + o), __ldcg(E.ck_in + o + E.ld))
+                                  : make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kGrp; i++) {
+            const int q = h + i;
+            c[q] = 0.f;
+            if (q >= nq) continue;
+            const size_t o_re = (size_t)(2 * (s0 + q)) * E.ld + m, o_im = o_re + E.ld;
+            const float2 v = make_float2(acc[2 * q], acc[2 * q + 1]);
+            if (KIND == EPI_STORE) {
+                put(E.out, E.out_lo, o_re, v.x);
+                put(E.out, E.out_lo, o_im, v.y);
+            } else if (KIND == EPI_FWD_EIG || KIND == EPI_FWD_PHASE) {
+                if (E.ckpt) {
+                    E.ckpt[o_re] = v.x;
+                    E.ckpt[o_im] = v.y;
+                }
+                const float2 w = cmul(v, turn_phase(ang[q].x, ang[q].y, xh, xl));
+                put(E.out, E.out_lo, o_re, w.x);
+                put(E.out, E.out_lo, o_im, w.y);
+            } else if (KIND == EPI_FWD_LAST) {
+                c[q] = xh * fmaf(v.x, v.x, v.y * v.y);
+                if (E.out) {
+                    E.out[o_re] = v.x;
+                    E.out[o_im] = v.y;
+                }
+                if (E.out2) {
+                    const float Cs = xh - c0;
+                    put(E.out2, E.out2_lo, o_re, Cs * v.x);
+                    put(E.out2, E.out2_lo, o_im, Cs * v.y);
+                }
+            } else {  // adjoint: partial with the checkpoint turned forward, then undo the phase on v
+                const float2 ph = turn_phase(ang[q].x, ang[q].y, xh, xl);
+                const float2 f = cmul(y[i], ph);
+                c[q] = (kEig ? xh + xl : xh - c0) * (v.x * f.y - v.y * f.x);
+                if (kEig || E.out) {
+                    const float2 w = make_float2(fmaf(v.x, ph.x, v.y * ph.y), fmaf(v.y, ph.x, -v.x * ph.y));
+                    put(E.out, E.out_lo, o_re, w.x);
+                    put(E.out, E.out_lo, o_im, w.y);
+                }
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(tc::NT, 1)
 gemm_tc_grouped_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                        const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int ntn,
@@ -637,10 +755,11 @@ gemm_tc_grouped_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_co
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf[tc::NACC], acce[tc::NACC];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf[tc::GNACC], acce[tc::GNACC];
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     __shared__ float red[4][TBN / 2];
+    __shared__ float2 s_ang[2][TBN / 2];  // per-set angles of a tile, by tile parity
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
@@ -654,7 +773,7 @@ gemm_tc_grouped_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_co
             tc::mbar_init(tc::su32(&full[st]), 1);
             tc::mbar_init(tc::su32(&empty[st]), 1);
         }
-        for (int b = 0; b < tc::NACC; b++) {
+        for (int b = 0; b < tc::GNACC; b++) {
             tc::mbar_init(tc::su32(&accf[b]), 1);
             tc::mbar_init(tc::su32(&acce[b]), tc::NDRAIN);
         }
@@ -693,12 +812,13 @@ gemm_tc_grouped_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_co
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int g = 0;
+            int g = 0, a = 0;  // chunks (stages), accumulator groups
             for (int tile = blockIdx.x; tile < ntiles && !tc::failed(&s_fail); tile += gridDim.x) {
                 const int nk = gt[tile / ntn].kext / BKF;
                 for (int kb = 0; kb < nk; kb++, g++) {
-                    const int st = g % STAGES, b = g % tc::NACC;
-                    if (g >= tc::NACC && !tc::mbar_wait(tc::su32(&acce[b]), ((g / tc::NACC) & 1) ^ 1)) {
+                    const int st = g % STAGES, b = a % tc::GNACC;
+                    const bool first = kb % tc::DGRP == 0, last = kb % tc::DGRP == tc::DGRP - 1 || kb == nk - 1;
+                    if (first && a >= tc::GNACC && !tc::mbar_wait(tc::su32(&acce[b]), ((a / tc::GNACC) & 1) ^ 1)) {
                         atomicExch(&s_fail, 1);
                         break;
                     }
@@ -708,18 +828,22 @@ gemm_tc_grouped_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_co
                     }
                     tc::fence_after();
                     const uint32_t base = tc::su32(smem + st * kStage);
-                    const uint32_t d = tmem + (uint32_t)(b * TBN);
+                    const uint32_t d = tmem + (uint32_t)(b * 2 * TBN), dc = d + (uint32_t)TBN;
 #pragma unroll
                     for (int kk = 0; kk < BKF / 8; kk++) {
                         const uint64_t ah = tc::sdesc(base + kk * 32), al = tc::sdesc(base + kTileA + kk * 32);
                         const uint64_t bh = tc::sdesc(base + 2 * kTileA + kk * 32),
                                        bl = tc::sdesc(base + 2 * kTileA + kTileB + kk * 32);
-                        tc::mma_tf32(d, al, bh, tc::kIdesc, kk ? 1u : 0u);
-                        tc::mma_tf32(d, ah, bl, tc::kIdesc, 1u);
-                        tc::mma_tf32(d, ah, bh, tc::kIdesc, 1u);
+                        const uint32_t accum = (first && kk == 0) ? 0u : 1u;
+                        tc::mma_tf32(dc, al, bh, tc::kIdesc, accum);
+                        tc::mma_tf32(dc, ah, bl, tc::kIdesc, 1u);
+                        tc::mma_tf32(d, ah, bh, tc::kIdesc, accum);
                     }
                     tc::mma_commit(tc::su32(&empty[st]));
-                    tc::mma_commit(tc::su32(&accf[b]));
+                    if (last) {
+                        tc::mma_commit(tc::su32(&accf[b]));
+                        a++;
+                    }
                 }
             }
         }
@@ -727,33 +851,39 @@ gemm_tc_grouped_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_co
         // draining warps: warp w reads accumulator rows (TMEM lanes) 32 (w % 4) ..
         // and columns kCols * ch .. (ch = which of the quarter's warps)
         constexpr int kCols = TBN / (tc::NDRAIN / 4);
+        static_assert(kCols == 32, "the epilogue takes 16 sets per thread");
         const uint32_t lrow = (uint32_t)((warp & 3) * 32) << 16;
         const int ch = (warp - 2) >> 2, rq = warp & 3, dt = tid - 64;
-        int g = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int a = 0, par = 0;  // accumulator groups drained, tile parity
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, par ^= 1) {
             const GroupTile G = gt[tile / ntn];
             const int n0 = (tile % ntn) * TBN, nk = G.kext / BKF;
+            // this tile's angles; the buffer was last read two tiles ago, before
+            // the draining warps' barrier of the previous tile
+            if (dt < TBN / 2 && n0 / 2 + dt < E.nsets && E.kind != EPI_STORE && E.kind != EPI_FWD_LAST)
+                s_ang[par][dt] = epi_angle(E, n0 / 2 + dt);
             float acc[kCols];
 #pragma unroll
             for (int c = 0; c < kCols; c++) acc[c] = 0.f;
             bool ok = !tc::failed(&s_fail);
-            for (int kb = 0; kb < nk && ok; kb++, g++) {
-                const int b = g % tc::NACC;
-                if (!tc::mbar_wait(tc::su32(&accf[b]), (g / tc::NACC) & 1)) {
+            for (int j = 0; j < (nk + tc::DGRP - 1) / tc::DGRP && ok; j++, a++) {
+                const int b = a % tc::GNACC;
+                if (!tc::mbar_wait(tc::su32(&accf[b]), (a / tc::GNACC) & 1)) {
                     atomicExch(&s_fail, 1);
                     ok = false;
                     break;
                 }
                 tc::fence_after();
-                uint32_t r[kCols / 16][16];
 #pragma unroll
-                for (int q = 0; q < kCols / 16; q++)
-                    tc::tmem_ld16(tmem + lrow + (uint32_t)(b * TBN + ch * kCols + 16 * q), r[q]);
-                tc::tmem_wait_ld();
+                for (int q = 0; q < kCols / 16; q++) {  // 16 columns of the pair at a time
+                    uint32_t r[16], rc[16];
+                    const uint32_t col = tmem + lrow + (uint32_t)(b * 2 * TBN + ch * kCols + 16 * q);
+                    tc::tmem_ld16(col, r);
+                    tc::tmem_ld16(col + TBN, rc);
+                    tc::tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < kCols / 16; q++)
-#pragma unroll
-                    for (int i = 0; i < 16; i++) acc[16 * q + i] += __uint_as_float(r[q][i]);
+                    for (int i = 0; i < 16; i++) acc[16 * q + i] += __uint_as_float(r[i]) + __uint_as_float(rc[i]);
+                }
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(tc::su32(&acce[b]));
@@ -761,17 +891,21 @@ gemm_tc_grouped_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_co
             // the draining warps agree on whether the tile completed
             if (tc::drain_sync_or(!ok || tc::failed(&s_fail))) break;
             const int m = G.out_row + rq * 32 + lane;
-#pragma unroll
-            for (int q = 0; q < kCols / 2; q++) {
-                const int qq = ch * (kCols / 2) + q;  // set within the tile
-                const int s = n0 / 2 + qq;
-                float contrib = 0.f;
-                if (m < G.row_end && s < E.nsets) contrib = epi_elem(E, m, s, make_float2(acc[2 * q], acc[2 * q + 1]));
-                if (E.part) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, o);
-                    if (lane == 0) red[rq][qq] = contrib;
-                }
+            const int s0 = n0 / 2 + ch * (kCols / 2);  // first of this thread's sets
+            const int nq = m < G.row_end ? min(kCols / 2, E.nsets - s0) : 0;
+            const float2 *ang = &s_ang[par][ch * (kCols / 2)];
+            float c[kCols / 2];
+            switch (E.kind) {
+            case EPI_STORE: epi_row16<EPI_STORE>(E, m, s0, nq, ang, acc, c); break;
+            case EPI_FWD_EIG: epi_row16<EPI_FWD_EIG>(E, m, s0, nq, ang, acc, c); break;
+            case EPI_FWD_PHASE: epi_row16<EPI_FWD_PHASE>(E, m, s0, nq, ang, acc, c); break;
+            case EPI_FWD_LAST: epi_row16<EPI_FWD_LAST>(E, m, s0, nq, ang, acc, c); break;
+            case EPI_BWD_EIG: epi_row16<EPI_BWD_EIG>(E, m, s0, nq, ang, acc, c); break;
+            default: epi_row16<EPI_BWD_PHASE>(E, m, s0, nq, ang, acc, c); break;
+            }
+            if (E.part) {
+                const float t = warp_sum16(c, lane);
+                if (!(lane & 1)) red[rq][ch * (kCols / 2) + (lane >> 1)] = t;
             }
             if (E.part) {
                 tc::drain_sync();
