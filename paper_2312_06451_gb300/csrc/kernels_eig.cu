@@ -297,8 +297,8 @@ struct SplitArgs {
 };
 
 namespace tc {
-constexpr int NACC = 4, NDRAIN = 16;  // accumulator buffers, draining warps
-// Grouped product: GNACC buffers, each a pair of TMEM accumulators (the
+constexpr int NACC = 4, NDRAIN = 16;  // 128-column accumulators in TMEM, draining warps
+// Both products: GNACC buffers, each a pair of TMEM accumulators (the
 // A_hi B_hi products, and the two small cross terms apart, so the large sum
 // takes only one truncating add per 8-wide K step), drained into the float32
 // registers (round to nearest) every DGRP K chunks.  The truncating adds bias
@@ -386,251 +386,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-}  // namespace tc
-
-__global__ void __launch_bounds__(tc::NT, 1)
-gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int Kp, int ntn,
-               EpiArgs E, SplitArgs SP, int *err, const GroupTile *__restrict__ gt) {
-    using tc::BKF;
-    using tc::kStage;
-    using tc::kTileA;
-    using tc::kTileB;
-    using tc::STAGES;
-    constexpr int TBM = tc::BM, TBN = tc::BN;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf[tc::NACC], acce[tc::NACC];
-    __shared__ uint32_t tmem_base;
-    __shared__ int s_fail;
-    __shared__ float red[4][TBN / 2];
-    __shared__ int s_last;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // blocks below SP.full take a whole tile; the rest take one K segment of
-    // one of the remaining tiles
-    int tile = blockIdx.x, seg = 0, nsegs = 1;
-    if ((int)blockIdx.x >= SP.full) {
-        const int u = blockIdx.x - SP.full;
-        tile = SP.full + u / SP.nseg;
-        seg = u % SP.nseg;
-        nsegs = SP.nseg;
-    }
-    const int mt = tile / ntn, nt = tile % ntn;
-    const int n0 = nt * TBN;
-    // plain product: the whole matrix in 128 x 128 tiles; grouped product
-    // (block-diagonal A): the block's rows, K range and valid rows from the table
-    int m0 = mt * TBM, a_row = mt * TBM, k_off = 0, kext = Kp, row_end = E.M, pidx = mt;
-    if (gt) {
-        const GroupTile g = gt[mt];
-        m0 = g.out_row;
-        a_row = g.a_row;
-        k_off = g.k_off;
-        kext = g.kext;
-        row_end = g.row_end;
-        pidx = g.part_idx;
-    }
-    const int nk_all = kext / BKF;
-    const int kb0 = (int)((int64_t)nk_all * seg / nsegs);
-    const int nk = (int)((int64_t)nk_all * (seg + 1) / nsegs) - kb0;
-
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&tmem_base)),
-                     "r"(tc::kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 32) {
-        for (int s = 0; s < STAGES; s++) {
-            tc::mbar_init(tc::su32(&full[s]), 1);
-            tc::mbar_init(tc::su32(&empty[s]), 1);
-        }
-        for (int b = 0; b < tc::NACC; b++) {
-            tc::mbar_init(tc::su32(&accf[b]), 1);
-            tc::mbar_init(tc::su32(&acce[b]), tc::NDRAIN);  // one arrive per draining warp
-        }
-        s_fail = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = tmem_base;
-    int issued = 0;  // stages the producer has started (for a clean exit on timeout)
-    constexpr int kCols = TBN / (tc::NDRAIN / 4);  // accumulator columns per draining warp
-    float acc[kCols];               // its part of one accumulator row
-
-    if (warp == 0) {
-        if (lane == 0) {
-            for (int kb = 0; kb < nk; kb++) {
-                const int s = kb % STAGES;
-                if (kb >= STAGES && !tc::mbar_wait(tc::su32(&empty[s]), ((kb / STAGES) & 1) ^ 1)) {
-                    atomicExch(&s_fail, 1);
-                    break;
-                }
-                const uint32_t base = tc::su32(smem + s * kStage);
-                const uint32_t fb = tc::su32(&full[s]);
-                tc::mbar_expect(fb, kStage);
-                const int kx = (kb0 + kb) * BKF;
-                tc::tma_2d(base, &tmAh, kx, a_row, fb);
-                tc::tma_2d(base + kTileA, &tmAl, kx, a_row, fb);
-                tc::tma_2d(base + 2 * kTileA, &tmBh, k_off + kx, n0, fb);
-                tc::tma_2d(base + 2 * kTileA + kTileB, &tmBl, k_off + kx, n0, fb);
-                issued = kb + 1;
-            }
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {
-            for (int kb = 0; kb < nk; kb++) {
-                const int s = kb % STAGES, b = kb % tc::NACC;
-                if (kb >= tc::NACC && !tc::mbar_wait(tc::su32(&acce[b]), ((kb / tc::NACC) & 1) ^ 1)) {
-                    atomicExch(&s_fail, 1);
-                    break;
-                }
-                if (!tc::mbar_wait(tc::su32(&full[s]), (kb / STAGES) & 1)) {
-                    atomicExch(&s_fail, 1);
-                    break;
-                }
-                tc::fence_after();
-                const uint32_t base = tc::su32(smem + s * kStage);
-                const uint32_t d = tmem + (uint32_t)(b * TBN);
-#pragma unroll
-                for (int kk = 0; kk < BKF / 8; kk++) {
-                    const uint64_t ah = tc::sdesc(base + kk * 32), al = tc::sdesc(base + kTileA + kk * 32);
-                    const uint64_t bh = tc::sdesc(base + 2 * kTileA + kk * 32),
-                                   bl = tc::sdesc(base + 2 * kTileA + kTileB + kk * 32);
-                    tc::mma_tf32(d, al, bh, tc::kIdesc, kk ? 1u : 0u);
-                    tc::mma_tf32(d, ah, bl, tc::kIdesc, 1u);
-                    tc::mma_tf32(d, ah, bh, tc::kIdesc, 1u);
-                }
-                tc::mma_commit(tc::su32(&empty[s]));
-                tc::mma_commit(tc::su32(&accf[b]));
-            }
-        }
-    } else {
-        // draining warps: warp w reads accumulator rows (TMEM lanes) 32 (w % 4) ..
-        // and columns kCols * ch .. (ch = which of the quarter's warps)
-        const uint32_t lrow = (uint32_t)((warp & 3) * 32) << 16;
-        const int ch = (warp - 2) >> 2;
-#pragma unroll
-        for (int c = 0; c < kCols; c++) acc[c] = 0.f;
-        for (int kb = 0; kb < nk; kb++) {
-            const int b = kb % tc::NACC;
-            if (!tc::mbar_wait(tc::su32(&accf[b]), (kb / tc::NACC) & 1)) {
-                atomicExch(&s_fail, 1);
-                break;
-            }
-            tc::fence_after();
-            {
-                uint32_t r[kCols / 16][16];
-#pragma unroll
-                for (int q = 0; q < kCols / 16; q++)
-                    tc::tmem_ld16(tmem + lrow + (uint32_t)(b * TBN + ch * kCols + 16 * q), r[q]);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int q = 0; q < kCols / 16; q++)
-#pragma unroll
-                    for (int i = 0; i < 16; i++) acc[16 * q + i] += __uint_as_float(r[q][i]);
-            }
-            tc::fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(tc::su32(&acce[b]));
-        }
-    }
-    __syncwarp();
-    const bool failed = __syncthreads_or(s_fail) != 0;
-    bool do_epi = !failed;
-    if (failed) {
-        if (tid == 0) atomicOr(err, DERR_TIMEOUT);
-        // let started loads land before the block exits
-        if (warp == 0 && lane == 0)
-            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; kb++)
-                tc::mbar_wait(tc::su32(&full[kb % STAGES]), (kb / STAGES) & 1);
-    } else if (nsegs > 1) {
-        // K segment of a split tile: store the partial accumulator; the
-        // segment that finishes last adds all partials in segment order (the
-        // same sum whichever finishes last) and runs the epilogue.  No block
-        // ever waits for another.
-        const int ti = tile - SP.full;
-        float *slots = SP.ws + (size_t)ti * nsegs * (TBM * TBN);
-        const int r = (warp & 3) * 32 + lane, c0 = ((warp - 2) >> 2) * kCols;
-        if (warp >= 2) {
-            float *dst = slots + (size_t)seg * (TBM * TBN) + (size_t)r * TBN + c0;
-#pragma unroll
-            for (int c = 0; c < kCols; c++) dst[c] = acc[c];
-        }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            const unsigned prev = atomicAdd(&SP.cnt[ti], 1u);
-            s_last = prev == (unsigned)(nsegs - 1) ? 1 : 0;
-            if (s_last) atomicExch(&SP.cnt[ti], 0u);  // ready for the next product
-        }
-        __syncthreads();
-        do_epi = s_last != 0;
-        if (do_epi && warp >= 2) {
-            __threadfence();
-#pragma unroll
-            for (int c = 0; c < kCols; c++) {
-                float v = 0.f;
-                for (int g = 0; g < nsegs; g++) v += __ldcg(slots + (size_t)g * (TBM * TBN) + (size_t)r * TBN + c0 + c);
-                acc[c] = v;
-            }
-        }
-    }
-    if (do_epi && warp >= 2) {
-        const int rq = warp & 3, ch = (warp - 2) >> 2;
-        const int m = m0 + rq * 32 + lane;
-#pragma unroll
-        for (int q = 0; q < kCols / 2; q++) {
-            const int qq = ch * (kCols / 2) + q;  // set within the tile
-            const int s = n0 / 2 + qq;
-            float contrib = 0.f;
-            if (m < row_end && s < E.nsets) contrib = epi_elem(E, m, s, make_float2(acc[2 * q], acc[2 * q + 1]));
-            if (E.part) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, o);
-                if (lane == 0) red[rq][qq] = contrib;
-            }
-        }
-    }
-    if (E.part && do_epi) {
-        __syncthreads();
-        if (tid < TBN / 2) {
-            const int s = n0 / 2 + tid;
-            const double t = ((double)red[0][tid] + (double)red[1][tid]) + ((double)red[2][tid] + (double)red[3][tid]);
-            if (s < E.nsets) E.part[(size_t)s * E.part_stride + pidx] = t;
-        }
-    }
-    tc::fence_before();
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::kTmemCols)
-                     : "memory");
-}
-
-// Persistent grouped (block-diagonal) variant: one CTA per SM walks the tile
-// table (tiles c, c + grid, ...; the table is sorted by K extent) with the
-// same TMA ring, MMA chain and per-chunk drain as gemm_tc_kernel.  TMEM is
-// allocated once and the barrier phases run on across tiles, so the TMA and
-// MMA warps start the next tile while the draining warps run this tile's
-// epilogue; the epilogue's per-set sums use a named barrier of the draining
-// warps only.
-namespace tc {
-// barrier of the draining warps only (named barrier 1)
-__device__ __forceinline__ void drain_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * NDRAIN) : "memory"); }
-// the same barrier, returning whether any draining thread passed true
-__device__ __forceinline__ bool drain_sync_or(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)v), "n"(32 * NDRAIN)
-        : "memory");
-    return r != 0;
-}
-__device__ __forceinline__ bool failed(const int *f) { return *reinterpret_cast<const volatile int *>(f) != 0; }
 }  // namespace tc
 
 // The angle pair an epilogue kind turns by: beta for the eigenvalue phases,
@@ -741,6 +496,261 @@ __device__ __forceinline__ void epi_row16(const EpiArgs &E, int m, int s0, int n
         }
     }
 }
+
+__global__ void __launch_bounds__(tc::NT, 1)
+gemm_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int Kp, int ntn,
+               EpiArgs E, SplitArgs SP, int *err, const GroupTile *__restrict__ gt) {
+    using tc::BKF;
+    using tc::kStage;
+    using tc::kTileA;
+    using tc::kTileB;
+    using tc::STAGES;
+    constexpr int TBM = tc::BM, TBN = tc::BN;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf[tc::GNACC], acce[tc::GNACC];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    __shared__ float red[4][TBN / 2];
+    __shared__ float2 s_ang[TBN / 2];  // per-set angles of the tile
+    __shared__ int s_last;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // blocks below SP.full take a whole tile; the rest take one K segment of
+    // one of the remaining tiles
+    int tile = blockIdx.x, seg = 0, nsegs = 1;
+    if ((int)blockIdx.x >= SP.full) {
+        const int u = blockIdx.x - SP.full;
+        tile = SP.full + u / SP.nseg;
+        seg = u % SP.nseg;
+        nsegs = SP.nseg;
+    }
+    const int mt = tile / ntn, nt = tile % ntn;
+    const int n0 = nt * TBN;
+    // plain product: the whole matrix in 128 x 128 tiles; grouped product
+    // (block-diagonal A): the block's rows, K range and valid rows from the table
+    int m0 = mt * TBM, a_row = mt * TBM, k_off = 0, kext = Kp, row_end = E.M, pidx = mt;
+    if (gt) {
+        const GroupTile g = gt[mt];
+        m0 = g.out_row;
+        a_row = g.a_row;
+        k_off = g.k_off;
+        kext = g.kext;
+        row_end = g.row_end;
+        pidx = g.part_idx;
+    }
+    const int nk_all = kext / BKF;
+    if (tid >= 64 && tid - 64 < TBN / 2 && n0 / 2 + tid - 64 < E.nsets && E.kind != EPI_STORE &&
+        E.kind != EPI_FWD_LAST)
+        s_ang[tid - 64] = epi_angle(E, n0 / 2 + tid - 64);  // read after the block barriers below
+    const int kb0 = (int)((int64_t)nk_all * seg / nsegs);
+    const int nk = (int)((int64_t)nk_all * (seg + 1) / nsegs) - kb0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&tmem_base)),
+                     "r"(tc::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        for (int s = 0; s < STAGES; s++) {
+            tc::mbar_init(tc::su32(&full[s]), 1);
+            tc::mbar_init(tc::su32(&empty[s]), 1);
+        }
+        for (int b = 0; b < tc::GNACC; b++) {
+            tc::mbar_init(tc::su32(&accf[b]), 1);
+            tc::mbar_init(tc::su32(&acce[b]), tc::NDRAIN);  // one arrive per draining warp
+        }
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_base;
+    int issued = 0;  // stages the producer has started (for a clean exit on timeout)
+    constexpr int kCols = TBN / (tc::NDRAIN / 4);  // accumulator columns per draining warp
+    float acc[kCols];               // its part of one accumulator row
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < nk; kb++) {
+                const int s = kb % STAGES;
+                if (kb >= STAGES && !tc::mbar_wait(tc::su32(&empty[s]), ((kb / STAGES) & 1) ^ 1)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                const uint32_t base = tc::su32(smem + s * kStage);
+                const uint32_t fb = tc::su32(&full[s]);
+                tc::mbar_expect(fb, kStage);
+                const int kx = (kb0 + kb) * BKF;
+                tc::tma_2d(base, &tmAh, kx, a_row, fb);
+                tc::tma_2d(base + kTileA, &tmAl, kx, a_row, fb);
+                tc::tma_2d(base + 2 * kTileA, &tmBh, k_off + kx, n0, fb);
+                tc::tma_2d(base + 2 * kTileA + kTileB, &tmBl, k_off + kx, n0, fb);
+                issued = kb + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (int kb = 0; kb < nk; kb++) {
+                const int s = kb % STAGES, a = kb / tc::DGRP, b = a % tc::GNACC;
+                const bool first = kb % tc::DGRP == 0, last = kb % tc::DGRP == tc::DGRP - 1 || kb == nk - 1;
+                if (first && a >= tc::GNACC && !tc::mbar_wait(tc::su32(&acce[b]), ((a / tc::GNACC) & 1) ^ 1)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                if (!tc::mbar_wait(tc::su32(&full[s]), (kb / STAGES) & 1)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t base = tc::su32(smem + s * kStage);
+                const uint32_t d = tmem + (uint32_t)(b * 2 * TBN), dc = d + (uint32_t)TBN;
+#pragma unroll
+                for (int kk = 0; kk < BKF / 8; kk++) {
+                    const uint64_t ah = tc::sdesc(base + kk * 32), al = tc::sdesc(base + kTileA + kk * 32);
+                    const uint64_t bh = tc::sdesc(base + 2 * kTileA + kk * 32),
+                                   bl = tc::sdesc(base + 2 * kTileA + kTileB + kk * 32);
+                    const uint32_t accum = (first && kk == 0) ? 0u : 1u;
+                    tc::mma_tf32(dc, al, bh, tc::kIdesc, accum);
+                    tc::mma_tf32(dc, ah, bl, tc::kIdesc, 1u);
+                    tc::mma_tf32(d, ah, bh, tc::kIdesc, accum);
+                }
+                tc::mma_commit(tc::su32(&empty[s]));
+                if (last) tc::mma_commit(tc::su32(&accf[b]));
+            }
+        }
+    } else {
+        // draining warps: warp w reads accumulator rows (TMEM lanes) 32 (w % 4) ..
+        // and columns kCols * ch .. (ch = which of the quarter's warps)
+        const uint32_t lrow = (uint32_t)((warp & 3) * 32) << 16;
+        const int ch = (warp - 2) >> 2;
+#pragma unroll
+        for (int c = 0; c < kCols; c++) acc[c] = 0.f;
+        for (int a = 0; a < (nk + tc::DGRP - 1) / tc::DGRP; a++) {
+            const int b = a % tc::GNACC;
+            if (!tc::mbar_wait(tc::su32(&accf[b]), (a / tc::GNACC) & 1)) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            tc::fence_after();
+#pragma unroll
+            for (int q = 0; q < kCols / 16; q++) {  // 16 columns of the pair at a time
+                uint32_t r[16], rc[16];
+                const uint32_t col = tmem + lrow + (uint32_t)(b * 2 * TBN + ch * kCols + 16 * q);
+                tc::tmem_ld16(col, r);
+                tc::tmem_ld16(col + TBN, rc);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; i++) acc[16 * q + i] += __uint_as_float(r[i]) + __uint_as_float(rc[i]);
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tc::su32(&acce[b]));
+        }
+    }
+    __syncwarp();
+    const bool failed = __syncthreads_or(s_fail) != 0;
+    bool do_epi = !failed;
+    if (failed) {
+        if (tid == 0) atomicOr(err, DERR_TIMEOUT);
+        // let started loads land before the block exits
+        if (warp == 0 && lane == 0)
+            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; kb++)
+                tc::mbar_wait(tc::su32(&full[kb % STAGES]), (kb / STAGES) & 1);
+    } else if (nsegs > 1) {
+        // K segment of a split tile: store the partial accumulator; the
+        // segment that finishes last adds all partials in segment order (the
+        // same sum whichever finishes last) and runs the epilogue.  No block
+        // ever waits for another.
+        const int ti = tile - SP.full;
+        float *slots = SP.ws + (size_t)ti * nsegs * (TBM * TBN);
+        const int r = (warp & 3) * 32 + lane, c0 = ((warp - 2) >> 2) * kCols;
+        if (warp >= 2) {
+            float *dst = slots + (size_t)seg * (TBM * TBN) + (size_t)r * TBN + c0;
+#pragma unroll
+            for (int c = 0; c < kCols; c++) dst[c] = acc[c];
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned prev = atomicAdd(&SP.cnt[ti], 1u);
+            s_last = prev == (unsigned)(nsegs - 1) ? 1 : 0;
+            if (s_last) atomicExch(&SP.cnt[ti], 0u);  // ready for the next product
+        }
+        __syncthreads();
+        do_epi = s_last != 0;
+        if (do_epi && warp >= 2) {
+            __threadfence();
+#pragma unroll
+            for (int c = 0; c < kCols; c++) {
+                float v = 0.f;
+                for (int g = 0; g < nsegs; g++) v += __ldcg(slots + (size_t)g * (TBM * TBN) + (size_t)r * TBN + c0 + c);
+                acc[c] = v;
+            }
+        }
+    }
+    if (do_epi && warp >= 2) {
+        static_assert(kCols == 32, "the epilogue takes 16 sets per thread");
+        const int rq = warp & 3, ch = (warp - 2) >> 2;
+        const int m = m0 + rq * 32 + lane;
+        const int s0 = n0 / 2 + ch * (kCols / 2);  // first of this thread's sets
+        const int nq = m < row_end ? min(kCols / 2, E.nsets - s0) : 0;
+        const float2 *ang = &s_ang[ch * (kCols / 2)];
+        float c[kCols / 2];
+        switch (E.kind) {
+        case EPI_STORE: epi_row16<EPI_STORE>(E, m, s0, nq, ang, acc, c); break;
+        case EPI_FWD_EIG: epi_row16<EPI_FWD_EIG>(E, m, s0, nq, ang, acc, c); break;
+        case EPI_FWD_PHASE: epi_row16<EPI_FWD_PHASE>(E, m, s0, nq, ang, acc, c); break;
+        case EPI_FWD_LAST: epi_row16<EPI_FWD_LAST>(E, m, s0, nq, ang, acc, c); break;
+        case EPI_BWD_EIG: epi_row16<EPI_BWD_EIG>(E, m, s0, nq, ang, acc, c); break;
+        default: epi_row16<EPI_BWD_PHASE>(E, m, s0, nq, ang, acc, c); break;
+        }
+        if (E.part) {
+            const float t = warp_sum16(c, lane);
+            if (!(lane & 1)) red[rq][ch * (kCols / 2) + (lane >> 1)] = t;
+        }
+    }
+    if (E.part && do_epi) {
+        __syncthreads();
+        if (tid < TBN / 2) {
+            const int s = n0 / 2 + tid;
+            const double t = ((double)red[0][tid] + (double)red[1][tid]) + ((double)red[2][tid] + (double)red[3][tid]);
+            if (s < E.nsets) E.part[(size_t)s * E.part_stride + pidx] = t;
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::kTmemCols)
+                     : "memory");
+}
+
+// Persistent grouped (block-diagonal) variant: one CTA per SM walks the tile
+// table (tiles c, c + grid, ...; the table is sorted by K extent) with the
+// same TMA ring, MMA chain and per-chunk drain as gemm_tc_kernel.  TMEM is
+// allocated once and the barrier phases run on across tiles, so the TMA and
+// MMA warps start the next tile while the draining warps run this tile's
+// epilogue; the epilogue's per-set sums use a named barrier of the draining
+// warps only.
+namespace tc {
+// barrier of the draining warps only (named barrier 1)
+__device__ __forceinline__ void drain_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * NDRAIN) : "memory"); }
+// the same barrier, returning whether any draining thread passed true
+__device__ __forceinline__ bool drain_sync_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(32 * NDRAIN)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ bool failed(const int *f) { return *reinterpret_cast<const volatile int *>(f) != 0; }
+}  // namespace tc
 
 __global__ void __launch_bounds__(tc::NT, 1)
 gemm_tc_grouped_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
