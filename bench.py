@@ -258,7 +258,7 @@ class Workload:
             xy = "clique" if mixer == "clique" else "ring"
             self.eig_form = eig_form
             if eig_form == "blocks":
-                mixer = qg.xy_sym_mixer(ctx, xy, n, k, precision=gemm)
+                mixer = qg.xy_sym_mixer(ctx, xy, n, k, precision=gemm, cache_file=eig_cache)
             else:
                 mixer = qg.xy_eigen_mixer(ctx, xy, n, k, precision=gemm, cache_file=eig_cache)
             torch.cuda.synchronize()
@@ -955,7 +955,8 @@ def main():
                          "(D=12870), 256 angle sets; 5: 512 uneven instances x 4 sets; "
                          "6: Grover mixer on cost degeneracies, densest 6-subgraph n=100")
     ap.add_argument("--eig-cache", default=None,
-                    help="workload 4: load the mixer's eigendecomposition from this file, or save it there")
+                    help="workload 4: load the mixer's eigendecomposition (dense V or its blocks) from this file, "
+                         "or save it there")
     ap.add_argument("--gemm", default="3xtf32", choices=["fp32", "3xtf32"],
                     help="eigenbasis product precision (workload 4): tcgen05 3xTF32 or CUDA-core float32")
     ap.add_argument("--eig", default="blocks", choices=["blocks", "dense"],

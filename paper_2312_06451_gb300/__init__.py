@@ -273,12 +273,23 @@ def xy_block_hamiltonians(kind: str, n: int, k: int):
     return dims.tolist(), out
 
 
-def xy_sym_mixer(ctx: "Context", kind: str, n: int, k: int, precision: str = "3xtf32") -> EigenSymMixer:
+def xy_sym_mixer(ctx: "Context", kind: str, n: int, k: int, precision: str = "3xtf32",
+                 cache_file: str | None = None) -> EigenSymMixer:
     """EigenSymMixer of the ring or clique XY mixer: the block matrices come
     from the library, each is diagonalised once in float64 with
     torch.linalg.eigh (the pre-computation the paper does for the dense
-    mixer, Sec. 2.1, now on blocks of about 2D/n states)."""
+    mixer, Sec. 2.1, now on blocks of about 2D/n states).  With cache_file the
+    block eigenvectors and eigenvalues are loaded from / saved to that file
+    (save_eigen_mixer's format, kind "<kind>-blocks")."""
+    import os
+
     dims, Hs = xy_block_hamiltonians(kind, n, k)
+    tag = f"{kind}-blocks"
+    if cache_file and os.path.exists(cache_file):
+        V, lam = load_eigen_mixer(cache_file, n, k, tag, ctx.device)
+        if V.numel() != sum(d * d for d in dims) or lam.numel() != sum(dims):
+            raise ValueError(f"mixer file {cache_file} does not match the {kind} blocks of n={n}, k={k}")
+        return EigenSymMixer(n, k, V.to(torch.float32), lam.to(torch.float64), dims, precision)
     dev = f"cuda:{ctx.device}"
     Vs, lams = [], []
     for H in Hs:
@@ -287,6 +298,8 @@ def xy_sym_mixer(ctx: "Context", kind: str, n: int, k: int, precision: str = "3x
         lams.append(lam)
     V = torch.cat(Vs).contiguous()
     lam = torch.cat(lams).contiguous()
+    if cache_file:
+        save_eigen_mixer(cache_file, n, k, V, lam, tag)
     return EigenSymMixer(n, k, V, lam, dims, precision)
 
 

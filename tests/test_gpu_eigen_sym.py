@@ -158,3 +158,30 @@ def test_prepared_operands_follow_the_mixer_not_its_address(Q, oracle_mod):
         dense.V.copy_(dense_ring.V)
         dense.lam.copy_(dense_ring.lam)
         check(*ctx.gradient(dc, dense, ang), *oracle_mod.qaoa_gradient(n, c, ang, "ring", st), c)
+
+
+def test_sym_mixer_cache_file_round_trip(Q, oracle_mod, tmp_path):
+    """The block eigendecomposition written to a cache file and read back
+    gives the same operands and the oracle's numbers; a file for another
+    shape or for the dense form is refused."""
+    qg, ctx = Q
+    n, k, p = 10, 4, 3
+    st, c, dc, _ = problem(qg, ctx, oracle_mod, n, k, 21, "3xtf32", "ring")
+    path = str(tmp_path / "ring10_4.blocks")
+    m1 = qg.xy_sym_mixer(ctx, "ring", n, k, precision="3xtf32", cache_file=path)
+    m2 = qg.xy_sym_mixer(ctx, "ring", n, k, precision="3xtf32", cache_file=path)
+    assert torch.equal(m1.V, m2.V) and torch.equal(m1.lam, m2.lam) and m1.block_dims == m2.block_dims
+    ang = uniform_angles(p, 22)[0]
+    E1, g1 = ctx.gradient(dc, m1, ang)
+    E2, g2 = ctx.gradient(dc, m2, ang)
+    assert E1 == E2 and np.array_equal(g1, g2)
+    E_ref, g_ref = oracle_mod.qaoa_gradient(n, c, ang, "ring", st)
+    check(E2, g2, E_ref, g_ref, c)
+    with pytest.raises(ValueError):
+        qg.xy_sym_mixer(ctx, "clique", n, k, cache_file=path)
+    with pytest.raises(ValueError):
+        qg.xy_sym_mixer(ctx, "ring", n, k + 1, cache_file=path)
+    dense_path = str(tmp_path / "ring10_4.dense")
+    qg.xy_eigen_mixer(ctx, "ring", n, k, cache_file=dense_path)
+    with pytest.raises(ValueError):
+        qg.xy_sym_mixer(ctx, "ring", n, k, cache_file=dense_path)
