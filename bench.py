@@ -14,8 +14,9 @@ mixer applied as a rank-one update.
 
 Prints one JSON line (rank 0).  `value` is measured on the device with CUDA
 events around K steps of the batched entry point (device-resident angles and
-results).  `e2e` times the same batched call end to end: angles copied in from pinned
-host memory and <C> and the gradients read back to the host, every step.
+results).  `e2e` times the same evaluation end to end through the host-buffer
+batched entry point (qaoa_expectation_batched_host): angles copied in from
+pinned host memory and <C> and the gradients read back to the host, every step.
 `roofline` divides the dominant kernel's algorithmic bytes by its CUDA-event
 time inside the timed region.  `cpu_baseline` times the CPU oracle on the host
 cores on one round of the same workload (scaled to the p-round unit).
@@ -381,17 +382,31 @@ class Workload:
         self._call.run()
 
     def e2e_step(self, step, pinned):
-        """Host angles (pinned) -> device, batched call, results -> host."""
+        """This step's angles from the pinned host pool into the call's pinned
+        angle buffers, then the host-buffer batched call
+        (qaoa_expectation_batched_host: angles copied in, launches, <C> and the
+        gradients copied back, synchronised); returns the host results."""
         import torch
 
-        for job, (pool, k, _, A), hp in zip(self.jobs, self.pools, pinned):
+        if getattr(self, "_hcall", None) is None:
+            self._h_ang, self._h_out, hjobs = [], [], []
+            for job, (_, k, _, A) in zip(self.jobs, self.pools):
+                na = A.shape[1]
+                ha = torch.empty(k, na, dtype=torch.float64).pin_memory()
+                hE = torch.empty(k, dtype=torch.float64).pin_memory()
+                hG = torch.empty(k, na, dtype=torch.float64).pin_memory() if self.grad else None
+                hjobs.append({"cost": job["cost"], "mixer": job["mixer"], "angles": ha, "E": hE, "grad": hG,
+                              "init": job.get("init")})
+                self._h_ang.append(ha)
+                self._h_out.append((hE, hG))
+            self._hcall = self.ctx.batched_call_host(hjobs, want_grad=self.grad)
+        for ha, hp, (pool, k, _, _) in zip(self._h_ang, pinned, self.pools):
             s = (step * k) % pool.shape[0]
-            job["angles"].copy_(hp[s:s + k], non_blocking=True)
-        self.run()
-        outs = [j["E"].to("cpu", non_blocking=True) for j in self.jobs]
+            ha.copy_(hp[s:s + k])
+        self._hcall.run()
+        outs = [e for e, _ in self._h_out]
         if self.grad:
-            outs += [j["grad"].to("cpu", non_blocking=True) for j in self.jobs]
-        torch.cuda.current_stream().synchronize()
+            outs += [g for _, g in self._h_out]
         return outs
 
     def h2d_bytes(self):
@@ -789,7 +804,9 @@ def measure(args, W, qg, ctx, stream, dist, ws, rank, local, dev, graph_mode, st
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "run": run,
             "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": W.h2d_bytes(),
-                    "d2h_bytes_per_step": W.d2h_bytes()},
+                    "d2h_bytes_per_step": W.d2h_bytes(),
+                    "api": ("qaoa_expectation_batched_host" if getattr(W, "_hcall", None) is not None
+                            else "device-buffer call with pinned torch copies")},
             "roofline": roof,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 4),
                             "GBps": round(v["algo_bytes"] / v["total_ms"] / 1e6, 1) if v["total_ms"] else None}

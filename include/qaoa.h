@@ -318,6 +318,40 @@ typedef struct {
 qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *jobs,
                                      int want_grad);
 
+/* The same batched evaluation with the angles and results in host memory, for
+ * an angle-finding loop (Sec. 2.3) that proposes angles on the host and reads
+ * <C> (and the gradients) back every iteration.  One call copies every job's
+ * angles to device staging held by the context, enqueues the batched
+ * launches, copies the results back and returns after the context stream has
+ * finished (synchronous).
+ *   h_angles  host, n_sets x 2p float64 (p (n + 1) for QAOA_MIXER_X_MA), read
+ *   h_E       host output, n_sets float64
+ *   h_grad    host output, n_sets rows like h_angles (ignored unless want_grad)
+ *   d_cost, mixer, d_init  device data as in qaoa_job
+ * Pinned host memory (cudaMallocHost, or a pinned tensor) gives asynchronous
+ * copies; pageable memory works at a lower rate.  The caller keeps ownership of
+ * every buffer; the call retains none of them.  Staging grows when a call
+ * needs more and is reused afterwards, so repeating a call with the same job
+ * shapes enqueues no allocation and re-uses the launch plan.  Errors: the
+ * checks of qaoa_expectation_batched, plus QAOA_ERR_INVALID for NULL host
+ * pointers or a capturing stream; a device-side error word raised by the
+ * launches is returned after the synchronisation (QAOA_ERR_INVALID for a
+ * non-finite angle, QAOA_ERR_TIMEOUT for a bounded wait that gave up). */
+typedef struct {
+    const void *d_cost;
+    int cost_dtype;
+    const qaoa_mixer *mixer;
+    int p;
+    int n_sets;
+    const double *h_angles;
+    double *h_E;
+    double *h_grad;
+    const void *d_init;
+} qaoa_host_job;
+
+qaoa_status qaoa_expectation_batched_host(qaoa_ctx *ctx, int n_jobs, const qaoa_host_job *jobs,
+                                          int want_grad);
+
 /* Checkpointing used by qaoa_expectation_batched gradients (default
  * QAOA_CKPT_PASS).  Per unit the planner steps down PASS -> ROUND -> NONE
  * when one angle set's scratch would not fit in free device memory. */

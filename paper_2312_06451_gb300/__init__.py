@@ -28,7 +28,8 @@ __all__ = ["Context", "XMixer", "EigenMixer", "QAOAExpectation", "QAOAError", "p
            "qaoa_cost_precompute", "qaoa_expectation", "qaoa_gradient", "qaoa_expectation_batched",
            "qaoa_gradient_small_noalloc", "ring_eigen_mixer", "clique_eigen_mixer", "xy_eigen_mixer",
            "save_eigen_mixer", "load_eigen_mixer", "GeneralXMixer", "x_terms_mixer", "grover_x_mixer", "GroverMixer",
-           "write_tuning_file", "read_tuning_file", "krawtchouk_weights", "EigenSymMixer", "xy_block_hamiltonians", "xy_sym_mixer", "BatchedCall"]
+           "write_tuning_file", "read_tuning_file", "krawtchouk_weights", "EigenSymMixer", "xy_block_hamiltonians", "xy_sym_mixer", "BatchedCall",
+           "HostBatchedCall", "qaoa_expectation_batched_host"]
 
 _MIXER_IDS = itertools.count(1)
 
@@ -54,6 +55,18 @@ def _dev_tensor(t, name):
         return None
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
         raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    return t
+
+
+def _host_tensor(t, name):
+    """A contiguous float64 host tensor (numpy arrays are wrapped, not copied)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        t = torch.from_numpy(t)
+    if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.is_contiguous()
+            and t.dtype == torch.float64):
+        raise ValueError(f"{name} must be a contiguous float64 host tensor or array")
     return t
 
 
@@ -569,6 +582,40 @@ class Context:
         takes the per-call argument handling off small problems."""
         return BatchedCall(self, jobs, want_grad)
 
+    def batched_call_host(self, jobs, want_grad: bool = False) -> "HostBatchedCall":
+        """qaoa_expectation_batched_host prepared once: jobs as for
+        batched_call, but angles, E and grad are host tensors (pinned ones give
+        asynchronous copies).  run() copies the angles in, evaluates, copies
+        <C> (and the gradients) back into the same host tensors and returns
+        when they are there."""
+        return HostBatchedCall(self, jobs, want_grad)
+
+    def expectation_batched_host(self, jobs, want_grad: bool = False):
+        """One synchronous host-buffer batched call (see batched_call_host)."""
+        self.batched_call_host(jobs, want_grad).run()
+
+    def _host_job_array(self, jobs, want_grad):
+        arr = (B.QaoaHostJob * len(jobs))()
+        keep = []
+        for i, j in enumerate(jobs):
+            ang = _host_tensor(j["angles"], "angles")
+            E = _host_tensor(j["E"], "E")
+            G = _host_tensor(j.get("grad"), "grad")
+            cost = _dev_tensor(j["cost"], "cost")
+            init = _dev_tensor(j.get("init"), "init")
+            n_sets = ang.shape[0] if ang.dim() == 2 else 1
+            mx = j["mixer"]
+            na = ang.shape[-1]
+            p = _rounds(mx, na)
+            if E.numel() < n_sets or (want_grad and (G is None or G.numel() < n_sets * na)):
+                raise ValueError("E (and grad) must hold a result per angle set")
+            keep.append(mx)
+            arr[i] = B.QaoaHostJob(cost.data_ptr(), _cost_dtype(cost), ctypes.pointer(mx.struct), p, n_sets,
+                                   ang.data_ptr(), E.data_ptr(), None if G is None else G.data_ptr(),
+                                   None if init is None else init.data_ptr())
+            keep.extend([ang, E, G, cost, init])
+        return arr, keep
+
     def _job_array(self, jobs):
         arr = (B.QaoaJob * len(jobs))()
         keep = []
@@ -634,6 +681,23 @@ class BatchedCall:
         c._check(c._lib.qaoa_expectation_batched(c._h, self._n, self._arr, self._grad))
 
 
+class HostBatchedCall:
+    """A qaoa_expectation_batched_host call prepared once
+    (Context.batched_call_host): the job structs point at the given host and
+    device tensors, which it keeps alive; run() copies the current contents of
+    the angle tensors in and the results back, synchronously."""
+
+    def __init__(self, ctx: Context, jobs, want_grad: bool = False):
+        self._ctx = ctx
+        self._grad = 1 if want_grad else 0
+        self._arr, self._keep = ctx._host_job_array(jobs, want_grad)
+        self._n = len(jobs)
+
+    def run(self):
+        c = self._ctx
+        c._check(c._lib.qaoa_expectation_batched_host(c._h, self._n, self._arr, self._grad))
+
+
 def _rounds(mixer, n_angles: int) -> int:
     """p from the length of one angle set."""
     if hasattr(mixer, "rounds"):
@@ -682,6 +746,10 @@ def qaoa_gradient(ctx: Context, *args, **kw):
 
 def qaoa_expectation_batched(ctx: Context, *args, **kw):
     return ctx.expectation_batched(*args, **kw)
+
+
+def qaoa_expectation_batched_host(ctx: Context, *args, **kw):
+    return ctx.expectation_batched_host(*args, **kw)
 
 
 def qaoa_gradient_small_noalloc(cost: torch.Tensor, n: int, angles: torch.Tensor, E: torch.Tensor,

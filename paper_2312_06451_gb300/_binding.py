@@ -44,6 +44,12 @@ class QaoaJob(ctypes.Structure):
                 ("d_grad", c_void_p), ("d_init", c_void_p)]
 
 
+class QaoaHostJob(ctypes.Structure):
+    _fields_ = [("d_cost", c_void_p), ("cost_dtype", c_int), ("mixer", ctypes.POINTER(QaoaMixer)),
+                ("p", c_int), ("n_sets", c_int), ("h_angles", c_void_p), ("h_E", c_void_p),
+                ("h_grad", c_void_p), ("d_init", c_void_p)]
+
+
 class QaoaXTune(ctypes.Structure):
     _fields_ = [("n", c_int), ("cost_dtype", c_int), ("cmin", c_int), ("split", c_int),
                 ("nbuf_bwd_contig", c_int), ("nbuf_bwd_gather", c_int), ("ms", c_double)]
@@ -69,6 +75,7 @@ SIGNATURES = {
     "qaoa_gradient": (c_int, [c_void_p, c_void_p, c_int, ctypes.POINTER(QaoaMixer), c_void_p, c_int,
                               c_void_p, c_void_p, c_void_p, c_int]),
     "qaoa_expectation_batched": (c_int, [c_void_p, c_int, ctypes.POINTER(QaoaJob), c_int]),
+    "qaoa_expectation_batched_host": (c_int, [c_void_p, c_int, ctypes.POINTER(QaoaHostJob), c_int]),
     "qaoa_set_profiling": (c_int, [c_void_p, c_int]),
     "qaoa_kernel_stats": (c_int, [c_void_p, ctypes.POINTER(QaoaKernelStat), c_int]),
     "qaoa_reset_stats": (None, [c_void_p]),

@@ -2517,6 +2517,70 @@ qaoa_status qaoa_expectation_batched(qaoa_ctx *ctx, int n_jobs, const qaoa_job *
     }
 }
 
+qaoa_status qaoa_expectation_batched_host(qaoa_ctx *ctx, int n_jobs, const qaoa_host_job *jobs, int want_grad) {
+    NvtxRange nvtx_range("qaoa_expectation_batched_host");
+    if (!ctx) return QAOA_ERR_INVALID;
+    try {
+        ctx->err.clear();
+        if (n_jobs < 1 || !jobs) return fail(ctx, QAOA_ERR_INVALID, "no jobs");
+        if (capturing(ctx)) return fail(ctx, QAOA_ERR_INVALID, "the host-buffer call synchronises; do not capture it");
+        cudaSetDevice(ctx->device);
+        // device staging, job after job: angles, <C>, gradients
+        std::vector<int64_t> na(n_jobs);
+        size_t total = 0;
+        for (int j = 0; j < n_jobs; j++) {
+            const qaoa_host_job &jb = jobs[j];
+            if (!jb.mixer) return fail(ctx, QAOA_ERR_INVALID, "job %d: mixer is NULL", j);
+            if (jb.p < 1 || jb.p > 4096) return fail(ctx, QAOA_ERR_INVALID, "job %d: p must be in [1, 4096]", j);
+            if (jb.n_sets < 1 || !jb.h_angles || !jb.h_E || (want_grad && !jb.h_grad))
+                return fail(ctx, QAOA_ERR_INVALID, "job %d: bad sets or host pointers", j);
+            na[j] = jb.mixer->kind == QAOA_MIXER_X_MA ? (int64_t)jb.p * (jb.mixer->n + 1) : 2 * (int64_t)jb.p;
+            total += (size_t)jb.n_sets * (size_t)(na[j] * (want_grad ? 2 : 1) + 1);
+        }
+        void *stage = nullptr;
+        qaoa_status st = scratch(ctx, "host_io", total * sizeof(double), &stage);
+        if (st) return st;
+        std::vector<qaoa_job> dj(n_jobs);
+        double *cur = static_cast<double *>(stage);
+        for (int j = 0; j < n_jobs; j++) {
+            const qaoa_host_job &jb = jobs[j];
+            const int64_t ns = jb.n_sets, a = ns * na[j];
+            qaoa_job &d = dj[j];
+            d.d_cost = jb.d_cost;
+            d.cost_dtype = jb.cost_dtype;
+            d.mixer = jb.mixer;
+            d.p = jb.p;
+            d.n_sets = jb.n_sets;
+            d.d_angles = cur;
+            d.d_E = cur + a;
+            d.d_grad = want_grad ? cur + a + ns : nullptr;
+            d.d_init = jb.d_init;
+            QG_CUDA(ctx, cudaMemcpyAsync(cur, jb.h_angles, (size_t)a * sizeof(double), cudaMemcpyHostToDevice,
+                                         ctx->stream),
+                    "angle upload");
+            cur += a + ns + (want_grad ? a : 0);
+        }
+        st = qaoa_expectation_batched(ctx, n_jobs, dj.data(), want_grad);
+        if (st) {
+            cudaStreamSynchronize(ctx->stream);  // the uploads read the caller's buffers
+            return st;
+        }
+        for (int j = 0; j < n_jobs; j++) {
+            const qaoa_host_job &jb = jobs[j];
+            QG_CUDA(ctx, cudaMemcpyAsync(jb.h_E, dj[j].d_E, (size_t)jb.n_sets * sizeof(double),
+                                         cudaMemcpyDeviceToHost, ctx->stream),
+                    "result download");
+            if (want_grad)
+                QG_CUDA(ctx, cudaMemcpyAsync(jb.h_grad, dj[j].d_grad, (size_t)jb.n_sets * na[j] * sizeof(double),
+                                             cudaMemcpyDeviceToHost, ctx->stream),
+                        "gradient download");
+        }
+        return read_dev_err(ctx);  // synchronises the stream
+    } catch (...) {
+        return fail(ctx, QAOA_ERR_OOM, "host allocation failed");
+    }
+}
+
 qaoa_status qaoa_cost_degeneracy(qaoa_ctx *ctx, const qaoa_problem *prob, int64_t *d_counts, int n_bins) {
     NvtxRange nvtx_range("qaoa_cost_degeneracy");
     if (!ctx) return QAOA_ERR_INVALID;
