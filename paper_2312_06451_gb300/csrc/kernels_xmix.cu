@@ -887,7 +887,11 @@ __device__ __forceinline__ void set_round(PassConst &K, const RoundCoef &cf, flo
 // 3 -> 2 -> 1 through the inverse transposes, and the result is stored from
 // the stage-1 (load) layout as 16-byte pairs.  KA is the round applied first
 // (forward: k; adjoint: k+1), KB the second; KP holds the phase (round k+1).
-template <int BWD, int COST, int NBUF, int MA, int MB>
+// PAT fixes the stages' active-qubit masks at compile time for the two groups
+// the default schedules use most: 1 = all twelve tile bits (the contiguous
+// group), 2 = tile bits 4..11 (a gathered group with four contiguous bits);
+// 0 takes them from the descriptor.
+template <int BWD, int COST, int NBUF, int MA, int MB, int PAT>
 __device__ __forceinline__ void tile_body_fused_impl(const PassConst &KA, const PassConst &KB, const PassConst &KP,
                                                 uint32_t g1, const uint32_t (&rs1)[3],
                                                 const PassDesc &D, const float2 *stab, unsigned char *bufs, int b,
@@ -908,8 +912,9 @@ __device__ __forceinline__ void tile_body_fused_impl(const PassConst &KA, const 
     const unsigned char *scost = bufs + b * G::kBufB + G::kPsiB * (BWD ? 2 : 1);
     float2 a[16], l[16];
     float pscale = 1.f, bA = 0.f, bB = 0.f, eacc = 0.f;
-    const uint32_t m1 = stage_mask(active, 0, 9, 10, 11), m2 = stage_mask(active, 1, 2, 3, 4),
-                   m3 = stage_mask(active, 5, 6, 7, 8);
+    const uint32_t m1 = PAT == 1 ? 0xFu : PAT == 2 ? 0xEu : stage_mask(active, 0, 9, 10, 11),
+                   m2 = PAT == 1 ? 0xFu : PAT == 2 ? 0x8u : stage_mask(active, 1, 2, 3, 4),
+                   m3 = PAT != 0 ? 0xFu : stage_mask(active, 5, 6, 7, 8);
 
     // ---------------- stage 1: read the landed tile
 #pragma unroll
@@ -1064,10 +1069,11 @@ __device__ __forceinline__ void tile_body_fused_impl(const PassConst &KA, const 
     }
 }
 
-// The common case (both rounds in the tan form) inline; the direct form
-// (|cos b| tiny, rare) out of line, so that its extra registers do not set
-// the register allocation of the common path.
-template <int BWD, int COST, int NBUF, int MA, int MB>
+// The common case (both rounds in the tan form, a mask pattern known at
+// compile time) inline; the direct form (|cos b| tiny, rare) and other
+// groups out of line, so that their registers do not set the register
+// allocation of the common path.
+template <int BWD, int COST, int NBUF, int MA, int MB, int PAT>
 __device__ __forceinline__ void tile_body_fused(const PassConst &KA, const PassConst &KB, const PassConst &KP,
                                                 uint32_t g1, const uint32_t (&rs1)[3],
                                                 const PassDesc &D, const float2 *stab, unsigned char *bufs, int b,
@@ -1075,8 +1081,8 @@ __device__ __forceinline__ void tile_body_fused(const PassConst &KA, const PassC
                                                 uint32_t tl, TileInfo *tinfo, const PassDesc *__restrict__ descs,
                                                 const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor,
                                                 const uint32_t *s_tr) {
-    tile_body_fused_impl<BWD, COST, NBUF, MA, MB>(KA, KB, KP, g1, rs1, D, stab, bufs, b, bar, sched, total, base, tl,
-                                                  tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+    tile_body_fused_impl<BWD, COST, NBUF, MA, MB, PAT>(KA, KB, KP, g1, rs1, D, stab, bufs, b, bar, sched, total,
+                                                       base, tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
 }
 template <int BWD, int COST, int NBUF, int MA, int MB>
 __device__ __noinline__ void tile_body_fused_rare(const PassConst &KA, const PassConst &KB, const PassConst &KP,
@@ -1086,8 +1092,8 @@ __device__ __noinline__ void tile_body_fused_rare(const PassConst &KA, const Pas
                                                   uint32_t tl, TileInfo *tinfo, const PassDesc *__restrict__ descs,
                                                   const uint32_t *__restrict__ tile_begin, int ndesc, int &cursor,
                                                   const uint32_t *s_tr) {
-    tile_body_fused_impl<BWD, COST, NBUF, MA, MB>(KA, KB, KP, g1, rs1, D, stab, bufs, b, bar, sched, total, base, tl,
-                                                  tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+    tile_body_fused_impl<BWD, COST, NBUF, MA, MB, 0>(KA, KB, KP, g1, rs1, D, stab, bufs, b, bar, sched, total, base,
+                                                     tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
 }
 
 template <int BWD, int COST, int NBUF, int VAR, int FUSED>
@@ -1221,9 +1227,18 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
             // forward: round k then round k+1; adjoint: k+1 first; the phase is round k+1's
             const PassConst &KA = s_kf[BWD ? 1 : 0], &KB = s_kf[BWD ? 0 : 1], &KP = s_kf[1];
             const int mk = (KA.R.mode == 0 ? 0 : 1) | (KB.R.mode == 0 ? 0 : 2);
-            if (mk == 0)
-                tile_body_fused<BWD, COST, NBUF, 0, 0>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched, total,
-                                                       ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+            if (mk == 0 && KA.active == 0xFFFu)
+                tile_body_fused<BWD, COST, NBUF, 0, 0, 1>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched,
+                                                          total, ti.base, ti.tl, tinfo, descs, tile_begin, ndesc,
+                                                          cursor, s_tr);
+            else if (mk == 0 && KA.active == 0xFF0u)
+                tile_body_fused<BWD, COST, NBUF, 0, 0, 2>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched,
+                                                          total, ti.base, ti.tl, tinfo, descs, tile_begin, ndesc,
+                                                          cursor, s_tr);
+            else if (mk == 0)
+                tile_body_fused_rare<BWD, COST, NBUF, 0, 0>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched,
+                                                            total, ti.base, ti.tl, tinfo, descs, tile_begin, ndesc,
+                                                            cursor, s_tr);
             else if (mk == 1)
                 tile_body_fused_rare<BWD, COST, NBUF, 2, 0>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched,
                                                             total, ti.base, ti.tl, tinfo, descs, tile_begin, ndesc,
