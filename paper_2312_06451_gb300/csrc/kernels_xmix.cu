@@ -544,8 +544,11 @@ struct PassConst {
 // MODE is the rotation form (0 tan, 2 direct); the two forms are separate
 // copies of this body so the common one stays compact in the instruction
 // cache.  Optional work (initial state, phase, epilogue) sits in loops of its
-// own that are skipped as a whole when a pass does not need them.
-template <int BWD, int COST, int NBUF, int MODE, int VAR>
+// own that are skipped as a whole when a pass does not need them.  PAT fixes
+// the stages' active-qubit masks at compile time as in the round-boundary
+// body (1: all twelve tile bits, 2: tile bits 4..11, 0: from the descriptor);
+// the forward passes use it, the adjoint ones would spill.
+template <int BWD, int COST, int NBUF, int MODE, int VAR, int PAT>
 __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D, const float2 *stab,
                                           const float4 *s_rot, const float4 *s_w,
                                           unsigned char *bufs, int b, uint32_t bar, uint32_t *sched, int cost_free,
@@ -561,6 +564,9 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     const uint32_t l3 = (uint32_t)lane | ((uint32_t)warp << 9);
     const uint32_t p1 = swz(l1), p2 = swz(l2), p3 = swz(l3);
     const uint32_t flags = K.flags, active = K.active;
+    const uint32_t m1 = PAT == 1 ? 0xFu : PAT == 2 ? 0xEu : stage_mask(active, 0, 9, 10, 11),
+                   m2 = PAT == 1 ? 0xFu : PAT == 2 ? 0x8u : stage_mask(active, 1, 2, 3, 4),
+                   m3 = PAT != 0 ? 0xFu : stage_mask(active, 5, 6, 7, 8);
     // warp 0: claim the next tile for this buffer and start its loads
     auto claim_issue = [&]() {
         uint32_t tn = 0;
@@ -665,7 +671,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
         }
     }
     if constexpr (MA) stage_rot_ma<BWD, MODE, 0, 9, 10, 11>(a, l, stage_mask(active, 0, 9, 10, 11), s_rot, bq, pscale, true);
-    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 0, 9, 10, 11), K.R, pscale, bacc, true, !GM);
+    else stage_rot<BWD, MODE>(a, l, m1, K.R, pscale, bacc, true, !GM);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs1);
         pscale = 1.f;
@@ -698,7 +704,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
         if (warp == 0) claim_issue();
     }
     if constexpr (MA) stage_rot_ma<BWD, MODE, 1, 2, 3, 4>(a, l, stage_mask(active, 1, 2, 3, 4), s_rot, bq, pscale, true);
-    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 1, 2, 3, 4), K.R, pscale, bacc, true, !GM);
+    else stage_rot<BWD, MODE>(a, l, m2, K.R, pscale, bacc, true, !GM);
     if (K.rescale) {
         scale_all<BWD>(a, l, K.fs2);
         pscale = 1.f;
@@ -778,7 +784,7 @@ __device__ __forceinline__ void tile_body(const PassConst &K, const PassDesc &D,
     // phase epilogue (the adjoint with per-pass checkpoints stores lambda only)
     const bool psi_live = !BWD || D.psi_out != nullptr || (flags & PF_PHASE) || (GM && (flags & PF_WDIAG));
     if constexpr (MA) stage_rot_ma<BWD, MODE, 5, 6, 7, 8>(a, l, stage_mask(active, 5, 6, 7, 8), s_rot, bq, pscale, psi_live);
-    else stage_rot<BWD, MODE>(a, l, stage_mask(active, 5, 6, 7, 8), K.R, pscale, bacc, psi_live, !GM);
+    else stage_rot<BWD, MODE>(a, l, m3, K.R, pscale, bacc, psi_live, !GM);
     scale_all<BWD>(a, l, K.rescale ? K.fs3 : K.fse);
     if (GM && BWD && (flags & PF_WDIAG)) {
         // general X mixer: the beta partial sum_x G(|x|) Im(conj(lam) psi) in
@@ -1251,18 +1257,31 @@ xpass_kernel(const PassDesc *__restrict__ descs, const uint32_t *__restrict__ ti
                 tile_body_fused_rare<BWD, COST, NBUF, 2, 2>(KA, KB, KP, K.g1, K.rs1, D, stab, bufs, b, bar, sched,
                                                             total, ti.base, ti.tl, tinfo, descs, tile_begin, ndesc,
                                                             cursor, s_tr);
+        } else if constexpr (VAR == 0 && !BWD) {  // (adjoint copies spill: measured slower)
+            if (K.R.mode == 0 && K.active == 0xFFFu)
+                tile_body<BWD, COST, NBUF, 0, 0, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total,
+                                                    ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+            else if (K.R.mode == 0 && K.active == 0xFF0u)
+                tile_body<BWD, COST, NBUF, 0, 0, 2>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total,
+                                                    ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+            else if (K.R.mode == 0)
+                tile_body<BWD, COST, NBUF, 0, 0, 0>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total,
+                                                    ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+            else
+                tile_body<BWD, COST, NBUF, 2, 0, 0>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total,
+                                                    ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
         } else if (VAR == 1 && K.R.mode == 0)
-            tile_body<BWD, COST, NBUF, 0, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base, ti.tl,
-                                             tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+            tile_body<BWD, COST, NBUF, 0, 1, 0>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base,
+                                                ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
         else if (VAR == 1)
-            tile_body<BWD, COST, NBUF, 2, 1>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base, ti.tl,
-                                             tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+            tile_body<BWD, COST, NBUF, 2, 1, 0>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base,
+                                                ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
         else if (K.R.mode == 0)
-            tile_body<BWD, COST, NBUF, 0, VAR>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base, ti.tl,
-                                             tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+            tile_body<BWD, COST, NBUF, 0, VAR, 0>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total,
+                                                  ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
         else
-            tile_body<BWD, COST, NBUF, 2, VAR>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total, ti.base, ti.tl,
-                                             tinfo, descs, tile_begin, ndesc, cursor, s_tr);
+            tile_body<BWD, COST, NBUF, 2, VAR, 0>(K, D, stab, s_rot, s_w, bufs, b, bar, sched, cost_free, total,
+                                                  ti.base, ti.tl, tinfo, descs, tile_begin, ndesc, cursor, s_tr);
     }
 }
 
