@@ -359,6 +359,22 @@ class Workload:
             out[n] = {k: t[k] for k in ("cmin", "split", "nbuf_bwd_contig", "nbuf_bwd_gather")}
         return out
 
+    def pin_schedule(self, split):
+        """Install the pass schedule (cmin 4, the given split) for every
+        X-mixer problem size in the workload; returns {n: schedule}."""
+        import torch
+
+        out = {}
+        for job in self.jobs:
+            n = job["mixer"].n
+            if not isinstance(job["mixer"], self.qg.XMixer) or n <= 12 or n in out:
+                continue
+            t = {"n": n, "cost_dtype": 0 if job["cost"].dtype == torch.float32 else 1, "cmin": 4, "split": split,
+                 "nbuf_bwd_contig": 1, "nbuf_bwd_gather": 1}
+            self.ctx.set_tuning(t)
+            out[n] = {k: t[k] for k in ("cmin", "split", "nbuf_bwd_contig", "nbuf_bwd_gather")}
+        return out
+
     def _add_job(self, cost, n, A, n_sets):
         import torch
 
@@ -700,7 +716,11 @@ def measure(args, W, qg, ctx, stream, dist, ws, rank, local, dev, graph_mode, st
     steps end to end from pinned host angles to host results."""
     import torch
 
-    if not args.no_autotune:
+    if args.split is not None:
+        sched = W.pin_schedule(args.split)
+        if sched:
+            W.run_info["schedule"] = sched if len(sched) > 1 else next(iter(sched.values()))
+    elif not args.no_autotune:
         sched = W.autotune()
         if sched:
             W.run_info["schedule"] = sched if len(sched) > 1 else next(iter(sched.values()))
@@ -986,6 +1006,9 @@ def main():
                          "workload 4: clique instead of ring XY mixer")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default X-mixer pass schedule instead of tuning it before the warm-up")
+    ap.add_argument("--split", type=int, default=None, choices=[0, 1, 2],
+                    help="pin the X-mixer pass schedule's chunk order (0 equal chunks, 1 full chunks first, "
+                         "2 remainder first) at the minimum contiguous run of 4, instead of tuning it")
     ap.add_argument("--no-batched", action="store_true",
                     help="default workload only: skip the batched sub-record (uneven 512-instance batch)")
     ap.add_argument("--no-grover", action="store_true",
