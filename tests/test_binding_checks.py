@@ -131,3 +131,21 @@ def test_tuning_file_round_trip_and_damage(tmp_path):
     json.dump(doc, open(path, "w"))
     with pytest.raises(ValueError, match="version"):
         qg.read_tuning_file(path)
+
+
+def test_host_buffers_of_the_host_batched_call():
+    """The host-buffer batched call takes contiguous float64 host tensors or
+    arrays (wrapped, not copied) and refuses anything else before marshalling."""
+    import numpy as np
+
+    from paper_2312_06451_gb300 import _host_tensor
+
+    a = np.arange(12, dtype=np.float64).reshape(3, 4)
+    t = _host_tensor(a, "angles")
+    assert t.data_ptr() == a.ctypes.data  # the caller's memory, no copy
+    assert _host_tensor(None, "grad") is None
+    assert _host_tensor(torch.zeros(5, dtype=torch.float64), "E").numel() == 5
+    for bad in (a.astype(np.float32), a[:, ::2], torch.zeros(4, dtype=torch.float32),
+                torch.zeros(4, 4, dtype=torch.float64).t(), [0.0, 1.0]):
+        with pytest.raises(ValueError):
+            _host_tensor(bad, "angles")
