@@ -133,3 +133,42 @@ def test_host_batched_errors_leave_the_context_usable(Q, oracle_mod):
     for s in range(2):
         E_ref = oracle_mod.qaoa_expectation(n, c, A[s])
         assert abs(E[s] - E_ref) <= 1e-5 * max(abs(E_ref), sigma(c))
+
+
+def test_host_batched_other_mixers(Q, oracle_mod):
+    """A Grover job (rank-one passes, float32 SK cost) and a block-diagonal
+    ring XY job (tensor-core products, DkS cost on the weight-4 states) in one
+    host-buffer call: the device-buffer call's numbers bit for bit, and the
+    oracle's."""
+    qg, ctx = Q
+    n1, p1 = 16, 3
+    J = sk_couplings(n1, 81)
+    cost1 = ctx.cost_precompute("sk", n1, J=J, dtype=torch.float32)
+    c1 = oracle_mod.cost_sk(n1, J.astype(np.float64))
+    A1 = uniform_angles(p1, 82, 3)
+    n2, k2, p2 = 10, 4, 2
+    e2 = erdos_renyi(n2, 0.5, 83)
+    st2 = oracle_mod.dicke_states(n2, k2)
+    c2 = oracle_mod.cost_dks(n2, e2, st2)
+    cost2 = ctx.cost_precompute("dks", n2, edges=e2, k=k2, dtype=torch.uint8)
+    A2 = uniform_angles(p2, 84, 4)
+    specs = [(cost1, qg.GroverMixer.full(n1), A1), (cost2, qg.xy_sym_mixer(ctx, "ring", n2, k2), A2)]
+    host = [{"cost": c, "mixer": m, "angles": torch.from_numpy(A.copy()).pin_memory(),
+             "E": torch.zeros(A.shape[0], dtype=torch.float64).pin_memory(),
+             "grad": torch.zeros(A.shape, dtype=torch.float64).pin_memory()} for c, m, A in specs]
+    dev = [{"cost": c, "mixer": m, "angles": torch.from_numpy(A).cuda(),
+            "E": torch.zeros(A.shape[0], dtype=torch.float64, device="cuda"),
+            "grad": torch.zeros(A.shape, dtype=torch.float64, device="cuda")} for c, m, A in specs]
+    ctx.expectation_batched_host(host, want_grad=True)
+    ctx.expectation_batched(dev, want_grad=True)
+    torch.cuda.synchronize()
+    for hj, dj in zip(host, dev):
+        assert torch.equal(hj["E"], dj["E"].cpu()) and torch.equal(hj["grad"], dj["grad"].cpu())
+    for s in range(A1.shape[0]):
+        E_ref, g_ref = oracle_mod.qaoa_gradient(n1, c1, A1[s], "grover")
+        assert abs(host[0]["E"][s].item() - E_ref) <= 1e-5 * max(abs(E_ref), sigma(c1))
+        np.testing.assert_allclose(host[0]["grad"][s].numpy(), g_ref, rtol=0, atol=1e-4 * np.abs(g_ref).max())
+    for s in range(A2.shape[0]):
+        E_ref, g_ref = oracle_mod.qaoa_gradient(n2, c2, A2[s], "ring", st2)
+        assert abs(host[1]["E"][s].item() - E_ref) <= 1e-5 * max(abs(E_ref), sigma(c2))
+        np.testing.assert_allclose(host[1]["grad"][s].numpy(), g_ref, rtol=0, atol=1e-4 * np.abs(g_ref).max())
